@@ -1,0 +1,282 @@
+"""ctypes wrapper around the C++ CPU oracle (``cga_oracle.cpp``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` load this module; the CUDA library and its
+Python binding never do.  The oracle computes the plain definitions of the
+paper's CGA operations (Sec. III arrays, Eq. 1 merge, Eq. 3 projection,
+Eq. 7-8 nearest neighbour) with std::sort / std::unique / std::set_union and
+exhaustive search.
+
+Parity pinned: tests/test_oracle_*.py pin every function against hand fixtures
+(tests/golden/), closed forms, invariants and independent numpy routines.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cga_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_NONFINITE = -2
+
+U32_MAX = 0xFFFFFFFF
+U64_MAX = 0xFFFFFFFFFFFFFFFF
+
+
+def compile_oracle(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (g++, no fused mul-add)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "cga_oracle.h"))
+    ):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(
+            ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-shared", "-fPIC",
+             "-o", tmp, _SRC]
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Cga(ctypes.Structure):
+    _fields_ = [
+        ("bits", ctypes.c_uint32),
+        ("h", ctypes.c_uint64),
+        ("g", ctypes.c_uint64),
+        ("u", ctypes.c_uint64),
+        ("X_index", ctypes.c_void_p),
+        ("X_pointer", ctypes.c_void_p),
+        ("Y_index", ctypes.c_void_p),
+        ("Y_pointer", ctypes.c_void_p),
+        ("Z_index", ctypes.c_void_p),
+    ]
+
+
+class _Cga2d(ctypes.Structure):
+    _fields_ = [
+        ("bits", ctypes.c_uint32),
+        ("h", ctypes.c_uint64),
+        ("g", ctypes.c_uint64),
+        ("U_index", ctypes.c_void_p),
+        ("U_pointer", ctypes.c_void_p),
+        ("V_index", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(compile_oracle())
+        P = ctypes.c_void_p
+        U32, U64, F = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_float
+        _lib.orc_grid_from_box.argtypes = [P, F, U32, P, P]
+        _lib.orc_quantize.argtypes = [P, U64, U32, F, P, P, P]
+        _lib.orc_from_sorted_keys.argtypes = [P, U64, U32, ctypes.POINTER(_Cga)]
+        _lib.orc_build.argtypes = [P, U64, U32, F, P, P, ctypes.POINTER(_Cga)]
+        _lib.orc_decode.argtypes = [ctypes.POINTER(_Cga), P]
+        _lib.orc_decode_keys.argtypes = [ctypes.POINTER(_Cga), P]
+        _lib.orc_lookup.argtypes = [ctypes.POINTER(_Cga), U32, U32, U32]
+        _lib.orc_lookup.restype = ctypes.c_int64
+        _lib.orc_merge.argtypes = [ctypes.POINTER(_Cga), ctypes.POINTER(_Cga),
+                                   ctypes.POINTER(_Cga)]
+        _lib.orc_project.argtypes = [ctypes.POINTER(_Cga), ctypes.c_int,
+                                     ctypes.POINTER(_Cga2d)]
+        for fn in (_lib.orc_nn_brute, _lib.orc_nn_window):
+            fn.argtypes = [ctypes.POINTER(_Cga), F, P, P, U64, P, P]
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Grid:
+    bits: int
+    scale: float  # float32 value held in a Python float
+    offset: tuple  # three float32 values
+
+    def offset_array(self) -> np.ndarray:
+        return np.asarray(self.offset, dtype=np.float32)
+
+
+@dataclass
+class Cga:
+    """Host copy of the five geometry arrays of a CGA."""
+    bits: int
+    X_index: np.ndarray
+    X_pointer: np.ndarray
+    Y_index: np.ndarray
+    Y_pointer: np.ndarray
+    Z_index: np.ndarray
+
+    @property
+    def h(self):
+        return len(self.X_index)
+
+    @property
+    def g(self):
+        return len(self.Y_index)
+
+    @property
+    def u(self):
+        return len(self.Z_index)
+
+    def nbytes(self) -> int:
+        return 2 * self.h + 4 * (self.h + 1) + 2 * self.g + 4 * (self.g + 1) + 2 * self.u
+
+    def _struct(self):
+        # keep contiguous arrays alive on the instance while the struct is used
+        self._keep = [np.ascontiguousarray(a) for a in (
+            self.X_index, self.X_pointer, self.Y_index, self.Y_pointer, self.Z_index)]
+        k = self._keep
+        return _Cga(self.bits, self.h, self.g, self.u,
+                    _ptr(k[0]), _ptr(k[1]), _ptr(k[2]), _ptr(k[3]), _ptr(k[4]))
+
+
+@dataclass
+class Cga2d:
+    bits: int
+    U_index: np.ndarray
+    U_pointer: np.ndarray
+    V_index: np.ndarray
+
+
+def _empty_out(bits: int, cap: int):
+    arrs = (np.zeros(cap, np.uint16), np.zeros(cap + 1, np.uint32),
+            np.zeros(cap, np.uint16), np.zeros(cap + 1, np.uint32),
+            np.zeros(cap, np.uint16))
+    s = _Cga(bits, 0, 0, 0, *(_ptr(a) for a in arrs))
+    return s, arrs
+
+
+def _from_struct(s: _Cga, arrs) -> Cga:
+    h, g, u = s.h, s.g, s.u
+    return Cga(s.bits, arrs[0][:h].copy(), arrs[1][:h + 1].copy(), arrs[2][:g].copy(),
+               arrs[3][:g + 1].copy(), arrs[4][:u].copy())
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code):
+        super().__init__(f"oracle error {code}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != OK:
+        raise OracleError(rc)
+
+
+def grid_from_box(lo, extent: float, bits: int) -> Grid:
+    lo = np.asarray(lo, dtype=np.float32)
+    scale = np.zeros(1, np.float32)
+    off = np.zeros(3, np.float32)
+    _check(lib().orc_grid_from_box(_ptr(lo), float(np.float32(extent)), bits,
+                                   _ptr(scale), _ptr(off)))
+    return Grid(bits, float(scale[0]), tuple(float(v) for v in off))
+
+
+def _f32xyz(xyz) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(xyz, dtype=np.float32).reshape(-1, 3))
+    return a
+
+
+def _xform(xform):
+    if xform is None:
+        return None, None
+    x = np.ascontiguousarray(np.asarray(xform, dtype=np.float32).reshape(12))
+    return x, _ptr(x)
+
+
+def quantize(xyz, grid: Grid, xform=None) -> np.ndarray:
+    p = _f32xyz(xyz)
+    keys = np.zeros(len(p), np.uint64)
+    x, xp = _xform(xform)
+    off = grid.offset_array()
+    _check(lib().orc_quantize(_ptr(p), len(p), grid.bits, grid.scale, _ptr(off), xp,
+                              _ptr(keys)))
+    return keys
+
+
+def from_sorted_keys(keys, bits: int) -> Cga:
+    k = np.ascontiguousarray(np.asarray(keys, dtype=np.uint64))
+    s, arrs = _empty_out(bits, len(k))
+    _check(lib().orc_from_sorted_keys(_ptr(k), len(k), bits, ctypes.byref(s)))
+    return _from_struct(s, arrs)
+
+
+def build(xyz, grid: Grid, xform=None) -> Cga:
+    p = _f32xyz(xyz)
+    s, arrs = _empty_out(grid.bits, len(p))
+    x, xp = _xform(xform)
+    off = grid.offset_array()
+    _check(lib().orc_build(_ptr(p), len(p), grid.bits, grid.scale, _ptr(off), xp,
+                           ctypes.byref(s)))
+    return _from_struct(s, arrs)
+
+
+def decode(a: Cga) -> np.ndarray:
+    out = np.zeros((a.u, 3), np.uint32)
+    s = a._struct()
+    _check(lib().orc_decode(ctypes.byref(s), _ptr(out)))
+    return out
+
+
+def decode_keys(a: Cga) -> np.ndarray:
+    out = np.zeros(a.u, np.uint64)
+    s = a._struct()
+    _check(lib().orc_decode_keys(ctypes.byref(s), _ptr(out)))
+    return out
+
+
+def lookup(a: Cga, x: int, y: int, z: int) -> int:
+    s = a._struct()
+    return int(lib().orc_lookup(ctypes.byref(s), x, y, z))
+
+
+def merge(a: Cga, b: Cga) -> Cga:
+    sa, sb = a._struct(), b._struct()
+    s, arrs = _empty_out(a.bits, a.u + b.u)
+    _check(lib().orc_merge(ctypes.byref(sa), ctypes.byref(sb), ctypes.byref(s)))
+    return _from_struct(s, arrs)
+
+
+PLANES = {"xy": 0, "xz": 1, "yz": 2}
+
+
+def project(a: Cga, plane) -> Cga2d:
+    p = PLANES[plane] if isinstance(plane, str) else int(plane)
+    sa = a._struct()
+    cap = a.u
+    arrs = (np.zeros(cap, np.uint16), np.zeros(cap + 1, np.uint32), np.zeros(cap, np.uint16))
+    s = _Cga2d(a.bits, 0, 0, *(_ptr(x) for x in arrs))
+    _check(lib().orc_project(ctypes.byref(sa), p, ctypes.byref(s)))
+    return Cga2d(a.bits, arrs[0][:s.h].copy(), arrs[1][:s.h + 1].copy(), arrs[2][:s.g].copy())
+
+
+def _nn(fn, a: Cga, grid: Grid, q):
+    qa = _f32xyz(q)
+    idx = np.zeros(len(qa), np.uint32)
+    d2 = np.zeros(len(qa), np.uint64)
+    s = a._struct()
+    off = grid.offset_array()
+    _check(fn(ctypes.byref(s), grid.scale, _ptr(off), _ptr(qa), len(qa), _ptr(idx), _ptr(d2)))
+    return idx, d2
+
+
+def nn_brute(a: Cga, grid: Grid, q):
+    return _nn(lib().orc_nn_brute, a, grid, q)
+
+
+def nn_window(a: Cga, grid: Grid, q):
+    return _nn(lib().orc_nn_window, a, grid, q)

@@ -1,0 +1,108 @@
+/*
+ * CPU oracle for the compressed-geometric-array (CGA) hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This plain, slow, single-threaded C++17 code is
+ * the reference the CUDA library is checked against.  It shares no code,
+ * header, table or helper with the CUDA path, and only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg may load it.  The product path
+ * never calls it and has no CPU fallback.
+ *
+ * Every function states the passage of the paper it follows ("Compressed
+ * Geometric Arrays for Point Cloud Processing", Roodaki & Nazm Bojnordi):
+ *   Sec. III (CGA arrays and their recurrences), Sec. III-A (point lookup and
+ *   merge), Sec. III-B (projection), Sec. III-C (NN search), Eq. 1 (merge as a
+ *   set union), Eq. 3 (orthogonal projection), Eq. 7-8 (Euclidean distance and
+ *   the NN set), Sec. II-E-2-a (bounding box including all points).
+ *
+ * Parity pinned: every function here is pinned by the not-gpu tests against
+ * hand-written fixtures, closed forms, invariants and independent library
+ * routines (numpy set/sort routines, exhaustive search).
+ */
+#ifndef CGA_ORACLE_H
+#define CGA_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_OK 0
+#define ORC_ERR_INVALID_ARG (-1)
+#define ORC_ERR_NONFINITE (-2)
+
+/* A CGA as six-array storage minus the attribute (Value) array: caller-owned
+ * host buffers.  Sizes: h = |X_index|, g = |Y_index|, u = |Z_index|;
+ * X_pointer has h+1 entries and Y_pointer g+1 entries. */
+typedef struct {
+  uint32_t bits;
+  uint64_t h, g, u;
+  uint16_t* X_index;
+  uint32_t* X_pointer;
+  uint16_t* Y_index;
+  uint32_t* Y_pointer;
+  uint16_t* Z_index;
+} orc_cga;
+
+/* 2-level CGA of a projection onto a coordinate plane: U_index (distinct
+ * first kept coordinate), U_pointer (h2+1), V_index (g2). */
+typedef struct {
+  uint32_t bits;
+  uint64_t h, g;
+  uint16_t* U_index;
+  uint32_t* U_pointer;
+  uint16_t* V_index;
+} orc_cga2d;
+
+/* Grid from a cubic box with lower corner lo[] and edge length extent:
+ * scale = 2^bits / extent, offset[a] = -(lo[a] * scale), all in float. */
+int orc_grid_from_box(const float lo[3], float extent, uint32_t bits,
+                      float* scale, float offset[3]);
+
+/* Quantize + encode: keys[i] = x << 2b | y << b | z.  xform12 (nullable) is
+ * R (3x3 row-major) followed by t (3). */
+int orc_quantize(const float* xyz, uint64_t n, uint32_t bits, float scale,
+                 const float offset[3], const float* xform12, uint64_t* keys);
+
+/* CGA arrays from a sorted, duplicate-free key list (Sec. III recurrences).
+ * Output buffers must hold u entries (X_pointer/Y_pointer u+1). */
+int orc_from_sorted_keys(const uint64_t* keys, uint64_t u, uint32_t bits,
+                         orc_cga* out);
+
+/* Build: quantize, sort, drop duplicates, arrays.  Buffers hold n (n+1). */
+int orc_build(const float* xyz, uint64_t n, uint32_t bits, float scale,
+              const float offset[3], const float* xform12, orc_cga* out);
+
+/* Decode to (x, y, z) uint32 triples in CGA order (u * 3 entries). */
+int orc_decode(const orc_cga* a, uint32_t* xyz);
+
+/* Decode to keys in CGA order (u entries). */
+int orc_decode_keys(const orc_cga* a, uint64_t* keys);
+
+/* Point lookup (Sec. III-A): index in CGA point order, or -1. */
+int64_t orc_lookup(const orc_cga* a, uint32_t x, uint32_t y, uint32_t z);
+
+/* Merge (Eq. 1, Sec. III-A).  out buffers hold a->u + b->u (+1). */
+int orc_merge(const orc_cga* a, const orc_cga* b, orc_cga* out);
+
+/* Orthogonal projection (Eq. 3 with m = 1, Sec. III-B) onto plane
+ * 0 = xy, 1 = xz, 2 = yz.  out buffers hold a->u (+1). */
+int orc_project(const orc_cga* a, int plane, orc_cga2d* out);
+
+/* Exact NN (Eq. 7-8) by exhaustive search over every stored voxel.
+ * Query voxel: floorf(fmaf(p, scale, offset)) clamped to [-2^30, 2^30].
+ * idx = CGA point index of the nearest voxel (ties: smaller key), dist2 =
+ * squared integer distance.  Empty CGA or non-finite query: idx = UINT32_MAX,
+ * dist2 = UINT64_MAX. */
+int orc_nn_brute(const orc_cga* a, float scale, const float offset[3],
+                 const float* q, uint64_t m, uint32_t* idx, uint64_t* dist2);
+
+/* Exact NN by the CGA procedure of Sec. III-C: exact-match lookup, else the
+ * nearest x -> nearest y -> nearest z bound, then every voxel inside the
+ * per-axis window of that bound.  Same outputs as orc_nn_brute. */
+int orc_nn_window(const orc_cga* a, float scale, const float offset[3],
+                  const float* q, uint64_t m, uint32_t* idx, uint64_t* dist2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
