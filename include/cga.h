@@ -1,0 +1,189 @@
+/*
+ * libcga -- compressed geometric arrays (CGA) on one GB300 (sm_103a).
+ *
+ * C ABI of the hot path of "Compressed Geometric Arrays for Point Cloud
+ * Processing" (Roodaki & Nazm Bojnordi): quantize float32 points to a voxel
+ * grid, encode and sort them into the CGA layout of Sec. III, and run the CGA
+ * operations of Sec. III-A..C (merge, orthogonal projection, exact nearest
+ * neighbour) plus lossless decode.  Every step runs in hand-written CUDA
+ * kernels; the host side only validates arguments, allocates and launches.
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are DEVICE pointers (current device); h_* are host.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is stream-ordered and asynchronous: a call returns once its kernels
+ *    are queued.  Only cga_info / cga_view / cga2d_info / cga2d_view wait.
+ *  - Handles (cga_t, cga2d_t) own their device arrays, obtained from the
+ *    caller's allocator (NULL allocator = cudaMallocAsync/cudaFreeAsync on the
+ *    call's stream).  Release them with cga_free / cga2d_free.
+ *  - Errors: every call returns CGA_OK (0) or a negative CGA_ERR_* code and
+ *    never aborts the process.  Argument errors are reported before any work
+ *    is queued and leave *out untouched.  Errors found on the device while the
+ *    queued work runs (non-finite input, a bounded wait that ran out) are
+ *    recorded in the output handle and returned by the next cga_info /
+ *    cga_view / cga2d_info on it; a merge or projection of a failed handle
+ *    carries the error on to its output.
+ *  - Coordinates: b = grid bits (1..16).  A voxel is (x, y, z), each in
+ *    [0, 2^b); its key is x << 2b | y << b | z, and CGA order is ascending key
+ *    order (x-major, then y, then z).  Coordinate arrays are uint16, pointer
+ *    arrays uint32.
+ */
+#ifndef CGA_H
+#define CGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CGA_OK 0
+#define CGA_ERR_INVALID_ARG (-1)   /* bad size, bits, plane, grid, null pointer */
+#define CGA_ERR_NONFINITE (-2)     /* NaN/Inf input point (or after transform) */
+#define CGA_ERR_GRID_MISMATCH (-3) /* merge of CGAs on different grids */
+#define CGA_ERR_OOM (-4)           /* the allocator returned NULL */
+#define CGA_ERR_CUDA (-5)          /* a CUDA runtime call failed */
+#define CGA_ERR_TIMEOUT (-6)       /* a bounded device wait ran out */
+#define CGA_ERR_INTERNAL (-7)      /* a device-side consistency check failed */
+
+/* Largest point count of one cloud (counts travel in 30-bit fields). */
+#define CGA_MAX_POINTS ((uint64_t)((1u << 30) - 1u))
+
+/* Voxel grid.  Quantization (the paper gives no formula; Sec. II-E-2-a asks
+ * for a bounding box holding every point, Sec. V uses QP = bits per axis):
+ *   q_a = clamp(floorf(fmaf(p_a, scale, offset[a])), 0, 2^bits - 1)
+ * evaluated in float32 with one rounding in the fma; the clamp keeps points on
+ * or outside the box faces inside the grid. */
+typedef struct {
+  uint32_t bits;    /* 1..16 */
+  float scale;      /* voxels per unit length, finite and > 0 */
+  float offset[3];  /* finite */
+} cga_grid;
+
+/* Grid of a cube with lower corner lo[3] and edge `extent`:
+ * scale = (float)2^bits / extent, offset[a] = -(lo[a] * scale).  Host only. */
+int cga_grid_from_box(const float lo[3], float extent, uint32_t bits, cga_grid* out);
+
+/* Device memory provider.  alloc returns a device pointer of at least `bytes`
+ * bytes usable in stream order on `stream` (NULL on failure -> CGA_ERR_OOM,
+ * nothing leaked); free releases one in stream order. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*free)(void* ctx, void* ptr, void* stream);
+} cga_allocator;
+
+typedef struct cga cga_t;      /* a 3-level CGA (Sec. III) */
+typedef struct cga2d cga2d_t;  /* a 2-level CGA of a projection (Sec. III-B) */
+
+typedef struct {
+  uint64_t h;         /* |X_index| distinct x                   */
+  uint64_t g;         /* |Y_index| distinct (x, y) columns      */
+  uint64_t u;         /* |Z_index| distinct voxels (points)     */
+  uint64_t bytes;     /* 2h + 4(h+1) + 2g + 4(g+1) + 2u          */
+  uint64_t capacity;  /* points the handle's buffers can hold   */
+} cga_sizes;
+
+typedef struct {
+  cga_grid grid;
+  uint64_t h, g, u;
+  const uint16_t* X_index;    /* h     device */
+  const uint32_t* X_pointer;  /* h + 1 device */
+  const uint16_t* Y_index;    /* g     device */
+  const uint32_t* Y_pointer;  /* g + 1 device */
+  const uint16_t* Z_index;    /* u     device */
+} cga_arrays;
+
+typedef struct {
+  uint32_t bits;
+  int32_t plane;              /* CGA_PLANE_* */
+  uint64_t h, g;              /* |U_index|, |V_index| */
+  const uint16_t* U_index;    /* h     device */
+  const uint32_t* U_pointer;  /* h + 1 device */
+  const uint16_t* V_index;    /* g     device */
+} cga2d_arrays;
+
+#define CGA_PLANE_XY 0
+#define CGA_PLANE_XZ 1
+#define CGA_PLANE_YZ 2
+
+/* Build (Sec. III, arrays; quantization as in cga_grid).
+ * d_xyz: n points, float32 AoS (x, y, z), device, caller-owned, 4-byte
+ *   aligned; n may be 0 (empty CGA: h = g = u = 0, X_pointer = Y_pointer = {0}).
+ * h_xform12: NULL or 12 host floats, R (3x3 row-major) then t, applied first as
+ *   p'_r = fmaf(R[r][0], x, fmaf(R[r][1], y, fmaf(R[r][2], z, t[r]))) -- the
+ *   rigid transform that brings a view into the common frame before a merge
+ *   (Sec. II-A).
+ * *out: new handle; duplicate voxels are stored once.  Non-finite p or p'
+ *   -> CGA_ERR_NONFINITE from the next cga_info.
+ * Errors: INVALID_ARG (n > CGA_MAX_POINTS, bad grid, NULL out/d_xyz with n>0),
+ *   OOM, CUDA. */
+int cga_build(const float* d_xyz, uint64_t n, const cga_grid* g, const float* h_xform12,
+              const cga_allocator* A, void* stream, cga_t** out);
+
+/* Merge (Eq. 1, Sec. III-A): *out holds the set union of the voxels of a and
+ * b, which must share one grid (bits, scale, offsets bit-identical), else
+ * CGA_ERR_GRID_MISMATCH.  Either input may be empty. */
+int cga_merge(const cga_t* a, const cga_t* b, const cga_allocator* A, void* stream,
+              cga_t** out);
+
+/* Orthogonal projection (Eq. 3 with m_x = m_y = 1, Sec. III-B) onto plane
+ * CGA_PLANE_XY (keeps x, y), _XZ (x, z) or _YZ (y, z): *out holds the set of
+ * distinct 2D voxels as a 2-level CGA, U_index/U_pointer over the first kept
+ * axis and V_index over the second, ascending at both levels. */
+int cga_project(const cga_t* a, int plane, const cga_allocator* A, void* stream,
+                cga2d_t** out);
+
+/* Exact nearest neighbour (Eq. 7-8, Sec. III-C).
+ * d_q: m query points, float32 AoS, device.  Each query maps to the voxel
+ *   floorf(fmaf(p_a, scale, offset_a)) of a's grid, clamped only to
+ *   [-2^30, 2^30] (queries outside the box are allowed).
+ * d_idx[j]: index, in CGA point order (the Z_index position), of the stored
+ *   voxel with the least squared integer distance to query j; among equal
+ *   distances the smaller key wins.  d_dist2[j]: that squared distance.
+ *   Empty CGA or non-finite query: UINT32_MAX / UINT64_MAX.
+ * Both output arrays hold m entries, device, caller-owned. */
+int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
+                 uint64_t* d_dist2, void* stream);
+
+/* Decode (lossless inverse of the build, CGA order): d_xyz receives u triples
+ * (x, y, z) as uint32, u from cga_info; device, caller-owned, >= 3u entries
+ * (may be NULL when the handle's capacity is 0). */
+int cga_decode(const cga_t* a, uint32_t* d_xyz, void* stream);
+
+/* Sizes of a handle; waits for the work that produced it.  Returns the
+ * device-side error recorded for the handle, if any. */
+int cga_info(const cga_t* a, cga_sizes* out);
+
+/* Device pointers of the geometry arrays (valid until cga_free); waits like
+ * cga_info. */
+int cga_view(const cga_t* a, cga_arrays* out);
+
+int cga2d_info(const cga2d_t* p, uint64_t* h, uint64_t* g);
+int cga2d_view(const cga2d_t* p, cga2d_arrays* out);
+
+/* Copy the geometry arrays to caller-owned HOST buffers sized from cga_info
+ * (X_index h, X_pointer h+1, Y_index g, Y_pointer g+1, Z_index u entries);
+ * waits like cga_info.  A CGA is its own serialized form: these five arrays
+ * and the grid rebuild it exactly. */
+int cga_download(const cga_t* a, uint16_t* h_X_index, uint32_t* h_X_pointer,
+                 uint16_t* h_Y_index, uint32_t* h_Y_pointer, uint16_t* h_Z_index);
+int cga2d_download(const cga2d_t* p, uint16_t* h_U_index, uint32_t* h_U_pointer,
+                   uint16_t* h_V_index);
+
+/* Release a handle in stream order on the stream of the call that made it. */
+void cga_free(cga_t* a);
+void cga2d_free(cga2d_t* p);
+
+/* Number of kernels this library has queued since the process started (all
+ * devices, all threads); a cheap counter for launch accounting. */
+uint64_t cga_kernel_launches(void);
+
+/* Static description of an error code. */
+const char* cga_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -91,6 +91,7 @@ def lib():
                                    ctypes.POINTER(_Cga)]
         _lib.orc_project.argtypes = [ctypes.POINTER(_Cga), ctypes.c_int,
                                      ctypes.POINTER(_Cga2d)]
+        _lib.orc_query_voxels.argtypes = [P, U64, F, P, P, P]
         for fn in (_lib.orc_nn_brute, _lib.orc_nn_window):
             fn.argtypes = [ctypes.POINTER(_Cga), F, P, P, U64, P, P]
     return _lib
@@ -272,6 +273,17 @@ def _nn(fn, a: Cga, grid: Grid, q):
     off = grid.offset_array()
     _check(fn(ctypes.byref(s), grid.scale, _ptr(off), _ptr(qa), len(qa), _ptr(idx), _ptr(d2)))
     return idx, d2
+
+
+def query_voxels(grid: Grid, q):
+    """(m, 3) int64 query voxels and an m-long validity mask (NN reading)."""
+    qa = _f32xyz(q)
+    out = np.zeros((len(qa), 3), np.int64)
+    valid = np.zeros(len(qa), np.uint8)
+    off = grid.offset_array()
+    _check(lib().orc_query_voxels(_ptr(qa), len(qa), grid.scale, _ptr(off), _ptr(out),
+                                  _ptr(valid)))
+    return out, valid.astype(bool)
 
 
 def nn_brute(a: Cga, grid: Grid, q):

@@ -348,6 +348,16 @@ void window_in(const uint16_t* lo, const uint16_t* hi, int64_t lo_v,
 
 }  // namespace
 
+int orc_query_voxels(const float* q, uint64_t m, float scale, const float offset[3],
+                     int64_t* out, uint8_t* valid) {
+  for (uint64_t j = 0; j < m; ++j) {
+    const Query Q = make_query(q + 3 * j, scale, offset);
+    valid[j] = Q.valid ? 1 : 0;
+    for (int a = 0; a < 3; ++a) out[3 * j + a] = Q.valid ? Q.q[a] : 0;
+  }
+  return ORC_OK;
+}
+
 // Eq. 7-8 by exhaustive search.
 int orc_nn_brute(const orc_cga* a, float scale, const float offset[3],
                  const float* q, uint64_t m, uint32_t* idx, uint64_t* dist2_out) {

@@ -96,6 +96,12 @@ int orc_project(const orc_cga* a, int plane, orc_cga2d* out);
 int orc_nn_brute(const orc_cga* a, float scale, const float offset[3],
                  const float* q, uint64_t m, uint32_t* idx, uint64_t* dist2);
 
+/* Query voxels of m points (the NN reading above): out[3j+a] =
+ * floorf(fmaf(q, scale, offset_a)) clamped to [-2^30, 2^30]; valid[j] = 0 for a
+ * non-finite query (its out entries are 0). */
+int orc_query_voxels(const float* q, uint64_t m, float scale, const float offset[3],
+                     int64_t* out, uint8_t* valid);
+
 /* Exact NN by the CGA procedure of Sec. III-C: exact-match lookup, else the
  * nearest x -> nearest y -> nearest z bound, then every voxel inside the
  * per-axis window of that bound.  Same outputs as orc_nn_brute. */

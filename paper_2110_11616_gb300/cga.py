@@ -1,0 +1,320 @@
+"""Thin Python binding of libcga (include/cga.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA kernels of libcga.so; this module
+passes torch device pointers, the current CUDA stream and a torch-backed
+allocator through the C ABI.  There is no CPU fallback: if libcga.so is missing
+or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcga.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_NONFINITE = -2
+ERR_GRID_MISMATCH = -3
+ERR_OOM = -4
+ERR_CUDA = -5
+ERR_TIMEOUT = -6
+ERR_INTERNAL = -7
+MAX_POINTS = (1 << 30) - 1
+PLANES = {"xy": 0, "xz": 1, "yz": 2}
+
+# Every symbol include/cga.h declares.
+EXPORTS = (
+    "cga_grid_from_box", "cga_build", "cga_merge", "cga_project", "cga_nn_query",
+    "cga_decode", "cga_info", "cga_view", "cga2d_info", "cga2d_view", "cga_download",
+    "cga2d_download", "cga_free", "cga2d_free", "cga_strerror", "cga_kernel_launches",
+)
+
+
+class CgaError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = _lib_strerror(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("bits", ctypes.c_uint32), ("scale", ctypes.c_float),
+                ("offset", ctypes.c_float * 3)]
+
+    def __repr__(self):
+        return f"Grid(bits={self.bits}, scale={self.scale}, offset={tuple(self.offset)})"
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [
+        ("ctx", ctypes.c_void_p),
+        ("alloc", ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                   ctypes.c_void_p)),
+        ("free", ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)),
+    ]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_uint64), ("g", ctypes.c_uint64), ("u", ctypes.c_uint64),
+                ("bytes", ctypes.c_uint64), ("capacity", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcga.so; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcga.so not found at {path}: build it with "
+                           "__graft_entry__.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(path)
+    P, U32, U64, I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    lib.cga_grid_from_box.argtypes = [P, ctypes.c_float, U32, ctypes.POINTER(Grid)]
+    lib.cga_build.argtypes = [P, U64, ctypes.POINTER(Grid), P, P, P, PP]
+    lib.cga_merge.argtypes = [P, P, P, P, PP]
+    lib.cga_project.argtypes = [P, I, P, P, PP]
+    lib.cga_nn_query.argtypes = [P, P, U64, P, P, P]
+    lib.cga_decode.argtypes = [P, P, P]
+    lib.cga_info.argtypes = [P, ctypes.POINTER(Sizes)]
+    lib.cga2d_info.argtypes = [P, ctypes.POINTER(U64), ctypes.POINTER(U64)]
+    lib.cga_download.argtypes = [P, P, P, P, P, P]
+    lib.cga2d_download.argtypes = [P, P, P, P]
+    lib.cga_free.argtypes = [P]
+    lib.cga_free.restype = None
+    lib.cga2d_free.argtypes = [P]
+    lib.cga2d_free.restype = None
+    lib.cga_kernel_launches.argtypes = []
+    lib.cga_kernel_launches.restype = ctypes.c_uint64
+    lib.cga_strerror.argtypes = [I]
+    lib.cga_strerror.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _lib_strerror(code):
+    try:
+        return load().cga_strerror(code).decode()
+    except Exception:  # library missing: still describe the code
+        return f"error {code}"
+
+
+def _check(rc, what=""):
+    if rc != OK:
+        raise CgaError(rc, what)
+
+
+# ------------------------------------------------------------------ allocator
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libcga needs a CUDA GPU; none is available")
+    return torch
+
+
+@ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+def _torch_alloc(ctx, nbytes, stream):
+    try:
+        import torch
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+    except Exception:
+        return None
+
+
+@ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+def _torch_free(ctx, ptr, stream):
+    try:
+        import torch
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:  # interpreter shutdown: the process is exiting anyway
+        pass
+
+
+TORCH_ALLOCATOR = Allocator(None, _torch_alloc, _torch_free)
+
+
+def _alloc_arg(allocator):
+    if allocator == "torch":
+        return ctypes.byref(TORCH_ALLOCATOR)
+    if allocator is None:
+        return None
+    return ctypes.byref(allocator)
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------- grid
+def grid_from_box(lo, extent: float, bits: int) -> Grid:
+    lo_a = np.ascontiguousarray(np.asarray(lo, np.float32).reshape(3))
+    g = Grid()
+    _check(load().cga_grid_from_box(lo_a.ctypes.data_as(ctypes.c_void_p), float(extent), int(bits),
+                                    ctypes.byref(g)), "cga_grid_from_box")
+    return g
+
+
+def make_grid(bits: int, scale: float, offset) -> Grid:
+    g = Grid()
+    g.bits = bits
+    g.scale = scale
+    for a in range(3):
+        g.offset[a] = offset[a]
+    return g
+
+
+# -------------------------------------------------------------------- handles
+class Cga:
+    """Owning wrapper of a cga_t*; frees it (stream-ordered) when collected."""
+
+    def __init__(self, ptr, grid: Grid, keep=()):
+        self.ptr = ptr
+        self.grid = grid
+        self._keep = keep
+
+    def info(self) -> dict:
+        s = Sizes()
+        _check(load().cga_info(self.ptr, ctypes.byref(s)), "cga_info")
+        return {"h": s.h, "g": s.g, "u": s.u, "bytes": s.bytes, "capacity": s.capacity}
+
+    def status(self) -> int:
+        s = Sizes()
+        return load().cga_info(self.ptr, ctypes.byref(s))
+
+    def download(self) -> dict:
+        s = Sizes()
+        rc = load().cga_info(self.ptr, ctypes.byref(s))
+        _check(rc, "cga_info")
+        out = {"X_index": np.zeros(s.h, np.uint16), "X_pointer": np.zeros(s.h + 1, np.uint32),
+               "Y_index": np.zeros(s.g, np.uint16), "Y_pointer": np.zeros(s.g + 1, np.uint32),
+               "Z_index": np.zeros(s.u, np.uint16)}
+        args = [out[k].ctypes.data_as(ctypes.c_void_p) for k in
+                ("X_index", "X_pointer", "Y_index", "Y_pointer", "Z_index")]
+        _check(load().cga_download(self.ptr, *args), "cga_download")
+        return out
+
+    def free(self):
+        if self.ptr:
+            load().cga_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Cga2d:
+    def __init__(self, ptr, bits: int, plane: int):
+        self.ptr = ptr
+        self.bits = bits
+        self.plane = plane
+
+    def info(self) -> dict:
+        h, g = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().cga2d_info(self.ptr, ctypes.byref(h), ctypes.byref(g)), "cga2d_info")
+        return {"h": h.value, "g": g.value}
+
+    def download(self) -> dict:
+        i = self.info()
+        out = {"U_index": np.zeros(i["h"], np.uint16), "U_pointer": np.zeros(i["h"] + 1, np.uint32),
+               "V_index": np.zeros(i["g"], np.uint16)}
+        args = [out[k].ctypes.data_as(ctypes.c_void_p) for k in ("U_index", "U_pointer", "V_index")]
+        _check(load().cga2d_download(self.ptr, *args), "cga2d_download")
+        return out
+
+    def free(self):
+        if self.ptr:
+            load().cga2d_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _dev_f32(t, what):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise TypeError(f"{what}: expected a contiguous float32 CUDA tensor")
+    return t
+
+
+# ----------------------------------------------------------------- operations
+def cga_build(points, grid: Grid, xform=None, stream=None, allocator="torch") -> Cga:
+    """points: (n, 3) float32 CUDA tensor; xform: None or 12 floats (R row-major, t)."""
+    _dev_f32(points, "cga_build")
+    n = points.numel() // 3
+    x = None
+    if xform is not None:
+        x = np.ascontiguousarray(np.asarray(xform, np.float32).reshape(12))
+    out = ctypes.c_void_p()
+    _check(load().cga_build(ctypes.c_void_p(points.data_ptr()), n, ctypes.byref(grid),
+                            None if x is None else x.ctypes.data_as(ctypes.c_void_p),
+                            _alloc_arg(allocator), _stream(stream), ctypes.byref(out)),
+           "cga_build")
+    return Cga(out, grid)
+
+
+def cga_merge(a: Cga, b: Cga, stream=None, allocator="torch") -> Cga:
+    out = ctypes.c_void_p()
+    _check(load().cga_merge(a.ptr, b.ptr, _alloc_arg(allocator), _stream(stream),
+                            ctypes.byref(out)), "cga_merge")
+    return Cga(out, a.grid)
+
+
+def cga_project(a: Cga, plane, stream=None, allocator="torch") -> Cga2d:
+    p = PLANES[plane] if isinstance(plane, str) else int(plane)
+    out = ctypes.c_void_p()
+    _check(load().cga_project(a.ptr, p, _alloc_arg(allocator), _stream(stream),
+                              ctypes.byref(out)), "cga_project")
+    return Cga2d(out, a.grid.bits, p)
+
+
+def cga_nn_query(a: Cga, queries, idx=None, dist2=None, stream=None):
+    """queries: (m, 3) float32 CUDA tensor.  Returns (idx int32 tensor holding
+    uint32 values, dist2 int64 tensor holding uint64 values)."""
+    torch = _torch()
+    _dev_f32(queries, "cga_nn_query")
+    m = queries.numel() // 3
+    if idx is None:
+        idx = torch.empty(m, dtype=torch.int32, device=queries.device)
+    if dist2 is None:
+        dist2 = torch.empty(m, dtype=torch.int64, device=queries.device)
+    _check(load().cga_nn_query(a.ptr, ctypes.c_void_p(queries.data_ptr()), m,
+                               ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(dist2.data_ptr()),
+                               _stream(stream)), "cga_nn_query")
+    return idx, dist2
+
+
+def cga_decode(a: Cga, out=None, stream=None):
+    """(u, 3) int32 CUDA tensor of (x, y, z) voxels in CGA order.  With `out`
+    given (>= 3u int32 entries) no size query (and no host wait) happens."""
+    torch = _torch()
+    if out is None:
+        u = a.info()["u"]
+        out = torch.empty((u, 3), dtype=torch.int32, device="cuda")
+        if u == 0:
+            return out
+    _check(load().cga_decode(a.ptr, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "cga_decode")
+    return out
+
+
+def kernel_launches() -> int:
+    return int(load().cga_kernel_launches())

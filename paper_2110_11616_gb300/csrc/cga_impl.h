@@ -1,0 +1,138 @@
+// Internal structures shared by the libcga kernels and the C-ABI layer.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace libcga {
+
+// Tiling shared by the sort pipeline: 256 threads x 16 keys per tile.
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;  // 4096
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxPasses = 6;  // 3 * 16 bits / 8
+
+// Device error bits recorded in a handle header.
+enum : uint32_t { kErrNonfinite = 1u, kErrTimeout = 2u };
+
+// Counts of a compacted level structure.  For a 3-level CGA cnt = {u, g, h};
+// for a 2-level projection cnt = {g2 (|V|), h2 (|U|), 0}.
+struct alignas(16) Header {
+  unsigned long long cnt[3];
+  unsigned int err;
+  unsigned int pad;
+};
+
+// Output (or input) arrays of a CGA.  Level 0 is the finest (Z_index, or
+// V_index of a projection); level 1 is Y (or U) with its pointer array;
+// level 2 is X (absent in a projection).
+struct Levels {
+  uint16_t* idx0;
+  uint16_t* idx1;
+  uint32_t* ptr1;
+  uint16_t* idx2;
+  uint32_t* ptr2;
+  Header* hdr;
+  uint32_t bits;
+  uint32_t nlevels;  // 3 or 2
+  uint64_t cap;      // capacity of level 0 (>= u)
+  uint64_t cap1;     // capacity of level 1
+  uint64_t cap2;     // capacity of level 2 (0 for a projection)
+};
+
+// One segment (cloud) of the sort pipeline.
+struct SortSeg {
+  // build input (nullptr for a projection)
+  const float* xyz;
+  float scale;
+  float off[3];
+  float X[12];
+  uint32_t has_x;
+  // projection input: the source CGA and the plane
+  Levels src;
+  int32_t plane;
+  uint32_t from_cga;  // 1: keys come from src (projection), 0: from xyz
+  // common
+  uint32_t n_host;      // element count when known on the host (build)
+  uint32_t bits;        // grid bits of this segment
+  uint32_t key_bits;    // significant key bits: 3b (build) or 2b (projection)
+  uint32_t passes;      // radix passes = ceil(key_bits / 8)
+  uint64_t key_base;    // first key slot of this segment in the key buffers
+  uint32_t tile_base;   // first global tile index
+  uint32_t num_tiles;   // tiles reserved (from the capacity)
+  Levels out;           // compacted output
+};
+
+// Scratch layout of one sort-pipeline run (all offsets from one base).
+struct SortScratch {
+  void* keys0;
+  void* keys1;
+  uint32_t* hist;      // [S][kMaxPasses][kRadix]
+  uint32_t* look;      // [kMaxPasses][total_tiles][kRadix]
+  uint32_t* clook;     // [total_tiles][3]
+  uint32_t* counters;  // [kMaxPasses + 1]
+  SortSeg* segs;       // [S]
+  size_t zero_bytes;   // bytes from hist to the end of counters
+};
+
+size_t sort_scratch_bytes(uint64_t total_keys, uint32_t total_tiles, int S, bool key64);
+SortScratch sort_scratch_carve(void* base, uint64_t total_keys, uint32_t total_tiles, int S,
+                               bool key64);
+
+// Queue the whole sort pipeline: header init, key generation (+ histograms),
+// radix passes, compaction.  `h_segs` is copied to the device first.
+cudaError_t run_sort_pipeline(const SortSeg* h_segs, int S, uint32_t total_tiles,
+                              uint32_t max_passes, bool key64, const SortScratch& sc,
+                              cudaStream_t stream);
+
+// ---- operations on built CGAs ---------------------------------------------
+
+// Decode a CGA to uint32 (x, y, z) triples in CGA order.
+cudaError_t run_decode(const Levels& a, uint32_t* xyz, cudaStream_t stream);
+
+// Merge: sorted union of pairs of 3-level CGAs.  Splitter keys are taken at
+// every kMergeHalf-th point of each input; between consecutive splitters (in
+// key order) each input contributes at most kMergeHalf points, so one tile of
+// kTile keys always holds the merged run.
+constexpr int kMergeHalf = kTile / 2;
+
+struct MergePair {
+  Levels a, b, out;
+  uint32_t spl_base;   // splitter slots: A's [spl_base, +spl_a), then B's spl_b
+  uint32_t spl_a, spl_b;
+  uint32_t tile_base;  // reserved tiles: spl_a + spl_b + 1
+  uint32_t num_tiles;
+};
+
+struct MergeScratch {
+  unsigned long long* spl;  // [total_spl]
+  uint32_t* bounds;         // [(total_tiles + S) * 2]; pair p at 2 * (tile_base + p)
+  uint32_t* ntiles;         // [S]
+  uint32_t* clook;          // [total_tiles][3]
+  uint32_t* counter;        // [1]
+  MergePair* pairs;         // [S]
+  size_t zero_bytes;        // clook .. counter
+};
+
+size_t merge_scratch_bytes(uint32_t total_spl, uint32_t total_tiles, int S);
+MergeScratch merge_scratch_carve(void* base, uint32_t total_spl, uint32_t total_tiles, int S);
+cudaError_t run_merge(const MergePair* h_pairs, int S, uint32_t total_spl, uint32_t total_tiles,
+                      const MergeScratch& sc, cudaStream_t stream);
+
+// Copy the top two levels of a CGA into a 2-level projection (plane xy).
+cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stream);
+
+// Exact NN queries against one CGA.
+cudaError_t run_nn(const Levels& a, float scale, const float off[3], const float* q, uint64_t m,
+                   uint32_t* idx, unsigned long long* dist2, cudaStream_t stream);
+
+int device_sm_count();
+
+// Launch accounting (cga_kernel_launches).
+void count_launch(unsigned n);
+
+}  // namespace libcga

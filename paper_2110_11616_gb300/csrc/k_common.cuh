@@ -1,0 +1,158 @@
+// Device helpers shared by the libcga kernels: relaxed flag access, bounded
+// decoupled look-back, block scans, and searches over the CGA arrays.
+#pragma once
+#include "cga_impl.h"
+
+namespace libcga {
+
+constexpr uint32_t kFlagAgg = 1u << 30;   // tile aggregate published
+constexpr uint32_t kFlagInc = 2u << 30;   // inclusive prefix published
+constexpr uint32_t kValMask = (1u << 30) - 1u;
+constexpr uint32_t kSpinLimit = 1u << 22;  // polls of one look-back word
+constexpr uint32_t kErrInternal = 4u;      // a device consistency check failed
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Decoupled look-back over the tiles (first, tile) of one segment.  Each
+// tile publishes one 32-bit word per counter: 2 flag bits + a 30-bit value.
+// Tile ids are handed out in launch order by an atomic counter, so every
+// predecessor is already resident and the wait ends; it is still bounded: after
+// kSpinLimit polls of one word the error bit is set and the wait stops.
+__device__ __forceinline__ uint32_t lookback(const uint32_t* look, uint32_t stride, uint32_t tile,
+                                             uint32_t first, unsigned int* err) {
+  uint32_t excl = 0;
+  uint32_t j = tile;
+  while (j > first) {
+    --j;
+    uint32_t v;
+    uint32_t spins = 0;
+    while (true) {
+      v = ld_relaxed(look + (size_t)j * stride);
+      if (v & (kFlagAgg | kFlagInc)) break;
+      if (++spins > kSpinLimit) {
+        atomicOr(err, kErrTimeout);
+        return excl;
+      }
+      if (spins > 32) __nanosleep(100);
+    }
+    excl += v & kValMask;
+    if (v & kFlagInc) break;
+  }
+  return excl;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan across a kThreads block.  s_warp: kWarps scratch words.
+// Contains two __syncthreads.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T& total, T* s_warp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  T before = 0, tot = 0;
+#pragma unroll
+  for (int i = 0; i < kWarps; ++i) {
+    T x = s_warp[i];
+    if (i < w) before += x;
+    tot += x;
+  }
+  __syncthreads();
+  total = tot;
+  return before + inc - v;
+}
+
+// Largest c in [lo, hi] with ptr[c] <= p (requires ptr[lo] <= p).
+__device__ __forceinline__ uint32_t search_le(const uint32_t* __restrict__ ptr, uint32_t lo,
+                                              uint32_t hi, uint32_t p) {
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(ptr + mid) <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// First index in [lo, hi) whose value is >= v (hi when none).
+__device__ __forceinline__ uint32_t lower_bound_u16(const uint16_t* __restrict__ a, uint32_t lo,
+                                                    uint32_t hi, uint32_t v) {
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if ((uint32_t)__ldg(a + mid) < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Key of the point at CGA position p (p < u).  g, h: level sizes.
+__device__ __forceinline__ unsigned long long key_at(const Levels& a, uint32_t g, uint32_t h,
+                                                     uint32_t p) {
+  const uint32_t b = a.bits;
+  const uint32_t c = search_le(a.ptr1, 0, g - 1, p);
+  const uint32_t xr = search_le(a.ptr2, 0, h - 1, c);
+  return ((unsigned long long)__ldg(a.idx2 + xr) << (2 * b)) |
+         ((unsigned long long)__ldg(a.idx1 + c) << b) | (unsigned long long)__ldg(a.idx0 + p);
+}
+
+// Number of stored keys smaller than `key`: the Sec. III-A lookup (x in
+// X_index, then y in its Y range, then z in its column) in lower-bound form.
+__device__ __forceinline__ uint32_t rank_of(const Levels& a, uint32_t h, unsigned long long key) {
+  const uint32_t b = a.bits, m = (1u << b) - 1u;
+  const uint32_t x = (uint32_t)(key >> (2 * b)), y = (uint32_t)(key >> b) & m,
+                 z = (uint32_t)key & m;
+  const uint32_t xr = lower_bound_u16(a.idx2, 0, h, x);
+  if (xr == h || __ldg(a.idx2 + xr) != x) return __ldg(a.ptr1 + __ldg(a.ptr2 + xr));
+  const uint32_t ys = __ldg(a.ptr2 + xr), ye = __ldg(a.ptr2 + xr + 1);
+  const uint32_t c = lower_bound_u16(a.idx1, ys, ye, y);
+  if (c == ye || __ldg(a.idx1 + c) != y) return __ldg(a.ptr1 + c);
+  return lower_bound_u16(a.idx0, __ldg(a.ptr1 + c), __ldg(a.ptr1 + c + 1), z);
+}
+
+// Column and x windows of the CGA positions [p0, p1] (inclusive, p1 < u).
+struct Window {
+  uint32_t c0, c1, x0, x1;
+};
+
+__device__ __forceinline__ Window window_of(const Levels& a, uint32_t g, uint32_t h, uint32_t p0,
+                                            uint32_t p1) {
+  Window w;
+  w.c0 = search_le(a.ptr1, 0, g - 1, p0);
+  w.c1 = search_le(a.ptr1, w.c0, g - 1, p1);
+  w.x0 = search_le(a.ptr2, 0, h - 1, w.c0);
+  w.x1 = search_le(a.ptr2, w.x0, h - 1, w.c1);
+  return w;
+}
+
+// (x, y, z) of the point at position p inside a window that contains it.
+__device__ __forceinline__ void point_at(const Levels& a, const Window& w, uint32_t p,
+                                         uint32_t& x, uint32_t& y, uint32_t& z) {
+  const uint32_t c = search_le(a.ptr1, w.c0, w.c1, p);
+  const uint32_t xr = search_le(a.ptr2, w.x0, w.x1, c);
+  x = __ldg(a.idx2 + xr);
+  y = __ldg(a.idx1 + c);
+  z = __ldg(a.idx0 + p);
+}
+
+}  // namespace libcga

@@ -1,0 +1,389 @@
+// Sort pipeline of the CGA build (and of the xz / yz projections):
+//   k_seg_init     headers and empty-CGA sentinels
+//   k_keys_hist    quantize (+ rigid transform) and encode each point, or
+//                  re-key a CGA point for a projection; per-segment digit
+//                  histograms of every radix pass in the same read
+//   k_onesweep     one LSD radix pass: warp-level digit ranking, decoupled
+//                  look-back over tiles for the global digit offsets, scatter
+//   k_compact      dedupe + CGA compaction (k_compact.cuh)
+// Every kernel works on a batch of segments (clouds); a tile never spans two
+// segments and look-back chains stop at the segment's first tile.
+#include <algorithm>
+
+#include "k_compact.cuh"
+
+namespace libcga {
+
+namespace {
+
+__device__ __forceinline__ int find_seg(const SortSeg* __restrict__ segs, int S, uint32_t t) {
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Element count of a segment: known on the host for a build, read from the
+// source header for a projection (the source is built earlier in the stream).
+__device__ __forceinline__ uint32_t seg_count(const SortSeg& s) {
+  if (s.from_cga) return (uint32_t)s.src.hdr->cnt[0];
+  return s.n_host;
+}
+
+__device__ __forceinline__ uint32_t quantize_axis(float v, float scale, float off, float hi) {
+  float f = floorf(__fmaf_rn(v, scale, off));
+  f = fminf(fmaxf(f, 0.0f), hi);
+  return (uint32_t)f;
+}
+
+__global__ void k_seg_init(const SortSeg* __restrict__ segs, int S) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const Levels& o = segs[s].out;
+  o.hdr->cnt[0] = 0;
+  o.hdr->cnt[1] = 0;
+  o.hdr->cnt[2] = 0;
+  o.hdr->err = segs[s].from_cga ? segs[s].src.hdr->err : 0u;
+  o.ptr1[0] = 0;
+  if (o.nlevels == 3) o.ptr2[0] = 0;
+}
+
+// Keys of the tiles [t0, t1) plus per-segment histograms of every pass.
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restrict__ segs, int S,
+                                                        uint32_t total_tiles,
+                                                        uint32_t tiles_per_cta, K* keys0,
+                                                        uint32_t* hist) {
+  __shared__ uint32_t s_hist[kMaxPasses][kRadix];
+  __shared__ float s_pts[kThreads * 3];
+  __shared__ Window s_win;
+  __shared__ uint32_t s_err;
+  const int tid = threadIdx.x;
+  const uint32_t t0 = blockIdx.x * tiles_per_cta;
+  const uint32_t t1 = min(t0 + tiles_per_cta, total_tiles);
+  if (t0 >= t1) return;
+  for (int i = tid; i < kMaxPasses * kRadix; i += kThreads) (&s_hist[0][0])[i] = 0;
+  if (tid == 0) s_err = 0;
+  __syncthreads();
+  int cur = find_seg(segs, S, t0);
+  auto flush = [&](int s) {
+    __syncthreads();
+    const uint32_t passes = segs[s].passes;
+    for (int i = tid; i < kMaxPasses * kRadix; i += kThreads) {
+      const uint32_t v = (&s_hist[0][0])[i];
+      if (v != 0 && (uint32_t)(i / kRadix) < passes) {
+        atomicAdd(hist + (size_t)s * kMaxPasses * kRadix + i, v);
+      }
+      (&s_hist[0][0])[i] = 0;
+    }
+    if (tid == 0 && s_err) {
+      atomicOr(&segs[s].out.hdr->err, s_err);
+      s_err = 0;
+    }
+    __syncthreads();
+  };
+  for (uint32_t t = t0; t < t1; ++t) {
+    const int s = find_seg(segs, S, t);
+    if (s != cur) {
+      flush(cur);
+      cur = s;
+    }
+    const SortSeg& sg = segs[s];
+    const uint32_t n = seg_count(sg);
+    const uint32_t start = (t - sg.tile_base) * kTile;
+    if (start >= n) continue;
+    const uint32_t cnt = min((uint32_t)kTile, n - start);
+    K* out = keys0 + sg.key_base + start;
+    const uint32_t passes = sg.passes;
+    const uint32_t b = sg.bits;
+    if (!sg.from_cga) {
+      const float* src = sg.xyz + (size_t)start * 3;
+      const float hi = (float)((1u << b) - 1u);
+      for (uint32_t c0 = 0; c0 < cnt; c0 += kThreads) {
+        const uint32_t m = min((uint32_t)kThreads, cnt - c0);
+        __syncthreads();
+        for (uint32_t i = tid; i < m * 3; i += kThreads) s_pts[i] = __ldg(src + (size_t)c0 * 3 + i);
+        __syncthreads();
+        if ((uint32_t)tid < m) {
+          float x = s_pts[3 * tid], y = s_pts[3 * tid + 1], z = s_pts[3 * tid + 2];
+          bool ok = isfinite(x) && isfinite(y) && isfinite(z);
+          if (sg.has_x) {
+            const float* X = sg.X;
+            const float x2 = __fmaf_rn(X[0], x, __fmaf_rn(X[1], y, __fmaf_rn(X[2], z, X[9])));
+            const float y2 = __fmaf_rn(X[3], x, __fmaf_rn(X[4], y, __fmaf_rn(X[5], z, X[10])));
+            const float z2 = __fmaf_rn(X[6], x, __fmaf_rn(X[7], y, __fmaf_rn(X[8], z, X[11])));
+            x = x2;
+            y = y2;
+            z = z2;
+            ok = ok && isfinite(x) && isfinite(y) && isfinite(z);
+          }
+          K key = 0;
+          if (ok) {
+            const uint32_t qx = quantize_axis(x, sg.scale, sg.off[0], hi);
+            const uint32_t qy = quantize_axis(y, sg.scale, sg.off[1], hi);
+            const uint32_t qz = quantize_axis(z, sg.scale, sg.off[2], hi);
+            key = ((K)qx << (2 * b)) | ((K)qy << b) | (K)qz;
+          } else {
+            atomicOr(&s_err, kErrNonfinite);
+          }
+          out[c0 + tid] = key;
+          for (uint32_t p = 0; p < passes; ++p) {
+            atomicAdd(&s_hist[p][(uint32_t)(key >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+          }
+        }
+      }
+    } else {
+      // projection: decode the source point, keep two axes
+      const Levels& a = sg.src;
+      if (tid == 0) {
+        s_win = window_of(a, (uint32_t)a.hdr->cnt[1], (uint32_t)a.hdr->cnt[2], start,
+                          start + cnt - 1);
+      }
+      __syncthreads();
+      const Window win = s_win;
+      for (uint32_t e = tid; e < cnt; e += kThreads) {
+        uint32_t x, y, z;
+        point_at(a, win, start + e, x, y, z);
+        uint32_t u = x, v = y;
+        if (sg.plane == 1) { u = x; v = z; }
+        if (sg.plane == 2) { u = y; v = z; }
+        const K key = ((K)u << b) | (K)v;
+        out[e] = key;
+        for (uint32_t p = 0; p < passes; ++p) {
+          atomicAdd(&s_hist[p][(uint32_t)(key >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  flush(cur);
+}
+
+// One LSD pass over digit `pass` of every segment that still needs it.
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_onesweep(const SortSeg* __restrict__ segs, int S,
+                                                       int pass, const K* __restrict__ in,
+                                                       K* __restrict__ out,
+                                                       const uint32_t* __restrict__ hist,
+                                                       uint32_t* look, uint32_t* counter) {
+  __shared__ K s_keys[kTile];
+  __shared__ uint32_t s_wh[kWarps][kRadix];
+  __shared__ uint32_t s_off[kRadix];
+  __shared__ uint32_t s_scan[kWarps];
+  __shared__ uint32_t s_tile;
+  __shared__ int s_seg;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) {
+    const uint32_t t = atomicAdd(counter, 1u);
+    s_tile = t;
+    s_seg = find_seg(segs, S, t);
+  }
+  for (int i = tid; i < kWarps * kRadix; i += kThreads) (&s_wh[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const int s = s_seg;
+  const SortSeg& sg = segs[s];
+  if (pass >= (int)sg.passes) return;
+  const uint32_t n = seg_count(sg);
+  const uint32_t lt = t - sg.tile_base;
+  const uint32_t start = lt * kTile;
+  if (start >= n) return;
+  const uint32_t cnt = min((uint32_t)kTile, n - start);
+  const K* src = in + sg.key_base + start;
+  const int shift = pass * kRadixBits;
+
+  K k[kItems];
+  uint32_t dg[kItems], rk[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const uint32_t e = (uint32_t)(w * 32 * kItems + i * 32 + lane);
+    const bool v = e < cnt;
+    k[i] = v ? src[e] : (K)0;
+    dg[i] = v ? ((uint32_t)(k[i] >> shift) & (kRadix - 1)) : 0xffffffffu;
+  }
+  // warp-level ranking: lanes holding the same digit form one match group
+  uint32_t* wh = s_wh[w];
+  const uint32_t ltm = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const uint32_t d = dg[i];
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t base = (d < (uint32_t)kRadix) ? wh[d] : 0u;
+    __syncwarp();
+    if (d < (uint32_t)kRadix && lane == __ffs(peers) - 1) wh[d] = base + __popc(peers);
+    __syncwarp();
+    rk[i] = base + __popc(peers & ltm);
+  }
+  __syncthreads();
+  // per digit (thread == digit): warp offsets, tile count, publish
+  const int d = tid;
+  uint32_t tile_cnt = 0;
+  for (int x = 0; x < kWarps; ++x) {
+    const uint32_t v = s_wh[x][d];
+    s_wh[x][d] = tile_cnt;
+    tile_cnt += v;
+  }
+  uint32_t* my = look + (size_t)t * kRadix + d;
+  st_relaxed(my, (lt == 0 ? kFlagInc : kFlagAgg) | tile_cnt);
+  uint32_t tot;
+  const uint32_t bin_start = block_excl_scan(tile_cnt, tot, s_scan);
+  const uint32_t hv = hist[((size_t)s * kMaxPasses + pass) * kRadix + d];
+  const uint32_t dbase = block_excl_scan(hv, tot, s_scan);
+  s_off[d] = bin_start;
+  __syncthreads();
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    if (dg[i] < (uint32_t)kRadix) {
+      const uint32_t pos = s_off[dg[i]] + s_wh[w][dg[i]] + rk[i];
+      if (pos < (uint32_t)kTile) s_keys[pos] = k[i]; else bad = true;
+    }
+  }
+  uint32_t excl = 0;
+  if (lt > 0) {
+    excl = lookback(look + d, kRadix, t, sg.tile_base, &sg.out.hdr->err);
+    st_relaxed(my, kFlagInc | ((excl + tile_cnt) & kValMask));
+  }
+  __syncthreads();
+  s_off[d] = dbase + excl - bin_start;
+  __syncthreads();
+  K* dst = out + sg.key_base;
+  for (uint32_t e = tid; e < cnt; e += kThreads) {
+    const K key = s_keys[e];
+    const uint32_t pos = s_off[(uint32_t)(key >> shift) & (kRadix - 1)] + e;
+    if (pos < n) dst[pos] = key; else bad = true;
+  }
+  if (bad) atomicOr(&sg.out.hdr->err, kErrInternal);
+}
+
+template <typename K, int LEVELS>
+__global__ void __launch_bounds__(kThreads) k_compact(const SortSeg* __restrict__ segs, int S,
+                                                      const K* __restrict__ keys0,
+                                                      const K* __restrict__ keys1,
+                                                      uint32_t* clook, uint32_t* counter) {
+  __shared__ CompactSmem sm;
+  __shared__ uint32_t s_tile;
+  __shared__ int s_seg;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) {
+    const uint32_t t = atomicAdd(counter, 1u);
+    s_tile = t;
+    s_seg = find_seg(segs, S, t);
+  }
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const SortSeg& sg = segs[s_seg];
+  const uint32_t n = seg_count(sg);
+  const uint32_t lt = t - sg.tile_base;
+  const uint32_t start = lt * kTile;
+  if (start >= n) return;
+  const uint32_t cnt = min((uint32_t)kTile, n - start);
+  const K* src = ((sg.passes & 1u) ? keys1 : keys0) + sg.key_base + start;
+  K k[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const uint32_t e = (uint32_t)(w * 32 * kItems + i * 32 + lane);
+    k[i] = (e < cnt) ? src[e] : (K)0;
+  }
+  const bool has_prev = start > 0;
+  const K prev = has_prev ? src[-1] : (K)0;
+  const bool last = (start + cnt == n);
+  compact_tile<LEVELS, K>(k, cnt, has_prev, prev, t, sg.tile_base, last, sg.out, clook, sm);
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t sort_scratch_bytes(uint64_t total_keys, uint32_t total_tiles, int S, bool key64) {
+  const size_t ks = key64 ? 8 : 4;
+  size_t b = 0;
+  b += align_up(total_keys * ks) * 2;
+  b += align_up((size_t)S * kMaxPasses * kRadix * 4);
+  b += align_up((size_t)kMaxPasses * total_tiles * kRadix * 4);
+  b += align_up((size_t)total_tiles * 3 * 4);
+  b += align_up((kMaxPasses + 1) * 4);
+  b += align_up((size_t)S * sizeof(SortSeg));
+  return b;
+}
+
+SortScratch sort_scratch_carve(void* base, uint64_t total_keys, uint32_t total_tiles, int S,
+                               bool key64) {
+  const size_t ks = key64 ? 8 : 4;
+  char* p = static_cast<char*>(base);
+  SortScratch sc{};
+  sc.keys0 = p;
+  p += align_up(total_keys * ks);
+  sc.keys1 = p;
+  p += align_up(total_keys * ks);
+  char* z0 = p;
+  sc.hist = reinterpret_cast<uint32_t*>(p);
+  p += align_up((size_t)S * kMaxPasses * kRadix * 4);
+  sc.look = reinterpret_cast<uint32_t*>(p);
+  p += align_up((size_t)kMaxPasses * total_tiles * kRadix * 4);
+  sc.clook = reinterpret_cast<uint32_t*>(p);
+  p += align_up((size_t)total_tiles * 3 * 4);
+  sc.counters = reinterpret_cast<uint32_t*>(p);
+  p += align_up((kMaxPasses + 1) * 4);
+  sc.zero_bytes = (size_t)(p - z0);
+  sc.segs = reinterpret_cast<SortSeg*>(p);
+  return sc;
+}
+
+int device_sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+template <typename K>
+static cudaError_t launch_pipeline(int S, uint32_t total_tiles, uint32_t max_passes, int levels,
+                                   const SortScratch& sc, cudaStream_t stream) {
+  K* k0 = static_cast<K*>(sc.keys0);
+  K* k1 = static_cast<K*>(sc.keys1);
+  const uint32_t ctas = std::min<uint32_t>(total_tiles, (uint32_t)device_sm_count() * 4);
+  const uint32_t per = (total_tiles + ctas - 1) / ctas;
+  k_keys_hist<K><<<ctas, kThreads, 0, stream>>>(sc.segs, S, total_tiles, per, k0, sc.hist);
+  count_launch(2 + max_passes);
+  for (uint32_t p = 0; p < max_passes; ++p) {
+    const K* in = (p & 1) ? k1 : k0;
+    K* out = (p & 1) ? k0 : k1;
+    k_onesweep<K><<<total_tiles, kThreads, 0, stream>>>(
+        sc.segs, S, (int)p, in, out, sc.hist, sc.look + (size_t)p * total_tiles * kRadix,
+        sc.counters + p);
+  }
+  if (levels == 3) {
+    k_compact<K, 3><<<total_tiles, kThreads, 0, stream>>>(sc.segs, S, k0, k1, sc.clook,
+                                                          sc.counters + kMaxPasses);
+  } else {
+    k_compact<K, 2><<<total_tiles, kThreads, 0, stream>>>(sc.segs, S, k0, k1, sc.clook,
+                                                          sc.counters + kMaxPasses);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t run_sort_pipeline(const SortSeg* h_segs, int S, uint32_t total_tiles,
+                              uint32_t max_passes, bool key64, const SortScratch& sc,
+                              cudaStream_t stream) {
+  cudaError_t e = cudaMemcpyAsync(sc.segs, h_segs, sizeof(SortSeg) * S, cudaMemcpyHostToDevice,
+                                  stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(sc.hist, 0, sc.zero_bytes, stream);
+  if (e != cudaSuccess) return e;
+  k_seg_init<<<(S + 127) / 128, 128, 0, stream>>>(sc.segs, S);
+  count_launch(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || total_tiles == 0) return e;
+  const int levels = (int)h_segs[0].out.nlevels;
+  return key64 ? launch_pipeline<unsigned long long>(S, total_tiles, max_passes, levels, sc, stream)
+               : launch_pipeline<uint32_t>(S, total_tiles, max_passes, levels, sc, stream);
+}
+
+}  // namespace libcga

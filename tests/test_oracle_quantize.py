@@ -104,3 +104,18 @@ def test_transform_overflow_is_nonfinite(orc):
     with pytest.raises(orc.OracleError) as e:
         orc.quantize(np.array([[10.0, 0.5, 0.5]], np.float32), g, xform=X)
     assert e.value.code == orc.ERR_NONFINITE
+
+
+def test_query_voxels_match_exact_arithmetic(orc):
+    q = synth.uniform_queries(300, 15, [-3, -3, -3], 7.0)
+    q[5] = [np.nan, 0, 0]
+    g = orc.grid_from_box([0, 0, 0], 1.0, 10)
+    v, ok = orc.query_voxels(g, q)
+    assert not ok[5] and ok.sum() == len(q) - 1
+    for i in range(len(q)):
+        if ok[i]:
+            assert [int(x) for x in v[i]] == [ex.quantize_query_axis(q[i, a], g.scale, g.offset[a])
+                                              for a in range(3)]
+    big = orc.Grid(4, 1.0e9, (0.0, 0.0, 0.0))
+    v, ok = orc.query_voxels(big, np.array([[10.0, -10.0, 0.0]], np.float32))
+    assert list(v[0]) == [1 << 30, -(1 << 30), 0]
