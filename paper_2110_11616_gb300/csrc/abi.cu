@@ -354,10 +354,28 @@ int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
   if (a == nullptr || (m > 0 && (d_q == nullptr || d_idx == nullptr || d_dist2 == nullptr))) {
     return CGA_ERR_INVALID_ARG;
   }
-  if (m > (uint64_t)0xFFFFFFFFull * 256) return CGA_ERR_INVALID_ARG;
-  return cuda_rc(libcga::run_nn(a->lv, a->grid.scale, a->grid.offset, d_q, m, d_idx,
-                             reinterpret_cast<unsigned long long*>(d_dist2),
-                             static_cast<cudaStream_t>(stream)));
+  if (m > libcga::kNnMaxQueries) return CGA_ERR_INVALID_ARG;
+  if (m == 0) return CGA_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  libcga::NnSeg seg{};
+  seg.a = a->lv;
+  seg.scale = a->grid.scale;
+  for (int k = 0; k < 3; ++k) seg.off[k] = a->grid.offset[k];
+  seg.q = d_q;
+  seg.m = (uint32_t)m;
+  seg.idx = d_idx;
+  seg.d2 = reinterpret_cast<unsigned long long*>(d_dist2);
+  seg.tile_base = 0;
+  seg.num_tiles = (uint32_t)((m + libcga::kTile - 1) / libcga::kTile);
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  void* scratch = nullptr;
+  if (m >= libcga::kNnSortMin) {
+    scratch = dalloc(A, libcga::nn_scratch_bytes(seg.num_tiles, 1), s);
+    if (scratch == nullptr) return CGA_ERR_OOM;
+  }
+  const int rc = cuda_rc(libcga::run_nn(&seg, 1, seg.num_tiles, scratch, s));
+  if (scratch != nullptr) dfree(A, a->has_alloc, scratch, s);
+  return rc;
 }
 
 int cga_decode(const cga_t* a, uint32_t* d_xyz, void* stream) {

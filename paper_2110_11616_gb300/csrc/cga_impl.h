@@ -61,6 +61,7 @@ struct SortSeg {
   uint32_t bits;        // grid bits of this segment
   uint32_t key_bits;    // significant key bits: 3b (build) or 2b (projection)
   uint32_t passes;      // radix passes = ceil(key_bits / 8)
+  uint32_t bit0;        // lowest key bit sorted on (pass p sorts bits bit0 + 8p ..)
   uint64_t key_base;    // first key slot of this segment in the key buffers
   uint32_t tile_base;   // first global tile index
   uint32_t num_tiles;   // tiles reserved (from the capacity)
@@ -82,6 +83,11 @@ struct SortScratch {
 size_t sort_scratch_bytes(uint64_t total_keys, uint32_t total_tiles, int S, bool key64);
 SortScratch sort_scratch_carve(void* base, uint64_t total_keys, uint32_t total_tiles, int S,
                                bool key64);
+
+// Queue only the radix passes (segments already on the device in sc.segs,
+// histograms filled, look-back words zeroed).
+cudaError_t run_radix_passes(int S, uint32_t total_tiles, uint32_t max_passes, bool key64,
+                             const SortScratch& sc, cudaStream_t stream);
 
 // Queue the whole sort pipeline: header init, key generation (+ histograms),
 // radix passes, compaction.  `h_segs` is copied to the device first.
@@ -126,9 +132,28 @@ cudaError_t run_merge(const MergePair* h_pairs, int S, uint32_t total_spl, uint3
 // Copy the top two levels of a CGA into a 2-level projection (plane xy).
 cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stream);
 
-// Exact NN queries against one CGA.
-cudaError_t run_nn(const Levels& a, float scale, const float off[3], const float* q, uint64_t m,
-                   uint32_t* idx, unsigned long long* dist2, cudaStream_t stream);
+// Exact NN: one segment per (CGA, query batch).  Queries occupy a slot space
+// of whole tiles (segment s owns slots [tile_base*kTile, (tile_base +
+// num_tiles)*kTile)).  With scratch the queries are first sorted along a
+// Morton curve so that neighbouring warps search neighbouring space.
+struct NnSeg {
+  Levels a;
+  float scale;
+  float off[3];
+  const float* q;
+  uint32_t m;
+  uint32_t* idx;
+  unsigned long long* d2;
+  uint32_t tile_base;
+  uint32_t num_tiles;
+};
+constexpr uint64_t kNnSortMin = 8192;
+constexpr uint64_t kNnMaxQueries = (1u << 30) - 1u;  // per segment
+size_t nn_scratch_bytes(uint32_t total_tiles, int S);
+// scratch == nullptr: no query sort, S must be 1 (the segment travels as a
+// kernel parameter).
+cudaError_t run_nn(const NnSeg* h_segs, int S, uint32_t total_tiles, void* scratch,
+                   cudaStream_t stream);
 
 int device_sm_count();
 

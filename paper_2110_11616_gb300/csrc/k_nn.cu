@@ -1,0 +1,292 @@
+// Exact nearest-neighbour search on a CGA (Eq. 7-8, Sec. III-C).
+//
+// The search is the paper's window search, with the bound shrinking as
+// closer voxels are found.  It visits x slabs outward from the query's x, and
+// in each slab the columns outward from the query's y.  A slab is skipped once
+// dx^2 exceeds the best squared distance found so far, and a column once
+// dx^2 + dy^2 does.  Each visited column contributes its two z neighbours of
+// the query (binary search).  Every voxel that could lie at or below the final
+// distance is examined, and ties go to the smaller key, so the result is
+// exactly Eq. 8's set reduced by the smaller-key rule.
+//
+// GPU mapping: one warp per query.  In each round the 32 lanes take 16 slabs
+// on each side of the query (lane parity picks the side).  Phase A: every lane
+// finds its slab's nearest column and that column's nearest voxel.  A warp
+// minimum then sets the bound.  Phase B: each lane scans its slab's remaining
+// columns under that bound, and a second warp minimum follows.  Queries are
+// visited in Morton order of their voxel (a 4-pass radix sort of
+// (morton << 32 | index) keys), so neighbouring warps read neighbouring slabs.
+#include <algorithm>
+
+#include "k_common.cuh"
+
+namespace libcga {
+
+namespace {
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+__device__ __forceinline__ int find_nn_seg(const NnSeg* __restrict__ segs, int S, uint32_t t) {
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ long long quantize_query(float v, float scale, float off) {
+  float f = floorf(__fmaf_rn(v, scale, off));
+  f = fminf(fmaxf(f, -1073741824.0f), 1073741824.0f);
+  return (long long)f;
+}
+
+__device__ __forceinline__ unsigned long long absdiff(long long a, long long b) {
+  return (unsigned long long)(a > b ? a - b : b - a);
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// Sort keys (morton30 << 32 | query index) and per-segment digit histograms
+// of the four passes over bits 32..63.  A block covers 256 slots of one tile.
+__global__ void __launch_bounds__(256) k_nn_keys(const NnSeg* __restrict__ segs, int S,
+                                                 unsigned long long* __restrict__ keys,
+                                                 uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_hist[4][kRadix];
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t slot = blockIdx.x * 256u + threadIdx.x;
+  const uint32_t tile = blockIdx.x / (kTile / 256);
+  const int s = find_nn_seg(segs, S, tile);
+  const NnSeg& sg = segs[s];
+  const uint32_t local = slot - sg.tile_base * (uint32_t)kTile;
+  if (local < sg.m) {
+    const float* p = sg.q + 3 * (size_t)local;
+    const float px = p[0], py = p[1], pz = p[2];
+    uint32_t mort = 0x3fffffffu;
+    if (isfinite(px) && isfinite(py) && isfinite(pz)) {
+      const uint32_t bits = sg.a.bits;
+      const float top = (float)((1u << bits) - 1u);
+      const float v[3] = {px, py, pz};
+      uint32_t c[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        float f = floorf(__fmaf_rn(v[a], sg.scale, sg.off[a]));
+        f = fminf(fmaxf(f, 0.0f), top);
+        const uint32_t u = (uint32_t)f;
+        c[a] = bits >= 10 ? (u >> (bits - 10)) : (u << (10 - bits));
+      }
+      mort = (spread3(c[0]) << 2) | (spread3(c[1]) << 1) | spread3(c[2]);
+    }
+    keys[slot] = ((unsigned long long)mort << 32) | local;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) atomicAdd(&s_hist[k][(mort >> (8 * k)) & (kRadix - 1)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
+    const uint32_t v = (&s_hist[0][0])[i];
+    if (v) atomicAdd(hist + (size_t)s * kMaxPasses * kRadix + i, v);
+  }
+}
+
+struct Best {
+  unsigned long long d2, key;
+  uint32_t idx;
+  __device__ __forceinline__ void offer(unsigned long long d, unsigned long long k, uint32_t i) {
+    if (d < d2 || (d == d2 && k < key)) {
+      d2 = d;
+      key = k;
+      idx = i;
+    }
+  }
+  __device__ __forceinline__ void warp_min() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long od = __shfl_xor_sync(0xffffffffu, d2, o);
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+      const uint32_t oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      offer(od, ok, oi);
+    }
+  }
+};
+
+// The two z neighbours of the query in column c.
+__device__ __forceinline__ void visit_column(const Levels& a, uint32_t c, unsigned long long kxy,
+                                             unsigned long long dxy, long long qz, uint32_t cqz,
+                                             Best& b) {
+  const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
+  const uint32_t zr = lower_bound_u16(a.idx0, zs, ze, cqz);
+  if (zr < ze) {
+    const uint32_t z = __ldg(a.idx0 + zr);
+    const unsigned long long dz = absdiff(z, qz);
+    b.offer(dxy + dz * dz, kxy | z, zr);
+  }
+  if (zr > zs) {
+    const uint32_t z = __ldg(a.idx0 + zr - 1);
+    const unsigned long long dz = absdiff(z, qz);
+    b.offer(dxy + dz * dz, kxy | z, zr - 1);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs, int S,
+                                                 NnSeg inline_seg, uint32_t total_slots,
+                                                 const unsigned long long* __restrict__ order,
+                                                 const unsigned int* __restrict__ order_err) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const bool sorted = order != nullptr && *order_err == 0u;
+  for (uint32_t slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total_slots;
+       slot += nwarps) {
+    const uint32_t tile = slot / (uint32_t)kTile;
+    const NnSeg& sg = segs != nullptr ? segs[find_nn_seg(segs, S, tile)] : inline_seg;
+    const uint32_t local = slot - sg.tile_base * (uint32_t)kTile;
+    if (local >= sg.m) continue;
+    const uint32_t j = sorted ? (uint32_t)order[slot] : local;
+    const Levels& a = sg.a;
+    const float* p = sg.q + 3 * (size_t)j;
+    const float px = p[0], py = p[1], pz = p[2];
+    const uint32_t u = (uint32_t)a.hdr->cnt[0], h = (uint32_t)a.hdr->cnt[2];
+    if (!(isfinite(px) && isfinite(py) && isfinite(pz)) || u == 0) {
+      if (lane == 0) {
+        sg.idx[j] = 0xffffffffu;
+        sg.d2[j] = ~0ull;
+      }
+      continue;
+    }
+    const uint32_t b = a.bits;
+    const long long top = (1ll << b) - 1;
+    const long long qx = quantize_query(px, sg.scale, sg.off[0]);
+    const long long qy = quantize_query(py, sg.scale, sg.off[1]);
+    const long long qz = quantize_query(pz, sg.scale, sg.off[2]);
+    const uint32_t cqx = (uint32_t)min(max(qx, 0ll), top);
+    const uint32_t cqy = (uint32_t)min(max(qy, 0ll), top);
+    const uint32_t cqz = (uint32_t)min(max(qz, 0ll), top);
+    const uint32_t xr0 = lower_bound_u16(a.idx2, 0, h, cqx);
+    Best best{~0ull, ~0ull, 0xffffffffu};
+    const bool right = (lane & 1u) == 0u;
+    for (uint32_t r = 0;; ++r) {
+      const long long k = (long long)r * 16 + (lane >> 1);
+      const long long slab = right ? (long long)xr0 + k : (long long)xr0 - 1 - k;
+      const bool valid = slab >= 0 && slab < (long long)h;
+      unsigned long long dx2 = ~0ull;
+      uint32_t x = 0;
+      if (valid) {
+        x = __ldg(a.idx2 + slab);
+        const unsigned long long dx = absdiff(x, qx);
+        dx2 = dx * dx;
+      }
+      const bool active = valid && dx2 <= best.d2;
+      if (!__any_sync(0xffffffffu, active)) break;
+      uint32_t ys = 0, ye = 0, yr0 = 0;
+      const unsigned long long kx = (unsigned long long)x << (2 * b);
+      if (active) {
+        ys = __ldg(a.ptr2 + slab);
+        ye = __ldg(a.ptr2 + slab + 1);
+        yr0 = lower_bound_u16(a.idx1, ys, ye, cqy);
+        if (yr0 < ye) {
+          const uint32_t y = __ldg(a.idx1 + yr0);
+          const unsigned long long dy = absdiff(y, qy);
+          const unsigned long long dxy = dx2 + dy * dy;
+          if (dxy <= best.d2) visit_column(a, yr0, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+        }
+        if (yr0 > ys) {
+          const uint32_t y = __ldg(a.idx1 + yr0 - 1);
+          const unsigned long long dy = absdiff(y, qy);
+          const unsigned long long dxy = dx2 + dy * dy;
+          if (dxy <= best.d2) visit_column(a, yr0 - 1, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+        }
+      }
+      best.warp_min();
+      if (active) {
+        long long R2 = (long long)yr0 + 1, L2 = (long long)yr0 - 2;
+        while (true) {
+          const bool hR = R2 < (long long)ye, hL = L2 >= (long long)ys;
+          if (!hR && !hL) break;
+          const unsigned long long eR = hR ? absdiff(__ldg(a.idx1 + R2), qy) : ~0ull;
+          const unsigned long long eL = hL ? absdiff(__ldg(a.idx1 + L2), qy) : ~0ull;
+          const bool gR = hR && (!hL || eR <= eL);
+          const unsigned long long dy = gR ? eR : eL;
+          const unsigned long long dxy = dx2 + dy * dy;
+          if (dxy > best.d2) break;
+          const uint32_t c = (uint32_t)(gR ? R2 : L2);
+          if (gR) ++R2; else --L2;
+          const uint32_t y = __ldg(a.idx1 + c);
+          visit_column(a, c, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+        }
+      }
+      best.warp_min();
+    }
+    if (lane == 0) {
+      sg.idx[j] = best.idx;
+      sg.d2[j] = best.d2;
+    }
+  }
+}
+
+}  // namespace
+
+size_t nn_scratch_bytes(uint32_t total_tiles, int S) {
+  return align_up(sizeof(Header)) + align_up((size_t)S * sizeof(NnSeg)) +
+         sort_scratch_bytes((uint64_t)total_tiles * kTile, total_tiles, S, true);
+}
+
+cudaError_t run_nn(const NnSeg* h_segs, int S, uint32_t total_tiles, void* scratch,
+                   cudaStream_t stream) {
+  if (total_tiles == 0) return cudaSuccess;
+  const unsigned long long* order = nullptr;
+  const unsigned int* order_err = nullptr;
+  const NnSeg* d_segs = nullptr;
+  const uint32_t total_slots = total_tiles * (uint32_t)kTile;
+  if (scratch != nullptr) {
+    char* p = static_cast<char*>(scratch);
+    Header* eh = reinterpret_cast<Header*>(p);
+    p += align_up(sizeof(Header));
+    NnSeg* segs = reinterpret_cast<NnSeg*>(p);
+    p += align_up((size_t)S * sizeof(NnSeg));
+    const SortScratch sc = sort_scratch_carve(p, (uint64_t)total_slots, total_tiles, S, true);
+    SortSeg* ss = new SortSeg[S]();
+    for (int s = 0; s < S; ++s) {
+      ss[s].n_host = h_segs[s].m;
+      ss[s].passes = 4;
+      ss[s].bit0 = 32;
+      ss[s].key_base = (uint64_t)h_segs[s].tile_base * kTile;
+      ss[s].tile_base = h_segs[s].tile_base;
+      ss[s].num_tiles = h_segs[s].num_tiles;
+      ss[s].out.hdr = eh;
+    }
+    cudaError_t e = cudaMemsetAsync(eh, 0, sizeof(Header), stream);
+    if (e == cudaSuccess) {
+      e = cudaMemcpyAsync(segs, h_segs, sizeof(NnSeg) * S, cudaMemcpyHostToDevice, stream);
+    }
+    if (e == cudaSuccess) {
+      e = cudaMemcpyAsync(sc.segs, ss, sizeof(SortSeg) * S, cudaMemcpyHostToDevice, stream);
+    }
+    delete[] ss;
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc.hist, 0, sc.zero_bytes, stream);
+    if (e != cudaSuccess) return e;
+    k_nn_keys<<<total_tiles * (kTile / 256), 256, 0, stream>>>(
+        segs, S, static_cast<unsigned long long*>(sc.keys0), sc.hist);
+    count_launch(1);
+    e = run_radix_passes(S, total_tiles, 4, true, sc, stream);
+    if (e != cudaSuccess) return e;
+    order = static_cast<const unsigned long long*>(sc.keys0);  // 4 passes end in keys0
+    order_err = &eh->err;
+    d_segs = segs;
+  } else if (S != 1) {
+    return cudaErrorInvalidValue;
+  }
+  const uint32_t warps_needed = total_slots;
+  const uint32_t blocks = std::min<uint32_t>((warps_needed + 7) / 8, (uint32_t)device_sm_count() * 8);
+  k_nn_warp<<<blocks, 256, 0, stream>>>(d_segs, S, h_segs[0], total_slots, order, order_err);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace libcga

@@ -269,106 +269,6 @@ __global__ void k_project_xy(Levels a, Levels o) {
   (void)u;
 }
 
-// ---------------------------------------------------------------------- NN
-__device__ __forceinline__ long long quantize_query(float v, float scale, float off) {
-  float f = floorf(__fmaf_rn(v, scale, off));
-  f = fminf(fmaxf(f, -1073741824.0f), 1073741824.0f);
-  return (long long)f;
-}
-
-__device__ __forceinline__ unsigned long long absdiff(long long a, long long b) {
-  return (unsigned long long)(a > b ? a - b : b - a);
-}
-
-// One thread per query.  x slabs are visited in order of |dx| from the
-// query, columns of a slab in order of |dy|, and each column gives its two z
-// neighbours of the query by binary search; a slab (column) is skipped once
-// dx^2 (dx^2 + dy^2) exceeds the best squared distance so far, so every voxel
-// that could be at or below the final distance is examined (Sec. III-C with
-// the bound shrinking as closer voxels are found).
-__global__ void __launch_bounds__(256) k_nn(Levels a, float scale, float o0, float o1, float o2,
-                                            const float* __restrict__ q, uint64_t m,
-                                            uint32_t* __restrict__ idx,
-                                            unsigned long long* __restrict__ d2o) {
-  const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  const float px = q[3 * j], py = q[3 * j + 1], pz = q[3 * j + 2];
-  const uint32_t u = (uint32_t)a.hdr->cnt[0], h = (uint32_t)a.hdr->cnt[2];
-  if (!(isfinite(px) && isfinite(py) && isfinite(pz)) || u == 0) {
-    idx[j] = 0xffffffffu;
-    d2o[j] = ~0ull;
-    return;
-  }
-  const uint32_t b = a.bits;
-  const long long top = (1ll << b) - 1;
-  const long long qx = quantize_query(px, scale, o0);
-  const long long qy = quantize_query(py, scale, o1);
-  const long long qz = quantize_query(pz, scale, o2);
-  const uint32_t cqx = (uint32_t)min(max(qx, 0ll), top);
-  const uint32_t cqy = (uint32_t)min(max(qy, 0ll), top);
-  const uint32_t cqz = (uint32_t)min(max(qz, 0ll), top);
-  unsigned long long best = ~0ull, bkey = ~0ull;
-  uint32_t bidx = 0xffffffffu;
-  const uint32_t xr0 = lower_bound_u16(a.idx2, 0, h, cqx);
-  long long R = xr0, L = (long long)xr0 - 1;
-  while (true) {
-    const bool hasR = R < (long long)h, hasL = L >= 0;
-    if (!hasR && !hasL) break;
-    const unsigned long long dR = hasR ? absdiff(__ldg(a.idx2 + R), qx) : ~0ull;
-    const unsigned long long dL = hasL ? absdiff(__ldg(a.idx2 + L), qx) : ~0ull;
-    const bool goR = hasR && (!hasL || dR <= dL);
-    const unsigned long long dx = goR ? dR : dL;
-    const unsigned long long dx2 = dx * dx;
-    if (dx2 > best) break;
-    const uint32_t xi = (uint32_t)(goR ? R : L);
-    if (goR) ++R; else --L;
-    const uint32_t x = __ldg(a.idx2 + xi);
-    const uint32_t ys = __ldg(a.ptr2 + xi), ye = __ldg(a.ptr2 + xi + 1);
-    const uint32_t yr0 = lower_bound_u16(a.idx1, ys, ye, cqy);
-    long long R2 = yr0, L2 = (long long)yr0 - 1;
-    while (true) {
-      const bool hR = R2 < (long long)ye, hL = L2 >= (long long)ys;
-      if (!hR && !hL) break;
-      const unsigned long long eR = hR ? absdiff(__ldg(a.idx1 + R2), qy) : ~0ull;
-      const unsigned long long eL = hL ? absdiff(__ldg(a.idx1 + L2), qy) : ~0ull;
-      const bool gR = hR && (!hL || eR <= eL);
-      const unsigned long long dy = gR ? eR : eL;
-      const unsigned long long dxy = dx2 + dy * dy;
-      if (dxy > best) break;
-      const uint32_t c = (uint32_t)(gR ? R2 : L2);
-      if (gR) ++R2; else --L2;
-      const uint32_t y = __ldg(a.idx1 + c);
-      const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
-      const uint32_t zr = lower_bound_u16(a.idx0, zs, ze, cqz);
-      const unsigned long long kxy = ((unsigned long long)x << (2 * b)) | ((unsigned long long)y << b);
-      if (zr < ze) {
-        const uint32_t z = __ldg(a.idx0 + zr);
-        const unsigned long long dz = absdiff(z, qz);
-        const unsigned long long d2 = dxy + dz * dz;
-        const unsigned long long key = kxy | z;
-        if (d2 < best || (d2 == best && key < bkey)) {
-          best = d2;
-          bkey = key;
-          bidx = zr;
-        }
-      }
-      if (zr > zs) {
-        const uint32_t z = __ldg(a.idx0 + zr - 1);
-        const unsigned long long dz = absdiff(z, qz);
-        const unsigned long long d2 = dxy + dz * dz;
-        const unsigned long long key = kxy | z;
-        if (d2 < best || (d2 == best && key < bkey)) {
-          best = d2;
-          bkey = key;
-          bidx = zr - 1;
-        }
-      }
-    }
-  }
-  idx[j] = bidx;
-  d2o[j] = best;
-}
-
 }  // namespace
 
 cudaError_t run_decode(const Levels& a, uint32_t* xyz, cudaStream_t stream) {
@@ -433,15 +333,6 @@ cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stre
   const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
                                                        (uint64_t)device_sm_count() * 8);
   k_project_xy<<<blocks, 256, 0, stream>>>(a, out);
-  count_launch(1);
-  return cudaGetLastError();
-}
-
-cudaError_t run_nn(const Levels& a, float scale, const float off[3], const float* q, uint64_t m,
-                   uint32_t* idx, unsigned long long* dist2, cudaStream_t stream) {
-  if (m == 0) return cudaSuccess;
-  const uint64_t blocks = (m + 255) / 256;
-  k_nn<<<(unsigned)blocks, 256, 0, stream>>>(a, scale, off[0], off[1], off[2], q, m, idx, dist2);
   count_launch(1);
   return cudaGetLastError();
 }

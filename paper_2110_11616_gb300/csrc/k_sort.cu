@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restric
           }
           out[c0 + tid] = key;
           for (uint32_t p = 0; p < passes; ++p) {
-            atomicAdd(&s_hist[p][(uint32_t)(key >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+            atomicAdd(&s_hist[p][(uint32_t)(key >> (sg.bit0 + p * kRadixBits)) & (kRadix - 1)], 1u);
           }
         }
       }
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restric
         const K key = ((K)u << b) | (K)v;
         out[e] = key;
         for (uint32_t p = 0; p < passes; ++p) {
-          atomicAdd(&s_hist[p][(uint32_t)(key >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+          atomicAdd(&s_hist[p][(uint32_t)(key >> (sg.bit0 + p * kRadixBits)) & (kRadix - 1)], 1u);
         }
       }
       __syncthreads();
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const SortSeg* __restrict
   if (start >= n) return;
   const uint32_t cnt = min((uint32_t)kTile, n - start);
   const K* src = in + sg.key_base + start;
-  const int shift = pass * kRadixBits;
+  const int shift = (int)sg.bit0 + pass * kRadixBits;
 
   K k[kItems];
   uint32_t dg[kItems], rk[kItems];
@@ -344,14 +344,10 @@ int device_sm_count() {
 }
 
 template <typename K>
-static cudaError_t launch_pipeline(int S, uint32_t total_tiles, uint32_t max_passes, int levels,
-                                   const SortScratch& sc, cudaStream_t stream) {
+static void launch_passes(int S, uint32_t total_tiles, uint32_t max_passes, const SortScratch& sc,
+                          cudaStream_t stream) {
   K* k0 = static_cast<K*>(sc.keys0);
   K* k1 = static_cast<K*>(sc.keys1);
-  const uint32_t ctas = std::min<uint32_t>(total_tiles, (uint32_t)device_sm_count() * 4);
-  const uint32_t per = (total_tiles + ctas - 1) / ctas;
-  k_keys_hist<K><<<ctas, kThreads, 0, stream>>>(sc.segs, S, total_tiles, per, k0, sc.hist);
-  count_launch(2 + max_passes);
   for (uint32_t p = 0; p < max_passes; ++p) {
     const K* in = (p & 1) ? k1 : k0;
     K* out = (p & 1) ? k0 : k1;
@@ -359,6 +355,30 @@ static cudaError_t launch_pipeline(int S, uint32_t total_tiles, uint32_t max_pas
         sc.segs, S, (int)p, in, out, sc.hist, sc.look + (size_t)p * total_tiles * kRadix,
         sc.counters + p);
   }
+  count_launch(max_passes);
+}
+
+cudaError_t run_radix_passes(int S, uint32_t total_tiles, uint32_t max_passes, bool key64,
+                             const SortScratch& sc, cudaStream_t stream) {
+  if (total_tiles == 0) return cudaSuccess;
+  if (key64) {
+    launch_passes<unsigned long long>(S, total_tiles, max_passes, sc, stream);
+  } else {
+    launch_passes<uint32_t>(S, total_tiles, max_passes, sc, stream);
+  }
+  return cudaGetLastError();
+}
+
+template <typename K>
+static cudaError_t launch_pipeline(int S, uint32_t total_tiles, uint32_t max_passes, int levels,
+                                   const SortScratch& sc, cudaStream_t stream) {
+  K* k0 = static_cast<K*>(sc.keys0);
+  K* k1 = static_cast<K*>(sc.keys1);
+  const uint32_t ctas = std::min<uint32_t>(total_tiles, (uint32_t)device_sm_count() * 4);
+  const uint32_t per = (total_tiles + ctas - 1) / ctas;
+  k_keys_hist<K><<<ctas, kThreads, 0, stream>>>(sc.segs, S, total_tiles, per, k0, sc.hist);
+  count_launch(2);
+  launch_passes<K>(S, total_tiles, max_passes, sc, stream);
   if (levels == 3) {
     k_compact<K, 3><<<total_tiles, kThreads, 0, stream>>>(sc.segs, S, k0, k1, sc.clook,
                                                           sc.counters + kMaxPasses);
