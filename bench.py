@@ -36,7 +36,8 @@ from paper_2110_11616_gb300 import synth  # noqa: E402
 
 METRIC = "CGA build Mpts/s, NN queries/s, merge GB/s vs HBM peak; batched vs plain"
 WORKLOAD = ("LiDAR frame set: 10 sweeps x 64 beams x 2048 azimuth (1,310,720 pts), b=16, "
-            "build (ego pose fused) + 9-merge tree + xy projection + 1M jittered NN + decode")
+            "batched build (ego pose fused) + 9-merge tree (batched per level) + xy projection "
+            "+ 1M jittered NN + decode")
 N_SWEEPS, BEAMS, STEPS_AZ, N_QUERIES = 10, 64, 2048, 1_000_000
 LO, EXTENT, BITS = (-128.0, -128.0, -128.0), 256.0, 16
 
@@ -131,23 +132,31 @@ class GpuPipeline:
         self.dec = torch.empty((self.n_points, 3), dtype=torch.int32, device="cuda")
         self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
 
-    def step(self, timed_events=True):
+    def step(self, timed_events=True, batched=True):
         cga = self.cga
         ev = self.ev
         if timed_events:
             ev[0].record()
-        sweeps = [cga.cga_build(d, self.grid, xform=p, allocator=None)
-                  for d, p in zip(self.d_sweeps, self.poses)]
+        if batched:
+            sweeps = cga.cga_build_batch(self.d_sweeps, self.grid, self.poses, allocator=None)
+        else:
+            sweeps = [cga.cga_build(d, self.grid, xform=p, allocator=None)
+                      for d, p in zip(self.d_sweeps, self.poses)]
         if timed_events:
             ev[1].record()
         merges = []
-
-        def mrg(a, b):
-            m = cga.cga_merge(a, b, allocator=None)
-            merges.append((a, b, m))
-            return m
-
-        world = merge_tree(sweeps, mrg)
+        level = list(sweeps)
+        while len(level) > 1:
+            a, b = level[0:len(level) - 1:2], level[1::2]
+            if batched:
+                nxt = cga.cga_merge_batch(a, b, allocator=None)
+            else:
+                nxt = [cga.cga_merge(x, y, allocator=None) for x, y in zip(a, b)]
+            merges.extend(zip(a, b, nxt))
+            if len(level) % 2:
+                nxt.append(level[-1])
+            level = nxt
+        world = level[0]
         if timed_events:
             ev[2].record()
         proj = cga.cga_project(world, "xy", allocator=None)
@@ -226,6 +235,18 @@ def run_gpu(args, rank, world_size, local_rank):
     step_ms = [s.elapsed_time(e) for s, e in zip(start_ev, end_ev)]
     total_ms = float(sum(step_ms))
 
+    # the same step as one call per cloud / per merge (the plain form)
+    plain_ms = []
+    for k in range(max(3, args.steps // 2)):
+        flush.fill_(float(k))
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        P.step(timed_events=False, batched=False)
+        e.record()
+        e.synchronize()
+        plain_ms.append(s.elapsed_time(e))
+
     # end to end: host (pinned) inputs -> device -> results back to host
     e2e_ms = []
     for k in range(max(3, args.steps // 3)):
@@ -284,6 +305,10 @@ def run_gpu(args, rank, world_size, local_rank):
         },
         "e2e": {"value": round(e2e_val, 3), "unit": "Mpts/s",
                 "h2d_bytes_per_step": P.bytes_in(), "d2h_bytes_per_step": P.bytes_out()},
+        "plain": {"ms_per_step": round(float(np.mean(plain_ms)), 4),
+                  "value": round(pts / (float(np.mean(plain_ms)) / 1e3) / 1e6, 3),
+                  "note": "one call per sweep build and per merge (the step above batches "
+                          "the 10 builds and each merge-tree level into one launch set)"},
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s": round(t_wall, 3),

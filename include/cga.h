@@ -152,6 +152,78 @@ int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
  * (may be NULL when the handle's capacity is 0). */
 int cga_decode(const cga_t* a, uint32_t* d_xyz, void* stream);
 
+/* ---- Batched forms: one set of kernel launches serves every item. --------
+ * Each item has the semantics of the single call; handles are independent
+ * (free each one).  On an error nothing is returned and no handle leaks. */
+
+typedef struct {
+  const float* d_xyz;      /* n points, device */
+  uint64_t n;
+  cga_grid grid;
+  const float* h_xform12;  /* NULL or 12 host floats, as in cga_build */
+} cga_cloud;
+
+/* cga_build for `count` clouds (grids may differ) -> out[count]. */
+int cga_build_batch(const cga_cloud* clouds, uint32_t count, const cga_allocator* A,
+                    void* stream, cga_t** out);
+
+/* cga_merge of a[i] and b[i] for every i -> out[count]. */
+int cga_merge_batch(const cga_t* const* a, const cga_t* const* b, uint32_t count,
+                    const cga_allocator* A, void* stream, cga_t** out);
+
+/* cga_project of a[i] onto planes[i] for every i -> out[count]. */
+int cga_project_batch(const cga_t* const* a, const int* planes, uint32_t count,
+                      const cga_allocator* A, void* stream, cga2d_t** out);
+
+typedef struct {
+  const float* d_q;   /* m query points, device */
+  uint64_t m;
+  uint32_t* d_idx;    /* m, device */
+  uint64_t* d_dist2;  /* m, device */
+} cga_queries;
+
+/* cga_nn_query of q[i] against a[i] for every i (scratch from A). */
+int cga_nn_query_batch(const cga_t* const* a, const cga_queries* q, uint32_t count,
+                       const cga_allocator* A, void* stream);
+
+/* ---- Pre-planned pipeline (capturable) ------------------------------------
+ * For each item i: build the cloud, build its twin (the same points under the
+ * rigid transform xform12, the view brought into the common frame of
+ * Sec. II-A), merge the two (Eq. 1), project the merge onto the xy plane
+ * (Eq. 3) and answer m NN queries against the merge (Eq. 7-8).  Create does
+ * every allocation (one arena from A) and uploads every descriptor; run then
+ * only queues memsets and kernels -- about twenty launches for all items, each
+ * launch covering every cloud -- so it is safe to capture in a CUDA graph.
+ * The inputs (points, queries) are read and the NN outputs written at the
+ * device addresses given at create, on every run. */
+typedef struct cga_pipeline cga_pipeline_t;
+
+typedef struct {
+  const float* d_xyz;  /* n points, device */
+  uint64_t n;          /* <= CGA_MAX_POINTS / 2 */
+  cga_grid grid;
+  float xform12[12];   /* twin transform: R row-major, then t */
+  const float* d_q;    /* m NN queries, device (may be NULL when m == 0) */
+  uint64_t m;
+  uint32_t* d_idx;     /* m, device */
+  uint64_t* d_dist2;   /* m, device */
+} cga_pipeline_item;
+
+/* Plan `count` items; waits until the descriptors are on the device. */
+int cga_pipeline_create(const cga_pipeline_item* items, uint32_t count, const cga_allocator* A,
+                        void* stream, cga_pipeline_t** out);
+/* Queue one pass of every stage on `stream`. */
+int cga_pipeline_run(cga_pipeline_t* p, void* stream);
+/* First call captures cga_pipeline_run into a CUDA graph (on a private
+ * stream); every call launches that graph on `stream`. */
+int cga_pipeline_run_graph(cga_pipeline_t* p, void* stream);
+/* Non-owning handles of item i's results (which: 0 cloud, 1 twin, 2 merged),
+ * valid until cga_pipeline_free; they refresh on every run.  cga_free on them
+ * does nothing. */
+int cga_pipeline_view(const cga_pipeline_t* p, uint32_t i, int which, const cga_t** out);
+int cga_pipeline_view_xy(const cga_pipeline_t* p, uint32_t i, const cga2d_t** out);
+void cga_pipeline_free(cga_pipeline_t* p);
+
 /* Sizes of a handle; waits for the work that produced it.  Returns the
  * device-side error recorded for the handle, if any. */
 int cga_info(const cga_t* a, cga_sizes* out);

@@ -31,6 +31,9 @@ EXPORTS = (
     "cga_grid_from_box", "cga_build", "cga_merge", "cga_project", "cga_nn_query",
     "cga_decode", "cga_info", "cga_view", "cga2d_info", "cga2d_view", "cga_download",
     "cga2d_download", "cga_free", "cga2d_free", "cga_strerror", "cga_kernel_launches",
+    "cga_build_batch", "cga_merge_batch", "cga_project_batch", "cga_nn_query_batch",
+    "cga_pipeline_create", "cga_pipeline_run", "cga_pipeline_run_graph", "cga_pipeline_view",
+    "cga_pipeline_view_xy", "cga_pipeline_free",
 )
 
 
@@ -318,3 +321,189 @@ def cga_decode(a: Cga, out=None, stream=None):
 
 def kernel_launches() -> int:
     return int(load().cga_kernel_launches())
+
+
+# -------------------------------------------------------------------- batches
+class Cloud(ctypes.Structure):
+    _fields_ = [("d_xyz", ctypes.c_void_p), ("n", ctypes.c_uint64), ("grid", Grid),
+                ("h_xform12", ctypes.c_void_p)]
+
+
+class Queries(ctypes.Structure):
+    _fields_ = [("d_q", ctypes.c_void_p), ("m", ctypes.c_uint64), ("d_idx", ctypes.c_void_p),
+                ("d_dist2", ctypes.c_void_p)]
+
+
+class PipelineItem(ctypes.Structure):
+    _fields_ = [("d_xyz", ctypes.c_void_p), ("n", ctypes.c_uint64), ("grid", Grid),
+                ("xform12", ctypes.c_float * 12), ("d_q", ctypes.c_void_p), ("m", ctypes.c_uint64),
+                ("d_idx", ctypes.c_void_p), ("d_dist2", ctypes.c_void_p)]
+
+
+def _setup_batch(lib):
+    if getattr(lib, "_batch_ready", False):
+        return
+    P, U32, I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int
+    lib.cga_build_batch.argtypes = [P, U32, P, P, P]
+    lib.cga_merge_batch.argtypes = [P, P, U32, P, P, P]
+    lib.cga_project_batch.argtypes = [P, P, U32, P, P, P]
+    lib.cga_nn_query_batch.argtypes = [P, P, U32, P, P]
+    lib.cga_pipeline_create.argtypes = [P, U32, P, P, ctypes.POINTER(ctypes.c_void_p)]
+    lib.cga_pipeline_run.argtypes = [P, P]
+    lib.cga_pipeline_run_graph.argtypes = [P, P]
+    lib.cga_pipeline_view.argtypes = [P, U32, I, ctypes.POINTER(ctypes.c_void_p)]
+    lib.cga_pipeline_view_xy.argtypes = [P, U32, ctypes.POINTER(ctypes.c_void_p)]
+    lib.cga_pipeline_free.argtypes = [P]
+    lib.cga_pipeline_free.restype = None
+    lib._batch_ready = True
+
+
+def _ptr_array(handles):
+    arr = (ctypes.c_void_p * max(len(handles), 1))()
+    for i, h in enumerate(handles):
+        arr[i] = h.ptr if isinstance(h, (Cga, Cga2d)) else h
+    return arr
+
+
+def cga_build_batch(points_list, grids, xforms=None, stream=None, allocator="torch"):
+    """One launch set for many clouds.  points_list: float32 CUDA tensors (n_i, 3);
+    grids: one Grid or a list; xforms: None or a list of None / 12 floats."""
+    lib = load()
+    _setup_batch(lib)
+    k = len(points_list)
+    grids = grids if isinstance(grids, (list, tuple)) else [grids] * k
+    xforms = xforms if xforms is not None else [None] * k
+    clouds = (Cloud * max(k, 1))()
+    keep = []
+    for i, (pts, g, x) in enumerate(zip(points_list, grids, xforms)):
+        _dev_f32(pts, "cga_build_batch")
+        clouds[i].d_xyz = pts.data_ptr()
+        clouds[i].n = pts.numel() // 3
+        clouds[i].grid = g
+        if x is not None:
+            xa = np.ascontiguousarray(np.asarray(x, np.float32).reshape(12))
+            keep.append(xa)
+            clouds[i].h_xform12 = xa.ctypes.data
+    out = (ctypes.c_void_p * max(k, 1))()
+    _check(lib.cga_build_batch(clouds, k, _alloc_arg(allocator), _stream(stream), out),
+           "cga_build_batch")
+    return [Cga(ctypes.c_void_p(out[i]), grids[i]) for i in range(k)]
+
+
+def cga_merge_batch(a_list, b_list, stream=None, allocator="torch"):
+    lib = load()
+    _setup_batch(lib)
+    k = len(a_list)
+    out = (ctypes.c_void_p * max(k, 1))()
+    _check(lib.cga_merge_batch(_ptr_array(a_list), _ptr_array(b_list), k, _alloc_arg(allocator),
+                               _stream(stream), out), "cga_merge_batch")
+    return [Cga(ctypes.c_void_p(out[i]), a_list[i].grid) for i in range(k)]
+
+
+def cga_project_batch(a_list, planes, stream=None, allocator="torch"):
+    lib = load()
+    _setup_batch(lib)
+    k = len(a_list)
+    pl = [PLANES[p] if isinstance(p, str) else int(p) for p in
+          (planes if isinstance(planes, (list, tuple)) else [planes] * k)]
+    parr = (ctypes.c_int * max(k, 1))(*pl)
+    out = (ctypes.c_void_p * max(k, 1))()
+    _check(lib.cga_project_batch(_ptr_array(a_list), parr, k, _alloc_arg(allocator),
+                                 _stream(stream), out), "cga_project_batch")
+    return [Cga2d(ctypes.c_void_p(out[i]), a_list[i].grid.bits, pl[i]) for i in range(k)]
+
+
+def cga_nn_query_batch(a_list, queries_list, stream=None, allocator="torch"):
+    """Returns [(idx int32, dist2 int64)] per item."""
+    torch = _torch()
+    lib = load()
+    _setup_batch(lib)
+    k = len(a_list)
+    qs = (Queries * max(k, 1))()
+    res = []
+    for i, q in enumerate(queries_list):
+        _dev_f32(q, "cga_nn_query_batch")
+        m = q.numel() // 3
+        idx = torch.empty(m, dtype=torch.int32, device=q.device)
+        d2 = torch.empty(m, dtype=torch.int64, device=q.device)
+        qs[i].d_q, qs[i].m, qs[i].d_idx, qs[i].d_dist2 = q.data_ptr(), m, idx.data_ptr(), d2.data_ptr()
+        res.append((idx, d2))
+    _check(lib.cga_nn_query_batch(_ptr_array(a_list), qs, k, _alloc_arg(allocator),
+                                  _stream(stream)), "cga_nn_query_batch")
+    return res
+
+
+class _View(Cga):
+    """Non-owning handle of a pipeline result (freeing it is a no-op)."""
+
+    def free(self):
+        self.ptr = None
+
+
+class _View2d(Cga2d):
+    def free(self):
+        self.ptr = None
+
+
+class Pipeline:
+    """Pre-planned batch: build + transformed twin + merge + xy projection + NN
+    for many clouds, queued by run() or replayed from a CUDA graph by run_graph()."""
+
+    def __init__(self, points_list, grids, xforms, queries_list, stream=None, allocator="torch"):
+        torch = _torch()
+        lib = load()
+        _setup_batch(lib)
+        k = len(points_list)
+        grids = grids if isinstance(grids, (list, tuple)) else [grids] * k
+        self.grids = grids
+        items = (PipelineItem * k)()
+        self.idx, self.dist2 = [], []
+        for i in range(k):
+            pts, q = points_list[i], queries_list[i]
+            _dev_f32(pts, "Pipeline")
+            it = items[i]
+            it.d_xyz, it.n, it.grid = pts.data_ptr(), pts.numel() // 3, grids[i]
+            x = np.asarray(xforms[i], np.float32).reshape(12)
+            for j in range(12):
+                it.xform12[j] = float(x[j])
+            m = 0 if q is None else q.numel() // 3
+            idx = torch.empty(m, dtype=torch.int32, device="cuda")
+            d2 = torch.empty(m, dtype=torch.int64, device="cuda")
+            if m:
+                _dev_f32(q, "Pipeline")
+                it.d_q, it.m, it.d_idx, it.d_dist2 = q.data_ptr(), m, idx.data_ptr(), d2.data_ptr()
+            self.idx.append(idx)
+            self.dist2.append(d2)
+        self._keep = (points_list, queries_list)
+        self.ptr = ctypes.c_void_p()
+        _check(lib.cga_pipeline_create(items, k, _alloc_arg(allocator), _stream(stream),
+                                       ctypes.byref(self.ptr)), "cga_pipeline_create")
+        self.count = k
+
+    def run(self, stream=None):
+        _check(load().cga_pipeline_run(self.ptr, _stream(stream)), "cga_pipeline_run")
+
+    def run_graph(self, stream=None):
+        _check(load().cga_pipeline_run_graph(self.ptr, _stream(stream)), "cga_pipeline_run_graph")
+
+    def view(self, i: int, which: str) -> Cga:
+        w = {"cloud": 0, "twin": 1, "merged": 2}[which]
+        out = ctypes.c_void_p()
+        _check(load().cga_pipeline_view(self.ptr, i, w, ctypes.byref(out)), "cga_pipeline_view")
+        return _View(out, self.grids[i])
+
+    def view_xy(self, i: int) -> Cga2d:
+        out = ctypes.c_void_p()
+        _check(load().cga_pipeline_view_xy(self.ptr, i, ctypes.byref(out)), "cga_pipeline_view_xy")
+        return _View2d(out, self.grids[i].bits, 0)
+
+    def free(self):
+        if self.ptr:
+            load().cga_pipeline_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

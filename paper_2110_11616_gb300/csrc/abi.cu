@@ -7,6 +7,7 @@
 #include <atomic>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "../../include/cga.h"
 #include "cga_impl.h"
@@ -21,6 +22,7 @@ struct cga {
   cga_allocator alloc;
   bool has_alloc;
   cudaStream_t stream;
+  bool view = false;  // arrays owned by a pipeline; cga_free leaves them alone
 };
 
 struct cga2d {
@@ -31,6 +33,7 @@ struct cga2d {
   cga_allocator alloc;
   bool has_alloc;
   cudaStream_t stream;
+  bool view = false;
 };
 
 namespace libcga {
@@ -177,7 +180,7 @@ cga* new_cga(const cga_grid& g, const cga_allocator* A, cudaStream_t s, uint64_t
 }
 
 void release(cga* h) {
-  if (h == nullptr) return;
+  if (h == nullptr || h->view) return;
   dfree(&h->alloc, h->has_alloc, h->mem, h->stream);
   delete h;
 }
@@ -478,8 +481,585 @@ int cga2d_download(const cga2d_t* p, uint16_t* h_U_index, uint32_t* h_U_pointer,
 void cga_free(cga_t* a) { release(a); }
 
 void cga2d_free(cga2d_t* p) {
-  if (p == nullptr) return;
+  if (p == nullptr || p->view) return;
   dfree(&p->alloc, p->has_alloc, p->mem, p->stream);
+  delete p;
+}
+
+
+// ------------------------------------------------------------------ batches
+
+int cga_build_batch(const cga_cloud* clouds, uint32_t count, const cga_allocator* A,
+                    void* stream, cga_t** out) {
+  if (out == nullptr || (count > 0 && clouds == nullptr)) return CGA_ERR_INVALID_ARG;
+  if (A != nullptr && (A->alloc == nullptr || A->free == nullptr)) return CGA_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < count; ++i) {
+    const cga_cloud& c = clouds[i];
+    if (!grid_ok(&c.grid) || c.n > CGA_MAX_POINTS || (c.n > 0 && c.d_xyz == nullptr)) {
+      return CGA_ERR_INVALID_ARG;
+    }
+  }
+  if (count == 0) return CGA_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<libcga::SortSeg> segs(count);
+  std::vector<cga*> hs(count, nullptr);
+  uint64_t tiles = 0;
+  uint32_t max_passes = 0;
+  bool key64 = false;
+  int rc = CGA_OK;
+  for (uint32_t i = 0; i < count && rc == CGA_OK; ++i) {
+    const cga_cloud& c = clouds[i];
+    hs[i] = new_cga(c.grid, A, s, c.n);
+    if (hs[i] == nullptr) {
+      rc = CGA_ERR_OOM;
+      break;
+    }
+    libcga::SortSeg& sg = segs[i];
+    sg = libcga::SortSeg{};
+    sg.xyz = c.d_xyz;
+    sg.scale = c.grid.scale;
+    for (int a = 0; a < 3; ++a) sg.off[a] = c.grid.offset[a];
+    if (c.h_xform12 != nullptr) {
+      std::memcpy(sg.X, c.h_xform12, sizeof(sg.X));
+      sg.has_x = 1;
+    }
+    sg.n_host = (uint32_t)c.n;
+    sg.bits = c.grid.bits;
+    sg.key_bits = 3 * c.grid.bits;
+    sg.passes = (sg.key_bits + libcga::kRadixBits - 1) / libcga::kRadixBits;
+    sg.tile_base = (uint32_t)tiles;
+    sg.num_tiles = (uint32_t)((c.n + libcga::kTile - 1) / libcga::kTile);
+    sg.key_base = tiles * libcga::kTile;
+    sg.out = hs[i]->lv;
+    tiles += sg.num_tiles;
+    max_passes = std::max(max_passes, sg.passes);
+    key64 = key64 || sg.key_bits > 32;
+  }
+  if (rc == CGA_OK && tiles > 0xFFFFFFFFull / libcga::kTile) rc = CGA_ERR_INVALID_ARG;
+  void* scratch = nullptr;
+  if (rc == CGA_OK) {
+    const uint64_t keys = tiles * libcga::kTile;
+    scratch = dalloc(A, libcga::sort_scratch_bytes(keys, (uint32_t)tiles, (int)count, key64), s);
+    if (scratch == nullptr) rc = CGA_ERR_OOM;
+    if (rc == CGA_OK) {
+      const libcga::SortScratch sc =
+          libcga::sort_scratch_carve(scratch, keys, (uint32_t)tiles, (int)count, key64);
+      rc = cuda_rc(libcga::run_sort_pipeline(segs.data(), (int)count, (uint32_t)tiles,
+                                             max_passes, key64, sc, s));
+      dfree(A, A != nullptr, scratch, s);
+    }
+  }
+  if (rc != CGA_OK) {
+    for (cga* h : hs) release(h);
+    return rc;
+  }
+  for (uint32_t i = 0; i < count; ++i) out[i] = hs[i];
+  return CGA_OK;
+}
+
+namespace {
+
+// Merge pair table + output handles for `count` pairs.
+int plan_merges(const cga_t* const* a, const cga_t* const* b, uint32_t count,
+                const cga_allocator* A, cudaStream_t s, std::vector<libcga::MergePair>& pairs,
+                std::vector<cga*>& hs, uint32_t& total_spl, uint32_t& total_tiles) {
+  pairs.assign(count, libcga::MergePair{});
+  hs.assign(count, nullptr);
+  uint64_t spl = 0, tiles = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    if (a[i] == nullptr || b[i] == nullptr) return CGA_ERR_INVALID_ARG;
+    if (!same_grid(a[i]->grid, b[i]->grid)) return CGA_ERR_GRID_MISMATCH;
+    const uint64_t cap = std::min<uint64_t>(a[i]->lv.cap + b[i]->lv.cap, pow2(3 * a[i]->grid.bits));
+    if (cap > CGA_MAX_POINTS) return CGA_ERR_INVALID_ARG;
+  }
+  for (uint32_t i = 0; i < count; ++i) {
+    const uint64_t cap = std::min<uint64_t>(a[i]->lv.cap + b[i]->lv.cap, pow2(3 * a[i]->grid.bits));
+    hs[i] = new_cga(a[i]->grid, A, s, cap);
+    if (hs[i] == nullptr) return CGA_ERR_OOM;
+    libcga::MergePair& P = pairs[i];
+    P.a = a[i]->lv;
+    P.b = b[i]->lv;
+    P.out = hs[i]->lv;
+    P.spl_a = a[i]->lv.cap > 0 ? (uint32_t)((a[i]->lv.cap - 1) / libcga::kMergeHalf) : 0u;
+    P.spl_b = b[i]->lv.cap > 0 ? (uint32_t)((b[i]->lv.cap - 1) / libcga::kMergeHalf) : 0u;
+    P.spl_base = (uint32_t)spl;
+    P.tile_base = (uint32_t)tiles;
+    P.num_tiles = P.spl_a + P.spl_b + 1;
+    spl += P.spl_a + P.spl_b;
+    tiles += P.num_tiles;
+    if (tiles > 0x7FFFFFFFull) return CGA_ERR_INVALID_ARG;
+  }
+  total_spl = (uint32_t)spl;
+  total_tiles = (uint32_t)tiles;
+  return CGA_OK;
+}
+
+}  // namespace
+
+int cga_merge_batch(const cga_t* const* a, const cga_t* const* b, uint32_t count,
+                    const cga_allocator* A, void* stream, cga_t** out) {
+  if (out == nullptr || (count > 0 && (a == nullptr || b == nullptr))) return CGA_ERR_INVALID_ARG;
+  if (A != nullptr && (A->alloc == nullptr || A->free == nullptr)) return CGA_ERR_INVALID_ARG;
+  if (count == 0) return CGA_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<libcga::MergePair> pairs;
+  std::vector<cga*> hs;
+  uint32_t total_spl = 0, total_tiles = 0;
+  int rc = plan_merges(a, b, count, A, s, pairs, hs, total_spl, total_tiles);
+  if (rc == CGA_OK) {
+    void* scratch = dalloc(A, libcga::merge_scratch_bytes(total_spl, total_tiles, (int)count), s);
+    if (scratch == nullptr) {
+      rc = CGA_ERR_OOM;
+    } else {
+      const libcga::MergeScratch sc =
+          libcga::merge_scratch_carve(scratch, total_spl, total_tiles, (int)count);
+      rc = cuda_rc(libcga::run_merge(pairs.data(), (int)count, total_spl, total_tiles, sc, s));
+      dfree(A, A != nullptr, scratch, s);
+    }
+  }
+  if (rc != CGA_OK) {
+    for (cga* h : hs) release(h);
+    return rc;
+  }
+  for (uint32_t i = 0; i < count; ++i) out[i] = hs[i];
+  return CGA_OK;
+}
+
+int cga_project_batch(const cga_t* const* a, const int* planes, uint32_t count,
+                      const cga_allocator* A, void* stream, cga2d_t** out) {
+  if (out == nullptr || (count > 0 && (a == nullptr || planes == nullptr))) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  if (A != nullptr && (A->alloc == nullptr || A->free == nullptr)) return CGA_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < count; ++i) {
+    if (a[i] == nullptr || planes[i] < CGA_PLANE_XY || planes[i] > CGA_PLANE_YZ) {
+      return CGA_ERR_INVALID_ARG;
+    }
+  }
+  if (count == 0) return CGA_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<cga2d*> ps(count, nullptr);
+  std::vector<libcga::ProjPair> xy;
+  std::vector<libcga::SortSeg> segs;
+  uint64_t tiles = 0, max_cap1 = 0;
+  int rc = CGA_OK;
+  for (uint32_t i = 0; i < count && rc == CGA_OK; ++i) {
+    const uint32_t b = a[i]->grid.bits;
+    uint64_t cap, cap1;
+    if (planes[i] == CGA_PLANE_XY) {
+      cap = a[i]->lv.cap1;
+      cap1 = a[i]->lv.cap2;
+    } else {
+      cap = std::min<uint64_t>(a[i]->lv.cap, pow2(2 * b));
+      cap1 = std::min<uint64_t>(cap, pow2(b));
+    }
+    void* mem = dalloc(A, levels_bytes(cap, cap1, 0, 2), s);
+    cga2d* p = mem ? new (std::nothrow) cga2d{} : nullptr;
+    if (p == nullptr) {
+      if (mem) dfree(A, A != nullptr, mem, s);
+      rc = CGA_ERR_OOM;
+      break;
+    }
+    p->bits = b;
+    p->plane = planes[i];
+    p->lv = levels_carve(mem, b, cap, cap1, 0, 2);
+    p->mem = mem;
+    p->has_alloc = A != nullptr;
+    if (A != nullptr) p->alloc = *A;
+    p->stream = s;
+    ps[i] = p;
+    if (planes[i] == CGA_PLANE_XY) {
+      xy.push_back(libcga::ProjPair{a[i]->lv, p->lv});
+      max_cap1 = std::max<uint64_t>(max_cap1, a[i]->lv.cap1);
+    } else {
+      libcga::SortSeg sg{};
+      sg.src = a[i]->lv;
+      sg.plane = planes[i];
+      sg.from_cga = 1;
+      sg.bits = b;
+      sg.key_bits = 2 * b;
+      sg.passes = (sg.key_bits + libcga::kRadixBits - 1) / libcga::kRadixBits;
+      sg.tile_base = (uint32_t)tiles;
+      sg.num_tiles = (uint32_t)((a[i]->lv.cap + libcga::kTile - 1) / libcga::kTile);
+      sg.key_base = tiles * libcga::kTile;
+      sg.out = p->lv;
+      tiles += sg.num_tiles;
+      segs.push_back(sg);
+    }
+  }
+  if (rc == CGA_OK && !xy.empty()) {
+    void* tab = dalloc(A, sizeof(libcga::ProjPair) * xy.size(), s);
+    if (tab == nullptr) {
+      rc = CGA_ERR_OOM;
+    } else {
+      cudaError_t e = cudaMemcpyAsync(tab, xy.data(), sizeof(libcga::ProjPair) * xy.size(),
+                                      cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) {
+        e = libcga::run_project_xy_device(static_cast<libcga::ProjPair*>(tab), (int)xy.size(),
+                                          max_cap1, s);
+      }
+      rc = cuda_rc(e);
+      dfree(A, A != nullptr, tab, s);
+    }
+  }
+  if (rc == CGA_OK && !segs.empty()) {
+    uint32_t max_passes = 0;
+    for (const auto& sg : segs) max_passes = std::max(max_passes, sg.passes);
+    const uint64_t keys = tiles * libcga::kTile;
+    void* scratch =
+        dalloc(A, libcga::sort_scratch_bytes(keys, (uint32_t)tiles, (int)segs.size(), false), s);
+    if (scratch == nullptr) {
+      rc = CGA_ERR_OOM;
+    } else {
+      const libcga::SortScratch sc =
+          libcga::sort_scratch_carve(scratch, keys, (uint32_t)tiles, (int)segs.size(), false);
+      rc = cuda_rc(libcga::run_sort_pipeline(segs.data(), (int)segs.size(), (uint32_t)tiles,
+                                             max_passes, false, sc, s));
+      dfree(A, A != nullptr, scratch, s);
+    }
+  }
+  if (rc != CGA_OK) {
+    for (cga2d* p : ps) cga2d_free(p);
+    return rc;
+  }
+  for (uint32_t i = 0; i < count; ++i) out[i] = ps[i];
+  return CGA_OK;
+}
+
+int cga_nn_query_batch(const cga_t* const* a, const cga_queries* q, uint32_t count,
+                       const cga_allocator* A, void* stream) {
+  if (count > 0 && (a == nullptr || q == nullptr)) return CGA_ERR_INVALID_ARG;
+  if (A != nullptr && (A->alloc == nullptr || A->free == nullptr)) return CGA_ERR_INVALID_ARG;
+  std::vector<libcga::NnSeg> segs;
+  uint64_t tiles = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    if (a[i] == nullptr || q[i].m > libcga::kNnMaxQueries) return CGA_ERR_INVALID_ARG;
+    if (q[i].m > 0 && (q[i].d_q == nullptr || q[i].d_idx == nullptr || q[i].d_dist2 == nullptr)) {
+      return CGA_ERR_INVALID_ARG;
+    }
+    if (q[i].m == 0) continue;
+    libcga::NnSeg sg{};
+    sg.a = a[i]->lv;
+    sg.scale = a[i]->grid.scale;
+    for (int k = 0; k < 3; ++k) sg.off[k] = a[i]->grid.offset[k];
+    sg.q = q[i].d_q;
+    sg.m = (uint32_t)q[i].m;
+    sg.idx = q[i].d_idx;
+    sg.d2 = reinterpret_cast<unsigned long long*>(q[i].d_dist2);
+    sg.tile_base = (uint32_t)tiles;
+    sg.num_tiles = (uint32_t)((q[i].m + libcga::kTile - 1) / libcga::kTile);
+    tiles += sg.num_tiles;
+    segs.push_back(sg);
+  }
+  if (segs.empty()) return CGA_OK;
+  if (tiles > 0xFFFFFFFFull / libcga::kTile) return CGA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* scratch = dalloc(A, libcga::nn_scratch_bytes((uint32_t)tiles, (int)segs.size()), s);
+  if (scratch == nullptr) return CGA_ERR_OOM;
+  const int rc = cuda_rc(libcga::run_nn(segs.data(), (int)segs.size(), (uint32_t)tiles, scratch, s));
+  dfree(A, A != nullptr, scratch, s);
+  return rc;
+}
+
+// ----------------------------------------------------------------- pipeline
+
+struct cga_pipeline {
+  uint32_t S = 0;
+  std::vector<cga> views;      // 3 per item: cloud, twin, merged
+  std::vector<cga2d> xy;       // 1 per item
+  void* arena = nullptr;
+  cga_allocator alloc{};
+  bool has_alloc = false;
+  cudaStream_t stream = nullptr;
+  libcga::SortScratch build{};
+  uint32_t build_tiles = 0, build_passes = 0;
+  bool key64 = false;
+  libcga::MergeScratch merge{};
+  uint32_t merge_spl = 0, merge_tiles = 0;
+  libcga::ProjPair* d_proj = nullptr;
+  uint64_t max_cap1 = 0;
+  libcga::NnTables nn{};
+  uint32_t nn_tiles = 0, nn_segs = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t graph_kernels = 0;
+};
+
+namespace {
+
+struct Bump {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += align_up(bytes);
+    return o;
+  }
+};
+
+int pipeline_queue(cga_pipeline* p, cudaStream_t s) {
+  cudaError_t e = libcga::run_sort_device((int)(2 * p->S), p->build_tiles, p->build_passes,
+                                          p->key64, 3, p->build, s);
+  if (e == cudaSuccess) e = libcga::run_merge_device((int)p->S, p->merge_spl, p->merge_tiles, p->merge, s);
+  if (e == cudaSuccess) e = libcga::run_project_xy_device(p->d_proj, (int)p->S, p->max_cap1, s);
+  if (e == cudaSuccess && p->nn_segs > 0) {
+    e = libcga::run_nn_device((int)p->nn_segs, p->nn_tiles, p->nn, s);
+  }
+  return cuda_rc(e);
+}
+
+}  // namespace
+
+int cga_pipeline_create(const cga_pipeline_item* items, uint32_t count, const cga_allocator* A,
+                        void* stream, cga_pipeline_t** out) {
+  if (out == nullptr || count == 0 || items == nullptr) return CGA_ERR_INVALID_ARG;
+  if (A != nullptr && (A->alloc == nullptr || A->free == nullptr)) return CGA_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < count; ++i) {
+    const cga_pipeline_item& it = items[i];
+    if (!grid_ok(&it.grid) || it.n > CGA_MAX_POINTS / 2 || (it.n > 0 && it.d_xyz == nullptr) ||
+        it.m > libcga::kNnMaxQueries ||
+        (it.m > 0 && (it.d_q == nullptr || it.d_idx == nullptr || it.d_dist2 == nullptr))) {
+      return CGA_ERR_INVALID_ARG;
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cga_pipeline* p = new (std::nothrow) cga_pipeline();
+  if (p == nullptr) return CGA_ERR_OOM;
+  const uint32_t S = count;
+  p->S = S;
+  p->stream = s;
+  p->has_alloc = A != nullptr;
+  if (A != nullptr) p->alloc = *A;
+  // --- layout
+  Bump bump;
+  std::vector<size_t> lv_off(4 * (size_t)S);
+  std::vector<uint64_t> caps(3 * (size_t)S);
+  uint64_t build_tiles = 0, spl = 0, mtiles = 0, nn_tiles = 0;
+  uint32_t nn_segs = 0;
+  for (uint32_t i = 0; i < S; ++i) {
+    const uint32_t b = items[i].grid.bits;
+    const uint64_t n = items[i].n;
+    const uint64_t cm = std::min<uint64_t>(2 * n, pow2(3 * b));
+    caps[3 * i] = n;
+    caps[3 * i + 1] = n;
+    caps[3 * i + 2] = cm;
+    for (int k = 0; k < 3; ++k) {
+      const uint64_t c = caps[3 * i + k];
+      lv_off[4 * i + k] =
+          bump.take(levels_bytes(c, std::min<uint64_t>(c, pow2(2 * b)), std::min<uint64_t>(c, pow2(b)), 3));
+    }
+    const uint64_t pc = std::min<uint64_t>(cm, pow2(2 * b)), pc1 = std::min<uint64_t>(cm, pow2(b));
+    lv_off[4 * i + 3] = bump.take(levels_bytes(pc, pc1, 0, 2));
+    const uint64_t t = (n + libcga::kTile - 1) / libcga::kTile;
+    build_tiles += 2 * t;
+    const uint64_t sa = n > 0 ? (n - 1) / libcga::kMergeHalf : 0;
+    spl += 2 * sa;
+    mtiles += 2 * sa + 1;
+    if (items[i].m > 0) {
+      nn_tiles += (items[i].m + libcga::kTile - 1) / libcga::kTile;
+      ++nn_segs;
+    }
+  }
+  if (build_tiles > 0xFFFFFFFFull / libcga::kTile || nn_tiles > 0xFFFFFFFFull / libcga::kTile ||
+      mtiles > 0x7FFFFFFFull) {
+    delete p;
+    return CGA_ERR_INVALID_ARG;
+  }
+  bool key64 = false;
+  uint32_t passes = 0;
+  for (uint32_t i = 0; i < S; ++i) {
+    key64 = key64 || 3 * items[i].grid.bits > 32;
+    passes = std::max<uint32_t>(passes, (3 * items[i].grid.bits + 7) / 8);
+  }
+  const size_t o_build = bump.take(libcga::sort_scratch_bytes(build_tiles * libcga::kTile,
+                                                              (uint32_t)build_tiles, (int)(2 * S), key64));
+  const size_t o_merge = bump.take(libcga::merge_scratch_bytes((uint32_t)spl, (uint32_t)mtiles, (int)S));
+  const size_t o_proj = bump.take(sizeof(libcga::ProjPair) * S);
+  const size_t o_nn = bump.take(nn_segs ? libcga::nn_scratch_bytes((uint32_t)nn_tiles, (int)nn_segs) : 0);
+  p->arena = dalloc(A, bump.off, s);
+  if (p->arena == nullptr) {
+    delete p;
+    return CGA_ERR_OOM;
+  }
+  char* base = static_cast<char*>(p->arena);
+  // --- views
+  p->views.resize(3 * (size_t)S);
+  p->xy.resize(S);
+  for (uint32_t i = 0; i < S; ++i) {
+    const uint32_t b = items[i].grid.bits;
+    for (int k = 0; k < 3; ++k) {
+      const uint64_t c = caps[3 * i + k];
+      cga& v = p->views[3 * i + k];
+      v.grid = items[i].grid;
+      v.lv = levels_carve(base + lv_off[4 * i + k], b, c, std::min<uint64_t>(c, pow2(2 * b)),
+                          std::min<uint64_t>(c, pow2(b)), 3);
+      v.mem = nullptr;
+      v.stream = s;
+      v.view = true;
+    }
+    const uint64_t cm = caps[3 * i + 2];
+    cga2d& x = p->xy[i];
+    x.bits = b;
+    x.plane = CGA_PLANE_XY;
+    x.lv = levels_carve(base + lv_off[4 * i + 3], b, std::min<uint64_t>(cm, pow2(2 * b)),
+                        std::min<uint64_t>(cm, pow2(b)), 0, 2);
+    x.mem = nullptr;
+    x.stream = s;
+    x.view = true;
+  }
+  // --- tables
+  std::vector<libcga::SortSeg> bsegs(2 * (size_t)S);
+  uint64_t tb = 0;
+  for (uint32_t i = 0; i < S; ++i) {
+    for (int k = 0; k < 2; ++k) {
+      libcga::SortSeg& sg = bsegs[2 * i + k];
+      sg = libcga::SortSeg{};
+      sg.xyz = items[i].d_xyz;
+      sg.scale = items[i].grid.scale;
+      for (int a = 0; a < 3; ++a) sg.off[a] = items[i].grid.offset[a];
+      if (k == 1) {
+        std::memcpy(sg.X, items[i].xform12, sizeof(sg.X));
+        sg.has_x = 1;
+      }
+      sg.n_host = (uint32_t)items[i].n;
+      sg.bits = items[i].grid.bits;
+      sg.key_bits = 3 * sg.bits;
+      sg.passes = (sg.key_bits + 7) / 8;
+      sg.tile_base = (uint32_t)tb;
+      sg.num_tiles = (uint32_t)((items[i].n + libcga::kTile - 1) / libcga::kTile);
+      sg.key_base = tb * libcga::kTile;
+      sg.out = p->views[3 * i + k].lv;
+      tb += sg.num_tiles;
+    }
+  }
+  p->build = libcga::sort_scratch_carve(base + o_build, build_tiles * libcga::kTile,
+                                        (uint32_t)build_tiles, (int)(2 * S), key64);
+  p->build_tiles = (uint32_t)build_tiles;
+  p->build_passes = passes;
+  p->key64 = key64;
+  std::vector<libcga::MergePair> pairs(S);
+  uint64_t sb = 0, mb = 0;
+  for (uint32_t i = 0; i < S; ++i) {
+    libcga::MergePair& P = pairs[i];
+    P.a = p->views[3 * i].lv;
+    P.b = p->views[3 * i + 1].lv;
+    P.out = p->views[3 * i + 2].lv;
+    P.spl_a = P.spl_b = items[i].n > 0 ? (uint32_t)((items[i].n - 1) / libcga::kMergeHalf) : 0u;
+    P.spl_base = (uint32_t)sb;
+    P.tile_base = (uint32_t)mb;
+    P.num_tiles = P.spl_a + P.spl_b + 1;
+    sb += P.spl_a + P.spl_b;
+    mb += P.num_tiles;
+  }
+  p->merge = libcga::merge_scratch_carve(base + o_merge, (uint32_t)spl, (uint32_t)mtiles, (int)S);
+  p->merge_spl = (uint32_t)spl;
+  p->merge_tiles = (uint32_t)mtiles;
+  std::vector<libcga::ProjPair> proj(S);
+  for (uint32_t i = 0; i < S; ++i) {
+    proj[i] = libcga::ProjPair{p->views[3 * i + 2].lv, p->xy[i].lv};
+    p->max_cap1 = std::max<uint64_t>(p->max_cap1, p->views[3 * i + 2].lv.cap1);
+  }
+  p->d_proj = reinterpret_cast<libcga::ProjPair*>(base + o_proj);
+  std::vector<libcga::NnSeg> nsegs;
+  uint64_t nt = 0;
+  for (uint32_t i = 0; i < S; ++i) {
+    if (items[i].m == 0) continue;
+    libcga::NnSeg sg{};
+    sg.a = p->views[3 * i + 2].lv;
+    sg.scale = items[i].grid.scale;
+    for (int k = 0; k < 3; ++k) sg.off[k] = items[i].grid.offset[k];
+    sg.q = items[i].d_q;
+    sg.m = (uint32_t)items[i].m;
+    sg.idx = items[i].d_idx;
+    sg.d2 = reinterpret_cast<unsigned long long*>(items[i].d_dist2);
+    sg.tile_base = (uint32_t)nt;
+    sg.num_tiles = (uint32_t)((items[i].m + libcga::kTile - 1) / libcga::kTile);
+    nt += sg.num_tiles;
+    nsegs.push_back(sg);
+  }
+  p->nn_segs = nn_segs;
+  p->nn_tiles = (uint32_t)nn_tiles;
+  cudaError_t e = cudaMemcpyAsync(p->build.segs, bsegs.data(), sizeof(libcga::SortSeg) * bsegs.size(),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    e = cudaMemcpyAsync(p->merge.pairs, pairs.data(), sizeof(libcga::MergePair) * S,
+                        cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) {
+    e = cudaMemcpyAsync(p->d_proj, proj.data(), sizeof(libcga::ProjPair) * S,
+                        cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess && nn_segs > 0) {
+    p->nn = libcga::nn_tables(base + o_nn, (uint32_t)nn_tiles, (int)nn_segs);
+    e = libcga::nn_upload(nsegs.data(), (int)nn_segs, p->nn, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    dfree(A, A != nullptr, p->arena, s);
+    delete p;
+    return cuda_rc(e);
+  }
+  *out = p;
+  return CGA_OK;
+}
+
+int cga_pipeline_run(cga_pipeline_t* p, void* stream) {
+  if (p == nullptr) return CGA_ERR_INVALID_ARG;
+  return pipeline_queue(p, static_cast<cudaStream_t>(stream));
+}
+
+int cga_pipeline_run_graph(cga_pipeline_t* p, void* stream) {
+  if (p == nullptr) return CGA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->exec == nullptr) {
+    cudaError_t e = cudaSuccess;
+    if (p->cap_stream == nullptr) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_rc(e);
+    const uint64_t k0 = libcga::g_launches.load();
+    e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_rc(e);
+    const int rc = pipeline_queue(p, p->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(p->cap_stream, &g);
+    if (rc != CGA_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc != CGA_OK ? rc : cuda_rc(e);
+    }
+    p->graph_kernels = libcga::g_launches.load() - k0;
+    libcga::g_launches.fetch_sub(p->graph_kernels);  // counted on each replay instead
+    e = cudaGraphInstantiate(&p->exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      p->exec = nullptr;
+      return cuda_rc(e);
+    }
+    p->graph = g;
+  }
+  libcga::count_launch((unsigned)p->graph_kernels);
+  return cuda_rc(cudaGraphLaunch(p->exec, s));
+}
+
+int cga_pipeline_view(const cga_pipeline_t* p, uint32_t i, int which, const cga_t** out) {
+  if (p == nullptr || out == nullptr || i >= p->S || which < 0 || which > 2) return CGA_ERR_INVALID_ARG;
+  *out = &p->views[3 * (size_t)i + which];
+  return CGA_OK;
+}
+
+int cga_pipeline_view_xy(const cga_pipeline_t* p, uint32_t i, const cga2d_t** out) {
+  if (p == nullptr || out == nullptr || i >= p->S) return CGA_ERR_INVALID_ARG;
+  *out = &p->xy[i];
+  return CGA_OK;
+}
+
+void cga_pipeline_free(cga_pipeline_t* p) {
+  if (p == nullptr) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cap_stream) {
+    cudaStreamSynchronize(p->cap_stream);
+    cudaStreamDestroy(p->cap_stream);
+  }
+  dfree(p->has_alloc ? &p->alloc : nullptr, p->has_alloc, p->arena, p->stream);
   delete p;
 }
 

@@ -89,6 +89,10 @@ SortScratch sort_scratch_carve(void* base, uint64_t total_keys, uint32_t total_t
 cudaError_t run_radix_passes(int S, uint32_t total_tiles, uint32_t max_passes, bool key64,
                              const SortScratch& sc, cudaStream_t stream);
 
+// Sort pipeline with the segment table already on the device (sc.segs).
+cudaError_t run_sort_device(int S, uint32_t total_tiles, uint32_t max_passes, bool key64,
+                            int levels, const SortScratch& sc, cudaStream_t stream);
+
 // Queue the whole sort pipeline: header init, key generation (+ histograms),
 // radix passes, compaction.  `h_segs` is copied to the device first.
 cudaError_t run_sort_pipeline(const SortSeg* h_segs, int S, uint32_t total_tiles,
@@ -128,9 +132,18 @@ size_t merge_scratch_bytes(uint32_t total_spl, uint32_t total_tiles, int S);
 MergeScratch merge_scratch_carve(void* base, uint32_t total_spl, uint32_t total_tiles, int S);
 cudaError_t run_merge(const MergePair* h_pairs, int S, uint32_t total_spl, uint32_t total_tiles,
                       const MergeScratch& sc, cudaStream_t stream);
+// Merge with the pair table already on the device (sc.pairs).
+cudaError_t run_merge_device(int S, uint32_t total_spl, uint32_t total_tiles,
+                             const MergeScratch& sc, cudaStream_t stream);
 
 // Copy the top two levels of a CGA into a 2-level projection (plane xy).
 cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stream);
+struct ProjPair {
+  Levels a, out;
+};
+// S xy projections in one launch (pair table on the device).
+cudaError_t run_project_xy_device(const ProjPair* d_pairs, int S, uint64_t max_cap1,
+                                  cudaStream_t stream);
 
 // Exact NN: one segment per (CGA, query batch).  Queries occupy a slot space
 // of whole tiles (segment s owns slots [tile_base*kTile, (tile_base +
@@ -154,6 +167,17 @@ size_t nn_scratch_bytes(uint32_t total_tiles, int S);
 // kernel parameter).
 cudaError_t run_nn(const NnSeg* h_segs, int S, uint32_t total_tiles, void* scratch,
                    cudaStream_t stream);
+// Device-side tables of an NN batch carved from its scratch.
+struct NnTables {
+  Header* err;
+  NnSeg* segs;
+  SortScratch sort;
+};
+NnTables nn_tables(void* scratch, uint32_t total_tiles, int S);
+// Upload the NnSeg and sort-segment tables (pageable copies, not capturable).
+cudaError_t nn_upload(const NnSeg* h_segs, int S, const NnTables& t, cudaStream_t stream);
+// Run with the tables on the device (capturable: memsets and kernels only).
+cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream);
 
 int device_sm_count();
 

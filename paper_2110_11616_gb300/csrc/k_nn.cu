@@ -17,6 +17,7 @@
 // visited in Morton order of their voxel (a 4-pass radix sort of
 // (morton << 32 | index) keys), so neighbouring warps read neighbouring slabs.
 #include <algorithm>
+#include <new>
 
 #include "k_common.cuh"
 
@@ -237,56 +238,75 @@ size_t nn_scratch_bytes(uint32_t total_tiles, int S) {
          sort_scratch_bytes((uint64_t)total_tiles * kTile, total_tiles, S, true);
 }
 
+NnTables nn_tables(void* scratch, uint32_t total_tiles, int S) {
+  char* p = static_cast<char*>(scratch);
+  NnTables t{};
+  t.err = reinterpret_cast<Header*>(p);
+  p += align_up(sizeof(Header));
+  t.segs = reinterpret_cast<NnSeg*>(p);
+  p += align_up((size_t)S * sizeof(NnSeg));
+  t.sort = sort_scratch_carve(p, (uint64_t)total_tiles * kTile, total_tiles, S, true);
+  return t;
+}
+
+cudaError_t nn_upload(const NnSeg* h_segs, int S, const NnTables& t, cudaStream_t stream) {
+  SortSeg* ss = new (std::nothrow) SortSeg[S]();
+  if (ss == nullptr) return cudaErrorMemoryAllocation;
+  for (int s = 0; s < S; ++s) {
+    ss[s].n_host = h_segs[s].m;
+    ss[s].passes = 4;
+    ss[s].bit0 = 32;
+    ss[s].key_base = (uint64_t)h_segs[s].tile_base * kTile;
+    ss[s].tile_base = h_segs[s].tile_base;
+    ss[s].num_tiles = h_segs[s].num_tiles;
+    ss[s].out.hdr = t.err;
+  }
+  cudaError_t e = cudaMemcpyAsync(t.segs, h_segs, sizeof(NnSeg) * S, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) {
+    e = cudaMemcpyAsync(t.sort.segs, ss, sizeof(SortSeg) * S, cudaMemcpyHostToDevice, stream);
+  }
+  delete[] ss;
+  return e;
+}
+
+static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
+                          uint32_t total_tiles, const unsigned long long* order,
+                          const unsigned int* order_err, cudaStream_t stream) {
+  const uint32_t total_slots = total_tiles * (uint32_t)kTile;
+  const uint32_t blocks =
+      std::min<uint32_t>((total_slots + 7) / 8, (uint32_t)device_sm_count() * 8);
+  k_nn_warp<<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order, order_err);
+  count_launch(1);
+}
+
+cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream) {
+  if (total_tiles == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(t.err, 0, sizeof(Header), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t.sort.hist, 0, t.sort.zero_bytes, stream);
+  if (e != cudaSuccess) return e;
+  k_nn_keys<<<total_tiles * (kTile / 256), 256, 0, stream>>>(
+      t.segs, S, static_cast<unsigned long long*>(t.sort.keys0), t.sort.hist);
+  count_launch(1);
+  e = run_radix_passes(S, total_tiles, 4, true, t.sort, stream);
+  if (e != cudaSuccess) return e;
+  // four passes leave the sorted keys in keys0
+  launch_search(t.segs, S, NnSeg{}, total_tiles,
+                static_cast<const unsigned long long*>(t.sort.keys0), &t.err->err, stream);
+  return cudaGetLastError();
+}
+
 cudaError_t run_nn(const NnSeg* h_segs, int S, uint32_t total_tiles, void* scratch,
                    cudaStream_t stream) {
   if (total_tiles == 0) return cudaSuccess;
-  const unsigned long long* order = nullptr;
-  const unsigned int* order_err = nullptr;
-  const NnSeg* d_segs = nullptr;
-  const uint32_t total_slots = total_tiles * (uint32_t)kTile;
-  if (scratch != nullptr) {
-    char* p = static_cast<char*>(scratch);
-    Header* eh = reinterpret_cast<Header*>(p);
-    p += align_up(sizeof(Header));
-    NnSeg* segs = reinterpret_cast<NnSeg*>(p);
-    p += align_up((size_t)S * sizeof(NnSeg));
-    const SortScratch sc = sort_scratch_carve(p, (uint64_t)total_slots, total_tiles, S, true);
-    SortSeg* ss = new SortSeg[S]();
-    for (int s = 0; s < S; ++s) {
-      ss[s].n_host = h_segs[s].m;
-      ss[s].passes = 4;
-      ss[s].bit0 = 32;
-      ss[s].key_base = (uint64_t)h_segs[s].tile_base * kTile;
-      ss[s].tile_base = h_segs[s].tile_base;
-      ss[s].num_tiles = h_segs[s].num_tiles;
-      ss[s].out.hdr = eh;
-    }
-    cudaError_t e = cudaMemsetAsync(eh, 0, sizeof(Header), stream);
-    if (e == cudaSuccess) {
-      e = cudaMemcpyAsync(segs, h_segs, sizeof(NnSeg) * S, cudaMemcpyHostToDevice, stream);
-    }
-    if (e == cudaSuccess) {
-      e = cudaMemcpyAsync(sc.segs, ss, sizeof(SortSeg) * S, cudaMemcpyHostToDevice, stream);
-    }
-    delete[] ss;
-    if (e == cudaSuccess) e = cudaMemsetAsync(sc.hist, 0, sc.zero_bytes, stream);
-    if (e != cudaSuccess) return e;
-    k_nn_keys<<<total_tiles * (kTile / 256), 256, 0, stream>>>(
-        segs, S, static_cast<unsigned long long*>(sc.keys0), sc.hist);
-    count_launch(1);
-    e = run_radix_passes(S, total_tiles, 4, true, sc, stream);
-    if (e != cudaSuccess) return e;
-    order = static_cast<const unsigned long long*>(sc.keys0);  // 4 passes end in keys0
-    order_err = &eh->err;
-    d_segs = segs;
-  } else if (S != 1) {
-    return cudaErrorInvalidValue;
+  if (scratch == nullptr) {
+    if (S != 1) return cudaErrorInvalidValue;
+    launch_search(nullptr, 1, h_segs[0], total_tiles, nullptr, nullptr, stream);
+    return cudaGetLastError();
   }
-  const uint32_t warps_needed = total_slots;
-  const uint32_t blocks = std::min<uint32_t>((warps_needed + 7) / 8, (uint32_t)device_sm_count() * 8);
-  k_nn_warp<<<blocks, 256, 0, stream>>>(d_segs, S, h_segs[0], total_slots, order, order_err);
-  count_launch(1);
-  return cudaGetLastError();
+  const NnTables t = nn_tables(scratch, total_tiles, S);
+  const cudaError_t e = nn_upload(h_segs, S, t, stream);
+  if (e != cudaSuccess) return e;
+  return run_nn_device(S, total_tiles, t, stream);
 }
 
 }  // namespace libcga

@@ -250,13 +250,9 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
 }
 
 // ------------------------------------------------------------- projection xy
-// The xy projection of a CGA is its top two levels (X_index, X_pointer,
-// Y_index): copy them.
-__global__ void k_project_xy(Levels a, Levels o) {
-  const uint32_t u = (uint32_t)a.hdr->cnt[0], g = (uint32_t)a.hdr->cnt[1],
-                 h = (uint32_t)a.hdr->cnt[2];
-  const uint32_t stride = gridDim.x * blockDim.x;
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void project_xy_body(const Levels& a, const Levels& o, uint32_t t,
+                                                uint32_t stride) {
+  const uint32_t g = (uint32_t)a.hdr->cnt[1], h = (uint32_t)a.hdr->cnt[2];
   for (uint32_t i = t; i < g; i += stride) o.idx0[i] = a.idx1[i];
   for (uint32_t i = t; i < h; i += stride) o.idx1[i] = a.idx2[i];
   for (uint32_t i = t; i <= h; i += stride) o.ptr1[i] = a.ptr2[i];
@@ -266,7 +262,18 @@ __global__ void k_project_xy(Levels a, Levels o) {
     o.hdr->cnt[2] = 0;
     o.hdr->err = a.hdr->err;
   }
-  (void)u;
+}
+
+// One projection per blockIdx.y.
+__global__ void k_project_xy_batch(const ProjPair* __restrict__ pairs) {
+  const ProjPair& P = pairs[blockIdx.y];
+  project_xy_body(P.a, P.out, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// The xy projection of a CGA is its top two levels (X_index, X_pointer,
+// Y_index): copy them.
+__global__ void k_project_xy(Levels a, Levels o) {
+  project_xy_body(a, o, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 }  // namespace
@@ -309,12 +316,9 @@ MergeScratch merge_scratch_carve(void* base, uint32_t total_spl, uint32_t total_
   return sc;
 }
 
-cudaError_t run_merge(const MergePair* h_pairs, int S, uint32_t total_spl, uint32_t total_tiles,
-                      const MergeScratch& sc, cudaStream_t stream) {
-  cudaError_t e = cudaMemcpyAsync(sc.pairs, h_pairs, sizeof(MergePair) * S,
-                                  cudaMemcpyHostToDevice, stream);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(sc.clook, 0, sc.zero_bytes, stream);
+cudaError_t run_merge_device(int S, uint32_t total_spl, uint32_t total_tiles,
+                             const MergeScratch& sc, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(sc.clook, 0, sc.zero_bytes, stream);
   if (e != cudaSuccess) return e;
   k_merge_init<<<(S + 127) / 128, 128, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles);
   count_launch(total_spl > 0 ? 4 : 2);
@@ -328,11 +332,28 @@ cudaError_t run_merge(const MergePair* h_pairs, int S, uint32_t total_spl, uint3
   return cudaGetLastError();
 }
 
+cudaError_t run_merge(const MergePair* h_pairs, int S, uint32_t total_spl, uint32_t total_tiles,
+                      const MergeScratch& sc, cudaStream_t stream) {
+  cudaError_t e = cudaMemcpyAsync(sc.pairs, h_pairs, sizeof(MergePair) * S,
+                                  cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return e;
+  return run_merge_device(S, total_spl, total_tiles, sc, stream);
+}
+
 cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stream) {
   const uint64_t work = std::max<uint64_t>(a.cap1, 1);
   const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
                                                        (uint64_t)device_sm_count() * 8);
   k_project_xy<<<blocks, 256, 0, stream>>>(a, out);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t run_project_xy_device(const ProjPair* d_pairs, int S, uint64_t max_cap1,
+                                  cudaStream_t stream) {
+  if (S == 0) return cudaSuccess;
+  const unsigned bx = (unsigned)std::min<uint64_t>((std::max<uint64_t>(max_cap1, 1) + 255) / 256, 64);
+  k_project_xy_batch<<<dim3(bx, (unsigned)S), 256, 0, stream>>>(d_pairs);
   count_launch(1);
   return cudaGetLastError();
 }

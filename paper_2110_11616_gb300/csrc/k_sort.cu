@@ -389,21 +389,26 @@ static cudaError_t launch_pipeline(int S, uint32_t total_tiles, uint32_t max_pas
   return cudaGetLastError();
 }
 
+cudaError_t run_sort_device(int S, uint32_t total_tiles, uint32_t max_passes, bool key64,
+                            int levels, const SortScratch& sc, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(sc.hist, 0, sc.zero_bytes, stream);
+  if (e != cudaSuccess) return e;
+  k_seg_init<<<(S + 127) / 128, 128, 0, stream>>>(sc.segs, S);
+  count_launch(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || total_tiles == 0) return e;
+  return key64 ? launch_pipeline<unsigned long long>(S, total_tiles, max_passes, levels, sc, stream)
+               : launch_pipeline<uint32_t>(S, total_tiles, max_passes, levels, sc, stream);
+}
+
 cudaError_t run_sort_pipeline(const SortSeg* h_segs, int S, uint32_t total_tiles,
                               uint32_t max_passes, bool key64, const SortScratch& sc,
                               cudaStream_t stream) {
   cudaError_t e = cudaMemcpyAsync(sc.segs, h_segs, sizeof(SortSeg) * S, cudaMemcpyHostToDevice,
                                   stream);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(sc.hist, 0, sc.zero_bytes, stream);
-  if (e != cudaSuccess) return e;
-  k_seg_init<<<(S + 127) / 128, 128, 0, stream>>>(sc.segs, S);
-  count_launch(1);
-  e = cudaGetLastError();
-  if (e != cudaSuccess || total_tiles == 0) return e;
-  const int levels = (int)h_segs[0].out.nlevels;
-  return key64 ? launch_pipeline<unsigned long long>(S, total_tiles, max_passes, levels, sc, stream)
-               : launch_pipeline<uint32_t>(S, total_tiles, max_passes, levels, sc, stream);
+  return run_sort_device(S, total_tiles, max_passes, key64, (int)h_segs[0].out.nlevels, sc,
+                         stream);
 }
 
 }  // namespace libcga
