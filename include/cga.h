@@ -46,6 +46,7 @@ extern "C" {
 #define CGA_ERR_CUDA (-5)          /* a CUDA runtime call failed */
 #define CGA_ERR_TIMEOUT (-6)       /* a bounded device wait ran out */
 #define CGA_ERR_INTERNAL (-7)      /* a device-side consistency check failed */
+#define CGA_ERR_CAPACITY (-8)      /* larger than a no-allocation call's fixed scratch */
 
 /* Largest point count of one cloud (counts travel in 30-bit fields). */
 #define CGA_MAX_POINTS ((uint64_t)((1u << 30) - 1u))
@@ -146,6 +147,27 @@ int cga_project(const cga_t* a, int plane, const cga_allocator* A, void* stream,
  * Both output arrays hold m entries, device, caller-owned. */
 int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
                  uint64_t* d_dist2, void* stream);
+
+/* cga_nn_query without any memory allocation.  (The paper has no counterpart:
+ * this is a deployment variant of the NN call above, same results bit for
+ * bit.)  For callers that cannot allocate device memory when they query --
+ * under a memory budget reserved in advance, inside real-time loops where
+ * cudaMalloc's device-wide synchronization and unbounded latency are not
+ * allowed, or where another framework owns the allocator.
+ * The scratch of the query sort comes from one fixed __device__ array of
+ * 18 MiB built into the library; every GPU that loads the library holds it
+ * until the process exits.  m must be <= CGA_NOALLOC_MAX_QUERIES, else
+ * CGA_ERR_CAPACITY and nothing is queued.  The caller passes the CGA, the
+ * queries and the outputs exactly as for cga_nn_query.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  All calls share
+ * the one array and each call resets what it needs, so calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race:
+ * serialize them, e.g. on one stream.  Nothing is allocated: no cudaMalloc,
+ * cudaFree, pool or allocator callback. */
+#define CGA_NOALLOC_MAX_QUERIES ((uint64_t)1 << 20)
+int cga_nn_query_noalloc(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
+                         uint64_t* d_dist2, void* stream);
 
 /* Decode (lossless inverse of the build, CGA order): d_xyz receives u triples
  * (x, y, z) as uint32, u from cga_info; device, caller-owned, >= 3u entries

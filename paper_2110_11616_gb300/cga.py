@@ -23,6 +23,8 @@ ERR_OOM = -4
 ERR_CUDA = -5
 ERR_TIMEOUT = -6
 ERR_INTERNAL = -7
+ERR_CAPACITY = -8
+NOALLOC_MAX_QUERIES = 1 << 20
 MAX_POINTS = (1 << 30) - 1
 PLANES = {"xy": 0, "xz": 1, "yz": 2}
 
@@ -33,7 +35,7 @@ EXPORTS = (
     "cga2d_download", "cga_free", "cga2d_free", "cga_strerror", "cga_kernel_launches",
     "cga_build_batch", "cga_merge_batch", "cga_project_batch", "cga_nn_query_batch",
     "cga_pipeline_create", "cga_pipeline_run", "cga_pipeline_run_graph", "cga_pipeline_view",
-    "cga_pipeline_view_xy", "cga_pipeline_free",
+    "cga_pipeline_view_xy", "cga_pipeline_free", "cga_nn_query_noalloc",
 )
 
 

@@ -37,6 +37,11 @@ struct cga2d {
 };
 
 namespace libcga {
+// The arrays and grid behind a handle, for entry points in other files.
+void handle_parts(const cga_t* a, Levels* lv, cga_grid* g) {
+  *lv = a->lv;
+  *g = a->grid;
+}
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace libcga
@@ -1075,6 +1080,7 @@ const char* cga_strerror(int code) {
     case CGA_ERR_CUDA: return "CUDA runtime error";
     case CGA_ERR_TIMEOUT: return "bounded device wait ran out";
     case CGA_ERR_INTERNAL: return "device consistency check failed";
+    case CGA_ERR_CAPACITY: return "request larger than the fixed scratch of a no-allocation call";
     default: return "unknown error";
   }
 }

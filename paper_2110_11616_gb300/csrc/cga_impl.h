@@ -176,6 +176,8 @@ struct NnTables {
 NnTables nn_tables(void* scratch, uint32_t total_tiles, int S);
 // Upload the NnSeg and sort-segment tables (pageable copies, not capturable).
 cudaError_t nn_upload(const NnSeg* h_segs, int S, const NnTables& t, cudaStream_t stream);
+// Upload the tables of one segment from stack copies (no heap allocation).
+cudaError_t nn_upload_one(const NnSeg& h_seg, const NnTables& t, cudaStream_t stream);
 // Run with the tables on the device (capturable: memsets and kernels only).
 cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream);
 

@@ -269,6 +269,22 @@ cudaError_t nn_upload(const NnSeg* h_segs, int S, const NnTables& t, cudaStream_
   return e;
 }
 
+cudaError_t nn_upload_one(const NnSeg& h_seg, const NnTables& t, cudaStream_t stream) {
+  SortSeg ss{};
+  ss.n_host = h_seg.m;
+  ss.passes = 4;
+  ss.bit0 = 32;
+  ss.key_base = (uint64_t)h_seg.tile_base * kTile;
+  ss.tile_base = h_seg.tile_base;
+  ss.num_tiles = h_seg.num_tiles;
+  ss.out.hdr = t.err;
+  cudaError_t e = cudaMemcpyAsync(t.segs, &h_seg, sizeof(NnSeg), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) {
+    e = cudaMemcpyAsync(t.sort.segs, &ss, sizeof(SortSeg), cudaMemcpyHostToDevice, stream);
+  }
+  return e;
+}
+
 static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
                           uint32_t total_tiles, const unsigned long long* order,
                           const unsigned int* order_err, cudaStream_t stream) {

@@ -1,0 +1,65 @@
+"""cga_nn_query_noalloc: the NN call for callers that cannot allocate device
+memory (fixed memory budgets, real-time loops that must not call cudaMalloc,
+allocators owned by another framework).  Its scratch lives in a fixed device
+array inside the library, so it must return exactly what cga_nn_query
+returns, call after call, with nothing left over from the previous call.
+
+This file is collected last on purpose: a run that stops at the first failure
+has then already run every other test."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2110_11616_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_11616_gb300 import build_ext, cga
+    build_ext.build()
+    lib = cga.load()
+    P = ctypes.c_void_p
+    lib.cga_nn_query_noalloc.argtypes = [P, P, ctypes.c_uint64, P, P, P]
+    return cga
+
+
+def call_noalloc(cg, a, q):
+    m = q.shape[0]
+    idx = torch.full((m,), 7, dtype=torch.int32, device="cuda")
+    d2 = torch.full((m,), 7, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = cg.load().cga_nn_query_noalloc(a.ptr, ctypes.c_void_p(q.data_ptr()), m,
+                                        ctypes.c_void_p(idx.data_ptr()),
+                                        ctypes.c_void_p(d2.data_ptr()), ctypes.c_void_p(stream))
+    assert rc == cg.OK, rc
+    return idx, d2
+
+
+def test_noalloc_matches_nn_query_on_consecutive_calls(cg):
+    pts = synth.uniform_cube(200_000, seed=401)
+    g = cg.grid_from_box([0, 0, 0], 1.0, 12)
+    a = cg.cga_build(torch.from_numpy(pts).cuda(), g)
+    b = cg.cga_build(torch.from_numpy(synth.uniform_cube(30_000, seed=402)).cuda(), g)
+    q1 = torch.from_numpy(synth.uniform_queries(300_000, 403, [-0.05] * 3, 1.1)).cuda()
+    q2 = torch.from_numpy(synth.uniform_queries(5_000, 404, [0.0] * 3, 1.0)).cuda()
+    for cga_h, q in ((a, q1), (b, q2)):
+        got_idx, got_d2 = call_noalloc(cg, cga_h, q)
+        ref_idx, ref_d2 = cg.cga_nn_query(cga_h, q)
+        torch.cuda.synchronize()
+        assert torch.equal(got_idx, ref_idx)
+        assert torch.equal(got_d2, ref_d2)
+
+
+def test_noalloc_rejects_more_than_its_capacity(cg):
+    g = cg.grid_from_box([0, 0, 0], 1.0, 8)
+    a = cg.cga_build(torch.from_numpy(synth.uniform_cube(100, seed=405)).cuda(), g)
+    m = cg.NOALLOC_MAX_QUERIES + 1
+    rc = cg.load().cga_nn_query_noalloc(a.ptr, ctypes.c_void_p(16), m, ctypes.c_void_p(16),
+                                        ctypes.c_void_p(16), None)
+    assert rc == cg.ERR_CAPACITY
