@@ -246,6 +246,63 @@ int cga_pipeline_view(const cga_pipeline_t* p, uint32_t i, int which, const cga_
 int cga_pipeline_view_xy(const cga_pipeline_t* p, uint32_t i, const cga2d_t** out);
 void cga_pipeline_free(cga_pipeline_t* p);
 
+/* ---- Served loop: continuous batching over device-resident CGAs ----------
+ * A scheduler thread keeps `slots` CUDA streams busy.  Whenever a stream is
+ * idle and requests are pending, it batches requests from the head of the
+ * queue (arrival order) while their device-memory footprint fits what is left
+ * of `memory_budget`, up to `max_batch` per batch.  All NN requests of a batch
+ * share one segmented NN launch set; all merge+project requests one batched
+ * merge (Eq. 1) and one batched projection (Eq. 3).  Requests that arrive while
+ * batches run are admitted onto free streams as memory frees up, so their work
+ * overlaps on the GPU.  Results equal the plain single calls bit for bit. */
+typedef struct cga_server cga_server_t;
+
+#define CGA_REQ_NN 0             /* m NN queries against pool[a] */
+#define CGA_REQ_MERGE_PROJECT 1  /* merge pool[a] with pool[b], project onto plane */
+
+typedef struct {
+  int32_t kind;
+  uint32_t a, b;       /* pool indices (b: merge+project only) */
+  int32_t plane;       /* merge+project: CGA_PLANE_* */
+  const float* d_q;    /* NN: m queries, device; must stay valid until done */
+  uint64_t m;
+  uint32_t* d_idx;     /* NN outputs, device, m entries */
+  uint64_t* d_dist2;
+} cga_request;
+
+typedef struct {
+  uint64_t ticket;       /* from cga_server_submit */
+  int32_t status;        /* CGA_OK or an error code */
+  uint64_t t_submit_ns;  /* cga_now_ns() clock: arrival */
+  uint64_t t_start_ns;   /* batch queued on a stream */
+  uint64_t t_done_ns;    /* completion seen by the scheduler */
+  cga_t* merged;         /* merge+project results: the caller frees them */
+  cga2d_t* projected;
+} cga_completion;
+
+typedef struct {
+  uint64_t memory_budget;  /* bytes of scratch + outputs in flight at once */
+  uint32_t slots;          /* concurrent batches (CUDA streams), 1..64 */
+  uint32_t max_batch;      /* requests per batch */
+} cga_server_config;
+
+/* pool: CGAs that stay resident and unchanged while the server lives (the
+ * call waits until they are built).  Scratch and results come from A. */
+int cga_server_create(const cga_t* const* pool, uint32_t count, const cga_server_config* cfg,
+                      const cga_allocator* A, cga_server_t** out);
+/* Thread-safe, non-blocking.  A request larger than the whole budget is
+ * refused with CGA_ERR_OOM; merge of pool CGAs on different grids with
+ * CGA_ERR_GRID_MISMATCH. */
+int cga_server_submit(cga_server_t* s, const cga_request* r, uint64_t* ticket);
+/* Up to `max` finished requests (oldest first); non-blocking. */
+int cga_server_poll(cga_server_t* s, cga_completion* out, uint32_t max, uint32_t* n);
+/* Wait until every submitted request has finished. */
+int cga_server_drain(cga_server_t* s);
+/* Finish outstanding work, free unpolled results, stop the scheduler. */
+void cga_server_free(cga_server_t* s);
+/* The server's clock (steady, nanoseconds). */
+uint64_t cga_now_ns(void);
+
 /* Sizes of a handle; waits for the work that produced it.  Returns the
  * device-side error recorded for the handle, if any. */
 int cga_info(const cga_t* a, cga_sizes* out);

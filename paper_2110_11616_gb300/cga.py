@@ -36,6 +36,8 @@ EXPORTS = (
     "cga_build_batch", "cga_merge_batch", "cga_project_batch", "cga_nn_query_batch",
     "cga_pipeline_create", "cga_pipeline_run", "cga_pipeline_run_graph", "cga_pipeline_view",
     "cga_pipeline_view_xy", "cga_pipeline_free", "cga_nn_query_noalloc",
+    "cga_server_create", "cga_server_submit", "cga_server_poll", "cga_server_drain",
+    "cga_server_free", "cga_now_ns",
 )
 
 
@@ -502,6 +504,103 @@ class Pipeline:
     def free(self):
         if self.ptr:
             load().cga_pipeline_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- served loop
+REQ_NN = 0
+REQ_MERGE_PROJECT = 1
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("a", ctypes.c_uint32), ("b", ctypes.c_uint32),
+                ("plane", ctypes.c_int32), ("d_q", ctypes.c_void_p), ("m", ctypes.c_uint64),
+                ("d_idx", ctypes.c_void_p), ("d_dist2", ctypes.c_void_p)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("t_submit_ns", ctypes.c_uint64), ("t_start_ns", ctypes.c_uint64),
+                ("t_done_ns", ctypes.c_uint64), ("merged", ctypes.c_void_p),
+                ("projected", ctypes.c_void_p)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_uint64), ("slots", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32)]
+
+
+def now_ns() -> int:
+    lib = load()
+    lib.cga_now_ns.restype = ctypes.c_uint64
+    return int(lib.cga_now_ns())
+
+
+class Server:
+    """Continuous-batching request loop over a pool of resident CGAs."""
+
+    def __init__(self, pool, memory_budget: int, slots: int = 4, max_batch: int = 64,
+                 allocator=None):
+        lib = load()
+        P = ctypes.c_void_p
+        lib.cga_server_create.argtypes = [P, ctypes.c_uint32, P, P, ctypes.POINTER(P)]
+        lib.cga_server_submit.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
+        lib.cga_server_poll.argtypes = [P, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
+        lib.cga_server_drain.argtypes = [P]
+        lib.cga_server_free.argtypes = [P]
+        lib.cga_server_free.restype = None
+        self.pool = list(pool)
+        cfg = ServerConfig(memory_budget, slots, max_batch)
+        self.ptr = ctypes.c_void_p()
+        _check(lib.cga_server_create(_ptr_array(self.pool), len(self.pool), ctypes.byref(cfg),
+                                     _alloc_arg(allocator), ctypes.byref(self.ptr)),
+               "cga_server_create")
+        self._keep = {}
+
+    def submit_nn(self, a: int, queries, idx, dist2, keep=None) -> int:
+        r = Request(REQ_NN, a, 0, 0, queries.data_ptr(), queries.numel() // 3, idx.data_ptr(),
+                    dist2.data_ptr())
+        t = ctypes.c_uint64()
+        _check(load().cga_server_submit(self.ptr, ctypes.byref(r), ctypes.byref(t)),
+               "cga_server_submit")
+        self._keep[t.value] = (queries, idx, dist2, keep)
+        return t.value
+
+    def submit_merge_project(self, a: int, b: int, plane="xy") -> int:
+        p = PLANES[plane] if isinstance(plane, str) else int(plane)
+        r = Request(REQ_MERGE_PROJECT, a, b, p, None, 0, None, None)
+        t = ctypes.c_uint64()
+        _check(load().cga_server_submit(self.ptr, ctypes.byref(r), ctypes.byref(t)),
+               "cga_server_submit")
+        return t.value
+
+    def poll(self, max_n: int = 4096):
+        arr = (Completion * max_n)()
+        n = ctypes.c_uint32()
+        _check(load().cga_server_poll(self.ptr, arr, max_n, ctypes.byref(n)), "cga_server_poll")
+        out = []
+        for i in range(n.value):
+            c = arr[i]
+            d = {"ticket": c.ticket, "status": c.status, "t_submit_ns": c.t_submit_ns,
+                 "t_start_ns": c.t_start_ns, "t_done_ns": c.t_done_ns,
+                 "merged": Cga(ctypes.c_void_p(c.merged), self.pool[0].grid) if c.merged else None,
+                 "projected": Cga2d(ctypes.c_void_p(c.projected), 0, 0) if c.projected else None}
+            self._keep.pop(c.ticket, None)
+            out.append(d)
+        return out
+
+    def drain(self):
+        _check(load().cga_server_drain(self.ptr), "cga_server_drain")
+
+    def free(self):
+        if self.ptr:
+            load().cga_server_free(self.ptr)
             self.ptr = None
 
     def __del__(self):

@@ -42,6 +42,10 @@ void handle_parts(const cga_t* a, Levels* lv, cga_grid* g) {
   *lv = a->lv;
   *g = a->grid;
 }
+void rebind_stream(cga_t* a, cga2d_t* p, cudaStream_t s) {
+  if (a != nullptr) a->stream = s;
+  if (p != nullptr) p->stream = s;
+}
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace libcga
