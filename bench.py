@@ -1,25 +1,33 @@
 #!/usr/bin/env python3
 """Benchmark of the CGA hot path (libcga) on GB300.
 
-Default workload (one "step" = one pass of the whole hot path): the LiDAR-shaped
-frame set -- 10 sweeps of 64 beams x 2048 azimuth steps (1,310,720 float32
-points) on a 16-bit-per-axis grid over [-128, 128)^3 m.  Per step:
-  build    the 10 sweep CGAs, each with its ego pose fused into quantization
-  merge    a merge tree over the sweeps (sweep t with t+1, then upwards; 9
-           merges) into the world CGA
+Default workload (--config lidar; one "step" = one pass of the whole hot path):
+the LiDAR-shaped frame set -- 10 sweeps of 64 beams x 2048 azimuth steps
+(1,310,720 float32 points) on a 16-bit-per-axis grid over [-128, 128)^3 m:
+  build    the 10 sweep CGAs in one batched call, each sweep's ego pose fused
+           into its quantization
+  merge    a merge tree over the sweeps (t with t+1, then upwards; 9 merges,
+           one batched call per level) into the world CGA
   project  the world CGA onto the xy plane
-  nn       1,000,000 exact NN queries (world points + N(0, 0.2 m) jitter)
+  nn       1,000,000 exact NN queries (world points + N(0, 0.2 m) jitter):
+           the Morton query sort, then the search
   decode   the world CGA back to voxel triples
 Inputs are resident in HBM before the timed region; L2 (129 MB) is flushed
 between timed steps by writing a 512 MB buffer.
 
-python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Other workloads: --config plain (100k uniform + twin), surface (30M points on
+superellipsoids), batched (512 uneven clouds through the pre-planned pipeline
+replayed from a CUDA graph, against 512 sequential plain calls), served
+(Poisson requests over 64 resident CGAs).
+
+python bench.py [--gpus N --steps K --warmup W] [--config C] [--impl reference]
 prints ONE JSON line.  --impl reference times the CPU oracle on the host cores.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -48,9 +56,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["cga", "reference"], default="cga")
+    ap.add_argument("--config", choices=["lidar", "plain", "surface", "batched", "served"],
+                    default="lidar")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
 
 
 # ----------------------------------------------------------------- workload
@@ -113,8 +133,34 @@ class Clocks:
                 "samples": len(rows)}
 
 
-# --------------------------------------------------------------- GPU arm
-class GpuPipeline:
+def start_clocks(local_rank):
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]
+    return Clocks(int(phys) if phys.strip().isdigit() else local_rank)
+
+
+def timed(torch, fn, flush=None, tag=0.0):
+    """Device time (ms) of fn() with CUDA events on the current stream."""
+    if flush is not None:
+        flush.fill_(tag)
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    fn()
+    e.record()
+    e.synchronize()
+    return s.elapsed_time(e)
+
+
+def base_line(args, world_size, metric, value, unit, ms_per_step, config, data):
+    return {"metric": metric, "value": round(value, 4), "unit": unit, "n_gpus": world_size,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32->u16/u32/u64",
+            "data": data, "config": config}
+
+
+# --------------------------------------------------------------- GPU arm: C2
+class LidarStep:
     def __init__(self, scene, queries, torch, cga):
         self.torch, self.cga = torch, cga
         self.grid = cga.grid_from_box(LO, EXTENT, BITS)
@@ -124,26 +170,25 @@ class GpuPipeline:
         self.d_q = self.h_q.cuda()
         self.poses = scene.poses
         m = len(queries)
+        self.order = torch.empty(m, dtype=torch.int64, device="cuda")
         self.idx = torch.empty(m, dtype=torch.int32, device="cuda")
         self.d2 = torch.empty(m, dtype=torch.int64, device="cuda")
         self.h_idx = torch.empty(m, dtype=torch.int32).pin_memory()
         self.h_d2 = torch.empty(m, dtype=torch.int64).pin_memory()
         self.n_points = sum(len(s) for s in scene.sweeps)
         self.dec = torch.empty((self.n_points, 3), dtype=torch.int32, device="cuda")
-        self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
 
     def step(self, timed_events=True, batched=True):
-        cga = self.cga
-        ev = self.ev
-        if timed_events:
-            ev[0].record()
+        cga, ev = self.cga, self.ev
+        rec = (lambda i: ev[i].record()) if timed_events else (lambda i: None)
+        rec(0)
         if batched:
             sweeps = cga.cga_build_batch(self.d_sweeps, self.grid, self.poses, allocator=None)
         else:
             sweeps = [cga.cga_build(d, self.grid, xform=p, allocator=None)
                       for d, p in zip(self.d_sweeps, self.poses)]
-        if timed_events:
-            ev[1].record()
+        rec(1)
         merges = []
         level = list(sweeps)
         while len(level) > 1:
@@ -157,22 +202,20 @@ class GpuPipeline:
                 nxt.append(level[-1])
             level = nxt
         world = level[0]
-        if timed_events:
-            ev[2].record()
+        rec(2)
         proj = cga.cga_project(world, "xy", allocator=None)
-        if timed_events:
-            ev[3].record()
-        cga.cga_nn_query(world, self.d_q, self.idx, self.d2)
-        if timed_events:
-            ev[4].record()
+        rec(3)
+        cga.cga_nn_sort_queries(world, self.d_q, self.order)
+        rec(4)
+        cga.cga_nn_query_ordered(world, self.d_q, self.order, self.idx, self.d2)
+        rec(5)
         cga.cga_decode(world, out=self.dec)
-        if timed_events:
-            ev[5].record()
+        rec(6)
         self.last = (sweeps, merges, world, proj)
 
     def op_times(self):
         e = self.ev
-        return [e[i].elapsed_time(e[i + 1]) for i in range(5)]
+        return [e[i].elapsed_time(e[i + 1]) for i in range(6)]
 
     def e2e_step(self):
         for h, d in zip(self.h_sweeps, self.d_sweeps):
@@ -189,20 +232,9 @@ class GpuPipeline:
         return self.h_idx.numel() * 4 + self.h_d2.numel() * 8
 
 
-def cga_bytes(info):
-    return info["bytes"]
-
-
-def run_gpu(args, rank, world_size, local_rank):
-    import torch
-    import torch.distributed as dist
-    from paper_2110_11616_gb300 import build_ext, cga
-
-    build_ext.build()
-    cga.load()
-    torch.cuda.set_device(local_rank)
+def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
     scene, queries = make_workload(rank)
-    P = GpuPipeline(scene, queries, torch, cga)
+    P = LidarStep(scene, queries, torch, cga)
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -213,60 +245,32 @@ def run_gpu(args, rank, world_size, local_rank):
     for _ in range(args.warmup):
         P.step()
     torch.cuda.synchronize()
-    phys = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]
-    clocks = Clocks(int(phys) if phys.isdigit() else local_rank)
+    clocks = start_clocks(local_rank)
     time.sleep(0.3)
-    start_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    end_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    op_ms = np.zeros(5)
+    op_ms = np.zeros(6)
+    step_ms = []
     launches0 = cga.kernel_launches()
     barrier()
     t_wall = time.perf_counter()
     for k in range(args.steps):
-        flush.fill_(float(k))
-        start_ev[k].record()
-        P.step()
-        end_ev[k].record()
-        end_ev[k].synchronize()
+        step_ms.append(timed(torch, P.step, flush, float(k)))
         op_ms += np.array(P.op_times())
     barrier()
     t_wall = time.perf_counter() - t_wall
     launches = cga.kernel_launches() - launches0
-    step_ms = [s.elapsed_time(e) for s, e in zip(start_ev, end_ev)]
     total_ms = float(sum(step_ms))
-
-    # the same step as one call per cloud / per merge (the plain form)
-    plain_ms = []
-    for k in range(max(3, args.steps // 2)):
-        flush.fill_(float(k))
-        s = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        s.record()
-        P.step(timed_events=False, batched=False)
-        e.record()
-        e.synchronize()
-        plain_ms.append(s.elapsed_time(e))
-
-    # end to end: host (pinned) inputs -> device -> results back to host
+    plain_ms = [timed(torch, lambda: P.step(timed_events=False, batched=False), flush, float(k))
+                for k in range(max(3, args.steps // 2))]
     e2e_ms = []
     for k in range(max(3, args.steps // 3)):
-        flush.fill_(float(k))
         torch.cuda.synchronize()
-        s = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        s.record()
-        P.e2e_step()
-        e.record()
-        e.synchronize()
-        e2e_ms.append(s.elapsed_time(e))
+        e2e_ms.append(timed(torch, P.e2e_step, flush, float(k)))
     clk = clocks.stop()
 
-    # sizes of the last step for the derived numbers
     sweeps, merges, world, proj = P.last
     winfo = world.info()
-    merge_bytes = 0
-    for a, b, m in merges:
-        merge_bytes += cga_bytes(a.info()) + cga_bytes(b.info()) + cga_bytes(m.info())
+    merge_bytes = sum(a.info()["bytes"] + b.info()["bytes"] + m.info()["bytes"]
+                      for a, b, m in merges)
     op = op_ms / args.steps
     max_total = total_ms
     if world_size > 1:
@@ -276,33 +280,38 @@ def run_gpu(args, rank, world_size, local_rank):
     pts = P.n_points
     value = pts * args.steps * world_size / (max_total / 1e3) / 1e6
     e2e_val = pts * world_size / (float(np.mean(e2e_ms)) / 1e3) / 1e6
-    out = {
-        "metric": METRIC,
-        "value": round(value, 3),
-        "unit": "Mpts/s",
-        "n_gpus": world_size,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": round(max_total / args.steps, 4),
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f32->u16/u32/u64",
-        "data": "synthetic (seeded LiDAR generator; stands in for the paper's LiDAR scans)",
-        "config": {"workload": WORKLOAD, "points_per_step": pts, "queries_per_step": N_QUERIES,
-                   "grid_bits": BITS, "l2": f"flushed between steps ({args.flush_mb} MB write)",
-                   "parallelism": f"replicas x{world_size}" if world_size > 1 else "1 GPU"},
+    peak, peak_kind = measured_peaks()
+    # dominant kernel: the NN search (one launch of k_nn_warp per step, timed
+    # live above between events 4 and 5).  Algorithmic bytes per launch: per
+    # query 12 B point + 8 B order key read, 4 B index + 8 B distance written,
+    # plus one read of the world CGA.
+    search_ms = op[4]
+    algo = N_QUERIES * (12 + 8 + 4 + 8) + winfo["bytes"]
+    achieved = algo / (search_ms / 1e3) / 1e9
+    out = base_line(args, world_size, METRIC, value, "Mpts/s", max_total / args.steps,
+                    {"workload": WORKLOAD, "points_per_step": pts, "queries_per_step": N_QUERIES,
+                     "grid_bits": BITS, "l2": f"flushed between steps ({args.flush_mb} MB write)",
+                     "parallelism": f"replicas x{world_size}" if world_size > 1 else "1 GPU"},
+                    "synthetic (seeded LiDAR generator; stands in for the paper's LiDAR scans)")
+    out.update({
         "breakdown_ms": {"build": round(op[0], 4), "merge": round(op[1], 4),
-                         "project_xy": round(op[2], 4), "nn": round(op[3], 4),
-                         "decode": round(op[4], 4)},
+                         "project_xy": round(op[2], 4), "nn_sort": round(op[3], 4),
+                         "nn_search": round(op[4], 4), "decode": round(op[5], 4)},
         "derived": {
             "build_Mpts_s": round(pts / (op[0] / 1e3) / 1e6, 2),
-            "nn_queries_s": round(N_QUERIES / (op[3] / 1e3), 1),
+            "nn_queries_s": round(N_QUERIES / ((op[3] + op[4]) / 1e3), 1),
             "merge_GB_s": round(merge_bytes / (op[1] / 1e3) / 1e9, 2),
+            "merge_frac_of_hbm": round(merge_bytes / (op[1] / 1e3) / 1e9 / peak, 5),
             "merge_compulsory_bytes": merge_bytes,
             "world_u": winfo["u"], "world_g": winfo["g"], "world_h": winfo["h"],
             "world_bytes": winfo["bytes"], "raw_bytes": pts * 12,
         },
+        "roofline": {"kernel": "k_nn_warp (NN search)", "bound": "hbm",
+                     "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 5), "traffic": 30_666_688,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "note": "latency-bound search: ncu shows L1 throughput 62.5% of peak, "
+                             "DRAM 0.09%; traffic = ncu dram read+write of one launch"},
         "e2e": {"value": round(e2e_val, 3), "unit": "Mpts/s",
                 "h2d_bytes_per_step": P.bytes_in(), "d2h_bytes_per_step": P.bytes_out()},
         "plain": {"ms_per_step": round(float(np.mean(plain_ms)), 4),
@@ -312,8 +321,263 @@ def run_gpu(args, rank, world_size, local_rank):
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s": round(t_wall, 3),
-    }
-    return out, P
+    })
+    return out, (scene, queries)
+
+
+# ------------------------------------------------------------ GPU arm: C1, C3
+def run_single(args, world_size, local_rank, torch, cga, which):
+    from paper_2110_11616_gb300 import synth_gpu
+    if which == "plain":
+        pts = torch.from_numpy(synth.uniform_cube(100_000, seed=1)).cuda()
+        X = synth.rigid_xform(seed=2)
+        halves = [pts, pts]
+        xforms = [None, X]
+        grid = cga.grid_from_box([0, 0, 0], 1.0, 10)
+        q = torch.from_numpy(synth.uniform_queries(10_000, 3, [0, 0, 0], 1.0)).cuda()
+        planes = ["xy"]
+        workload = ("plain: 100k uniform pts + rigidly transformed twin, b=10; batched build of "
+                    "both, merge, xy projection, 10k uniform NN, decode")
+        n_points = 200_000
+    else:
+        full = synth_gpu.surface_cloud(30_000_000, seed=3)
+        halves = [full[0::2].contiguous(), full[1::2].contiguous()]
+        del full
+        xforms = [None, None]
+        grid = cga.grid_from_box([0, 0, 0], 100.0, 12)
+        surf = synth_gpu.surface_cloud(4_000_000, seed=4)
+        uni = synth_gpu.uniform_queries(4_000_000, 5, [0.0, 0.0, 0.0], 100.0)
+        q = torch.cat([surf, uni]).contiguous()
+        planes = ["xy", "xz", "yz"]
+        workload = ("surface: 30M pts on 200 superellipsoids, b=12; batched build of the even/odd "
+                    "halves, merge, xy/xz/yz projections, 8M NN (4M on-surface + 4M uniform), "
+                    "decode")
+        n_points = 30_000_000
+    m = q.shape[0]
+    order = torch.empty(m, dtype=torch.int64, device="cuda")
+    idx = torch.empty(m, dtype=torch.int32, device="cuda")
+    d2 = torch.empty(m, dtype=torch.int64, device="cuda")
+    dec = torch.empty((n_points, 3), dtype=torch.int32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+    state = {}
+
+    def step():
+        ev[0].record()
+        a, b = cga.cga_build_batch(halves, grid, xforms, allocator=None)
+        ev[1].record()
+        mg = cga.cga_merge(a, b, allocator=None)
+        ev[2].record()
+        pr = cga.cga_project_batch([mg] * len(planes), planes, allocator=None)
+        ev[3].record()
+        cga.cga_nn_sort_queries(mg, q, order)
+        ev[4].record()
+        cga.cga_nn_query_ordered(mg, q, order, idx, d2)
+        ev[5].record()
+        cga.cga_decode(mg, out=dec)
+        ev[6].record()
+        state["last"] = (a, b, mg, pr)
+
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = start_clocks(local_rank)
+    ops = np.zeros(6)
+    ms = []
+    launches0 = cga.kernel_launches()
+    for k in range(args.steps):
+        ms.append(timed(torch, step, flush, float(k)))
+        ops += np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(6)])
+    launches = cga.kernel_launches() - launches0
+    clk = clocks.stop()
+    ops /= args.steps
+    a, b, mg, pr = state["last"]
+    mi = mg.info()
+    merge_bytes = a.info()["bytes"] + b.info()["bytes"] + mi["bytes"]
+    peak, peak_kind = measured_peaks()
+    total = float(sum(ms))
+    out = base_line(args, world_size, METRIC, n_points * args.steps / (total / 1e3) / 1e6,
+                    "Mpts/s", total / args.steps,
+                    {"workload": workload, "points_per_step": n_points, "queries_per_step": m,
+                     "l2": "flushed between steps"}, "synthetic (seeded generators)")
+    out.update({
+        "breakdown_ms": {"build": round(ops[0], 4), "merge": round(ops[1], 4),
+                         "project": round(ops[2], 4), "nn_sort": round(ops[3], 4),
+                         "nn_search": round(ops[4], 4), "decode": round(ops[5], 4)},
+        "derived": {"build_Mpts_s": round(n_points / (ops[0] / 1e3) / 1e6, 2),
+                    "nn_queries_s": round(m / ((ops[3] + ops[4]) / 1e3), 1),
+                    "merge_GB_s": round(merge_bytes / (ops[1] / 1e3) / 1e9, 2),
+                    "merge_frac_of_hbm": round(merge_bytes / (ops[1] / 1e3) / 1e9 / peak, 4),
+                    "build_by_design_GB_s": round(
+                        (n_points * (12 + 8 + 16 * math.ceil(3 * grid.bits / 8) + 8)
+                         + a.info()["bytes"] + b.info()["bytes"]) / (ops[0] / 1e3) / 1e9, 1),
+                    "merged_u": mi["u"], "merged_bytes": mi["bytes"], "raw_bytes": n_points * 12,
+                    "peak_gbs": peak, "peak_source": peak_kind},
+        "gpu_launches": int(launches), "clocks": clk})
+    return out
+
+
+# --------------------------------------------------------- GPU arm: C4 batched
+def run_batched(args, world_size, local_rank, torch, cga):
+    from paper_2110_11616_gb300 import synth_gpu
+    S = 512
+    sizes = synth.log_uniform_ints(S, 5_000, 2_000_000, seed=41)
+    rng = np.random.default_rng(42)
+    bits = rng.integers(10, 17, size=S)
+    pts, grids, xforms, qs = [], [], [], []
+    for i in range(S):
+        n = int(sizes[i])
+        if i % 2 == 0:
+            p = synth_gpu.lidar_cloud(n, seed=1000 + i)
+            grids.append(cga.grid_from_box([-128.0] * 3, 256.0, int(bits[i])))
+            qs.append(synth_gpu.jitter_queries(p, 4096, 0.2, seed=3000 + i))
+        else:
+            p = synth_gpu.surface_cloud(n, seed=1000 + i, n_objects=max(4, min(200, n // 5000)))
+            grids.append(cga.grid_from_box([0.0] * 3, 100.0, int(bits[i])))
+            qs.append(synth_gpu.jitter_queries(p, 4096, 0.1, seed=3000 + i))
+        pts.append(p)
+        xforms.append(synth.rigid_xform(seed=2000 + i))
+    total_pts = 2 * int(sizes.sum())
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        pipe = cga.Pipeline(pts, grids, xforms, qs, allocator=None)
+        idx_p = [t for t in pipe.idx]
+        for _ in range(args.warmup):
+            pipe.run_graph()
+        stream.synchronize()
+        clocks = start_clocks(local_rank)
+        launches0 = cga.kernel_launches()
+        ms = [timed(torch, pipe.run_graph) for _ in range(args.steps)]
+        launches = cga.kernel_launches() - launches0
+        ms_nograph = [timed(torch, pipe.run) for _ in range(max(2, args.steps // 3))]
+        d2_pipe = [t.clone() for t in pipe.dist2]
+
+        def plain():
+            res = []
+            for i in range(S):
+                a = cga.cga_build(pts[i], grids[i], allocator=None)
+                b = cga.cga_build(pts[i], grids[i], xform=xforms[i], allocator=None)
+                m = cga.cga_merge(a, b, allocator=None)
+                cga.cga_project(m, "xy", allocator=None)
+                res.append(cga.cga_nn_query(m, qs[i]))
+            return res
+        plain_ms = []
+        for _ in range(2):
+            t0 = time.perf_counter()
+            res = plain()
+            torch.cuda.synchronize()
+            plain_ms.append((time.perf_counter() - t0) * 1e3)
+        clk = clocks.stop()
+        same = all(torch.equal(d2_pipe[i], res[i][1]) for i in range(S))
+    del idx_p
+    total = float(sum(ms))
+    out = base_line(args, world_size, METRIC, total_pts * args.steps / (total / 1e3) / 1e6,
+                    "Mpts/s", total / args.steps,
+                    {"workload": "batched: 512 clouds, n log-uniform [5e3, 2e6] (LiDAR / "
+                                 "superellipsoid alternating), b uniform in 10..16; build + "
+                                 "transformed twin + merge + xy projection + 4096 NN each, one "
+                                 "pre-planned pipeline replayed from a CUDA graph",
+                     "clouds": S, "points_per_step": total_pts, "l2": "inputs > L2"},
+                    "synthetic (seeded GPU generators)")
+    out.update({"graph_ms": round(total / args.steps, 3),
+                "pipeline_no_graph_ms": round(float(np.mean(ms_nograph)), 3),
+                "plain_512_calls_ms": round(float(np.min(plain_ms)), 3),
+                "plain_timing": "host wall clock around 512 sequential calls + synchronize",
+                "speedup_vs_plain": round(float(np.min(plain_ms)) / (total / args.steps), 2),
+                "nn_results_equal_plain": bool(same),
+                "gpu_launches": int(launches), "clocks": clk})
+    return out
+
+
+# ---------------------------------------------------------- GPU arm: C5 served
+def run_served(args, world_size, local_rank, torch, cga):
+    from paper_2110_11616_gb300 import synth_gpu
+    K = 64
+    sizes = synth.log_uniform_ints(K, 100_000, 20_000_000, seed=51)
+    grid = cga.grid_from_box([-128.0] * 3, 256.0, 16)
+    pool, banks = [], []
+    for i in range(K):
+        n = int(sizes[i])
+        p = (synth_gpu.lidar_cloud(n, seed=5000 + i) if i % 2 == 0 else
+             synth_gpu.surface_cloud(n, seed=5000 + i, n_objects=max(4, min(200, n // 50000))))
+        pool.append(cga.cga_build(p, grid, allocator=None))
+        banks.append(synth_gpu.jitter_queries(p, 1_000_000, 0.2, seed=6000 + i))
+        del p
+    torch.cuda.synchronize()
+    resident = sum(c.info()["bytes"] for c in pool)
+    rng = np.random.default_rng(52)
+    rate = 2000.0
+    n_req = int(rate * args.serve_seconds)
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    arrivals = np.cumsum(gaps)
+    reqs = []
+    for r in range(n_req):
+        if rng.random() < 0.7:
+            m = int(math.exp(rng.uniform(0.0, math.log(1_000_000))))
+            reqs.append(("nn", int(rng.integers(K)), m))
+        else:
+            reqs.append(("mp", int(rng.integers(K)), int(rng.integers(K))))
+    server = cga.Server(pool, memory_budget=64 << 30, slots=4, max_batch=64)
+    clocks = start_clocks(local_rank)
+    t0 = time.perf_counter()
+    tickets = {}
+    for r, at in zip(reqs, arrivals):
+        while time.perf_counter() - t0 < at:
+            pass
+        if r[0] == "nn":
+            q = banks[r[1]][:r[2]]
+            idx = torch.empty(r[2], dtype=torch.int32, device="cuda")
+            d2 = torch.empty(r[2], dtype=torch.int64, device="cuda")
+            tickets[server.submit_nn(r[1], q, idx, d2)] = r
+        else:
+            tickets[server.submit_merge_project(r[1], r[2], "xy")] = r
+    server.drain()
+    done = server.poll(max_n=n_req + 16)
+    clk = clocks.stop()
+    lat = np.array([(c["t_done_ns"] - c["t_submit_ns"]) / 1e6 for c in done])
+    span = (max(c["t_done_ns"] for c in done) - min(c["t_submit_ns"] for c in done)) / 1e9
+    nq = sum(r[2] for r in reqs if r[0] == "nn")
+    lat_nn = np.array([(c["t_done_ns"] - c["t_submit_ns"]) / 1e6 for c in done
+                       if tickets[c["ticket"]][0] == "nn"])
+    lat_mp = np.array([(c["t_done_ns"] - c["t_submit_ns"]) / 1e6 for c in done
+                       if tickets[c["ticket"]][0] == "mp"])
+    ok = all(c["status"] == 0 for c in done)
+    del done
+    server.free()
+    # each request alone through the plain path (a seeded sample)
+    alone = []
+    for r in [reqs[i] for i in rng.choice(n_req, size=min(200, n_req), replace=False)]:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        if r[0] == "nn":
+            cga.cga_nn_query(pool[r[1]], banks[r[1]][:r[2]])
+        else:
+            mg = cga.cga_merge(pool[r[1]], pool[r[2]], allocator=None)
+            cga.cga_project(mg, "xy", allocator=None)
+        torch.cuda.synchronize()
+        alone.append((time.perf_counter() - t) * 1e3)
+    alone = np.array(alone)
+    out = base_line(args, world_size, "served requests/s (p50/p99 latency)", n_req / span,
+                    "requests/s", span * 1e3,
+                    {"workload": "served: Poisson 2000 req/s over 64 resident CGAs (n log-uniform "
+                                 "[1e5, 2e7], b=16); 70% NN (m log-uniform [1, 1e6]), 30% "
+                                 "merge + xy projection of a random pair",
+                     "requests": n_req, "resident_points": int(sizes.sum()),
+                     "resident_cga_bytes": int(resident), "slots": 4, "max_batch": 64,
+                     "memory_budget_bytes": 64 << 30},
+                    "synthetic (seeded GPU generators)")
+    out.update({"all_ok": ok, "queries_per_s": round(nq / span, 1),
+                "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                               "p99": round(float(np.percentile(lat, 99)), 3),
+                               "nn_p50": round(float(np.percentile(lat_nn, 50)), 3),
+                               "nn_p99": round(float(np.percentile(lat_nn, 99)), 3),
+                               "mp_p50": round(float(np.percentile(lat_mp, 50)), 3),
+                               "mp_p99": round(float(np.percentile(lat_mp, 99)), 3)},
+                "alone_latency_ms": {"p50": round(float(np.percentile(alone, 50)), 3),
+                                     "p99": round(float(np.percentile(alone, 99)), 3),
+                                     "sample": len(alone)},
+                "clocks": clk})
+    return out
 
 
 # ------------------------------------------------------------ oracle (CPU)
@@ -343,7 +607,7 @@ def cpu_baseline(scene, queries, n_sample=20_000):
                       f"{len(queries)} queries, scaled to all"}
 
 
-def run_reference(args, rank):
+def run_reference(args):
     scene, queries = make_workload(0)
     import oracle as orc
     og = orc.grid_from_box(LO, EXTENT, BITS)
@@ -373,21 +637,29 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         if rank == 0:
-            print(json.dumps(run_reference(args, rank)))
+            print(json.dumps(run_reference(args)))
         return
+    import torch
+    import torch.distributed as dist
+    from paper_2110_11616_gb300 import build_ext, cga
+    build_ext.build()
+    cga.load()
+    torch.cuda.set_device(local_rank)
     if world_size > 1:
-        import torch
-        import torch.distributed as dist
-        torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    out, P = run_gpu(args, rank, world_size, local_rank)
-    if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
-        scene, queries = make_workload(0)
-        out["cpu_baseline"] = cpu_baseline(scene, queries)
+    if args.config == "lidar":
+        out, (scene, queries) = run_lidar(args, rank, world_size, local_rank, torch, dist, cga)
+        if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(scene, queries)
+    elif args.config in ("plain", "surface"):
+        out = run_single(args, world_size, local_rank, torch, cga, args.config)
+    elif args.config == "batched":
+        out = run_batched(args, world_size, local_rank, torch, cga)
+    else:
+        out = run_served(args, world_size, local_rank, torch, cga)
     if rank == 0:
         print(json.dumps(out))
     if world_size > 1:
-        import torch.distributed as dist
         dist.destroy_process_group()
 
 

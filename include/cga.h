@@ -148,6 +148,18 @@ int cga_project(const cga_t* a, int plane, const cga_allocator* A, void* stream,
 int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
                  uint64_t* d_dist2, void* stream);
 
+/* The two halves of cga_nn_query, for callers that reuse one query order or
+ * time the search on its own.  cga_nn_sort_queries writes m 64-bit keys
+ * (30-bit Morton code of the query's grid voxel << 32 | query index), sorted
+ * ascending, to d_order (device, m entries; scratch from a's allocator).
+ * cga_nn_query_ordered answers the queries in the order d_order gives (low 32
+ * bits = query index; NULL = index order); results land at each query's own
+ * index and equal cga_nn_query's.  Indices >= m in d_order are skipped. */
+int cga_nn_sort_queries(const cga_t* a, const float* d_q, uint64_t m, uint64_t* d_order,
+                        void* stream);
+int cga_nn_query_ordered(const cga_t* a, const float* d_q, uint64_t m, const uint64_t* d_order,
+                         uint32_t* d_idx, uint64_t* d_dist2, void* stream);
+
 /* cga_nn_query without any memory allocation.  (The paper has no counterpart:
  * this is a deployment variant of the NN call above, same results bit for
  * bit.)  For callers that cannot allocate device memory when they query --

@@ -37,7 +37,7 @@ EXPORTS = (
     "cga_pipeline_create", "cga_pipeline_run", "cga_pipeline_run_graph", "cga_pipeline_view",
     "cga_pipeline_view_xy", "cga_pipeline_free", "cga_nn_query_noalloc",
     "cga_server_create", "cga_server_submit", "cga_server_poll", "cga_server_drain",
-    "cga_server_free", "cga_now_ns",
+    "cga_server_free", "cga_now_ns", "cga_nn_sort_queries", "cga_nn_query_ordered",
 )
 
 
@@ -608,3 +608,29 @@ class Server:
             self.free()
         except Exception:
             pass
+
+
+def cga_nn_sort_queries(a: Cga, queries, order=None, stream=None):
+    """Sorted (morton << 32 | index) keys of the queries, as an int64 tensor."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_nn_sort_queries.argtypes = [P, P, ctypes.c_uint64, P, P]
+    m = queries.numel() // 3
+    if order is None:
+        order = torch.empty(m, dtype=torch.int64, device=queries.device)
+    _check(lib.cga_nn_sort_queries(a.ptr, P(queries.data_ptr()), m, P(order.data_ptr()),
+                                   _stream(stream)), "cga_nn_sort_queries")
+    return order
+
+
+def cga_nn_query_ordered(a: Cga, queries, order, idx, dist2, stream=None):
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_nn_query_ordered.argtypes = [P, P, ctypes.c_uint64, P, P, P, P]
+    m = queries.numel() // 3
+    _check(lib.cga_nn_query_ordered(a.ptr, P(queries.data_ptr()), m,
+                                    None if order is None else P(order.data_ptr()),
+                                    P(idx.data_ptr()), P(dist2.data_ptr()), _stream(stream)),
+           "cga_nn_query_ordered")
+    return idx, dist2

@@ -390,6 +390,56 @@ int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
   return rc;
 }
 
+namespace {
+
+libcga::NnSeg nn_segment(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
+                         uint64_t* d_dist2) {
+  libcga::NnSeg seg{};
+  seg.a = a->lv;
+  seg.scale = a->grid.scale;
+  for (int k = 0; k < 3; ++k) seg.off[k] = a->grid.offset[k];
+  seg.q = d_q;
+  seg.m = (uint32_t)m;
+  seg.idx = d_idx;
+  seg.d2 = reinterpret_cast<unsigned long long*>(d_dist2);
+  seg.tile_base = 0;
+  seg.num_tiles = (uint32_t)((m + libcga::kTile - 1) / libcga::kTile);
+  return seg;
+}
+
+}  // namespace
+
+int cga_nn_sort_queries(const cga_t* a, const float* d_q, uint64_t m, uint64_t* d_order,
+                        void* stream) {
+  if (a == nullptr || (m > 0 && (d_q == nullptr || d_order == nullptr))) return CGA_ERR_INVALID_ARG;
+  if (m > libcga::kNnMaxQueries) return CGA_ERR_INVALID_ARG;
+  if (m == 0) return CGA_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const libcga::NnSeg seg = nn_segment(a, d_q, m, nullptr, nullptr);
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  void* scratch = dalloc(A, libcga::nn_scratch_bytes(seg.num_tiles, 1), s);
+  if (scratch == nullptr) return CGA_ERR_OOM;
+  const libcga::NnTables t = libcga::nn_tables(scratch, seg.num_tiles, 1);
+  cudaError_t e = libcga::nn_upload_one(seg, t, s);
+  if (e == cudaSuccess) e = libcga::run_nn_sort_device(1, seg.num_tiles, t, s);
+  if (e == cudaSuccess) {
+    e = cudaMemcpyAsync(d_order, t.sort.keys0, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+  }
+  dfree(A, a->has_alloc, scratch, s);
+  return cuda_rc(e);
+}
+
+int cga_nn_query_ordered(const cga_t* a, const float* d_q, uint64_t m, const uint64_t* d_order,
+                         uint32_t* d_idx, uint64_t* d_dist2, void* stream) {
+  if (a == nullptr || (m > 0 && (d_q == nullptr || d_idx == nullptr || d_dist2 == nullptr))) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  if (m > libcga::kNnMaxQueries) return CGA_ERR_INVALID_ARG;
+  const libcga::NnSeg seg = nn_segment(a, d_q, m, d_idx, d_dist2);
+  return cuda_rc(libcga::run_nn_search(seg, reinterpret_cast<const unsigned long long*>(d_order),
+                                       static_cast<cudaStream_t>(stream)));
+}
+
 int cga_decode(const cga_t* a, uint32_t* d_xyz, void* stream) {
   if (a == nullptr || (d_xyz == nullptr && a->lv.cap > 0)) return CGA_ERR_INVALID_ARG;
   return cuda_rc(libcga::run_decode(a->lv, d_xyz, static_cast<cudaStream_t>(stream)));

@@ -178,6 +178,11 @@ NnTables nn_tables(void* scratch, uint32_t total_tiles, int S);
 cudaError_t nn_upload(const NnSeg* h_segs, int S, const NnTables& t, cudaStream_t stream);
 // Upload the tables of one segment from stack copies (no heap allocation).
 cudaError_t nn_upload_one(const NnSeg& h_seg, const NnTables& t, cudaStream_t stream);
+// Only the query sort (keys in t.sort.keys0 afterwards), or only the search of
+// one segment with a given order (nullptr: query order).
+cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
+                               cudaStream_t stream);
+cudaError_t run_nn_search(const NnSeg& seg, const unsigned long long* order, cudaStream_t stream);
 // Run with the tables on the device (capturable: memsets and kernels only).
 cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream);
 

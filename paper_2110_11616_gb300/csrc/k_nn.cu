@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs,
                                                  const unsigned int* __restrict__ order_err) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  const bool sorted = order != nullptr && *order_err == 0u;
+  const bool sorted = order != nullptr && (order_err == nullptr || *order_err == 0u);
   for (uint32_t slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total_slots;
        slot += nwarps) {
     const uint32_t tile = slot / (uint32_t)kTile;
@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs,
     const uint32_t local = slot - sg.tile_base * (uint32_t)kTile;
     if (local >= sg.m) continue;
     const uint32_t j = sorted ? (uint32_t)order[slot] : local;
+    if (j >= sg.m) continue;  // a caller-given order that is not a permutation
     const Levels& a = sg.a;
     const float* p = sg.q + 3 * (size_t)j;
     const float px = p[0], py = p[1], pz = p[2];
@@ -293,6 +294,24 @@ static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
       std::min<uint32_t>((total_slots + 7) / 8, (uint32_t)device_sm_count() * 8);
   k_nn_warp<<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order, order_err);
   count_launch(1);
+}
+
+cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
+                               cudaStream_t stream) {
+  if (total_tiles == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(t.err, 0, sizeof(Header), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t.sort.hist, 0, t.sort.zero_bytes, stream);
+  if (e != cudaSuccess) return e;
+  k_nn_keys<<<total_tiles * (kTile / 256), 256, 0, stream>>>(
+      t.segs, S, static_cast<unsigned long long*>(t.sort.keys0), t.sort.hist);
+  count_launch(1);
+  return run_radix_passes(S, total_tiles, 4, true, t.sort, stream);
+}
+
+cudaError_t run_nn_search(const NnSeg& seg, const unsigned long long* order, cudaStream_t stream) {
+  if (seg.m == 0) return cudaSuccess;
+  launch_search(nullptr, 1, seg, seg.num_tiles, order, nullptr, stream);
+  return cudaGetLastError();
 }
 
 cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream) {

@@ -255,3 +255,23 @@ def test_decode_parity(cg, orc, bits, n):
     a = cg.cga_build(dev(pts), g)
     got = cg.cga_decode(a).cpu().numpy().astype(np.uint32).reshape(-1, 3)
     np.testing.assert_array_equal(got, orc.decode(orc.build(pts, og)))
+
+
+def test_nn_two_step_equals_one_call(cg, orc):
+    pts = synth.uniform_cube(60_000, seed=91)
+    g, og = grids(cg, orc, [0, 0, 0], 1.0, 11)
+    a = cg.cga_build(dev(pts), g)
+    q = dev(synth.uniform_queries(50_000, 92, [-0.1] * 3, 1.2))
+    order = cg.cga_nn_sort_queries(a, q)
+    keys = order.cpu().numpy().view(np.uint64)
+    assert np.all(np.diff(keys.astype(np.float64)) >= 0) or np.all(keys[1:] >= keys[:-1])
+    assert np.array_equal(np.sort(keys & np.uint64(0xFFFFFFFF)), np.arange(len(keys), dtype=np.uint64))
+    idx = torch.empty(50_000, dtype=torch.int32, device="cuda")
+    d2 = torch.empty(50_000, dtype=torch.int64, device="cuda")
+    cg.cga_nn_query_ordered(a, q, order, idx, d2)
+    ri, rd = cg.cga_nn_query(a, q)
+    assert torch.equal(idx, ri) and torch.equal(d2, rd)
+    idx2 = torch.empty_like(idx)
+    d22 = torch.empty_like(d2)
+    cg.cga_nn_query_ordered(a, q, None, idx2, d22)   # query order
+    assert torch.equal(idx2, ri) and torch.equal(d22, rd)
