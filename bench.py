@@ -339,20 +339,23 @@ def run_single(args, world_size, local_rank, torch, cga, which):
         workload = ("plain: 100k uniform pts + rigidly transformed twin, b=10; batched build of "
                     "both, merge, xy projection, 10k uniform NN, decode")
         n_points = 200_000
+        coarse_shift = 0
     else:
-        full = synth_gpu.surface_cloud(30_000_000, seed=3)
+        scene = synth_gpu.surface_scene(3)
+        full = synth_gpu.sample_scene(scene, 30_000_000, seed=4)
         halves = [full[0::2].contiguous(), full[1::2].contiguous()]
         del full
         xforms = [None, None]
         grid = cga.grid_from_box([0, 0, 0], 100.0, 12)
-        surf = synth_gpu.surface_cloud(4_000_000, seed=4)
-        uni = synth_gpu.uniform_queries(4_000_000, 5, [0.0, 0.0, 0.0], 100.0)
+        surf = synth_gpu.sample_scene(scene, 4_000_000, seed=5)
+        uni = synth_gpu.uniform_queries(4_000_000, 6, [0.0, 0.0, 0.0], 100.0)
         q = torch.cat([surf, uni]).contiguous()
         planes = ["xy", "xz", "yz"]
         workload = ("surface: 30M pts on 200 superellipsoids, b=12; batched build of the even/odd "
                     "halves, merge, xy/xz/yz projections, 8M NN (4M on-surface + 4M uniform), "
                     "decode")
         n_points = 30_000_000
+        coarse_shift = 2  # two-level NN search: coarse cells of 4 voxels
     m = q.shape[0]
     order = torch.empty(m, dtype=torch.int64, device="cuda")
     idx = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -369,6 +372,8 @@ def run_single(args, world_size, local_rank, torch, cga, which):
         ev[2].record()
         pr = cga.cga_project_batch([mg] * len(planes), planes, allocator=None)
         ev[3].record()
+        if coarse_shift:
+            cga.cga_nn_prepare(mg, coarse_shift)
         cga.cga_nn_sort_queries(mg, q, order)
         ev[4].record()
         cga.cga_nn_query_ordered(mg, q, order, idx, d2)
@@ -402,7 +407,7 @@ def run_single(args, world_size, local_rank, torch, cga, which):
                      "l2": "flushed between steps"}, "synthetic (seeded generators)")
     out.update({
         "breakdown_ms": {"build": round(ops[0], 4), "merge": round(ops[1], 4),
-                         "project": round(ops[2], 4), "nn_sort": round(ops[3], 4),
+                         "project": round(ops[2], 4), "nn_prepare_sort": round(ops[3], 4),
                          "nn_search": round(ops[4], 4), "decode": round(ops[5], 4)},
         "derived": {"build_Mpts_s": round(n_points / (ops[0] / 1e3) / 1e6, 2),
                     "nn_queries_s": round(m / ((ops[3] + ops[4]) / 1e3), 1),

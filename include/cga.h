@@ -148,6 +148,15 @@ int cga_project(const cga_t* a, int plane, const cga_allocator* A, void* stream,
 int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
                  uint64_t* d_dist2, void* stream);
 
+/* Build (once per CGA) the coarse companion that lets NN search skip empty
+ * space: the CGA of the occupied cells of 2^shift voxels per axis, plus for
+ * each coarse x slab the index of its first fine slab.  Afterwards every NN
+ * call on `a` searches the coarse cells first and refines only those whose
+ * box lower bound can beat the best distance found so far (same results).
+ * shift in 1..min(8, bits-1); shift 0 removes the companion.  Memory comes from
+ * a's allocator and is released with a.  Stream-ordered. */
+int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream);
+
 /* The two halves of cga_nn_query, for callers that reuse one query order or
  * time the search on its own.  cga_nn_sort_queries writes m 64-bit keys
  * (30-bit Morton code of the query's grid voxel << 32 | query index), sorted

@@ -38,6 +38,7 @@ EXPORTS = (
     "cga_pipeline_view_xy", "cga_pipeline_free", "cga_nn_query_noalloc",
     "cga_server_create", "cga_server_submit", "cga_server_poll", "cga_server_drain",
     "cga_server_free", "cga_now_ns", "cga_nn_sort_queries", "cga_nn_query_ordered",
+    "cga_nn_prepare",
 )
 
 
@@ -634,3 +635,11 @@ def cga_nn_query_ordered(a: Cga, queries, order, idx, dist2, stream=None):
                                     P(idx.data_ptr()), P(dist2.data_ptr()), _stream(stream)),
            "cga_nn_query_ordered")
     return idx, dist2
+
+
+def cga_nn_prepare(a: Cga, shift: int, stream=None):
+    """Build the coarse companion (cells of 2^shift voxels) used by NN search."""
+    lib = load()
+    lib.cga_nn_prepare.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
+    _check(lib.cga_nn_prepare(a.ptr, shift, _stream(stream)), "cga_nn_prepare")
+    return a

@@ -23,6 +23,11 @@ struct cga {
   bool has_alloc;
   cudaStream_t stream;
   bool view = false;  // arrays owned by a pipeline; cga_free leaves them alone
+  // coarse companion for NN (cga_nn_prepare): CGA of occupied 2^cshift cells
+  void* cmem = nullptr;
+  Levels clv{};
+  uint32_t* xs = nullptr;
+  uint32_t cshift = 0;
 };
 
 struct cga2d {
@@ -190,8 +195,18 @@ cga* new_cga(const cga_grid& g, const cga_allocator* A, cudaStream_t s, uint64_t
 
 void release(cga* h) {
   if (h == nullptr || h->view) return;
+  if (h->cmem != nullptr) dfree(&h->alloc, h->has_alloc, h->cmem, h->stream);
   dfree(&h->alloc, h->has_alloc, h->mem, h->stream);
   delete h;
+}
+
+// NN searches use the coarse companion when cga_nn_prepare built one.
+void attach_coarse(const cga* a, libcga::NnSeg& seg) {
+  if (a->cmem == nullptr) return;
+  seg.c = a->clv;
+  seg.xs = a->xs;
+  seg.shift = a->cshift;
+  seg.has_coarse = 1;
 }
 
 }  // namespace
@@ -379,6 +394,7 @@ int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
   seg.d2 = reinterpret_cast<unsigned long long*>(d_dist2);
   seg.tile_base = 0;
   seg.num_tiles = (uint32_t)((m + libcga::kTile - 1) / libcga::kTile);
+  attach_coarse(a, seg);
   const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
   void* scratch = nullptr;
   if (m >= libcga::kNnSortMin) {
@@ -404,10 +420,62 @@ libcga::NnSeg nn_segment(const cga_t* a, const float* d_q, uint64_t m, uint32_t*
   seg.d2 = reinterpret_cast<unsigned long long*>(d_dist2);
   seg.tile_base = 0;
   seg.num_tiles = (uint32_t)((m + libcga::kTile - 1) / libcga::kTile);
+  attach_coarse(a, seg);
   return seg;
 }
 
 }  // namespace
+
+int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream) {
+  if (a == nullptr || a->view || shift >= a->grid.bits || shift > 8) return CGA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  if (a->cmem != nullptr) {
+    dfree(A, a->has_alloc, a->cmem, a->stream);
+    a->cmem = nullptr;
+  }
+  if (shift == 0) return CGA_OK;
+  const uint32_t bc = a->grid.bits - shift;
+  const uint64_t cap = std::min<uint64_t>(a->lv.cap, pow2(3 * bc));
+  const uint64_t cap1 = std::min<uint64_t>(cap, pow2(2 * bc));
+  const uint64_t cap2 = std::min<uint64_t>(cap, pow2(bc));
+  const size_t lb = levels_bytes(cap, cap1, cap2, 3);
+  void* mem = dalloc(A, lb + align_up((cap2 + 1) * 4), s);
+  if (mem == nullptr) return CGA_ERR_OOM;
+  const Levels clv = levels_carve(mem, bc, cap, cap1, cap2, 3);
+  uint32_t* xs = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb);
+  libcga::SortSeg seg{};
+  seg.src = a->lv;
+  seg.plane = 3;
+  seg.shift = shift;
+  seg.from_cga = 1;
+  seg.bits = bc;
+  seg.key_bits = 3 * bc;
+  seg.passes = (seg.key_bits + libcga::kRadixBits - 1) / libcga::kRadixBits;
+  seg.num_tiles = (uint32_t)((a->lv.cap + libcga::kTile - 1) / libcga::kTile);
+  seg.out = clv;
+  const bool key64 = seg.key_bits > 32;
+  const uint32_t tiles = seg.num_tiles;
+  const uint64_t keys = (uint64_t)tiles * libcga::kTile;
+  void* scratch = dalloc(A, libcga::sort_scratch_bytes(keys, tiles, 1, key64), s);
+  int rc = CGA_ERR_OOM;
+  if (scratch != nullptr) {
+    const libcga::SortScratch sc = libcga::sort_scratch_carve(scratch, keys, tiles, 1, key64);
+    cudaError_t e = libcga::run_sort_pipeline(&seg, 1, tiles, seg.passes, key64, sc, s);
+    if (e == cudaSuccess) e = libcga::run_coarse_slab_index(a->lv, clv, shift, xs, s);
+    rc = cuda_rc(e);
+    dfree(A, a->has_alloc, scratch, s);
+  }
+  if (rc != CGA_OK) {
+    dfree(A, a->has_alloc, mem, s);
+    return rc;
+  }
+  a->cmem = mem;
+  a->clv = clv;
+  a->xs = xs;
+  a->cshift = shift;
+  return CGA_OK;
+}
 
 int cga_nn_sort_queries(const cga_t* a, const float* d_q, uint64_t m, uint64_t* d_order,
                         void* stream) {
@@ -807,6 +875,7 @@ int cga_nn_query_batch(const cga_t* const* a, const cga_queries* q, uint32_t cou
     sg.d2 = reinterpret_cast<unsigned long long*>(q[i].d_dist2);
     sg.tile_base = (uint32_t)tiles;
     sg.num_tiles = (uint32_t)((q[i].m + libcga::kTile - 1) / libcga::kTile);
+    attach_coarse(a[i], sg);
     tiles += sg.num_tiles;
     segs.push_back(sg);
   }

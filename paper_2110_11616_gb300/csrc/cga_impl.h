@@ -54,7 +54,8 @@ struct SortSeg {
   uint32_t has_x;
   // projection input: the source CGA and the plane
   Levels src;
-  int32_t plane;
+  int32_t plane;      // 0 xy, 1 xz, 2 yz: 2D re-key; 3: coarsen (3D, >> shift)
+  uint32_t shift;     // plane 3: coarse cell = 2^shift voxels per axis
   uint32_t from_cga;  // 1: keys come from src (projection), 0: from xyz
   // common
   uint32_t n_host;      // element count when known on the host (build)
@@ -151,6 +152,13 @@ cudaError_t run_project_xy_device(const ProjPair* d_pairs, int S, uint64_t max_c
 // Morton curve so that neighbouring warps search neighbouring space.
 struct NnSeg {
   Levels a;
+  // optional coarse companion of `a` (has_coarse): the CGA of the occupied
+  // cells of 2^shift voxels per axis, and for each coarse slab the index of
+  // its first fine slab in a's X_index (xs[h_coarse] = h_fine)
+  Levels c;
+  const uint32_t* xs;
+  uint32_t shift;
+  uint32_t has_coarse;
   float scale;
   float off[3];
   const float* q;
@@ -185,6 +193,11 @@ cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
 cudaError_t run_nn_search(const NnSeg& seg, const unsigned long long* order, cudaStream_t stream);
 // Run with the tables on the device (capturable: memsets and kernels only).
 cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream);
+
+// For each slab k of the coarse CGA c (cells of 2^shift voxels), xs[k] = first
+// index of a's X_index whose x >> shift equals c's X_index[k]; xs[h_c] = h_a.
+cudaError_t run_coarse_slab_index(const Levels& a, const Levels& c, uint32_t shift, uint32_t* xs,
+                                  cudaStream_t stream);
 
 int device_sm_count();
 

@@ -136,6 +136,184 @@ __device__ __forceinline__ void visit_column(const Levels& a, uint32_t c, unsign
   }
 }
 
+// Window search over the fine CGA alone (one warp, 16 slabs per side per round).
+__device__ __forceinline__ void search_fine(const Levels& a, uint32_t h, long long qx, long long qy,
+                                            long long qz, uint32_t cqx, uint32_t cqy, uint32_t cqz,
+                                            uint32_t lane, Best& best) {
+  const uint32_t b = a.bits;
+  const uint32_t xr0 = lower_bound_u16(a.idx2, 0, h, cqx);
+  const bool right = (lane & 1u) == 0u;
+  for (uint32_t r = 0;; ++r) {
+    const long long k = (long long)r * 16 + (lane >> 1);
+    const long long slab = right ? (long long)xr0 + k : (long long)xr0 - 1 - k;
+    const bool valid = slab >= 0 && slab < (long long)h;
+    unsigned long long dx2 = ~0ull;
+    uint32_t x = 0;
+    if (valid) {
+      x = __ldg(a.idx2 + slab);
+      const unsigned long long dx = absdiff(x, qx);
+      dx2 = dx * dx;
+    }
+    const bool active = valid && dx2 <= best.d2;
+    if (!__any_sync(0xffffffffu, active)) break;
+    uint32_t ys = 0, ye = 0, yr0 = 0;
+    const unsigned long long kx = (unsigned long long)x << (2 * b);
+    if (active) {
+      ys = __ldg(a.ptr2 + slab);
+      ye = __ldg(a.ptr2 + slab + 1);
+      yr0 = lower_bound_u16(a.idx1, ys, ye, cqy);
+      if (yr0 < ye) {
+        const uint32_t y = __ldg(a.idx1 + yr0);
+        const unsigned long long dy = absdiff(y, qy);
+        const unsigned long long dxy = dx2 + dy * dy;
+        if (dxy <= best.d2) visit_column(a, yr0, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+      }
+      if (yr0 > ys) {
+        const uint32_t y = __ldg(a.idx1 + yr0 - 1);
+        const unsigned long long dy = absdiff(y, qy);
+        const unsigned long long dxy = dx2 + dy * dy;
+        if (dxy <= best.d2) visit_column(a, yr0 - 1, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+      }
+    }
+    best.warp_min();
+    if (active) {
+      long long R2 = (long long)yr0 + 1, L2 = (long long)yr0 - 2;
+      while (true) {
+        const bool hR = R2 < (long long)ye, hL = L2 >= (long long)ys;
+        if (!hR && !hL) break;
+        const unsigned long long eR = hR ? absdiff(__ldg(a.idx1 + R2), qy) : ~0ull;
+        const unsigned long long eL = hL ? absdiff(__ldg(a.idx1 + L2), qy) : ~0ull;
+        const bool gR = hR && (!hL || eR <= eL);
+        const unsigned long long dy = gR ? eR : eL;
+        const unsigned long long dxy = dx2 + dy * dy;
+        if (dxy > best.d2) break;
+        const uint32_t c = (uint32_t)(gR ? R2 : L2);
+        if (gR) ++R2; else --L2;
+        const uint32_t y = __ldg(a.idx1 + c);
+        visit_column(a, c, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+      }
+    }
+    best.warp_min();
+  }
+}
+
+// Distance from q to the voxel interval [lo, lo + s - 1] (0 inside).
+__device__ __forceinline__ unsigned long long interval_dist(long long q, uint32_t lo, uint32_t s) {
+  const long long l = lo, hi = (long long)lo + s - 1;
+  return q < l ? (unsigned long long)(l - q) : (q > hi ? (unsigned long long)(q - hi) : 0ull);
+}
+
+// Every fine column inside the footprint of one coarse column: fine slabs
+// [fx0, fx1) (the fine slabs of the coarse slab), y in [ylo, ylo + s).
+__device__ __forceinline__ void refine_footprint(const Levels& a, uint32_t fx0, uint32_t fx1,
+                                                 uint32_t ylo, uint32_t s, long long qx,
+                                                 long long qy, long long qz, uint32_t cqz,
+                                                 Best& best) {
+  const uint32_t b = a.bits;
+  for (uint32_t xi = fx0; xi < fx1; ++xi) {
+    const uint32_t x = __ldg(a.idx2 + xi);
+    const unsigned long long dx = absdiff(x, qx);
+    const unsigned long long dx2 = dx * dx;
+    if (dx2 > best.d2) continue;
+    const uint32_t ys = __ldg(a.ptr2 + xi), ye = __ldg(a.ptr2 + xi + 1);
+    const unsigned long long kx = (unsigned long long)x << (2 * b);
+    for (uint32_t c = lower_bound_u16(a.idx1, ys, ye, ylo); c < ye; ++c) {
+      const uint32_t y = __ldg(a.idx1 + c);
+      if (y >= ylo + s) break;
+      const unsigned long long dy = absdiff(y, qy);
+      const unsigned long long dxy = dx2 + dy * dy;
+      if (dxy > best.d2) continue;
+      visit_column(a, c, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+    }
+  }
+}
+
+// A coarse column (cx, cy): its nearest occupied coarse cell along z bounds
+// every point below it; refine the fine footprint only if that bound can beat
+// the best distance so far.
+__device__ __forceinline__ void visit_coarse_column(const NnSeg& sg, uint32_t cc, uint32_t cy,
+                                                    unsigned long long dxl2,
+                                                    unsigned long long dyl2, uint32_t fx0,
+                                                    uint32_t fx1, long long qx, long long qy,
+                                                    long long qz, uint32_t cqz, Best& best) {
+  if (dxl2 + dyl2 > best.d2) return;
+  const Levels& c = sg.c;
+  const uint32_t L = sg.shift, s = 1u << L;
+  const uint32_t zs = __ldg(c.ptr1 + cc), ze = __ldg(c.ptr1 + cc + 1);
+  const uint32_t zr = lower_bound_u16(c.idx0, zs, ze, cqz >> L);
+  unsigned long long dzl = ~0ull;
+  if (zr < ze) dzl = min(dzl, interval_dist(qz, (uint32_t)__ldg(c.idx0 + zr) << L, s));
+  if (zr > zs) dzl = min(dzl, interval_dist(qz, (uint32_t)__ldg(c.idx0 + zr - 1) << L, s));
+  if (dxl2 + dyl2 + dzl * dzl > best.d2) return;
+  refine_footprint(sg.a, fx0, fx1, cy << L, s, qx, qy, qz, cqz, best);
+}
+
+// Two-level window search: the same round structure over the coarse CGA (the
+// occupied cells of 2^shift voxels), with box lower bounds deciding which
+// cells' fine footprints are searched.  A point lies in an occupied cell whose
+// bound never exceeds the point's distance, so pruning by "bound > best"
+// never drops a point at or below the final distance.
+__device__ __forceinline__ void search_two_level(const NnSeg& sg, long long qx, long long qy,
+                                                 long long qz, uint32_t cqx, uint32_t cqy,
+                                                 uint32_t cqz, uint32_t lane, Best& best) {
+  const Levels& c = sg.c;
+  const uint32_t L = sg.shift, s = 1u << L;
+  const uint32_t hc = (uint32_t)c.hdr->cnt[2];
+  const uint32_t xr0 = lower_bound_u16(c.idx2, 0, hc, cqx >> L);
+  const uint32_t cqy_c = cqy >> L;
+  const bool right = (lane & 1u) == 0u;
+  for (uint32_t r = 0;; ++r) {
+    const long long k = (long long)r * 16 + (lane >> 1);
+    const long long slab = right ? (long long)xr0 + k : (long long)xr0 - 1 - k;
+    const bool valid = slab >= 0 && slab < (long long)hc;
+    unsigned long long dxl2 = ~0ull;
+    if (valid) {
+      const unsigned long long dxl = interval_dist(qx, (uint32_t)__ldg(c.idx2 + slab) << L, s);
+      dxl2 = dxl * dxl;
+    }
+    const bool active = valid && dxl2 <= best.d2;
+    if (!__any_sync(0xffffffffu, active)) break;
+    uint32_t ys = 0, ye = 0, yr0 = 0, fx0 = 0, fx1 = 0;
+    if (active) {
+      ys = __ldg(c.ptr2 + slab);
+      ye = __ldg(c.ptr2 + slab + 1);
+      yr0 = lower_bound_u16(c.idx1, ys, ye, cqy_c);
+      fx0 = __ldg(sg.xs + slab);
+      fx1 = __ldg(sg.xs + slab + 1);
+      if (yr0 < ye) {
+        const uint32_t cy = __ldg(c.idx1 + yr0);
+        const unsigned long long dyl = interval_dist(qy, cy << L, s);
+        visit_coarse_column(sg, yr0, cy, dxl2, dyl * dyl, fx0, fx1, qx, qy, qz, cqz, best);
+      }
+      if (yr0 > ys) {
+        const uint32_t cy = __ldg(c.idx1 + yr0 - 1);
+        const unsigned long long dyl = interval_dist(qy, cy << L, s);
+        visit_coarse_column(sg, yr0 - 1, cy, dxl2, dyl * dyl, fx0, fx1, qx, qy, qz, cqz, best);
+      }
+    }
+    best.warp_min();
+    if (active) {
+      long long R2 = (long long)yr0 + 1, L2 = (long long)yr0 - 2;
+      while (true) {
+        const bool hR = R2 < (long long)ye, hL = L2 >= (long long)ys;
+        if (!hR && !hL) break;
+        const unsigned long long eR =
+            hR ? interval_dist(qy, (uint32_t)__ldg(c.idx1 + R2) << L, s) : ~0ull;
+        const unsigned long long eL =
+            hL ? interval_dist(qy, (uint32_t)__ldg(c.idx1 + L2) << L, s) : ~0ull;
+        const bool gR = hR && (!hL || eR <= eL);
+        const unsigned long long dyl = gR ? eR : eL;
+        if (dxl2 + dyl * dyl > best.d2) break;
+        const uint32_t cc = (uint32_t)(gR ? R2 : L2);
+        if (gR) ++R2; else --L2;
+        visit_coarse_column(sg, cc, __ldg(c.idx1 + cc), dxl2, dyl * dyl, fx0, fx1, qx, qy, qz,
+                            cqz, best);
+      }
+    }
+    best.warp_min();
+  }
+}
+
 __global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs, int S,
                                                  NnSeg inline_seg, uint32_t total_slots,
                                                  const unsigned long long* __restrict__ order,
@@ -170,60 +348,11 @@ __global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs,
     const uint32_t cqx = (uint32_t)min(max(qx, 0ll), top);
     const uint32_t cqy = (uint32_t)min(max(qy, 0ll), top);
     const uint32_t cqz = (uint32_t)min(max(qz, 0ll), top);
-    const uint32_t xr0 = lower_bound_u16(a.idx2, 0, h, cqx);
     Best best{~0ull, ~0ull, 0xffffffffu};
-    const bool right = (lane & 1u) == 0u;
-    for (uint32_t r = 0;; ++r) {
-      const long long k = (long long)r * 16 + (lane >> 1);
-      const long long slab = right ? (long long)xr0 + k : (long long)xr0 - 1 - k;
-      const bool valid = slab >= 0 && slab < (long long)h;
-      unsigned long long dx2 = ~0ull;
-      uint32_t x = 0;
-      if (valid) {
-        x = __ldg(a.idx2 + slab);
-        const unsigned long long dx = absdiff(x, qx);
-        dx2 = dx * dx;
-      }
-      const bool active = valid && dx2 <= best.d2;
-      if (!__any_sync(0xffffffffu, active)) break;
-      uint32_t ys = 0, ye = 0, yr0 = 0;
-      const unsigned long long kx = (unsigned long long)x << (2 * b);
-      if (active) {
-        ys = __ldg(a.ptr2 + slab);
-        ye = __ldg(a.ptr2 + slab + 1);
-        yr0 = lower_bound_u16(a.idx1, ys, ye, cqy);
-        if (yr0 < ye) {
-          const uint32_t y = __ldg(a.idx1 + yr0);
-          const unsigned long long dy = absdiff(y, qy);
-          const unsigned long long dxy = dx2 + dy * dy;
-          if (dxy <= best.d2) visit_column(a, yr0, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
-        }
-        if (yr0 > ys) {
-          const uint32_t y = __ldg(a.idx1 + yr0 - 1);
-          const unsigned long long dy = absdiff(y, qy);
-          const unsigned long long dxy = dx2 + dy * dy;
-          if (dxy <= best.d2) visit_column(a, yr0 - 1, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
-        }
-      }
-      best.warp_min();
-      if (active) {
-        long long R2 = (long long)yr0 + 1, L2 = (long long)yr0 - 2;
-        while (true) {
-          const bool hR = R2 < (long long)ye, hL = L2 >= (long long)ys;
-          if (!hR && !hL) break;
-          const unsigned long long eR = hR ? absdiff(__ldg(a.idx1 + R2), qy) : ~0ull;
-          const unsigned long long eL = hL ? absdiff(__ldg(a.idx1 + L2), qy) : ~0ull;
-          const bool gR = hR && (!hL || eR <= eL);
-          const unsigned long long dy = gR ? eR : eL;
-          const unsigned long long dxy = dx2 + dy * dy;
-          if (dxy > best.d2) break;
-          const uint32_t c = (uint32_t)(gR ? R2 : L2);
-          if (gR) ++R2; else --L2;
-          const uint32_t y = __ldg(a.idx1 + c);
-          visit_column(a, c, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
-        }
-      }
-      best.warp_min();
+    if (sg.has_coarse) {
+      search_two_level(sg, qx, qy, qz, cqx, cqy, cqz, lane, best);
+    } else {
+      search_fine(a, h, qx, qy, qz, cqx, cqy, cqz, lane, best);
     }
     if (lane == 0) {
       sg.idx[j] = best.idx;

@@ -249,6 +249,15 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
                                       lt == nt - 1, P.out, clook, sm);
 }
 
+// ------------------------------------------------------- coarse slab index
+__global__ void k_coarse_slab_index(Levels a, Levels c, uint32_t shift, uint32_t* xs) {
+  const uint32_t hc = (uint32_t)c.hdr->cnt[2], ha = (uint32_t)a.hdr->cnt[2];
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= hc; k += stride) {
+    xs[k] = (k == hc) ? ha : lower_bound_u16(a.idx2, 0, ha, (uint32_t)__ldg(c.idx2 + k) << shift);
+  }
+}
+
 // ------------------------------------------------------------- projection xy
 __device__ __forceinline__ void project_xy_body(const Levels& a, const Levels& o, uint32_t t,
                                                 uint32_t stride) {
@@ -345,6 +354,16 @@ cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stre
   const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
                                                        (uint64_t)device_sm_count() * 8);
   k_project_xy<<<blocks, 256, 0, stream>>>(a, out);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t run_coarse_slab_index(const Levels& a, const Levels& c, uint32_t shift, uint32_t* xs,
+                                  cudaStream_t stream) {
+  const uint64_t work = c.cap2 + 1;
+  const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
+                                                       (uint64_t)device_sm_count() * 8);
+  k_coarse_slab_index<<<blocks, 256, 0, stream>>>(a, c, shift, xs);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -146,10 +146,16 @@ __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restric
       for (uint32_t e = tid; e < cnt; e += kThreads) {
         uint32_t x, y, z;
         point_at(a, win, start + e, x, y, z);
-        uint32_t u = x, v = y;
-        if (sg.plane == 1) { u = x; v = z; }
-        if (sg.plane == 2) { u = y; v = z; }
-        const K key = ((K)u << b) | (K)v;
+        K key;
+        if (sg.plane == 3) {
+          const uint32_t L = sg.shift;
+          key = ((K)(x >> L) << (2 * b)) | ((K)(y >> L) << b) | (K)(z >> L);
+        } else {
+          uint32_t u = x, v = y;
+          if (sg.plane == 1) { u = x; v = z; }
+          if (sg.plane == 2) { u = y; v = z; }
+          key = ((K)u << b) | (K)v;
+        }
         out[e] = key;
         for (uint32_t p = 0; p < passes; ++p) {
           atomicAdd(&s_hist[p][(uint32_t)(key >> (sg.bit0 + p * kRadixBits)) & (kRadix - 1)], 1u);

@@ -57,8 +57,9 @@ def lidar_cloud(n: int, seed: int, device="cuda") -> torch.Tensor:
     return (o + dw * t[:, None]).to(torch.float32).contiguous()
 
 
-def surface_cloud(n: int, seed: int, n_objects: int = 200, lo: float = 0.0, extent: float = 100.0,
-                  device="cuda") -> torch.Tensor:
+def surface_scene(seed: int, n_objects: int = 200, lo: float = 0.0, extent: float = 100.0,
+                  device="cuda") -> dict:
+    """Parameters of n_objects seeded superellipsoids inside [lo, lo + extent)^3."""
     g = _gen(seed, device)
     f64 = dict(dtype=torch.float64, device=device)
     e = torch.rand(n_objects, 2, generator=g, **f64) * 2.7 + 0.3
@@ -73,6 +74,15 @@ def surface_cloud(n: int, seed: int, n_objects: int = 200, lo: float = 0.0, exte
         torch.stack([2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)], 1),
     ], 1)
     ctr = torch.rand(n_objects, 3, generator=g, **f64) * (0.8 * extent) + lo + 0.1 * extent
+    return {"e": e, "axes": axes, "R": R, "ctr": ctr}
+
+
+def sample_scene(scene: dict, n: int, seed: int) -> torch.Tensor:
+    """n float32 points on the scene's surfaces (object share ~ mean axis^2)."""
+    e, axes, R, ctr = scene["e"], scene["axes"], scene["R"], scene["ctr"]
+    device = e.device
+    g = _gen(seed, device)
+    f64 = dict(dtype=torch.float64, device=device)
     wgt = axes.mean(1) ** 2
     obj = torch.multinomial((wgt / wgt.sum()).float(), n, replacement=True, generator=g)
     eta = (torch.rand(n, generator=g, **f64) - 0.5) * math.pi
@@ -88,6 +98,12 @@ def surface_cloud(n: int, seed: int, n_objects: int = 200, lo: float = 0.0, exte
     local = torch.stack([ax[:, 0] * ce * co, ax[:, 1] * ce * so, ax[:, 2] * se], 1)
     pts = torch.einsum("nij,nj->ni", R[obj], local) + ctr[obj]
     return pts.to(torch.float32).contiguous()
+
+
+def surface_cloud(n: int, seed: int, n_objects: int = 200, lo: float = 0.0, extent: float = 100.0,
+                  device="cuda") -> torch.Tensor:
+    """n points of the scene drawn from `seed` (sampled with seed + 1)."""
+    return sample_scene(surface_scene(seed, n_objects, lo, extent, device), n, seed + 1)
 
 
 def jitter_queries(points: torch.Tensor, m: int, sigma: float, seed: int) -> torch.Tensor:

@@ -275,3 +275,37 @@ def test_nn_two_step_equals_one_call(cg, orc):
     d22 = torch.empty_like(d2)
     cg.cga_nn_query_ordered(a, q, None, idx2, d22)   # query order
     assert torch.equal(idx2, ri) and torch.equal(d22, rd)
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3, 5])
+@pytest.mark.parametrize("kind", ["uniform", "surface", "lidar"])
+def test_nn_two_level_parity(cg, orc, shift, kind):
+    """NN after cga_nn_prepare (coarse cells of 2^shift voxels) equals the oracle,
+    for queries near the points, uniform in the box and far outside it."""
+    if kind == "uniform":
+        pts = synth.uniform_cube(30_000, seed=95)
+        lo, ext, bits = [0.0] * 3, 1.0, 10
+    elif kind == "surface":
+        scene = synth.superellipsoid_scene(n_objects=12, seed=96, extent=100.0)
+        pts = synth.sample_surfaces(scene, 60_000, seed=97)
+        lo, ext, bits = [0.0] * 3, 100.0, 12
+    else:
+        sc = synth.lidar_sweeps(2, 64, 512, seed=98)
+        pts = sc.world.astype(np.float32)
+        lo, ext, bits = [-128.0] * 3, 256.0, 16
+    g, og = grids(cg, orc, lo, ext, bits)
+    a = cg.cga_build(dev(pts), g)
+    cg.cga_nn_prepare(a, shift)
+    oa = orc.build(pts, og)
+    lo_a = np.asarray(lo, np.float64)
+    q = np.concatenate([
+        (pts[:1500].astype(np.float64) + np.random.default_rng(1).normal(0, ext / 200, (1500, 3))),
+        synth.uniform_queries(1500, 99, lo, ext),
+        synth.uniform_queries(200, 100, lo_a - ext, 3 * ext),
+    ]).astype(np.float32)
+    nn_check(cg, orc, a, oa, og, q, brute=False)
+    # the same with the queries sorted (large batch path)
+    idx, d2 = cg.cga_nn_query(a, dev(np.tile(q, (4, 1))))
+    oi, od = orc.nn_window(oa, og, q)
+    assert np.array_equal(d2.cpu().numpy().view(np.uint64), np.tile(od, 4))
+    assert np.array_equal(idx.cpu().numpy().view(np.uint32), np.tile(oi, 4))
