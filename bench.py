@@ -178,6 +178,7 @@ class LidarStep:
         self.n_points = sum(len(s) for s in scene.sweeps)
         self.dec = torch.empty((self.n_points, 3), dtype=torch.int32, device="cuda")
         self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        self.nn_shift = 0  # NN strategy picked by cga_nn_autotune before timing
 
     def step(self, timed_events=True, batched=True):
         cga, ev = self.cga, self.ev
@@ -205,6 +206,8 @@ class LidarStep:
         rec(2)
         proj = cga.cga_project(world, "xy", allocator=None)
         rec(3)
+        if self.nn_shift:
+            cga.cga_nn_prepare(world, self.nn_shift)
         cga.cga_nn_sort_queries(world, self.d_q, self.order)
         rec(4)
         cga.cga_nn_query_ordered(world, self.d_q, self.order, self.idx, self.d2)
@@ -242,6 +245,9 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # NN strategy by measurement on a 64k sample of this workload's queries
+    P.step(timed_events=False)
+    P.nn_shift, nn_tune = cga.cga_nn_autotune(P.last[2], P.d_q[:65536].contiguous())
     for _ in range(args.warmup):
         P.step()
     torch.cuda.synchronize()
@@ -318,6 +324,7 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
                   "value": round(pts / (float(np.mean(plain_ms)) / 1e3) / 1e6, 3),
                   "note": "one call per sweep build and per merge (the step above batches "
                           "the 10 builds and each merge-tree level into one launch set)"},
+        "nn_autotune": {"chosen_shift": P.nn_shift, "sample_ms": nn_tune},
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s": round(t_wall, 3),
@@ -355,7 +362,7 @@ def run_single(args, world_size, local_rank, torch, cga, which):
                     "halves, merge, xy/xz/yz projections, 8M NN (4M on-surface + 4M uniform), "
                     "decode")
         n_points = 30_000_000
-        coarse_shift = 2  # two-level NN search: coarse cells of 4 voxels
+        coarse_shift = 0  # NN strategy: set by cga_nn_autotune below
     m = q.shape[0]
     order = torch.empty(m, dtype=torch.int64, device="cuda")
     idx = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -383,6 +390,11 @@ def run_single(args, world_size, local_rank, torch, cga, which):
         state["last"] = (a, b, mg, pr)
 
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+    # NN strategy by measurement on a 64k sample mixing both query halves
+    step()
+    sample = q[torch.randperm(m, device="cuda", generator=torch.Generator("cuda").manual_seed(7))
+               [:65536]].contiguous()
+    coarse_shift, nn_tune = cga.cga_nn_autotune(state["last"][2], sample)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -418,6 +430,7 @@ def run_single(args, world_size, local_rank, torch, cga, which):
                          + a.info()["bytes"] + b.info()["bytes"]) / (ops[0] / 1e3) / 1e9, 1),
                     "merged_u": mi["u"], "merged_bytes": mi["bytes"], "raw_bytes": n_points * 12,
                     "peak_gbs": peak, "peak_source": peak_kind},
+        "nn_autotune": {"chosen_shift": coarse_shift, "sample_ms": nn_tune},
         "gpu_launches": int(launches), "clocks": clk})
     return out
 

@@ -157,6 +157,15 @@ int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
  * a's allocator and is released with a.  Stream-ordered. */
 int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream);
 
+/* Pick the NN search strategy for `a` by measurement: run the m sample queries
+ * d_q (device; a few tens of thousands representative queries suffice) with
+ * the fine search alone and with coarse companions of 4, 8, 16 and 32 voxels,
+ * keep the fastest (it stays prepared on `a`), and report its shift (0 = fine
+ * search alone).  times_ms (NULL or 5 floats) receives each candidate's time,
+ * -1 for a shift the grid cannot take.  Waits for the timings. */
+int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shift,
+                    float* times_ms, void* stream);
+
 /* The two halves of cga_nn_query, for callers that reuse one query order or
  * time the search on its own.  cga_nn_sort_queries writes m 64-bit keys
  * (30-bit Morton code of the query's grid voxel << 32 | query index), sorted

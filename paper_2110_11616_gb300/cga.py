@@ -38,7 +38,7 @@ EXPORTS = (
     "cga_pipeline_view_xy", "cga_pipeline_free", "cga_nn_query_noalloc",
     "cga_server_create", "cga_server_submit", "cga_server_poll", "cga_server_drain",
     "cga_server_free", "cga_now_ns", "cga_nn_sort_queries", "cga_nn_query_ordered",
-    "cga_nn_prepare",
+    "cga_nn_prepare", "cga_nn_autotune",
 )
 
 
@@ -643,3 +643,19 @@ def cga_nn_prepare(a: Cga, shift: int, stream=None):
     lib.cga_nn_prepare.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
     _check(lib.cga_nn_prepare(a.ptr, shift, _stream(stream)), "cga_nn_prepare")
     return a
+
+
+def cga_nn_autotune(a: Cga, sample_queries, stream=None):
+    """Measure the NN strategies on a query sample; keep the fastest on `a`.
+    Returns (shift, {shift: ms})."""
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_nn_autotune.argtypes = [P, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32),
+                                    P, P]
+    _dev_f32(sample_queries, "cga_nn_autotune")
+    shift = ctypes.c_uint32()
+    times = (ctypes.c_float * 5)()
+    _check(lib.cga_nn_autotune(a.ptr, P(sample_queries.data_ptr()), sample_queries.numel() // 3,
+                               ctypes.byref(shift), times, _stream(stream)), "cga_nn_autotune")
+    cands = (0, 2, 3, 4, 5)
+    return shift.value, {c: float(t) for c, t in zip(cands, times) if t >= 0}

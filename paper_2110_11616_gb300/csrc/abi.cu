@@ -477,6 +477,56 @@ int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream) {
   return CGA_OK;
 }
 
+int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shift,
+                    float* times_ms, void* stream) {
+  if (a == nullptr || a->view || chosen_shift == nullptr || m == 0 || d_q == nullptr ||
+      m > libcga::kNnMaxQueries) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  void* out = dalloc(A, (size_t)m * 12 + 256, s);
+  if (out == nullptr) return CGA_ERR_OOM;
+  uint32_t* idx = static_cast<uint32_t*>(out);
+  uint64_t* d2 = reinterpret_cast<uint64_t*>(static_cast<char*>(out) + align_up((size_t)m * 4));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = cuda_rc(cudaEventCreate(&e0));
+  if (rc == CGA_OK) rc = cuda_rc(cudaEventCreate(&e1));
+  // candidates: the fine search alone, then coarse cells of 4..32 voxels
+  const uint32_t cand[] = {0, 2, 3, 4, 5};
+  float best_ms = 0.0f;
+  uint32_t best_shift = 0;
+  bool have = false;
+  for (int k = 0; k < 5 && rc == CGA_OK; ++k) {
+    const uint32_t sh = cand[k];
+    if (sh >= a->grid.bits || sh > 8) {
+      if (times_ms) times_ms[k] = -1.0f;
+      continue;
+    }
+    rc = cga_nn_prepare(a, sh, stream);
+    if (rc == CGA_OK) rc = cga_nn_query(a, d_q, m, idx, d2, stream);  // warm-up
+    if (rc == CGA_OK) rc = cuda_rc(cudaEventRecord(e0, s));
+    if (rc == CGA_OK) rc = cga_nn_query(a, d_q, m, idx, d2, stream);
+    if (rc == CGA_OK) rc = cuda_rc(cudaEventRecord(e1, s));
+    if (rc == CGA_OK) rc = cuda_rc(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    if (rc == CGA_OK) rc = cuda_rc(cudaEventElapsedTime(&ms, e0, e1));
+    if (rc != CGA_OK) break;
+    if (times_ms) times_ms[k] = ms;
+    if (!have || ms < best_ms) {
+      best_ms = ms;
+      best_shift = sh;
+      have = true;
+    }
+  }
+  if (rc == CGA_OK) rc = cga_nn_prepare(a, best_shift, stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dfree(A, a->has_alloc, out, s);
+  if (rc == CGA_OK) *chosen_shift = best_shift;
+  return rc;
+}
+
 int cga_nn_sort_queries(const cga_t* a, const float* d_q, uint64_t m, uint64_t* d_order,
                         void* stream) {
   if (a == nullptr || (m > 0 && (d_q == nullptr || d_order == nullptr))) return CGA_ERR_INVALID_ARG;

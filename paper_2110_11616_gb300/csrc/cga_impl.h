@@ -192,7 +192,10 @@ cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
                                cudaStream_t stream);
 cudaError_t run_nn_search(const NnSeg& seg, const unsigned long long* order, cudaStream_t stream);
 // Run with the tables on the device (capturable: memsets and kernels only).
-cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream);
+// any_coarse: some segment carries a coarse companion (selects the kernel
+// compiled with the two-level search).
+cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream,
+                          bool any_coarse = false);
 
 // For each slab k of the coarse CGA c (cells of 2^shift voxels), xs[k] = first
 // index of a's X_index whose x >> shift equals c's X_index[k]; xs[h_c] = h_a.

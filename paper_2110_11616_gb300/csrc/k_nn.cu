@@ -314,6 +314,9 @@ __device__ __forceinline__ void search_two_level(const NnSeg& sg, long long qx, 
   }
 }
 
+// COARSE: compiled with the two-level search (used when a segment carries a
+// coarse companion); the fine-only instantiation keeps fewer registers.
+template <bool COARSE>
 __global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs, int S,
                                                  NnSeg inline_seg, uint32_t total_slots,
                                                  const unsigned long long* __restrict__ order,
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs,
     const uint32_t cqy = (uint32_t)min(max(qy, 0ll), top);
     const uint32_t cqz = (uint32_t)min(max(qz, 0ll), top);
     Best best{~0ull, ~0ull, 0xffffffffu};
-    if (sg.has_coarse) {
+    if (COARSE && sg.has_coarse) {
       search_two_level(sg, qx, qy, qz, cqx, cqy, cqz, lane, best);
     } else {
       search_fine(a, h, qx, qy, qz, cqx, cqy, cqz, lane, best);
@@ -417,11 +420,17 @@ cudaError_t nn_upload_one(const NnSeg& h_seg, const NnTables& t, cudaStream_t st
 
 static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
                           uint32_t total_tiles, const unsigned long long* order,
-                          const unsigned int* order_err, cudaStream_t stream) {
+                          const unsigned int* order_err, bool coarse, cudaStream_t stream) {
   const uint32_t total_slots = total_tiles * (uint32_t)kTile;
   const uint32_t blocks =
       std::min<uint32_t>((total_slots + 7) / 8, (uint32_t)device_sm_count() * 8);
-  k_nn_warp<<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order, order_err);
+  if (coarse) {
+    k_nn_warp<true><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
+                                                order_err);
+  } else {
+    k_nn_warp<false><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
+                                                 order_err);
+  }
   count_launch(1);
 }
 
@@ -439,11 +448,12 @@ cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
 
 cudaError_t run_nn_search(const NnSeg& seg, const unsigned long long* order, cudaStream_t stream) {
   if (seg.m == 0) return cudaSuccess;
-  launch_search(nullptr, 1, seg, seg.num_tiles, order, nullptr, stream);
+  launch_search(nullptr, 1, seg, seg.num_tiles, order, nullptr, seg.has_coarse != 0, stream);
   return cudaGetLastError();
 }
 
-cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream) {
+cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream,
+                          bool any_coarse) {
   if (total_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(t.err, 0, sizeof(Header), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(t.sort.hist, 0, t.sort.zero_bytes, stream);
@@ -455,7 +465,8 @@ cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaSt
   if (e != cudaSuccess) return e;
   // four passes leave the sorted keys in keys0
   launch_search(t.segs, S, NnSeg{}, total_tiles,
-                static_cast<const unsigned long long*>(t.sort.keys0), &t.err->err, stream);
+                static_cast<const unsigned long long*>(t.sort.keys0), &t.err->err, any_coarse,
+                stream);
   return cudaGetLastError();
 }
 
@@ -464,13 +475,16 @@ cudaError_t run_nn(const NnSeg* h_segs, int S, uint32_t total_tiles, void* scrat
   if (total_tiles == 0) return cudaSuccess;
   if (scratch == nullptr) {
     if (S != 1) return cudaErrorInvalidValue;
-    launch_search(nullptr, 1, h_segs[0], total_tiles, nullptr, nullptr, stream);
+    launch_search(nullptr, 1, h_segs[0], total_tiles, nullptr, nullptr,
+                  h_segs[0].has_coarse != 0, stream);
     return cudaGetLastError();
   }
   const NnTables t = nn_tables(scratch, total_tiles, S);
   const cudaError_t e = nn_upload(h_segs, S, t, stream);
   if (e != cudaSuccess) return e;
-  return run_nn_device(S, total_tiles, t, stream);
+  bool any_coarse = false;
+  for (int s = 0; s < S; ++s) any_coarse = any_coarse || h_segs[s].has_coarse != 0;
+  return run_nn_device(S, total_tiles, t, stream, any_coarse);
 }
 
 }  // namespace libcga

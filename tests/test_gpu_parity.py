@@ -309,3 +309,16 @@ def test_nn_two_level_parity(cg, orc, shift, kind):
     oi, od = orc.nn_window(oa, og, q)
     assert np.array_equal(d2.cpu().numpy().view(np.uint64), np.tile(od, 4))
     assert np.array_equal(idx.cpu().numpy().view(np.uint32), np.tile(oi, 4))
+
+
+def test_nn_autotune_keeps_results(cg, orc):
+    scene = synth.superellipsoid_scene(n_objects=10, seed=120, extent=100.0)
+    pts = synth.sample_surfaces(scene, 80_000, seed=121)
+    g, og = grids(cg, orc, [0.0] * 3, 100.0, 12)
+    a = cg.cga_build(dev(pts), g)
+    q = np.concatenate([synth.sample_surfaces(scene, 2000, seed=122),
+                        synth.uniform_queries(2000, 123, [0.0] * 3, 100.0)])
+    shift, times = cg.cga_nn_autotune(a, dev(q))
+    assert shift in times and min(times, key=times.get) == shift
+    assert set(times) == {0, 2, 3, 4, 5}
+    nn_check(cg, orc, a, orc.build(pts, og), og, q, brute=False)
