@@ -153,8 +153,12 @@ int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
  * each coarse x slab the index of its first fine slab.  Afterwards every NN
  * call on `a` searches the coarse cells first and refines only those whose
  * box lower bound can beat the best distance found so far (same results).
- * shift in 1..min(8, bits-1); shift 0 removes the companion.  Memory comes from
- * a's allocator and is released with a.  Stream-ordered. */
+ * Every call also builds (once) an x directory: for each x value v of the grid
+ * the index of the first X_index entry >= v -- the dense per-x table of
+ * G-Arrays (Sec. III) used only to start each query's slab walk in one lookup
+ * (4 * (2^bits + 1) bytes).
+ * shift in 1..min(8, bits-1); shift 0 keeps only the x directory (fine search).
+ * Memory comes from a's allocator and is released with a.  Stream-ordered. */
 int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream);
 
 /* Pick the NN search strategy for `a` by measurement: run the m sample queries

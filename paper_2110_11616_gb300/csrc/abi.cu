@@ -28,6 +28,10 @@ struct cga {
   Levels clv{};
   uint32_t* xs = nullptr;
   uint32_t cshift = 0;
+  uint32_t* cxdir = nullptr;  // x directory of the coarse companion (inside cmem)
+  // x directory of this CGA for NN (cga_nn_prepare): first X_index entry >= v
+  void* xdmem = nullptr;
+  uint32_t* xdir = nullptr;
 };
 
 struct cga2d {
@@ -196,17 +200,20 @@ cga* new_cga(const cga_grid& g, const cga_allocator* A, cudaStream_t s, uint64_t
 void release(cga* h) {
   if (h == nullptr || h->view) return;
   if (h->cmem != nullptr) dfree(&h->alloc, h->has_alloc, h->cmem, h->stream);
+  if (h->xdmem != nullptr) dfree(&h->alloc, h->has_alloc, h->xdmem, h->stream);
   dfree(&h->alloc, h->has_alloc, h->mem, h->stream);
   delete h;
 }
 
 // NN searches use the coarse companion when cga_nn_prepare built one.
 void attach_coarse(const cga* a, libcga::NnSeg& seg) {
+  seg.xdir = a->xdir;
   if (a->cmem == nullptr) return;
   seg.c = a->clv;
   seg.xs = a->xs;
   seg.shift = a->cshift;
   seg.has_coarse = 1;
+  seg.cxdir = a->cxdir;
 }
 
 }  // namespace
@@ -433,6 +440,18 @@ int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream) {
   if (a->cmem != nullptr) {
     dfree(A, a->has_alloc, a->cmem, a->stream);
     a->cmem = nullptr;
+    a->cxdir = nullptr;
+  }
+  if (a->xdmem == nullptr) {
+    void* xm = dalloc(A, ((size_t)pow2(a->grid.bits) + 1) * 4, s);
+    if (xm == nullptr) return CGA_ERR_OOM;
+    const int rc = cuda_rc(libcga::run_x_directory(a->lv, static_cast<uint32_t*>(xm), s));
+    if (rc != CGA_OK) {
+      dfree(A, a->has_alloc, xm, s);
+      return rc;
+    }
+    a->xdmem = xm;
+    a->xdir = static_cast<uint32_t*>(xm);
   }
   if (shift == 0) return CGA_OK;
   const uint32_t bc = a->grid.bits - shift;
@@ -440,10 +459,12 @@ int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream) {
   const uint64_t cap1 = std::min<uint64_t>(cap, pow2(2 * bc));
   const uint64_t cap2 = std::min<uint64_t>(cap, pow2(bc));
   const size_t lb = levels_bytes(cap, cap1, cap2, 3);
-  void* mem = dalloc(A, lb + align_up((cap2 + 1) * 4), s);
+  const size_t xsb = align_up((cap2 + 1) * 4);
+  void* mem = dalloc(A, lb + xsb + align_up(((size_t)pow2(bc) + 1) * 4), s);
   if (mem == nullptr) return CGA_ERR_OOM;
   const Levels clv = levels_carve(mem, bc, cap, cap1, cap2, 3);
   uint32_t* xs = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb);
+  uint32_t* cxdir = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb + xsb);
   libcga::SortSeg seg{};
   seg.src = a->lv;
   seg.plane = 3;
@@ -463,6 +484,7 @@ int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream) {
     const libcga::SortScratch sc = libcga::sort_scratch_carve(scratch, keys, tiles, 1, key64);
     cudaError_t e = libcga::run_sort_pipeline(&seg, 1, tiles, seg.passes, key64, sc, s);
     if (e == cudaSuccess) e = libcga::run_coarse_slab_index(a->lv, clv, shift, xs, s);
+    if (e == cudaSuccess) e = libcga::run_x_directory(clv, cxdir, s);
     rc = cuda_rc(e);
     dfree(A, a->has_alloc, scratch, s);
   }
@@ -474,6 +496,7 @@ int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream) {
   a->clv = clv;
   a->xs = xs;
   a->cshift = shift;
+  a->cxdir = cxdir;
   return CGA_OK;
 }
 

@@ -159,6 +159,10 @@ struct NnSeg {
   const uint32_t* xs;
   uint32_t shift;
   uint32_t has_coarse;
+  // optional x directories (built by cga_nn_prepare): for every x value v of
+  // the fine (coarse) grid, the index of the first X_index entry >= v
+  const uint32_t* xdir;
+  const uint32_t* cxdir;
   float scale;
   float off[3];
   const float* q;
@@ -201,6 +205,9 @@ cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaSt
 // index of a's X_index whose x >> shift equals c's X_index[k]; xs[h_c] = h_a.
 cudaError_t run_coarse_slab_index(const Levels& a, const Levels& c, uint32_t shift, uint32_t* xs,
                                   cudaStream_t stream);
+
+// xdir[v] = first index of a's X_index with value >= v, for v in [0, 2^bits].
+cudaError_t run_x_directory(const Levels& a, uint32_t* xdir, cudaStream_t stream);
 
 int device_sm_count();
 

@@ -137,11 +137,12 @@ __device__ __forceinline__ void visit_column(const Levels& a, uint32_t c, unsign
 }
 
 // Window search over the fine CGA alone (one warp, 16 slabs per side per round).
-__device__ __forceinline__ void search_fine(const Levels& a, uint32_t h, long long qx, long long qy,
-                                            long long qz, uint32_t cqx, uint32_t cqy, uint32_t cqz,
+__device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdir, uint32_t h,
+                                            long long qx, long long qy, long long qz,
+                                            uint32_t cqx, uint32_t cqy, uint32_t cqz,
                                             uint32_t lane, Best& best) {
   const uint32_t b = a.bits;
-  const uint32_t xr0 = lower_bound_u16(a.idx2, 0, h, cqx);
+  const uint32_t xr0 = xdir != nullptr ? __ldg(xdir + cqx) : lower_bound_u16(a.idx2, 0, h, cqx);
   const bool right = (lane & 1u) == 0u;
   for (uint32_t r = 0;; ++r) {
     const long long k = (long long)r * 16 + (lane >> 1);
@@ -259,7 +260,8 @@ __device__ __forceinline__ void search_two_level(const NnSeg& sg, long long qx, 
   const Levels& c = sg.c;
   const uint32_t L = sg.shift, s = 1u << L;
   const uint32_t hc = (uint32_t)c.hdr->cnt[2];
-  const uint32_t xr0 = lower_bound_u16(c.idx2, 0, hc, cqx >> L);
+  const uint32_t xr0 = sg.cxdir != nullptr ? __ldg(sg.cxdir + (cqx >> L))
+                                            : lower_bound_u16(c.idx2, 0, hc, cqx >> L);
   const uint32_t cqy_c = cqy >> L;
   const bool right = (lane & 1u) == 0u;
   for (uint32_t r = 0;; ++r) {
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs,
     if (COARSE && sg.has_coarse) {
       search_two_level(sg, qx, qy, qz, cqx, cqy, cqz, lane, best);
     } else {
-      search_fine(a, h, qx, qy, qz, cqx, cqy, cqz, lane, best);
+      search_fine(a, sg.xdir, h, qx, qy, qz, cqx, cqy, cqz, lane, best);
     }
     if (lane == 0) {
       sg.idx[j] = best.idx;

@@ -258,6 +258,18 @@ __global__ void k_coarse_slab_index(Levels a, Levels c, uint32_t shift, uint32_t
   }
 }
 
+// ------------------------------------------------------------ x directory
+// The dense per-x-value table of G-Arrays (Sec. III), here only as a lookup
+// accelerator: xdir[v] = number of stored x values below v.
+__global__ void k_x_directory(Levels a, uint32_t* xdir) {
+  const uint32_t h = (uint32_t)a.hdr->cnt[2];
+  const uint32_t n = 1u << a.bits;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += stride) {
+    xdir[v] = lower_bound_u16(a.idx2, 0, h, v);
+  }
+}
+
 // ------------------------------------------------------------- projection xy
 __device__ __forceinline__ void project_xy_body(const Levels& a, const Levels& o, uint32_t t,
                                                 uint32_t stride) {
@@ -364,6 +376,15 @@ cudaError_t run_coarse_slab_index(const Levels& a, const Levels& c, uint32_t shi
   const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
                                                        (uint64_t)device_sm_count() * 8);
   k_coarse_slab_index<<<blocks, 256, 0, stream>>>(a, c, shift, xs);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t run_x_directory(const Levels& a, uint32_t* xdir, cudaStream_t stream) {
+  const uint64_t n = (1ull << a.bits) + 1;
+  const unsigned blocks = (unsigned)std::min<uint64_t>((n + 255) / 256,
+                                                       (uint64_t)device_sm_count() * 8);
+  k_x_directory<<<blocks, 256, 0, stream>>>(a, xdir);
   count_launch(1);
   return cudaGetLastError();
 }
