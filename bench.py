@@ -151,6 +151,21 @@ def timed(torch, fn, flush=None, tag=0.0):
     return s.elapsed_time(e)
 
 
+def max_over_ranks(ms: float, world_size: int, torch, dist, device) -> float:
+    """The slowest rank's time: replicas run in parallel, so the job takes as
+    long as its slowest GPU (weak scaling, no data-path collective)."""
+    if world_size <= 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(points_per_step: int, steps: int, world_size: int, max_ms: float) -> float:
+    """Whole-job Mpts/s: every rank processes its own replica of the workload."""
+    return points_per_step * steps * world_size / (max_ms / 1e3) / 1e6
+
+
 def base_line(args, world_size, metric, value, unit, ms_per_step, config, data):
     return {"metric": metric, "value": round(value, 4), "unit": unit, "n_gpus": world_size,
             "steps": args.steps, "warmup": args.warmup,
@@ -278,13 +293,9 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
     merge_bytes = sum(a.info()["bytes"] + b.info()["bytes"] + m.info()["bytes"]
                       for a, b, m in merges)
     op = op_ms / args.steps
-    max_total = total_ms
-    if world_size > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        max_total = float(t.item())
+    max_total = max_over_ranks(total_ms, world_size, torch, dist, "cuda")
     pts = P.n_points
-    value = pts * args.steps * world_size / (max_total / 1e3) / 1e6
+    value = job_value(pts, args.steps, world_size, max_total)
     e2e_val = pts * world_size / (float(np.mean(e2e_ms)) / 1e3) / 1e6
     peak, peak_kind = measured_peaks()
     # dominant kernel: the NN search (one launch of k_nn_warp per step, timed

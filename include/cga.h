@@ -361,6 +361,14 @@ int cga2d_download(const cga2d_t* p, uint16_t* h_U_index, uint32_t* h_U_pointer,
 void cga_free(cga_t* a);
 void cga2d_free(cga2d_t* p);
 
+/* Self-test of the bounded device waits: queues one radix-sort tile whose
+ * predecessor tile never runs, so the look-back word it waits on is never
+ * published.  The wait gives up after its limit (about one second), records
+ * the timeout and the kernel returns; *observed receives the status the tile
+ * recorded (CGA_ERR_TIMEOUT when the bound works) and the device stays usable.
+ * Waits for the result. */
+int cga_selftest_wait_timeout(void* stream, int* observed);
+
 /* Number of kernels this library has queued since the process started (all
  * devices, all threads); a cheap counter for launch accounting. */
 uint64_t cga_kernel_launches(void);

@@ -38,7 +38,7 @@ EXPORTS = (
     "cga_pipeline_view_xy", "cga_pipeline_free", "cga_nn_query_noalloc",
     "cga_server_create", "cga_server_submit", "cga_server_poll", "cga_server_drain",
     "cga_server_free", "cga_now_ns", "cga_nn_sort_queries", "cga_nn_query_ordered",
-    "cga_nn_prepare", "cga_nn_autotune",
+    "cga_nn_prepare", "cga_nn_autotune", "cga_selftest_wait_timeout",
 )
 
 
@@ -659,3 +659,13 @@ def cga_nn_autotune(a: Cga, sample_queries, stream=None):
                                ctypes.byref(shift), times, _stream(stream)), "cga_nn_autotune")
     cands = (0, 2, 3, 4, 5)
     return shift.value, {c: float(t) for c, t in zip(cands, times) if t >= 0}
+
+
+def selftest_wait_timeout(stream=None) -> int:
+    """Run the bounded-wait self-test; returns the status the device recorded."""
+    lib = load()
+    lib.cga_selftest_wait_timeout.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
+    obs = ctypes.c_int(0)
+    _check(lib.cga_selftest_wait_timeout(_stream(stream), ctypes.byref(obs)),
+           "cga_selftest_wait_timeout")
+    return obs.value

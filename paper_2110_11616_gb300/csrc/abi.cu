@@ -1264,6 +1264,23 @@ void cga_pipeline_free(cga_pipeline_t* p) {
   delete p;
 }
 
+int cga_selftest_wait_timeout(void* stream, int* observed) {
+  if (observed == nullptr) return CGA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* scratch = dalloc(nullptr, libcga::wait_selftest_bytes(), s);
+  if (scratch == nullptr) return CGA_ERR_OOM;
+  cudaError_t e = libcga::run_wait_selftest(scratch, s);
+  Header hd{};
+  if (e == cudaSuccess) {
+    e = cudaMemcpyAsync(&hd, scratch, sizeof(Header), cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(nullptr, false, scratch, s);
+  if (e != cudaSuccess) return cuda_rc(e);
+  *observed = err_from_bits(hd.err);
+  return CGA_OK;
+}
+
 uint64_t cga_kernel_launches(void) { return libcga::g_launches.load(std::memory_order_relaxed); }
 
 const char* cga_strerror(int code) {

@@ -209,6 +209,10 @@ cudaError_t run_coarse_slab_index(const Levels& a, const Levels& c, uint32_t shi
 // xdir[v] = first index of a's X_index with value >= v, for v in [0, 2^bits].
 cudaError_t run_x_directory(const Levels& a, uint32_t* xdir, cudaStream_t stream);
 
+// Self-test of the bounded device waits (see cga_selftest_wait_timeout).
+size_t wait_selftest_bytes();
+cudaError_t run_wait_selftest(void* scratch, cudaStream_t stream);
+
 int device_sm_count();
 
 // Launch accounting (cga_kernel_launches).

@@ -27,11 +27,20 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // one second per word
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Decoupled look-back over the tiles (first, tile) of one segment.  Each
 // tile publishes one 32-bit word per counter: 2 flag bits + a 30-bit value.
 // Tile ids are handed out in launch order by an atomic counter, so every
 // predecessor is already resident and the wait ends; it is still bounded: after
-// kSpinLimit polls of one word the error bit is set and the wait stops.
+// kSpinLimit polls, or one second, on one word the error bit is set and the
+// wait stops.
 __device__ __forceinline__ uint32_t lookback(const uint32_t* look, uint32_t stride, uint32_t tile,
                                              uint32_t first, unsigned int* err) {
   uint32_t excl = 0;
@@ -40,10 +49,13 @@ __device__ __forceinline__ uint32_t lookback(const uint32_t* look, uint32_t stri
     --j;
     uint32_t v;
     uint32_t spins = 0;
+    unsigned long long t0 = 0;
     while (true) {
       v = ld_relaxed(look + (size_t)j * stride);
       if (v & (kFlagAgg | kFlagInc)) break;
-      if (++spins > kSpinLimit) {
+      ++spins;
+      if (spins == 32) t0 = global_ns();
+      if (spins > kSpinLimit || (spins > 32 && (spins & 63) == 0 && global_ns() - t0 > kWaitLimitNs)) {
         atomicOr(err, kErrTimeout);
         return excl;
       }

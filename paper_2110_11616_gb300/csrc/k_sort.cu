@@ -407,6 +407,37 @@ cudaError_t run_sort_device(int S, uint32_t total_tiles, uint32_t max_passes, bo
                : launch_pipeline<uint32_t>(S, total_tiles, max_passes, levels, sc, stream);
 }
 
+size_t wait_selftest_bytes() {
+  return align_up(sizeof(Header)) + sort_scratch_bytes(2 * kTile, 2, 1, true);
+}
+
+// One radix-pass tile that draws tile id 1 of a two-tile segment whose tile 0
+// never runs: its look-back word for tile 0 is never published, so the wait
+// must give up on its own and record kErrTimeout in *hdr.
+cudaError_t run_wait_selftest(void* scratch, cudaStream_t stream) {
+  const size_t bytes = wait_selftest_bytes();
+  Header* hdr = static_cast<Header*>(scratch);
+  const SortScratch sc = sort_scratch_carve(static_cast<char*>(scratch) + align_up(sizeof(Header)),
+                                            2 * kTile, 2, 1, true);
+  SortSeg seg{};
+  seg.n_host = 2 * kTile;
+  seg.passes = 1;
+  seg.num_tiles = 2;
+  seg.out.hdr = hdr;
+  const uint32_t first_id = 1;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, bytes, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sc.segs, &seg, sizeof(SortSeg), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) {
+    e = cudaMemcpyAsync(sc.counters, &first_id, sizeof(uint32_t), cudaMemcpyHostToDevice, stream);
+  }
+  if (e != cudaSuccess) return e;
+  k_onesweep<unsigned long long><<<1, kThreads, 0, stream>>>(
+      sc.segs, 1, 0, static_cast<const unsigned long long*>(sc.keys0),
+      static_cast<unsigned long long*>(sc.keys1), sc.hist, sc.look, sc.counters);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
 cudaError_t run_sort_pipeline(const SortSeg* h_segs, int S, uint32_t total_tiles,
                               uint32_t max_passes, bool key64, const SortScratch& sc,
                               cudaStream_t stream) {
