@@ -167,17 +167,40 @@ __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restric
   flush(cur);
 }
 
-// One LSD pass over digit `pass` of every segment that still needs it.
-template <typename K>
-__global__ void __launch_bounds__(kThreads) k_onesweep(const SortSeg* __restrict__ segs, int S,
-                                                       int pass, const K* __restrict__ in,
-                                                       K* __restrict__ out,
-                                                       const uint32_t* __restrict__ hist,
-                                                       uint32_t* look, uint32_t* counter) {
+// Exclusive scan across a block of TH threads (s_warp: TH/32 words).
+template <int TH, typename T>
+__device__ __forceinline__ T block_scan_th(T v, T& total, T* s_warp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  T before = 0, tot = 0;
+#pragma unroll
+  for (int i = 0; i < TH / 32; ++i) {
+    const T x = s_warp[i];
+    if (i < w) before += x;
+    tot += x;
+  }
+  __syncthreads();
+  total = tot;
+  return before + inc - v;
+}
+
+// One LSD pass over digit `pass` of every segment that still needs it.  A
+// tile of kTile keys is TH threads x kTile/TH keys (warp-striped); threads
+// tid < kRadix own one digit each for the per-digit steps.
+template <typename K, int TH>
+__global__ void __launch_bounds__(TH) k_onesweep(const SortSeg* __restrict__ segs, int S,
+                                                 int pass, const K* __restrict__ in,
+                                                 K* __restrict__ out,
+                                                 const uint32_t* __restrict__ hist,
+                                                 uint32_t* look, uint32_t* counter) {
+  constexpr int IT = kTile / TH, WARPS = TH / 32;
+  static_assert(IT * TH == kTile && TH >= kRadix, "tile shape");
   __shared__ K s_keys[kTile];
-  __shared__ uint32_t s_wh[kWarps][kRadix];
+  __shared__ uint16_t s_wh[WARPS][kRadix];  // per-warp digit counts, then warp offsets
   __shared__ uint32_t s_off[kRadix];
-  __shared__ uint32_t s_scan[kWarps];
+  __shared__ uint32_t s_scan[WARPS];
   __shared__ uint32_t s_tile;
   __shared__ int s_seg;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -186,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const SortSeg* __restrict
     s_tile = t;
     s_seg = find_seg(segs, S, t);
   }
-  for (int i = tid; i < kWarps * kRadix; i += kThreads) (&s_wh[0][0])[i] = 0;
+  for (int i = tid; i < WARPS * kRadix; i += TH) (&s_wh[0][0])[i] = 0;
   __syncthreads();
   const uint32_t t = s_tile;
   const int s = s_seg;
@@ -200,69 +223,79 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const SortSeg* __restrict
   const K* src = in + sg.key_base + start;
   const int shift = (int)sg.bit0 + pass * kRadixBits;
 
-  K k[kItems];
-  uint32_t dg[kItems], rk[kItems];
+  K k[IT];
+  uint32_t dg[IT], rk[IT];
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
-    const uint32_t e = (uint32_t)(w * 32 * kItems + i * 32 + lane);
+  for (int i = 0; i < IT; ++i) {
+    const uint32_t e = (uint32_t)(w * 32 * IT + i * 32 + lane);
     const bool v = e < cnt;
     k[i] = v ? src[e] : (K)0;
     dg[i] = v ? ((uint32_t)(k[i] >> shift) & (kRadix - 1)) : 0xffffffffu;
   }
   // warp-level ranking: lanes holding the same digit form one match group
-  uint32_t* wh = s_wh[w];
+  uint16_t* wh = s_wh[w];
   const uint32_t ltm = lanemask_lt();
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
+  for (int i = 0; i < IT; ++i) {
     const uint32_t d = dg[i];
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t base = (d < (uint32_t)kRadix) ? wh[d] : 0u;
     __syncwarp();
-    if (d < (uint32_t)kRadix && lane == __ffs(peers) - 1) wh[d] = base + __popc(peers);
+    if (d < (uint32_t)kRadix && lane == __ffs(peers) - 1) wh[d] = (uint16_t)(base + __popc(peers));
     __syncwarp();
     rk[i] = base + __popc(peers & ltm);
   }
   __syncthreads();
-  // per digit (thread == digit): warp offsets, tile count, publish
+  // per digit (thread tid == digit): warp offsets, tile count, publish
   const int d = tid;
+  const bool owner = tid < kRadix;
   uint32_t tile_cnt = 0;
-  for (int x = 0; x < kWarps; ++x) {
-    const uint32_t v = s_wh[x][d];
-    s_wh[x][d] = tile_cnt;
-    tile_cnt += v;
-  }
   uint32_t* my = look + (size_t)t * kRadix + d;
-  st_relaxed(my, (lt == 0 ? kFlagInc : kFlagAgg) | tile_cnt);
+  if (owner) {
+    for (int x = 0; x < WARPS; ++x) {
+      const uint32_t v = s_wh[x][d];
+      s_wh[x][d] = (uint16_t)tile_cnt;
+      tile_cnt += v;
+    }
+    st_relaxed(my, (lt == 0 ? kFlagInc : kFlagAgg) | tile_cnt);
+  }
   uint32_t tot;
-  const uint32_t bin_start = block_excl_scan(tile_cnt, tot, s_scan);
-  const uint32_t hv = hist[((size_t)s * kMaxPasses + pass) * kRadix + d];
-  const uint32_t dbase = block_excl_scan(hv, tot, s_scan);
-  s_off[d] = bin_start;
+  const uint32_t bin_start = block_scan_th<TH>(owner ? tile_cnt : 0u, tot, s_scan);
+  const uint32_t hv = owner ? hist[((size_t)s * kMaxPasses + pass) * kRadix + d] : 0u;
+  const uint32_t dbase = block_scan_th<TH>(hv, tot, s_scan);
+  if (owner) s_off[d] = bin_start;
   __syncthreads();
   bool bad = false;
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
+  for (int i = 0; i < IT; ++i) {
     if (dg[i] < (uint32_t)kRadix) {
       const uint32_t pos = s_off[dg[i]] + s_wh[w][dg[i]] + rk[i];
       if (pos < (uint32_t)kTile) s_keys[pos] = k[i]; else bad = true;
     }
   }
   uint32_t excl = 0;
-  if (lt > 0) {
+  if (owner && lt > 0) {
     excl = lookback(look + d, kRadix, t, sg.tile_base, &sg.out.hdr->err);
     st_relaxed(my, kFlagInc | ((excl + tile_cnt) & kValMask));
   }
   __syncthreads();
-  s_off[d] = dbase + excl - bin_start;
+  if (owner) s_off[d] = dbase + excl - bin_start;
   __syncthreads();
   K* dst = out + sg.key_base;
-  for (uint32_t e = tid; e < cnt; e += kThreads) {
+  for (uint32_t e = tid; e < cnt; e += TH) {
     const K key = s_keys[e];
     const uint32_t pos = s_off[(uint32_t)(key >> shift) & (kRadix - 1)] + e;
     if (pos < n) dst[pos] = key; else bad = true;
   }
   if (bad) atomicOr(&sg.out.hdr->err, kErrInternal);
 }
+
+// Threads per radix-pass block: 512 x 8 keys per tile (half the registers per
+// thread and twice the resident warps of 256 x 16).
+template <typename K>
+struct PassShape {
+  static constexpr int kTh = 512;
+};
 
 template <typename K, int LEVELS>
 __global__ void __launch_bounds__(kThreads) k_compact(const SortSeg* __restrict__ segs, int S,
@@ -357,7 +390,7 @@ static void launch_passes(int S, uint32_t total_tiles, uint32_t max_passes, cons
   for (uint32_t p = 0; p < max_passes; ++p) {
     const K* in = (p & 1) ? k1 : k0;
     K* out = (p & 1) ? k0 : k1;
-    k_onesweep<K><<<total_tiles, kThreads, 0, stream>>>(
+    k_onesweep<K, PassShape<K>::kTh><<<total_tiles, PassShape<K>::kTh, 0, stream>>>(
         sc.segs, S, (int)p, in, out, sc.hist, sc.look + (size_t)p * total_tiles * kRadix,
         sc.counters + p);
   }
@@ -431,7 +464,8 @@ cudaError_t run_wait_selftest(void* scratch, cudaStream_t stream) {
     e = cudaMemcpyAsync(sc.counters, &first_id, sizeof(uint32_t), cudaMemcpyHostToDevice, stream);
   }
   if (e != cudaSuccess) return e;
-  k_onesweep<unsigned long long><<<1, kThreads, 0, stream>>>(
+  k_onesweep<unsigned long long, PassShape<unsigned long long>::kTh>
+      <<<1, PassShape<unsigned long long>::kTh, 0, stream>>>(
       sc.segs, 1, 0, static_cast<const unsigned long long*>(sc.keys0),
       static_cast<unsigned long long*>(sc.keys1), sc.hist, sc.look, sc.counters);
   count_launch(1);
