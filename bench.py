@@ -193,7 +193,7 @@ class LidarStep:
         self.n_points = sum(len(s) for s in scene.sweeps)
         self.dec = torch.empty((self.n_points, 3), dtype=torch.int32, device="cuda")
         self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
-        self.nn_shift = 0  # NN strategy picked by cga_nn_autotune before timing
+        self.nn_shift = ()  # NN coarse levels picked by cga_nn_autotune before timing
 
     def step(self, timed_events=True, batched=True):
         cga, ev = self.cga, self.ev
@@ -221,8 +221,7 @@ class LidarStep:
         rec(2)
         proj = cga.cga_project(world, "xy", allocator=None)
         rec(3)
-        if self.nn_shift:
-            cga.cga_nn_prepare(world, self.nn_shift)
+        cga.cga_nn_prepare(world, self.nn_shift)
         cga.cga_nn_sort_queries(world, self.d_q, self.order)
         rec(4)
         cga.cga_nn_query_ordered(world, self.d_q, self.order, self.idx, self.d2)
@@ -248,6 +247,13 @@ class LidarStep:
 
     def bytes_out(self):
         return self.h_idx.numel() * 4 + self.h_d2.numel() * 8
+
+
+def tune_record(shifts, times):
+    """cga_nn_autotune's choice and sample timings for the JSON line."""
+    name = lambda c: ",".join(map(str, c)) if c else "fine"
+    return {"chosen_coarse_shifts": list(shifts),
+            "sample_ms": {name(c): round(t, 4) for c, t in times.items()}}
 
 
 def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
@@ -335,7 +341,7 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
                   "value": round(pts / (float(np.mean(plain_ms)) / 1e3) / 1e6, 3),
                   "note": "one call per sweep build and per merge (the step above batches "
                           "the 10 builds and each merge-tree level into one launch set)"},
-        "nn_autotune": {"chosen_shift": P.nn_shift, "sample_ms": nn_tune},
+        "nn_autotune": tune_record(P.nn_shift, nn_tune),
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s": round(t_wall, 3),
@@ -357,7 +363,7 @@ def run_single(args, world_size, local_rank, torch, cga, which):
         workload = ("plain: 100k uniform pts + rigidly transformed twin, b=10; batched build of "
                     "both, merge, xy projection, 10k uniform NN, decode")
         n_points = 200_000
-        coarse_shift = 0
+        coarse_shift = ()
     else:
         scene = synth_gpu.surface_scene(3)
         full = synth_gpu.sample_scene(scene, 30_000_000, seed=4)
@@ -373,7 +379,7 @@ def run_single(args, world_size, local_rank, torch, cga, which):
                     "halves, merge, xy/xz/yz projections, 8M NN (4M on-surface + 4M uniform), "
                     "decode")
         n_points = 30_000_000
-        coarse_shift = 0  # NN strategy: set by cga_nn_autotune below
+        coarse_shift = ()  # NN coarse levels: set by cga_nn_autotune below
     m = q.shape[0]
     order = torch.empty(m, dtype=torch.int64, device="cuda")
     idx = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -390,8 +396,7 @@ def run_single(args, world_size, local_rank, torch, cga, which):
         ev[2].record()
         pr = cga.cga_project_batch([mg] * len(planes), planes, allocator=None)
         ev[3].record()
-        if coarse_shift:
-            cga.cga_nn_prepare(mg, coarse_shift)
+        cga.cga_nn_prepare(mg, coarse_shift)
         cga.cga_nn_sort_queries(mg, q, order)
         ev[4].record()
         cga.cga_nn_query_ordered(mg, q, order, idx, d2)
@@ -441,7 +446,7 @@ def run_single(args, world_size, local_rank, torch, cga, which):
                          + a.info()["bytes"] + b.info()["bytes"]) / (ops[0] / 1e3) / 1e9, 1),
                     "merged_u": mi["u"], "merged_bytes": mi["bytes"], "raw_bytes": n_points * 12,
                     "peak_gbs": peak, "peak_source": peak_kind},
-        "nn_autotune": {"chosen_shift": coarse_shift, "sample_ms": nn_tune},
+        "nn_autotune": tune_record(coarse_shift, nn_tune),
         "gpu_launches": int(launches), "clocks": clk})
     return out
 

@@ -148,26 +148,42 @@ int cga_project(const cga_t* a, int plane, const cga_allocator* A, void* stream,
 int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
                  uint64_t* d_dist2, void* stream);
 
-/* Build (once per CGA) the coarse companion that lets NN search skip empty
- * space: the CGA of the occupied cells of 2^shift voxels per axis, plus for
- * each coarse x slab the index of its first fine slab.  Afterwards every NN
- * call on `a` searches the coarse cells first and refines only those whose
- * box lower bound can beat the best distance found so far (same results).
- * Every call also builds (once) an x directory: for each x value v of the grid
+#define CGA_NN_MAX_LEVELS 2          /* coarse levels cga_nn_prepare_levels takes */
+#define CGA_NN_MAX_SHIFT 12          /* largest coarse cell: 2^12 voxels per axis */
+#define CGA_NN_AUTOTUNE_CANDIDATES 9 /* strategies cga_nn_autotune measures */
+
+/* Build (once per CGA) the coarse levels that let NN search skip empty space.
+ * Level k is the CGA of the occupied cells of 2^shifts[k] voxels per axis
+ * (built by re-keying the next finer level), with, for each of its x slabs,
+ * the index of the first slab of the next finer level inside it.  Afterwards
+ * every NN call on `a` walks the coarsest level's cells outward from the query
+ * and refines, level by level down to the CGA's own columns, only the cells
+ * whose box lower bound can beat the best distance found so far (the results
+ * do not change: the exact nearest voxel, ties to the smaller key).
+ * Every call also builds (once) an x directory per level: for each x value v
  * the index of the first X_index entry >= v -- the dense per-x table of
- * G-Arrays (Sec. III) used only to start each query's slab walk in one lookup
- * (4 * (2^bits + 1) bytes).
- * shift in 1..min(8, bits-1); shift 0 keeps only the x directory (fine search).
- * Memory comes from a's allocator and is released with a.  Stream-ordered. */
+ * G-Arrays (Sec. III) used only to start a slab walk in one lookup
+ * (4 * (2^bits + 1) bytes for the CGA itself).
+ * shifts: count (0..CGA_NN_MAX_LEVELS) strictly increasing values in
+ * 1..min(CGA_NN_MAX_SHIFT, bits-1), host memory; count 0 drops the coarse
+ * levels and keeps only the x directory (fine search).  Replaces any earlier
+ * preparation.  Memory comes from a's allocator and is released with a.
+ * Stream-ordered.  CGA_ERR_INVALID_ARG for a view handle or bad shifts. */
+int cga_nn_prepare_levels(cga_t* a, const uint32_t* shifts, uint32_t count, void* stream);
+
+/* cga_nn_prepare_levels with one coarse level of 2^shift voxel cells, or none
+ * when shift is 0. */
 int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream);
 
 /* Pick the NN search strategy for `a` by measurement: run the m sample queries
- * d_q (device; a few tens of thousands representative queries suffice) with
- * the fine search alone and with coarse companions of 4, 8, 16 and 32 voxels,
- * keep the fastest (it stays prepared on `a`), and report its shift (0 = fine
- * search alone).  times_ms (NULL or 5 floats) receives each candidate's time,
- * -1 for a shift the grid cannot take.  Waits for the timings. */
-int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shift,
+ * d_q (device; a few tens of thousands representative queries suffice) under
+ * each candidate and keep the fastest prepared on `a`.  Candidates, in order
+ * (coarse shifts): none (fine search alone); 2; 3; 4; 5; 2,5; 3,6; 3,7; 4,8.
+ * chosen_shifts (CGA_NN_MAX_LEVELS entries) receives the winner's shifts, 0
+ * for an unused level.  times_ms (NULL or CGA_NN_AUTOTUNE_CANDIDATES floats)
+ * receives each candidate's time, -1 for one the grid cannot take.  Waits for
+ * the timings. */
+int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shifts,
                     float* times_ms, void* stream);
 
 /* The two halves of cga_nn_query, for callers that reuse one query order or

@@ -38,7 +38,8 @@ EXPORTS = (
     "cga_pipeline_view_xy", "cga_pipeline_free", "cga_nn_query_noalloc",
     "cga_server_create", "cga_server_submit", "cga_server_poll", "cga_server_drain",
     "cga_server_free", "cga_now_ns", "cga_nn_sort_queries", "cga_nn_query_ordered",
-    "cga_nn_prepare", "cga_nn_autotune", "cga_selftest_wait_timeout",
+    "cga_nn_prepare", "cga_nn_prepare_levels", "cga_nn_autotune",
+    "cga_selftest_wait_timeout",
 )
 
 
@@ -637,28 +638,40 @@ def cga_nn_query_ordered(a: Cga, queries, order, idx, dist2, stream=None):
     return idx, dist2
 
 
-def cga_nn_prepare(a: Cga, shift: int, stream=None):
-    """Build the coarse companion (cells of 2^shift voxels) used by NN search."""
+NN_MAX_LEVELS = 2
+# cga_nn_autotune's candidates, in the order of its timings (coarse shifts)
+NN_AUTOTUNE_CANDIDATES = ((), (2,), (3,), (4,), (5,), (2, 5), (3, 6), (3, 7), (4, 8))
+
+
+def cga_nn_prepare(a: Cga, shifts=(), stream=None):
+    """Build the coarse levels (cells of 2^shift voxels, finest first) used by
+    NN search; an int is one level, 0 or () none (x directory only)."""
+    if isinstance(shifts, int):
+        shifts = () if shifts == 0 else (shifts,)
+    shifts = tuple(int(v) for v in shifts)
     lib = load()
-    lib.cga_nn_prepare.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
-    _check(lib.cga_nn_prepare(a.ptr, shift, _stream(stream)), "cga_nn_prepare")
+    lib.cga_nn_prepare_levels.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32),
+                                          ctypes.c_uint32, ctypes.c_void_p]
+    arr = (ctypes.c_uint32 * max(1, len(shifts)))(*shifts)
+    _check(lib.cga_nn_prepare_levels(a.ptr, arr, len(shifts), _stream(stream)),
+           "cga_nn_prepare_levels")
     return a
 
 
 def cga_nn_autotune(a: Cga, sample_queries, stream=None):
     """Measure the NN strategies on a query sample; keep the fastest on `a`.
-    Returns (shift, {shift: ms})."""
+    Returns (shifts, {shifts: ms}) with shifts a tuple of coarse shifts."""
     lib = load()
     P = ctypes.c_void_p
     lib.cga_nn_autotune.argtypes = [P, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32),
                                     P, P]
     _dev_f32(sample_queries, "cga_nn_autotune")
-    shift = ctypes.c_uint32()
-    times = (ctypes.c_float * 5)()
+    chosen = (ctypes.c_uint32 * NN_MAX_LEVELS)()
+    times = (ctypes.c_float * len(NN_AUTOTUNE_CANDIDATES))()
     _check(lib.cga_nn_autotune(a.ptr, P(sample_queries.data_ptr()), sample_queries.numel() // 3,
-                               ctypes.byref(shift), times, _stream(stream)), "cga_nn_autotune")
-    cands = (0, 2, 3, 4, 5)
-    return shift.value, {c: float(t) for c, t in zip(cands, times) if t >= 0}
+                               chosen, times, _stream(stream)), "cga_nn_autotune")
+    shifts = tuple(int(v) for v in chosen if v != 0)
+    return shifts, {c: float(t) for c, t in zip(NN_AUTOTUNE_CANDIDATES, times) if t >= 0}
 
 
 def selftest_wait_timeout(stream=None) -> int:

@@ -23,12 +23,15 @@ struct cga {
   bool has_alloc;
   cudaStream_t stream;
   bool view = false;  // arrays owned by a pipeline; cga_free leaves them alone
-  // coarse companion for NN (cga_nn_prepare): CGA of occupied 2^cshift cells
-  void* cmem = nullptr;
-  Levels clv{};
-  uint32_t* xs = nullptr;
-  uint32_t cshift = 0;
-  uint32_t* cxdir = nullptr;  // x directory of the coarse companion (inside cmem)
+  // coarse levels for NN (cga_nn_prepare_levels): level k is the CGA of the
+  // occupied cells of 2^cshift[k] voxels, with its slab index into the next
+  // finer level and its own x directory (all inside cmem[k])
+  uint32_t ncoarse = 0;
+  void* cmem[libcga::kMaxCoarse] = {};
+  Levels clv[libcga::kMaxCoarse] = {};
+  uint32_t* xs[libcga::kMaxCoarse] = {};
+  uint32_t cshift[libcga::kMaxCoarse] = {};
+  uint32_t* cxdir[libcga::kMaxCoarse] = {};
   // x directory of this CGA for NN (cga_nn_prepare): first X_index entry >= v
   void* xdmem = nullptr;
   uint32_t* xdir = nullptr;
@@ -199,21 +202,24 @@ cga* new_cga(const cga_grid& g, const cga_allocator* A, cudaStream_t s, uint64_t
 
 void release(cga* h) {
   if (h == nullptr || h->view) return;
-  if (h->cmem != nullptr) dfree(&h->alloc, h->has_alloc, h->cmem, h->stream);
+  for (int k = 0; k < libcga::kMaxCoarse; ++k) {
+    if (h->cmem[k] != nullptr) dfree(&h->alloc, h->has_alloc, h->cmem[k], h->stream);
+  }
   if (h->xdmem != nullptr) dfree(&h->alloc, h->has_alloc, h->xdmem, h->stream);
   dfree(&h->alloc, h->has_alloc, h->mem, h->stream);
   delete h;
 }
 
-// NN searches use the coarse companion when cga_nn_prepare built one.
+// NN searches use the coarse levels that cga_nn_prepare_levels built.
 void attach_coarse(const cga* a, libcga::NnSeg& seg) {
   seg.xdir = a->xdir;
-  if (a->cmem == nullptr) return;
-  seg.c = a->clv;
-  seg.xs = a->xs;
-  seg.shift = a->cshift;
-  seg.has_coarse = 1;
-  seg.cxdir = a->cxdir;
+  seg.ncoarse = a->ncoarse;
+  for (uint32_t k = 0; k < a->ncoarse; ++k) {
+    seg.c[k] = a->clv[k];
+    seg.xs[k] = a->xs[k];
+    seg.shift[k] = a->cshift[k];
+    seg.cxdir[k] = a->cxdir[k];
+  }
 }
 
 }  // namespace
@@ -433,15 +439,92 @@ libcga::NnSeg nn_segment(const cga_t* a, const float* d_q, uint64_t m, uint32_t*
 
 }  // namespace
 
-int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream) {
-  if (a == nullptr || a->view || shift >= a->grid.bits || shift > 8) return CGA_ERR_INVALID_ARG;
+namespace {
+
+static_assert(libcga::kMaxCoarse == CGA_NN_MAX_LEVELS, "coarse level count");
+
+void drop_coarse(cga* a) {
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  for (int k = 0; k < libcga::kMaxCoarse; ++k) {
+    if (a->cmem[k] != nullptr) dfree(A, a->has_alloc, a->cmem[k], a->stream);
+    a->cmem[k] = nullptr;
+    a->clv[k] = Levels{};
+    a->xs[k] = nullptr;
+    a->cxdir[k] = nullptr;
+    a->cshift[k] = 0;
+  }
+  a->ncoarse = 0;
+}
+
+// Coarse level k of `a`: re-key the next finer level (the CGA itself for
+// k = 0) by cells of 2^(shift - finer shift) of its voxels, then index each
+// coarse slab's first finer slab and build the level's x directory.
+int build_coarse_level(cga* a, int k, uint32_t shift, cudaStream_t s) {
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  const Levels& fine = k == 0 ? a->lv : a->clv[k - 1];
+  const uint32_t dsh = shift - (k == 0 ? 0u : a->cshift[k - 1]);
+  const uint32_t bc = a->grid.bits - shift;
+  const uint64_t cap = std::min<uint64_t>(fine.cap, pow2(3 * bc));
+  const uint64_t cap1 = std::min<uint64_t>(cap, pow2(2 * bc));
+  const uint64_t cap2 = std::min<uint64_t>(cap, pow2(bc));
+  const size_t lb = levels_bytes(cap, cap1, cap2, 3);
+  const size_t xsb = align_up((cap2 + 1) * 4);
+  void* mem = dalloc(A, lb + xsb + align_up(((size_t)pow2(bc) + 1) * 4), s);
+  if (mem == nullptr) return CGA_ERR_OOM;
+  const Levels clv = levels_carve(mem, bc, cap, cap1, cap2, 3);
+  uint32_t* xs = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb);
+  uint32_t* cxdir = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb + xsb);
+  libcga::SortSeg seg{};
+  seg.src = fine;
+  seg.plane = 3;
+  seg.shift = dsh;
+  seg.from_cga = 1;
+  seg.bits = bc;
+  seg.key_bits = 3 * bc;
+  seg.passes = (seg.key_bits + libcga::kRadixBits - 1) / libcga::kRadixBits;
+  seg.num_tiles = (uint32_t)((fine.cap + libcga::kTile - 1) / libcga::kTile);
+  seg.out = clv;
+  const bool key64 = seg.key_bits > 32;
+  const uint32_t tiles = seg.num_tiles;
+  const uint64_t keys = (uint64_t)tiles * libcga::kTile;
+  void* scratch = dalloc(A, libcga::sort_scratch_bytes(keys, tiles, 1, key64), s);
+  int rc = CGA_ERR_OOM;
+  if (scratch != nullptr) {
+    const libcga::SortScratch sc = libcga::sort_scratch_carve(scratch, keys, tiles, 1, key64);
+    cudaError_t e = libcga::run_sort_pipeline(&seg, 1, tiles, seg.passes, key64, sc, s);
+    if (e == cudaSuccess) e = libcga::run_coarse_slab_index(fine, clv, dsh, xs, s);
+    if (e == cudaSuccess) e = libcga::run_x_directory(clv, cxdir, s);
+    rc = cuda_rc(e);
+    dfree(A, a->has_alloc, scratch, s);
+  }
+  if (rc != CGA_OK) {
+    dfree(A, a->has_alloc, mem, s);
+    return rc;
+  }
+  a->cmem[k] = mem;
+  a->clv[k] = clv;
+  a->xs[k] = xs;
+  a->cshift[k] = shift;
+  a->cxdir[k] = cxdir;
+  a->ncoarse = (uint32_t)k + 1;
+  return CGA_OK;
+}
+
+}  // namespace
+
+int cga_nn_prepare_levels(cga_t* a, const uint32_t* shifts, uint32_t count, void* stream) {
+  if (a == nullptr || a->view || count > CGA_NN_MAX_LEVELS || (count > 0 && shifts == nullptr)) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  for (uint32_t k = 0; k < count; ++k) {
+    if (shifts[k] < 1 || shifts[k] >= a->grid.bits || shifts[k] > CGA_NN_MAX_SHIFT ||
+        (k > 0 && shifts[k] <= shifts[k - 1])) {
+      return CGA_ERR_INVALID_ARG;
+    }
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
-  if (a->cmem != nullptr) {
-    dfree(A, a->has_alloc, a->cmem, a->stream);
-    a->cmem = nullptr;
-    a->cxdir = nullptr;
-  }
+  drop_coarse(a);
   if (a->xdmem == nullptr) {
     void* xm = dalloc(A, ((size_t)pow2(a->grid.bits) + 1) * 4, s);
     if (xm == nullptr) return CGA_ERR_OOM;
@@ -453,56 +536,23 @@ int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream) {
     a->xdmem = xm;
     a->xdir = static_cast<uint32_t*>(xm);
   }
-  if (shift == 0) return CGA_OK;
-  const uint32_t bc = a->grid.bits - shift;
-  const uint64_t cap = std::min<uint64_t>(a->lv.cap, pow2(3 * bc));
-  const uint64_t cap1 = std::min<uint64_t>(cap, pow2(2 * bc));
-  const uint64_t cap2 = std::min<uint64_t>(cap, pow2(bc));
-  const size_t lb = levels_bytes(cap, cap1, cap2, 3);
-  const size_t xsb = align_up((cap2 + 1) * 4);
-  void* mem = dalloc(A, lb + xsb + align_up(((size_t)pow2(bc) + 1) * 4), s);
-  if (mem == nullptr) return CGA_ERR_OOM;
-  const Levels clv = levels_carve(mem, bc, cap, cap1, cap2, 3);
-  uint32_t* xs = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb);
-  uint32_t* cxdir = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb + xsb);
-  libcga::SortSeg seg{};
-  seg.src = a->lv;
-  seg.plane = 3;
-  seg.shift = shift;
-  seg.from_cga = 1;
-  seg.bits = bc;
-  seg.key_bits = 3 * bc;
-  seg.passes = (seg.key_bits + libcga::kRadixBits - 1) / libcga::kRadixBits;
-  seg.num_tiles = (uint32_t)((a->lv.cap + libcga::kTile - 1) / libcga::kTile);
-  seg.out = clv;
-  const bool key64 = seg.key_bits > 32;
-  const uint32_t tiles = seg.num_tiles;
-  const uint64_t keys = (uint64_t)tiles * libcga::kTile;
-  void* scratch = dalloc(A, libcga::sort_scratch_bytes(keys, tiles, 1, key64), s);
-  int rc = CGA_ERR_OOM;
-  if (scratch != nullptr) {
-    const libcga::SortScratch sc = libcga::sort_scratch_carve(scratch, keys, tiles, 1, key64);
-    cudaError_t e = libcga::run_sort_pipeline(&seg, 1, tiles, seg.passes, key64, sc, s);
-    if (e == cudaSuccess) e = libcga::run_coarse_slab_index(a->lv, clv, shift, xs, s);
-    if (e == cudaSuccess) e = libcga::run_x_directory(clv, cxdir, s);
-    rc = cuda_rc(e);
-    dfree(A, a->has_alloc, scratch, s);
+  for (uint32_t k = 0; k < count; ++k) {
+    const int rc = build_coarse_level(a, (int)k, shifts[k], s);
+    if (rc != CGA_OK) {
+      drop_coarse(a);
+      return rc;
+    }
   }
-  if (rc != CGA_OK) {
-    dfree(A, a->has_alloc, mem, s);
-    return rc;
-  }
-  a->cmem = mem;
-  a->clv = clv;
-  a->xs = xs;
-  a->cshift = shift;
-  a->cxdir = cxdir;
   return CGA_OK;
 }
 
-int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shift,
+int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream) {
+  return cga_nn_prepare_levels(a, &shift, shift == 0 ? 0u : 1u, stream);
+}
+
+int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shifts,
                     float* times_ms, void* stream) {
-  if (a == nullptr || a->view || chosen_shift == nullptr || m == 0 || d_q == nullptr ||
+  if (a == nullptr || a->view || chosen_shifts == nullptr || m == 0 || d_q == nullptr ||
       m > libcga::kNnMaxQueries) {
     return CGA_ERR_INVALID_ARG;
   }
@@ -515,18 +565,20 @@ int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shi
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = cuda_rc(cudaEventCreate(&e0));
   if (rc == CGA_OK) rc = cuda_rc(cudaEventCreate(&e1));
-  // candidates: the fine search alone, then coarse cells of 4..32 voxels
-  const uint32_t cand[] = {0, 2, 3, 4, 5};
+  // candidates (coarse shifts, 0 = unused): the fine search alone, one coarse
+  // level of 4..32 voxel cells, two coarse levels
+  static const uint32_t cand[CGA_NN_AUTOTUNE_CANDIDATES][CGA_NN_MAX_LEVELS] = {
+      {0, 0}, {2, 0}, {3, 0}, {4, 0}, {5, 0}, {2, 5}, {3, 6}, {3, 7}, {4, 8}};
   float best_ms = 0.0f;
-  uint32_t best_shift = 0;
+  int best = 0;
   bool have = false;
-  for (int k = 0; k < 5 && rc == CGA_OK; ++k) {
-    const uint32_t sh = cand[k];
-    if (sh >= a->grid.bits || sh > 8) {
+  for (int k = 0; k < CGA_NN_AUTOTUNE_CANDIDATES && rc == CGA_OK; ++k) {
+    const uint32_t count = cand[k][0] == 0 ? 0u : (cand[k][1] == 0 ? 1u : 2u);
+    if (count > 0 && cand[k][count - 1] >= a->grid.bits) {
       if (times_ms) times_ms[k] = -1.0f;
       continue;
     }
-    rc = cga_nn_prepare(a, sh, stream);
+    rc = cga_nn_prepare_levels(a, cand[k], count, stream);
     if (rc == CGA_OK) rc = cga_nn_query(a, d_q, m, idx, d2, stream);  // warm-up
     if (rc == CGA_OK) rc = cuda_rc(cudaEventRecord(e0, s));
     if (rc == CGA_OK) rc = cga_nn_query(a, d_q, m, idx, d2, stream);
@@ -538,15 +590,18 @@ int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shi
     if (times_ms) times_ms[k] = ms;
     if (!have || ms < best_ms) {
       best_ms = ms;
-      best_shift = sh;
+      best = k;
       have = true;
     }
   }
-  if (rc == CGA_OK) rc = cga_nn_prepare(a, best_shift, stream);
+  const uint32_t best_count = cand[best][0] == 0 ? 0u : (cand[best][1] == 0 ? 1u : 2u);
+  if (rc == CGA_OK) rc = cga_nn_prepare_levels(a, cand[best], best_count, stream);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   dfree(A, a->has_alloc, out, s);
-  if (rc == CGA_OK) *chosen_shift = best_shift;
+  if (rc == CGA_OK) {
+    for (int k = 0; k < CGA_NN_MAX_LEVELS; ++k) chosen_shifts[k] = cand[best][k];
+  }
   return rc;
 }
 

@@ -150,19 +150,22 @@ cudaError_t run_project_xy_device(const ProjPair* d_pairs, int S, uint64_t max_c
 // of whole tiles (segment s owns slots [tile_base*kTile, (tile_base +
 // num_tiles)*kTile)).  With scratch the queries are first sorted along a
 // Morton curve so that neighbouring warps search neighbouring space.
+constexpr int kMaxCoarse = 2;
+
 struct NnSeg {
   Levels a;
-  // optional coarse companion of `a` (has_coarse): the CGA of the occupied
-  // cells of 2^shift voxels per axis, and for each coarse slab the index of
-  // its first fine slab in a's X_index (xs[h_coarse] = h_fine)
-  Levels c;
-  const uint32_t* xs;
-  uint32_t shift;
-  uint32_t has_coarse;
-  // optional x directories (built by cga_nn_prepare): for every x value v of
-  // the fine (coarse) grid, the index of the first X_index entry >= v
+  // optional coarse levels (ncoarse = 0..kMaxCoarse, coarsest last): c[k] is
+  // the CGA of the occupied cells of 2^shift[k] voxels per axis, xs[k][j] the
+  // first slab of the next finer level inside c[k]'s slab j (one past the last
+  // slab = that level's slab count), cxdir[k] c[k]'s x directory (or null)
+  Levels c[kMaxCoarse];
+  const uint32_t* xs[kMaxCoarse];
+  uint32_t shift[kMaxCoarse];
+  const uint32_t* cxdir[kMaxCoarse];
+  uint32_t ncoarse;
+  // optional x directory of `a` (cga_nn_prepare): for every x value v of the
+  // grid, the index of the first X_index entry >= v
   const uint32_t* xdir;
-  const uint32_t* cxdir;
   float scale;
   float off[3];
   const float* q;
@@ -196,10 +199,10 @@ cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
                                cudaStream_t stream);
 cudaError_t run_nn_search(const NnSeg& seg, const unsigned long long* order, cudaStream_t stream);
 // Run with the tables on the device (capturable: memsets and kernels only).
-// any_coarse: some segment carries a coarse companion (selects the kernel
-// compiled with the two-level search).
+// max_coarse: the most coarse levels any segment carries (selects the kernel
+// instantiation).
 cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream,
-                          bool any_coarse = false);
+                          uint32_t max_coarse = 0);
 
 // For each slab k of the coarse CGA c (cells of 2^shift voxels), xs[k] = first
 // index of a's X_index whose x >> shift equals c's X_index[k]; xs[h_c] = h_a.

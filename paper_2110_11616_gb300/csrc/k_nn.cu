@@ -204,73 +204,195 @@ __device__ __forceinline__ unsigned long long interval_dist(long long q, uint32_
   return q < l ? (unsigned long long)(l - q) : (q > hi ? (unsigned long long)(q - hi) : 0ull);
 }
 
-// Every fine column inside the footprint of one coarse column: fine slabs
-// [fx0, fx1) (the fine slabs of the coarse slab), y in [ylo, ylo + s).
-__device__ __forceinline__ void refine_footprint(const Levels& a, uint32_t fx0, uint32_t fx1,
-                                                 uint32_t ylo, uint32_t s, long long qx,
-                                                 long long qy, long long qz, uint32_t cqz,
-                                                 Best& best) {
-  const uint32_t b = a.bits;
-  for (uint32_t xi = fx0; xi < fx1; ++xi) {
-    const uint32_t x = __ldg(a.idx2 + xi);
-    const unsigned long long dx = absdiff(x, qx);
-    const unsigned long long dx2 = dx * dx;
-    if (dx2 > best.d2) continue;
-    const uint32_t ys = __ldg(a.ptr2 + xi), ye = __ldg(a.ptr2 + xi + 1);
-    const unsigned long long kx = (unsigned long long)x << (2 * b);
-    for (uint32_t c = lower_bound_u16(a.idx1, ys, ye, ylo); c < ye; ++c) {
-      const uint32_t y = __ldg(a.idx1 + c);
-      if (y >= ylo + s) break;
-      const unsigned long long dy = absdiff(y, qy);
-      const unsigned long long dxy = dx2 + dy * dy;
-      if (dxy > best.d2) continue;
-      visit_column(a, c, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+// A query in voxel units: unclamped (x, y, z) for distances, clamped
+// (cx, cy, cz) inside the grid for searches.
+struct Qry {
+  long long x, y, z;
+  uint32_t cx, cy, cz;
+};
+
+// Level K of a segment: 0 is the CGA itself, 1..ncoarse its coarse levels.
+template <int K>
+__device__ __forceinline__ const Levels& level(const NnSeg& sg) {
+  if constexpr (K == 0) return sg.a; else return sg.c[K - 1];
+}
+template <int K>
+__device__ __forceinline__ uint32_t level_shift(const NnSeg& sg) {
+  if constexpr (K == 0) return 0u; else return sg.shift[K - 1];
+}
+
+template <int K>
+__device__ void visit_cell_column(const NnSeg& sg, uint32_t c, uint32_t cy,
+                                  unsigned long long dxl2, unsigned long long dyl2, uint32_t cx0,
+                                  uint32_t cx1, const Qry& q, Best& best);
+
+// The slabs [x0, x1) of level K restricted to columns with y in [ylo, ylo +
+// ysz) (level-K units): slabs are taken nearest to the query first, and the
+// columns of a slab nearest first, so the best distance tightens early and
+// each walk stops once its lower bound exceeds it.  Level 0 visits the fine
+// columns; a column of a coarse level is refined one level down.
+template <int K>
+__device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t ylo,
+                             uint32_t ysz, const Qry& q, Best& best) {
+  const Levels& L = level<K>(sg);
+  const uint32_t sh = level_shift<K>(sg), cell = 1u << sh;
+  const uint32_t qyc = q.cy >> sh;
+  const uint32_t split = lower_bound_u16(L.idx2, x0, x1, q.cx >> sh);
+  long long r = split, l = (long long)split - 1;
+  while (true) {
+    const bool hr = r < (long long)x1, hl = l >= (long long)x0;
+    if (!hr && !hl) break;
+    const uint32_t vr = hr ? (uint32_t)__ldg(L.idx2 + r) : 0u;
+    const uint32_t vl = hl ? (uint32_t)__ldg(L.idx2 + l) : 0u;
+    const unsigned long long er = hr ? interval_dist(q.x, vr << sh, cell) : ~0ull;
+    const unsigned long long el = hl ? interval_dist(q.x, vl << sh, cell) : ~0ull;
+    const bool gr = hr && (!hl || er <= el);
+    const unsigned long long dxl = gr ? er : el;
+    const unsigned long long dxl2 = dxl * dxl;
+    if (dxl2 > best.d2) break;
+    const uint32_t xi = (uint32_t)(gr ? r : l), xv = gr ? vr : vl;
+    if (gr) ++r; else --l;
+    const uint32_t ys = __ldg(L.ptr2 + xi), ye = __ldg(L.ptr2 + xi + 1);
+    // columns [c0, c1) of this slab lie in the y range; cs: the first at or
+    // beyond the query's row
+    const uint32_t c0 = lower_bound_u16(L.idx1, ys, ye, ylo);
+    uint32_t cs = c0, c1 = c0;
+    while (c1 < ye) {
+      const uint32_t y = __ldg(L.idx1 + c1);
+      if (y >= ylo + ysz) break;
+      if (y < qyc) cs = c1 + 1;
+      ++c1;
+    }
+    if (c0 == c1) continue;
+    uint32_t fx0 = 0, fx1 = 0;
+    if constexpr (K > 0) {
+      fx0 = __ldg(sg.xs[K - 1] + xi);
+      fx1 = __ldg(sg.xs[K - 1] + xi + 1);
+    }
+    long long R = cs, Lc = (long long)cs - 1;
+    while (true) {
+      const bool hR = R < (long long)c1, hL = Lc >= (long long)c0;
+      if (!hR && !hL) break;
+      const uint32_t yR = hR ? (uint32_t)__ldg(L.idx1 + R) : 0u;
+      const uint32_t yL = hL ? (uint32_t)__ldg(L.idx1 + Lc) : 0u;
+      const unsigned long long eR = hR ? interval_dist(q.y, yR << sh, cell) : ~0ull;
+      const unsigned long long eL = hL ? interval_dist(q.y, yL << sh, cell) : ~0ull;
+      const bool gR = hR && (!hL || eR <= eL);
+      const unsigned long long dyl = gR ? eR : eL;
+      if (dxl2 + dyl * dyl > best.d2) break;
+      const uint32_t c = (uint32_t)(gR ? R : Lc), yv = gR ? yR : yL;
+      if (gR) ++R; else --Lc;
+      if constexpr (K == 0) {
+        const uint32_t b = L.bits;
+        visit_column(L, c, ((unsigned long long)xv << (2 * b)) | ((unsigned long long)yv << b),
+                     dxl2 + dyl * dyl, q.z, q.cz, best);
+      } else {
+        visit_cell_column<K>(sg, c, yv, dxl2, dyl * dyl, fx0, fx1, q, best);
+      }
     }
   }
 }
 
-// A coarse column (cx, cy): its nearest occupied coarse cell along z bounds
-// every point below it; refine the fine footprint only if that bound can beat
-// the best distance so far.
-__device__ __forceinline__ void visit_coarse_column(const NnSeg& sg, uint32_t cc, uint32_t cy,
-                                                    unsigned long long dxl2,
-                                                    unsigned long long dyl2, uint32_t fx0,
-                                                    uint32_t fx1, long long qx, long long qy,
-                                                    long long qz, uint32_t cqz, Best& best) {
-  if (dxl2 + dyl2 > best.d2) return;
-  const Levels& c = sg.c;
-  const uint32_t L = sg.shift, s = 1u << L;
-  const uint32_t zs = __ldg(c.ptr1 + cc), ze = __ldg(c.ptr1 + cc + 1);
-  const uint32_t zr = lower_bound_u16(c.idx0, zs, ze, cqz >> L);
+// Distance along z from the query to the nearest occupied cell of column c
+// of level K >= 1.
+template <int K>
+__device__ __forceinline__ unsigned long long cell_z_dist(const NnSeg& sg, uint32_t c,
+                                                          const Qry& q) {
+  const Levels& L = level<K>(sg);
+  const uint32_t sh = level_shift<K>(sg), cell = 1u << sh;
+  const uint32_t zs = __ldg(L.ptr1 + c), ze = __ldg(L.ptr1 + c + 1);
+  const uint32_t zr = lower_bound_u16(L.idx0, zs, ze, q.cz >> sh);
   unsigned long long dzl = ~0ull;
-  if (zr < ze) dzl = min(dzl, interval_dist(qz, (uint32_t)__ldg(c.idx0 + zr) << L, s));
-  if (zr > zs) dzl = min(dzl, interval_dist(qz, (uint32_t)__ldg(c.idx0 + zr - 1) << L, s));
-  if (dxl2 + dyl2 + dzl * dzl > best.d2) return;
-  refine_footprint(sg.a, fx0, fx1, cy << L, s, qx, qy, qz, cqz, best);
+  if (zr < ze) dzl = min(dzl, interval_dist(q.z, (uint32_t)__ldg(L.idx0 + zr) << sh, cell));
+  if (zr > zs) dzl = min(dzl, interval_dist(q.z, (uint32_t)__ldg(L.idx0 + zr - 1) << sh, cell));
+  return dzl;
 }
 
-// Two-level window search: the same round structure over the coarse CGA (the
-// occupied cells of 2^shift voxels), with box lower bounds deciding which
-// cells' fine footprints are searched.  A point lies in an occupied cell whose
-// bound never exceeds the point's distance, so pruning by "bound > best"
-// never drops a point at or below the final distance.
-__device__ __forceinline__ void search_two_level(const NnSeg& sg, long long qx, long long qy,
-                                                 long long qz, uint32_t cqx, uint32_t cqy,
-                                                 uint32_t cqz, uint32_t lane, Best& best) {
-  const Levels& c = sg.c;
-  const uint32_t L = sg.shift, s = 1u << L;
+// Column c (y = cy) of level K >= 1: its nearest occupied cells along z bound
+// every point below it; refine the column's footprint one level down (the
+// finer slabs [cx0, cx1), y range of the cell) only if that bound can beat the
+// best distance so far.
+template <int K>
+__device__ void visit_cell_column(const NnSeg& sg, uint32_t c, uint32_t cy,
+                                  unsigned long long dxl2, unsigned long long dyl2, uint32_t cx0,
+                                  uint32_t cx1, const Qry& q, Best& best) {
+  if (dxl2 + dyl2 > best.d2) return;
+  const unsigned long long dzl = cell_z_dist<K>(sg, c, q);
+  if (dxl2 + dyl2 + dzl * dzl > best.d2) return;
+  const uint32_t dsh = level_shift<K>(sg) - level_shift<K - 1>(sg);
+  refine_level<K - 1>(sg, cx0, cx1, cy << dsh, 1u << dsh, q, best);
+}
+
+// Window search whose rounds run over the coarsest level TOP (cells of
+// 2^shift voxels) with box lower bounds; surviving cells are refined level by
+// level down to the fine columns.  A point lies in an occupied cell at every
+// level whose bound never exceeds the point's distance, so pruning by
+// "bound > best" never drops a point at or below the final distance.
+template <int TOP>
+__device__ void search_levels(const NnSeg& sg, const Qry& q, uint32_t lane, Best& best) {
+  const Levels& c = level<TOP>(sg);
+  const uint32_t L = level_shift<TOP>(sg), s = 1u << L;
+  const uint32_t* xs = sg.xs[TOP - 1];
+  const uint32_t* cxdir = sg.cxdir[TOP - 1];
   const uint32_t hc = (uint32_t)c.hdr->cnt[2];
-  const uint32_t xr0 = sg.cxdir != nullptr ? __ldg(sg.cxdir + (cqx >> L))
-                                            : lower_bound_u16(c.idx2, 0, hc, cqx >> L);
-  const uint32_t cqy_c = cqy >> L;
+  const uint32_t xr0 = cxdir != nullptr ? __ldg(cxdir + (q.cx >> L))
+                                        : lower_bound_u16(c.idx2, 0, hc, q.cx >> L);
+  const uint32_t cqy_c = q.cy >> L;
   const bool right = (lane & 1u) == 0u;
+  {
+    // Seed: each lane bounds the two columns of one nearest slab that are
+    // nearest in y (box lower bound with z from the column's nearest cells);
+    // only the column with the least bound in the warp is refined, so the
+    // rounds below start from a real candidate instead of an infinite bound.
+    const long long slab = right ? (long long)xr0 + (lane >> 1) : (long long)xr0 - 1 - (lane >> 1);
+    unsigned long long lb = ~0ull, sdx2 = 0, sdy2 = 0;
+    uint32_t sc = 0, scy = 0, sfx0 = 0, sfx1 = 0;
+    if (slab >= 0 && slab < (long long)hc) {
+      const unsigned long long dxl = interval_dist(q.x, (uint32_t)__ldg(c.idx2 + slab) << L, s);
+      const uint32_t ys = __ldg(c.ptr2 + slab), ye = __ldg(c.ptr2 + slab + 1);
+      const uint32_t yr0 = lower_bound_u16(c.idx1, ys, ye, cqy_c);
+      sfx0 = __ldg(xs + slab);
+      sfx1 = __ldg(xs + slab + 1);
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const uint32_t cc = yr0 - (uint32_t)t;
+        if (t == 0 ? yr0 >= ye : yr0 <= ys) continue;
+        const uint32_t cy = __ldg(c.idx1 + cc);
+        const unsigned long long dyl = interval_dist(q.y, cy << L, s);
+        const unsigned long long dzl = cell_z_dist<TOP>(sg, cc, q);
+        const unsigned long long bnd = dxl * dxl + dyl * dyl + dzl * dzl;
+        if (bnd < lb) {
+          lb = bnd;
+          sc = cc;
+          scy = cy;
+          sdx2 = dxl * dxl;
+          sdy2 = dyl * dyl;
+        }
+      }
+    }
+    unsigned long long v = lb;
+    uint32_t win = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const uint32_t ol = __shfl_xor_sync(0xffffffffu, win, o);
+      if (ov < v || (ov == v && ol < win)) {
+        v = ov;
+        win = ol;
+      }
+    }
+    if (v != ~0ull && lane == win) {
+      visit_cell_column<TOP>(sg, sc, scy, sdx2, sdy2, sfx0, sfx1, q, best);
+    }
+    best.warp_min();
+  }
   for (uint32_t r = 0;; ++r) {
     const long long k = (long long)r * 16 + (lane >> 1);
     const long long slab = right ? (long long)xr0 + k : (long long)xr0 - 1 - k;
     const bool valid = slab >= 0 && slab < (long long)hc;
     unsigned long long dxl2 = ~0ull;
     if (valid) {
-      const unsigned long long dxl = interval_dist(qx, (uint32_t)__ldg(c.idx2 + slab) << L, s);
+      const unsigned long long dxl = interval_dist(q.x, (uint32_t)__ldg(c.idx2 + slab) << L, s);
       dxl2 = dxl * dxl;
     }
     const bool active = valid && dxl2 <= best.d2;
@@ -280,17 +402,17 @@ __device__ __forceinline__ void search_two_level(const NnSeg& sg, long long qx, 
       ys = __ldg(c.ptr2 + slab);
       ye = __ldg(c.ptr2 + slab + 1);
       yr0 = lower_bound_u16(c.idx1, ys, ye, cqy_c);
-      fx0 = __ldg(sg.xs + slab);
-      fx1 = __ldg(sg.xs + slab + 1);
+      fx0 = __ldg(xs + slab);
+      fx1 = __ldg(xs + slab + 1);
       if (yr0 < ye) {
         const uint32_t cy = __ldg(c.idx1 + yr0);
-        const unsigned long long dyl = interval_dist(qy, cy << L, s);
-        visit_coarse_column(sg, yr0, cy, dxl2, dyl * dyl, fx0, fx1, qx, qy, qz, cqz, best);
+        const unsigned long long dyl = interval_dist(q.y, cy << L, s);
+        visit_cell_column<TOP>(sg, yr0, cy, dxl2, dyl * dyl, fx0, fx1, q, best);
       }
       if (yr0 > ys) {
         const uint32_t cy = __ldg(c.idx1 + yr0 - 1);
-        const unsigned long long dyl = interval_dist(qy, cy << L, s);
-        visit_coarse_column(sg, yr0 - 1, cy, dxl2, dyl * dyl, fx0, fx1, qx, qy, qz, cqz, best);
+        const unsigned long long dyl = interval_dist(q.y, cy << L, s);
+        visit_cell_column<TOP>(sg, yr0 - 1, cy, dxl2, dyl * dyl, fx0, fx1, q, best);
       }
     }
     best.warp_min();
@@ -300,25 +422,24 @@ __device__ __forceinline__ void search_two_level(const NnSeg& sg, long long qx, 
         const bool hR = R2 < (long long)ye, hL = L2 >= (long long)ys;
         if (!hR && !hL) break;
         const unsigned long long eR =
-            hR ? interval_dist(qy, (uint32_t)__ldg(c.idx1 + R2) << L, s) : ~0ull;
+            hR ? interval_dist(q.y, (uint32_t)__ldg(c.idx1 + R2) << L, s) : ~0ull;
         const unsigned long long eL =
-            hL ? interval_dist(qy, (uint32_t)__ldg(c.idx1 + L2) << L, s) : ~0ull;
+            hL ? interval_dist(q.y, (uint32_t)__ldg(c.idx1 + L2) << L, s) : ~0ull;
         const bool gR = hR && (!hL || eR <= eL);
         const unsigned long long dyl = gR ? eR : eL;
         if (dxl2 + dyl * dyl > best.d2) break;
         const uint32_t cc = (uint32_t)(gR ? R2 : L2);
         if (gR) ++R2; else --L2;
-        visit_coarse_column(sg, cc, __ldg(c.idx1 + cc), dxl2, dyl * dyl, fx0, fx1, qx, qy, qz,
-                            cqz, best);
+        visit_cell_column<TOP>(sg, cc, __ldg(c.idx1 + cc), dxl2, dyl * dyl, fx0, fx1, q, best);
       }
     }
     best.warp_min();
   }
 }
 
-// COARSE: compiled with the two-level search (used when a segment carries a
-// coarse companion); the fine-only instantiation keeps fewer registers.
-template <bool COARSE>
+// NC: the most coarse levels any segment of the launch carries (0, 1 or 2);
+// the fine-only instantiation keeps fewer registers.
+template <int NC>
 __global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs, int S,
                                                  NnSeg inline_seg, uint32_t total_slots,
                                                  const unsigned long long* __restrict__ order,
@@ -354,8 +475,10 @@ __global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs,
     const uint32_t cqy = (uint32_t)min(max(qy, 0ll), top);
     const uint32_t cqz = (uint32_t)min(max(qz, 0ll), top);
     Best best{~0ull, ~0ull, 0xffffffffu};
-    if (COARSE && sg.has_coarse) {
-      search_two_level(sg, qx, qy, qz, cqx, cqy, cqz, lane, best);
+    if (NC >= 2 && sg.ncoarse >= 2) {
+      if constexpr (NC >= 2) search_levels<2>(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane, best);
+    } else if (NC >= 1 && sg.ncoarse >= 1) {
+      if constexpr (NC >= 1) search_levels<1>(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane, best);
     } else {
       search_fine(a, sg.xdir, h, qx, qy, qz, cqx, cqy, cqz, lane, best);
     }
@@ -422,16 +545,20 @@ cudaError_t nn_upload_one(const NnSeg& h_seg, const NnTables& t, cudaStream_t st
 
 static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
                           uint32_t total_tiles, const unsigned long long* order,
-                          const unsigned int* order_err, bool coarse, cudaStream_t stream) {
+                          const unsigned int* order_err, uint32_t ncoarse,
+                          cudaStream_t stream) {
   const uint32_t total_slots = total_tiles * (uint32_t)kTile;
   const uint32_t blocks =
       std::min<uint32_t>((total_slots + 7) / 8, (uint32_t)device_sm_count() * 8);
-  if (coarse) {
-    k_nn_warp<true><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
-                                                order_err);
+  if (ncoarse >= 2) {
+    k_nn_warp<2><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
+                                             order_err);
+  } else if (ncoarse == 1) {
+    k_nn_warp<1><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
+                                             order_err);
   } else {
-    k_nn_warp<false><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
-                                                 order_err);
+    k_nn_warp<0><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
+                                             order_err);
   }
   count_launch(1);
 }
@@ -450,12 +577,12 @@ cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
 
 cudaError_t run_nn_search(const NnSeg& seg, const unsigned long long* order, cudaStream_t stream) {
   if (seg.m == 0) return cudaSuccess;
-  launch_search(nullptr, 1, seg, seg.num_tiles, order, nullptr, seg.has_coarse != 0, stream);
+  launch_search(nullptr, 1, seg, seg.num_tiles, order, nullptr, seg.ncoarse, stream);
   return cudaGetLastError();
 }
 
 cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream,
-                          bool any_coarse) {
+                          uint32_t max_coarse) {
   if (total_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(t.err, 0, sizeof(Header), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(t.sort.hist, 0, t.sort.zero_bytes, stream);
@@ -467,7 +594,7 @@ cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaSt
   if (e != cudaSuccess) return e;
   // four passes leave the sorted keys in keys0
   launch_search(t.segs, S, NnSeg{}, total_tiles,
-                static_cast<const unsigned long long*>(t.sort.keys0), &t.err->err, any_coarse,
+                static_cast<const unsigned long long*>(t.sort.keys0), &t.err->err, max_coarse,
                 stream);
   return cudaGetLastError();
 }
@@ -477,16 +604,16 @@ cudaError_t run_nn(const NnSeg* h_segs, int S, uint32_t total_tiles, void* scrat
   if (total_tiles == 0) return cudaSuccess;
   if (scratch == nullptr) {
     if (S != 1) return cudaErrorInvalidValue;
-    launch_search(nullptr, 1, h_segs[0], total_tiles, nullptr, nullptr,
-                  h_segs[0].has_coarse != 0, stream);
+    launch_search(nullptr, 1, h_segs[0], total_tiles, nullptr, nullptr, h_segs[0].ncoarse,
+                  stream);
     return cudaGetLastError();
   }
   const NnTables t = nn_tables(scratch, total_tiles, S);
   const cudaError_t e = nn_upload(h_segs, S, t, stream);
   if (e != cudaSuccess) return e;
-  bool any_coarse = false;
-  for (int s = 0; s < S; ++s) any_coarse = any_coarse || h_segs[s].has_coarse != 0;
-  return run_nn_device(S, total_tiles, t, stream, any_coarse);
+  uint32_t max_coarse = 0;
+  for (int s = 0; s < S; ++s) max_coarse = std::max(max_coarse, h_segs[s].ncoarse);
+  return run_nn_device(S, total_tiles, t, stream, max_coarse);
 }
 
 }  // namespace libcga

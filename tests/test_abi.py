@@ -70,6 +70,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.cga_project(None, 0, None, None, ctypes.byref(out)) == cga.ERR_INVALID_ARG
     assert lib.cga_nn_query(None, None, 1, None, None, None) == cga.ERR_INVALID_ARG
     assert lib.cga_decode(None, None, None) == cga.ERR_INVALID_ARG
+    assert lib.cga_nn_prepare_levels(None, None, 0, None) == cga.ERR_INVALID_ARG
+    assert lib.cga_nn_prepare(None, 0, None) == cga.ERR_INVALID_ARG
     assert out.value is None
 
 

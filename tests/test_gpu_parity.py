@@ -277,11 +277,12 @@ def test_nn_two_step_equals_one_call(cg, orc):
     assert torch.equal(idx2, ri) and torch.equal(d22, rd)
 
 
-@pytest.mark.parametrize("shift", [1, 2, 3, 5])
+@pytest.mark.parametrize("shift", [1, 2, 3, 5, (1, 2), (2, 5), (3, 7), (4, 9)])
 @pytest.mark.parametrize("kind", ["uniform", "surface", "lidar"])
 def test_nn_two_level_parity(cg, orc, shift, kind):
-    """NN after cga_nn_prepare (coarse cells of 2^shift voxels) equals the oracle,
-    for queries near the points, uniform in the box and far outside it."""
+    """NN after cga_nn_prepare (one or two coarse levels, cells of 2^shift
+    voxels) equals the oracle, for queries near the points, uniform in the box
+    and far outside it."""
     if kind == "uniform":
         pts = synth.uniform_cube(30_000, seed=95)
         lo, ext, bits = [0.0] * 3, 1.0, 10
@@ -318,7 +319,26 @@ def test_nn_autotune_keeps_results(cg, orc):
     a = cg.cga_build(dev(pts), g)
     q = np.concatenate([synth.sample_surfaces(scene, 2000, seed=122),
                         synth.uniform_queries(2000, 123, [0.0] * 3, 100.0)])
-    shift, times = cg.cga_nn_autotune(a, dev(q))
-    assert shift in times and min(times, key=times.get) == shift
-    assert set(times) == {0, 2, 3, 4, 5}
+    shifts, times = cg.cga_nn_autotune(a, dev(q))
+    assert shifts in times and min(times, key=times.get) == shifts
+    assert set(times) == set(cg.NN_AUTOTUNE_CANDIDATES)
     nn_check(cg, orc, a, orc.build(pts, og), og, q, brute=False)
+    # a small grid cannot take the deepest candidates: they report no time
+    g6, og6 = grids(cg, orc, [0.0] * 3, 100.0, 6)
+    a6 = cg.cga_build(dev(pts), g6)
+    shifts6, times6 = cg.cga_nn_autotune(a6, dev(q))
+    assert (3, 6) not in times6 and (4, 8) not in times6 and (2, 5) in times6
+    assert min(times6, key=times6.get) == shifts6
+    nn_check(cg, orc, a6, orc.build(pts, og6), og6, q, brute=False)
+
+
+def test_nn_prepare_levels_args(cg):
+    """Coarse shifts must be strictly increasing, in 1..bits-1, at most two."""
+    pts = synth.uniform_cube(5000, seed=124)
+    a = cg.cga_build(dev(pts), cg.grid_from_box([0.0] * 3, 1.0, 8))
+    for bad in [(3, 3), (4, 2), (8,), (1, 2, 3)]:
+        with pytest.raises(cg.CgaError):
+            cg.cga_nn_prepare(a, bad)
+    cg.cga_nn_prepare(a, (1, 7))
+    idx, d2 = cg.cga_nn_query(a, dev(pts[:100]))
+    assert int(d2.max()) == 0
