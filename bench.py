@@ -256,6 +256,24 @@ def tune_record(shifts, times):
             "sample_ms": {name(c): round(t, 4) for c, t in times.items()}}
 
 
+def shape_record(shape, times):
+    """A launch shape chosen by cga_autotune / cga_pipeline_autotune, with the
+    candidates' times, for the JSON line."""
+    return {"shape": shape,
+            "sort_ms": {f"{rb}b/{th}t": round(t, 4) for (rb, th), t in times["sort"].items()},
+            "merge_ms": {str(h): round(t, 4) for h, t in times["merge"].items()}}
+
+
+def tune_launch_shapes(cga, clouds, grid):
+    """cga_autotune on representative clouds, one per size bucket the step
+    sorts or merges; returns {n: record}."""
+    out = {}
+    for c in clouds:
+        shape, times = cga.cga_autotune(c.contiguous(), grid)
+        out[str(c.numel() // 3)] = shape_record(shape, times)
+    return out
+
+
 def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
     scene, queries = make_workload(rank)
     P = LidarStep(scene, queries, torch, cga)
@@ -266,6 +284,10 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # sort / merge launch shapes by measurement on clouds of 1, 2, 4 and 8
+    # sweeps (the size buckets of the builds and of each merge level)
+    shapes = tune_launch_shapes(
+        cga, [torch.cat(P.d_sweeps[:k]) for k in (1, 2, 4, 8) if k <= len(P.d_sweeps)], P.grid)
     # NN strategy by measurement on a 64k sample of this workload's queries
     P.step(timed_events=False)
     P.nn_shift, nn_tune = cga.cga_nn_autotune(P.last[2], P.d_q[:65536].contiguous())
@@ -342,6 +364,7 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
                   "note": "one call per sweep build and per merge (the step above batches "
                           "the 10 builds and each merge-tree level into one launch set)"},
         "nn_autotune": tune_record(P.nn_shift, nn_tune),
+        "launch_shapes": shapes,
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s": round(t_wall, 3),
@@ -406,6 +429,11 @@ def run_single(args, world_size, local_rank, torch, cga, which):
         state["last"] = (a, b, mg, pr)
 
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+    # sort / merge launch shapes by measurement (the surface config's halves and
+    # the whole cloud; the plain config's cloud)
+    reps = [halves[0], torch.cat(halves)]
+    shapes = tune_launch_shapes(cga, reps, grid)
+    del reps
     # NN strategy by measurement on a 64k sample mixing both query halves
     step()
     sample = q[torch.randperm(m, device="cuda", generator=torch.Generator("cuda").manual_seed(7))
@@ -447,6 +475,7 @@ def run_single(args, world_size, local_rank, torch, cga, which):
                     "merged_u": mi["u"], "merged_bytes": mi["bytes"], "raw_bytes": n_points * 12,
                     "peak_gbs": peak, "peak_source": peak_kind},
         "nn_autotune": tune_record(coarse_shift, nn_tune),
+        "launch_shapes": shapes,
         "gpu_launches": int(launches), "clocks": clk})
     return out
 
@@ -474,6 +503,9 @@ def run_batched(args, world_size, local_rank, torch, cga):
     total_pts = 2 * int(sizes.sum())
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
+        # radix digit width, threads per tile and merge-path partition of the
+        # pipeline, by timing its graph replay under each candidate
+        shape, tune_times = cga.pipeline_autotune(pts, grids, xforms, qs)
         pipe = cga.Pipeline(pts, grids, xforms, qs, allocator=None)
         idx_p = [t for t in pipe.idx]
         for _ in range(args.warmup):
@@ -519,6 +551,7 @@ def run_batched(args, world_size, local_rank, torch, cga):
                 "plain_timing": "host wall clock around 512 sequential calls + synchronize",
                 "speedup_vs_plain": round(float(np.min(plain_ms)) / (total / args.steps), 2),
                 "nn_results_equal_plain": bool(same),
+                "launch_shape": shape_record(shape, tune_times),
                 "gpu_launches": int(launches), "clocks": clk})
     return out
 

@@ -258,6 +258,43 @@ typedef struct {
 int cga_nn_query_batch(const cga_t* const* a, const cga_queries* q, uint32_t count,
                        const cga_allocator* A, void* stream);
 
+/* ---- Launch-shape tuning ---------------------------------------------------
+ * The sort (build, xz/yz projection, NN coarse levels) and merge kernels run
+ * in one of several launch shapes, all with identical results.  A
+ * process-wide table keyed by (grid bits, bit length of the element count)
+ * holds the shape each call uses: the sort looks up (bits, n) of its largest
+ * input, the merge (bits, capacity of A + capacity of B); a batch looks up
+ * its largest item; a pipeline looks up (largest bits, largest n) once at
+ * create, for its sort and its merge alike.
+ * Entries default to {8, 512, 2048}.  Host-only and thread-safe. */
+typedef struct {
+  uint32_t radix_bits;    /* digit width of an LSD pass: 8 or 9 (9 needs sort_threads 512) */
+  uint32_t sort_threads;  /* threads per 4096-key tile: 256 (16 keys each) or 512 (8 keys each) */
+  uint32_t merge_half;    /* merge-path partition: a splitter every 512, 1024 or 2048 points
+                             of each input (tiles of at most 2 * merge_half keys) */
+} cga_tuning;
+
+#define CGA_TUNE_SORT_CANDIDATES 3  /* (8, 256), (8, 512), (9, 512) */
+#define CGA_TUNE_MERGE_CANDIDATES 3 /* 512, 1024, 2048 */
+
+/* Set (t != NULL) or clear (t == NULL: back to the default) the entry for
+ * grids of `bits` per axis and element counts with n's bit length.
+ * CGA_ERR_INVALID_ARG for bits outside 1..16 or a shape not listed above. */
+int cga_tuning_set(uint32_t bits, uint64_t n, const cga_tuning* t);
+/* The shape a call with (bits, n) would use now. */
+int cga_tuning_get(uint32_t bits, uint64_t n, cga_tuning* out);
+
+/* Fill the entry for (g->bits, n) by measurement on the caller's cloud d_xyz
+ * (n >= 2 float32 points, device): time a build of the whole cloud under each
+ * sort candidate, then the merge of the CGAs of its two halves under each
+ * merge candidate, and keep the fastest of each.  chosen receives the stored
+ * shape; times_ms (NULL or CGA_TUNE_SORT_CANDIDATES + CGA_TUNE_MERGE_CANDIDATES
+ * floats) each candidate's least time of two runs, in the order listed above.
+ * Allocates from the library pool, waits for the timings; on an error the
+ * entry is left as it was. */
+int cga_autotune(const float* d_xyz, uint64_t n, const cga_grid* g, cga_tuning* chosen,
+                 float* times_ms, void* stream);
+
 /* ---- Pre-planned pipeline (capturable) ------------------------------------
  * For each item i: build the cloud, build its twin (the same points under the
  * rigid transform xform12, the view brought into the common frame of
@@ -280,6 +317,15 @@ typedef struct {
   uint32_t* d_idx;     /* m, device */
   uint64_t* d_dist2;   /* m, device */
 } cga_pipeline_item;
+
+/* cga_autotune for a pipeline: create the pipeline of these items under each
+ * sort candidate, then each merge candidate, time two graph replays of each
+ * (after the capturing one) and store the fastest shape in the entry the
+ * pipeline looks up, (largest bits, largest n).  chosen and times_ms as in
+ * cga_autotune.  Every candidate pipeline is freed before the next is made;
+ * the items' NN outputs are overwritten. */
+int cga_pipeline_autotune(const cga_pipeline_item* items, uint32_t count, cga_tuning* chosen,
+                          float* times_ms, void* stream);
 
 /* Plan `count` items; waits until the descriptors are on the device. */
 int cga_pipeline_create(const cga_pipeline_item* items, uint32_t count, const cga_allocator* A,

@@ -39,6 +39,7 @@ EXPORTS = (
     "cga_server_create", "cga_server_submit", "cga_server_poll", "cga_server_drain",
     "cga_server_free", "cga_now_ns", "cga_nn_sort_queries", "cga_nn_query_ordered",
     "cga_nn_prepare", "cga_nn_prepare_levels", "cga_nn_autotune",
+    "cga_tuning_set", "cga_tuning_get", "cga_autotune", "cga_pipeline_autotune",
     "cga_selftest_wait_timeout",
 )
 
@@ -451,40 +452,65 @@ class _View2d(Cga2d):
         self.ptr = None
 
 
+def _pipeline_items(points_list, grids, xforms, queries_list):
+    """cga_pipeline_item array plus the NN output tensors of every item."""
+    torch = _torch()
+    k = len(points_list)
+    grids = grids if isinstance(grids, (list, tuple)) else [grids] * k
+    items = (PipelineItem * k)()
+    idxs, d2s = [], []
+    for i in range(k):
+        pts, q = points_list[i], queries_list[i]
+        _dev_f32(pts, "Pipeline")
+        it = items[i]
+        it.d_xyz, it.n, it.grid = pts.data_ptr(), pts.numel() // 3, grids[i]
+        x = np.asarray(xforms[i], np.float32).reshape(12)
+        for j in range(12):
+            it.xform12[j] = float(x[j])
+        m = 0 if q is None else q.numel() // 3
+        idx = torch.empty(m, dtype=torch.int32, device="cuda")
+        d2 = torch.empty(m, dtype=torch.int64, device="cuda")
+        if m:
+            _dev_f32(q, "Pipeline")
+            it.d_q, it.m, it.d_idx, it.d_dist2 = q.data_ptr(), m, idx.data_ptr(), d2.data_ptr()
+        idxs.append(idx)
+        d2s.append(d2)
+    return items, list(grids), idxs, d2s
+
+
+def pipeline_autotune(points_list, grids, xforms, queries_list, stream=None):
+    """cga_pipeline_autotune: time the graph-replayed pipeline of these items
+    under every launch shape and keep the fastest for their (largest bits,
+    largest n).  Returns (shape, {"sort": {...}, "merge": {...}})."""
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_pipeline_autotune.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(Tuning), P, P]
+    items, grids, _, _ = _pipeline_items(points_list, grids, xforms, queries_list)
+    t = Tuning()
+    times = (ctypes.c_float * (len(SORT_CANDIDATES) + len(MERGE_CANDIDATES)))()
+    _check(lib.cga_pipeline_autotune(items, len(items), ctypes.byref(t), times, _stream(stream)),
+           "cga_pipeline_autotune")
+    key = (max(g.bits for g in grids), _bucket(max(it.n for it in items)))
+    _tuned[key] = t.as_dict()
+    k = len(SORT_CANDIDATES)
+    return t.as_dict(), {"sort": {c: float(v) for c, v in zip(SORT_CANDIDATES, times[:k])},
+                         "merge": {c: float(v) for c, v in zip(MERGE_CANDIDATES, times[k:])}}
+
+
 class Pipeline:
     """Pre-planned batch: build + transformed twin + merge + xy projection + NN
     for many clouds, queued by run() or replayed from a CUDA graph by run_graph()."""
 
     def __init__(self, points_list, grids, xforms, queries_list, stream=None, allocator="torch"):
-        torch = _torch()
         lib = load()
         _setup_batch(lib)
-        k = len(points_list)
-        grids = grids if isinstance(grids, (list, tuple)) else [grids] * k
-        self.grids = grids
-        items = (PipelineItem * k)()
-        self.idx, self.dist2 = [], []
-        for i in range(k):
-            pts, q = points_list[i], queries_list[i]
-            _dev_f32(pts, "Pipeline")
-            it = items[i]
-            it.d_xyz, it.n, it.grid = pts.data_ptr(), pts.numel() // 3, grids[i]
-            x = np.asarray(xforms[i], np.float32).reshape(12)
-            for j in range(12):
-                it.xform12[j] = float(x[j])
-            m = 0 if q is None else q.numel() // 3
-            idx = torch.empty(m, dtype=torch.int32, device="cuda")
-            d2 = torch.empty(m, dtype=torch.int64, device="cuda")
-            if m:
-                _dev_f32(q, "Pipeline")
-                it.d_q, it.m, it.d_idx, it.d_dist2 = q.data_ptr(), m, idx.data_ptr(), d2.data_ptr()
-            self.idx.append(idx)
-            self.dist2.append(d2)
+        items, self.grids, self.idx, self.dist2 = _pipeline_items(points_list, grids, xforms,
+                                                                  queries_list)
         self._keep = (points_list, queries_list)
         self.ptr = ctypes.c_void_p()
-        _check(lib.cga_pipeline_create(items, k, _alloc_arg(allocator), _stream(stream),
+        _check(lib.cga_pipeline_create(items, len(items), _alloc_arg(allocator), _stream(stream),
                                        ctypes.byref(self.ptr)), "cga_pipeline_create")
-        self.count = k
+        self.count = len(items)
 
     def run(self, stream=None):
         _check(load().cga_pipeline_run(self.ptr, _stream(stream)), "cga_pipeline_run")
@@ -672,6 +698,98 @@ def cga_nn_autotune(a: Cga, sample_queries, stream=None):
                                chosen, times, _stream(stream)), "cga_nn_autotune")
     shifts = tuple(int(v) for v in chosen if v != 0)
     return shifts, {c: float(t) for c, t in zip(NN_AUTOTUNE_CANDIDATES, times) if t >= 0}
+
+
+# -------------------------------------------------------- launch-shape tuning
+class Tuning(ctypes.Structure):
+    _fields_ = [("radix_bits", ctypes.c_uint32), ("sort_threads", ctypes.c_uint32),
+                ("merge_half", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {"radix_bits": self.radix_bits, "sort_threads": self.sort_threads,
+                "merge_half": self.merge_half}
+
+
+# cga_autotune's candidates, in the order of its timings
+SORT_CANDIDATES = ((8, 256), (8, 512), (9, 512))  # (radix_bits, sort_threads)
+MERGE_CANDIDATES = (512, 1024, 2048)               # merge_half
+DEFAULT_TUNING = {"radix_bits": 8, "sort_threads": 512, "merge_half": 2048}
+_tuned: dict = {}  # (bits, bit length of n) -> shape set through this module
+
+
+def _bucket(n: int) -> int:
+    return int(n).bit_length()
+
+
+def tuning_get(bits: int, n: int) -> dict:
+    """The launch shape a sort or merge with (grid bits, n elements) uses now."""
+    lib = load()
+    lib.cga_tuning_get.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(Tuning)]
+    t = Tuning()
+    _check(lib.cga_tuning_get(bits, n, ctypes.byref(t)), "cga_tuning_get")
+    return t.as_dict()
+
+
+def tuning_set(bits: int, n: int, shape=None):
+    """Set the table entry for (bits, n's bit length); None restores the default."""
+    lib = load()
+    lib.cga_tuning_set.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(Tuning)]
+    if shape is None:
+        _check(lib.cga_tuning_set(bits, n, None), "cga_tuning_set")
+        _tuned.pop((bits, _bucket(n)), None)
+        return
+    t = Tuning(shape["radix_bits"], shape["sort_threads"], shape["merge_half"])
+    _check(lib.cga_tuning_set(bits, n, ctypes.byref(t)), "cga_tuning_set")
+    _tuned[(bits, _bucket(n))] = t.as_dict()
+
+
+def cga_autotune(points, grid: Grid, stream=None):
+    """Time every sort and merge launch shape on this cloud; keep the fastest
+    for (grid.bits, len(points)).  Returns (shape, {"sort": {...}, "merge": {...}})."""
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_autotune.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(Grid), ctypes.POINTER(Tuning),
+                                 P, P]
+    _dev_f32(points, "cga_autotune")
+    n = points.numel() // 3
+    t = Tuning()
+    times = (ctypes.c_float * (len(SORT_CANDIDATES) + len(MERGE_CANDIDATES)))()
+    _check(lib.cga_autotune(P(points.data_ptr()), n, ctypes.byref(grid), ctypes.byref(t), times,
+                            _stream(stream)), "cga_autotune")
+    _tuned[(grid.bits, _bucket(n))] = t.as_dict()
+    k = len(SORT_CANDIDATES)
+    return t.as_dict(), {"sort": {c: float(v) for c, v in zip(SORT_CANDIDATES, times[:k])},
+                         "merge": {c: float(v) for c, v in zip(MERGE_CANDIDATES, times[k:])}}
+
+
+def tuning_cache_save(path: str, device: str | None = None):
+    """Write the shapes set through this module to a JSON cache, under the
+    current device's name (entries of other devices already in the file stay)."""
+    import json
+    device = device or _torch().cuda.get_device_name()
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    data[device] = [{"bits": b, "n_bit_length": nb, **shape}
+                    for (b, nb), shape in sorted(_tuned.items())]
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+
+
+def tuning_cache_load(path: str, device: str | None = None) -> int:
+    """Apply the cached shapes of the current device; returns how many."""
+    import json
+    device = device or _torch().cuda.get_device_name()
+    if not os.path.exists(path):
+        return 0
+    with open(path) as f:
+        entries = json.load(f).get(device, [])
+    for e in entries:
+        nb = int(e["n_bit_length"])
+        tuning_set(int(e["bits"]), (1 << (nb - 1)) if nb > 0 else 0,
+                   {k: int(e[k]) for k in ("radix_bits", "sort_threads", "merge_half")})
+    return len(entries)
 
 
 def selftest_wait_timeout(stream=None) -> int:

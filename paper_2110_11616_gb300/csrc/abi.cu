@@ -265,7 +265,8 @@ int cga_build(const float* d_xyz, uint64_t n, const cga_grid* g, const float* h_
   seg.n_host = (uint32_t)n;
   seg.bits = g->bits;
   seg.key_bits = 3 * g->bits;
-  seg.passes = (seg.key_bits + libcga::kRadixBits - 1) / libcga::kRadixBits;
+  const libcga::Tuning tu = libcga::tuning_for(g->bits, n);
+  seg.passes = libcga::radix_passes(seg.key_bits, tu.radix_bits);
   seg.key_base = 0;
   seg.tile_base = 0;
   seg.num_tiles = (uint32_t)((n + libcga::kTile - 1) / libcga::kTile);
@@ -273,12 +274,12 @@ int cga_build(const float* d_xyz, uint64_t n, const cga_grid* g, const float* h_
   const bool key64 = seg.key_bits > 32;
   const uint32_t tiles = seg.num_tiles;
   const uint64_t keys = (uint64_t)tiles * libcga::kTile;
-  void* scratch = dalloc(A, libcga::sort_scratch_bytes(keys, tiles, 1, key64), s);
+  void* scratch = dalloc(A, libcga::sort_scratch_bytes(keys, tiles, 1, key64, tu.radix_bits), s);
   if (scratch == nullptr) {
     release(h);
     return CGA_ERR_OOM;
   }
-  const libcga::SortScratch sc = libcga::sort_scratch_carve(scratch, keys, tiles, 1, key64);
+  const libcga::SortScratch sc = libcga::sort_scratch_carve(scratch, keys, tiles, 1, key64, tu);
   const int rc = cuda_rc(libcga::run_sort_pipeline(&seg, 1, tiles, seg.passes, key64, sc, s));
   dfree(A, A != nullptr, scratch, s);
   if (rc != CGA_OK) {
@@ -305,8 +306,9 @@ int cga_merge(const cga_t* a, const cga_t* b, const cga_allocator* A, void* stre
   P.b = b->lv;
   P.out = h->lv;
   P.spl_base = 0;
-  P.spl_a = a->lv.cap > 0 ? (uint32_t)((a->lv.cap - 1) / libcga::kMergeHalf) : 0u;
-  P.spl_b = b->lv.cap > 0 ? (uint32_t)((b->lv.cap - 1) / libcga::kMergeHalf) : 0u;
+  const uint32_t half = libcga::tuning_for(bits, a->lv.cap + b->lv.cap).merge_half;
+  P.spl_a = libcga::merge_splitters(a->lv.cap, half);
+  P.spl_b = libcga::merge_splitters(b->lv.cap, half);
   P.tile_base = 0;
   P.num_tiles = P.spl_a + P.spl_b + 1;
   const uint32_t total_spl = P.spl_a + P.spl_b;
@@ -315,7 +317,8 @@ int cga_merge(const cga_t* a, const cga_t* b, const cga_allocator* A, void* stre
     release(h);
     return CGA_ERR_OOM;
   }
-  const libcga::MergeScratch sc = libcga::merge_scratch_carve(scratch, total_spl, P.num_tiles, 1);
+  const libcga::MergeScratch sc =
+      libcga::merge_scratch_carve(scratch, total_spl, P.num_tiles, 1, half);
   const int rc = cuda_rc(libcga::run_merge(&P, 1, total_spl, P.num_tiles, sc, s));
   dfree(A, A != nullptr, scratch, s);
   if (rc != CGA_OK) {
@@ -366,16 +369,18 @@ int cga_project(const cga_t* a, int plane, const cga_allocator* A, void* stream,
     seg.from_cga = 1;
     seg.bits = b;
     seg.key_bits = 2 * b;
-    seg.passes = (seg.key_bits + libcga::kRadixBits - 1) / libcga::kRadixBits;
+    const libcga::Tuning tu = libcga::tuning_for(b, a->lv.cap);
+    seg.passes = libcga::radix_passes(seg.key_bits, tu.radix_bits);
     seg.num_tiles = (uint32_t)((a->lv.cap + libcga::kTile - 1) / libcga::kTile);
     seg.out = p->lv;
     const uint32_t tiles = seg.num_tiles;
     const uint64_t keys = (uint64_t)tiles * libcga::kTile;
-    void* scratch = dalloc(A, libcga::sort_scratch_bytes(keys, tiles, 1, false), s);
+    void* scratch = dalloc(A, libcga::sort_scratch_bytes(keys, tiles, 1, false, tu.radix_bits), s);
     if (scratch == nullptr) {
       rc = CGA_ERR_OOM;
     } else {
-      const libcga::SortScratch sc = libcga::sort_scratch_carve(scratch, keys, tiles, 1, false);
+      const libcga::SortScratch sc =
+          libcga::sort_scratch_carve(scratch, keys, tiles, 1, false, tu);
       rc = cuda_rc(libcga::run_sort_pipeline(&seg, 1, tiles, seg.passes, false, sc, s));
       dfree(A, A != nullptr, scratch, s);
     }
@@ -481,16 +486,18 @@ int build_coarse_level(cga* a, int k, uint32_t shift, cudaStream_t s) {
   seg.from_cga = 1;
   seg.bits = bc;
   seg.key_bits = 3 * bc;
-  seg.passes = (seg.key_bits + libcga::kRadixBits - 1) / libcga::kRadixBits;
+  const libcga::Tuning tu = libcga::tuning_for(bc, fine.cap);
+  seg.passes = libcga::radix_passes(seg.key_bits, tu.radix_bits);
   seg.num_tiles = (uint32_t)((fine.cap + libcga::kTile - 1) / libcga::kTile);
   seg.out = clv;
   const bool key64 = seg.key_bits > 32;
   const uint32_t tiles = seg.num_tiles;
   const uint64_t keys = (uint64_t)tiles * libcga::kTile;
-  void* scratch = dalloc(A, libcga::sort_scratch_bytes(keys, tiles, 1, key64), s);
+  void* scratch = dalloc(A, libcga::sort_scratch_bytes(keys, tiles, 1, key64, tu.radix_bits), s);
   int rc = CGA_ERR_OOM;
   if (scratch != nullptr) {
-    const libcga::SortScratch sc = libcga::sort_scratch_carve(scratch, keys, tiles, 1, key64);
+    const libcga::SortScratch sc =
+        libcga::sort_scratch_carve(scratch, keys, tiles, 1, key64, tu);
     cudaError_t e = libcga::run_sort_pipeline(&seg, 1, tiles, seg.passes, key64, sc, s);
     if (e == cudaSuccess) e = libcga::run_coarse_slab_index(fine, clv, dsh, xs, s);
     if (e == cudaSuccess) e = libcga::run_x_directory(clv, cxdir, s);
@@ -756,6 +763,13 @@ int cga_build_batch(const cga_cloud* clouds, uint32_t count, const cga_allocator
   }
   if (count == 0) return CGA_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t max_bits = 1;
+  uint64_t max_n = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    max_bits = std::max(max_bits, clouds[i].grid.bits);
+    max_n = std::max<uint64_t>(max_n, clouds[i].n);
+  }
+  const libcga::Tuning tu = libcga::tuning_for(max_bits, max_n);
   std::vector<libcga::SortSeg> segs(count);
   std::vector<cga*> hs(count, nullptr);
   uint64_t tiles = 0;
@@ -781,7 +795,7 @@ int cga_build_batch(const cga_cloud* clouds, uint32_t count, const cga_allocator
     sg.n_host = (uint32_t)c.n;
     sg.bits = c.grid.bits;
     sg.key_bits = 3 * c.grid.bits;
-    sg.passes = (sg.key_bits + libcga::kRadixBits - 1) / libcga::kRadixBits;
+    sg.passes = libcga::radix_passes(sg.key_bits, tu.radix_bits);
     sg.tile_base = (uint32_t)tiles;
     sg.num_tiles = (uint32_t)((c.n + libcga::kTile - 1) / libcga::kTile);
     sg.key_base = tiles * libcga::kTile;
@@ -794,11 +808,12 @@ int cga_build_batch(const cga_cloud* clouds, uint32_t count, const cga_allocator
   void* scratch = nullptr;
   if (rc == CGA_OK) {
     const uint64_t keys = tiles * libcga::kTile;
-    scratch = dalloc(A, libcga::sort_scratch_bytes(keys, (uint32_t)tiles, (int)count, key64), s);
+    scratch = dalloc(
+        A, libcga::sort_scratch_bytes(keys, (uint32_t)tiles, (int)count, key64, tu.radix_bits), s);
     if (scratch == nullptr) rc = CGA_ERR_OOM;
     if (rc == CGA_OK) {
       const libcga::SortScratch sc =
-          libcga::sort_scratch_carve(scratch, keys, (uint32_t)tiles, (int)count, key64);
+          libcga::sort_scratch_carve(scratch, keys, (uint32_t)tiles, (int)count, key64, tu);
       rc = cuda_rc(libcga::run_sort_pipeline(segs.data(), (int)count, (uint32_t)tiles,
                                              max_passes, key64, sc, s));
       dfree(A, A != nullptr, scratch, s);
@@ -817,16 +832,22 @@ namespace {
 // Merge pair table + output handles for `count` pairs.
 int plan_merges(const cga_t* const* a, const cga_t* const* b, uint32_t count,
                 const cga_allocator* A, cudaStream_t s, std::vector<libcga::MergePair>& pairs,
-                std::vector<cga*>& hs, uint32_t& total_spl, uint32_t& total_tiles) {
+                std::vector<cga*>& hs, uint32_t& total_spl, uint32_t& total_tiles,
+                uint32_t& half) {
   pairs.assign(count, libcga::MergePair{});
   hs.assign(count, nullptr);
   uint64_t spl = 0, tiles = 0;
+  uint32_t max_bits = 1;
+  uint64_t max_in = 0;
   for (uint32_t i = 0; i < count; ++i) {
     if (a[i] == nullptr || b[i] == nullptr) return CGA_ERR_INVALID_ARG;
     if (!same_grid(a[i]->grid, b[i]->grid)) return CGA_ERR_GRID_MISMATCH;
     const uint64_t cap = std::min<uint64_t>(a[i]->lv.cap + b[i]->lv.cap, pow2(3 * a[i]->grid.bits));
     if (cap > CGA_MAX_POINTS) return CGA_ERR_INVALID_ARG;
+    max_bits = std::max(max_bits, a[i]->grid.bits);
+    max_in = std::max<uint64_t>(max_in, a[i]->lv.cap + b[i]->lv.cap);
   }
+  half = libcga::tuning_for(max_bits, max_in).merge_half;
   for (uint32_t i = 0; i < count; ++i) {
     const uint64_t cap = std::min<uint64_t>(a[i]->lv.cap + b[i]->lv.cap, pow2(3 * a[i]->grid.bits));
     hs[i] = new_cga(a[i]->grid, A, s, cap);
@@ -835,8 +856,8 @@ int plan_merges(const cga_t* const* a, const cga_t* const* b, uint32_t count,
     P.a = a[i]->lv;
     P.b = b[i]->lv;
     P.out = hs[i]->lv;
-    P.spl_a = a[i]->lv.cap > 0 ? (uint32_t)((a[i]->lv.cap - 1) / libcga::kMergeHalf) : 0u;
-    P.spl_b = b[i]->lv.cap > 0 ? (uint32_t)((b[i]->lv.cap - 1) / libcga::kMergeHalf) : 0u;
+    P.spl_a = libcga::merge_splitters(a[i]->lv.cap, half);
+    P.spl_b = libcga::merge_splitters(b[i]->lv.cap, half);
     P.spl_base = (uint32_t)spl;
     P.tile_base = (uint32_t)tiles;
     P.num_tiles = P.spl_a + P.spl_b + 1;
@@ -859,15 +880,15 @@ int cga_merge_batch(const cga_t* const* a, const cga_t* const* b, uint32_t count
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<libcga::MergePair> pairs;
   std::vector<cga*> hs;
-  uint32_t total_spl = 0, total_tiles = 0;
-  int rc = plan_merges(a, b, count, A, s, pairs, hs, total_spl, total_tiles);
+  uint32_t total_spl = 0, total_tiles = 0, half = libcga::kMergeHalf;
+  int rc = plan_merges(a, b, count, A, s, pairs, hs, total_spl, total_tiles, half);
   if (rc == CGA_OK) {
     void* scratch = dalloc(A, libcga::merge_scratch_bytes(total_spl, total_tiles, (int)count), s);
     if (scratch == nullptr) {
       rc = CGA_ERR_OOM;
     } else {
       const libcga::MergeScratch sc =
-          libcga::merge_scratch_carve(scratch, total_spl, total_tiles, (int)count);
+          libcga::merge_scratch_carve(scratch, total_spl, total_tiles, (int)count, half);
       rc = cuda_rc(libcga::run_merge(pairs.data(), (int)count, total_spl, total_tiles, sc, s));
       dfree(A, A != nullptr, scratch, s);
     }
@@ -933,7 +954,6 @@ int cga_project_batch(const cga_t* const* a, const int* planes, uint32_t count,
       sg.from_cga = 1;
       sg.bits = b;
       sg.key_bits = 2 * b;
-      sg.passes = (sg.key_bits + libcga::kRadixBits - 1) / libcga::kRadixBits;
       sg.tile_base = (uint32_t)tiles;
       sg.num_tiles = (uint32_t)((a[i]->lv.cap + libcga::kTile - 1) / libcga::kTile);
       sg.key_base = tiles * libcga::kTile;
@@ -958,16 +978,27 @@ int cga_project_batch(const cga_t* const* a, const int* planes, uint32_t count,
     }
   }
   if (rc == CGA_OK && !segs.empty()) {
+    uint32_t max_bits = 1;
+    uint64_t max_cap = 0;
+    for (const auto& sg : segs) {
+      max_bits = std::max(max_bits, sg.bits);
+      max_cap = std::max<uint64_t>(max_cap, sg.src.cap);
+    }
+    const libcga::Tuning tu = libcga::tuning_for(max_bits, max_cap);
     uint32_t max_passes = 0;
-    for (const auto& sg : segs) max_passes = std::max(max_passes, sg.passes);
+    for (auto& sg : segs) {
+      sg.passes = libcga::radix_passes(sg.key_bits, tu.radix_bits);
+      max_passes = std::max(max_passes, sg.passes);
+    }
     const uint64_t keys = tiles * libcga::kTile;
-    void* scratch =
-        dalloc(A, libcga::sort_scratch_bytes(keys, (uint32_t)tiles, (int)segs.size(), false), s);
+    void* scratch = dalloc(
+        A, libcga::sort_scratch_bytes(keys, (uint32_t)tiles, (int)segs.size(), false, tu.radix_bits),
+        s);
     if (scratch == nullptr) {
       rc = CGA_ERR_OOM;
     } else {
       const libcga::SortScratch sc =
-          libcga::sort_scratch_carve(scratch, keys, (uint32_t)tiles, (int)segs.size(), false);
+          libcga::sort_scratch_carve(scratch, keys, (uint32_t)tiles, (int)segs.size(), false, tu);
       rc = cuda_rc(libcga::run_sort_pipeline(segs.data(), (int)segs.size(), (uint32_t)tiles,
                                              max_passes, false, sc, s));
       dfree(A, A != nullptr, scratch, s);
@@ -1086,6 +1117,15 @@ int cga_pipeline_create(const cga_pipeline_item* items, uint32_t count, const cg
   p->stream = s;
   p->has_alloc = A != nullptr;
   if (A != nullptr) p->alloc = *A;
+  // --- launch shapes: one per pipeline, from its largest item
+  uint32_t max_bits = 1;
+  uint64_t max_n = 0;
+  for (uint32_t i = 0; i < S; ++i) {
+    max_bits = std::max(max_bits, items[i].grid.bits);
+    max_n = std::max<uint64_t>(max_n, items[i].n);
+  }
+  const libcga::Tuning tu = libcga::tuning_for(max_bits, max_n);
+  const uint32_t half = tu.merge_half;
   // --- layout
   Bump bump;
   std::vector<size_t> lv_off(4 * (size_t)S);
@@ -1108,7 +1148,7 @@ int cga_pipeline_create(const cga_pipeline_item* items, uint32_t count, const cg
     lv_off[4 * i + 3] = bump.take(levels_bytes(pc, pc1, 0, 2));
     const uint64_t t = (n + libcga::kTile - 1) / libcga::kTile;
     build_tiles += 2 * t;
-    const uint64_t sa = n > 0 ? (n - 1) / libcga::kMergeHalf : 0;
+    const uint64_t sa = libcga::merge_splitters(n, half);
     spl += 2 * sa;
     mtiles += 2 * sa + 1;
     if (items[i].m > 0) {
@@ -1125,10 +1165,10 @@ int cga_pipeline_create(const cga_pipeline_item* items, uint32_t count, const cg
   uint32_t passes = 0;
   for (uint32_t i = 0; i < S; ++i) {
     key64 = key64 || 3 * items[i].grid.bits > 32;
-    passes = std::max<uint32_t>(passes, (3 * items[i].grid.bits + 7) / 8);
+    passes = std::max<uint32_t>(passes, libcga::radix_passes(3 * items[i].grid.bits, tu.radix_bits));
   }
-  const size_t o_build = bump.take(libcga::sort_scratch_bytes(build_tiles * libcga::kTile,
-                                                              (uint32_t)build_tiles, (int)(2 * S), key64));
+  const size_t o_build = bump.take(libcga::sort_scratch_bytes(
+      build_tiles * libcga::kTile, (uint32_t)build_tiles, (int)(2 * S), key64, tu.radix_bits));
   const size_t o_merge = bump.take(libcga::merge_scratch_bytes((uint32_t)spl, (uint32_t)mtiles, (int)S));
   const size_t o_proj = bump.take(sizeof(libcga::ProjPair) * S);
   const size_t o_nn = bump.take(nn_segs ? libcga::nn_scratch_bytes((uint32_t)nn_tiles, (int)nn_segs) : 0);
@@ -1180,7 +1220,7 @@ int cga_pipeline_create(const cga_pipeline_item* items, uint32_t count, const cg
       sg.n_host = (uint32_t)items[i].n;
       sg.bits = items[i].grid.bits;
       sg.key_bits = 3 * sg.bits;
-      sg.passes = (sg.key_bits + 7) / 8;
+      sg.passes = libcga::radix_passes(sg.key_bits, tu.radix_bits);
       sg.tile_base = (uint32_t)tb;
       sg.num_tiles = (uint32_t)((items[i].n + libcga::kTile - 1) / libcga::kTile);
       sg.key_base = tb * libcga::kTile;
@@ -1189,7 +1229,7 @@ int cga_pipeline_create(const cga_pipeline_item* items, uint32_t count, const cg
     }
   }
   p->build = libcga::sort_scratch_carve(base + o_build, build_tiles * libcga::kTile,
-                                        (uint32_t)build_tiles, (int)(2 * S), key64);
+                                        (uint32_t)build_tiles, (int)(2 * S), key64, tu);
   p->build_tiles = (uint32_t)build_tiles;
   p->build_passes = passes;
   p->key64 = key64;
@@ -1200,14 +1240,15 @@ int cga_pipeline_create(const cga_pipeline_item* items, uint32_t count, const cg
     P.a = p->views[3 * i].lv;
     P.b = p->views[3 * i + 1].lv;
     P.out = p->views[3 * i + 2].lv;
-    P.spl_a = P.spl_b = items[i].n > 0 ? (uint32_t)((items[i].n - 1) / libcga::kMergeHalf) : 0u;
+    P.spl_a = P.spl_b = libcga::merge_splitters(items[i].n, half);
     P.spl_base = (uint32_t)sb;
     P.tile_base = (uint32_t)mb;
     P.num_tiles = P.spl_a + P.spl_b + 1;
     sb += P.spl_a + P.spl_b;
     mb += P.num_tiles;
   }
-  p->merge = libcga::merge_scratch_carve(base + o_merge, (uint32_t)spl, (uint32_t)mtiles, (int)S);
+  p->merge =
+      libcga::merge_scratch_carve(base + o_merge, (uint32_t)spl, (uint32_t)mtiles, (int)S, half);
   p->merge_spl = (uint32_t)spl;
   p->merge_tiles = (uint32_t)mtiles;
   std::vector<libcga::ProjPair> proj(S);
@@ -1270,6 +1311,7 @@ int cga_pipeline_run_graph(cga_pipeline_t* p, void* stream) {
   if (p->exec == nullptr) {
     cudaError_t e = cudaSuccess;
     if (p->cap_stream == nullptr) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = libcga::init_sort_kernels();  // kernel attributes before capture
     if (e != cudaSuccess) return cuda_rc(e);
     const uint64_t k0 = libcga::g_launches.load();
     e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);

@@ -12,9 +12,27 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 16;
 constexpr int kTile = kThreads * kItems;  // 4096
-constexpr int kRadixBits = 8;
+constexpr int kRadixBits = 8;  // default digit width (and the NN query sort's)
 constexpr int kRadix = 1 << kRadixBits;
-constexpr int kMaxPasses = 6;  // 3 * 16 bits / 8
+constexpr int kRadixMaxBits = 9;
+constexpr int kMaxPasses = 6;  // 3 * 16 bits / 8 (or / 9)
+
+// Launch shape of the sort and merge kernels, chosen per (grid bits, size
+// bucket) by measurement (cga_autotune) and held in a process-wide table.
+struct Tuning {
+  uint32_t radix_bits;    // digit width of an LSD pass: 8 or 9
+  uint32_t sort_threads;  // threads per 4096-key tile: 256 (16 keys each) or 512 (8 keys each)
+  uint32_t merge_half;    // merge-path partition: a splitter every merge_half points (512..2048)
+};
+constexpr Tuning kDefaultTuning{8u, 512u, 2048u};
+bool tuning_valid(const Tuning& t);
+// The table entry for grids of `bits` per axis and n elements (the default
+// when none was set).  Host only, thread-safe.
+Tuning tuning_for(uint32_t bits, uint64_t n);
+void tuning_store(uint32_t bits, uint64_t n, const Tuning* t);  // nullptr: back to the default
+inline uint32_t radix_passes(uint32_t key_bits, uint32_t radix_bits) {
+  return (key_bits + radix_bits - 1) / radix_bits;
+}
 
 // Device error bits recorded in a handle header.
 enum : uint32_t { kErrNonfinite = 1u, kErrTimeout = 2u };
@@ -61,8 +79,8 @@ struct SortSeg {
   uint32_t n_host;      // element count when known on the host (build)
   uint32_t bits;        // grid bits of this segment
   uint32_t key_bits;    // significant key bits: 3b (build) or 2b (projection)
-  uint32_t passes;      // radix passes = ceil(key_bits / 8)
-  uint32_t bit0;        // lowest key bit sorted on (pass p sorts bits bit0 + 8p ..)
+  uint32_t passes;      // radix passes = ceil(key_bits / radix_bits)
+  uint32_t bit0;        // lowest key bit sorted on (pass p sorts bits bit0 + p * radix_bits ..)
   uint64_t key_base;    // first key slot of this segment in the key buffers
   uint32_t tile_base;   // first global tile index
   uint32_t num_tiles;   // tiles reserved (from the capacity)
@@ -73,17 +91,25 @@ struct SortSeg {
 struct SortScratch {
   void* keys0;
   void* keys1;
-  uint32_t* hist;      // [S][kMaxPasses][kRadix]
-  uint32_t* look;      // [kMaxPasses][total_tiles][kRadix]
+  uint32_t* hist;      // [S][kMaxPasses][2^radix_bits]
+  uint32_t* look;      // [kMaxPasses][total_tiles][2^radix_bits]
   uint32_t* clook;     // [total_tiles][3]
   uint32_t* counters;  // [kMaxPasses + 1]
   SortSeg* segs;       // [S]
   size_t zero_bytes;   // bytes from hist to the end of counters
+  uint32_t radix_bits;    // launch shape of the passes (Tuning)
+  uint32_t sort_threads;
 };
 
-size_t sort_scratch_bytes(uint64_t total_keys, uint32_t total_tiles, int S, bool key64);
+// Scratch of a sort run; the digit width sizes the histogram and look-back
+// tables, the thread count only selects the pass kernel.
+size_t sort_scratch_bytes(uint64_t total_keys, uint32_t total_tiles, int S, bool key64,
+                          uint32_t radix_bits = kRadixBits);
 SortScratch sort_scratch_carve(void* base, uint64_t total_keys, uint32_t total_tiles, int S,
-                               bool key64);
+                               bool key64, const Tuning& tu = kDefaultTuning);
+// Set the shared-memory limits of the pass kernels (once; before any graph
+// capture that launches them).
+cudaError_t init_sort_kernels();
 
 // Queue only the radix passes (segments already on the device in sc.segs,
 // histograms filled, look-back words zeroed).
@@ -106,10 +132,14 @@ cudaError_t run_sort_pipeline(const SortSeg* h_segs, int S, uint32_t total_tiles
 cudaError_t run_decode(const Levels& a, uint32_t* xyz, cudaStream_t stream);
 
 // Merge: sorted union of pairs of 3-level CGAs.  Splitter keys are taken at
-// every kMergeHalf-th point of each input; between consecutive splitters (in
-// key order) each input contributes at most kMergeHalf points, so one tile of
-// kTile keys always holds the merged run.
-constexpr int kMergeHalf = kTile / 2;
+// every half-th point of each input (half = Tuning::merge_half <= kTile / 2);
+// between consecutive splitters (in key order) each input contributes at most
+// half points, so one tile of 2 * half <= kTile keys always holds the merged
+// run.
+constexpr int kMergeHalf = kTile / 2;  // largest partition
+inline uint32_t merge_splitters(uint64_t cap, uint32_t half) {
+  return cap > 0 ? (uint32_t)((cap - 1) / half) : 0u;
+}
 
 struct MergePair {
   Levels a, b, out;
@@ -127,10 +157,12 @@ struct MergeScratch {
   uint32_t* counter;        // [1]
   MergePair* pairs;         // [S]
   size_t zero_bytes;        // clook .. counter
+  uint32_t half;            // merge-path partition the splitters were counted with
 };
 
 size_t merge_scratch_bytes(uint32_t total_spl, uint32_t total_tiles, int S);
-MergeScratch merge_scratch_carve(void* base, uint32_t total_spl, uint32_t total_tiles, int S);
+MergeScratch merge_scratch_carve(void* base, uint32_t total_spl, uint32_t total_tiles, int S,
+                                 uint32_t half = kMergeHalf);
 cudaError_t run_merge(const MergePair* h_pairs, int S, uint32_t total_spl, uint32_t total_tiles,
                       const MergeScratch& sc, cudaStream_t stream);
 // Merge with the pair table already on the device (sc.pairs).

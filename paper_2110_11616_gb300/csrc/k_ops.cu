@@ -53,19 +53,19 @@ __device__ __forceinline__ int find_pair_tile(const MergePair* __restrict__ P, i
   return lo;
 }
 
-__device__ __forceinline__ uint32_t n_splitters(uint32_t u, uint32_t reserved) {
-  const uint32_t k = u > 0 ? (u - 1) / kMergeHalf : 0u;
+__device__ __forceinline__ uint32_t n_splitters(uint32_t u, uint32_t reserved, uint32_t half) {
+  const uint32_t k = u > 0 ? (u - 1) / half : 0u;
   return min(k, reserved);
 }
 
 // Output header, empty-CGA sentinels, first and last tile bounds.
-__global__ void k_merge_init(const MergePair* __restrict__ pairs, int S, uint32_t* bounds,
-                             uint32_t* ntiles) {
+__global__ void k_merge_init(const MergePair* __restrict__ pairs, int S, uint32_t half,
+                             uint32_t* bounds, uint32_t* ntiles) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= S) return;
   const MergePair& P = pairs[p];
   const uint32_t uA = (uint32_t)P.a.hdr->cnt[0], uB = (uint32_t)P.b.hdr->cnt[0];
-  const uint32_t NA = n_splitters(uA, P.spl_a), NB = n_splitters(uB, P.spl_b);
+  const uint32_t NA = n_splitters(uA, P.spl_a, half), NB = n_splitters(uB, P.spl_b, half);
   const uint32_t nt = NA + NB + 1;
   ntiles[p] = nt;
   uint32_t* bnd = bounds + 2 * ((size_t)P.tile_base + p);
@@ -81,9 +81,9 @@ __global__ void k_merge_init(const MergePair* __restrict__ pairs, int S, uint32_
   P.out.ptr2[0] = 0;
 }
 
-// Splitter keys: every kMergeHalf-th point of A, then of B.
+// Splitter keys: every half-th point of A, then of B.
 __global__ void k_merge_spl(const MergePair* __restrict__ pairs, int S, uint32_t total,
-                            unsigned long long* spl) {
+                            uint32_t half, unsigned long long* spl) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   const MergePair& P = pairs[find_pair_spl(pairs, S, i)];
@@ -92,7 +92,7 @@ __global__ void k_merge_spl(const MergePair* __restrict__ pairs, int S, uint32_t
   const Levels& L = isA ? P.a : P.b;
   const uint32_t k = isA ? local : local - P.spl_a;
   const uint32_t u = (uint32_t)L.hdr->cnt[0];
-  const uint32_t pos = (k + 1) * (uint32_t)kMergeHalf;
+  const uint32_t pos = (k + 1) * half;
   spl[i] = (pos < u) ? key_at(L, (uint32_t)L.hdr->cnt[1], (uint32_t)L.hdr->cnt[2], pos)
                      : ~0ull;
 }
@@ -100,14 +100,15 @@ __global__ void k_merge_spl(const MergePair* __restrict__ pairs, int S, uint32_t
 // Tile bounds: each splitter s becomes the cut (rank_A(s), rank_B(s)) at its
 // place in the key order of all splitters.
 __global__ void k_merge_bounds(const MergePair* __restrict__ pairs, int S, uint32_t total,
-                               const unsigned long long* __restrict__ spl, uint32_t* bounds) {
+                               uint32_t half, const unsigned long long* __restrict__ spl,
+                               uint32_t* bounds) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   const int p = find_pair_spl(pairs, S, i);
   const MergePair& P = pairs[p];
   const uint32_t local = i - P.spl_base;
   const uint32_t uA = (uint32_t)P.a.hdr->cnt[0], uB = (uint32_t)P.b.hdr->cnt[0];
-  const uint32_t NA = n_splitters(uA, P.spl_a), NB = n_splitters(uB, P.spl_b);
+  const uint32_t NA = n_splitters(uA, P.spl_a, half), NB = n_splitters(uB, P.spl_b, half);
   const unsigned long long* sa = spl + P.spl_base;
   const unsigned long long* sb = sa + P.spl_a;
   const unsigned long long s = spl[i];
@@ -121,7 +122,7 @@ __global__ void k_merge_bounds(const MergePair* __restrict__ pairs, int S, uint3
       if (sb[mid] < s) lo = mid + 1; else hi = mid;
     }
     pos = k + lo;
-    ca = (k + 1) * (uint32_t)kMergeHalf;
+    ca = (k + 1) * half;
     cb = rank_of(P.b, (uint32_t)P.b.hdr->cnt[2], s);
   } else {
     const uint32_t k = local - P.spl_a;
@@ -133,20 +134,24 @@ __global__ void k_merge_bounds(const MergePair* __restrict__ pairs, int S, uint3
     }
     pos = k + lo;
     ca = rank_of(P.a, (uint32_t)P.a.hdr->cnt[2], s);
-    cb = (k + 1) * (uint32_t)kMergeHalf;
+    cb = (k + 1) * half;
   }
   uint32_t* bnd = bounds + 2 * ((size_t)P.tile_base + p);
   bnd[2 * (pos + 1)] = ca;
   bnd[2 * (pos + 1) + 1] = cb;
 }
 
-// Merge one tile: decode both runs into shared memory, merge-path split per
-// thread, sequential merge, then the shared dedupe + compaction.
+// Merge one tile: decode both runs (at most MH points each) into shared
+// memory, merge-path split per thread, sequential merge, then the shared
+// dedupe + compaction.
+template <int MH>
 __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __restrict__ pairs,
                                                           int S, const uint32_t* __restrict__ bounds,
                                                           const uint32_t* __restrict__ ntiles,
                                                           uint32_t* clook, uint32_t* counter) {
-  __shared__ unsigned long long s_ab[kTile];
+  constexpr int IT = 2 * MH / kThreads;  // merged keys per thread
+  static_assert(IT * kThreads == 2 * MH && 2 * MH <= kTile, "merge tile shape");
+  __shared__ unsigned long long s_ab[2 * MH];
   __shared__ CompactSmem sm;
   __shared__ Window s_wa, s_wb;
   __shared__ unsigned long long s_prev;
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
   const uint32_t* bnd = bounds + 2 * ((size_t)P.tile_base + p + lt);
   uint32_t a0 = bnd[0], b0 = bnd[1], a1 = bnd[2], b1 = bnd[3];
   uint32_t na = a1 - a0, nb = b1 - b0;
-  const bool bad = a1 < a0 || b1 < b0 || na > (uint32_t)kMergeHalf || nb > (uint32_t)kMergeHalf;
+  const bool bad = a1 < a0 || b1 < b0 || na > (uint32_t)MH || nb > (uint32_t)MH;
   if (bad) {
     na = 0;
     nb = 0;
@@ -208,25 +213,25 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
     for (uint32_t e = tid; e < nb; e += kThreads) {
       uint32_t x, y, z;
       point_at(P.b, wb, b0 + e, x, y, z);
-      s_ab[kMergeHalf + e] = ((unsigned long long)x << (2 * bA)) | ((unsigned long long)y << bA) | z;
+      s_ab[MH + e] = ((unsigned long long)x << (2 * bA)) | ((unsigned long long)y << bA) | z;
     }
   }
   __syncthreads();
   const uint32_t cnt = na + nb;
-  const uint32_t diag = min((uint32_t)(tid * kItems), cnt);
+  const uint32_t diag = min((uint32_t)(tid * IT), cnt);
   uint32_t lo = diag > nb ? diag - nb : 0u, hi = min(diag, na);
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (s_ab[mid] <= s_ab[kMergeHalf + diag - 1 - mid]) lo = mid + 1; else hi = mid;
+    if (s_ab[mid] <= s_ab[MH + diag - 1 - mid]) lo = mid + 1; else hi = mid;
   }
   uint32_t i = lo, j = diag - lo;
-  unsigned long long r[kItems];
+  unsigned long long r[IT];
 #pragma unroll
-  for (int it = 0; it < kItems; ++it) {
-    const bool takeA = i < na && (j >= nb || s_ab[i] <= s_ab[kMergeHalf + j]);
+  for (int it = 0; it < IT; ++it) {
+    const bool takeA = i < na && (j >= nb || s_ab[i] <= s_ab[MH + j]);
     const bool any = i < na || j < nb;
     unsigned long long v = 0;
-    if (any) v = takeA ? s_ab[i] : s_ab[kMergeHalf + j];
+    if (any) v = takeA ? s_ab[i] : s_ab[MH + j];
     if (any) {
       if (takeA) ++i; else ++j;
     }
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
   }
   __syncthreads();
 #pragma unroll
-  for (int it = 0; it < kItems; ++it) {
+  for (int it = 0; it < IT; ++it) {
     const uint32_t pos = diag + it;
     if (pos < cnt) s_ab[pos] = r[it];
   }
@@ -318,9 +323,11 @@ size_t merge_scratch_bytes(uint32_t total_spl, uint32_t total_tiles, int S) {
   return b;
 }
 
-MergeScratch merge_scratch_carve(void* base, uint32_t total_spl, uint32_t total_tiles, int S) {
+MergeScratch merge_scratch_carve(void* base, uint32_t total_spl, uint32_t total_tiles, int S,
+                                 uint32_t half) {
   char* p = static_cast<char*>(base);
   MergeScratch sc{};
+  sc.half = half;
   sc.spl = reinterpret_cast<unsigned long long*>(p);
   p += align_up((size_t)total_spl * 8);
   sc.bounds = reinterpret_cast<uint32_t*>(p);
@@ -341,15 +348,25 @@ cudaError_t run_merge_device(int S, uint32_t total_spl, uint32_t total_tiles,
                              const MergeScratch& sc, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(sc.clook, 0, sc.zero_bytes, stream);
   if (e != cudaSuccess) return e;
-  k_merge_init<<<(S + 127) / 128, 128, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles);
+  if (sc.half != 512 && sc.half != 1024 && sc.half != 2048) return cudaErrorInvalidValue;
+  k_merge_init<<<(S + 127) / 128, 128, 0, stream>>>(sc.pairs, S, sc.half, sc.bounds, sc.ntiles);
   count_launch(total_spl > 0 ? 4 : 2);
   if (total_spl > 0) {
-    k_merge_spl<<<(total_spl + 255) / 256, 256, 0, stream>>>(sc.pairs, S, total_spl, sc.spl);
-    k_merge_bounds<<<(total_spl + 255) / 256, 256, 0, stream>>>(sc.pairs, S, total_spl, sc.spl,
-                                                               sc.bounds);
+    k_merge_spl<<<(total_spl + 255) / 256, 256, 0, stream>>>(sc.pairs, S, total_spl, sc.half,
+                                                            sc.spl);
+    k_merge_bounds<<<(total_spl + 255) / 256, 256, 0, stream>>>(sc.pairs, S, total_spl, sc.half,
+                                                               sc.spl, sc.bounds);
   }
-  k_merge_tiles<<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles,
-                                                      sc.clook, sc.counter);
+  if (sc.half == 512) {
+    k_merge_tiles<512><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles,
+                                                             sc.clook, sc.counter);
+  } else if (sc.half == 1024) {
+    k_merge_tiles<1024><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles,
+                                                              sc.clook, sc.counter);
+  } else {
+    k_merge_tiles<2048><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles,
+                                                              sc.clook, sc.counter);
+  }
   return cudaGetLastError();
 }
 

@@ -9,6 +9,7 @@
 // Every kernel works on a batch of segments (clouds); a tile never spans two
 // segments and look-back chains stop at the segment's first tile.
 #include <algorithm>
+#include <mutex>
 
 #include "k_compact.cuh"
 
@@ -50,13 +51,15 @@ __global__ void k_seg_init(const SortSeg* __restrict__ segs, int S) {
   if (o.nlevels == 3) o.ptr2[0] = 0;
 }
 
-// Keys of the tiles [t0, t1) plus per-segment histograms of every pass.
-template <typename K>
+// Keys of the tiles [t0, t1) plus per-segment histograms of every pass
+// (digits of RB bits).
+template <typename K, int RB>
 __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restrict__ segs, int S,
                                                         uint32_t total_tiles,
                                                         uint32_t tiles_per_cta, K* keys0,
                                                         uint32_t* hist) {
-  __shared__ uint32_t s_hist[kMaxPasses][kRadix];
+  constexpr int R = 1 << RB;
+  __shared__ uint32_t s_hist[kMaxPasses][R];
   __shared__ float s_pts[kThreads * 3];
   __shared__ Window s_win;
   __shared__ uint32_t s_err;
@@ -64,17 +67,17 @@ __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restric
   const uint32_t t0 = blockIdx.x * tiles_per_cta;
   const uint32_t t1 = min(t0 + tiles_per_cta, total_tiles);
   if (t0 >= t1) return;
-  for (int i = tid; i < kMaxPasses * kRadix; i += kThreads) (&s_hist[0][0])[i] = 0;
+  for (int i = tid; i < kMaxPasses * R; i += kThreads) (&s_hist[0][0])[i] = 0;
   if (tid == 0) s_err = 0;
   __syncthreads();
   int cur = find_seg(segs, S, t0);
   auto flush = [&](int s) {
     __syncthreads();
     const uint32_t passes = segs[s].passes;
-    for (int i = tid; i < kMaxPasses * kRadix; i += kThreads) {
+    for (int i = tid; i < kMaxPasses * R; i += kThreads) {
       const uint32_t v = (&s_hist[0][0])[i];
-      if (v != 0 && (uint32_t)(i / kRadix) < passes) {
-        atomicAdd(hist + (size_t)s * kMaxPasses * kRadix + i, v);
+      if (v != 0 && (uint32_t)(i >> RB) < passes) {
+        atomicAdd(hist + (size_t)s * kMaxPasses * R + i, v);
       }
       (&s_hist[0][0])[i] = 0;
     }
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restric
           }
           out[c0 + tid] = key;
           for (uint32_t p = 0; p < passes; ++p) {
-            atomicAdd(&s_hist[p][(uint32_t)(key >> (sg.bit0 + p * kRadixBits)) & (kRadix - 1)], 1u);
+            atomicAdd(&s_hist[p][(uint32_t)(key >> (sg.bit0 + p * RB)) & (R - 1)], 1u);
           }
         }
       }
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restric
         }
         out[e] = key;
         for (uint32_t p = 0; p < passes; ++p) {
-          atomicAdd(&s_hist[p][(uint32_t)(key >> (sg.bit0 + p * kRadixBits)) & (kRadix - 1)], 1u);
+          atomicAdd(&s_hist[p][(uint32_t)(key >> (sg.bit0 + p * RB)) & (R - 1)], 1u);
         }
       }
       __syncthreads();
@@ -186,21 +189,31 @@ __device__ __forceinline__ T block_scan_th(T v, T& total, T* s_warp) {
   return before + inc - v;
 }
 
-// One LSD pass over digit `pass` of every segment that still needs it.  A
-// tile of kTile keys is TH threads x kTile/TH keys (warp-striped); threads
-// tid < kRadix own one digit each for the per-digit steps.
-template <typename K, int TH>
-__global__ void __launch_bounds__(TH) k_onesweep(const SortSeg* __restrict__ segs, int S,
+// Dynamic shared memory of one pass block: the tile's keys, per-warp digit
+// counts (u16), per-digit offsets and the warp scan words.
+template <typename K, int TH, int RB>
+constexpr size_t onesweep_smem() {
+  return (size_t)kTile * sizeof(K) + (size_t)(TH / 32) * (1 << RB) * 2 + (size_t)(1 << RB) * 4 +
+         (size_t)(TH / 32) * 4;
+}
+
+// One LSD pass over digit `pass` (RB bits) of every segment that still needs
+// it.  A tile of kTile keys is TH threads x kTile/TH keys (warp-striped);
+// threads tid < 2^RB own one digit each for the per-digit steps.
+template <typename K, int TH, int RB>
+__global__ void __launch_bounds__(TH, 2) k_onesweep(const SortSeg* __restrict__ segs, int S,
                                                  int pass, const K* __restrict__ in,
                                                  K* __restrict__ out,
                                                  const uint32_t* __restrict__ hist,
                                                  uint32_t* look, uint32_t* counter) {
-  constexpr int IT = kTile / TH, WARPS = TH / 32;
-  static_assert(IT * TH == kTile && TH >= kRadix, "tile shape");
-  __shared__ K s_keys[kTile];
-  __shared__ uint16_t s_wh[WARPS][kRadix];  // per-warp digit counts, then warp offsets
-  __shared__ uint32_t s_off[kRadix];
-  __shared__ uint32_t s_scan[WARPS];
+  constexpr int IT = kTile / TH, WARPS = TH / 32, R = 1 << RB;
+  static_assert(IT * TH == kTile && TH >= R, "tile shape");
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  K* s_keys = reinterpret_cast<K*>(s_raw);
+  uint16_t (*s_wh)[R] = reinterpret_cast<uint16_t (*)[R]>(s_raw + (size_t)kTile * sizeof(K));
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(s_raw + (size_t)kTile * sizeof(K) +
+                                                (size_t)WARPS * R * 2);
+  uint32_t* s_scan = s_off + R;
   __shared__ uint32_t s_tile;
   __shared__ int s_seg;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -209,7 +222,7 @@ __global__ void __launch_bounds__(TH) k_onesweep(const SortSeg* __restrict__ seg
     s_tile = t;
     s_seg = find_seg(segs, S, t);
   }
-  for (int i = tid; i < WARPS * kRadix; i += TH) (&s_wh[0][0])[i] = 0;
+  for (int i = tid; i < WARPS * R; i += TH) (&s_wh[0][0])[i] = 0;
   __syncthreads();
   const uint32_t t = s_tile;
   const int s = s_seg;
@@ -221,7 +234,7 @@ __global__ void __launch_bounds__(TH) k_onesweep(const SortSeg* __restrict__ seg
   if (start >= n) return;
   const uint32_t cnt = min((uint32_t)kTile, n - start);
   const K* src = in + sg.key_base + start;
-  const int shift = (int)sg.bit0 + pass * kRadixBits;
+  const int shift = (int)sg.bit0 + pass * RB;
 
   K k[IT];
   uint32_t dg[IT], rk[IT];
@@ -230,7 +243,7 @@ __global__ void __launch_bounds__(TH) k_onesweep(const SortSeg* __restrict__ seg
     const uint32_t e = (uint32_t)(w * 32 * IT + i * 32 + lane);
     const bool v = e < cnt;
     k[i] = v ? src[e] : (K)0;
-    dg[i] = v ? ((uint32_t)(k[i] >> shift) & (kRadix - 1)) : 0xffffffffu;
+    dg[i] = v ? ((uint32_t)(k[i] >> shift) & (R - 1)) : 0xffffffffu;
   }
   // warp-level ranking: lanes holding the same digit form one match group
   uint16_t* wh = s_wh[w];
@@ -239,18 +252,18 @@ __global__ void __launch_bounds__(TH) k_onesweep(const SortSeg* __restrict__ seg
   for (int i = 0; i < IT; ++i) {
     const uint32_t d = dg[i];
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t base = (d < (uint32_t)kRadix) ? wh[d] : 0u;
+    const uint32_t base = (d < (uint32_t)R) ? wh[d] : 0u;
     __syncwarp();
-    if (d < (uint32_t)kRadix && lane == __ffs(peers) - 1) wh[d] = (uint16_t)(base + __popc(peers));
+    if (d < (uint32_t)R && lane == __ffs(peers) - 1) wh[d] = (uint16_t)(base + __popc(peers));
     __syncwarp();
     rk[i] = base + __popc(peers & ltm);
   }
   __syncthreads();
   // per digit (thread tid == digit): warp offsets, tile count, publish
   const int d = tid;
-  const bool owner = tid < kRadix;
+  const bool owner = tid < R;
   uint32_t tile_cnt = 0;
-  uint32_t* my = look + (size_t)t * kRadix + d;
+  uint32_t* my = look + (size_t)t * R + d;
   if (owner) {
     for (int x = 0; x < WARPS; ++x) {
       const uint32_t v = s_wh[x][d];
@@ -261,21 +274,21 @@ __global__ void __launch_bounds__(TH) k_onesweep(const SortSeg* __restrict__ seg
   }
   uint32_t tot;
   const uint32_t bin_start = block_scan_th<TH>(owner ? tile_cnt : 0u, tot, s_scan);
-  const uint32_t hv = owner ? hist[((size_t)s * kMaxPasses + pass) * kRadix + d] : 0u;
+  const uint32_t hv = owner ? hist[((size_t)s * kMaxPasses + pass) * R + d] : 0u;
   const uint32_t dbase = block_scan_th<TH>(hv, tot, s_scan);
   if (owner) s_off[d] = bin_start;
   __syncthreads();
   bool bad = false;
 #pragma unroll
   for (int i = 0; i < IT; ++i) {
-    if (dg[i] < (uint32_t)kRadix) {
+    if (dg[i] < (uint32_t)R) {
       const uint32_t pos = s_off[dg[i]] + s_wh[w][dg[i]] + rk[i];
       if (pos < (uint32_t)kTile) s_keys[pos] = k[i]; else bad = true;
     }
   }
   uint32_t excl = 0;
   if (owner && lt > 0) {
-    excl = lookback(look + d, kRadix, t, sg.tile_base, &sg.out.hdr->err);
+    excl = lookback(look + d, R, t, sg.tile_base, &sg.out.hdr->err);
     st_relaxed(my, kFlagInc | ((excl + tile_cnt) & kValMask));
   }
   __syncthreads();
@@ -284,18 +297,12 @@ __global__ void __launch_bounds__(TH) k_onesweep(const SortSeg* __restrict__ seg
   K* dst = out + sg.key_base;
   for (uint32_t e = tid; e < cnt; e += TH) {
     const K key = s_keys[e];
-    const uint32_t pos = s_off[(uint32_t)(key >> shift) & (kRadix - 1)] + e;
+    const uint32_t pos = s_off[(uint32_t)(key >> shift) & (R - 1)] + e;
     if (pos < n) dst[pos] = key; else bad = true;
   }
   if (bad) atomicOr(&sg.out.hdr->err, kErrInternal);
 }
 
-// Threads per radix-pass block: 512 x 8 keys per tile (half the registers per
-// thread and twice the resident warps of 256 x 16).
-template <typename K>
-struct PassShape {
-  static constexpr int kTh = 512;
-};
 
 template <typename K, int LEVELS>
 __global__ void __launch_bounds__(kThreads) k_compact(const SortSeg* __restrict__ segs, int S,
@@ -336,12 +343,14 @@ size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 }  // namespace
 
-size_t sort_scratch_bytes(uint64_t total_keys, uint32_t total_tiles, int S, bool key64) {
+size_t sort_scratch_bytes(uint64_t total_keys, uint32_t total_tiles, int S, bool key64,
+                          uint32_t radix_bits) {
   const size_t ks = key64 ? 8 : 4;
+  const size_t R = (size_t)1 << radix_bits;
   size_t b = 0;
   b += align_up(total_keys * ks) * 2;
-  b += align_up((size_t)S * kMaxPasses * kRadix * 4);
-  b += align_up((size_t)kMaxPasses * total_tiles * kRadix * 4);
+  b += align_up((size_t)S * kMaxPasses * R * 4);
+  b += align_up((size_t)kMaxPasses * total_tiles * R * 4);
   b += align_up((size_t)total_tiles * 3 * 4);
   b += align_up((kMaxPasses + 1) * 4);
   b += align_up((size_t)S * sizeof(SortSeg));
@@ -349,19 +358,22 @@ size_t sort_scratch_bytes(uint64_t total_keys, uint32_t total_tiles, int S, bool
 }
 
 SortScratch sort_scratch_carve(void* base, uint64_t total_keys, uint32_t total_tiles, int S,
-                               bool key64) {
+                               bool key64, const Tuning& tu) {
   const size_t ks = key64 ? 8 : 4;
+  const size_t R = (size_t)1 << tu.radix_bits;
   char* p = static_cast<char*>(base);
   SortScratch sc{};
+  sc.radix_bits = tu.radix_bits;
+  sc.sort_threads = tu.sort_threads;
   sc.keys0 = p;
   p += align_up(total_keys * ks);
   sc.keys1 = p;
   p += align_up(total_keys * ks);
   char* z0 = p;
   sc.hist = reinterpret_cast<uint32_t*>(p);
-  p += align_up((size_t)S * kMaxPasses * kRadix * 4);
+  p += align_up((size_t)S * kMaxPasses * R * 4);
   sc.look = reinterpret_cast<uint32_t*>(p);
-  p += align_up((size_t)kMaxPasses * total_tiles * kRadix * 4);
+  p += align_up((size_t)kMaxPasses * total_tiles * R * 4);
   sc.clook = reinterpret_cast<uint32_t*>(p);
   p += align_up((size_t)total_tiles * 3 * 4);
   sc.counters = reinterpret_cast<uint32_t*>(p);
@@ -382,24 +394,60 @@ int device_sm_count() {
   return sms;
 }
 
-template <typename K>
-static void launch_passes(int S, uint32_t total_tiles, uint32_t max_passes, const SortScratch& sc,
-                          cudaStream_t stream) {
+template <typename K, int TH, int RB>
+static cudaError_t set_pass_smem() {
+  return cudaFuncSetAttribute(k_onesweep<K, TH, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)onesweep_smem<K, TH, RB>());
+}
+
+template <typename K, int TH, int RB>
+static void launch_shape(int S, uint32_t total_tiles, uint32_t max_passes, const SortScratch& sc,
+                         cudaStream_t stream) {
   K* k0 = static_cast<K*>(sc.keys0);
   K* k1 = static_cast<K*>(sc.keys1);
+  constexpr size_t smem = onesweep_smem<K, TH, RB>();
   for (uint32_t p = 0; p < max_passes; ++p) {
     const K* in = (p & 1) ? k1 : k0;
     K* out = (p & 1) ? k0 : k1;
-    k_onesweep<K, PassShape<K>::kTh><<<total_tiles, PassShape<K>::kTh, 0, stream>>>(
-        sc.segs, S, (int)p, in, out, sc.hist, sc.look + (size_t)p * total_tiles * kRadix,
+    k_onesweep<K, TH, RB><<<total_tiles, TH, smem, stream>>>(
+        sc.segs, S, (int)p, in, out, sc.hist, sc.look + ((size_t)p * total_tiles << RB),
         sc.counters + p);
   }
   count_launch(max_passes);
 }
 
+template <typename K>
+static void launch_passes(int S, uint32_t total_tiles, uint32_t max_passes, const SortScratch& sc,
+                          cudaStream_t stream) {
+  if (sc.radix_bits == 9) {
+    launch_shape<K, 512, 9>(S, total_tiles, max_passes, sc, stream);
+  } else if (sc.sort_threads == 256) {
+    launch_shape<K, 256, 8>(S, total_tiles, max_passes, sc, stream);
+  } else {
+    launch_shape<K, 512, 8>(S, total_tiles, max_passes, sc, stream);
+  }
+}
+
+cudaError_t init_sort_kernels() {
+  static std::once_flag once;
+  static cudaError_t rc = cudaSuccess;
+  std::call_once(once, [] {
+    const cudaError_t es[] = {
+        set_pass_smem<uint32_t, 256, 8>(),           set_pass_smem<uint32_t, 512, 8>(),
+        set_pass_smem<uint32_t, 512, 9>(),           set_pass_smem<unsigned long long, 256, 8>(),
+        set_pass_smem<unsigned long long, 512, 8>(), set_pass_smem<unsigned long long, 512, 9>()};
+    for (cudaError_t e : es) {
+      if (e != cudaSuccess && rc == cudaSuccess) rc = e;
+    }
+  });
+  return rc;
+}
+
 cudaError_t run_radix_passes(int S, uint32_t total_tiles, uint32_t max_passes, bool key64,
                              const SortScratch& sc, cudaStream_t stream) {
   if (total_tiles == 0) return cudaSuccess;
+  const cudaError_t ei = init_sort_kernels();
+  if (ei != cudaSuccess) return ei;
   if (key64) {
     launch_passes<unsigned long long>(S, total_tiles, max_passes, sc, stream);
   } else {
@@ -415,7 +463,13 @@ static cudaError_t launch_pipeline(int S, uint32_t total_tiles, uint32_t max_pas
   K* k1 = static_cast<K*>(sc.keys1);
   const uint32_t ctas = std::min<uint32_t>(total_tiles, (uint32_t)device_sm_count() * 4);
   const uint32_t per = (total_tiles + ctas - 1) / ctas;
-  k_keys_hist<K><<<ctas, kThreads, 0, stream>>>(sc.segs, S, total_tiles, per, k0, sc.hist);
+  const cudaError_t ei = init_sort_kernels();
+  if (ei != cudaSuccess) return ei;
+  if (sc.radix_bits == 9) {
+    k_keys_hist<K, 9><<<ctas, kThreads, 0, stream>>>(sc.segs, S, total_tiles, per, k0, sc.hist);
+  } else {
+    k_keys_hist<K, 8><<<ctas, kThreads, 0, stream>>>(sc.segs, S, total_tiles, per, k0, sc.hist);
+  }
   count_launch(2);
   launch_passes<K>(S, total_tiles, max_passes, sc, stream);
   if (levels == 3) {
@@ -464,8 +518,10 @@ cudaError_t run_wait_selftest(void* scratch, cudaStream_t stream) {
     e = cudaMemcpyAsync(sc.counters, &first_id, sizeof(uint32_t), cudaMemcpyHostToDevice, stream);
   }
   if (e != cudaSuccess) return e;
-  k_onesweep<unsigned long long, PassShape<unsigned long long>::kTh>
-      <<<1, PassShape<unsigned long long>::kTh, 0, stream>>>(
+  e = init_sort_kernels();
+  if (e != cudaSuccess) return e;
+  k_onesweep<unsigned long long, 512, 8>
+      <<<1, 512, onesweep_smem<unsigned long long, 512, 8>(), stream>>>(
       sc.segs, 1, 0, static_cast<const unsigned long long*>(sc.keys0),
       static_cast<unsigned long long*>(sc.keys1), sc.hist, sc.look, sc.counters);
   count_launch(1);
