@@ -139,13 +139,17 @@ def start_clocks(local_rank):
 
 
 def timed(torch, fn, flush=None, tag=0.0):
-    """Device time (ms) of fn() with CUDA events on the current stream."""
+    """Device time (ms) of fn() with CUDA events on the current stream.  The
+    launches of fn() sit in an NVTX range "cga_step" (ncu --nvtx-include
+    "cga_step/" selects exactly the timed steps' kernels)."""
     if flush is not None:
         flush.fill_(tag)
     s = torch.cuda.Event(enable_timing=True)
     e = torch.cuda.Event(enable_timing=True)
     s.record()
+    torch.cuda.nvtx.range_push("cga_step")
     fn()
+    torch.cuda.nvtx.range_pop()
     e.record()
     e.synchronize()
     return s.elapsed_time(e)

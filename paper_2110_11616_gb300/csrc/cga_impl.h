@@ -150,7 +150,6 @@ struct MergePair {
 };
 
 struct MergeScratch {
-  unsigned long long* spl;  // [total_spl]
   uint32_t* bounds;         // [(total_tiles + S) * 2]; pair p at 2 * (tile_base + p)
   uint32_t* ntiles;         // [S]
   uint32_t* clook;          // [total_tiles][3]

@@ -11,26 +11,30 @@ size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // ------------------------------------------------------------------ decode
 // Lossless inverse of the build: the walk X -> Y -> Z of Sec. III-A, done per
-// tile of Z positions (each position finds its column and slab by binary
-// search inside the tile's window).
+// tile of Z positions (the tile's window is expanded into per-position column
+// and slab indices in shared memory).
 __global__ void __launch_bounds__(kThreads) k_decode(Levels a, uint32_t* __restrict__ xyz) {
   __shared__ Window s_win;
+  __shared__ uint16_t s_col[kTile], s_slab[kTile];
+  __shared__ uint32_t s_warp[kWarps];
   const uint32_t u = (uint32_t)a.hdr->cnt[0];
   const uint32_t start = blockIdx.x * kTile;
   if (start >= u) return;
   const uint32_t cnt = min((uint32_t)kTile, u - start);
-  if (threadIdx.x == 0) {
-    s_win = window_of(a, (uint32_t)a.hdr->cnt[1], (uint32_t)a.hdr->cnt[2], start, start + cnt - 1);
+  if (threadIdx.x < 32) {
+    const Window wv =
+        warp_window_of(a, (uint32_t)a.hdr->cnt[1], (uint32_t)a.hdr->cnt[2], start, start + cnt - 1);
+    if (threadIdx.x == 0) s_win = wv;
   }
   __syncthreads();
   const Window w = s_win;
+  expand_window(a, w, start, cnt, s_col, s_slab, s_warp);
   for (uint32_t e = threadIdx.x; e < cnt; e += kThreads) {
-    uint32_t x, y, z;
-    point_at(a, w, start + e, x, y, z);
+    const uint32_t cr = s_col[e];
     uint32_t* o = xyz + (size_t)(start + e) * 3;
-    o[0] = x;
-    o[1] = y;
-    o[2] = z;
+    o[0] = __ldg(a.idx2 + w.x0 + s_slab[cr]);
+    o[1] = __ldg(a.idx1 + w.c0 + cr);
+    o[2] = __ldg(a.idx0 + start + e);
   }
 }
 
@@ -81,64 +85,41 @@ __global__ void k_merge_init(const MergePair* __restrict__ pairs, int S, uint32_
   P.out.ptr2[0] = 0;
 }
 
-// Splitter keys: every half-th point of A, then of B.
-__global__ void k_merge_spl(const MergePair* __restrict__ pairs, int S, uint32_t total,
-                            uint32_t half, unsigned long long* spl) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= total) return;
-  const MergePair& P = pairs[find_pair_spl(pairs, S, i)];
-  const uint32_t local = i - P.spl_base;
-  const bool isA = local < P.spl_a;
-  const Levels& L = isA ? P.a : P.b;
-  const uint32_t k = isA ? local : local - P.spl_a;
-  const uint32_t u = (uint32_t)L.hdr->cnt[0];
-  const uint32_t pos = (k + 1) * half;
-  spl[i] = (pos < u) ? key_at(L, (uint32_t)L.hdr->cnt[1], (uint32_t)L.hdr->cnt[2], pos)
-                     : ~0ull;
-}
-
-// Tile bounds: each splitter s becomes the cut (rank_A(s), rank_B(s)) at its
-// place in the key order of all splitters.
-__global__ void k_merge_bounds(const MergePair* __restrict__ pairs, int S, uint32_t total,
-                               uint32_t half, const unsigned long long* __restrict__ spl,
-                               uint32_t* bounds) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+// Tile cuts, one warp per splitter.  Splitter k of A is A's key s at
+// position (k + 1) * half; its cut is (rank_A(s), rank_B(s)) = ((k + 1) *
+// half, #B keys < s), and its place among all splitters (A's before B's on
+// equal keys) is k + #B splitters < s, where B splitter j (the key at
+// (j + 1) * half) is below s exactly when (j + 1) * half < rank_B(s).  B's
+// splitters mirror this with #A keys <= s.  The Sec. III-A lookup gives the
+// ranks.
+__global__ void k_merge_cuts(const MergePair* __restrict__ pairs, int S, uint32_t total,
+                             uint32_t half, uint32_t* bounds) {
+  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
   if (i >= total) return;
   const int p = find_pair_spl(pairs, S, i);
   const MergePair& P = pairs[p];
   const uint32_t local = i - P.spl_base;
   const uint32_t uA = (uint32_t)P.a.hdr->cnt[0], uB = (uint32_t)P.b.hdr->cnt[0];
   const uint32_t NA = n_splitters(uA, P.spl_a, half), NB = n_splitters(uB, P.spl_b, half);
-  const unsigned long long* sa = spl + P.spl_base;
-  const unsigned long long* sb = sa + P.spl_a;
-  const unsigned long long s = spl[i];
-  uint32_t pos, ca, cb;
-  if (local < P.spl_a) {
-    const uint32_t k = local;
-    if (k >= NA) return;
-    uint32_t lo = 0, hi = NB;  // B splitters < s
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (sb[mid] < s) lo = mid + 1; else hi = mid;
-    }
-    pos = k + lo;
-    ca = (k + 1) * half;
-    cb = rank_of(P.b, (uint32_t)P.b.hdr->cnt[2], s);
-  } else {
-    const uint32_t k = local - P.spl_a;
-    if (k >= NB) return;
-    uint32_t lo = 0, hi = NA;  // A splitters <= s
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (sa[mid] <= s) lo = mid + 1; else hi = mid;
-    }
-    pos = k + lo;
-    ca = rank_of(P.a, (uint32_t)P.a.hdr->cnt[2], s);
-    cb = (k + 1) * half;
+  const bool isA = local < P.spl_a;
+  const uint32_t k = isA ? local : local - P.spl_a;
+  if (k >= (isA ? NA : NB)) return;
+  const Levels& own = isA ? P.a : P.b;
+  const Levels& oth = isA ? P.b : P.a;
+  const unsigned long long s =
+      warp_key_at(own, (uint32_t)own.hdr->cnt[1], (uint32_t)own.hdr->cnt[2], (k + 1) * half);
+  bool found = false;
+  const uint32_t r = warp_rank_of(oth, (uint32_t)oth.hdr->cnt[2], s, &found);
+  // other-side splitters before this one: below s (A's turn), or at most s (B's)
+  const uint32_t rk = isA ? r : r + (found ? 1u : 0u);
+  const uint32_t before = rk > 0 ? min(isA ? NB : NA, (rk - 1) / half) : 0u;
+  const uint32_t pos = k + before;
+  if (lane == 0) {
+    uint32_t* bnd = bounds + 2 * ((size_t)P.tile_base + p);
+    bnd[2 * (pos + 1)] = isA ? (k + 1) * half : r;
+    bnd[2 * (pos + 1) + 1] = isA ? r : (k + 1) * half;
   }
-  uint32_t* bnd = bounds + 2 * ((size_t)P.tile_base + p);
-  bnd[2 * (pos + 1)] = ca;
-  bnd[2 * (pos + 1) + 1] = cb;
 }
 
 // Merge one tile: decode both runs (at most MH points each) into shared
@@ -152,9 +133,11 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
   constexpr int IT = 2 * MH / kThreads;  // merged keys per thread
   static_assert(IT * kThreads == 2 * MH && 2 * MH <= kTile, "merge tile shape");
   __shared__ unsigned long long s_ab[2 * MH];
+  __shared__ uint16_t s_col[MH], s_slab[MH];
+  __shared__ uint32_t s_warp[kWarps];
   __shared__ CompactSmem sm;
   __shared__ Window s_wa, s_wb;
-  __shared__ unsigned long long s_prev;
+  __shared__ unsigned long long s_prev, s_prev2[2];
   __shared__ uint32_t s_tile, s_has_prev;
   __shared__ int s_p;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -180,40 +163,54 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
   }
   const uint32_t gA = (uint32_t)P.a.hdr->cnt[1], hA = (uint32_t)P.a.hdr->cnt[2];
   const uint32_t gB = (uint32_t)P.b.hdr->cnt[1], hB = (uint32_t)P.b.hdr->cnt[2];
+  // the tile's windows in both inputs and the key just before it: four
+  // independent warp-cooperative searches
+  if (w == 0) {
+    if (bad && lane == 0) atomicOr(&P.out.hdr->err, kErrInternal);
+    if (na) {
+      const Window wa = warp_window_of(P.a, gA, hA, a0, a1 - 1);
+      if (lane == 0) s_wa = wa;
+    }
+  } else if (w == 1) {
+    if (nb) {
+      const Window wb = warp_window_of(P.b, gB, hB, b0, b1 - 1);
+      if (lane == 0) s_wb = wb;
+    }
+  } else if (w == 2) {
+    const unsigned long long ka = a0 > 0 ? warp_key_at(P.a, gA, hA, a0 - 1) : 0ull;
+    if (lane == 0) s_prev2[0] = ka;
+  } else if (w == 3) {
+    const unsigned long long kb = b0 > 0 ? warp_key_at(P.b, gB, hB, b0 - 1) : 0ull;
+    if (lane == 0) s_prev2[1] = kb;
+  }
+  __syncthreads();
   if (tid == 0) {
-    if (bad) atomicOr(&P.out.hdr->err, kErrInternal);
-    if (na) s_wa = window_of(P.a, gA, hA, a0, a1 - 1);
-    if (nb) s_wb = window_of(P.b, gB, hB, b0, b1 - 1);
-    unsigned long long pk = 0;
-    uint32_t has = 0;
-    if (a0 > 0) {
-      pk = key_at(P.a, gA, hA, a0 - 1);
-      has = 1;
-    }
-    if (b0 > 0) {
-      const unsigned long long kb = key_at(P.b, gB, hB, b0 - 1);
-      pk = has ? max(pk, kb) : kb;
-      has = 1;
-    }
-    s_prev = pk;
-    s_has_prev = has;
+    // the predecessor key of the merged run is the larger of the two
+    s_prev = max(a0 > 0 ? s_prev2[0] : 0ull, b0 > 0 ? s_prev2[1] : 0ull);
+    s_has_prev = (a0 > 0 || b0 > 0) ? 1u : 0u;
   }
   __syncthreads();
   const uint32_t bA = P.a.bits;
+  // decode both runs (tile-uniform branches: the window expansion has barriers)
   if (na) {
     const Window wa = s_wa;
+    expand_window(P.a, wa, a0, na, s_col, s_slab, s_warp);
     for (uint32_t e = tid; e < na; e += kThreads) {
-      uint32_t x, y, z;
-      point_at(P.a, wa, a0 + e, x, y, z);
-      s_ab[e] = ((unsigned long long)x << (2 * bA)) | ((unsigned long long)y << bA) | z;
+      const uint32_t cr = s_col[e];
+      const uint32_t x = __ldg(P.a.idx2 + wa.x0 + s_slab[cr]), y = __ldg(P.a.idx1 + wa.c0 + cr);
+      s_ab[e] = ((unsigned long long)x << (2 * bA)) | ((unsigned long long)y << bA) |
+                __ldg(P.a.idx0 + a0 + e);
     }
+    __syncthreads();
   }
   if (nb) {
     const Window wb = s_wb;
+    expand_window(P.b, wb, b0, nb, s_col, s_slab, s_warp);
     for (uint32_t e = tid; e < nb; e += kThreads) {
-      uint32_t x, y, z;
-      point_at(P.b, wb, b0 + e, x, y, z);
-      s_ab[MH + e] = ((unsigned long long)x << (2 * bA)) | ((unsigned long long)y << bA) | z;
+      const uint32_t cr = s_col[e];
+      const uint32_t x = __ldg(P.b.idx2 + wb.x0 + s_slab[cr]), y = __ldg(P.b.idx1 + wb.c0 + cr);
+      s_ab[MH + e] = ((unsigned long long)x << (2 * bA)) | ((unsigned long long)y << bA) |
+                     __ldg(P.b.idx0 + b0 + e);
     }
   }
   __syncthreads();
@@ -313,8 +310,8 @@ cudaError_t run_decode(const Levels& a, uint32_t* xyz, cudaStream_t stream) {
 }
 
 size_t merge_scratch_bytes(uint32_t total_spl, uint32_t total_tiles, int S) {
+  (void)total_spl;
   size_t b = 0;
-  b += align_up((size_t)total_spl * 8);
   b += align_up(((size_t)total_tiles + S) * 2 * 4 + 8);
   b += align_up((size_t)S * 4);
   b += align_up((size_t)total_tiles * 3 * 4);
@@ -328,8 +325,7 @@ MergeScratch merge_scratch_carve(void* base, uint32_t total_spl, uint32_t total_
   char* p = static_cast<char*>(base);
   MergeScratch sc{};
   sc.half = half;
-  sc.spl = reinterpret_cast<unsigned long long*>(p);
-  p += align_up((size_t)total_spl * 8);
+  (void)total_spl;
   sc.bounds = reinterpret_cast<uint32_t*>(p);
   p += align_up(((size_t)total_tiles + S) * 2 * 4 + 8);
   sc.ntiles = reinterpret_cast<uint32_t*>(p);
@@ -350,12 +346,10 @@ cudaError_t run_merge_device(int S, uint32_t total_spl, uint32_t total_tiles,
   if (e != cudaSuccess) return e;
   if (sc.half != 512 && sc.half != 1024 && sc.half != 2048) return cudaErrorInvalidValue;
   k_merge_init<<<(S + 127) / 128, 128, 0, stream>>>(sc.pairs, S, sc.half, sc.bounds, sc.ntiles);
-  count_launch(total_spl > 0 ? 4 : 2);
+  count_launch(total_spl > 0 ? 3 : 2);
   if (total_spl > 0) {
-    k_merge_spl<<<(total_spl + 255) / 256, 256, 0, stream>>>(sc.pairs, S, total_spl, sc.half,
-                                                            sc.spl);
-    k_merge_bounds<<<(total_spl + 255) / 256, 256, 0, stream>>>(sc.pairs, S, total_spl, sc.half,
-                                                               sc.spl, sc.bounds);
+    k_merge_cuts<<<(total_spl + 7) / 8, 256, 0, stream>>>(sc.pairs, S, total_spl, sc.half,
+                                                         sc.bounds);
   }
   if (sc.half == 512) {
     k_merge_tiles<512><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles,

@@ -62,6 +62,8 @@ __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restric
   __shared__ uint32_t s_hist[kMaxPasses][R];
   __shared__ float s_pts[kThreads * 3];
   __shared__ Window s_win;
+  __shared__ uint16_t s_col[kTile], s_slab[kTile];
+  __shared__ uint32_t s_warp[kWarps];
   __shared__ uint32_t s_err;
   const int tid = threadIdx.x;
   const uint32_t t0 = blockIdx.x * tiles_per_cta;
@@ -140,15 +142,19 @@ __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restric
     } else {
       // projection: decode the source point, keep two axes
       const Levels& a = sg.src;
-      if (tid == 0) {
-        s_win = window_of(a, (uint32_t)a.hdr->cnt[1], (uint32_t)a.hdr->cnt[2], start,
-                          start + cnt - 1);
+      if (tid < 32) {
+        const Window wv = warp_window_of(a, (uint32_t)a.hdr->cnt[1], (uint32_t)a.hdr->cnt[2],
+                                         start, start + cnt - 1);
+        if (tid == 0) s_win = wv;
       }
       __syncthreads();
       const Window win = s_win;
+      expand_window(a, win, start, cnt, s_col, s_slab, s_warp);
       for (uint32_t e = tid; e < cnt; e += kThreads) {
-        uint32_t x, y, z;
-        point_at(a, win, start + e, x, y, z);
+        const uint32_t cr = s_col[e];
+        const uint32_t x = __ldg(a.idx2 + win.x0 + s_slab[cr]);
+        const uint32_t y = __ldg(a.idx1 + win.c0 + cr);
+        const uint32_t z = __ldg(a.idx0 + start + e);
         K key;
         if (sg.plane == 3) {
           const uint32_t L = sg.shift;
