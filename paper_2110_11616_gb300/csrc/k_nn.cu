@@ -234,6 +234,29 @@ __device__ void visit_cell_column(const NnSeg& sg, uint32_t c, uint32_t cy,
 template <int K>
 __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t ylo,
                              uint32_t ysz, const Qry& q, Best& best) {
+  if constexpr (K == 0) {
+    // the fine columns of one cell: few enough that a plain ascending scan
+    // with the bound test per slab and per column beats ordering them
+    const Levels& a = sg.a;
+    const uint32_t b = a.bits;
+    for (uint32_t xi = x0; xi < x1; ++xi) {
+      const uint32_t x = __ldg(a.idx2 + xi);
+      const unsigned long long dx = absdiff(x, q.x);
+      const unsigned long long dx2 = dx * dx;
+      if (dx2 > best.d2) continue;
+      const uint32_t ys = __ldg(a.ptr2 + xi), ye = __ldg(a.ptr2 + xi + 1);
+      const unsigned long long kx = (unsigned long long)x << (2 * b);
+      for (uint32_t c = lower_bound_u16(a.idx1, ys, ye, ylo); c < ye; ++c) {
+        const uint32_t y = __ldg(a.idx1 + c);
+        if (y >= ylo + ysz) break;
+        const unsigned long long dy = absdiff(y, q.y);
+        const unsigned long long dxy = dx2 + dy * dy;
+        if (dxy > best.d2) continue;
+        visit_column(a, c, kx | ((unsigned long long)y << b), dxy, q.z, q.cz, best);
+      }
+    }
+    return;
+  }
   const Levels& L = level<K>(sg);
   const uint32_t sh = level_shift<K>(sg), cell = 1u << sh;
   const uint32_t qyc = q.cy >> sh;
