@@ -357,10 +357,11 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
         },
         "roofline": {"kernel": "k_nn_warp (NN search)", "bound": "hbm",
                      "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 5), "traffic": 30_666_688,
+                     "frac": round(achieved / peak, 5), "traffic": 31_919_360,
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "note": "latency-bound search: ncu shows L1 throughput 62.5% of peak, "
-                             "DRAM 0.09%; traffic = ncu dram read+write of one launch"},
+                             "DRAM 0.09%; traffic = ncu dram read+write of one launch of the "
+                             "timed step (profiles/launches_lidar_frame_set.md)"},
         "e2e": {"value": round(e2e_val, 3), "unit": "Mpts/s",
                 "h2d_bytes_per_step": P.bytes_in(), "d2h_bytes_per_step": P.bytes_out()},
         "plain": {"ms_per_step": round(float(np.mean(plain_ms)), 4),
