@@ -32,6 +32,7 @@ struct cga {
   uint32_t* xs[libcga::kMaxCoarse] = {};
   uint32_t cshift[libcga::kMaxCoarse] = {};
   uint32_t* cxdir[libcga::kMaxCoarse] = {};
+  uint32_t* czr[libcga::kMaxCoarse] = {};
   // x directory of this CGA for NN (cga_nn_prepare): first X_index entry >= v
   void* xdmem = nullptr;
   uint32_t* xdir = nullptr;
@@ -219,6 +220,7 @@ void attach_coarse(const cga* a, libcga::NnSeg& seg) {
     seg.xs[k] = a->xs[k];
     seg.shift[k] = a->cshift[k];
     seg.cxdir[k] = a->cxdir[k];
+    seg.zr[k] = a->czr[k];
   }
 }
 
@@ -456,6 +458,7 @@ void drop_coarse(cga* a) {
     a->clv[k] = Levels{};
     a->xs[k] = nullptr;
     a->cxdir[k] = nullptr;
+    a->czr[k] = nullptr;
     a->cshift[k] = 0;
   }
   a->ncoarse = 0;
@@ -474,11 +477,13 @@ int build_coarse_level(cga* a, int k, uint32_t shift, cudaStream_t s) {
   const uint64_t cap2 = std::min<uint64_t>(cap, pow2(bc));
   const size_t lb = levels_bytes(cap, cap1, cap2, 3);
   const size_t xsb = align_up((cap2 + 1) * 4);
-  void* mem = dalloc(A, lb + xsb + align_up(((size_t)pow2(bc) + 1) * 4), s);
+  const size_t xdb = align_up(((size_t)pow2(bc) + 1) * 4);
+  void* mem = dalloc(A, lb + xsb + xdb + align_up(cap1 * 4), s);
   if (mem == nullptr) return CGA_ERR_OOM;
   const Levels clv = levels_carve(mem, bc, cap, cap1, cap2, 3);
   uint32_t* xs = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb);
   uint32_t* cxdir = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb + xsb);
+  uint32_t* czr = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb + xsb + xdb);
   libcga::SortSeg seg{};
   seg.src = fine;
   seg.plane = 3;
@@ -501,6 +506,7 @@ int build_coarse_level(cga* a, int k, uint32_t shift, cudaStream_t s) {
     cudaError_t e = libcga::run_sort_pipeline(&seg, 1, tiles, seg.passes, key64, sc, s);
     if (e == cudaSuccess) e = libcga::run_coarse_slab_index(fine, clv, dsh, xs, s);
     if (e == cudaSuccess) e = libcga::run_x_directory(clv, cxdir, s);
+    if (e == cudaSuccess) e = libcga::run_column_zrange(clv, czr, s);
     rc = cuda_rc(e);
     dfree(A, a->has_alloc, scratch, s);
   }
@@ -513,6 +519,7 @@ int build_coarse_level(cga* a, int k, uint32_t shift, cudaStream_t s) {
   a->xs[k] = xs;
   a->cshift[k] = shift;
   a->cxdir[k] = cxdir;
+  a->czr[k] = czr;
   a->ncoarse = (uint32_t)k + 1;
   return CGA_OK;
 }

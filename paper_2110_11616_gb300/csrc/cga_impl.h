@@ -193,6 +193,8 @@ struct NnSeg {
   const uint32_t* xs[kMaxCoarse];
   uint32_t shift[kMaxCoarse];
   const uint32_t* cxdir[kMaxCoarse];
+  // zr[k][c] = lowest | highest << 16 cell z of column c of c[k] (or null)
+  const uint32_t* zr[kMaxCoarse];
   uint32_t ncoarse;
   // optional x directory of `a` (cga_nn_prepare): for every x value v of the
   // grid, the index of the first X_index entry >= v
@@ -240,6 +242,9 @@ cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaSt
 cudaError_t run_coarse_slab_index(const Levels& a, const Levels& c, uint32_t shift, uint32_t* xs,
                                   cudaStream_t stream);
 
+// zr[c] = Z_index[Y_pointer[c]] | Z_index[Y_pointer[c + 1] - 1] << 16 for every column c
+// of a (a.cap1 entries reserved).
+cudaError_t run_column_zrange(const Levels& a, uint32_t* zr, cudaStream_t stream);
 // xdir[v] = first index of a's X_index with value >= v, for v in [0, 2^bits].
 cudaError_t run_x_directory(const Levels& a, uint32_t* xdir, cudaStream_t stream);
 

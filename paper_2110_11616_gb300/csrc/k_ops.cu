@@ -260,6 +260,18 @@ __global__ void k_coarse_slab_index(Levels a, Levels c, uint32_t shift, uint32_t
   }
 }
 
+// ------------------------------------------------------- column z range
+// Lowest and highest z of every column: a bound that needs no search when
+// the query lies below or above the whole column.
+__global__ void k_column_zrange(Levels a, uint32_t* zr) {
+  const uint32_t g = (uint32_t)a.hdr->cnt[1];
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < g; c += stride) {
+    const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
+    zr[c] = (uint32_t)__ldg(a.idx0 + zs) | ((uint32_t)__ldg(a.idx0 + ze - 1) << 16);
+  }
+}
+
 // ------------------------------------------------------------ x directory
 // The dense per-x-value table of G-Arrays (Sec. III), here only as a lookup
 // accelerator: xdir[v] = number of stored x values below v.
@@ -387,6 +399,15 @@ cudaError_t run_coarse_slab_index(const Levels& a, const Levels& c, uint32_t shi
   const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
                                                        (uint64_t)device_sm_count() * 8);
   k_coarse_slab_index<<<blocks, 256, 0, stream>>>(a, c, shift, xs);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t run_column_zrange(const Levels& a, uint32_t* zr, cudaStream_t stream) {
+  const uint64_t work = std::max<uint64_t>(a.cap1, 1);
+  const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
+                                                       (uint64_t)device_sm_count() * 8);
+  k_column_zrange<<<blocks, 256, 0, stream>>>(a, zr);
   count_launch(1);
   return cudaGetLastError();
 }
