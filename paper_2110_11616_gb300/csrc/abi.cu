@@ -33,6 +33,7 @@ struct cga {
   uint32_t cshift[libcga::kMaxCoarse] = {};
   uint32_t* cxdir[libcga::kMaxCoarse] = {};
   uint32_t* czr[libcga::kMaxCoarse] = {};
+  uint32_t* cchild[libcga::kMaxCoarse] = {};
   // x directory of this CGA for NN (cga_nn_prepare): first X_index entry >= v
   void* xdmem = nullptr;
   uint32_t* xdir = nullptr;
@@ -221,6 +222,7 @@ void attach_coarse(const cga* a, libcga::NnSeg& seg) {
     seg.shift[k] = a->cshift[k];
     seg.cxdir[k] = a->cxdir[k];
     seg.zr[k] = a->czr[k];
+    seg.child[k] = a->cchild[k];
   }
 }
 
@@ -449,6 +451,7 @@ libcga::NnSeg nn_segment(const cga_t* a, const float* d_q, uint64_t m, uint32_t*
 namespace {
 
 static_assert(libcga::kMaxCoarse == CGA_NN_MAX_LEVELS, "coarse level count");
+constexpr size_t kChildTableMaxBytes = (size_t)512 << 20;
 
 void drop_coarse(cga* a) {
   const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
@@ -459,6 +462,7 @@ void drop_coarse(cga* a) {
     a->xs[k] = nullptr;
     a->cxdir[k] = nullptr;
     a->czr[k] = nullptr;
+    a->cchild[k] = nullptr;
     a->cshift[k] = 0;
   }
   a->ncoarse = 0;
@@ -478,12 +482,17 @@ int build_coarse_level(cga* a, int k, uint32_t shift, cudaStream_t s) {
   const size_t lb = levels_bytes(cap, cap1, cap2, 3);
   const size_t xsb = align_up((cap2 + 1) * 4);
   const size_t xdb = align_up(((size_t)pow2(bc) + 1) * 4);
-  void* mem = dalloc(A, lb + xsb + xdb + align_up(cap1 * 4), s);
+  const size_t zrb = align_up(cap1 * 4);
+  // child-column table: skipped (searched instead) when it would be large
+  const size_t chb = (cap1 << dsh) * 4 <= kChildTableMaxBytes ? align_up((cap1 << dsh) * 4) : 0;
+  void* mem = dalloc(A, lb + xsb + xdb + zrb + chb, s);
   if (mem == nullptr) return CGA_ERR_OOM;
   const Levels clv = levels_carve(mem, bc, cap, cap1, cap2, 3);
   uint32_t* xs = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb);
   uint32_t* cxdir = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb + xsb);
   uint32_t* czr = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb + xsb + xdb);
+  uint32_t* cchild =
+      chb ? reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb + xsb + xdb + zrb) : nullptr;
   libcga::SortSeg seg{};
   seg.src = fine;
   seg.plane = 3;
@@ -507,6 +516,9 @@ int build_coarse_level(cga* a, int k, uint32_t shift, cudaStream_t s) {
     if (e == cudaSuccess) e = libcga::run_coarse_slab_index(fine, clv, dsh, xs, s);
     if (e == cudaSuccess) e = libcga::run_x_directory(clv, cxdir, s);
     if (e == cudaSuccess) e = libcga::run_column_zrange(clv, czr, s);
+    if (e == cudaSuccess && cchild != nullptr) {
+      e = libcga::run_child_columns(fine, clv, xs, dsh, cchild, s);
+    }
     rc = cuda_rc(e);
     dfree(A, a->has_alloc, scratch, s);
   }
@@ -520,6 +532,7 @@ int build_coarse_level(cga* a, int k, uint32_t shift, cudaStream_t s) {
   a->cshift[k] = shift;
   a->cxdir[k] = cxdir;
   a->czr[k] = czr;
+  a->cchild[k] = cchild;
   a->ncoarse = (uint32_t)k + 1;
   return CGA_OK;
 }

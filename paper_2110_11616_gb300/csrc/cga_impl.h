@@ -195,6 +195,10 @@ struct NnSeg {
   const uint32_t* cxdir[kMaxCoarse];
   // zr[k][c] = lowest | highest << 16 cell z of column c of c[k] (or null)
   const uint32_t* zr[kMaxCoarse];
+  // child[k][(c << dsh) + j]: for column c of c[k] (dsh = its shift minus the
+  // next finer level's), the first column of the j-th finer slab under it
+  // with y >= its y << dsh (or null: found by a search instead)
+  const uint32_t* child[kMaxCoarse];
   uint32_t ncoarse;
   // optional x directory of `a` (cga_nn_prepare): for every x value v of the
   // grid, the index of the first X_index entry >= v
@@ -242,6 +246,11 @@ cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaSt
 cudaError_t run_coarse_slab_index(const Levels& a, const Levels& c, uint32_t shift, uint32_t* xs,
                                   cudaStream_t stream);
 
+// For every column of the coarse level c (dsh bits coarser than f, xs its
+// slab index into f): the first column of each finer slab under it at or
+// above its y range.  child has c.cap1 << dsh entries.
+cudaError_t run_child_columns(const Levels& f, const Levels& c, const uint32_t* xs, uint32_t dsh,
+                              uint32_t* child, cudaStream_t stream);
 // zr[c] = Z_index[Y_pointer[c]] | Z_index[Y_pointer[c + 1] - 1] << 16 for every column c
 // of a (a.cap1 entries reserved).
 cudaError_t run_column_zrange(const Levels& a, uint32_t* zr, cudaStream_t stream);

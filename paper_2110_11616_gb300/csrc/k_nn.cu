@@ -233,7 +233,7 @@ __device__ void visit_cell_column(const NnSeg& sg, uint32_t c, uint32_t cy,
 // columns; a column of a coarse level is refined one level down.
 template <int K>
 __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t ylo,
-                             uint32_t ysz, const Qry& q, Best& best) {
+                             uint32_t ysz, const uint32_t* starts, const Qry& q, Best& best) {
   if constexpr (K == 0) {
     // the fine columns of one cell: few enough that a plain ascending scan
     // with the bound test per slab and per column beats ordering them
@@ -246,7 +246,9 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
       if (dx2 > best.d2) continue;
       const uint32_t ys = __ldg(a.ptr2 + xi), ye = __ldg(a.ptr2 + xi + 1);
       const unsigned long long kx = (unsigned long long)x << (2 * b);
-      for (uint32_t c = lower_bound_u16(a.idx1, ys, ye, ylo); c < ye; ++c) {
+      const uint32_t c0 = starts != nullptr ? __ldg(starts + (xi - x0))
+                                            : lower_bound_u16(a.idx1, ys, ye, ylo);
+      for (uint32_t c = c0; c < ye; ++c) {
         const uint32_t y = __ldg(a.idx1 + c);
         if (y >= ylo + ysz) break;
         const unsigned long long dy = absdiff(y, q.y);
@@ -278,7 +280,8 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
     const uint32_t ys = __ldg(L.ptr2 + xi), ye = __ldg(L.ptr2 + xi + 1);
     // columns [c0, c1) of this slab lie in the y range; cs: the first at or
     // beyond the query's row
-    const uint32_t c0 = lower_bound_u16(L.idx1, ys, ye, ylo);
+    const uint32_t c0 = starts != nullptr ? __ldg(starts + (xi - x0))
+                                          : lower_bound_u16(L.idx1, ys, ye, ylo);
     uint32_t cs = c0, c1 = c0;
     while (c1 < ye) {
       const uint32_t y = __ldg(L.idx1 + c1);
@@ -351,7 +354,9 @@ __device__ void visit_cell_column(const NnSeg& sg, uint32_t c, uint32_t cy,
   const unsigned long long dzl = cell_z_dist<K>(sg, c, q);
   if (dxl2 + dyl2 + dzl * dzl > best.d2) return;
   const uint32_t dsh = level_shift<K>(sg) - level_shift<K - 1>(sg);
-  refine_level<K - 1>(sg, cx0, cx1, cy << dsh, 1u << dsh, q, best);
+  const uint32_t* child = sg.child[K - 1];
+  refine_level<K - 1>(sg, cx0, cx1, cy << dsh, 1u << dsh,
+                      child != nullptr ? child + ((size_t)c << dsh) : nullptr, q, best);
 }
 
 // Window search whose rounds run over the coarsest level TOP (cells of

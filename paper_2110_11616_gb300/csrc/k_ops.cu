@@ -260,6 +260,25 @@ __global__ void k_coarse_slab_index(Levels a, Levels c, uint32_t shift, uint32_t
   }
 }
 
+// ---------------------------------------------------------- child columns
+// Where each coarse column's cell starts in every finer slab below it: the
+// refinement of a cell reads its starting columns instead of searching.
+__global__ void k_child_columns(Levels f, Levels c, const uint32_t* __restrict__ xs, uint32_t dsh,
+                                uint32_t* child) {
+  const uint32_t gc = (uint32_t)c.hdr->cnt[1], hc = (uint32_t)c.hdr->cnt[2];
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t col = blockIdx.x * blockDim.x + threadIdx.x; col < gc; col += stride) {
+    const uint32_t X = search_le(c.ptr2, 0, hc - 1, col);
+    const uint32_t fx0 = __ldg(xs + X), fx1 = __ldg(xs + X + 1);
+    const uint32_t ylo = (uint32_t)__ldg(c.idx1 + col) << dsh;
+    for (uint32_t j = 0; j < fx1 - fx0; ++j) {
+      const uint32_t xi = fx0 + j;
+      child[((size_t)col << dsh) + j] =
+          lower_bound_u16(f.idx1, __ldg(f.ptr2 + xi), __ldg(f.ptr2 + xi + 1), ylo);
+    }
+  }
+}
+
 // ------------------------------------------------------- column z range
 // Lowest and highest z of every column: a bound that needs no search when
 // the query lies below or above the whole column.
@@ -399,6 +418,16 @@ cudaError_t run_coarse_slab_index(const Levels& a, const Levels& c, uint32_t shi
   const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
                                                        (uint64_t)device_sm_count() * 8);
   k_coarse_slab_index<<<blocks, 256, 0, stream>>>(a, c, shift, xs);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t run_child_columns(const Levels& f, const Levels& c, const uint32_t* xs, uint32_t dsh,
+                              uint32_t* child, cudaStream_t stream) {
+  const uint64_t work = std::max<uint64_t>(c.cap1, 1);
+  const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
+                                                       (uint64_t)device_sm_count() * 8);
+  k_child_columns<<<blocks, 256, 0, stream>>>(f, c, xs, dsh, child);
   count_launch(1);
   return cudaGetLastError();
 }
