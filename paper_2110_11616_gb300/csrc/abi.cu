@@ -37,6 +37,9 @@ struct cga {
   // x directory of this CGA for NN (cga_nn_prepare): first X_index entry >= v
   void* xdmem = nullptr;
   uint32_t* xdir = nullptr;
+  // column z ranges of this CGA for NN (cga_nn_prepare)
+  void* zrmem = nullptr;
+  uint32_t* zr0 = nullptr;
 };
 
 struct cga2d {
@@ -208,6 +211,7 @@ void release(cga* h) {
     if (h->cmem[k] != nullptr) dfree(&h->alloc, h->has_alloc, h->cmem[k], h->stream);
   }
   if (h->xdmem != nullptr) dfree(&h->alloc, h->has_alloc, h->xdmem, h->stream);
+  if (h->zrmem != nullptr) dfree(&h->alloc, h->has_alloc, h->zrmem, h->stream);
   dfree(&h->alloc, h->has_alloc, h->mem, h->stream);
   delete h;
 }
@@ -215,6 +219,7 @@ void release(cga* h) {
 // NN searches use the coarse levels that cga_nn_prepare_levels built.
 void attach_coarse(const cga* a, libcga::NnSeg& seg) {
   seg.xdir = a->xdir;
+  seg.zr0 = a->zr0;
   seg.ncoarse = a->ncoarse;
   for (uint32_t k = 0; k < a->ncoarse; ++k) {
     seg.c[k] = a->clv[k];
@@ -562,6 +567,17 @@ int cga_nn_prepare_levels(cga_t* a, const uint32_t* shifts, uint32_t count, void
     }
     a->xdmem = xm;
     a->xdir = static_cast<uint32_t*>(xm);
+  }
+  if (a->zrmem == nullptr) {
+    void* zm = dalloc(A, (size_t)std::max<uint64_t>(a->lv.cap1, 1) * 4, s);
+    if (zm == nullptr) return CGA_ERR_OOM;
+    const int rc = cuda_rc(libcga::run_column_zrange(a->lv, static_cast<uint32_t*>(zm), s));
+    if (rc != CGA_OK) {
+      dfree(A, a->has_alloc, zm, s);
+      return rc;
+    }
+    a->zrmem = zm;
+    a->zr0 = static_cast<uint32_t*>(zm);
   }
   for (uint32_t k = 0; k < count; ++k) {
     const int rc = build_coarse_level(a, (int)k, shifts[k], s);

@@ -203,6 +203,8 @@ struct NnSeg {
   // optional x directory of `a` (cga_nn_prepare): for every x value v of the
   // grid, the index of the first X_index entry >= v
   const uint32_t* xdir;
+  // optional column z ranges of `a` (cga_nn_prepare): lowest | highest << 16
+  const uint32_t* zr0;
   float scale;
   float off[3];
   const float* q;

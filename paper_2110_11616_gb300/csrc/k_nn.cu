@@ -118,10 +118,26 @@ struct Best {
   }
 };
 
-// The two z neighbours of the query in column c.
-__device__ __forceinline__ void visit_column(const Levels& a, uint32_t c, unsigned long long kxy,
-                                             unsigned long long dxy, long long qz, uint32_t cqz,
-                                             Best& b) {
+// The two z neighbours of the query in column c.  zr0 (or null): the
+// column's lowest | highest z << 16; when the query lies below or above the
+// whole column, that end is the only neighbour and no search is needed.
+__device__ __forceinline__ void visit_column(const Levels& a, const uint32_t* zr0, uint32_t c,
+                                             unsigned long long kxy, unsigned long long dxy,
+                                             long long qz, uint32_t cqz, Best& b) {
+  if (zr0 != nullptr) {
+    const uint32_t zz = __ldg(zr0 + c);
+    const uint32_t zlo = zz & 0xffffu, zhi = zz >> 16;
+    if (cqz <= zlo) {
+      const unsigned long long dz = absdiff(zlo, qz);
+      b.offer(dxy + dz * dz, kxy | zlo, __ldg(a.ptr1 + c));
+      return;
+    }
+    if (cqz >= zhi) {
+      const unsigned long long dz = absdiff(zhi, qz);
+      b.offer(dxy + dz * dz, kxy | zhi, __ldg(a.ptr1 + c + 1) - 1);
+      return;
+    }
+  }
   const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
   const uint32_t zr = lower_bound_u16(a.idx0, zs, ze, cqz);
   if (zr < ze) {
@@ -137,7 +153,8 @@ __device__ __forceinline__ void visit_column(const Levels& a, uint32_t c, unsign
 }
 
 // Window search over the fine CGA alone (one warp, 16 slabs per side per round).
-__device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdir, uint32_t h,
+__device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdir,
+                                            const uint32_t* zr0, uint32_t h,
                                             long long qx, long long qy, long long qz,
                                             uint32_t cqx, uint32_t cqy, uint32_t cqz,
                                             uint32_t lane, Best& best) {
@@ -167,13 +184,17 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
         const uint32_t y = __ldg(a.idx1 + yr0);
         const unsigned long long dy = absdiff(y, qy);
         const unsigned long long dxy = dx2 + dy * dy;
-        if (dxy <= best.d2) visit_column(a, yr0, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+        if (dxy <= best.d2) {
+          visit_column(a, zr0, yr0, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+        }
       }
       if (yr0 > ys) {
         const uint32_t y = __ldg(a.idx1 + yr0 - 1);
         const unsigned long long dy = absdiff(y, qy);
         const unsigned long long dxy = dx2 + dy * dy;
-        if (dxy <= best.d2) visit_column(a, yr0 - 1, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+        if (dxy <= best.d2) {
+          visit_column(a, zr0, yr0 - 1, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+        }
       }
     }
     best.warp_min();
@@ -191,7 +212,7 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
         const uint32_t c = (uint32_t)(gR ? R2 : L2);
         if (gR) ++R2; else --L2;
         const uint32_t y = __ldg(a.idx1 + c);
-        visit_column(a, c, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+        visit_column(a, zr0, c, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
       }
     }
     best.warp_min();
@@ -254,7 +275,7 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
         const unsigned long long dy = absdiff(y, q.y);
         const unsigned long long dxy = dx2 + dy * dy;
         if (dxy > best.d2) continue;
-        visit_column(a, c, kx | ((unsigned long long)y << b), dxy, q.z, q.cz, best);
+        visit_column(a, sg.zr0, c, kx | ((unsigned long long)y << b), dxy, q.z, q.cz, best);
       }
     }
     return;
@@ -310,7 +331,7 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
       if (gR) ++R; else --Lc;
       if constexpr (K == 0) {
         const uint32_t b = L.bits;
-        visit_column(L, c, ((unsigned long long)xv << (2 * b)) | ((unsigned long long)yv << b),
+        visit_column(L, sg.zr0, c, ((unsigned long long)xv << (2 * b)) | ((unsigned long long)yv << b),
                      dxl2 + dyl * dyl, q.z, q.cz, best);
       } else {
         visit_cell_column<K>(sg, c, yv, dxl2, dyl * dyl, fx0, fx1, q, best);
@@ -474,9 +495,11 @@ __device__ void search_levels(const NnSeg& sg, const Qry& q, uint32_t lane, Best
 }
 
 // NC: the most coarse levels any segment of the launch carries (0, 1 or 2);
-// the fine-only instantiation keeps fewer registers.
+// the fine-only instantiation keeps fewer registers.  The coarse ones are
+// held to 64 registers (four blocks per SM): the extra warps hide more of the
+// search's load latency than the few spilled values cost.
 template <int NC>
-__global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs, int S,
+__global__ void __launch_bounds__(256, NC > 0 ? 4 : 1) k_nn_warp(const NnSeg* __restrict__ segs, int S,
                                                  NnSeg inline_seg, uint32_t total_slots,
                                                  const unsigned long long* __restrict__ order,
                                                  const unsigned int* __restrict__ order_err) {
@@ -516,7 +539,7 @@ __global__ void __launch_bounds__(256) k_nn_warp(const NnSeg* __restrict__ segs,
     } else if (NC >= 1 && sg.ncoarse >= 1) {
       if constexpr (NC >= 1) search_levels<1>(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane, best);
     } else {
-      search_fine(a, sg.xdir, h, qx, qy, qz, cqx, cqy, cqz, lane, best);
+      search_fine(a, sg.xdir, sg.zr0, h, qx, qy, qz, cqx, cqy, cqz, lane, best);
     }
     if (lane == 0) {
       sg.idx[j] = best.idx;
