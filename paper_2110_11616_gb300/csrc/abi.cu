@@ -1348,6 +1348,7 @@ int cga_pipeline_run_graph(cga_pipeline_t* p, void* stream) {
     cudaError_t e = cudaSuccess;
     if (p->cap_stream == nullptr) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = libcga::init_sort_kernels();  // kernel attributes before capture
+    libcga::init_nn_kernels();
     if (e != cudaSuccess) return cuda_rc(e);
     const uint64_t k0 = libcga::g_launches.load();
     e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);

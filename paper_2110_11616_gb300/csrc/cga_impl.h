@@ -110,6 +110,8 @@ SortScratch sort_scratch_carve(void* base, uint64_t total_keys, uint32_t total_t
 // Set the shared-memory limits of the pass kernels (once; before any graph
 // capture that launches them).
 cudaError_t init_sort_kernels();
+// Query the residency of the NN search kernels (once; before any capture).
+void init_nn_kernels();
 
 // Queue only the radix passes (segments already on the device in sc.segs,
 // histograms filled, look-back words zeroed).

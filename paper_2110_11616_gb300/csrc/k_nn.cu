@@ -17,6 +17,7 @@
 // visited in Morton order of their voxel (a 4-pass radix sort of
 // (morton << 32 | index) keys), so neighbouring warps read neighbouring slabs.
 #include <algorithm>
+#include <atomic>
 #include <new>
 
 #include "k_common.cuh"
@@ -602,13 +603,34 @@ cudaError_t nn_upload_one(const NnSeg& h_seg, const NnTables& t, cudaStream_t st
   return e;
 }
 
+// Blocks of k_nn_warp<kind> that fit on one SM (queried once per kind).
+static uint32_t resident_blocks(uint32_t kind) {
+  static std::atomic<int> cache[3] = {{0}, {0}, {0}};
+  int n = cache[kind].load(std::memory_order_relaxed);
+  if (n == 0) {
+    cudaError_t e = cudaErrorInvalidValue;
+    if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_warp<0>, 256, 0);
+    if (kind == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_warp<1>, 256, 0);
+    if (kind == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_warp<2>, 256, 0);
+    if (e != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 4;
+    }
+    cache[kind].store(n, std::memory_order_relaxed);
+  }
+  return (uint32_t)n;
+}
+
 static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
                           uint32_t total_tiles, const unsigned long long* order,
                           const unsigned int* order_err, uint32_t ncoarse,
                           cudaStream_t stream) {
   const uint32_t total_slots = total_tiles * (uint32_t)kTile;
-  const uint32_t blocks =
-      std::min<uint32_t>((total_slots + 7) / 8, (uint32_t)device_sm_count() * 8);
+  // one wave: as many blocks as stay resident (the warps stride over the
+  // query slots, so a second wave would only add its own tail)
+  const uint32_t kind = ncoarse >= 2 ? 2u : ncoarse;
+  const uint32_t blocks = std::min<uint32_t>((total_slots + 7) / 8,
+                                             (uint32_t)device_sm_count() * resident_blocks(kind));
   if (ncoarse >= 2) {
     k_nn_warp<2><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
                                              order_err);
@@ -620,6 +642,10 @@ static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
                                              order_err);
   }
   count_launch(1);
+}
+
+void init_nn_kernels() {
+  for (uint32_t k = 0; k < 3; ++k) resident_blocks(k);
 }
 
 cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
