@@ -108,14 +108,22 @@ struct Best {
       idx = i;
     }
   }
+  // Lexicographic minimum of (d2, key) over the warp, by 32-bit warp
+  // reductions of the high then low words; the index comes from a lane that
+  // holds the minimum (equal keys are the same voxel, so the same index).
   __device__ __forceinline__ void warp_min() {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long od = __shfl_xor_sync(0xffffffffu, d2, o);
-      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
-      const uint32_t oi = __shfl_xor_sync(0xffffffffu, idx, o);
-      offer(od, ok, oi);
-    }
+    const uint32_t full = 0xffffffffu;
+    const uint32_t dh = (uint32_t)(d2 >> 32), dl = (uint32_t)d2;
+    const uint32_t mh = __reduce_min_sync(full, dh);
+    const uint32_t ml = __reduce_min_sync(full, dh == mh ? dl : full);
+    const bool at_min = dh == mh && dl == ml;
+    const uint32_t kh = (uint32_t)(key >> 32), kl = (uint32_t)key;
+    const uint32_t mkh = __reduce_min_sync(full, at_min ? kh : full);
+    const uint32_t mkl = __reduce_min_sync(full, at_min && kh == mkh ? kl : full);
+    const uint32_t holders = __ballot_sync(full, at_min && kh == mkh && kl == mkl);
+    idx = __shfl_sync(full, idx, __ffs(holders) - 1);
+    d2 = ((unsigned long long)mh << 32) | ml;
+    key = ((unsigned long long)mkh << 32) | mkl;
   }
 };
 
