@@ -133,21 +133,22 @@ struct Best {
 __device__ __forceinline__ void visit_column(const Levels& a, const uint32_t* zr0, uint32_t c,
                                              unsigned long long kxy, unsigned long long dxy,
                                              long long qz, uint32_t cqz, Best& b) {
+  // the column's voxel range, loaded together with its z range
+  const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
   if (zr0 != nullptr) {
     const uint32_t zz = __ldg(zr0 + c);
     const uint32_t zlo = zz & 0xffffu, zhi = zz >> 16;
     if (cqz <= zlo) {
       const unsigned long long dz = absdiff(zlo, qz);
-      b.offer(dxy + dz * dz, kxy | zlo, __ldg(a.ptr1 + c));
+      b.offer(dxy + dz * dz, kxy | zlo, zs);
       return;
     }
     if (cqz >= zhi) {
       const unsigned long long dz = absdiff(zhi, qz);
-      b.offer(dxy + dz * dz, kxy | zhi, __ldg(a.ptr1 + c + 1) - 1);
+      b.offer(dxy + dz * dz, kxy | zhi, ze - 1);
       return;
     }
   }
-  const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
   const uint32_t zr = lower_bound_u16(a.idx0, zs, ze, cqz);
   if (zr < ze) {
     const uint32_t z = __ldg(a.idx0 + zr);
