@@ -176,19 +176,19 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
     const long long slab = right ? (long long)xr0 + k : (long long)xr0 - 1 - k;
     const bool valid = slab >= 0 && slab < (long long)h;
     unsigned long long dx2 = ~0ull;
-    uint32_t x = 0;
+    uint32_t x = 0, ys = 0, ye = 0, yr0 = 0;
     if (valid) {
+      // the slab's column range is loaded together with its x value
       x = __ldg(a.idx2 + slab);
+      ys = __ldg(a.ptr2 + slab);
+      ye = __ldg(a.ptr2 + slab + 1);
       const unsigned long long dx = absdiff(x, qx);
       dx2 = dx * dx;
     }
     const bool active = valid && dx2 <= best.d2;
     if (!__any_sync(0xffffffffu, active)) break;
-    uint32_t ys = 0, ye = 0, yr0 = 0;
     const unsigned long long kx = (unsigned long long)x << (2 * b);
     if (active) {
-      ys = __ldg(a.ptr2 + slab);
-      ye = __ldg(a.ptr2 + slab + 1);
       yr0 = lower_bound_u16(a.idx1, ys, ye, cqy);
       if (yr0 < ye) {
         const uint32_t y = __ldg(a.idx1 + yr0);
