@@ -92,6 +92,10 @@ def lib():
         _lib.orc_project.argtypes = [ctypes.POINTER(_Cga), ctypes.c_int,
                                      ctypes.POINTER(_Cga2d)]
         _lib.orc_query_voxels.argtypes = [P, U64, F, P, P, P]
+        _lib.orc_build_values.argtypes = [P, P, U32, U64, U32, F, P, P, ctypes.c_int,
+                                          ctypes.POINTER(_Cga), P]
+        _lib.orc_merge_values.argtypes = [ctypes.POINTER(_Cga), P, ctypes.POINTER(_Cga), P, U32,
+                                          ctypes.c_int, ctypes.POINTER(_Cga), P]
         for fn in (_lib.orc_nn_brute, _lib.orc_nn_window):
             fn.argtypes = [ctypes.POINTER(_Cga), F, P, P, U64, P, P]
     return _lib
@@ -250,6 +254,48 @@ def merge(a: Cga, b: Cga) -> Cga:
     s, arrs = _empty_out(a.bits, a.u + b.u)
     _check(lib().orc_merge(ctypes.byref(sa), ctypes.byref(sb), ctypes.byref(s)))
     return _from_struct(s, arrs)
+
+
+VALUE_POLICIES = {"average": 0, "first": 1}
+MERGE_POLICIES = {"base": 0, "average": 1}
+
+
+def _attrs(attr, n):
+    a = np.asarray(attr, dtype=np.uint8)
+    if a.ndim == 1:
+        a = a.reshape(-1, 1)
+    if a.shape[0] != n:
+        raise ValueError("one attribute row per point")
+    return np.ascontiguousarray(a)
+
+
+def build_values(xyz, attr, grid: Grid, xform=None, policy="average"):
+    """Build plus the Value array (Sec. III): returns (Cga, values (u, channels) uint8)."""
+    p = _f32xyz(xyz)
+    a = _attrs(attr, len(p))
+    ch = a.shape[1]
+    s, arrs = _empty_out(grid.bits, len(p))
+    vals = np.zeros((max(len(p), 1), ch), np.uint8)
+    x, xp = _xform(xform)
+    off = grid.offset_array()
+    _check(lib().orc_build_values(_ptr(p), _ptr(a), ch, len(p), grid.bits, grid.scale, _ptr(off),
+                                  xp, VALUE_POLICIES[policy], ctypes.byref(s), _ptr(vals)))
+    c = _from_struct(s, arrs)
+    return c, vals[:c.u].copy()
+
+
+def merge_values(a: Cga, va, b: Cga, vb, policy="base"):
+    """Merge with the Value arrays of a (the base) and b: returns (Cga, values)."""
+    va = np.ascontiguousarray(np.asarray(va, dtype=np.uint8))
+    vb = np.ascontiguousarray(np.asarray(vb, dtype=np.uint8))
+    ch = va.shape[1] if va.ndim > 1 else 1
+    sa, sb = a._struct(), b._struct()
+    s, arrs = _empty_out(a.bits, a.u + b.u)
+    vals = np.zeros((max(a.u + b.u, 1), ch), np.uint8)
+    _check(lib().orc_merge_values(ctypes.byref(sa), _ptr(va), ctypes.byref(sb), _ptr(vb), ch,
+                                  MERGE_POLICIES[policy], ctypes.byref(s), _ptr(vals)))
+    c = _from_struct(s, arrs)
+    return c, vals[:c.u].copy()
 
 
 PLANES = {"xy": 0, "xz": 1, "yz": 2}

@@ -434,4 +434,78 @@ int orc_nn_window(const orc_cga* a, float scale, const float offset[3],
   return ORC_OK;
 }
 
+// Sec. III Value array.  Duplicate points of one voxel: Sec. V averages the
+// attributes of the points merged into one box (pcdownsample); the other
+// policy keeps the first point's.  Pairs (key, input index) sorted by key,
+// then by index, give each voxel's points in input order.
+int orc_build_values(const float* xyz, const uint8_t* attr, uint32_t channels, uint64_t n,
+                     uint32_t bits, float scale, const float offset[3], const float* xform12,
+                     int policy, orc_cga* out, uint8_t* values) {
+  if (!bits_ok(bits) || channels < 1 || channels > 4) return ORC_ERR_INVALID_ARG;
+  if (policy != ORC_VALUE_AVERAGE && policy != ORC_VALUE_FIRST) return ORC_ERR_INVALID_ARG;
+  std::vector<uint64_t> keys(n);
+  const int st = orc_quantize(xyz, n, bits, scale, offset, xform12, keys.data());
+  if (st != ORC_OK) return st;
+  std::vector<std::pair<uint64_t, uint64_t>> kp(n);
+  for (uint64_t i = 0; i < n; ++i) kp[i] = {keys[i], i};
+  std::sort(kp.begin(), kp.end());
+  std::vector<uint64_t> ukeys;
+  uint64_t i = 0;
+  while (i < n) {
+    uint64_t j = i;
+    while (j < n && kp[j].first == kp[i].first) ++j;
+    const uint64_t p = ukeys.size();
+    for (uint32_t c = 0; c < channels; ++c) {
+      if (policy == ORC_VALUE_FIRST) {
+        values[p * channels + c] = attr[kp[i].second * channels + c];
+      } else {
+        uint64_t sum = 0;
+        for (uint64_t k = i; k < j; ++k) sum += attr[kp[k].second * channels + c];
+        const uint64_t cnt = j - i;
+        values[p * channels + c] = (uint8_t)((sum + cnt / 2) / cnt);
+      }
+    }
+    ukeys.push_back(kp[i].first);
+    i = j;
+  }
+  return orc_from_sorted_keys(ukeys.data(), ukeys.size(), bits, out);
+}
+
+// Eq. 1 as a sorted union; a voxel in both inputs takes the base's (a's)
+// attributes or the average of the two (Sec. II-A).
+int orc_merge_values(const orc_cga* a, const uint8_t* va, const orc_cga* b, const uint8_t* vb,
+                     uint32_t channels, int policy, orc_cga* out, uint8_t* values) {
+  if (a->bits != b->bits || channels < 1 || channels > 4) return ORC_ERR_INVALID_ARG;
+  if (policy != ORC_MERGE_BASE && policy != ORC_MERGE_AVERAGE) return ORC_ERR_INVALID_ARG;
+  std::vector<uint64_t> ka(a->u), kb(b->u), ko;
+  if (orc_decode_keys(a, ka.data()) != ORC_OK) return ORC_ERR_INVALID_ARG;
+  if (orc_decode_keys(b, kb.data()) != ORC_OK) return ORC_ERR_INVALID_ARG;
+  uint64_t i = 0, j = 0;
+  while (i < ka.size() || j < kb.size()) {
+    const uint64_t p = ko.size();
+    const bool takeA = j == kb.size() || (i < ka.size() && ka[i] <= kb[j]);
+    const bool both = i < ka.size() && j < kb.size() && ka[i] == kb[j];
+    for (uint32_t c = 0; c < channels; ++c) {
+      uint32_t v;
+      if (both) {
+        v = policy == ORC_MERGE_BASE ? va[i * channels + c]
+                                     : (va[i * channels + c] + vb[j * channels + c] + 1u) / 2u;
+      } else {
+        v = takeA ? va[i * channels + c] : vb[j * channels + c];
+      }
+      values[p * channels + c] = (uint8_t)v;
+    }
+    ko.push_back(takeA ? ka[i] : kb[j]);
+    if (both) {
+      ++i;
+      ++j;
+    } else if (takeA) {
+      ++i;
+    } else {
+      ++j;
+    }
+  }
+  return orc_from_sorted_keys(ko.data(), ko.size(), a->bits, out);
+}
+
 }  // extern "C"

@@ -108,6 +108,28 @@ int orc_query_voxels(const float* q, uint64_t m, float scale, const float offset
 int orc_nn_window(const orc_cga* a, float scale, const float offset[3],
                   const float* q, uint64_t m, uint32_t* idx, uint64_t* dist2);
 
+/* ---- Value (attribute) array, Sec. III ------------------------------------
+ * Every stored voxel carries `channels` (1..4) uint8 attributes, in CGA point
+ * order (values[p * channels + c] belongs to Z_index[p]). */
+#define ORC_VALUE_AVERAGE 0 /* Sec. V (pcdownsample): the points of one voxel are averaged */
+#define ORC_VALUE_FIRST 1   /* the voxel keeps the attributes of its first input point */
+#define ORC_MERGE_BASE 0    /* Sec. II-A: an overlapping voxel keeps the base cloud's (a's) */
+#define ORC_MERGE_AVERAGE 1 /* Sec. II-A: or the average of the two */
+
+/* Build with values.  attr: n * channels input attributes in point order.
+ * The average of a voxel's k points is the round-half-up integer mean
+ * (sum + k / 2) / k per channel; FIRST keeps the lowest input index.
+ * values: n * channels entries (u * channels are written). */
+int orc_build_values(const float* xyz, const uint8_t* attr, uint32_t channels, uint64_t n,
+                     uint32_t bits, float scale, const float offset[3], const float* xform12,
+                     int policy, orc_cga* out, uint8_t* values);
+
+/* Merge with values (Eq. 1 with the Sec. II-A attribute rule; a is the base).
+ * The average of a voxel present in both is (va + vb + 1) / 2 per channel.
+ * out and values hold a->u + b->u entries (values times channels). */
+int orc_merge_values(const orc_cga* a, const uint8_t* va, const orc_cga* b, const uint8_t* vb,
+                     uint32_t channels, int policy, orc_cga* out, uint8_t* values);
+
 #ifdef __cplusplus
 }
 #endif
