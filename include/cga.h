@@ -224,6 +224,40 @@ int cga_nn_query_noalloc(const cga_t* a, const float* d_q, uint64_t m, uint32_t*
  * (may be NULL when the handle's capacity is 0). */
 int cga_decode(const cga_t* a, uint32_t* d_xyz, void* stream);
 
+/* ---- Value (attribute) array, Sec. III --------------------------------------
+ * A CGA may carry one row of `channels` (1..CGA_MAX_CHANNELS) uint8
+ * attributes per stored voxel, in CGA point order: row p belongs to
+ * Z_index[p].  Several points quantized into one voxel give it the
+ * round-half-up integer mean (sum + k/2) / k of their k rows per channel
+ * (Sec. V: the colours of the points merged into one box are averaged), or the
+ * row of the first of them in input order.  A merge keeps, for a voxel held by
+ * both inputs, the base's (a's) row or (a + b + 1) / 2 per channel (Sec. II-A);
+ * a voxel held by one input keeps its row. */
+#define CGA_MAX_CHANNELS 4
+#define CGA_VALUE_AVERAGE 0
+#define CGA_VALUE_FIRST 1
+#define CGA_MERGE_BASE 0
+#define CGA_MERGE_AVERAGE 1
+
+/* cga_build plus the Value array.  d_attr: n * channels uint8 rows, device,
+ * point order (the same points as d_xyz).  Each point finds its voxel by the
+ * Sec. III-A lookup; sums are exact integers, so the result does not depend
+ * on arrival order.  Errors as cga_build; CGA_ERR_INVALID_ARG for channels or
+ * policy out of range or a NULL d_attr with n > 0. */
+int cga_build_values(const float* d_xyz, const uint8_t* d_attr, uint32_t channels, uint64_t n,
+                     const cga_grid* g, const float* h_xform12, int policy,
+                     const cga_allocator* A, void* stream, cga_t** out);
+
+/* cga_merge plus the Value array (a is the base).  Both inputs must carry
+ * values with the same channel count (else CGA_ERR_INVALID_ARG). */
+int cga_merge_values(const cga_t* a, const cga_t* b, int policy, const cga_allocator* A,
+                     void* stream, cga_t** out);
+
+/* Device pointer to a's Value array (u * channels bytes, valid while a
+ * lives; stream-ordered after the call that made a) and its channel count;
+ * NULL and 0 when a has no values. */
+int cga_values(const cga_t* a, const uint8_t** d_values, uint32_t* channels);
+
 /* ---- Batched forms: one set of kernel launches serves every item. --------
  * Each item has the semantics of the single call; handles are independent
  * (free each one).  On an error nothing is returned and no handle leaks. */

@@ -40,6 +40,7 @@ EXPORTS = (
     "cga_server_free", "cga_now_ns", "cga_nn_sort_queries", "cga_nn_query_ordered",
     "cga_nn_prepare", "cga_nn_prepare_levels", "cga_nn_autotune",
     "cga_tuning_set", "cga_tuning_get", "cga_autotune", "cga_pipeline_autotune",
+    "cga_build_values", "cga_merge_values", "cga_values",
     "cga_selftest_wait_timeout",
 )
 
@@ -698,6 +699,74 @@ def cga_nn_autotune(a: Cga, sample_queries, stream=None):
                                chosen, times, _stream(stream)), "cga_nn_autotune")
     shifts = tuple(int(v) for v in chosen if v != 0)
     return shifts, {c: float(t) for c, t in zip(NN_AUTOTUNE_CANDIDATES, times) if t >= 0}
+
+
+# ------------------------------------------------------------- value array
+VALUE_POLICIES = {"average": 0, "first": 1}
+MERGE_POLICIES = {"base": 0, "average": 1}
+
+
+class _DeviceBytes:
+    """A borrowed device byte range as a CUDA array (for torch.as_tensor)."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "|u1",
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+def cga_values(a: Cga):
+    """A copy of a's Value array as a (u, channels) uint8 CUDA tensor, or None."""
+    torch = _torch()
+    lib = load()
+    lib.cga_values.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                               ctypes.POINTER(ctypes.c_uint32)]
+    ptr, ch = ctypes.c_void_p(), ctypes.c_uint32()
+    _check(lib.cga_values(a.ptr, ctypes.byref(ptr), ctypes.byref(ch)), "cga_values")
+    if not ptr.value or ch.value == 0:
+        return None
+    u = a.info()["u"]
+    if u == 0:
+        return torch.zeros((0, ch.value), dtype=torch.uint8, device="cuda")
+    return torch.as_tensor(_DeviceBytes(ptr.value, (u, ch.value)), device="cuda").clone()
+
+
+def cga_build_values(points, attrs, grid: Grid, xform=None, policy="average", stream=None,
+                     allocator="torch") -> Cga:
+    """cga_build plus per-voxel uint8 attributes: attrs is an (n, channels)
+    uint8 CUDA tensor aligned with points."""
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_build_values.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint64,
+                                     ctypes.POINTER(Grid), P, ctypes.c_int, P, P,
+                                     ctypes.POINTER(ctypes.c_void_p)]
+    _dev_f32(points, "cga_build_values")
+    n = points.numel() // 3
+    if not attrs.is_cuda or attrs.dtype != _torch().uint8 or not attrs.is_contiguous():
+        raise ValueError("cga_build_values: attrs must be a contiguous uint8 CUDA tensor")
+    ch = attrs.numel() // max(n, 1) if n else (attrs.shape[-1] if attrs.dim() > 1 else 1)
+    if n and attrs.numel() != n * ch:
+        raise ValueError("cga_build_values: one attribute row per point")
+    x = None
+    if xform is not None:
+        x = np.ascontiguousarray(np.asarray(xform, np.float32).reshape(12))
+    out = ctypes.c_void_p()
+    _check(lib.cga_build_values(P(points.data_ptr()), P(attrs.data_ptr()), ch, n,
+                                ctypes.byref(grid),
+                                x.ctypes.data_as(P) if x is not None else None,
+                                VALUE_POLICIES[policy], _alloc_arg(allocator), _stream(stream),
+                                ctypes.byref(out)), "cga_build_values")
+    return Cga(out, grid)
+
+
+def cga_merge_values(a: Cga, b: Cga, policy="base", stream=None, allocator="torch") -> Cga:
+    """cga_merge plus the Value array (a is the base)."""
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_merge_values.argtypes = [P, P, ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_void_p)]
+    out = ctypes.c_void_p()
+    _check(lib.cga_merge_values(a.ptr, b.ptr, MERGE_POLICIES[policy], _alloc_arg(allocator),
+                                _stream(stream), ctypes.byref(out)), "cga_merge_values")
+    return Cga(out, a.grid)
 
 
 # -------------------------------------------------------- launch-shape tuning

@@ -34,6 +34,10 @@ struct cga {
   uint32_t* cxdir[libcga::kMaxCoarse] = {};
   uint32_t* czr[libcga::kMaxCoarse] = {};
   uint32_t* cchild[libcga::kMaxCoarse] = {};
+  // Value array (cga_build_values / cga_merge_values): channels bytes per voxel
+  void* vmem = nullptr;
+  uint8_t* values = nullptr;
+  uint32_t channels = 0;
   // x directory of this CGA for NN (cga_nn_prepare): first X_index entry >= v
   void* xdmem = nullptr;
   uint32_t* xdir = nullptr;
@@ -211,6 +215,7 @@ void release(cga* h) {
     if (h->cmem[k] != nullptr) dfree(&h->alloc, h->has_alloc, h->cmem[k], h->stream);
   }
   if (h->xdmem != nullptr) dfree(&h->alloc, h->has_alloc, h->xdmem, h->stream);
+  if (h->vmem != nullptr) dfree(&h->alloc, h->has_alloc, h->vmem, h->stream);
   if (h->zrmem != nullptr) dfree(&h->alloc, h->has_alloc, h->zrmem, h->stream);
   dfree(&h->alloc, h->has_alloc, h->mem, h->stream);
   delete h;
@@ -335,6 +340,88 @@ int cga_merge(const cga_t* a, const cga_t* b, const cga_allocator* A, void* stre
     return rc;
   }
   *out = h;
+  return CGA_OK;
+}
+
+int cga_build_values(const float* d_xyz, const uint8_t* d_attr, uint32_t channels, uint64_t n,
+                     const cga_grid* g, const float* h_xform12, int policy,
+                     const cga_allocator* A, void* stream, cga_t** out) {
+  if (out == nullptr || channels < 1 || channels > CGA_MAX_CHANNELS ||
+      (policy != CGA_VALUE_AVERAGE && policy != CGA_VALUE_FIRST) || (n > 0 && d_attr == nullptr)) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  cga_t* h = nullptr;
+  int rc = cga_build(d_xyz, n, g, h_xform12, A, stream, &h);
+  if (rc != CGA_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t cap = std::max<uint64_t>(h->lv.cap, 1);
+  void* vm = dalloc(A, cap * channels, s);
+  void* scratch = dalloc(A, libcga::value_scratch_bytes(h->lv.cap, channels, policy), s);
+  if (vm == nullptr || scratch == nullptr) {
+    if (vm) dfree(A, A != nullptr, vm, s);
+    if (scratch) dfree(A, A != nullptr, scratch, s);
+    release(h);
+    return CGA_ERR_OOM;
+  }
+  libcga::ValueInput in{};
+  in.xyz = d_xyz;
+  in.attr = d_attr;
+  in.n = n;
+  in.channels = channels;
+  in.policy = policy;
+  in.scale = g->scale;
+  for (int k = 0; k < 3; ++k) in.off[k] = g->offset[k];
+  if (h_xform12 != nullptr) {
+    std::memcpy(in.X, h_xform12, sizeof(in.X));
+    in.has_x = 1;
+  }
+  rc = cuda_rc(libcga::run_build_values(h->lv, in, scratch, static_cast<uint8_t*>(vm), s));
+  dfree(A, A != nullptr, scratch, s);
+  h->vmem = vm;
+  h->values = static_cast<uint8_t*>(vm);
+  h->channels = channels;
+  if (rc != CGA_OK) {
+    release(h);
+    return rc;
+  }
+  *out = h;
+  return CGA_OK;
+}
+
+int cga_merge_values(const cga_t* a, const cga_t* b, int policy, const cga_allocator* A,
+                     void* stream, cga_t** out) {
+  if (a == nullptr || b == nullptr || out == nullptr || a->values == nullptr ||
+      b->values == nullptr || a->channels != b->channels ||
+      (policy != CGA_MERGE_BASE && policy != CGA_MERGE_AVERAGE)) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  cga_t* m = nullptr;
+  int rc = cga_merge(a, b, A, stream, &m);
+  if (rc != CGA_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint32_t C = a->channels;
+  void* vm = dalloc(A, std::max<uint64_t>(m->lv.cap, 1) * C, s);
+  if (vm == nullptr) {
+    release(m);
+    return CGA_ERR_OOM;
+  }
+  m->vmem = vm;
+  m->values = static_cast<uint8_t*>(vm);
+  m->channels = C;
+  rc = cuda_rc(libcga::run_merge_values(m->lv, a->lv, b->lv, a->values, b->values, C, policy,
+                                        m->values, s));
+  if (rc != CGA_OK) {
+    release(m);
+    return rc;
+  }
+  *out = m;
+  return CGA_OK;
+}
+
+int cga_values(const cga_t* a, const uint8_t** d_values, uint32_t* channels) {
+  if (a == nullptr || d_values == nullptr || channels == nullptr) return CGA_ERR_INVALID_ARG;
+  *d_values = a->values;
+  *channels = a->channels;
   return CGA_OK;
 }
 

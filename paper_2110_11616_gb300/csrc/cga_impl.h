@@ -170,6 +170,35 @@ cudaError_t run_merge(const MergePair* h_pairs, int S, uint32_t total_spl, uint3
 cudaError_t run_merge_device(int S, uint32_t total_spl, uint32_t total_tiles,
                              const MergeScratch& sc, cudaStream_t stream);
 
+// ---- Value array (Sec. III) -----------------------------------------------
+constexpr int kValueAverage = 0;  // a voxel's row: round-half-up mean of its points
+constexpr int kValueFirst = 1;    // a voxel's row: its first input point's
+constexpr int kMergeBase = 0;     // a voxel in both merge inputs keeps the base's row
+constexpr int kMergeAverage = 1;  // or (a + b + 1) / 2 per channel
+
+// The points and attributes a build's Value array is made from, with the
+// build's grid and transform (the same voxel keys as the build).
+struct ValueInput {
+  const float* xyz;
+  const uint8_t* attr;  // n * channels, point order
+  uint64_t n;
+  uint32_t channels;    // 1..4
+  int policy;           // kValueAverage or kValueFirst
+  float scale;
+  float off[3];
+  float X[12];
+  uint32_t has_x;
+};
+size_t value_scratch_bytes(uint64_t cap, uint32_t channels, int policy);
+// values (a.cap * channels bytes) for the CGA a built from in (queued after
+// the build on the same stream); scratch of value_scratch_bytes.
+cudaError_t run_build_values(const Levels& a, const ValueInput& in, void* scratch,
+                             uint8_t* values, cudaStream_t stream);
+// vm (m.cap * channels bytes) for m = merge(a, b) with rows va, vb.
+cudaError_t run_merge_values(const Levels& m, const Levels& a, const Levels& b, const uint8_t* va,
+                             const uint8_t* vb, uint32_t channels, int policy, uint8_t* vm,
+                             cudaStream_t stream);
+
 // Copy the top two levels of a CGA into a 2-level projection (plane xy).
 cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stream);
 struct ProjPair {

@@ -67,6 +67,40 @@ __device__ __forceinline__ uint32_t lookback(const uint32_t* look, uint32_t stri
   return excl;
 }
 
+// One axis of the grid (Sec. II-E-2-a box): floorf(fmaf(v, scale, off))
+// clamped in float to [0, hi].
+__device__ __forceinline__ uint32_t quantize_axis(float v, float scale, float off, float hi) {
+  float f = floorf(__fmaf_rn(v, scale, off));
+  f = fminf(fmaxf(f, 0.0f), hi);
+  return (uint32_t)f;
+}
+
+// Voxel key x << 2b | y << b | z of one point, after the rigid transform X
+// (R row-major, then t) by the fixed fmaf nesting when has_x.  False for a
+// non-finite point or transform result (key left 0).
+template <typename K>
+__device__ __forceinline__ bool point_key(float x, float y, float z, bool has_x, const float* X,
+                                          float scale, const float* off, uint32_t b, K& key) {
+  bool ok = isfinite(x) && isfinite(y) && isfinite(z);
+  if (has_x) {
+    const float x2 = __fmaf_rn(X[0], x, __fmaf_rn(X[1], y, __fmaf_rn(X[2], z, X[9])));
+    const float y2 = __fmaf_rn(X[3], x, __fmaf_rn(X[4], y, __fmaf_rn(X[5], z, X[10])));
+    const float z2 = __fmaf_rn(X[6], x, __fmaf_rn(X[7], y, __fmaf_rn(X[8], z, X[11])));
+    x = x2;
+    y = y2;
+    z = z2;
+    ok = ok && isfinite(x) && isfinite(y) && isfinite(z);
+  }
+  key = 0;
+  if (!ok) return false;
+  const float hi = (float)((1u << b) - 1u);
+  const uint32_t qx = quantize_axis(x, scale, off[0], hi);
+  const uint32_t qy = quantize_axis(y, scale, off[1], hi);
+  const uint32_t qz = quantize_axis(z, scale, off[2], hi);
+  key = ((K)qx << (2 * b)) | ((K)qy << b) | (K)qz;
+  return true;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_incl_scan(T v) {
   const int lane = threadIdx.x & 31;
@@ -203,6 +237,24 @@ __device__ __forceinline__ uint32_t warp_rank_of(const Levels& a, uint32_t h,
   const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
   const uint32_t zr = warp_lower_bound_u16(a.idx0, zs, ze, z);
   *found = zr < ze && __ldg(a.idx0 + zr) == z;
+  return zr;
+}
+
+// rank_of, and whether `key` itself is stored (then the rank is its index).
+__device__ __forceinline__ uint32_t rank_of_found(const Levels& a, uint32_t h,
+                                                  unsigned long long key, bool& found) {
+  const uint32_t b = a.bits, m = (1u << b) - 1u;
+  const uint32_t x = (uint32_t)(key >> (2 * b)), y = (uint32_t)(key >> b) & m,
+                 z = (uint32_t)key & m;
+  found = false;
+  const uint32_t xr = lower_bound_u16(a.idx2, 0, h, x);
+  if (xr == h || __ldg(a.idx2 + xr) != x) return __ldg(a.ptr1 + __ldg(a.ptr2 + xr));
+  const uint32_t ys = __ldg(a.ptr2 + xr), ye = __ldg(a.ptr2 + xr + 1);
+  const uint32_t c = lower_bound_u16(a.idx1, ys, ye, y);
+  if (c == ye || __ldg(a.idx1 + c) != y) return __ldg(a.ptr1 + c);
+  const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
+  const uint32_t zr = lower_bound_u16(a.idx0, zs, ze, z);
+  found = zr < ze && __ldg(a.idx0 + zr) == z;
   return zr;
 }
 

@@ -33,12 +33,6 @@ __device__ __forceinline__ uint32_t seg_count(const SortSeg& s) {
   return s.n_host;
 }
 
-__device__ __forceinline__ uint32_t quantize_axis(float v, float scale, float off, float hi) {
-  float f = floorf(__fmaf_rn(v, scale, off));
-  f = fminf(fmaxf(f, 0.0f), hi);
-  return (uint32_t)f;
-}
-
 __global__ void k_seg_init(const SortSeg* __restrict__ segs, int S) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
@@ -105,32 +99,15 @@ __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restric
     const uint32_t b = sg.bits;
     if (!sg.from_cga) {
       const float* src = sg.xyz + (size_t)start * 3;
-      const float hi = (float)((1u << b) - 1u);
       for (uint32_t c0 = 0; c0 < cnt; c0 += kThreads) {
         const uint32_t m = min((uint32_t)kThreads, cnt - c0);
         __syncthreads();
         for (uint32_t i = tid; i < m * 3; i += kThreads) s_pts[i] = __ldg(src + (size_t)c0 * 3 + i);
         __syncthreads();
         if ((uint32_t)tid < m) {
-          float x = s_pts[3 * tid], y = s_pts[3 * tid + 1], z = s_pts[3 * tid + 2];
-          bool ok = isfinite(x) && isfinite(y) && isfinite(z);
-          if (sg.has_x) {
-            const float* X = sg.X;
-            const float x2 = __fmaf_rn(X[0], x, __fmaf_rn(X[1], y, __fmaf_rn(X[2], z, X[9])));
-            const float y2 = __fmaf_rn(X[3], x, __fmaf_rn(X[4], y, __fmaf_rn(X[5], z, X[10])));
-            const float z2 = __fmaf_rn(X[6], x, __fmaf_rn(X[7], y, __fmaf_rn(X[8], z, X[11])));
-            x = x2;
-            y = y2;
-            z = z2;
-            ok = ok && isfinite(x) && isfinite(y) && isfinite(z);
-          }
-          K key = 0;
-          if (ok) {
-            const uint32_t qx = quantize_axis(x, sg.scale, sg.off[0], hi);
-            const uint32_t qy = quantize_axis(y, sg.scale, sg.off[1], hi);
-            const uint32_t qz = quantize_axis(z, sg.scale, sg.off[2], hi);
-            key = ((K)qx << (2 * b)) | ((K)qy << b) | (K)qz;
-          } else {
+          K key;
+          if (!point_key<K>(s_pts[3 * tid], s_pts[3 * tid + 1], s_pts[3 * tid + 2],
+                            sg.has_x != 0, sg.X, sg.scale, sg.off, b, key)) {
             atomicOr(&s_err, kErrNonfinite);
           }
           out[c0 + tid] = key;
