@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["cga", "reference"], default="cga")
-    ap.add_argument("--config", choices=["lidar", "plain", "surface", "batched", "served"],
+    ap.add_argument("--config", choices=["lidar", "plain", "surface", "batched", "served", "values"],
                     default="lidar")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
@@ -652,6 +652,70 @@ def run_served(args, world_size, local_rank, torch, cga):
     return out
 
 
+# ------------------------------------------------------ GPU arm: Value arrays
+def run_values(args, world_size, local_rank, torch, cga):
+    """The surface cloud with an RGB row per point: both halves built with
+    per-voxel averaged colours, then merged with averaged overlaps."""
+    from paper_2110_11616_gb300 import synth_gpu
+    scene = synth_gpu.surface_scene(3)
+    full = synth_gpu.sample_scene(scene, 30_000_000, seed=4)
+    gen = torch.Generator(device="cuda").manual_seed(8)
+    noise = torch.randint(-12, 13, full.shape, device="cuda", generator=gen, dtype=torch.int32)
+    colour = ((full * 2.55).to(torch.int32) + noise).clamp(0, 255).to(torch.uint8).contiguous()
+    halves = [full[0::2].contiguous(), full[1::2].contiguous()]
+    cols = [colour[0::2].contiguous(), colour[1::2].contiguous()]
+    del full, colour, noise
+    grid = cga.grid_from_box([0, 0, 0], 100.0, 12)
+    n_points = sum(h.shape[0] for h in halves)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+    state = {}
+
+    def step():
+        ev[0].record()
+        a = cga.cga_build_values(halves[0], cols[0], grid, policy="average", allocator=None)
+        b = cga.cga_build_values(halves[1], cols[1], grid, policy="average", allocator=None)
+        ev[1].record()
+        m = cga.cga_merge_values(a, b, policy="average", allocator=None)
+        ev[2].record()
+        state["last"] = (a, b, m)
+
+    def plain_step():
+        a = cga.cga_build(halves[0], grid, allocator=None)
+        b = cga.cga_build(halves[1], grid, allocator=None)
+        cga.cga_merge(a, b, allocator=None)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = start_clocks(local_rank)
+    launches0 = cga.kernel_launches()
+    ms, ops = [], np.zeros(2)
+    for k in range(args.steps):
+        ms.append(timed(torch, step, flush, float(k)))
+        ops += np.array([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])])
+    launches = cga.kernel_launches() - launches0
+    plain = [timed(torch, plain_step, flush, float(k)) for k in range(max(3, args.steps // 2))]
+    clk = clocks.stop()
+    a, b, m = state["last"]
+    u = m.info()["u"]
+    total = float(sum(ms))
+    op = ops / args.steps
+    out = base_line(args, world_size, METRIC, n_points * args.steps / (total / 1e3) / 1e6,
+                    "Mpts/s", total / args.steps,
+                    {"workload": "values: 30M surface pts with an RGB row each, b=12; both "
+                                 "halves built with per-voxel averaged colours, merged with "
+                                 "averaged overlaps",
+                     "points_per_step": n_points, "channels": 3, "l2": "flushed between steps"},
+                    "synthetic (seeded GPU generators; colours from position plus noise)")
+    out.update({"breakdown_ms": {"build_values": round(op[0], 4),
+                                 "merge_values": round(op[1], 4)},
+                "geometry_only_ms": round(float(np.mean(plain)), 4),
+                "value_overhead_ms": round(total / args.steps - float(np.mean(plain)), 4),
+                "merged_u": u, "gpu_launches": int(launches), "clocks": clk})
+    return out
+
+
 # ------------------------------------------------------------ oracle (CPU)
 def oracle_step(orc, og, scene, queries, n_sample):
     t0 = time.perf_counter()
@@ -732,6 +796,8 @@ def main():
         out = run_single(args, world_size, local_rank, torch, cga, args.config)
     elif args.config == "batched":
         out = run_batched(args, world_size, local_rank, torch, cga)
+    elif args.config == "values":
+        out = run_values(args, world_size, local_rank, torch, cga)
     else:
         out = run_served(args, world_size, local_rank, torch, cga)
     if rank == 0:

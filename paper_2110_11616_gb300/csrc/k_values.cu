@@ -8,8 +8,9 @@
 //   k_merge_values      per voxel of a merge: the row of the input holding
 //                       it; in both, the base's (a's) row or the average
 //                       (a + b + 1) / 2 (Sec. II-A)
-// Sums are 64-bit integer atomics (no overflow for any number of points per
-// voxel), so every result is independent of the order in which points arrive.
+// Sums are integer atomics, 32-bit when no voxel can reach 2^32 (n * 255 <
+// 2^32) and 64-bit otherwise, so every result is independent of the order in
+// which points arrive.
 #include <algorithm>
 
 #include "k_common.cuh"
@@ -18,6 +19,7 @@ namespace libcga {
 
 namespace {
 
+template <typename S>
 __global__ void k_value_accumulate(Levels a, ValueInput in, void* scratch) {
   const uint32_t h = (uint32_t)a.hdr->cnt[2];
   const uint32_t C = in.channels;
@@ -38,15 +40,14 @@ __global__ void k_value_accumulate(Levels a, ValueInput in, void* scratch) {
     if (in.policy == kValueFirst) {
       atomicMin(static_cast<uint32_t*>(scratch) + v, (uint32_t)i);
     } else {
-      unsigned long long* s = static_cast<unsigned long long*>(scratch) + (size_t)v * (C + 1);
-      for (uint32_t c = 0; c < C; ++c) {
-        atomicAdd(s + c, (unsigned long long)__ldg(in.attr + i * C + c));
-      }
-      atomicAdd(s + C, 1ull);
+      S* s = static_cast<S*>(scratch) + (size_t)v * (C + 1);
+      for (uint32_t c = 0; c < C; ++c) atomicAdd(s + c, (S)__ldg(in.attr + i * C + c));
+      atomicAdd(s + C, (S)1);
     }
   }
 }
 
+template <typename S>
 __global__ void k_value_finalize(Levels a, ValueInput in, const void* scratch, uint8_t* values) {
   const uint32_t u = (uint32_t)a.hdr->cnt[0];
   const uint32_t C = in.channels;
@@ -58,9 +59,8 @@ __global__ void k_value_finalize(Levels a, ValueInput in, const void* scratch, u
         values[(size_t)v * C + c] = i < in.n ? __ldg(in.attr + (size_t)i * C + c) : (uint8_t)0;
       }
     } else {
-      const unsigned long long* s =
-          static_cast<const unsigned long long*>(scratch) + (size_t)v * (C + 1);
-      const unsigned long long k = s[C];
+      const S* s = static_cast<const S*>(scratch) + (size_t)v * (C + 1);
+      const S k = s[C];
       for (uint32_t c = 0; c < C; ++c) {
         values[(size_t)v * C + c] = k > 0 ? (uint8_t)((s[c] + k / 2) / k) : (uint8_t)0;
       }
@@ -125,17 +125,29 @@ unsigned blocks_for(uint64_t work) {
 
 }  // namespace
 
+// 32-bit sums suffice while n points of at most 255 each cannot reach 2^32.
+static bool narrow_sums(uint64_t n) { return n * 255ull < (1ull << 32); }
+
 size_t value_scratch_bytes(uint64_t cap, uint32_t channels, int policy) {
+  // sized for the wider sums: the count n is not known here
   return (size_t)std::max<uint64_t>(cap, 1) * (policy == kValueFirst ? 4 : 8 * (channels + 1));
 }
 
 cudaError_t run_build_values(const Levels& a, const ValueInput& in, void* scratch,
                              uint8_t* values, cudaStream_t stream) {
-  const size_t bytes = value_scratch_bytes(a.cap, in.channels, in.policy);
+  const bool narrow = in.policy != kValueFirst && narrow_sums(in.n);
+  const size_t bytes = narrow ? (size_t)std::max<uint64_t>(a.cap, 1) * 4 * (in.channels + 1)
+                              : value_scratch_bytes(a.cap, in.channels, in.policy);
   cudaError_t e = cudaMemsetAsync(scratch, in.policy == kValueFirst ? 0xff : 0, bytes, stream);
   if (e != cudaSuccess) return e;
-  k_value_accumulate<<<blocks_for(in.n), 256, 0, stream>>>(a, in, scratch);
-  k_value_finalize<<<blocks_for(a.cap), 256, 0, stream>>>(a, in, scratch, values);
+  if (narrow) {
+    k_value_accumulate<uint32_t><<<blocks_for(in.n), 256, 0, stream>>>(a, in, scratch);
+    k_value_finalize<uint32_t><<<blocks_for(a.cap), 256, 0, stream>>>(a, in, scratch, values);
+  } else {
+    k_value_accumulate<unsigned long long><<<blocks_for(in.n), 256, 0, stream>>>(a, in, scratch);
+    k_value_finalize<unsigned long long><<<blocks_for(a.cap), 256, 0, stream>>>(a, in, scratch,
+                                                                             values);
+  }
   count_launch(2);
   return cudaGetLastError();
 }
