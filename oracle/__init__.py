@@ -92,6 +92,7 @@ def lib():
         _lib.orc_project.argtypes = [ctypes.POINTER(_Cga), ctypes.c_int,
                                      ctypes.POINTER(_Cga2d)]
         _lib.orc_query_voxels.argtypes = [P, U64, F, P, P, P]
+        _lib.orc_perspective.argtypes = [ctypes.POINTER(_Cga), P, F, F, F, U32, U32, P, P]
         _lib.orc_build_values.argtypes = [P, P, U32, U64, U32, F, P, P, ctypes.c_int,
                                           ctypes.POINTER(_Cga), P]
         _lib.orc_merge_values.argtypes = [ctypes.POINTER(_Cga), P, ctypes.POINTER(_Cga), P, U32,
@@ -296,6 +297,18 @@ def merge_values(a: Cga, va, b: Cga, vb, policy="base"):
                                   MERGE_POLICIES[policy], ctypes.byref(s), _ptr(vals)))
     c = _from_struct(s, arrs)
     return c, vals[:c.u].copy()
+
+
+def perspective(a: Cga, eye, cos_t: float, sin_t: float, D: float, W: int, H: int):
+    """Perspective z-buffer image (Eq. 5-6): (index (H, W) uint32, depth (H, W) float32)."""
+    e = np.ascontiguousarray(np.asarray(eye, np.float32).reshape(3))
+    idx = np.zeros(W * H, np.uint32)
+    dep = np.zeros(W * H, np.float32)
+    s = a._struct()
+    _check(lib().orc_perspective(ctypes.byref(s), _ptr(e), float(np.float32(cos_t)),
+                                 float(np.float32(sin_t)), float(np.float32(D)), W, H, _ptr(idx),
+                                 _ptr(dep)))
+    return idx.reshape(H, W), dep.reshape(H, W)
 
 
 PLANES = {"xy": 0, "xz": 1, "yz": 2}

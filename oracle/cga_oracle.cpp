@@ -508,4 +508,40 @@ int orc_merge_values(const orc_cga* a, const uint8_t* va, const orc_cga* b, cons
   return orc_from_sorted_keys(ko.data(), ko.size(), a->bits, out);
 }
 
+// Eq. 6 (rotation about y) then Eq. 5 (perspective divide onto the plane at
+// D); a pixel keeps its nearest voxel (a z-buffer), ties to the smaller index.
+int orc_perspective(const orc_cga* a, const float eye[3], float cos_t, float sin_t, float D,
+                    uint32_t W, uint32_t H, uint32_t* index, float* depth) {
+  if (W == 0 || H == 0 || !(D > 0.0f)) return ORC_ERR_INVALID_ARG;
+  const uint64_t npix = (uint64_t)W * H;
+  for (uint64_t i = 0; i < npix; ++i) {
+    index[i] = 0xffffffffu;
+    depth[i] = INFINITY;
+  }
+  std::vector<uint32_t> xyz(a->u * 3);
+  if (orc_decode(a, xyz.data()) != ORC_OK) return ORC_ERR_INVALID_ARG;
+  const float half_w = (float)W * 0.5f, half_h = (float)H * 0.5f;
+  const float neg_sin = -sin_t;
+  for (uint64_t p = 0; p < a->u; ++p) {
+    const float sx = (float)xyz[3 * p] - eye[0];
+    const float sy = (float)xyz[3 * p + 1] - eye[1];
+    const float sz = (float)xyz[3 * p + 2] - eye[2];
+    const float m1 = neg_sin * sz;
+    const float xr = std::fmaf(cos_t, sx, m1);
+    const float m2 = cos_t * sz;
+    const float zr = std::fmaf(sin_t, sx, m2);
+    if (!(zr > 0.0f)) continue;
+    const float nx = D * xr, ny = D * sy;
+    const float px = nx / zr, py = ny / zr;
+    const float fu = std::floor(px + half_w), fv = std::floor(py + half_h);
+    if (!(fu >= 0.0f && fu < (float)W && fv >= 0.0f && fv < (float)H)) continue;
+    const uint64_t pix = (uint64_t)fv * W + (uint64_t)fu;
+    if (zr < depth[pix] || (zr == depth[pix] && p < index[pix])) {
+      depth[pix] = zr;
+      index[pix] = (uint32_t)p;
+    }
+  }
+  return ORC_OK;
+}
+
 }  // extern "C"

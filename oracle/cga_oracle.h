@@ -130,6 +130,21 @@ int orc_build_values(const float* xyz, const uint8_t* attr, uint32_t channels, u
 int orc_merge_values(const orc_cga* a, const uint8_t* va, const orc_cga* b, const uint8_t* vb,
                      uint32_t channels, int policy, orc_cga* out, uint8_t* values);
 
+/* ---- Perspective projection (Eq. 5-6, rotation about y) --------------------
+ * Each stored voxel (x, y, z) becomes s = (x - ex, y - ey, z - ez) in float
+ * (voxel units, eye e), is rotated about the y axis by theta (Eq. 6 matrix:
+ * x' = cos*sx - sin*sz, z' = sin*sx + cos*sz, y' = sy; cos and sin given as
+ * floats) and projected onto the plane at distance D (Eq. 5): px = D*x'/z',
+ * py = D*y'/z'.  Voxels with z' <= 0 are behind the eye and dropped.  Pixel
+ * (floor(px + W/2), floor(py + H/2)) inside a W x H image keeps the voxel of
+ * least z' (ties: the smaller CGA index).  Every step is one float
+ * operation in this order: fmaf(cos, sx, (-sin)*sz) and fmaf(sin, sx, cos*sz)
+ * for the rotation, (D*x')/z' for the projection, floor(px + W/2) for the
+ * pixel.  Outputs: index[v*W+u] = CGA index or UINT32_MAX, depth[v*W+u] = z'
+ * (+inf when empty). */
+int orc_perspective(const orc_cga* a, const float eye[3], float cos_t, float sin_t, float D,
+                    uint32_t W, uint32_t H, uint32_t* index, float* depth);
+
 #ifdef __cplusplus
 }
 #endif
