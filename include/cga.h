@@ -258,6 +258,23 @@ int cga_merge_values(const cga_t* a, const cga_t* b, int policy, const cga_alloc
  * NULL and 0 when a has no values. */
 int cga_values(const cga_t* a, const uint8_t** d_values, uint32_t* channels);
 
+/* ---- Perspective projection (Eq. 5-6) ---------------------------------------
+ * Each stored voxel (x, y, z) is taken to the eye's frame, s = (x - eye[0],
+ * y - eye[1], z - eye[2]) (float, voxel units), rotated about the y axis by
+ * the angle whose cosine and sine are cos_t, sin_t (Eq. 6: x' = cos*sx -
+ * sin*sz, z' = sin*sx + cos*sz, y' = sy) and divided onto the plane at
+ * distance D (Eq. 5: px = D*x'/z', py = D*y'/z').  Voxels with z' <= 0 are
+ * dropped.  Pixel (floor(px + W/2), floor(py + H/2)) of the W x H image keeps
+ * the voxel of least z', ties to the smaller CGA index.  Each step is one IEEE
+ * float operation in this order: fmaf(cos, sx, (-sin)*sz), fmaf(sin, sx,
+ * cos*sz), (D*x')/z', floor(px + W/2).
+ * d_index (W*H, device): CGA index of the pixel's voxel or UINT32_MAX;
+ * d_depth (W*H, device): its z' or +inf.  Row-major (v*W + u).  Scratch of
+ * 8*W*H bytes from a's allocator. */
+#define CGA_MAX_PIXELS (1ull << 28)
+int cga_perspective(const cga_t* a, const float eye[3], float cos_t, float sin_t, float D,
+                    uint32_t W, uint32_t H, uint32_t* d_index, float* d_depth, void* stream);
+
 /* ---- Batched forms: one set of kernel launches serves every item. --------
  * Each item has the semantics of the single call; handles are independent
  * (free each one).  On an error nothing is returned and no handle leaks. */

@@ -40,7 +40,7 @@ EXPORTS = (
     "cga_server_free", "cga_now_ns", "cga_nn_sort_queries", "cga_nn_query_ordered",
     "cga_nn_prepare", "cga_nn_prepare_levels", "cga_nn_autotune",
     "cga_tuning_set", "cga_tuning_get", "cga_autotune", "cga_pipeline_autotune",
-    "cga_build_values", "cga_merge_values", "cga_values",
+    "cga_build_values", "cga_merge_values", "cga_values", "cga_perspective",
     "cga_selftest_wait_timeout",
 )
 
@@ -699,6 +699,25 @@ def cga_nn_autotune(a: Cga, sample_queries, stream=None):
                                chosen, times, _stream(stream)), "cga_nn_autotune")
     shifts = tuple(int(v) for v in chosen if v != 0)
     return shifts, {c: float(t) for c, t in zip(NN_AUTOTUNE_CANDIDATES, times) if t >= 0}
+
+
+# ------------------------------------------------------ perspective projection
+def cga_perspective(a: Cga, eye, cos_t: float, sin_t: float, D: float, W: int, H: int,
+                    stream=None):
+    """Perspective z-buffer image of a (Eq. 5-6): (index (H, W) int32 tensor holding
+    uint32 values, depth (H, W) float32 tensor)."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_perspective.argtypes = [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_uint32, ctypes.c_uint32, P, P, P]
+    e = np.ascontiguousarray(np.asarray(eye, np.float32).reshape(3))
+    idx = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    dep = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    _check(lib.cga_perspective(a.ptr, e.ctypes.data_as(P), float(cos_t), float(sin_t), float(D),
+                               W, H, P(idx.data_ptr()), P(dep.data_ptr()), _stream(stream)),
+           "cga_perspective")
+    return idx, dep
 
 
 # ------------------------------------------------------------- value array

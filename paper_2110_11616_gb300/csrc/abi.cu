@@ -418,6 +418,32 @@ int cga_merge_values(const cga_t* a, const cga_t* b, int policy, const cga_alloc
   return CGA_OK;
 }
 
+int cga_perspective(const cga_t* a, const float eye[3], float cos_t, float sin_t, float D,
+                    uint32_t W, uint32_t H, uint32_t* d_index, float* d_depth, void* stream) {
+  if (a == nullptr || eye == nullptr || d_index == nullptr || d_depth == nullptr || W == 0 ||
+      H == 0 || (uint64_t)W * H > CGA_MAX_PIXELS || !(D > 0.0f) || !std::isfinite(D) ||
+      !std::isfinite(cos_t) || !std::isfinite(sin_t) || !std::isfinite(eye[0]) ||
+      !std::isfinite(eye[1]) || !std::isfinite(eye[2])) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  const uint64_t npix = (uint64_t)W * H;
+  void* zbuf = dalloc(A, npix * 8, s);
+  if (zbuf == nullptr) return CGA_ERR_OOM;
+  libcga::Camera cam{};
+  for (int k = 0; k < 3; ++k) cam.eye[k] = eye[k];
+  cam.cos_t = cos_t;
+  cam.sin_t = sin_t;
+  cam.D = D;
+  cam.W = W;
+  cam.H = H;
+  const int rc = cuda_rc(libcga::run_perspective(
+      a->lv, cam, static_cast<unsigned long long*>(zbuf), d_index, d_depth, s));
+  dfree(A, a->has_alloc, zbuf, s);
+  return rc;
+}
+
 int cga_values(const cga_t* a, const uint8_t** d_values, uint32_t* channels) {
   if (a == nullptr || d_values == nullptr || channels == nullptr) return CGA_ERR_INVALID_ARG;
   *d_values = a->values;

@@ -199,6 +199,17 @@ cudaError_t run_merge_values(const Levels& m, const Levels& a, const Levels& b, 
                              const uint8_t* vb, uint32_t channels, int policy, uint8_t* vm,
                              cudaStream_t stream);
 
+// ---- Perspective projection (Eq. 5-6) ---------------------------------------
+struct Camera {
+  float eye[3];         // voxel units
+  float cos_t, sin_t;   // rotation about the y axis
+  float D;              // distance of the projection plane
+  uint32_t W, H;        // image size in pixels
+};
+// index / depth: W * H pixels; zbuf: W * H 64-bit words of scratch.
+cudaError_t run_perspective(const Levels& a, const Camera& cam, unsigned long long* zbuf,
+                            uint32_t* index, float* depth, cudaStream_t stream);
+
 // Copy the top two levels of a CGA into a 2-level projection (plane xy).
 cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stream);
 struct ProjPair {
