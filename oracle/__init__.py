@@ -92,6 +92,9 @@ def lib():
         _lib.orc_project.argtypes = [ctypes.POINTER(_Cga), ctypes.c_int,
                                      ctypes.POINTER(_Cga2d)]
         _lib.orc_query_voxels.argtypes = [P, U64, F, P, P, P]
+        _lib.orc_radius_count.argtypes = [ctypes.POINTER(_Cga), F, P, P, U64, U64, P]
+        _lib.orc_radius_fill.argtypes = [ctypes.POINTER(_Cga), F, P, P, U64, U64, P, P, P]
+        _lib.orc_knn.argtypes = [ctypes.POINTER(_Cga), F, P, P, U64, U32, P, P]
         _lib.orc_perspective.argtypes = [ctypes.POINTER(_Cga), P, F, F, F, U32, U32, P, P]
         _lib.orc_build_values.argtypes = [P, P, U32, U64, U32, F, P, P, ctypes.c_int,
                                           ctypes.POINTER(_Cga), P]
@@ -297,6 +300,37 @@ def merge_values(a: Cga, va, b: Cga, vb, policy="base"):
                                   MERGE_POLICIES[policy], ctypes.byref(s), _ptr(vals)))
     c = _from_struct(s, arrs)
     return c, vals[:c.u].copy()
+
+
+def radius(a: Cga, grid: Grid, q, r2: int):
+    """Radius search: (offsets (m+1,) uint64, idx uint32, dist2 uint64) with query j's
+    voxels, ascending CGA index, at [offsets[j], offsets[j+1])."""
+    qq = _f32xyz(q)
+    off = grid.offset_array()
+    s = a._struct()
+    counts = np.zeros(max(len(qq), 1), np.uint64)
+    _check(lib().orc_radius_count(ctypes.byref(s), grid.scale, _ptr(off), _ptr(qq), len(qq),
+                                  int(r2), _ptr(counts)))
+    offsets = np.zeros(len(qq) + 1, np.uint64)
+    offsets[1:] = np.cumsum(counts[:len(qq)])
+    total = int(offsets[-1])
+    idx = np.zeros(max(total, 1), np.uint32)
+    d2 = np.zeros(max(total, 1), np.uint64)
+    _check(lib().orc_radius_fill(ctypes.byref(s), grid.scale, _ptr(off), _ptr(qq), len(qq),
+                                 int(r2), _ptr(offsets), _ptr(idx), _ptr(d2)))
+    return offsets, idx[:total], d2[:total]
+
+
+def knn(a: Cga, grid: Grid, q, k: int):
+    """k nearest stored voxels per query by (distance^2, key): (idx (m, k), dist2 (m, k))."""
+    qq = _f32xyz(q)
+    off = grid.offset_array()
+    s = a._struct()
+    idx = np.zeros(max(len(qq) * k, 1), np.uint32)
+    d2 = np.zeros(max(len(qq) * k, 1), np.uint64)
+    _check(lib().orc_knn(ctypes.byref(s), grid.scale, _ptr(off), _ptr(qq), len(qq), k,
+                         _ptr(idx), _ptr(d2)))
+    return idx[:len(qq) * k].reshape(len(qq), k), d2[:len(qq) * k].reshape(len(qq), k)
 
 
 def perspective(a: Cga, eye, cos_t: float, sin_t: float, D: float, W: int, H: int):

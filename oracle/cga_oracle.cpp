@@ -544,4 +544,73 @@ int orc_perspective(const orc_cga* a, const float eye[3], float cos_t, float sin
   return ORC_OK;
 }
 
+// Radius search by exhaustive scan in CGA order: every voxel within the
+// squared radius, ascending index.
+int orc_radius_count(const orc_cga* a, float scale, const float offset[3], const float* q,
+                     uint64_t m, uint64_t r2, uint64_t* counts) {
+  std::vector<uint64_t> keys(a->u);
+  if (orc_decode_keys(a, keys.data()) != ORC_OK) return ORC_ERR_INVALID_ARG;
+  const uint32_t b = a->bits;
+  for (uint64_t j = 0; j < m; ++j) {
+    const Query Q = make_query(q + 3 * j, scale, offset);
+    uint64_t c = 0;
+    if (Q.valid) {
+      for (uint64_t i = 0; i < a->u; ++i) {
+        if (dist2(Q.q, key_x(keys[i], b), key_y(keys[i], b), key_z(keys[i], b)) <= r2) ++c;
+      }
+    }
+    counts[j] = c;
+  }
+  return ORC_OK;
+}
+
+int orc_radius_fill(const orc_cga* a, float scale, const float offset[3], const float* q,
+                    uint64_t m, uint64_t r2, const uint64_t* offsets, uint32_t* idx,
+                    uint64_t* dist2_out) {
+  std::vector<uint64_t> keys(a->u);
+  if (orc_decode_keys(a, keys.data()) != ORC_OK) return ORC_ERR_INVALID_ARG;
+  const uint32_t b = a->bits;
+  for (uint64_t j = 0; j < m; ++j) {
+    const Query Q = make_query(q + 3 * j, scale, offset);
+    if (!Q.valid) continue;
+    uint64_t o = offsets[j];
+    for (uint64_t i = 0; i < a->u; ++i) {
+      const uint64_t d = dist2(Q.q, key_x(keys[i], b), key_y(keys[i], b), key_z(keys[i], b));
+      if (d <= r2) {
+        idx[o] = (uint32_t)i;
+        dist2_out[o] = d;
+        ++o;
+      }
+    }
+  }
+  return ORC_OK;
+}
+
+// k nearest by exhaustive search: the k least (distance^2, key) pairs.
+int orc_knn(const orc_cga* a, float scale, const float offset[3], const float* q, uint64_t m,
+            uint32_t k, uint32_t* idx, uint64_t* dist2_out) {
+  if (k == 0) return ORC_ERR_INVALID_ARG;
+  std::vector<uint64_t> keys(a->u);
+  if (orc_decode_keys(a, keys.data()) != ORC_OK) return ORC_ERR_INVALID_ARG;
+  const uint32_t b = a->bits;
+  std::vector<std::pair<uint64_t, uint64_t>> cand(a->u);  // (distance^2, index); index order = key order
+  for (uint64_t j = 0; j < m; ++j) {
+    const Query Q = make_query(q + 3 * j, scale, offset);
+    uint64_t n = 0;
+    if (Q.valid) {
+      for (uint64_t i = 0; i < a->u; ++i) {
+        cand[i] = {dist2(Q.q, key_x(keys[i], b), key_y(keys[i], b), key_z(keys[i], b)), i};
+      }
+      n = a->u;
+    }
+    const uint64_t take = std::min<uint64_t>(k, n);
+    std::partial_sort(cand.begin(), cand.begin() + take, cand.begin() + n);
+    for (uint32_t t = 0; t < k; ++t) {
+      idx[j * k + t] = t < take ? (uint32_t)cand[t].second : UINT32_MAX;
+      dist2_out[j * k + t] = t < take ? cand[t].first : UINT64_MAX;
+    }
+  }
+  return ORC_OK;
+}
+
 }  // extern "C"

@@ -145,6 +145,21 @@ int orc_merge_values(const orc_cga* a, const uint8_t* va, const orc_cga* b, cons
 int orc_perspective(const orc_cga* a, const float eye[3], float cos_t, float sin_t, float D,
                     uint32_t W, uint32_t H, uint32_t* index, float* depth);
 
+/* ---- Radius search and k-NN (the Eq. 8 set generalised) --------------------
+ * Query voxels as for NN.  Radius: every stored voxel with squared integer
+ * distance <= r2, in ascending CGA index.  counts[j] = how many; fill writes
+ * query j's voxels at [offsets[j], offsets[j] + counts[j]).  Non-finite query:
+ * none.  k-NN: the k stored voxels of least (distance^2, key), ascending; slots
+ * beyond the number of stored voxels (or for a non-finite query) hold
+ * UINT32_MAX / UINT64_MAX.  idx and dist2 hold m * k entries. */
+int orc_radius_count(const orc_cga* a, float scale, const float offset[3], const float* q,
+                     uint64_t m, uint64_t r2, uint64_t* counts);
+int orc_radius_fill(const orc_cga* a, float scale, const float offset[3], const float* q,
+                    uint64_t m, uint64_t r2, const uint64_t* offsets, uint32_t* idx,
+                    uint64_t* dist2);
+int orc_knn(const orc_cga* a, float scale, const float offset[3], const float* q, uint64_t m,
+            uint32_t k, uint32_t* idx, uint64_t* dist2);
+
 #ifdef __cplusplus
 }
 #endif
