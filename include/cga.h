@@ -258,6 +258,30 @@ int cga_merge_values(const cga_t* a, const cga_t* b, int policy, const cga_alloc
  * NULL and 0 when a has no values. */
 int cga_values(const cga_t* a, const uint8_t** d_values, uint32_t* channels);
 
+/* ---- Radius search (the Eq. 8 set within a radius) -------------------------
+ * Query voxels as for cga_nn_query.  Query j's result is every stored voxel
+ * with squared integer distance <= r2 (voxel units), in ascending CGA index.
+ * cga_radius_count writes d_offsets (m + 1 uint64, device): the exclusive
+ * prefix of the per-query counts, d_offsets[m] = the total (read it to size
+ * the outputs).  cga_radius_fill then writes query j's voxels at
+ * [d_offsets[j], d_offsets[j + 1]) of d_idx (CGA index) and d_dist2.  A
+ * non-finite query has none.  r2 <= CGA_MAX_RADIUS2. */
+#define CGA_MAX_RADIUS2 (1ull << 62)
+int cga_radius_count(const cga_t* a, const float* d_q, uint64_t m, uint64_t r2,
+                     uint64_t* d_offsets, void* stream);
+int cga_radius_fill(const cga_t* a, const float* d_q, uint64_t m, uint64_t r2,
+                    const uint64_t* d_offsets, uint32_t* d_idx, uint64_t* d_dist2,
+                    void* stream);
+
+/* k nearest stored voxels of each query: the k least (squared integer
+ * distance, key) pairs, ascending, at d_idx / d_dist2 [j * k, j * k + k)
+ * (device, m * k entries each).  Slots past the number of stored voxels,
+ * and all slots of a non-finite query, hold UINT32_MAX / UINT64_MAX.
+ * k = 1 is cga_nn_query's answer.  1 <= k <= CGA_KNN_MAX_K. */
+#define CGA_KNN_MAX_K 32
+int cga_knn(const cga_t* a, const float* d_q, uint64_t m, uint32_t k, uint32_t* d_idx,
+            uint64_t* d_dist2, void* stream);
+
 /* ---- Perspective projection (Eq. 5-6) ---------------------------------------
  * Each stored voxel (x, y, z) is taken to the eye's frame, s = (x - eye[0],
  * y - eye[1], z - eye[2]) (float, voxel units), rotated about the y axis by

@@ -41,6 +41,7 @@ EXPORTS = (
     "cga_nn_prepare", "cga_nn_prepare_levels", "cga_nn_autotune",
     "cga_tuning_set", "cga_tuning_get", "cga_autotune", "cga_pipeline_autotune",
     "cga_build_values", "cga_merge_values", "cga_values", "cga_perspective",
+    "cga_radius_count", "cga_radius_fill", "cga_knn",
     "cga_selftest_wait_timeout",
 )
 
@@ -699,6 +700,46 @@ def cga_nn_autotune(a: Cga, sample_queries, stream=None):
                                chosen, times, _stream(stream)), "cga_nn_autotune")
     shifts = tuple(int(v) for v in chosen if v != 0)
     return shifts, {c: float(t) for c, t in zip(NN_AUTOTUNE_CANDIDATES, times) if t >= 0}
+
+
+# ------------------------------------------------------------ radius search
+def cga_radius(a: Cga, queries, r2: int, stream=None):
+    """Every stored voxel within squared distance r2 of each query: (offsets (m+1)
+    int64, idx int32 holding uint32, dist2 int64), query j's at [offsets[j],
+    offsets[j+1]) in ascending CGA index.  Waits once for the total."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_radius_count.argtypes = [P, P, ctypes.c_uint64, ctypes.c_uint64, P, P]
+    lib.cga_radius_fill.argtypes = [P, P, ctypes.c_uint64, ctypes.c_uint64, P, P, P, P]
+    _dev_f32(queries, "cga_radius")
+    m = queries.numel() // 3
+    offsets = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    _check(lib.cga_radius_count(a.ptr, P(queries.data_ptr()), m, int(r2), P(offsets.data_ptr()),
+                                _stream(stream)), "cga_radius_count")
+    total = int(offsets[m].item())
+    idx = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
+    d2 = torch.empty(max(total, 1), dtype=torch.int64, device="cuda")
+    _check(lib.cga_radius_fill(a.ptr, P(queries.data_ptr()), m, int(r2), P(offsets.data_ptr()),
+                               P(idx.data_ptr()), P(d2.data_ptr()), _stream(stream)),
+           "cga_radius_fill")
+    return offsets, idx[:total], d2[:total]
+
+
+def cga_knn(a: Cga, queries, k: int, stream=None):
+    """The k nearest stored voxels of each query: (idx (m, k) int32 holding uint32,
+    dist2 (m, k) int64 holding uint64), ascending by (distance^2, key)."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_knn.argtypes = [P, P, ctypes.c_uint64, ctypes.c_uint32, P, P, P]
+    _dev_f32(queries, "cga_knn")
+    m = queries.numel() // 3
+    idx = torch.empty((m, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((m, k), dtype=torch.int64, device="cuda")
+    _check(lib.cga_knn(a.ptr, P(queries.data_ptr()), m, k, P(idx.data_ptr()), P(d2.data_ptr()),
+                       _stream(stream)), "cga_knn")
+    return idx, d2
 
 
 # ------------------------------------------------------ perspective projection

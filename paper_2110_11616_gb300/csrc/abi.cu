@@ -418,6 +418,60 @@ int cga_merge_values(const cga_t* a, const cga_t* b, int policy, const cga_alloc
   return CGA_OK;
 }
 
+namespace {
+
+libcga::SearchSeg search_segment(const cga_t* a, const float* d_q, uint64_t m) {
+  libcga::SearchSeg sg{};
+  sg.a = a->lv;
+  sg.scale = a->grid.scale;
+  for (int k = 0; k < 3; ++k) sg.off[k] = a->grid.offset[k];
+  sg.q = d_q;
+  sg.m = (uint32_t)m;
+  return sg;
+}
+
+}  // namespace
+
+int cga_radius_count(const cga_t* a, const float* d_q, uint64_t m, uint64_t r2,
+                     uint64_t* d_offsets, void* stream) {
+  if (a == nullptr || d_offsets == nullptr || (m > 0 && d_q == nullptr) || m > CGA_MAX_POINTS ||
+      r2 > CGA_MAX_RADIUS2) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  void* scratch = dalloc(A, libcga::radius_scratch_bytes(), s);
+  if (scratch == nullptr) return CGA_ERR_OOM;
+  const int rc = cuda_rc(libcga::run_radius_count(search_segment(a, d_q, m), r2,
+                                                  reinterpret_cast<unsigned long long*>(d_offsets),
+                                                  scratch, s));
+  dfree(A, a->has_alloc, scratch, s);
+  return rc;
+}
+
+int cga_radius_fill(const cga_t* a, const float* d_q, uint64_t m, uint64_t r2,
+                    const uint64_t* d_offsets, uint32_t* d_idx, uint64_t* d_dist2,
+                    void* stream) {
+  if (a == nullptr || (m > 0 && (d_q == nullptr || d_offsets == nullptr)) ||
+      m > CGA_MAX_POINTS || r2 > CGA_MAX_RADIUS2) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  return cuda_rc(libcga::run_radius_fill(
+      search_segment(a, d_q, m), r2, reinterpret_cast<const unsigned long long*>(d_offsets),
+      d_idx, reinterpret_cast<unsigned long long*>(d_dist2), static_cast<cudaStream_t>(stream)));
+}
+
+int cga_knn(const cga_t* a, const float* d_q, uint64_t m, uint32_t k, uint32_t* d_idx,
+            uint64_t* d_dist2, void* stream) {
+  if (a == nullptr || k < 1 || k > CGA_KNN_MAX_K || m > CGA_MAX_POINTS ||
+      (m > 0 && (d_q == nullptr || d_idx == nullptr || d_dist2 == nullptr))) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  return cuda_rc(libcga::run_knn(search_segment(a, d_q, m), k, d_idx,
+                                 reinterpret_cast<unsigned long long*>(d_dist2),
+                                 static_cast<cudaStream_t>(stream)));
+}
+
 int cga_perspective(const cga_t* a, const float eye[3], float cos_t, float sin_t, float D,
                     uint32_t W, uint32_t H, uint32_t* d_index, float* d_depth, void* stream) {
   if (a == nullptr || eye == nullptr || d_index == nullptr || d_depth == nullptr || W == 0 ||

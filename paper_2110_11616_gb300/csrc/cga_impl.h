@@ -199,6 +199,26 @@ cudaError_t run_merge_values(const Levels& m, const Levels& a, const Levels& b, 
                              const uint8_t* vb, uint32_t channels, int policy, uint8_t* vm,
                              cudaStream_t stream);
 
+// ---- Radius search and k-NN ------------------------------------------------
+// One CGA and its queries (grid as the CGA's).
+struct SearchSeg {
+  Levels a;
+  float scale;
+  float off[3];
+  const float* q;  // m points, float32 AoS
+  uint32_t m;
+};
+size_t radius_scratch_bytes();
+// offsets (m + 1): exclusive prefix of the per-query counts, offsets[m] = total.
+cudaError_t run_radius_count(const SearchSeg& sg, unsigned long long r2,
+                             unsigned long long* offsets, void* scratch, cudaStream_t stream);
+cudaError_t run_radius_fill(const SearchSeg& sg, unsigned long long r2,
+                            const unsigned long long* offsets, uint32_t* idx,
+                            unsigned long long* d2, cudaStream_t stream);
+// idx, d2: m * k entries (k <= 32), query j's k nearest ascending.
+cudaError_t run_knn(const SearchSeg& sg, uint32_t k, uint32_t* idx, unsigned long long* d2,
+                    cudaStream_t stream);
+
 // ---- Perspective projection (Eq. 5-6) ---------------------------------------
 struct Camera {
   float eye[3];         // voxel units

@@ -75,6 +75,15 @@ __device__ __forceinline__ uint32_t quantize_axis(float v, float scale, float of
   return (uint32_t)f;
 }
 
+// Query voxel coordinate of an NN / radius / k-NN search: floorf(fmaf(v,
+// scale, off)) clamped only to [-2^30, 2^30] (queries outside the box keep
+// their true distance).
+__device__ __forceinline__ long long quantize_query(float v, float scale, float off) {
+  float f = floorf(__fmaf_rn(v, scale, off));
+  f = fminf(fmaxf(f, -1073741824.0f), 1073741824.0f);
+  return (long long)f;
+}
+
 // Voxel key x << 2b | y << b | z of one point, after the rigid transform X
 // (R row-major, then t) by the fixed fmaf nesting when has_x.  False for a
 // non-finite point or transform result (key left 0).

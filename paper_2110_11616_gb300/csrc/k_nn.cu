@@ -37,12 +37,6 @@ __device__ __forceinline__ int find_nn_seg(const NnSeg* __restrict__ segs, int S
   return lo;
 }
 
-__device__ __forceinline__ long long quantize_query(float v, float scale, float off) {
-  float f = floorf(__fmaf_rn(v, scale, off));
-  f = fminf(fmaxf(f, -1073741824.0f), 1073741824.0f);
-  return (long long)f;
-}
-
 __device__ __forceinline__ unsigned long long absdiff(long long a, long long b) {
   return (unsigned long long)(a > b ? a - b : b - a);
 }

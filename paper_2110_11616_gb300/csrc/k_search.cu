@@ -1,0 +1,371 @@
+// Radius search and k-NN over a CGA (the Eq. 8 set generalised): every
+// stored voxel within a squared integer distance r2 of each query voxel in
+// ascending CGA index, or the k least (distance^2, key) in ascending order.
+//   k_radius_count  one warp per query: the slabs whose x lies within the
+//                   radius are shared 32 at a time among the lanes; a lane
+//                   walks its slab's columns inside the circle left for y and
+//                   counts each column's z interval by two searches
+//   k_scan_*        exclusive prefix of the counts (64-bit offsets)
+//   k_radius_fill   the same walk; per group of 32 slabs a warp scan of the
+//                   lanes' counts places every slab's voxels, so the output
+//                   is in (x, y, z) = CGA order without sorting
+#include <algorithm>
+
+#include "k_common.cuh"
+
+namespace libcga {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long absdiff_ll(long long a, long long b) {
+  return (unsigned long long)(a > b ? a - b : b - a);
+}
+
+// Largest s with s * s <= v (v < 2^63).
+__device__ __forceinline__ unsigned long long isqrt_u64(unsigned long long v) {
+  unsigned long long s = (unsigned long long)sqrt((double)v);
+  while (s > 0 && s * s > v) --s;
+  while ((s + 1) * (s + 1) <= v) ++s;
+  return s;
+}
+
+struct RQuery {
+  long long x, y, z;  // query voxel (unclamped)
+  bool valid;
+};
+
+__device__ __forceinline__ RQuery radius_query(const SearchSeg& sg, uint32_t j) {
+  const float* p = sg.q + 3 * (size_t)j;
+  const float px = __ldg(p), py = __ldg(p + 1), pz = __ldg(p + 2);
+  RQuery q;
+  q.valid = isfinite(px) && isfinite(py) && isfinite(pz);
+  q.x = q.valid ? quantize_query(px, sg.scale, sg.off[0]) : 0;
+  q.y = q.valid ? quantize_query(py, sg.scale, sg.off[1]) : 0;
+  q.z = q.valid ? quantize_query(pz, sg.scale, sg.off[2]) : 0;
+  return q;
+}
+
+// Slabs [s0, s1) of a whose x lies within the radius of the query.
+__device__ __forceinline__ void radius_slabs(const Levels& a, uint32_t h, const RQuery& q,
+                                             unsigned long long r2, uint32_t& s0, uint32_t& s1) {
+  s0 = s1 = 0;
+  if (!q.valid || h == 0) return;
+  const long long r = (long long)isqrt_u64(r2), top = (1ll << a.bits) - 1;
+  const long long lo = q.x - r, hi = q.x + r;
+  if (hi < 0 || lo > top) return;
+  s0 = lower_bound_u16(a.idx2, 0, h, (uint32_t)max(lo, 0ll));
+  s1 = lower_bound_u16(a.idx2, s0, h, (uint32_t)min(hi, top) + 1);
+}
+
+// Count (EMIT = false) or write in (y, z) order from position `pos` (EMIT =
+// true) the voxels of one slab within the radius; returns the count.
+template <bool EMIT>
+__device__ __forceinline__ unsigned long long radius_slab(const Levels& a, uint32_t slab,
+                                                          const RQuery& q, unsigned long long r2,
+                                                          uint32_t* idx, unsigned long long* d2,
+                                                          unsigned long long pos) {
+  const long long top = (1ll << a.bits) - 1;
+  const uint32_t x = __ldg(a.idx2 + slab);
+  const unsigned long long dx = absdiff_ll(x, q.x), dx2 = dx * dx;
+  if (dx2 > r2) return 0;
+  const long long ry = (long long)isqrt_u64(r2 - dx2);
+  const long long ylo = q.y - ry, yhi = q.y + ry;
+  if (yhi < 0 || ylo > top) return 0;
+  const uint32_t ys = __ldg(a.ptr2 + slab), ye = __ldg(a.ptr2 + slab + 1);
+  unsigned long long n = 0;
+  for (uint32_t c = lower_bound_u16(a.idx1, ys, ye, (uint32_t)max(ylo, 0ll)); c < ye; ++c) {
+    const uint32_t y = __ldg(a.idx1 + c);
+    if ((long long)y > yhi) break;
+    const unsigned long long dy = absdiff_ll(y, q.y), dxy = dx2 + dy * dy;
+    const long long rz = (long long)isqrt_u64(r2 - dxy);
+    const long long zlo = q.z - rz, zhi = q.z + rz;
+    if (zhi < 0 || zlo > top) continue;
+    const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
+    const uint32_t p0 = lower_bound_u16(a.idx0, zs, ze, (uint32_t)max(zlo, 0ll));
+    const uint32_t p1 = lower_bound_u16(a.idx0, p0, ze, (uint32_t)min(zhi, top) + 1);
+    if (EMIT) {
+      for (uint32_t p = p0; p < p1; ++p) {
+        const unsigned long long dz = absdiff_ll(__ldg(a.idx0 + p), q.z);
+        idx[pos + n + (p - p0)] = p;
+        d2[pos + n + (p - p0)] = dxy + dz * dz;
+      }
+    }
+    n += p1 - p0;
+  }
+  return n;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void k_radius_count(SearchSeg sg, unsigned long long r2,
+                               unsigned long long* counts) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t h = (uint32_t)sg.a.hdr->cnt[2];
+  for (uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < sg.m; j += nw) {
+    const RQuery q = radius_query(sg, j);
+    uint32_t s0, s1;
+    radius_slabs(sg.a, h, q, r2, s0, s1);
+    unsigned long long n = 0;
+    for (uint32_t s = s0 + lane; s < s1; s += 32) {
+      n += radius_slab<false>(sg.a, s, q, r2, nullptr, nullptr, 0);
+    }
+    n = warp_sum_u64(n);
+    if (lane == 0) counts[j] = n;
+  }
+}
+
+__global__ void k_radius_fill(SearchSeg sg, unsigned long long r2,
+                              const unsigned long long* __restrict__ offsets, uint32_t* idx,
+                              unsigned long long* d2) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t h = (uint32_t)sg.a.hdr->cnt[2];
+  for (uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < sg.m; j += nw) {
+    const RQuery q = radius_query(sg, j);
+    uint32_t s0, s1;
+    radius_slabs(sg.a, h, q, r2, s0, s1);
+    unsigned long long base = offsets[j];
+    for (uint32_t g = s0; g < s1; g += 32) {
+      const uint32_t s = g + lane;
+      const unsigned long long n =
+          s < s1 ? radius_slab<false>(sg.a, s, q, r2, nullptr, nullptr, 0) : 0ull;
+      unsigned long long inc = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += t;
+      }
+      if (n > 0) radius_slab<true>(sg.a, s, q, r2, idx, d2, base + inc - n);
+      base += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+}
+
+// Exclusive scan of v[0, m) in place, v[m] = total: B blocks, each owning a
+// contiguous chunk; block totals are scanned by one block, then each chunk
+// is rescanned with its prefix.
+__global__ void k_scan_totals(const unsigned long long* v, uint64_t m, uint64_t chunk,
+                              unsigned long long* totals) {
+  __shared__ unsigned long long s_warp[kWarps];
+  const uint64_t lo = blockIdx.x * chunk, hi = min(lo + chunk, m);
+  unsigned long long t = 0;
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += kThreads) t += v[i];
+  unsigned long long tot;
+  block_excl_scan(t, tot, s_warp);
+  if (threadIdx.x == 0) totals[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(unsigned long long* totals, uint32_t B) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned long long run = 0;
+  for (uint32_t b = 0; b < B; ++b) {
+    const unsigned long long t = totals[b];
+    totals[b] = run;
+    run += t;
+  }
+  totals[B] = run;
+}
+
+__global__ void k_scan_apply(unsigned long long* v, uint64_t m, uint64_t chunk,
+                             const unsigned long long* totals, uint32_t B) {
+  __shared__ unsigned long long s_warp[kWarps];
+  const uint64_t lo = blockIdx.x * chunk, hi = min(lo + chunk, m);
+  unsigned long long run = totals[blockIdx.x];
+  for (uint64_t b0 = lo; b0 < hi; b0 += kThreads) {
+    const uint64_t i = b0 + threadIdx.x;
+    const unsigned long long x = i < hi ? v[i] : 0ull;
+    unsigned long long tot;
+    const unsigned long long ex = block_excl_scan(x, tot, s_warp);
+    if (i < hi) v[i] = run + ex;
+    run += tot;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) v[m] = totals[B];
+}
+
+// ---- k nearest -------------------------------------------------------------
+// The warp's list of the k best (distance^2, key, index) so far, lane i
+// holding the i-th; lanes >= k hold nothing.
+struct TopK {
+  unsigned long long d2, key;
+  uint32_t idx;
+};
+
+// Offer one candidate (the same in every lane): it enters before the first
+// entry that is not lexicographically below it, the entries after it move up
+// one lane and the k-th falls out.
+__device__ __forceinline__ void topk_insert(TopK& t, uint32_t lane, uint32_t k,
+                                            unsigned long long cd, unsigned long long ck,
+                                            uint32_t ci) {
+  const bool before = lane < k && (t.d2 < cd || (t.d2 == cd && t.key < ck));
+  const uint32_t pos = __popc(__ballot_sync(0xffffffffu, before));
+  const unsigned long long ud = __shfl_up_sync(0xffffffffu, t.d2, 1);
+  const unsigned long long uk = __shfl_up_sync(0xffffffffu, t.key, 1);
+  const uint32_t ui = __shfl_up_sync(0xffffffffu, t.idx, 1);
+  if (pos < k) {
+    if (lane == pos) {
+      t.d2 = cd;
+      t.key = ck;
+      t.idx = ci;
+    } else if (lane > pos && lane < k) {
+      t.d2 = ud;
+      t.key = uk;
+      t.idx = ui;
+    }
+  }
+}
+
+// k nearest of one query, one warp: slab rounds as in the NN search (16 per
+// side), every lane walking its slab's columns nearest-first in y and each
+// column's voxels nearest-first in z, in lockstep so that each step's
+// candidates (at most one per lane) enter the list together and the k-th
+// distance prunes every walk.
+__global__ void k_knn(SearchSeg sg, uint32_t k, uint32_t* out_idx, unsigned long long* out_d2) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const Levels& a = sg.a;
+  const uint32_t u = (uint32_t)a.hdr->cnt[0], h = (uint32_t)a.hdr->cnt[2];
+  const uint32_t b = a.bits;
+  const long long top = (1ll << b) - 1;
+  for (uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < sg.m; j += nw) {
+    TopK t{~0ull, ~0ull, 0xffffffffu};
+    const RQuery q = radius_query(sg, j);
+    if (q.valid && u > 0) {
+      const uint32_t cqx = (uint32_t)min(max(q.x, 0ll), top);
+      const uint32_t cqy = (uint32_t)min(max(q.y, 0ll), top);
+      const uint32_t cqz = (uint32_t)min(max(q.z, 0ll), top);
+      const uint32_t xr0 = lower_bound_u16(a.idx2, 0, h, cqx);
+      const bool right = (lane & 1u) == 0u;
+      unsigned long long bound = ~0ull;
+      for (uint32_t r = 0;; ++r) {
+        const long long kk = (long long)r * 16 + (lane >> 1);
+        const long long slab = right ? (long long)xr0 + kk : (long long)xr0 - 1 - kk;
+        bool work = slab >= 0 && slab < (long long)h;
+        unsigned long long dx2 = 0;
+        uint32_t x = 0, ys = 0, ye = 0;
+        if (work) {
+          x = __ldg(a.idx2 + slab);
+          ys = __ldg(a.ptr2 + slab);
+          ye = __ldg(a.ptr2 + slab + 1);
+          const unsigned long long dx = absdiff_ll(x, q.x);
+          dx2 = dx * dx;
+          work = dx2 <= bound;
+        }
+        if (!__any_sync(0xffffffffu, work)) break;
+        // column cursors (outward from the query's y) and the current column
+        long long cr = 0, cl = -1;
+        if (work) {
+          cr = lower_bound_u16(a.idx1, ys, ye, cqy);
+          cl = cr - 1;
+        }
+        bool in_col = false;
+        unsigned long long dxy = 0;
+        long long zu = 0, zd = -1, zs = 0, ze = 0;
+        uint32_t yv = 0;
+        while (__any_sync(0xffffffffu, work)) {
+          bool has = false;
+          unsigned long long cd = 0, ck = 0;
+          uint32_t ci = 0;
+          if (work && !in_col) {
+            // the next column, nearest in y first, while it can still beat the bound
+            const bool hr = cr < (long long)ye, hl = cl >= (long long)ys;
+            const unsigned long long er = hr ? absdiff_ll(__ldg(a.idx1 + cr), q.y) : ~0ull;
+            const unsigned long long el = hl ? absdiff_ll(__ldg(a.idx1 + cl), q.y) : ~0ull;
+            const bool gr = hr && (!hl || er <= el);
+            const unsigned long long dy = gr ? er : el;
+            if ((!hr && !hl) || dx2 + dy * dy > bound) {
+              work = false;
+            } else {
+              const long long c = gr ? cr : cl;
+              if (gr) ++cr; else --cl;
+              yv = __ldg(a.idx1 + c);
+              dxy = dx2 + dy * dy;
+              zs = __ldg(a.ptr1 + c);
+              ze = __ldg(a.ptr1 + c + 1);
+              zu = lower_bound_u16(a.idx0, (uint32_t)zs, (uint32_t)ze, cqz);
+              zd = zu - 1;
+              in_col = true;
+            }
+          } else if (work) {
+            // the next voxel of the column, nearest in z first
+            const bool hu = zu < ze, hd = zd >= zs;
+            const unsigned long long eu = hu ? absdiff_ll(__ldg(a.idx0 + zu), q.z) : ~0ull;
+            const unsigned long long ed = hd ? absdiff_ll(__ldg(a.idx0 + zd), q.z) : ~0ull;
+            const bool gu = hu && (!hd || eu <= ed);
+            const unsigned long long dz = gu ? eu : ed;
+            if ((!hu && !hd) || dxy + dz * dz > bound) {
+              in_col = false;
+            } else {
+              const long long p = gu ? zu : zd;
+              if (gu) ++zu; else --zd;
+              has = true;
+              cd = dxy + dz * dz;
+              ci = (uint32_t)p;
+              ck = ((unsigned long long)x << (2 * b)) | ((unsigned long long)yv << b) |
+                   (unsigned long long)__ldg(a.idx0 + p);
+            }
+          }
+          uint32_t pending = __ballot_sync(0xffffffffu, has);
+          while (pending) {
+            const uint32_t src = __ffs(pending) - 1;
+            pending &= pending - 1;
+            topk_insert(t, lane, k, __shfl_sync(0xffffffffu, cd, src),
+                        __shfl_sync(0xffffffffu, ck, src), __shfl_sync(0xffffffffu, ci, src));
+          }
+          bound = __shfl_sync(0xffffffffu, t.d2, k - 1);
+        }
+      }
+    }
+    if (lane < k) {
+      out_idx[(size_t)j * k + lane] = t.idx;
+      out_d2[(size_t)j * k + lane] = t.d2;
+    }
+  }
+}
+
+unsigned search_blocks(uint64_t m) {
+  return (unsigned)std::min<uint64_t>((std::max<uint64_t>(m, 1) + 7) / 8,
+                                      (uint64_t)device_sm_count() * 8);
+}
+
+}  // namespace
+
+cudaError_t run_knn(const SearchSeg& sg, uint32_t k, uint32_t* idx, unsigned long long* d2,
+                    cudaStream_t stream) {
+  if (sg.m == 0) return cudaSuccess;
+  k_knn<<<search_blocks(sg.m), 256, 0, stream>>>(sg, k, idx, d2);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+size_t radius_scratch_bytes() { return 1025 * sizeof(unsigned long long); }
+
+cudaError_t run_radius_count(const SearchSeg& sg, unsigned long long r2,
+                             unsigned long long* offsets, void* scratch, cudaStream_t stream) {
+  unsigned long long* totals = static_cast<unsigned long long*>(scratch);
+  if (sg.m > 0) {
+    k_radius_count<<<search_blocks(sg.m), 256, 0, stream>>>(sg, r2, offsets);
+  }
+  const uint32_t B = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(1024, (sg.m + 4095) / 4096));
+  const uint64_t chunk = (sg.m + B - 1) / B;
+  k_scan_totals<<<B, kThreads, 0, stream>>>(offsets, sg.m, std::max<uint64_t>(chunk, 1), totals);
+  k_scan_top<<<1, 32, 0, stream>>>(totals, B);
+  k_scan_apply<<<B, kThreads, 0, stream>>>(offsets, sg.m, std::max<uint64_t>(chunk, 1), totals, B);
+  count_launch(sg.m > 0 ? 4 : 3);
+  return cudaGetLastError();
+}
+
+cudaError_t run_radius_fill(const SearchSeg& sg, unsigned long long r2,
+                            const unsigned long long* offsets, uint32_t* idx,
+                            unsigned long long* d2, cudaStream_t stream) {
+  if (sg.m == 0) return cudaSuccess;
+  k_radius_fill<<<search_blocks(sg.m), 256, 0, stream>>>(sg, r2, offsets, idx, d2);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace libcga
