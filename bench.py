@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["cga", "reference"], default="cga")
     ap.add_argument("--config", choices=["lidar", "plain", "surface", "batched", "served", "values",
-                                         "perspective"],
+                                         "perspective", "search"],
                     default="lidar")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
@@ -767,6 +767,53 @@ def run_perspective(args, world_size, local_rank, torch, cga):
     return out
 
 
+# ------------------------------------------- GPU arm: k-NN and radius search
+def run_search(args, world_size, local_rank, torch, cga):
+    """The LiDAR frame set's world (1.3M voxels, b = 16) and its 1M jittered
+    queries: 8 nearest per query, and every voxel within 10 cm (25.6 voxels)."""
+    scene, queries = make_workload(0)
+    grid = cga.grid_from_box(LO, EXTENT, BITS)
+    world = cga.cga_build(torch.from_numpy(scene.world.astype(np.float32)).cuda(), grid,
+                          allocator=None)
+    q = torch.from_numpy(queries).cuda()
+    m, k = q.shape[0], 8
+    r2 = 655  # (25.6 voxels)^2: 10 cm at 3.9 mm voxels
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+    state = {}
+
+    def knn_step():
+        state["knn"] = cga.cga_knn(world, q, k)
+
+    def radius_step():
+        state["radius"] = cga.cga_radius(world, q, r2)
+
+    for _ in range(args.warmup):
+        knn_step()
+        radius_step()
+    torch.cuda.synchronize()
+    clocks = start_clocks(local_rank)
+    launches0 = cga.kernel_launches()
+    knn_ms = [timed(torch, knn_step, flush, float(i)) for i in range(args.steps)]
+    rad_ms = [timed(torch, radius_step, flush, float(i)) for i in range(args.steps)]
+    launches = cga.kernel_launches() - launches0
+    clk = clocks.stop()
+    total_results = int(state["radius"][0][-1].item())
+    kt, rt = float(np.mean(knn_ms)), float(np.mean(rad_ms))
+    out = base_line(args, world_size, METRIC, m * args.steps / (sum(knn_ms) / 1e3),
+                    "queries/s", kt,
+                    {"workload": "search: LiDAR world (1.3M voxels, b=16), 1M jittered queries; "
+                                 "8-NN per query, and a radius search of 10 cm",
+                     "queries": m, "k": k, "r2_voxels": r2, "l2": "flushed between steps"},
+                    "synthetic (seeded LiDAR generator)")
+    out.update({"knn_ms": round(kt, 4), "radius_ms": round(rt, 4),
+                "radius_queries_s": round(m / (rt / 1e3), 1),
+                "radius_results": total_results,
+                "radius_results_per_s": round(total_results / (rt / 1e3), 1),
+                "note": "radius_ms includes the wait for the total between count and fill",
+                "gpu_launches": int(launches), "clocks": clk})
+    return out
+
+
 # ------------------------------------------------------------ oracle (CPU)
 def oracle_step(orc, og, scene, queries, n_sample):
     t0 = time.perf_counter()
@@ -851,6 +898,8 @@ def main():
         out = run_values(args, world_size, local_rank, torch, cga)
     elif args.config == "perspective":
         out = run_perspective(args, world_size, local_rank, torch, cga)
+    elif args.config == "search":
+        out = run_search(args, world_size, local_rank, torch, cga)
     else:
         out = run_served(args, world_size, local_rank, torch, cga)
     if rank == 0:

@@ -420,6 +420,49 @@ int cga_merge_values(const cga_t* a, const cga_t* b, int policy, const cga_alloc
 
 namespace {
 
+libcga::NnSeg nn_segment(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
+                         uint64_t* d_dist2) {
+  libcga::NnSeg seg{};
+  seg.a = a->lv;
+  seg.scale = a->grid.scale;
+  for (int k = 0; k < 3; ++k) seg.off[k] = a->grid.offset[k];
+  seg.q = d_q;
+  seg.m = (uint32_t)m;
+  seg.idx = d_idx;
+  seg.d2 = reinterpret_cast<unsigned long long*>(d_dist2);
+  seg.tile_base = 0;
+  seg.num_tiles = (uint32_t)((m + libcga::kTile - 1) / libcga::kTile);
+  attach_coarse(a, seg);
+  return seg;
+}
+
+}  // namespace
+
+namespace {
+
+// The NN search's Morton order of a query batch (sort scratch to release
+// after the kernels that read it), or none for small batches.
+int query_order(const cga_t* a, const float* d_q, uint64_t m, cudaStream_t s, void** scratch,
+                const unsigned long long** order) {
+  *scratch = nullptr;
+  *order = nullptr;
+  if (m < libcga::kNnSortMin || m > libcga::kNnMaxQueries) return CGA_OK;
+  const libcga::NnSeg seg = nn_segment(a, d_q, m, nullptr, nullptr);
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  void* sc = dalloc(A, libcga::nn_scratch_bytes(seg.num_tiles, 1), s);
+  if (sc == nullptr) return CGA_ERR_OOM;
+  const libcga::NnTables t = libcga::nn_tables(sc, seg.num_tiles, 1);
+  cudaError_t e = libcga::nn_upload_one(seg, t, s);
+  if (e == cudaSuccess) e = libcga::run_nn_sort_device(1, seg.num_tiles, t, s);
+  if (e != cudaSuccess) {
+    dfree(A, a->has_alloc, sc, s);
+    return cuda_rc(e);
+  }
+  *scratch = sc;
+  *order = static_cast<const unsigned long long*>(t.sort.keys0);
+  return CGA_OK;
+}
+
 libcga::SearchSeg search_segment(const cga_t* a, const float* d_q, uint64_t m) {
   libcga::SearchSeg sg{};
   sg.a = a->lv;
@@ -442,9 +485,15 @@ int cga_radius_count(const cga_t* a, const float* d_q, uint64_t m, uint64_t r2,
   const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
   void* scratch = dalloc(A, libcga::radius_scratch_bytes(), s);
   if (scratch == nullptr) return CGA_ERR_OOM;
-  const int rc = cuda_rc(libcga::run_radius_count(search_segment(a, d_q, m), r2,
-                                                  reinterpret_cast<unsigned long long*>(d_offsets),
-                                                  scratch, s));
+  void* osc = nullptr;
+  const unsigned long long* order = nullptr;
+  int rc = query_order(a, d_q, m, s, &osc, &order);
+  if (rc == CGA_OK) {
+    rc = cuda_rc(libcga::run_radius_count(search_segment(a, d_q, m), r2, order,
+                                          reinterpret_cast<unsigned long long*>(d_offsets),
+                                          scratch, s));
+  }
+  if (osc != nullptr) dfree(A, a->has_alloc, osc, s);
   dfree(A, a->has_alloc, scratch, s);
   return rc;
 }
@@ -456,9 +505,18 @@ int cga_radius_fill(const cga_t* a, const float* d_q, uint64_t m, uint64_t r2,
       m > CGA_MAX_POINTS || r2 > CGA_MAX_RADIUS2) {
     return CGA_ERR_INVALID_ARG;
   }
-  return cuda_rc(libcga::run_radius_fill(
-      search_segment(a, d_q, m), r2, reinterpret_cast<const unsigned long long*>(d_offsets),
-      d_idx, reinterpret_cast<unsigned long long*>(d_dist2), static_cast<cudaStream_t>(stream)));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  void* osc = nullptr;
+  const unsigned long long* order = nullptr;
+  int rc = query_order(a, d_q, m, s, &osc, &order);
+  if (rc == CGA_OK) {
+    rc = cuda_rc(libcga::run_radius_fill(
+        search_segment(a, d_q, m), r2, order, reinterpret_cast<const unsigned long long*>(d_offsets),
+        d_idx, reinterpret_cast<unsigned long long*>(d_dist2), s));
+  }
+  if (osc != nullptr) dfree(A, a->has_alloc, osc, s);
+  return rc;
 }
 
 int cga_knn(const cga_t* a, const float* d_q, uint64_t m, uint32_t k, uint32_t* d_idx,
@@ -467,9 +525,17 @@ int cga_knn(const cga_t* a, const float* d_q, uint64_t m, uint32_t k, uint32_t* 
       (m > 0 && (d_q == nullptr || d_idx == nullptr || d_dist2 == nullptr))) {
     return CGA_ERR_INVALID_ARG;
   }
-  return cuda_rc(libcga::run_knn(search_segment(a, d_q, m), k, d_idx,
-                                 reinterpret_cast<unsigned long long*>(d_dist2),
-                                 static_cast<cudaStream_t>(stream)));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  void* osc = nullptr;
+  const unsigned long long* order = nullptr;
+  int rc = query_order(a, d_q, m, s, &osc, &order);
+  if (rc == CGA_OK) {
+    rc = cuda_rc(libcga::run_knn(search_segment(a, d_q, m), k, order, d_idx,
+                                 reinterpret_cast<unsigned long long*>(d_dist2), s));
+  }
+  if (osc != nullptr) dfree(A, a->has_alloc, osc, s);
+  return rc;
 }
 
 int cga_perspective(const cga_t* a, const float eye[3], float cos_t, float sin_t, float D,
@@ -599,26 +665,6 @@ int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
   if (scratch != nullptr) dfree(A, a->has_alloc, scratch, s);
   return rc;
 }
-
-namespace {
-
-libcga::NnSeg nn_segment(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
-                         uint64_t* d_dist2) {
-  libcga::NnSeg seg{};
-  seg.a = a->lv;
-  seg.scale = a->grid.scale;
-  for (int k = 0; k < 3; ++k) seg.off[k] = a->grid.offset[k];
-  seg.q = d_q;
-  seg.m = (uint32_t)m;
-  seg.idx = d_idx;
-  seg.d2 = reinterpret_cast<unsigned long long*>(d_dist2);
-  seg.tile_base = 0;
-  seg.num_tiles = (uint32_t)((m + libcga::kTile - 1) / libcga::kTile);
-  attach_coarse(a, seg);
-  return seg;
-}
-
-}  // namespace
 
 namespace {
 

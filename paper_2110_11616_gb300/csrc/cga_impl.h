@@ -209,15 +209,18 @@ struct SearchSeg {
   uint32_t m;
 };
 size_t radius_scratch_bytes();
+// order (or null): the queries' Morton keys of the NN search (query index in
+// the low 32 bits), visited in that order.
 // offsets (m + 1): exclusive prefix of the per-query counts, offsets[m] = total.
 cudaError_t run_radius_count(const SearchSeg& sg, unsigned long long r2,
-                             unsigned long long* offsets, void* scratch, cudaStream_t stream);
+                             const unsigned long long* order, unsigned long long* offsets,
+                             void* scratch, cudaStream_t stream);
 cudaError_t run_radius_fill(const SearchSeg& sg, unsigned long long r2,
-                            const unsigned long long* offsets, uint32_t* idx,
-                            unsigned long long* d2, cudaStream_t stream);
+                            const unsigned long long* order, const unsigned long long* offsets,
+                            uint32_t* idx, unsigned long long* d2, cudaStream_t stream);
 // idx, d2: m * k entries (k <= 32), query j's k nearest ascending.
-cudaError_t run_knn(const SearchSeg& sg, uint32_t k, uint32_t* idx, unsigned long long* d2,
-                    cudaStream_t stream);
+cudaError_t run_knn(const SearchSeg& sg, uint32_t k, const unsigned long long* order, uint32_t* idx,
+                    unsigned long long* d2, cudaStream_t stream);
 
 // ---- Perspective projection (Eq. 5-6) ---------------------------------------
 struct Camera {

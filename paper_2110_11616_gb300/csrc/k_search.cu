@@ -21,9 +21,15 @@ __device__ __forceinline__ unsigned long long absdiff_ll(long long a, long long 
   return (unsigned long long)(a > b ? a - b : b - a);
 }
 
-// Largest s with s * s <= v (v < 2^63).
+// Largest s with s * s <= v (v < 2^63).  Below 2^46 a single-precision
+// estimate is within 2 of the root (the rounding of v to float moves the
+// root by at most a quarter, sqrtf's own rounding by at most half a unit of
+// a number below 2^23), so two exact integer steps at most fix it; the rare
+// larger arguments take the double-precision estimate, which GB300 runs at a
+// small fraction of the single-precision rate.
 __device__ __forceinline__ unsigned long long isqrt_u64(unsigned long long v) {
-  unsigned long long s = (unsigned long long)sqrt((double)v);
+  unsigned long long s = v < (1ull << 46) ? (unsigned long long)sqrtf((float)v)
+                                          : (unsigned long long)sqrt((double)v);
   while (s > 0 && s * s > v) --s;
   while ((s + 1) * (s + 1) <= v) ++s;
   return s;
@@ -101,12 +107,21 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
   return v;
 }
 
+// Query of slot `slot`: the slot itself, or the index in the low 32 bits of
+// the Morton-ordered key when an order is given (neighbouring warps then
+// search neighbouring space and share the cache).
+__device__ __forceinline__ uint32_t slot_query(const unsigned long long* order, uint32_t slot) {
+  return order != nullptr ? (uint32_t)__ldg(order + slot) : slot;
+}
+
 __global__ void k_radius_count(SearchSeg sg, unsigned long long r2,
+                               const unsigned long long* __restrict__ order,
                                unsigned long long* counts) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const uint32_t h = (uint32_t)sg.a.hdr->cnt[2];
-  for (uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < sg.m; j += nw) {
+  for (uint32_t sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < sg.m; sl += nw) {
+    const uint32_t j = slot_query(order, sl);
     const RQuery q = radius_query(sg, j);
     uint32_t s0, s1;
     radius_slabs(sg.a, h, q, r2, s0, s1);
@@ -120,12 +135,14 @@ __global__ void k_radius_count(SearchSeg sg, unsigned long long r2,
 }
 
 __global__ void k_radius_fill(SearchSeg sg, unsigned long long r2,
+                              const unsigned long long* __restrict__ order,
                               const unsigned long long* __restrict__ offsets, uint32_t* idx,
                               unsigned long long* d2) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const uint32_t h = (uint32_t)sg.a.hdr->cnt[2];
-  for (uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < sg.m; j += nw) {
+  for (uint32_t sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < sg.m; sl += nw) {
+    const uint32_t j = slot_query(order, sl);
     const RQuery q = radius_query(sg, j);
     uint32_t s0, s1;
     radius_slabs(sg.a, h, q, r2, s0, s1);
@@ -188,51 +205,98 @@ __global__ void k_scan_apply(unsigned long long* v, uint64_t m, uint64_t chunk,
 }
 
 // ---- k nearest -------------------------------------------------------------
-// The warp's list of the k best (distance^2, key, index) so far, lane i
-// holding the i-th; lanes >= k hold nothing.
+// The warp's list of the k best (distance^2, index) so far, lane i holding
+// the i-th; lanes >= k hold the sentinel (~0, ~0).  The CGA index of a voxel
+// rises with its key, so (distance^2, index) order is (distance^2, key) order.
 struct TopK {
-  unsigned long long d2, key;
+  unsigned long long d2;
   uint32_t idx;
 };
 
+__device__ __forceinline__ bool pair_less(unsigned long long da, uint32_t ia,
+                                          unsigned long long db, uint32_t ib) {
+  return da < db || (da == db && ia < ib);
+}
+
 // Offer one candidate (the same in every lane): it enters before the first
-// entry that is not lexicographically below it, the entries after it move up
-// one lane and the k-th falls out.
+// entry that is not below it, the entries after it move up one lane and the
+// k-th falls out.
 __device__ __forceinline__ void topk_insert(TopK& t, uint32_t lane, uint32_t k,
-                                            unsigned long long cd, unsigned long long ck,
-                                            uint32_t ci) {
-  const bool before = lane < k && (t.d2 < cd || (t.d2 == cd && t.key < ck));
+                                            unsigned long long cd, uint32_t ci) {
+  const bool before = lane < k && pair_less(t.d2, t.idx, cd, ci);
   const uint32_t pos = __popc(__ballot_sync(0xffffffffu, before));
   const unsigned long long ud = __shfl_up_sync(0xffffffffu, t.d2, 1);
-  const unsigned long long uk = __shfl_up_sync(0xffffffffu, t.key, 1);
   const uint32_t ui = __shfl_up_sync(0xffffffffu, t.idx, 1);
   if (pos < k) {
     if (lane == pos) {
       t.d2 = cd;
-      t.key = ck;
       t.idx = ci;
     } else if (lane > pos && lane < k) {
       t.d2 = ud;
-      t.key = uk;
       t.idx = ui;
     }
   }
 }
+
+// One compare-exchange step of a bitonic network across the warp: the pair
+// (lane, lane ^ j) is put in ascending order when `up`, descending otherwise.
+__device__ __forceinline__ void bitonic_step(unsigned long long& d, uint32_t& i, uint32_t lane,
+                                             uint32_t j, bool up) {
+  const unsigned long long od = __shfl_xor_sync(0xffffffffu, d, j);
+  const uint32_t oi = __shfl_xor_sync(0xffffffffu, i, j);
+  const bool keep_min = ((lane & j) == 0) == up;
+  const bool take = keep_min ? pair_less(od, oi, d, i) : pair_less(d, i, od, oi);
+  if (take) {
+    d = od;
+    i = oi;
+  }
+}
+
+// Offer every lane's candidate at once (sentinel where a lane has none): the
+// candidates are sorted by a bitonic network, the lane-wise minimum of the
+// list and the reversed candidates holds the 32 least of both as a bitonic
+// sequence, and a bitonic merge orders it.
+__device__ __forceinline__ void topk_insert_all(TopK& t, uint32_t lane, uint32_t k,
+                                                unsigned long long cd, uint32_t ci) {
+#pragma unroll
+  for (uint32_t w = 2; w <= 32; w <<= 1) {
+#pragma unroll
+    for (uint32_t j = w >> 1; j > 0; j >>= 1) bitonic_step(cd, ci, lane, j, (lane & w) == 0);
+  }
+  const unsigned long long rd = __shfl_sync(0xffffffffu, cd, 31 - lane);
+  const uint32_t ri = __shfl_sync(0xffffffffu, ci, 31 - lane);
+  if (pair_less(rd, ri, t.d2, t.idx)) {
+    t.d2 = rd;
+    t.idx = ri;
+  }
+#pragma unroll
+  for (uint32_t j = 16; j > 0; j >>= 1) bitonic_step(t.d2, t.idx, lane, j, true);
+  if (lane >= k) {
+    t.d2 = ~0ull;
+    t.idx = 0xffffffffu;
+  }
+}
+
+// Above this many candidates in one step, one bitonic merge is cheaper than
+// inserting them one by one.
+constexpr int kKnnBatch = 8;
 
 // k nearest of one query, one warp: slab rounds as in the NN search (16 per
 // side), every lane walking its slab's columns nearest-first in y and each
 // column's voxels nearest-first in z, in lockstep so that each step's
 // candidates (at most one per lane) enter the list together and the k-th
 // distance prunes every walk.
-__global__ void k_knn(SearchSeg sg, uint32_t k, uint32_t* out_idx, unsigned long long* out_d2) {
+__global__ void __launch_bounds__(256, 4) k_knn(SearchSeg sg, uint32_t k, const unsigned long long* __restrict__ order,
+                      uint32_t* out_idx, unsigned long long* out_d2) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const Levels& a = sg.a;
   const uint32_t u = (uint32_t)a.hdr->cnt[0], h = (uint32_t)a.hdr->cnt[2];
   const uint32_t b = a.bits;
   const long long top = (1ll << b) - 1;
-  for (uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < sg.m; j += nw) {
-    TopK t{~0ull, ~0ull, 0xffffffffu};
+  for (uint32_t sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < sg.m; sl += nw) {
+    const uint32_t j = slot_query(order, sl);
+    TopK t{~0ull, 0xffffffffu};
     const RQuery q = radius_query(sg, j);
     if (q.valid && u > 0) {
       const uint32_t cqx = (uint32_t)min(max(q.x, 0ll), top);
@@ -265,11 +329,10 @@ __global__ void k_knn(SearchSeg sg, uint32_t k, uint32_t* out_idx, unsigned long
         bool in_col = false;
         unsigned long long dxy = 0;
         long long zu = 0, zd = -1, zs = 0, ze = 0;
-        uint32_t yv = 0;
         while (__any_sync(0xffffffffu, work)) {
           bool has = false;
-          unsigned long long cd = 0, ck = 0;
-          uint32_t ci = 0;
+          unsigned long long cd = ~0ull;
+          uint32_t ci = 0xffffffffu;
           if (work && !in_col) {
             // the next column, nearest in y first, while it can still beat the bound
             const bool hr = cr < (long long)ye, hl = cl >= (long long)ys;
@@ -282,7 +345,6 @@ __global__ void k_knn(SearchSeg sg, uint32_t k, uint32_t* out_idx, unsigned long
             } else {
               const long long c = gr ? cr : cl;
               if (gr) ++cr; else --cl;
-              yv = __ldg(a.idx1 + c);
               dxy = dx2 + dy * dy;
               zs = __ldg(a.ptr1 + c);
               ze = __ldg(a.ptr1 + c + 1);
@@ -305,16 +367,18 @@ __global__ void k_knn(SearchSeg sg, uint32_t k, uint32_t* out_idx, unsigned long
               has = true;
               cd = dxy + dz * dz;
               ci = (uint32_t)p;
-              ck = ((unsigned long long)x << (2 * b)) | ((unsigned long long)yv << b) |
-                   (unsigned long long)__ldg(a.idx0 + p);
             }
           }
           uint32_t pending = __ballot_sync(0xffffffffu, has);
-          while (pending) {
-            const uint32_t src = __ffs(pending) - 1;
-            pending &= pending - 1;
-            topk_insert(t, lane, k, __shfl_sync(0xffffffffu, cd, src),
-                        __shfl_sync(0xffffffffu, ck, src), __shfl_sync(0xffffffffu, ci, src));
+          if (__popc(pending) > kKnnBatch) {
+            topk_insert_all(t, lane, k, cd, ci);
+          } else {
+            while (pending) {
+              const uint32_t src = __ffs(pending) - 1;
+              pending &= pending - 1;
+              topk_insert(t, lane, k, __shfl_sync(0xffffffffu, cd, src),
+                          __shfl_sync(0xffffffffu, ci, src));
+            }
           }
           bound = __shfl_sync(0xffffffffu, t.d2, k - 1);
         }
@@ -334,10 +398,10 @@ unsigned search_blocks(uint64_t m) {
 
 }  // namespace
 
-cudaError_t run_knn(const SearchSeg& sg, uint32_t k, uint32_t* idx, unsigned long long* d2,
-                    cudaStream_t stream) {
+cudaError_t run_knn(const SearchSeg& sg, uint32_t k, const unsigned long long* order, uint32_t* idx,
+                    unsigned long long* d2, cudaStream_t stream) {
   if (sg.m == 0) return cudaSuccess;
-  k_knn<<<search_blocks(sg.m), 256, 0, stream>>>(sg, k, idx, d2);
+  k_knn<<<search_blocks(sg.m), 256, 0, stream>>>(sg, k, order, idx, d2);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -345,10 +409,11 @@ cudaError_t run_knn(const SearchSeg& sg, uint32_t k, uint32_t* idx, unsigned lon
 size_t radius_scratch_bytes() { return 1025 * sizeof(unsigned long long); }
 
 cudaError_t run_radius_count(const SearchSeg& sg, unsigned long long r2,
-                             unsigned long long* offsets, void* scratch, cudaStream_t stream) {
+                             const unsigned long long* order, unsigned long long* offsets,
+                             void* scratch, cudaStream_t stream) {
   unsigned long long* totals = static_cast<unsigned long long*>(scratch);
   if (sg.m > 0) {
-    k_radius_count<<<search_blocks(sg.m), 256, 0, stream>>>(sg, r2, offsets);
+    k_radius_count<<<search_blocks(sg.m), 256, 0, stream>>>(sg, r2, order, offsets);
   }
   const uint32_t B = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(1024, (sg.m + 4095) / 4096));
   const uint64_t chunk = (sg.m + B - 1) / B;
@@ -360,10 +425,10 @@ cudaError_t run_radius_count(const SearchSeg& sg, unsigned long long r2,
 }
 
 cudaError_t run_radius_fill(const SearchSeg& sg, unsigned long long r2,
-                            const unsigned long long* offsets, uint32_t* idx,
-                            unsigned long long* d2, cudaStream_t stream) {
+                            const unsigned long long* order, const unsigned long long* offsets,
+                            uint32_t* idx, unsigned long long* d2, cudaStream_t stream) {
   if (sg.m == 0) return cudaSuccess;
-  k_radius_fill<<<search_blocks(sg.m), 256, 0, stream>>>(sg, r2, offsets, idx, d2);
+  k_radius_fill<<<search_blocks(sg.m), 256, 0, stream>>>(sg, r2, order, offsets, idx, d2);
   count_launch(1);
   return cudaGetLastError();
 }

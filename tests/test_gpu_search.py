@@ -78,10 +78,28 @@ def test_knn_one_equals_nn(cg):
     pts = synth.uniform_cube(30_000, seed=3)
     g = cg.grid_from_box([0, 0, 0], 1.0, 12)
     a = cg.cga_build(dev(pts), g)
-    q = dev(synth.uniform_queries(5000, 4, [-0.1] * 3, 1.2))
+    q = dev(synth.uniform_queries(12_000, 4, [-0.1] * 3, 1.2))   # Morton-ordered batch
     ki, kd = cg.cga_knn(a, q, 1)
     ni, nd = cg.cga_nn_query(a, q)
     assert torch.equal(ki[:, 0], ni) and torch.equal(kd[:, 0], nd)
+
+
+@pytest.mark.parametrize("kind,bits", [("uniform", 10), ("surface", 10)])
+def test_ordered_batch_parity(cg, orc, kind, bits):
+    """Batches of 8192 queries and more are searched in Morton order; every
+    result still lands in its own query's row."""
+    pts, lo, ext, g, og, a, oa = world(cg, orc, kind, bits)
+    q = queries(pts, lo, ext, 9000, bits + 5)
+    assert len(q) >= 8192
+    off, idx, d2 = cg.cga_radius(a, dev(q), 40)
+    ooff, oidx, od2 = orc.radius(oa, og, q, 40)
+    np.testing.assert_array_equal(off.cpu().numpy().view(np.uint64), ooff)
+    np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), oidx)
+    np.testing.assert_array_equal(d2.cpu().numpy().view(np.uint64), od2)
+    ki, kd = cg.cga_knn(a, dev(q), 8)
+    oi, od = orc.knn(oa, og, q, 8)
+    np.testing.assert_array_equal(kd.cpu().numpy().view(np.uint64), od)
+    np.testing.assert_array_equal(ki.cpu().numpy().view(np.uint32), oi)
 
 
 def test_lattice_ties_and_few_voxels(cg, orc):
