@@ -281,92 +281,105 @@ __device__ __forceinline__ void topk_insert_all(TopK& t, uint32_t lane, uint32_t
 // inserting them one by one.
 constexpr int kKnnBatch = 8;
 
+// |v - q| of a stored coordinate and a query coordinate (clamped to
+// +-2^30, so the difference fits 31 bits).
+__device__ __forceinline__ uint32_t absdiff32(uint32_t v, int q) {
+  const int d = (int)v - q;
+  return (uint32_t)(d < 0 ? -d : d);
+}
+
+__device__ __forceinline__ unsigned long long sq(uint32_t d) {
+  return (unsigned long long)d * d;
+}
+
 // k nearest of one query, one warp: slab rounds as in the NN search (16 per
 // side), every lane walking its slab's columns nearest-first in y and each
-// column's voxels nearest-first in z, in lockstep so that each step's
-// candidates (at most one per lane) enter the list together and the k-th
-// distance prunes every walk.
-__global__ void __launch_bounds__(256, 4) k_knn(SearchSeg sg, uint32_t k, const unsigned long long* __restrict__ order,
-                      uint32_t* out_idx, unsigned long long* out_d2) {
+// column's voxels nearest-first in z.  The lanes step in lockstep, each step
+// offering at most one candidate per lane, so that the candidates enter the
+// list together and the k-th distance prunes every walk; a lane whose column
+// runs out moves to its next column (and offers that column's nearest voxel)
+// in the same step.
+__global__ void __launch_bounds__(256, 4) k_knn(SearchSeg sg, uint32_t k,
+                                                const unsigned long long* __restrict__ order,
+                                                uint32_t* out_idx, unsigned long long* out_d2) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const Levels& a = sg.a;
   const uint32_t u = (uint32_t)a.hdr->cnt[0], h = (uint32_t)a.hdr->cnt[2];
-  const uint32_t b = a.bits;
-  const long long top = (1ll << b) - 1;
+  const int top = (1 << a.bits) - 1;
   for (uint32_t sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < sg.m; sl += nw) {
     const uint32_t j = slot_query(order, sl);
     TopK t{~0ull, 0xffffffffu};
     const RQuery q = radius_query(sg, j);
     if (q.valid && u > 0) {
-      const uint32_t cqx = (uint32_t)min(max(q.x, 0ll), top);
-      const uint32_t cqy = (uint32_t)min(max(q.y, 0ll), top);
-      const uint32_t cqz = (uint32_t)min(max(q.z, 0ll), top);
-      const uint32_t xr0 = lower_bound_u16(a.idx2, 0, h, cqx);
+      const int qx = (int)q.x, qy = (int)q.y, qz = (int)q.z;
+      const uint32_t cqy = (uint32_t)min(max(qy, 0), top);
+      const uint32_t cqz = (uint32_t)min(max(qz, 0), top);
+      const uint32_t xr0 = lower_bound_u16(a.idx2, 0, h, (uint32_t)min(max(qx, 0), top));
       const bool right = (lane & 1u) == 0u;
       unsigned long long bound = ~0ull;
       for (uint32_t r = 0;; ++r) {
-        const long long kk = (long long)r * 16 + (lane >> 1);
-        const long long slab = right ? (long long)xr0 + kk : (long long)xr0 - 1 - kk;
-        bool work = slab >= 0 && slab < (long long)h;
+        const int kk = (int)(r * 16u + (lane >> 1));
+        const int slab = right ? (int)xr0 + kk : (int)xr0 - 1 - kk;
+        bool work = slab >= 0 && slab < (int)h;
         unsigned long long dx2 = 0;
-        uint32_t x = 0, ys = 0, ye = 0;
+        uint32_t ys = 0, ye = 0;
         if (work) {
-          x = __ldg(a.idx2 + slab);
+          dx2 = sq(absdiff32(__ldg(a.idx2 + slab), qx));
           ys = __ldg(a.ptr2 + slab);
           ye = __ldg(a.ptr2 + slab + 1);
-          const unsigned long long dx = absdiff_ll(x, q.x);
-          dx2 = dx * dx;
           work = dx2 <= bound;
         }
         if (!__any_sync(0xffffffffu, work)) break;
-        // column cursors (outward from the query's y) and the current column
-        long long cr = 0, cl = -1;
+        // column cursors outward from the query's y: [cr, ye) to the right,
+        // [ys, cl) to the left; z cursors likewise within the column
+        uint32_t cr = 0, cl = 0;
         if (work) {
           cr = lower_bound_u16(a.idx1, ys, ye, cqy);
-          cl = cr - 1;
+          cl = cr;
         }
         bool in_col = false;
         unsigned long long dxy = 0;
-        long long zu = 0, zd = -1, zs = 0, ze = 0;
+        uint32_t zs = 0, ze = 0, zu = 0, zd = 0;
         while (__any_sync(0xffffffffu, work)) {
           bool has = false;
           unsigned long long cd = ~0ull;
           uint32_t ci = 0xffffffffu;
-          if (work && !in_col) {
-            // the next column, nearest in y first, while it can still beat the bound
-            const bool hr = cr < (long long)ye, hl = cl >= (long long)ys;
-            const unsigned long long er = hr ? absdiff_ll(__ldg(a.idx1 + cr), q.y) : ~0ull;
-            const unsigned long long el = hl ? absdiff_ll(__ldg(a.idx1 + cl), q.y) : ~0ull;
-            const bool gr = hr && (!hl || er <= el);
-            const unsigned long long dy = gr ? er : el;
-            if ((!hr && !hl) || dx2 + dy * dy > bound) {
-              work = false;
-            } else {
-              const long long c = gr ? cr : cl;
-              if (gr) ++cr; else --cl;
-              dxy = dx2 + dy * dy;
-              zs = __ldg(a.ptr1 + c);
-              ze = __ldg(a.ptr1 + c + 1);
-              zu = lower_bound_u16(a.idx0, (uint32_t)zs, (uint32_t)ze, cqz);
-              zd = zu - 1;
-              in_col = true;
+#pragma unroll 1
+          for (int pass = 0; pass < 2; ++pass) {
+            if (work && !has && !in_col) {
+              // the next column, nearest in y first, while it can still beat the bound
+              const bool hr = cr < ye, hl = cl > ys;
+              const uint32_t er = hr ? absdiff32(__ldg(a.idx1 + cr), qy) : 0xffffffffu;
+              const uint32_t el = hl ? absdiff32(__ldg(a.idx1 + cl - 1), qy) : 0xffffffffu;
+              const bool gr = hr && (!hl || er <= el);
+              const unsigned long long d = dx2 + sq(gr ? er : el);
+              if ((!hr && !hl) || d > bound) {
+                work = false;
+              } else {
+                const uint32_t c = gr ? cr++ : --cl;
+                dxy = d;
+                zs = __ldg(a.ptr1 + c);
+                ze = __ldg(a.ptr1 + c + 1);
+                zu = lower_bound_u16(a.idx0, zs, ze, cqz);
+                zd = zu;
+                in_col = true;
+              }
             }
-          } else if (work) {
-            // the next voxel of the column, nearest in z first
-            const bool hu = zu < ze, hd = zd >= zs;
-            const unsigned long long eu = hu ? absdiff_ll(__ldg(a.idx0 + zu), q.z) : ~0ull;
-            const unsigned long long ed = hd ? absdiff_ll(__ldg(a.idx0 + zd), q.z) : ~0ull;
-            const bool gu = hu && (!hd || eu <= ed);
-            const unsigned long long dz = gu ? eu : ed;
-            if ((!hu && !hd) || dxy + dz * dz > bound) {
-              in_col = false;
-            } else {
-              const long long p = gu ? zu : zd;
-              if (gu) ++zu; else --zd;
-              has = true;
-              cd = dxy + dz * dz;
-              ci = (uint32_t)p;
+            if (work && !has && in_col) {
+              // the column's next voxel, nearest in z first
+              const bool hu = zu < ze, hd = zd > zs;
+              const uint32_t eu = hu ? absdiff32(__ldg(a.idx0 + zu), qz) : 0xffffffffu;
+              const uint32_t ed = hd ? absdiff32(__ldg(a.idx0 + zd - 1), qz) : 0xffffffffu;
+              const bool gu = hu && (!hd || eu <= ed);
+              const unsigned long long d = dxy + sq(gu ? eu : ed);
+              if ((!hu && !hd) || d > bound) {
+                in_col = false;
+              } else {
+                ci = gu ? zu++ : --zd;
+                cd = d;
+                has = true;
+              }
             }
           }
           uint32_t pending = __ballot_sync(0xffffffffu, has);
