@@ -787,14 +787,20 @@ def run_search(args, world_size, local_rank, torch, cga):
     def radius_step():
         state["radius"] = cga.cga_radius(world, q, r2)
 
+    def knn400_step():
+        state["knn400"] = cga.cga_knn(world, q, 400)
+        del state["knn400"]
+
     for _ in range(args.warmup):
         knn_step()
         radius_step()
+        knn400_step()
     torch.cuda.synchronize()
     clocks = start_clocks(local_rank)
     launches0 = cga.kernel_launches()
     knn_ms = [timed(torch, knn_step, flush, float(i)) for i in range(args.steps)]
     rad_ms = [timed(torch, radius_step, flush, float(i)) for i in range(args.steps)]
+    k400_ms = [timed(torch, knn400_step, flush, float(i)) for i in range(args.steps)]
     launches = cga.kernel_launches() - launches0
     clk = clocks.stop()
     total_results = int(state["radius"][0][-1].item())
@@ -809,6 +815,7 @@ def run_search(args, world_size, local_rank, torch, cga):
                 "radius_queries_s": round(m / (rt / 1e3), 1),
                 "radius_results": total_results,
                 "radius_results_per_s": round(total_results / (rt / 1e3), 1),
+                "knn400_ms": round(float(np.mean(k400_ms)), 4),
                 "note": "radius_ms includes the wait for the total between count and fill",
                 "gpu_launches": int(launches), "clocks": clk})
     return out

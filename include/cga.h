@@ -277,8 +277,9 @@ int cga_radius_fill(const cga_t* a, const float* d_q, uint64_t m, uint64_t r2,
  * distance, key) pairs, ascending, at d_idx / d_dist2 [j * k, j * k + k)
  * (device, m * k entries each).  Slots past the number of stored voxels,
  * and all slots of a non-finite query, hold UINT32_MAX / UINT64_MAX.
- * k = 1 is cga_nn_query's answer.  1 <= k <= CGA_KNN_MAX_K. */
-#define CGA_KNN_MAX_K 32
+ * k = 1 is cga_nn_query's answer.  1 <= k <= CGA_KNN_MAX_K (the paper's
+ * Fig. 3 shows 400 neighbours). */
+#define CGA_KNN_MAX_K 1024
 int cga_knn(const cga_t* a, const float* d_q, uint64_t m, uint32_t k, uint32_t* d_idx,
             uint64_t* d_dist2, void* stream);
 

@@ -519,6 +519,8 @@ int cga_radius_fill(const cga_t* a, const float* d_q, uint64_t m, uint64_t r2,
   return rc;
 }
 
+static_assert(CGA_KNN_MAX_K == libcga::kKnnMaxK, "k-NN limit");
+
 int cga_knn(const cga_t* a, const float* d_q, uint64_t m, uint32_t k, uint32_t* d_idx,
             uint64_t* d_dist2, void* stream) {
   if (a == nullptr || k < 1 || k > CGA_KNN_MAX_K || m > CGA_MAX_POINTS ||

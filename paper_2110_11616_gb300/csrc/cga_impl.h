@@ -218,7 +218,8 @@ cudaError_t run_radius_count(const SearchSeg& sg, unsigned long long r2,
 cudaError_t run_radius_fill(const SearchSeg& sg, unsigned long long r2,
                             const unsigned long long* order, const unsigned long long* offsets,
                             uint32_t* idx, unsigned long long* d2, cudaStream_t stream);
-// idx, d2: m * k entries (k <= 32), query j's k nearest ascending.
+// idx, d2: m * k entries (k <= kKnnMaxK), query j's k nearest ascending.
+constexpr uint32_t kKnnMaxK = 1024;
 cudaError_t run_knn(const SearchSeg& sg, uint32_t k, const unsigned long long* order, uint32_t* idx,
                     unsigned long long* d2, cudaStream_t stream);
 

@@ -10,6 +10,8 @@
 //                   lanes' counts places every slab's voxels, so the output
 //                   is in (x, y, z) = CGA order without sorting
 #include <algorithm>
+#include <mutex>
+#include <type_traits>
 
 #include "k_common.cuh"
 
@@ -280,6 +282,114 @@ __device__ __forceinline__ void topk_insert_all(TopK& t, uint32_t lane, uint32_t
 // Above this many candidates in one step, one bitonic merge is cheaper than
 // inserting them one by one.
 constexpr int kKnnBatch = 8;
+constexpr uint32_t kKnnLargeThreads = 128;  // 4 warps, each with its own buffer
+
+// Candidate collection for k <= 32: the list in registers.
+struct RegList {
+  TopK t;
+  uint32_t k;
+
+  __device__ __forceinline__ void init(uint32_t kk) {
+    t = TopK{~0ull, 0xffffffffu};
+    k = kk;
+  }
+  // Offer each lane's candidate (if any); returns the new pruning bound.
+  __device__ __forceinline__ unsigned long long offer(bool has, unsigned long long cd, uint32_t ci,
+                                                      uint32_t lane) {
+    uint32_t pending = __ballot_sync(0xffffffffu, has);
+    if (__popc(pending) > kKnnBatch) {
+      topk_insert_all(t, lane, k, cd, ci);
+    } else {
+      while (pending) {
+        const uint32_t src = __ffs(pending) - 1;
+        pending &= pending - 1;
+        topk_insert(t, lane, k, __shfl_sync(0xffffffffu, cd, src),
+                    __shfl_sync(0xffffffffu, ci, src));
+      }
+    }
+    return __shfl_sync(0xffffffffu, t.d2, k - 1);
+  }
+  __device__ __forceinline__ void finish(uint32_t lane, size_t row, uint32_t* out_idx,
+                                         unsigned long long* out_d2) {
+    if (lane < k) {
+      out_idx[row + lane] = t.idx;
+      out_d2[row + lane] = t.d2;
+    }
+  }
+};
+
+// Candidate collection for 32 < k <= CGA_KNN_MAX_K: the warp's buffer of
+// `cap` (a power of two, at least 2k) entries in shared memory.  Candidates
+// are appended unsorted; whenever the next step could overflow it, or when it
+// first holds k, the buffer is sorted by a bitonic network and cut to k, and
+// the k-th distance becomes the bound.  Every voxel pruned by a bound is
+// beaten by k collected ones, so the final sort's first k are the answer.
+struct SmemList {
+  unsigned long long* d;
+  uint32_t* ix;
+  uint32_t n, k, cap;
+
+  __device__ __forceinline__ void sort_cut(uint32_t lane) {
+    uint32_t P = 32;
+    while (P < n) P <<= 1;
+    for (uint32_t e = n + lane; e < P; e += 32) {
+      d[e] = ~0ull;
+      ix[e] = 0xffffffffu;
+    }
+    __syncwarp();
+    for (uint32_t w = 2; w <= P; w <<= 1) {
+      for (uint32_t jj = w >> 1; jj > 0; jj >>= 1) {
+        for (uint32_t tt = lane; tt < P / 2; tt += 32) {
+          const uint32_t i = ((tt & ~(jj - 1)) << 1) | (tt & (jj - 1)), l = i + jj;
+          const unsigned long long di = d[i], dl = d[l];
+          const uint32_t xi = ix[i], xl = ix[l];
+          const bool up = (i & w) == 0;
+          if (up ? pair_less(dl, xl, di, xi) : pair_less(di, xi, dl, xl)) {
+            d[i] = dl;
+            ix[i] = xl;
+            d[l] = di;
+            ix[l] = xi;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    n = min(n, k);
+  }
+  __device__ __forceinline__ void init(uint32_t kk, uint32_t cp, unsigned long long* dd,
+                                       uint32_t* xx) {
+    d = dd;
+    ix = xx;
+    n = 0;
+    k = kk;
+    cap = cp;
+  }
+  __device__ __forceinline__ unsigned long long offer(bool has, unsigned long long cd, uint32_t ci,
+                                                      uint32_t lane, unsigned long long bound) {
+    const uint32_t pending = __ballot_sync(0xffffffffu, has);
+    if (has) {
+      const uint32_t pos = n + __popc(pending & ((1u << lane) - 1u));
+      d[pos] = cd;
+      ix[pos] = ci;
+    }
+    n += __popc(pending);
+    __syncwarp();
+    if (n + 32 > cap || (bound == ~0ull && n >= k)) {
+      sort_cut(lane);
+      return n >= k ? d[k - 1] : ~0ull;
+    }
+    return bound;
+  }
+  __device__ __forceinline__ void finish(uint32_t lane, size_t row, uint32_t* out_idx,
+                                         unsigned long long* out_d2) {
+    sort_cut(lane);
+    for (uint32_t e = lane; e < k; e += 32) {
+      out_idx[row + e] = e < n ? ix[e] : 0xffffffffu;
+      out_d2[row + e] = e < n ? d[e] : ~0ull;
+    }
+    __syncwarp();
+  }
+};
 
 // |v - q| of a stored coordinate and a query coordinate (clamped to
 // +-2^30, so the difference fits 31 bits).
@@ -299,17 +409,27 @@ __device__ __forceinline__ unsigned long long sq(uint32_t d) {
 // list together and the k-th distance prunes every walk; a lane whose column
 // runs out moves to its next column (and offers that column's nearest voxel)
 // in the same step.
-__global__ void __launch_bounds__(256, 4) k_knn(SearchSeg sg, uint32_t k,
-                                                const unsigned long long* __restrict__ order,
-                                                uint32_t* out_idx, unsigned long long* out_d2) {
+template <bool LARGE>
+__global__ void __launch_bounds__(LARGE ? kKnnLargeThreads : 256, LARGE ? 1 : 4)
+    k_knn(SearchSeg sg, uint32_t k, uint32_t cap, const unsigned long long* __restrict__ order,
+          uint32_t* out_idx, unsigned long long* out_d2) {
+  extern __shared__ unsigned long long s_knn[];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const Levels& a = sg.a;
   const uint32_t u = (uint32_t)a.hdr->cnt[0], h = (uint32_t)a.hdr->cnt[2];
   const int top = (1 << a.bits) - 1;
+  typename std::conditional<LARGE, SmemList, RegList>::type list;
   for (uint32_t sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < sg.m; sl += nw) {
     const uint32_t j = slot_query(order, sl);
-    TopK t{~0ull, 0xffffffffu};
+    if constexpr (LARGE) {
+      const uint32_t wb = threadIdx.x >> 5;
+      unsigned long long* base = s_knn + (size_t)wb * cap;
+      list.init(k, cap, base,
+                reinterpret_cast<uint32_t*>(s_knn + (size_t)(blockDim.x >> 5) * cap) + (size_t)wb * cap);
+    } else {
+      list.init(k);
+    }
     const RQuery q = radius_query(sg, j);
     if (q.valid && u > 0) {
       const int qx = (int)q.x, qy = (int)q.y, qz = (int)q.z;
@@ -382,25 +502,15 @@ __global__ void __launch_bounds__(256, 4) k_knn(SearchSeg sg, uint32_t k,
               }
             }
           }
-          uint32_t pending = __ballot_sync(0xffffffffu, has);
-          if (__popc(pending) > kKnnBatch) {
-            topk_insert_all(t, lane, k, cd, ci);
+          if constexpr (LARGE) {
+            bound = list.offer(has, cd, ci, lane, bound);
           } else {
-            while (pending) {
-              const uint32_t src = __ffs(pending) - 1;
-              pending &= pending - 1;
-              topk_insert(t, lane, k, __shfl_sync(0xffffffffu, cd, src),
-                          __shfl_sync(0xffffffffu, ci, src));
-            }
+            bound = list.offer(has, cd, ci, lane);
           }
-          bound = __shfl_sync(0xffffffffu, t.d2, k - 1);
         }
       }
     }
-    if (lane < k) {
-      out_idx[(size_t)j * k + lane] = t.idx;
-      out_d2[(size_t)j * k + lane] = t.d2;
-    }
+    list.finish(lane, (size_t)j * k, out_idx, out_d2);
   }
 }
 
@@ -411,10 +521,32 @@ unsigned search_blocks(uint64_t m) {
 
 }  // namespace
 
+// Buffer entries per warp for k > 32: the least power of two >= 2k.
+static uint32_t knn_cap(uint32_t k) {
+  uint32_t c = 64;
+  while (c < 2 * k) c <<= 1;
+  return c;
+}
+
 cudaError_t run_knn(const SearchSeg& sg, uint32_t k, const unsigned long long* order, uint32_t* idx,
                     unsigned long long* d2, cudaStream_t stream) {
   if (sg.m == 0) return cudaSuccess;
-  k_knn<<<search_blocks(sg.m), 256, 0, stream>>>(sg, k, order, idx, d2);
+  if (k <= 32) {
+    k_knn<false><<<search_blocks(sg.m), 256, 0, stream>>>(sg, k, 0, order, idx, d2);
+  } else {
+    const uint32_t cap = knn_cap(k);
+    const size_t smem = (size_t)(kKnnLargeThreads / 32) * cap * 12;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+      attr = cudaFuncSetAttribute(k_knn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)((kKnnLargeThreads / 32) * knn_cap(kKnnMaxK) * 12));
+    });
+    if (attr != cudaSuccess) return attr;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((sg.m + 3) / 4,
+                                                         (uint64_t)device_sm_count() * 4);
+    k_knn<true><<<blocks, kKnnLargeThreads, smem, stream>>>(sg, k, cap, order, idx, d2);
+  }
   count_launch(1);
   return cudaGetLastError();
 }

@@ -74,6 +74,33 @@ def test_knn_parity(cg, orc, kind, bits, k):
     np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), oi)
 
 
+@pytest.mark.parametrize("kind,bits", [("uniform", 7), ("surface", 10), ("lidar", 16)])
+@pytest.mark.parametrize("k", [33, 100, 400, 1024])
+def test_knn_large_k_parity(cg, orc, kind, bits, k):
+    """k above 32 collects candidates in a shared-memory buffer that is sorted
+    and cut to k whenever it fills (the paper's Fig. 3 shows 400-NN)."""
+    pts, lo, ext, g, og, a, oa = world(cg, orc, kind, bits)
+    q = queries(pts, lo, ext, 120, bits * k)
+    idx, d2 = cg.cga_knn(a, dev(q), k)
+    oi, od = orc.knn(oa, og, q, k)
+    np.testing.assert_array_equal(d2.cpu().numpy().view(np.uint64), od)
+    np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), oi)
+
+
+def test_knn_large_k_few_voxels(cg, orc):
+    """Fewer stored voxels than k: the tail holds the sentinels."""
+    ax = np.arange(4, dtype=np.float32)
+    vox = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3) + 0.5
+    og, g = orc.Grid(4, 1.0, (0.0, 0.0, 0.0)), cg.make_grid(4, 1.0, (0.0, 0.0, 0.0))
+    a, oa = cg.cga_build(dev(vox), g), orc.build(vox, og)
+    q = np.array([[1.5, 1.5, 1.5], [9, 9, 9], [np.inf, 0, 0]], np.float32)
+    for k in (40, 64, 65, 200):
+        idx, d2 = cg.cga_knn(a, dev(q), k)
+        oi, od = orc.knn(oa, og, q, k)
+        np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), oi)
+        np.testing.assert_array_equal(d2.cpu().numpy().view(np.uint64), od)
+
+
 def test_knn_one_equals_nn(cg):
     pts = synth.uniform_cube(30_000, seed=3)
     g = cg.grid_from_box([0, 0, 0], 1.0, 12)
@@ -123,6 +150,6 @@ def test_lattice_ties_and_few_voxels(cg, orc):
 def test_search_arguments(cg):
     a = cg.cga_build(dev(np.zeros((1, 3))), cg.grid_from_box([0, 0, 0], 1.0, 8))
     with pytest.raises(cg.CgaError):
-        cg.cga_knn(a, dev(np.zeros((2, 3))), 33)
+        cg.cga_knn(a, dev(np.zeros((2, 3))), 1025)
     with pytest.raises(cg.CgaError):
         cg.cga_knn(a, dev(np.zeros((2, 3))), 0)
