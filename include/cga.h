@@ -3,8 +3,8 @@
  *
  * C ABI of the hot path of "Compressed Geometric Arrays for Point Cloud
  * Processing" (Roodaki & Nazm Bojnordi): quantize float32 points to a voxel
- * grid, encode and sort them into the CGA layout of Sec. III, and run the CGA
- * operations of Sec. III-A..C (merge, orthogonal projection, exact nearest
+ * grid, encode and sort them into the CGA layout of Sec. V, and run the CGA
+ * operations of Sec. V-A..C (merge, orthogonal projection, exact nearest
  * neighbour) plus lossless decode.  Every step runs in hand-written CUDA
  * kernels; the host side only validates arguments, allocates and launches.
  *
@@ -52,7 +52,7 @@ extern "C" {
 #define CGA_MAX_POINTS ((uint64_t)((1u << 30) - 1u))
 
 /* Voxel grid.  Quantization (the paper gives no formula; Sec. II-E-2-a asks
- * for a bounding box holding every point, Sec. V uses QP = bits per axis):
+ * for a bounding box holding every point, Sec. VI-C uses QP = bits per axis):
  *   q_a = clamp(floorf(fmaf(p_a, scale, offset[a])), 0, 2^bits - 1)
  * evaluated in float32 with one rounding in the fma; the clamp keeps points on
  * or outside the box faces inside the grid. */
@@ -75,8 +75,8 @@ typedef struct {
   void (*free)(void* ctx, void* ptr, void* stream);
 } cga_allocator;
 
-typedef struct cga cga_t;      /* a 3-level CGA (Sec. III) */
-typedef struct cga2d cga2d_t;  /* a 2-level CGA of a projection (Sec. III-B) */
+typedef struct cga cga_t;      /* a 3-level CGA (Sec. V) */
+typedef struct cga2d cga2d_t;  /* a 2-level CGA of a projection (Sec. V-B) */
 
 typedef struct {
   uint64_t h;         /* |X_index| distinct x                   */
@@ -109,7 +109,7 @@ typedef struct {
 #define CGA_PLANE_XZ 1
 #define CGA_PLANE_YZ 2
 
-/* Build (Sec. III, arrays; quantization as in cga_grid).
+/* Build (Sec. V, arrays; quantization as in cga_grid).
  * d_xyz: n points, float32 AoS (x, y, z), device, caller-owned, 4-byte
  *   aligned; n may be 0 (empty CGA: h = g = u = 0, X_pointer = Y_pointer = {0}).
  * h_xform12: NULL or 12 host floats, R (3x3 row-major) then t, applied first as
@@ -123,20 +123,20 @@ typedef struct {
 int cga_build(const float* d_xyz, uint64_t n, const cga_grid* g, const float* h_xform12,
               const cga_allocator* A, void* stream, cga_t** out);
 
-/* Merge (Eq. 1, Sec. III-A): *out holds the set union of the voxels of a and
+/* Merge (Eq. 1, Sec. V-A): *out holds the set union of the voxels of a and
  * b, which must share one grid (bits, scale, offsets bit-identical), else
  * CGA_ERR_GRID_MISMATCH.  Either input may be empty. */
 int cga_merge(const cga_t* a, const cga_t* b, const cga_allocator* A, void* stream,
               cga_t** out);
 
-/* Orthogonal projection (Eq. 3 with m_x = m_y = 1, Sec. III-B) onto plane
+/* Orthogonal projection (Eq. 3 with m_x = m_y = 1, Sec. V-B) onto plane
  * CGA_PLANE_XY (keeps x, y), _XZ (x, z) or _YZ (y, z): *out holds the set of
  * distinct 2D voxels as a 2-level CGA, U_index/U_pointer over the first kept
  * axis and V_index over the second, ascending at both levels. */
 int cga_project(const cga_t* a, int plane, const cga_allocator* A, void* stream,
                 cga2d_t** out);
 
-/* Exact nearest neighbour (Eq. 7-8, Sec. III-C).
+/* Exact nearest neighbour (Eq. 7-8, Sec. V-C).
  * d_q: m query points, float32 AoS, device.  Each query maps to the voxel
  *   floorf(fmaf(p_a, scale, offset_a)) of a's grid, clamped only to
  *   [-2^30, 2^30] (queries outside the box are allowed).
@@ -162,7 +162,7 @@ int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
  * do not change: the exact nearest voxel, ties to the smaller key).
  * Every call also builds (once) an x directory per level: for each x value v
  * the index of the first X_index entry >= v -- the dense per-x table of
- * G-Arrays (Sec. III) used only to start a slab walk in one lookup
+ * G-Arrays (Sec. V) used only to start a slab walk in one lookup
  * (4 * (2^bits + 1) bytes for the CGA itself).
  * shifts: count (0..CGA_NN_MAX_LEVELS) strictly increasing values in
  * 1..min(CGA_NN_MAX_SHIFT, bits-1), host memory; count 0 drops the coarse
@@ -224,12 +224,12 @@ int cga_nn_query_noalloc(const cga_t* a, const float* d_q, uint64_t m, uint32_t*
  * (may be NULL when the handle's capacity is 0). */
 int cga_decode(const cga_t* a, uint32_t* d_xyz, void* stream);
 
-/* ---- Value (attribute) array, Sec. III --------------------------------------
+/* ---- Value (attribute) array, Sec. V --------------------------------------
  * A CGA may carry one row of `channels` (1..CGA_MAX_CHANNELS) uint8
  * attributes per stored voxel, in CGA point order: row p belongs to
  * Z_index[p].  Several points quantized into one voxel give it the
  * round-half-up integer mean (sum + k/2) / k of their k rows per channel
- * (Sec. V: the colours of the points merged into one box are averaged), or the
+ * (Sec. III-B: the colours of the points merged into one box are averaged), or the
  * row of the first of them in input order.  A merge keeps, for a voxel held by
  * both inputs, the base's (a's) row or (a + b + 1) / 2 per channel (Sec. II-A);
  * a voxel held by one input keeps its row. */
@@ -241,7 +241,7 @@ int cga_decode(const cga_t* a, uint32_t* d_xyz, void* stream);
 
 /* cga_build plus the Value array.  d_attr: n * channels uint8 rows, device,
  * point order (the same points as d_xyz).  Each point finds its voxel by the
- * Sec. III-A lookup; sums are exact integers, so the result does not depend
+ * Sec. V-A lookup; sums are exact integers, so the result does not depend
  * on arrival order.  Errors as cga_build; CGA_ERR_INVALID_ARG for channels or
  * policy out of range or a NULL d_attr with n > 0. */
 int cga_build_values(const float* d_xyz, const uint8_t* d_attr, uint32_t channels, uint64_t n,

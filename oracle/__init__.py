@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` load this module; the CUDA library and its
 Python binding never do.  The oracle computes the plain definitions of the
-paper's CGA operations (Sec. III arrays, Eq. 1 merge, Eq. 3 projection,
+paper's CGA operations (Sec. V arrays, Eq. 1 merge, Eq. 3 projection,
 Eq. 7-8 nearest neighbour) with std::sort / std::unique / std::set_union and
 exhaustive search.
 
@@ -100,6 +100,14 @@ def lib():
                                           ctypes.POINTER(_Cga), P]
         _lib.orc_merge_values.argtypes = [ctypes.POINTER(_Cga), P, ctypes.POINTER(_Cga), P, U32,
                                           ctypes.c_int, ctypes.POINTER(_Cga), P]
+        C = ctypes.POINTER(_Cga)
+        _lib.orc_lookup_voxels.argtypes = [C, P, U64, P]
+        _lib.orc_garrays_x.argtypes = [C, P]
+        _lib.orc_garrays_lookup.argtypes = [C, P, P, U64, P]
+        _lib.orc_nn_voxels.argtypes = [C, P, U64, P, P]
+        _lib.orc_kmeans.argtypes = [C, U32, P, P, P, P]
+        _lib.orc_motion_vectors.argtypes = [P, P, P, P, P]
+        _lib.orc_reconstruct.argtypes = [C, P, P, P]
         for fn in (_lib.orc_nn_brute, _lib.orc_nn_window):
             fn.argtypes = [ctypes.POINTER(_Cga), F, P, P, U64, P, P]
     return _lib
@@ -274,7 +282,7 @@ def _attrs(attr, n):
 
 
 def build_values(xyz, attr, grid: Grid, xform=None, policy="average"):
-    """Build plus the Value array (Sec. III): returns (Cga, values (u, channels) uint8)."""
+    """Build plus the Value array (Sec. V): returns (Cga, values (u, channels) uint8)."""
     p = _f32xyz(xyz)
     a = _attrs(attr, len(p))
     ch = a.shape[1]
@@ -385,3 +393,79 @@ def nn_brute(a: Cga, grid: Grid, q):
 
 def nn_window(a: Cga, grid: Grid, q):
     return _nn(lib().orc_nn_window, a, grid, q)
+
+
+# ---- compression pieces (Sec. V-D) and the G-Arrays form (Sec. V) -----------
+def _i32xyz(v) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(v, dtype=np.int32).reshape(-1, 3))
+
+
+def lookup_voxels(a: Cga, qv):
+    """CGA index of each integer voxel (uint32), UINT32_MAX when absent."""
+    q = _i32xyz(qv)
+    out = np.zeros(max(len(q), 1), np.uint32)
+    s = a._struct()
+    _check(lib().orc_lookup_voxels(ctypes.byref(s), _ptr(q), len(q), _ptr(out)))
+    return out[:len(q)]
+
+
+def garrays_x(a: Cga):
+    """The G-Arrays X_pointer: 2^bits + 1 cells, xptr[v] = columns with x < v."""
+    out = np.zeros((1 << a.bits) + 1, np.uint32)
+    s = a._struct()
+    _check(lib().orc_garrays_x(ctypes.byref(s), _ptr(out)))
+    return out
+
+
+def garrays_lookup(a: Cga, xptr, qv):
+    """The lookup through the G-Arrays X_pointer (same answer as lookup_voxels)."""
+    q = _i32xyz(qv)
+    xp = np.ascontiguousarray(np.asarray(xptr, np.uint32))
+    out = np.zeros(max(len(q), 1), np.uint32)
+    s = a._struct()
+    _check(lib().orc_garrays_lookup(ctypes.byref(s), _ptr(xp), _ptr(q), len(q), _ptr(out)))
+    return out[:len(q)]
+
+
+def nn_voxels(a: Cga, qv):
+    """Exact NN of integer query voxels: (idx uint32, dist2 uint64)."""
+    q = _i32xyz(qv)
+    idx = np.zeros(max(len(q), 1), np.uint32)
+    d2 = np.zeros(max(len(q), 1), np.uint64)
+    s = a._struct()
+    _check(lib().orc_nn_voxels(ctypes.byref(s), _ptr(q), len(q), _ptr(idx), _ptr(d2)))
+    return idx[:len(q)], d2[:len(q)]
+
+
+def kmeans(a: Cga, max_iter: int):
+    """k-means of the stored voxels, 8 corner-seeded centres (Sec. V-D):
+    (labels (u,) uint8, centres (8, 3) int64 in 1/256 voxel, counts (8,) uint64, passes)."""
+    lab = np.zeros(max(a.u, 1), np.uint8)
+    cen = np.zeros(24, np.int64)
+    cnt = np.zeros(8, np.uint64)
+    it = np.zeros(1, np.uint32)
+    s = a._struct()
+    _check(lib().orc_kmeans(ctypes.byref(s), int(max_iter), _ptr(lab), _ptr(cen), _ptr(cnt),
+                            _ptr(it)))
+    return lab[:a.u], cen.reshape(8, 3), cnt, int(it[0])
+
+
+def motion_vectors(ref_centres, ref_counts, pred_centres, pred_counts):
+    """mv[c] = ref[c] - pred[c] (1/256 voxel), 0 where either cluster is empty."""
+    rc = np.ascontiguousarray(np.asarray(ref_centres, np.int64).reshape(24))
+    pc = np.ascontiguousarray(np.asarray(pred_centres, np.int64).reshape(24))
+    rn = np.ascontiguousarray(np.asarray(ref_counts, np.uint64).reshape(8))
+    pn = np.ascontiguousarray(np.asarray(pred_counts, np.uint64).reshape(8))
+    mv = np.zeros(24, np.int64)
+    _check(lib().orc_motion_vectors(_ptr(rc), _ptr(rn), _ptr(pc), _ptr(pn), _ptr(mv)))
+    return mv.reshape(8, 3)
+
+
+def reconstruct(a: Cga, labels, mv):
+    """Each voxel moved by its cluster's motion vector rounded half up: (u, 3) int32."""
+    lab = np.ascontiguousarray(np.asarray(labels, np.uint8))
+    m = np.ascontiguousarray(np.asarray(mv, np.int64).reshape(24))
+    out = np.zeros((max(a.u, 1), 3), np.int32)
+    s = a._struct()
+    _check(lib().orc_reconstruct(ctypes.byref(s), _ptr(lab), _ptr(m), _ptr(out)))
+    return out[:a.u]

@@ -9,13 +9,13 @@
  * Readings of the paper where it is silent (each also listed in the design
  * notes of the repository):
  *  - Quantization (the paper gives no formula; Sec. II-E-2-a asks for a
- *    bounding box that includes all points, Sec. V uses QP = bits per axis):
+ *    bounding box that includes all points, Sec. VI-C uses QP = bits per axis):
  *    q = floorf(fmaf(p, scale, offset)), clamped in float to [0, 2^b - 1].
  *  - Rigid transform before merging (Sec. II-A, views brought to a common
  *    frame): p' = R p + t with the fixed nesting
  *    p'_r = fmaf(R[r][0], x, fmaf(R[r][1], y, fmaf(R[r][2], z, t[r]))).
  *  - Arrays are sorted ascending at every level (x, then y, then z), duplicate
- *    voxels are stored once (Sec. III), X_pointer is indexed by rank in
+ *    voxels are stored once (Sec. V), X_pointer is indexed by rank in
  *    X_index (h + 1 entries), and a Y_pointer count is per (x, y) column.
  *  - NN: query voxel not clamped to the grid (only to +-2^30), squared integer
  *    distance, ties broken by the smaller key (Eq. 8 allows a set).
@@ -35,7 +35,7 @@ namespace {
 
 bool finite(float v) { return std::isfinite(v); }
 
-// Sec. II-E-2-a / Sec. V reading: one float per axis, clamped to the box.
+// Sec. II-E-2-a / Sec. VI-C reading: one float per axis, clamped to the box.
 uint32_t quantize_axis(float v, float scale, float offset, uint32_t bits) {
   float f = std::floor(std::fmaf(v, scale, offset));
   const float hi = (float)((1u << bits) - 1u);
@@ -129,7 +129,7 @@ int orc_quantize(const float* xyz, uint64_t n, uint32_t bits, float scale,
   return status;
 }
 
-// Sec. III: Z_index holds the z of every stored point; Y_index the y of every
+// Sec. V: Z_index holds the z of every stored point; Y_index the y of every
 // distinct (x, y) column with Y_pointer[0] = 0 and Y_pointer[i+1] =
 // Y_pointer[i] + (points in column i); X_index every distinct x with
 // X_pointer[0] = 0 and X_pointer[i+1] = X_pointer[i] + (distinct y at that x).
@@ -185,7 +185,7 @@ int orc_build(const float* xyz, uint64_t n, uint32_t bits, float scale,
   return orc_from_sorted_keys(keys.data(), keys.size(), bits, out);
 }
 
-// Nested walk X -> Y -> Z (Sec. III-A access order).
+// Nested walk X -> Y -> Z (Sec. V-A access order).
 int orc_decode_keys(const orc_cga* a, uint64_t* keys) {
   uint64_t p = 0;
   for (uint64_t i = 0; i < a->h; ++i) {
@@ -214,7 +214,7 @@ int orc_decode(const orc_cga* a, uint32_t* xyz) {
   return p == a->u ? ORC_OK : ORC_ERR_INVALID_ARG;
 }
 
-// Sec. III-A lookup: find x in X_index, then y among Y_index[X_pointer[i] ..
+// Sec. V-A lookup: find x in X_index, then y among Y_index[X_pointer[i] ..
 // X_pointer[i+1]), then z among Z_index[Y_pointer[k] .. Y_pointer[k+1]).
 int64_t orc_lookup(const orc_cga* a, uint32_t x, uint32_t y, uint32_t z) {
   const uint16_t* xb = a->X_index;
@@ -248,7 +248,7 @@ int orc_merge(const orc_cga* a, const orc_cga* b, orc_cga* out) {
 
 // Eq. 3 with m_x = m_y = 1 drops one axis; the projected cloud is the set of
 // distinct 2D voxels, stored as a 2-level CGA (U_pointer recurrence as
-// X_pointer in Sec. III).
+// X_pointer in Sec. V).
 int orc_project(const orc_cga* a, int plane, orc_cga2d* out) {
   if (plane < 0 || plane > 2) return ORC_ERR_INVALID_ARG;
   const uint32_t b = a->bits;
@@ -380,7 +380,7 @@ int orc_nn_brute(const orc_cga* a, float scale, const float offset[3],
   return ORC_OK;
 }
 
-// Sec. III-C procedure.
+// Sec. V-C procedure.
 int orc_nn_window(const orc_cga* a, float scale, const float offset[3],
                   const float* q, uint64_t m, uint32_t* idx, uint64_t* dist2_out) {
   const uint32_t b = a->bits;
@@ -434,7 +434,7 @@ int orc_nn_window(const orc_cga* a, float scale, const float offset[3],
   return ORC_OK;
 }
 
-// Sec. III Value array.  Duplicate points of one voxel: Sec. V averages the
+// Sec. V Value array.  Duplicate points of one voxel: Sec. III-B averages the
 // attributes of the points merged into one box (pcdownsample); the other
 // policy keeps the first point's.  Pairs (key, input index) sorted by key,
 // then by index, give each voxel's points in input order.
@@ -608,6 +608,181 @@ int orc_knn(const orc_cga* a, float scale, const float offset[3], const float* q
     for (uint32_t t = 0; t < k; ++t) {
       idx[j * k + t] = t < take ? (uint32_t)cand[t].second : UINT32_MAX;
       dist2_out[j * k + t] = t < take ? cand[t].first : UINT64_MAX;
+    }
+  }
+  return ORC_OK;
+}
+
+// ---- Compression pieces (Sec. V-D) and G-Arrays (Sec. V) ----------------
+
+// Voxel query lookup: each int32 voxel (any value) by the Sec. V-A lookup.
+int orc_lookup_voxels(const orc_cga* a, const int32_t* qv, uint64_t m, uint32_t* idx) {
+  for (uint64_t j = 0; j < m; ++j) {
+    const int32_t x = qv[3 * j], y = qv[3 * j + 1], z = qv[3 * j + 2];
+    int64_t r = -1;
+    if (x >= 0 && y >= 0 && z >= 0 && x <= 0xFFFF && y <= 0xFFFF && z <= 0xFFFF) {
+      r = orc_lookup(a, (uint32_t)x, (uint32_t)y, (uint32_t)z);
+    }
+    idx[j] = r < 0 ? UINT32_MAX : (uint32_t)r;
+  }
+  return ORC_OK;
+}
+
+// G-Arrays X_pointer (Sec. V, the G-Arrays form): one cell per x value of
+// the whole axis, xptr[v] = the number of (x, y) columns with x < v, so the
+// columns of x = v are [xptr[v], xptr[v + 1]) and an absent x owns none.
+int orc_garrays_x(const orc_cga* a, uint32_t* xptr) {
+  const uint64_t side = 1ull << a->bits;
+  std::vector<uint64_t> cols(side, 0);
+  for (uint64_t i = 0; i < a->h; ++i) cols[a->X_index[i]] = a->X_pointer[i + 1] - a->X_pointer[i];
+  uint64_t run = 0;
+  for (uint64_t v = 0; v < side; ++v) {
+    xptr[v] = (uint32_t)run;
+    run += cols[v];
+  }
+  xptr[side] = (uint32_t)run;
+  return run == a->g ? ORC_OK : ORC_ERR_INVALID_ARG;
+}
+
+// The same lookup through the G-Arrays X_pointer: the x value indexes the
+// pointer array directly, then y and z are searched as in Sec. V-A.
+int orc_garrays_lookup(const orc_cga* a, const uint32_t* xptr, const int32_t* qv, uint64_t m,
+                       uint32_t* idx) {
+  const int64_t side = 1ll << a->bits;
+  for (uint64_t j = 0; j < m; ++j) {
+    const int64_t x = qv[3 * j], y = qv[3 * j + 1], z = qv[3 * j + 2];
+    idx[j] = UINT32_MAX;
+    if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) continue;
+    const uint16_t* yb = a->Y_index + xptr[x];
+    const uint16_t* ye = a->Y_index + xptr[x + 1];
+    const uint16_t* yi = std::lower_bound(yb, ye, (uint16_t)y);
+    if (yi == ye || *yi != y) continue;
+    const uint64_t k = (uint64_t)(yi - a->Y_index);
+    const uint16_t* zb = a->Z_index + a->Y_pointer[k];
+    const uint16_t* ze = a->Z_index + a->Y_pointer[k + 1];
+    const uint16_t* zi = std::lower_bound(zb, ze, (uint16_t)z);
+    if (zi == ze || *zi != z) continue;
+    idx[j] = (uint32_t)(zi - a->Z_index);
+  }
+  return ORC_OK;
+}
+
+// Eq. 7-8 by exhaustive search for integer query voxels (clamped to
+// [-2^30, 2^30] like quantized queries).
+int orc_nn_voxels(const orc_cga* a, const int32_t* qv, uint64_t m, uint32_t* idx,
+                  uint64_t* dist2_out) {
+  std::vector<uint64_t> keys(a->u);
+  if (orc_decode_keys(a, keys.data()) != ORC_OK) return ORC_ERR_INVALID_ARG;
+  const uint32_t b = a->bits;
+  const int64_t lim = 1ll << 30;
+  for (uint64_t j = 0; j < m; ++j) {
+    int64_t q[3];
+    for (int c = 0; c < 3; ++c) q[c] = std::min(std::max((int64_t)qv[3 * j + c], -lim), lim);
+    Best best;
+    for (uint64_t i = 0; i < a->u; ++i) {
+      best.offer(dist2(q, key_x(keys[i], b), key_y(keys[i], b), key_z(keys[i], b)), keys[i], i);
+    }
+    idx[j] = best.idx == UINT64_MAX ? UINT32_MAX : (uint32_t)best.idx;
+    dist2_out[j] = best.d2;
+  }
+  return ORC_OK;
+}
+
+// Sec. V-D clustering: k-means (Lloyd's iteration) of the stored voxels with
+// eight centres, first placed at the corners of the frame's bounding box
+// (corner c takes the maximum of axis a when bit a of c is set, else the
+// minimum).  Centres are kept in 1/256 voxel units.  Each pass assigns every
+// voxel to the centre of least squared distance (ties: the lower cluster);
+// when a pass changes no label the iteration has converged and stops, else
+// each non-empty cluster's centre becomes its members' mean, rounded half up
+// to 1/256 (an empty cluster keeps its centre).  At most max_iter passes.
+int orc_kmeans(const orc_cga* a, uint32_t max_iter, uint8_t* label, int64_t* centres,
+               uint64_t* counts, uint32_t* iters) {
+  if (max_iter == 0) return ORC_ERR_INVALID_ARG;
+  const uint64_t u = a->u;
+  std::vector<uint32_t> v(3 * u);
+  if (orc_decode(a, v.data()) != ORC_OK) return ORC_ERR_INVALID_ARG;
+  for (int i = 0; i < 24; ++i) centres[i] = 0;
+  for (int c = 0; c < 8; ++c) counts[c] = 0;
+  *iters = 0;
+  if (u == 0) return ORC_OK;
+  uint32_t lo[3] = {UINT32_MAX, UINT32_MAX, UINT32_MAX}, hi[3] = {0, 0, 0};
+  for (uint64_t i = 0; i < u; ++i) {
+    for (int ax = 0; ax < 3; ++ax) {
+      lo[ax] = std::min(lo[ax], v[3 * i + ax]);
+      hi[ax] = std::max(hi[ax], v[3 * i + ax]);
+    }
+  }
+  for (int c = 0; c < 8; ++c) {
+    for (int ax = 0; ax < 3; ++ax) centres[3 * c + ax] = 256 * (int64_t)(((c >> ax) & 1) ? hi[ax] : lo[ax]);
+  }
+  std::vector<uint8_t> prev(u, 0);
+  uint32_t t = 0;
+  while (t < max_iter) {
+    ++t;
+    bool changed = false;
+    for (uint64_t i = 0; i < u; ++i) {
+      uint64_t best = UINT64_MAX;
+      uint8_t bl = 0;
+      for (int c = 0; c < 8; ++c) {
+        uint64_t d = 0;
+        for (int ax = 0; ax < 3; ++ax) {
+          const int64_t diff = 256 * (int64_t)v[3 * i + ax] - centres[3 * c + ax];
+          d += (uint64_t)(diff * diff);
+        }
+        if (d < best) {
+          best = d;
+          bl = (uint8_t)c;
+        }
+      }
+      if (t > 1 && bl != prev[i]) changed = true;
+      label[i] = bl;
+    }
+    if (t > 1 && !changed) break;
+    uint64_t S[8][3] = {}, N[8] = {};
+    for (uint64_t i = 0; i < u; ++i) {
+      ++N[label[i]];
+      for (int ax = 0; ax < 3; ++ax) S[label[i]][ax] += v[3 * i + ax];
+      prev[i] = label[i];
+    }
+    for (int c = 0; c < 8; ++c) {
+      if (N[c] == 0) continue;
+      for (int ax = 0; ax < 3; ++ax) centres[3 * c + ax] = (int64_t)((256 * S[c][ax] + N[c] / 2) / N[c]);
+    }
+  }
+  for (uint64_t i = 0; i < u; ++i) ++counts[label[i]];
+  *iters = t;
+  return ORC_OK;
+}
+
+// Sec. V-D cluster motion: the change of each cluster's centroid between the
+// predicted and the reference frame, mv[c] = ref[c] - pred[c] (1/256 voxel),
+// zero where either cluster is empty.
+int orc_motion_vectors(const int64_t* ref_centres, const uint64_t* ref_counts,
+                       const int64_t* pred_centres, const uint64_t* pred_counts, int64_t* mv) {
+  for (int c = 0; c < 8; ++c) {
+    for (int ax = 0; ax < 3; ++ax) {
+      mv[3 * c + ax] = (ref_counts[c] > 0 && pred_counts[c] > 0)
+                           ? ref_centres[3 * c + ax] - pred_centres[3 * c + ax]
+                           : 0;
+    }
+  }
+  return ORC_OK;
+}
+
+// Sec. V-D reconstructed frame: every voxel of the predicted frame moved by
+// its cluster's motion vector rounded half up to whole voxels,
+// r = v + floor((mv + 128) / 256) per axis (not clamped to the grid).
+int orc_reconstruct(const orc_cga* a, const uint8_t* label, const int64_t* mv, int32_t* out) {
+  std::vector<uint32_t> v(3 * a->u);
+  if (orc_decode(a, v.data()) != ORC_OK) return ORC_ERR_INVALID_ARG;
+  for (uint64_t i = 0; i < a->u; ++i) {
+    if (label[i] > 7) return ORC_ERR_INVALID_ARG;
+    for (int ax = 0; ax < 3; ++ax) {
+      const int64_t m = mv[3 * label[i] + ax];
+      const int64_t num = m + 128;
+      const int64_t fl = num >= 0 ? num / 256 : -((-num + 255) / 256);
+      out[3 * i + ax] = (int32_t)((int64_t)v[3 * i + ax] + fl);
     }
   }
   return ORC_OK;

@@ -9,10 +9,13 @@
  *
  * Every function states the passage of the paper it follows ("Compressed
  * Geometric Arrays for Point Cloud Processing", Roodaki & Nazm Bojnordi):
- *   Sec. III (CGA arrays and their recurrences), Sec. III-A (point lookup and
- *   merge), Sec. III-B (projection), Sec. III-C (NN search), Eq. 1 (merge as a
+ *   Sec. V (CGA arrays and their recurrences), Sec. V-A (point lookup and
+ *   merge), Sec. V-B (projection), Sec. V-C (NN search), Eq. 1 (merge as a
  *   set union), Eq. 3 (orthogonal projection), Eq. 7-8 (Euclidean distance and
- *   the NN set), Sec. II-E-2-a (bounding box including all points).
+ *   the NN set), Sec. II-E-2-a (bounding box including all points), Sec. V-D
+ *   (clustering with corner-seeded k-means, cluster motion vectors and the
+ *   reconstructed frame matched to the reference by NN), and the G-Arrays
+ *   form of X_pointer that Sec. V contrasts with the CGA.
  *
  * Parity pinned: every function here is pinned by the not-gpu tests against
  * hand-written fixtures, closed forms, invariants and independent library
@@ -63,7 +66,7 @@ int orc_grid_from_box(const float lo[3], float extent, uint32_t bits,
 int orc_quantize(const float* xyz, uint64_t n, uint32_t bits, float scale,
                  const float offset[3], const float* xform12, uint64_t* keys);
 
-/* CGA arrays from a sorted, duplicate-free key list (Sec. III recurrences).
+/* CGA arrays from a sorted, duplicate-free key list (Sec. V recurrences).
  * Output buffers must hold u entries (X_pointer/Y_pointer u+1). */
 int orc_from_sorted_keys(const uint64_t* keys, uint64_t u, uint32_t bits,
                          orc_cga* out);
@@ -78,13 +81,13 @@ int orc_decode(const orc_cga* a, uint32_t* xyz);
 /* Decode to keys in CGA order (u entries). */
 int orc_decode_keys(const orc_cga* a, uint64_t* keys);
 
-/* Point lookup (Sec. III-A): index in CGA point order, or -1. */
+/* Point lookup (Sec. V-A): index in CGA point order, or -1. */
 int64_t orc_lookup(const orc_cga* a, uint32_t x, uint32_t y, uint32_t z);
 
-/* Merge (Eq. 1, Sec. III-A).  out buffers hold a->u + b->u (+1). */
+/* Merge (Eq. 1, Sec. V-A).  out buffers hold a->u + b->u (+1). */
 int orc_merge(const orc_cga* a, const orc_cga* b, orc_cga* out);
 
-/* Orthogonal projection (Eq. 3 with m = 1, Sec. III-B) onto plane
+/* Orthogonal projection (Eq. 3 with m = 1, Sec. V-B) onto plane
  * 0 = xy, 1 = xz, 2 = yz.  out buffers hold a->u (+1). */
 int orc_project(const orc_cga* a, int plane, orc_cga2d* out);
 
@@ -102,16 +105,16 @@ int orc_nn_brute(const orc_cga* a, float scale, const float offset[3],
 int orc_query_voxels(const float* q, uint64_t m, float scale, const float offset[3],
                      int64_t* out, uint8_t* valid);
 
-/* Exact NN by the CGA procedure of Sec. III-C: exact-match lookup, else the
+/* Exact NN by the CGA procedure of Sec. V-C: exact-match lookup, else the
  * nearest x -> nearest y -> nearest z bound, then every voxel inside the
  * per-axis window of that bound.  Same outputs as orc_nn_brute. */
 int orc_nn_window(const orc_cga* a, float scale, const float offset[3],
                   const float* q, uint64_t m, uint32_t* idx, uint64_t* dist2);
 
-/* ---- Value (attribute) array, Sec. III ------------------------------------
+/* ---- Value (attribute) array, Sec. V ------------------------------------
  * Every stored voxel carries `channels` (1..4) uint8 attributes, in CGA point
  * order (values[p * channels + c] belongs to Z_index[p]). */
-#define ORC_VALUE_AVERAGE 0 /* Sec. V (pcdownsample): the points of one voxel are averaged */
+#define ORC_VALUE_AVERAGE 0 /* Sec. III-B (pcdownsample): the points of one voxel are averaged */
 #define ORC_VALUE_FIRST 1   /* the voxel keeps the attributes of its first input point */
 #define ORC_MERGE_BASE 0    /* Sec. II-A: an overlapping voxel keeps the base cloud's (a's) */
 #define ORC_MERGE_AVERAGE 1 /* Sec. II-A: or the average of the two */
@@ -159,6 +162,36 @@ int orc_radius_fill(const orc_cga* a, float scale, const float offset[3], const 
                     uint64_t* dist2);
 int orc_knn(const orc_cga* a, float scale, const float offset[3], const float* q, uint64_t m,
             uint32_t k, uint32_t* idx, uint64_t* dist2);
+
+/* ---- Compression pieces (Sec. V-D) and the G-Arrays form (Sec. V) -------
+ * Integer query voxels qv (m * 3 int32, any value).
+ * lookup_voxels: CGA index of each voxel, UINT32_MAX when absent.
+ * garrays_x: the G-Arrays X_pointer, one cell per x value of the whole axis
+ * (2^bits + 1 entries): xptr[v] = number of (x, y) columns with x < v.
+ * garrays_lookup: the lookup through that pointer array (same answer).
+ * nn_voxels: exact NN (Eq. 7-8) of integer voxels clamped to +-2^30. */
+int orc_lookup_voxels(const orc_cga* a, const int32_t* qv, uint64_t m, uint32_t* idx);
+int orc_garrays_x(const orc_cga* a, uint32_t* xptr);
+int orc_garrays_lookup(const orc_cga* a, const uint32_t* xptr, const int32_t* qv, uint64_t m,
+                       uint32_t* idx);
+int orc_nn_voxels(const orc_cga* a, const int32_t* qv, uint64_t m, uint32_t* idx,
+                  uint64_t* dist2);
+
+/* k-means of the stored voxels (Sec. V-D clustering): 8 centres seeded at
+ * the bounding box's corners (corner c: max of axis a where bit a of c is
+ * set), centres in 1/256 voxel (int64, 8 * 3), squared distances to them in
+ * those units, ties to the lower cluster; stop after the first pass that
+ * changes no label, or after max_iter (>= 1) passes; an update sets each
+ * non-empty cluster's centre to (256 * sum + n / 2) / n per axis.
+ * label: u entries; counts: 8; iters: passes done (0 for an empty CGA, whose
+ * centres and counts are 0). */
+int orc_kmeans(const orc_cga* a, uint32_t max_iter, uint8_t* label, int64_t* centres,
+               uint64_t* counts, uint32_t* iters);
+/* mv[c] = ref[c] - pred[c] per axis (1/256 voxel), 0 where either is empty. */
+int orc_motion_vectors(const int64_t* ref_centres, const uint64_t* ref_counts,
+                       const int64_t* pred_centres, const uint64_t* pred_counts, int64_t* mv);
+/* out[3i + a] = voxel_a + floor((mv[label][a] + 128) / 256), u * 3 int32. */
+int orc_reconstruct(const orc_cga* a, const uint8_t* label, const int64_t* mv, int32_t* out);
 
 #ifdef __cplusplus
 }

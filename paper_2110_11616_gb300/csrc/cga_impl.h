@@ -170,7 +170,7 @@ cudaError_t run_merge(const MergePair* h_pairs, int S, uint32_t total_spl, uint3
 cudaError_t run_merge_device(int S, uint32_t total_spl, uint32_t total_tiles,
                              const MergeScratch& sc, cudaStream_t stream);
 
-// ---- Value array (Sec. III) -----------------------------------------------
+// ---- Value array (Sec. V) -----------------------------------------------
 constexpr int kValueAverage = 0;  // a voxel's row: round-half-up mean of its points
 constexpr int kValueFirst = 1;    // a voxel's row: its first input point's
 constexpr int kMergeBase = 0;     // a voxel in both merge inputs keeps the base's row

@@ -217,7 +217,7 @@ __device__ __forceinline__ unsigned long long key_at(const Levels& a, uint32_t g
          ((unsigned long long)__ldg(a.idx1 + c) << b) | (unsigned long long)__ldg(a.idx0 + p);
 }
 
-// Number of stored keys smaller than `key`: the Sec. III-A lookup (x in
+// Number of stored keys smaller than `key`: the Sec. V-A lookup (x in
 // X_index, then y in its Y range, then z in its column) in lower-bound form.
 __device__ __forceinline__ uint32_t rank_of(const Levels& a, uint32_t h, unsigned long long key) {
   const uint32_t b = a.bits, m = (1u << b) - 1u;

@@ -1,4 +1,4 @@
-// CGA compaction of one tile of sorted keys (Sec. III arrays).
+// CGA compaction of one tile of sorted keys (Sec. V arrays).
 //
 // Each key opens a new voxel when it differs from its predecessor, a new level-1
 // group (an (x, y) column, or a U value of a projection) when key >> b differs,
@@ -8,7 +8,7 @@
 // coordinate and, for a group head, the pointer to its first child:
 //   Y_pointer[column] = index of the column's first voxel,
 //   X_pointer[slab]   = index of the slab's first column,
-// which is the recurrence of Sec. III written as an exclusive prefix count.
+// which is the recurrence of Sec. V written as an exclusive prefix count.
 // The last tile writes the sentinels Y_pointer[g] = u, X_pointer[h] = g and
 // the level sizes.
 #pragma once

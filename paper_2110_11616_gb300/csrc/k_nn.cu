@@ -1,4 +1,4 @@
-// Exact nearest-neighbour search on a CGA (Eq. 7-8, Sec. III-C).
+// Exact nearest-neighbour search on a CGA (Eq. 7-8, Sec. V-C).
 //
 // The search is the paper's window search, with the bound shrinking as
 // closer voxels are found.  It visits x slabs outward from the query's x, and

@@ -10,7 +10,7 @@ namespace {
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // ------------------------------------------------------------------ decode
-// Lossless inverse of the build: the walk X -> Y -> Z of Sec. III-A, done per
+// Lossless inverse of the build: the walk X -> Y -> Z of Sec. V-A, done per
 // tile of Z positions (the tile's window is expanded into per-position column
 // and slab indices in shared memory).
 __global__ void __launch_bounds__(kThreads) k_decode(Levels a, uint32_t* __restrict__ xyz) {
@@ -90,7 +90,7 @@ __global__ void k_merge_init(const MergePair* __restrict__ pairs, int S, uint32_
 // half, #B keys < s), and its place among all splitters (A's before B's on
 // equal keys) is k + #B splitters < s, where B splitter j (the key at
 // (j + 1) * half) is below s exactly when (j + 1) * half < rank_B(s).  B's
-// splitters mirror this with #A keys <= s.  The Sec. III-A lookup gives the
+// splitters mirror this with #A keys <= s.  The Sec. V-A lookup gives the
 // ranks.
 __global__ void k_merge_cuts(const MergePair* __restrict__ pairs, int S, uint32_t total,
                              uint32_t half, uint32_t* bounds) {
@@ -292,7 +292,7 @@ __global__ void k_column_zrange(Levels a, uint32_t* zr) {
 }
 
 // ------------------------------------------------------------ x directory
-// The dense per-x-value table of G-Arrays (Sec. III), here only as a lookup
+// The dense per-x-value table of G-Arrays (Sec. V), here only as a lookup
 // accelerator: xdir[v] = number of stored x values below v.
 __global__ void k_x_directory(Levels a, uint32_t* xdir) {
   const uint32_t h = (uint32_t)a.hdr->cnt[2];

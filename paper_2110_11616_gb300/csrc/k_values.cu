@@ -1,9 +1,9 @@
-// The Value (attribute) array of a CGA (Sec. III): one row of uint8 channels
+// The Value (attribute) array of a CGA (Sec. V): one row of uint8 channels
 // per stored voxel, in CGA point order.
-//   k_value_accumulate  each input point finds its voxel by the Sec. III-A
+//   k_value_accumulate  each input point finds its voxel by the Sec. V-A
 //                       lookup and adds its attributes (or offers its index)
 //   k_value_finalize    per voxel: round-half-up mean (sum + k/2) / k of its
-//                       k points (Sec. V: the colours of the points merged
+//                       k points (Sec. III-B: the colours of the points merged
 //                       into one box are averaged), or the first point's row
 //   k_merge_values      per voxel of a merge: the row of the input holding
 //                       it; in both, the base's (a's) row or the average
@@ -70,7 +70,7 @@ __global__ void k_value_finalize(Levels a, ValueInput in, const void* scratch, u
 
 // One tile of the merged CGA's positions: the window is expanded into
 // column and slab indices in shared memory, each voxel's key is looked up in
-// both inputs (Sec. III-A) and its row follows the merge policy.
+// both inputs (Sec. V-A) and its row follows the merge policy.
 __global__ void __launch_bounds__(kThreads) k_merge_values(Levels m, Levels a, Levels b,
                                                            const uint8_t* __restrict__ va,
                                                            const uint8_t* __restrict__ vb,

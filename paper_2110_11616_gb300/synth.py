@@ -1,7 +1,7 @@
 """Seeded synthetic point clouds, rigid transforms and query sets.
 
 These generators stand in for the paper's datasets (the 8i surface light-field
-sequences and the Paris-Lille-3D / GT_Madame LiDAR scans, Sec. V-B), which are
+sequences and the Paris-Lille-3D / GT_Madame LiDAR scans, Sec. VI-B), which are
 not used: every input is produced here from a fixed seed.  The module holds no
 part of the CGA method itself (no quantization, encoding, sorting or search):
 it only draws float32 coordinates and float32 rigid transforms, and both the

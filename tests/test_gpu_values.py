@@ -1,4 +1,4 @@
-"""GPU parity of the Value array (Sec. III): per-voxel attribute rows of
+"""GPU parity of the Value array (Sec. V): per-voxel attribute rows of
 builds (average or first point) and merges (base or average) equal the CPU
 oracle's byte for byte, together with the geometry."""
 import numpy as np

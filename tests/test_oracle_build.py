@@ -1,8 +1,8 @@
 """Pins for the oracle's build (a1-a3) and decode (a4).
 
 Expected values: the hand-derived fixtures of tests/golden/cga_fixtures.txt
-(Sec. III recurrences worked by hand), the closed form of a full lattice,
-the structural invariants of the Sec. III arrays, and numpy's own
+(Sec. V recurrences worked by hand), the closed form of a full lattice,
+the structural invariants of the Sec. V arrays, and numpy's own
 sort/unique routines (independent of the oracle's std::sort/std::unique).
 """
 import numpy as np
@@ -28,7 +28,7 @@ def test_fixture_arrays(orc, name):
 
 
 def check_invariants(a, n=None):
-    """Structural facts of the Sec. III arrays."""
+    """Structural facts of the Sec. V arrays."""
     h, g, u = a.h, a.g, a.u
     assert h <= g <= u and (n is None or u <= n)
     assert len(a.X_pointer) == h + 1 and len(a.Y_pointer) == g + 1

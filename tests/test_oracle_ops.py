@@ -5,7 +5,7 @@ and the algebra of a union (idempotent, identity, commutative, associative).
 Projection: Eq. 3 with m = 1 -- checked against numpy.unique of the 2D voxels,
 the hand fixtures, the xy identity with the CGA's own top two levels, and the
 closed form of a lattice.  NN: Eq. 7-8 -- the exhaustive oracle against a
-vectorised numpy search, the Sec. III-C window oracle against the exhaustive
+vectorised numpy search, the Sec. V-C window oracle against the exhaustive
 one, hand-built ties, a stored voxel, and the closed form of a full lattice.
 """
 import numpy as np

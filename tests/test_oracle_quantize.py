@@ -1,7 +1,7 @@
 """Pins for the oracle's grid and quantize/encode step (a1).
 
 The paper gives no quantization formula (Sec. II-E-2-a asks for a bounding box
-that holds every point; Sec. V sets QP = bits per axis).  The reading pinned
+that holds every point; Sec. VI-C sets QP = bits per axis).  The reading pinned
 here: q = floorf(fmaf(p, scale, offset)) clamped to [0, 2^b - 1], key =
 x << 2b | y << b | z, with the rigid transform evaluated as a fixed fmaf chain.
 Expected values come from exact rational arithmetic (tests/exact_f32.py) or

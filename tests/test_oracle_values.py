@@ -1,4 +1,4 @@
-"""Pins of the oracle's Value array (Sec. III) for builds and merges.
+"""Pins of the oracle's Value array (Sec. V) for builds and merges.
 
 Expected values: the hand-derived fixtures of tests/golden/value_fixtures.txt,
 closed forms (identical attributes average to themselves; the average of a
