@@ -283,6 +283,60 @@ int cga_radius_fill(const cga_t* a, const float* d_q, uint64_t m, uint64_t r2,
 int cga_knn(const cga_t* a, const float* d_q, uint64_t m, uint32_t k, uint32_t* d_idx,
             uint64_t* d_dist2, void* stream);
 
+/* ---- Compression pieces (Sec. V-D) and the G-Arrays X pointer (Sec. V) -------
+ * Sec. V-D predicts a frame from a reference frame: both are clustered,
+ * each cluster's centroid motion is a motion vector, the predicted frame's
+ * points are moved by their cluster's vector, and each moved point is matched
+ * to its corresponding point of the reference by a search of the reference's
+ * CGA.  Here the clustering runs on a CGA's stored voxels (integers), with
+ * results independent of the visiting order:
+ *
+ * cga_kmeans: k-means (Lloyd passes) with the eight centres first placed at
+ * the corners of the voxels' bounding box (corner c: the greatest coordinate
+ * of axis a where bit a of c is set, else the least).  Centres are int64 in
+ * 1/256 voxel; a pass labels every voxel with the centre of least squared
+ * distance (ties: the lower cluster) and stops the run if it changed no label
+ * (after the first pass); otherwise each non-empty cluster's centre becomes
+ * (256 * sum + n / 2) / n per axis (empty clusters keep theirs).  At most
+ * max_iter (1..CGA_KMEANS_MAX_ITER) passes.  Outputs (device): d_label[u]
+ * (0..7, CGA order), d_centres[8 * 3], d_counts[8] (voxels per cluster in the
+ * last pass), *d_iters (passes done; 0 for an empty CGA, whose centres and
+ * counts are 0).  Stream-ordered, no host synchronization.
+ *
+ * cga_motion_vectors: d_mv[c * 3 + a] = ref - pred centre (1/256 voxel) for
+ * every cluster non-empty in both frames, else 0 (8 * 3 int64, device).
+ *
+ * cga_reconstruct: the predicted frame moved by its clusters' vectors:
+ * d_out[3 i + a] = voxel_a(i) + floor((mv[label(i)][a] + 128) / 256), int32,
+ * u * 3 (not clamped to the grid).  Labels must be 0..7.
+ *
+ * cga_nn_query_voxels: cga_nn_query for integer query voxels (d_qv: m * 3
+ * int32, each clamped to +-2^30), e.g. the reconstructed frame against the
+ * reference's CGA: the corresponding point of each reconstructed voxel.
+ *
+ * cga_lookup: the Sec. V-A point lookup of integer voxels: d_idx[j] = CGA
+ * index of voxel j, or UINT32_MAX when it is not stored (or off the grid).
+ *
+ * cga_garrays_x: the X pointer in the G-Arrays form (one cell per x value
+ * of the whole axis, which Sec. V contrasts with the CGA's compact X_index +
+ * X_pointer): d_xptr[v] = number of (x, y) columns with x < v, for v in
+ * [0, 2^bits] (2^bits + 1 uint32, device).  cga_garrays_lookup answers
+ * cga_lookup through it (x indexes the pointer array directly). */
+#define CGA_KMEANS_MAX_ITER 1024
+int cga_kmeans(const cga_t* a, uint32_t max_iter, uint8_t* d_label, int64_t* d_centres,
+               uint64_t* d_counts, uint32_t* d_iters, void* stream);
+int cga_motion_vectors(const int64_t* d_ref_centres, const uint64_t* d_ref_counts,
+                       const int64_t* d_pred_centres, const uint64_t* d_pred_counts,
+                       int64_t* d_mv, void* stream);
+int cga_reconstruct(const cga_t* pred, const uint8_t* d_label, const int64_t* d_mv,
+                    int32_t* d_out, void* stream);
+int cga_nn_query_voxels(const cga_t* a, const int32_t* d_qv, uint64_t m, uint32_t* d_idx,
+                        uint64_t* d_dist2, void* stream);
+int cga_lookup(const cga_t* a, const int32_t* d_qv, uint64_t m, uint32_t* d_idx, void* stream);
+int cga_garrays_x(const cga_t* a, uint32_t* d_xptr, void* stream);
+int cga_garrays_lookup(const cga_t* a, const uint32_t* d_xptr, const int32_t* d_qv, uint64_t m,
+                       uint32_t* d_idx, void* stream);
+
 /* ---- Perspective projection (Eq. 5-6) ---------------------------------------
  * Each stored voxel (x, y, z) is taken to the eye's frame, s = (x - eye[0],
  * y - eye[1], z - eye[2]) (float, voxel units), rotated about the y axis by

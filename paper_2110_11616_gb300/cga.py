@@ -42,6 +42,8 @@ EXPORTS = (
     "cga_tuning_set", "cga_tuning_get", "cga_autotune", "cga_pipeline_autotune",
     "cga_build_values", "cga_merge_values", "cga_values", "cga_perspective",
     "cga_radius_count", "cga_radius_fill", "cga_knn",
+    "cga_kmeans", "cga_motion_vectors", "cga_reconstruct", "cga_nn_query_voxels", "cga_lookup",
+    "cga_garrays_x", "cga_garrays_lookup",
     "cga_selftest_wait_timeout",
 )
 
@@ -929,3 +931,116 @@ def selftest_wait_timeout(stream=None) -> int:
     _check(lib.cga_selftest_wait_timeout(_stream(stream), ctypes.byref(obs)),
            "cga_selftest_wait_timeout")
     return obs.value
+
+
+# ------------------------------------------- compression pieces and G-Arrays
+KMEANS_MAX_ITER = 1024
+
+
+def _dev_i32xyz(t, what):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32
+            and t.is_contiguous() and t.numel() % 3 == 0):
+        raise TypeError(f"{what}: expected a contiguous (m, 3) int32 CUDA tensor")
+    return t
+
+
+def cga_kmeans(a: Cga, max_iter: int = 64, stream=None):
+    """k-means of a's voxels with 8 corner-seeded centres (Sec. V-D): (labels (u,)
+    uint8, centres (8, 3) int64 in 1/256 voxel, counts (8,) int64, passes (1,) int32),
+    all device tensors; nothing is synchronized."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_kmeans.argtypes = [P, ctypes.c_uint32, P, P, P, P, P]
+    u = a.info()["u"]
+    lab = torch.empty(max(u, 1), dtype=torch.uint8, device="cuda")
+    cen = torch.empty((8, 3), dtype=torch.int64, device="cuda")
+    cnt = torch.empty(8, dtype=torch.int64, device="cuda")
+    it = torch.empty(1, dtype=torch.int32, device="cuda")
+    _check(lib.cga_kmeans(a.ptr, int(max_iter), P(lab.data_ptr()), P(cen.data_ptr()),
+                          P(cnt.data_ptr()), P(it.data_ptr()), _stream(stream)), "cga_kmeans")
+    return lab[:u], cen, cnt, it
+
+
+def cga_motion_vectors(ref_centres, ref_counts, pred_centres, pred_counts, stream=None):
+    """mv = ref - pred centre per cluster non-empty in both frames: (8, 3) int64."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_motion_vectors.argtypes = [P, P, P, P, P, P]
+    for t in (ref_centres, ref_counts, pred_centres, pred_counts):
+        if not (t.is_cuda and t.dtype == torch.int64 and t.is_contiguous()):
+            raise TypeError("cga_motion_vectors: expected contiguous int64 CUDA tensors")
+    mv = torch.empty((8, 3), dtype=torch.int64, device="cuda")
+    _check(lib.cga_motion_vectors(P(ref_centres.data_ptr()), P(ref_counts.data_ptr()),
+                                  P(pred_centres.data_ptr()), P(pred_counts.data_ptr()),
+                                  P(mv.data_ptr()), _stream(stream)), "cga_motion_vectors")
+    return mv
+
+
+def cga_reconstruct(pred: Cga, labels, mv, stream=None):
+    """pred's voxels moved by their cluster's vector rounded half up: (u, 3) int32."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_reconstruct.argtypes = [P, P, P, P, P]
+    u = pred.info()["u"]
+    out = torch.empty((max(u, 1), 3), dtype=torch.int32, device="cuda")
+    _check(lib.cga_reconstruct(pred.ptr, P(labels.data_ptr()), P(mv.data_ptr()),
+                               P(out.data_ptr()), _stream(stream)), "cga_reconstruct")
+    return out[:u]
+
+
+def cga_nn_query_voxels(a: Cga, qv, stream=None):
+    """Exact NN of integer query voxels: (idx (m,) int32 holding uint32, dist2 (m,) int64)."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_nn_query_voxels.argtypes = [P, P, ctypes.c_uint64, P, P, P]
+    _dev_i32xyz(qv, "cga_nn_query_voxels")
+    m = qv.numel() // 3
+    idx = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+    d2 = torch.empty(max(m, 1), dtype=torch.int64, device="cuda")
+    _check(lib.cga_nn_query_voxels(a.ptr, P(qv.data_ptr()), m, P(idx.data_ptr()),
+                                   P(d2.data_ptr()), _stream(stream)), "cga_nn_query_voxels")
+    return idx[:m], d2[:m]
+
+
+def cga_lookup(a: Cga, qv, stream=None):
+    """CGA index of each integer voxel (int32 holding uint32; UINT32_MAX when absent)."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_lookup.argtypes = [P, P, ctypes.c_uint64, P, P]
+    _dev_i32xyz(qv, "cga_lookup")
+    m = qv.numel() // 3
+    idx = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+    _check(lib.cga_lookup(a.ptr, P(qv.data_ptr()), m, P(idx.data_ptr()), _stream(stream)),
+           "cga_lookup")
+    return idx[:m]
+
+
+def cga_garrays_x(a: Cga, stream=None):
+    """The G-Arrays X pointer: 2^bits + 1 cells (int32 holding uint32)."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_garrays_x.argtypes = [P, P, P]
+    out = torch.empty((1 << a.grid.bits) + 1, dtype=torch.int32, device="cuda")
+    _check(lib.cga_garrays_x(a.ptr, P(out.data_ptr()), _stream(stream)), "cga_garrays_x")
+    return out
+
+
+def cga_garrays_lookup(a: Cga, xptr, qv, stream=None):
+    """cga_lookup through the dense G-Arrays X pointer."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_garrays_lookup.argtypes = [P, P, P, ctypes.c_uint64, P, P]
+    _dev_i32xyz(qv, "cga_garrays_lookup")
+    m = qv.numel() // 3
+    idx = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+    _check(lib.cga_garrays_lookup(a.ptr, P(xptr.data_ptr()), P(qv.data_ptr()), m,
+                                  P(idx.data_ptr()), _stream(stream)), "cga_garrays_lookup")
+    return idx[:m]

@@ -638,25 +638,14 @@ int cga_project(const cga_t* a, int plane, const cga_allocator* A, void* stream,
   return CGA_OK;
 }
 
-int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
-                 uint64_t* d_dist2, void* stream) {
-  if (a == nullptr || (m > 0 && (d_q == nullptr || d_idx == nullptr || d_dist2 == nullptr))) {
-    return CGA_ERR_INVALID_ARG;
-  }
-  if (m > libcga::kNnMaxQueries) return CGA_ERR_INVALID_ARG;
-  if (m == 0) return CGA_OK;
+namespace {
+
+// One NN batch of float (d_q) or integer (d_qv) queries.
+int nn_query_any(const cga_t* a, const float* d_q, const int32_t* d_qv, uint64_t m,
+                 uint32_t* d_idx, uint64_t* d_dist2, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  libcga::NnSeg seg{};
-  seg.a = a->lv;
-  seg.scale = a->grid.scale;
-  for (int k = 0; k < 3; ++k) seg.off[k] = a->grid.offset[k];
-  seg.q = d_q;
-  seg.m = (uint32_t)m;
-  seg.idx = d_idx;
-  seg.d2 = reinterpret_cast<unsigned long long*>(d_dist2);
-  seg.tile_base = 0;
-  seg.num_tiles = (uint32_t)((m + libcga::kTile - 1) / libcga::kTile);
-  attach_coarse(a, seg);
+  libcga::NnSeg seg = nn_segment(a, d_q, m, d_idx, d_dist2);
+  seg.qv = d_qv;
   const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
   void* scratch = nullptr;
   if (m >= libcga::kNnSortMin) {
@@ -666,6 +655,95 @@ int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
   const int rc = cuda_rc(libcga::run_nn(&seg, 1, seg.num_tiles, scratch, s));
   if (scratch != nullptr) dfree(A, a->has_alloc, scratch, s);
   return rc;
+}
+
+}  // namespace
+
+int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
+                 uint64_t* d_dist2, void* stream) {
+  if (a == nullptr || (m > 0 && (d_q == nullptr || d_idx == nullptr || d_dist2 == nullptr))) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  if (m > libcga::kNnMaxQueries) return CGA_ERR_INVALID_ARG;
+  if (m == 0) return CGA_OK;
+  return nn_query_any(a, d_q, nullptr, m, d_idx, d_dist2, stream);
+}
+
+int cga_nn_query_voxels(const cga_t* a, const int32_t* d_qv, uint64_t m, uint32_t* d_idx,
+                        uint64_t* d_dist2, void* stream) {
+  if (a == nullptr || (m > 0 && (d_qv == nullptr || d_idx == nullptr || d_dist2 == nullptr))) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  if (m > libcga::kNnMaxQueries) return CGA_ERR_INVALID_ARG;
+  if (m == 0) return CGA_OK;
+  return nn_query_any(a, nullptr, d_qv, m, d_idx, d_dist2, stream);
+}
+
+int cga_kmeans(const cga_t* a, uint32_t max_iter, uint8_t* d_label, int64_t* d_centres,
+               uint64_t* d_counts, uint32_t* d_iters, void* stream) {
+  if (a == nullptr || d_centres == nullptr || d_counts == nullptr || d_iters == nullptr ||
+      (a->lv.cap > 0 && d_label == nullptr) || max_iter < 1 || max_iter > CGA_KMEANS_MAX_ITER) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  void* st = dalloc(A, sizeof(libcga::KmState), s);
+  if (st == nullptr) return CGA_ERR_OOM;
+  const int rc = cuda_rc(libcga::run_kmeans(
+      a->lv, max_iter, static_cast<libcga::KmState*>(st), d_label,
+      reinterpret_cast<long long*>(d_centres), reinterpret_cast<unsigned long long*>(d_counts),
+      d_iters, s));
+  dfree(A, a->has_alloc, st, s);
+  return rc;
+}
+
+int cga_motion_vectors(const int64_t* d_ref_centres, const uint64_t* d_ref_counts,
+                       const int64_t* d_pred_centres, const uint64_t* d_pred_counts,
+                       int64_t* d_mv, void* stream) {
+  if (d_ref_centres == nullptr || d_ref_counts == nullptr || d_pred_centres == nullptr ||
+      d_pred_counts == nullptr || d_mv == nullptr) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  return cuda_rc(libcga::run_motion(
+      reinterpret_cast<const long long*>(d_ref_centres),
+      reinterpret_cast<const unsigned long long*>(d_ref_counts),
+      reinterpret_cast<const long long*>(d_pred_centres),
+      reinterpret_cast<const unsigned long long*>(d_pred_counts),
+      reinterpret_cast<long long*>(d_mv), static_cast<cudaStream_t>(stream)));
+}
+
+int cga_reconstruct(const cga_t* pred, const uint8_t* d_label, const int64_t* d_mv,
+                    int32_t* d_out, void* stream) {
+  if (pred == nullptr || d_mv == nullptr ||
+      (pred->lv.cap > 0 && (d_label == nullptr || d_out == nullptr))) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  return cuda_rc(libcga::run_reconstruct(pred->lv, d_label,
+                                         reinterpret_cast<const long long*>(d_mv), d_out,
+                                         static_cast<cudaStream_t>(stream)));
+}
+
+int cga_garrays_x(const cga_t* a, uint32_t* d_xptr, void* stream) {
+  if (a == nullptr || d_xptr == nullptr) return CGA_ERR_INVALID_ARG;
+  return cuda_rc(libcga::run_garrays_x(a->lv, d_xptr, static_cast<cudaStream_t>(stream)));
+}
+
+int cga_lookup(const cga_t* a, const int32_t* d_qv, uint64_t m, uint32_t* d_idx, void* stream) {
+  if (a == nullptr || (m > 0 && (d_qv == nullptr || d_idx == nullptr)) || m > CGA_MAX_POINTS) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  return cuda_rc(libcga::run_lookup(a->lv, nullptr, d_qv, (uint32_t)m, d_idx,
+                                    static_cast<cudaStream_t>(stream)));
+}
+
+int cga_garrays_lookup(const cga_t* a, const uint32_t* d_xptr, const int32_t* d_qv, uint64_t m,
+                       uint32_t* d_idx, void* stream) {
+  if (a == nullptr || d_xptr == nullptr || (m > 0 && (d_qv == nullptr || d_idx == nullptr)) ||
+      m > CGA_MAX_POINTS) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  return cuda_rc(libcga::run_lookup(a->lv, d_xptr, d_qv, (uint32_t)m, d_idx,
+                                    static_cast<cudaStream_t>(stream)));
 }
 
 namespace {

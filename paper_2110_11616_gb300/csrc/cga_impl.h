@@ -234,6 +234,31 @@ struct Camera {
 cudaError_t run_perspective(const Levels& a, const Camera& cam, unsigned long long* zbuf,
                             uint32_t* index, float* depth, cudaStream_t stream);
 
+// ---- Compression pieces (Sec. V-D) and the G-Arrays X pointer ----------------
+constexpr uint32_t kKmClusters = 8;  // one centre per corner of the bounding box
+// Device state of one k-means run.
+struct KmState {
+  unsigned long long sum[kKmClusters][4];  // x, y, z sums and count of a pass
+  unsigned long long changed;              // labels a pass changed
+  uint32_t box[6];                         // least y, z (box[1..2]), greatest (box[4..5])
+  uint32_t pass, done, max_iter;
+};
+// labels: u bytes; centres: 8 * 3 in 1/256 voxel; counts: 8; iters: 1.
+cudaError_t run_kmeans(const Levels& a, uint32_t max_iter, KmState* st, uint8_t* labels,
+                       long long* centres, unsigned long long* counts, uint32_t* iters,
+                       cudaStream_t stream);
+cudaError_t run_motion(const long long* ref_c, const unsigned long long* ref_n,
+                       const long long* pred_c, const unsigned long long* pred_n, long long* mv,
+                       cudaStream_t stream);
+// out: u * 3 int32 voxels.
+cudaError_t run_reconstruct(const Levels& a, const uint8_t* labels, const long long* mv, int* out,
+                            cudaStream_t stream);
+// xptr: 2^bits + 1 entries.
+cudaError_t run_garrays_x(const Levels& a, uint32_t* xptr, cudaStream_t stream);
+// xptr == nullptr: the CGA lookup; else through the dense X pointer.
+cudaError_t run_lookup(const Levels& a, const uint32_t* xptr, const int* qv, uint32_t m,
+                       uint32_t* idx, cudaStream_t stream);
+
 // Copy the top two levels of a CGA into a 2-level projection (plane xy).
 cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stream);
 struct ProjPair {
@@ -274,6 +299,8 @@ struct NnSeg {
   float scale;
   float off[3];
   const float* q;
+  // integer query voxels (m * 3) instead of q when not null
+  const int* qv;
   uint32_t m;
   uint32_t* idx;
   unsigned long long* d2;

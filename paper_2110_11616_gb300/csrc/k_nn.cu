@@ -63,7 +63,21 @@ __global__ void __launch_bounds__(256) k_nn_keys(const NnSeg* __restrict__ segs,
   const int s = find_nn_seg(segs, S, tile);
   const NnSeg& sg = segs[s];
   const uint32_t local = slot - sg.tile_base * (uint32_t)kTile;
-  if (local < sg.m) {
+  if (local < sg.m && sg.qv != nullptr) {
+    // integer query voxels: clamped to the grid for the ordering only
+    const uint32_t bits = sg.a.bits;
+    const int top = (1 << bits) - 1;
+    uint32_t c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const uint32_t u = (uint32_t)min(max(__ldg(sg.qv + 3 * (size_t)local + a), 0), top);
+      c[a] = bits >= 10 ? (u >> (bits - 10)) : (u << (10 - bits));
+    }
+    const uint32_t mort = (spread3(c[0]) << 2) | (spread3(c[1]) << 1) | spread3(c[2]);
+    keys[slot] = ((unsigned long long)mort << 32) | local;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) atomicAdd(&s_hist[k][(mort >> (8 * k)) & (kRadix - 1)], 1u);
+  } else if (local < sg.m) {
     const float* p = sg.q + 3 * (size_t)local;
     const float px = p[0], py = p[1], pz = p[2];
     uint32_t mort = 0x3fffffffu;
@@ -231,6 +245,8 @@ __device__ __forceinline__ unsigned long long interval_dist(long long q, uint32_
 
 // A query in voxel units: unclamped (x, y, z) for distances, clamped
 // (cx, cy, cz) inside the grid for searches.
+constexpr long long kQueryLimit = 1ll << 30;
+
 struct Qry {
   long long x, y, z;
   uint32_t cx, cy, cz;
@@ -519,10 +535,25 @@ __global__ void __launch_bounds__(256, NC > 0 ? 4 : 1) k_nn_warp(const NnSeg* __
     const uint32_t j = sorted ? (uint32_t)order[slot] : local;
     if (j >= sg.m) continue;  // a caller-given order that is not a permutation
     const Levels& a = sg.a;
-    const float* p = sg.q + 3 * (size_t)j;
-    const float px = p[0], py = p[1], pz = p[2];
     const uint32_t u = (uint32_t)a.hdr->cnt[0], h = (uint32_t)a.hdr->cnt[2];
-    if (!(isfinite(px) && isfinite(py) && isfinite(pz)) || u == 0) {
+    long long qx, qy, qz;
+    bool valid;
+    if (sg.qv != nullptr) {
+      // integer query voxels, clamped like quantized ones to +-2^30
+      const int* v = sg.qv + 3 * (size_t)j;
+      qx = min(max((long long)__ldg(v), -kQueryLimit), kQueryLimit);
+      qy = min(max((long long)__ldg(v + 1), -kQueryLimit), kQueryLimit);
+      qz = min(max((long long)__ldg(v + 2), -kQueryLimit), kQueryLimit);
+      valid = true;
+    } else {
+      const float* p = sg.q + 3 * (size_t)j;
+      const float px = p[0], py = p[1], pz = p[2];
+      valid = isfinite(px) && isfinite(py) && isfinite(pz);
+      qx = valid ? quantize_query(px, sg.scale, sg.off[0]) : 0;
+      qy = valid ? quantize_query(py, sg.scale, sg.off[1]) : 0;
+      qz = valid ? quantize_query(pz, sg.scale, sg.off[2]) : 0;
+    }
+    if (!valid || u == 0) {
       if (lane == 0) {
         sg.idx[j] = 0xffffffffu;
         sg.d2[j] = ~0ull;
@@ -531,9 +562,6 @@ __global__ void __launch_bounds__(256, NC > 0 ? 4 : 1) k_nn_warp(const NnSeg* __
     }
     const uint32_t b = a.bits;
     const long long top = (1ll << b) - 1;
-    const long long qx = quantize_query(px, sg.scale, sg.off[0]);
-    const long long qy = quantize_query(py, sg.scale, sg.off[1]);
-    const long long qz = quantize_query(pz, sg.scale, sg.off[2]);
     const uint32_t cqx = (uint32_t)min(max(qx, 0ll), top);
     const uint32_t cqy = (uint32_t)min(max(qy, 0ll), top);
     const uint32_t cqz = (uint32_t)min(max(qz, 0ll), top);
