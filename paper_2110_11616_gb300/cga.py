@@ -945,15 +945,15 @@ def _dev_i32xyz(t, what):
     return t
 
 
-def cga_kmeans(a: Cga, max_iter: int = 64, stream=None):
+def cga_kmeans(a: Cga, max_iter: int = 64, stream=None, u=None):
     """k-means of a's voxels with 8 corner-seeded centres (Sec. V-D): (labels (u,)
     uint8, centres (8, 3) int64 in 1/256 voxel, counts (8,) int64, passes (1,) int32),
-    all device tensors; nothing is synchronized."""
+    all device tensors.  With u (a's voxel count) given nothing is synchronized."""
     torch = _torch()
     lib = load()
     P = ctypes.c_void_p
     lib.cga_kmeans.argtypes = [P, ctypes.c_uint32, P, P, P, P, P]
-    u = a.info()["u"]
+    u = a.info()["u"] if u is None else int(u)
     lab = torch.empty(max(u, 1), dtype=torch.uint8, device="cuda")
     cen = torch.empty((8, 3), dtype=torch.int64, device="cuda")
     cnt = torch.empty(8, dtype=torch.int64, device="cuda")
@@ -979,13 +979,13 @@ def cga_motion_vectors(ref_centres, ref_counts, pred_centres, pred_counts, strea
     return mv
 
 
-def cga_reconstruct(pred: Cga, labels, mv, stream=None):
+def cga_reconstruct(pred: Cga, labels, mv, stream=None, u=None):
     """pred's voxels moved by their cluster's vector rounded half up: (u, 3) int32."""
     torch = _torch()
     lib = load()
     P = ctypes.c_void_p
     lib.cga_reconstruct.argtypes = [P, P, P, P, P]
-    u = pred.info()["u"]
+    u = pred.info()["u"] if u is None else int(u)
     out = torch.empty((max(u, 1), 3), dtype=torch.int32, device="cuda")
     _check(lib.cga_reconstruct(pred.ptr, P(labels.data_ptr()), P(mv.data_ptr()),
                                P(out.data_ptr()), _stream(stream)), "cga_reconstruct")
