@@ -321,9 +321,12 @@ struct RegList {
 // Candidate collection for 32 < k <= CGA_KNN_MAX_K: the warp's buffer of
 // `cap` (a power of two, at least 2k) entries in shared memory.  Candidates
 // are appended unsorted; whenever the next step could overflow it, or when it
-// first holds k, the buffer is sorted by a bitonic network and cut to k, and
-// the k-th distance becomes the bound.  Every voxel pruned by a bound is
-// beaten by k collected ones, so the final sort's first k are the answer.
+// first holds k, the k-th least distance B is found by bisection on the count
+// of entries at most a trial value, every entry beyond B is dropped, and B
+// becomes the bound (if ties at B leave too little room, the buffer is
+// sorted by a bitonic network and cut to exactly k instead).  Every voxel
+// pruned by a bound is beaten by k collected ones, so the final sort's first
+// k are the answer.
 struct SmemList {
   unsigned long long* d;
   uint32_t* ix;
@@ -356,6 +359,44 @@ struct SmemList {
     }
     n = min(n, k);
   }
+  // Keep the entries of distance at most B, the k-th least; returns B.
+  __device__ __forceinline__ unsigned long long select_cut(uint32_t lane) {
+    unsigned long long lo = ~0ull, hi = 0;
+    for (uint32_t e = lane; e < n; e += 32) {
+      lo = min(lo, d[e]);
+      hi = max(hi, d[e]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    while (lo < hi) {
+      const unsigned long long mid = lo + ((hi - lo) >> 1);
+      uint32_t c = 0;
+      for (uint32_t e = lane; e < n; e += 32) c += d[e] <= mid ? 1u : 0u;
+      if (__reduce_add_sync(0xffffffffu, c) >= k) hi = mid; else lo = mid + 1;
+    }
+    uint32_t out = 0;
+    for (uint32_t base = 0; base < n; base += 32) {
+      const uint32_t e = base + lane;
+      const bool keep = e < n && d[e] <= lo;
+      const unsigned long long dv = keep ? d[e] : 0ull;
+      const uint32_t xv = keep ? ix[e] : 0u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+      __syncwarp();
+      if (keep) {
+        const uint32_t p = out + __popc(bal & ((1u << lane) - 1u));
+        d[p] = dv;
+        ix[p] = xv;
+      }
+      out += __popc(bal);
+      __syncwarp();
+    }
+    n = out;
+    if (n + 32 > cap) sort_cut(lane);  // too many ties at B: cut to exactly k
+    return lo;
+  }
   __device__ __forceinline__ void init(uint32_t kk, uint32_t cp, unsigned long long* dd,
                                        uint32_t* xx) {
     d = dd;
@@ -374,10 +415,7 @@ struct SmemList {
     }
     n += __popc(pending);
     __syncwarp();
-    if (n + 32 > cap || (bound == ~0ull && n >= k)) {
-      sort_cut(lane);
-      return n >= k ? d[k - 1] : ~0ull;
-    }
+    if (n + 32 > cap || (bound == ~0ull && n >= k)) return select_cut(lane);
     return bound;
   }
   __device__ __forceinline__ void finish(uint32_t lane, size_t row, uint32_t* out_idx,
