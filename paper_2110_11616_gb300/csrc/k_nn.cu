@@ -37,8 +37,11 @@ __device__ __forceinline__ int find_nn_seg(const NnSeg* __restrict__ segs, int S
   return lo;
 }
 
-__device__ __forceinline__ unsigned long long absdiff(long long a, long long b) {
-  return (unsigned long long)(a > b ? a - b : b - a);
+// |v - q| of a stored coordinate and a query coordinate (clamped to +-2^30,
+// so the difference fits 31 bits; its square is one widening multiply).
+__device__ __forceinline__ uint32_t absdiff(uint32_t v, int q) {
+  const int d = (int)v - q;
+  return (uint32_t)(d < 0 ? -d : d);
 }
 
 __device__ __forceinline__ uint32_t spread3(uint32_t v) {
@@ -106,32 +109,27 @@ __global__ void __launch_bounds__(256) k_nn_keys(const NnSeg* __restrict__ segs,
   }
 }
 
+// The best (distance^2, index) so far.  The CGA index of a voxel rises with
+// its key, so the least index among equal distances is the smallest key
+// (Eq. 8's tie rule).
 struct Best {
-  unsigned long long d2, key;
+  unsigned long long d2;
   uint32_t idx;
-  __device__ __forceinline__ void offer(unsigned long long d, unsigned long long k, uint32_t i) {
-    if (d < d2 || (d == d2 && k < key)) {
+  __device__ __forceinline__ void offer(unsigned long long d, uint32_t i) {
+    if (d < d2 || (d == d2 && i < idx)) {
       d2 = d;
-      key = k;
       idx = i;
     }
   }
-  // Lexicographic minimum of (d2, key) over the warp, by 32-bit warp
-  // reductions of the high then low words; the index comes from a lane that
-  // holds the minimum (equal keys are the same voxel, so the same index).
+  // Lexicographic minimum of (d2, idx) over the warp, by 32-bit warp
+  // reductions of the high then the low distance word, then the index.
   __device__ __forceinline__ void warp_min() {
     const uint32_t full = 0xffffffffu;
     const uint32_t dh = (uint32_t)(d2 >> 32), dl = (uint32_t)d2;
     const uint32_t mh = __reduce_min_sync(full, dh);
     const uint32_t ml = __reduce_min_sync(full, dh == mh ? dl : full);
-    const bool at_min = dh == mh && dl == ml;
-    const uint32_t kh = (uint32_t)(key >> 32), kl = (uint32_t)key;
-    const uint32_t mkh = __reduce_min_sync(full, at_min ? kh : full);
-    const uint32_t mkl = __reduce_min_sync(full, at_min && kh == mkh ? kl : full);
-    const uint32_t holders = __ballot_sync(full, at_min && kh == mkh && kl == mkl);
-    idx = __shfl_sync(full, idx, __ffs(holders) - 1);
+    idx = __reduce_min_sync(full, dh == mh && dl == ml ? idx : full);
     d2 = ((unsigned long long)mh << 32) | ml;
-    key = ((unsigned long long)mkh << 32) | mkl;
   }
 };
 
@@ -139,8 +137,8 @@ struct Best {
 // column's lowest | highest z << 16; when the query lies below or above the
 // whole column, that end is the only neighbour and no search is needed.
 __device__ __forceinline__ void visit_column(const Levels& a, const uint32_t* zr0, uint32_t c,
-                                             unsigned long long kxy, unsigned long long dxy,
-                                             long long qz, uint32_t cqz, Best& b) {
+                                             unsigned long long dxy, int qz, uint32_t cqz,
+                                             Best& b) {
   // the column's voxel range, loaded together with its z range
   const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
   if (zr0 != nullptr) {
@@ -148,12 +146,12 @@ __device__ __forceinline__ void visit_column(const Levels& a, const uint32_t* zr
     const uint32_t zlo = zz & 0xffffu, zhi = zz >> 16;
     if (cqz <= zlo) {
       const unsigned long long dz = absdiff(zlo, qz);
-      b.offer(dxy + dz * dz, kxy | zlo, zs);
+      b.offer(dxy + dz * dz, zs);
       return;
     }
     if (cqz >= zhi) {
       const unsigned long long dz = absdiff(zhi, qz);
-      b.offer(dxy + dz * dz, kxy | zhi, ze - 1);
+      b.offer(dxy + dz * dz, ze - 1);
       return;
     }
   }
@@ -161,22 +159,21 @@ __device__ __forceinline__ void visit_column(const Levels& a, const uint32_t* zr
   if (zr < ze) {
     const uint32_t z = __ldg(a.idx0 + zr);
     const unsigned long long dz = absdiff(z, qz);
-    b.offer(dxy + dz * dz, kxy | z, zr);
+    b.offer(dxy + dz * dz, zr);
   }
   if (zr > zs) {
     const uint32_t z = __ldg(a.idx0 + zr - 1);
     const unsigned long long dz = absdiff(z, qz);
-    b.offer(dxy + dz * dz, kxy | z, zr - 1);
+    b.offer(dxy + dz * dz, zr - 1);
   }
 }
 
 // Window search over the fine CGA alone (one warp, 16 slabs per side per round).
 __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdir,
                                             const uint32_t* zr0, uint32_t h,
-                                            long long qx, long long qy, long long qz,
+                                            int qx, int qy, int qz,
                                             uint32_t cqx, uint32_t cqy, uint32_t cqz,
                                             uint32_t lane, Best& best) {
-  const uint32_t b = a.bits;
   const uint32_t xr0 = xdir != nullptr ? __ldg(xdir + cqx) : lower_bound_u16(a.idx2, 0, h, cqx);
   const bool right = (lane & 1u) == 0u;
   for (uint32_t r = 0;; ++r) {
@@ -195,7 +192,6 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
     }
     const bool active = valid && dx2 <= best.d2;
     if (!__any_sync(0xffffffffu, active)) break;
-    const unsigned long long kx = (unsigned long long)x << (2 * b);
     if (active) {
       yr0 = lower_bound_u16(a.idx1, ys, ye, cqy);
       if (yr0 < ye) {
@@ -203,7 +199,7 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
         const unsigned long long dy = absdiff(y, qy);
         const unsigned long long dxy = dx2 + dy * dy;
         if (dxy <= best.d2) {
-          visit_column(a, zr0, yr0, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+          visit_column(a, zr0, yr0, dxy, qz, cqz, best);
         }
       }
       if (yr0 > ys) {
@@ -211,7 +207,7 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
         const unsigned long long dy = absdiff(y, qy);
         const unsigned long long dxy = dx2 + dy * dy;
         if (dxy <= best.d2) {
-          visit_column(a, zr0, yr0 - 1, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+          visit_column(a, zr0, yr0 - 1, dxy, qz, cqz, best);
         }
       }
     }
@@ -229,8 +225,7 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
         if (dxy > best.d2) break;
         const uint32_t c = (uint32_t)(gR ? R2 : L2);
         if (gR) ++R2; else --L2;
-        const uint32_t y = __ldg(a.idx1 + c);
-        visit_column(a, zr0, c, kx | ((unsigned long long)y << b), dxy, qz, cqz, best);
+        visit_column(a, zr0, c, dxy, qz, cqz, best);
       }
     }
     best.warp_min();
@@ -238,17 +233,17 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
 }
 
 // Distance from q to the voxel interval [lo, lo + s - 1] (0 inside).
-__device__ __forceinline__ unsigned long long interval_dist(long long q, uint32_t lo, uint32_t s) {
-  const long long l = lo, hi = (long long)lo + s - 1;
-  return q < l ? (unsigned long long)(l - q) : (q > hi ? (unsigned long long)(q - hi) : 0ull);
+__device__ __forceinline__ uint32_t interval_dist(int q, uint32_t lo, uint32_t s) {
+  const int l = (int)lo, hi = (int)(lo + s - 1);
+  return q < l ? (uint32_t)(l - q) : (q > hi ? (uint32_t)(q - hi) : 0u);
 }
 
 // A query in voxel units: unclamped (x, y, z) for distances, clamped
 // (cx, cy, cz) inside the grid for searches.
-constexpr long long kQueryLimit = 1ll << 30;
+constexpr int kQueryLimit = 1 << 30;
 
 struct Qry {
-  long long x, y, z;
+  int x, y, z;
   uint32_t cx, cy, cz;
 };
 
@@ -279,14 +274,12 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
     // the fine columns of one cell: few enough that a plain ascending scan
     // with the bound test per slab and per column beats ordering them
     const Levels& a = sg.a;
-    const uint32_t b = a.bits;
     for (uint32_t xi = x0; xi < x1; ++xi) {
       const uint32_t x = __ldg(a.idx2 + xi);
       const unsigned long long dx = absdiff(x, q.x);
       const unsigned long long dx2 = dx * dx;
       if (dx2 > best.d2) continue;
       const uint32_t ys = __ldg(a.ptr2 + xi), ye = __ldg(a.ptr2 + xi + 1);
-      const unsigned long long kx = (unsigned long long)x << (2 * b);
       const uint32_t c0 = starts != nullptr ? __ldg(starts + (xi - x0))
                                             : lower_bound_u16(a.idx1, ys, ye, ylo);
       for (uint32_t c = c0; c < ye; ++c) {
@@ -295,7 +288,7 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
         const unsigned long long dy = absdiff(y, q.y);
         const unsigned long long dxy = dx2 + dy * dy;
         if (dxy > best.d2) continue;
-        visit_column(a, sg.zr0, c, kx | ((unsigned long long)y << b), dxy, q.z, q.cz, best);
+        visit_column(a, sg.zr0, c, dxy, q.z, q.cz, best);
       }
     }
     return;
@@ -350,9 +343,7 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
       const uint32_t c = (uint32_t)(gR ? R : Lc), yv = gR ? yR : yL;
       if (gR) ++R; else --Lc;
       if constexpr (K == 0) {
-        const uint32_t b = L.bits;
-        visit_column(L, sg.zr0, c, ((unsigned long long)xv << (2 * b)) | ((unsigned long long)yv << b),
-                     dxl2 + dyl * dyl, q.z, q.cz, best);
+        visit_column(L, sg.zr0, c, dxl2 + dyl * dyl, q.z, q.cz, best);
       } else {
         visit_cell_column<K>(sg, c, yv, dxl2, dyl * dyl, fx0, fx1, q, best);
       }
@@ -378,8 +369,10 @@ __device__ __forceinline__ unsigned long long cell_z_dist(const NnSeg& sg, uint3
   const uint32_t zs = __ldg(L.ptr1 + c), ze = __ldg(L.ptr1 + c + 1);
   const uint32_t zr = lower_bound_u16(L.idx0, zs, ze, q.cz >> sh);
   unsigned long long dzl = ~0ull;
-  if (zr < ze) dzl = min(dzl, interval_dist(q.z, (uint32_t)__ldg(L.idx0 + zr) << sh, cell));
-  if (zr > zs) dzl = min(dzl, interval_dist(q.z, (uint32_t)__ldg(L.idx0 + zr - 1) << sh, cell));
+  if (zr < ze) dzl = min(dzl, (unsigned long long)interval_dist(q.z, (uint32_t)__ldg(L.idx0 + zr) << sh, cell));
+  if (zr > zs) {
+    dzl = min(dzl, (unsigned long long)interval_dist(q.z, (uint32_t)__ldg(L.idx0 + zr - 1) << sh, cell));
+  }
   return dzl;
 }
 
@@ -536,22 +529,22 @@ __global__ void __launch_bounds__(256, NC > 0 ? 4 : 1) k_nn_warp(const NnSeg* __
     if (j >= sg.m) continue;  // a caller-given order that is not a permutation
     const Levels& a = sg.a;
     const uint32_t u = (uint32_t)a.hdr->cnt[0], h = (uint32_t)a.hdr->cnt[2];
-    long long qx, qy, qz;
+    // query voxel, clamped to +-2^30 (so every coordinate difference fits 31 bits)
+    int qx, qy, qz;
     bool valid;
     if (sg.qv != nullptr) {
-      // integer query voxels, clamped like quantized ones to +-2^30
       const int* v = sg.qv + 3 * (size_t)j;
-      qx = min(max((long long)__ldg(v), -kQueryLimit), kQueryLimit);
-      qy = min(max((long long)__ldg(v + 1), -kQueryLimit), kQueryLimit);
-      qz = min(max((long long)__ldg(v + 2), -kQueryLimit), kQueryLimit);
+      qx = min(max(__ldg(v), -kQueryLimit), kQueryLimit);
+      qy = min(max(__ldg(v + 1), -kQueryLimit), kQueryLimit);
+      qz = min(max(__ldg(v + 2), -kQueryLimit), kQueryLimit);
       valid = true;
     } else {
       const float* p = sg.q + 3 * (size_t)j;
       const float px = p[0], py = p[1], pz = p[2];
       valid = isfinite(px) && isfinite(py) && isfinite(pz);
-      qx = valid ? quantize_query(px, sg.scale, sg.off[0]) : 0;
-      qy = valid ? quantize_query(py, sg.scale, sg.off[1]) : 0;
-      qz = valid ? quantize_query(pz, sg.scale, sg.off[2]) : 0;
+      qx = valid ? (int)quantize_query(px, sg.scale, sg.off[0]) : 0;
+      qy = valid ? (int)quantize_query(py, sg.scale, sg.off[1]) : 0;
+      qz = valid ? (int)quantize_query(pz, sg.scale, sg.off[2]) : 0;
     }
     if (!valid || u == 0) {
       if (lane == 0) {
@@ -561,11 +554,11 @@ __global__ void __launch_bounds__(256, NC > 0 ? 4 : 1) k_nn_warp(const NnSeg* __
       continue;
     }
     const uint32_t b = a.bits;
-    const long long top = (1ll << b) - 1;
-    const uint32_t cqx = (uint32_t)min(max(qx, 0ll), top);
-    const uint32_t cqy = (uint32_t)min(max(qy, 0ll), top);
-    const uint32_t cqz = (uint32_t)min(max(qz, 0ll), top);
-    Best best{~0ull, ~0ull, 0xffffffffu};
+    const int top = (1 << b) - 1;
+    const uint32_t cqx = (uint32_t)min(max(qx, 0), top);
+    const uint32_t cqy = (uint32_t)min(max(qy, 0), top);
+    const uint32_t cqz = (uint32_t)min(max(qz, 0), top);
+    Best best{~0ull, 0xffffffffu};
     if (NC >= 2 && sg.ncoarse >= 2) {
       if constexpr (NC >= 2) search_levels<2>(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane, best);
     } else if (NC >= 1 && sg.ncoarse >= 1) {
