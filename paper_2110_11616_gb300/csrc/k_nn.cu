@@ -177,9 +177,9 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
   const uint32_t xr0 = xdir != nullptr ? __ldg(xdir + cqx) : lower_bound_u16(a.idx2, 0, h, cqx);
   const bool right = (lane & 1u) == 0u;
   for (uint32_t r = 0;; ++r) {
-    const long long k = (long long)r * 16 + (lane >> 1);
-    const long long slab = right ? (long long)xr0 + k : (long long)xr0 - 1 - k;
-    const bool valid = slab >= 0 && slab < (long long)h;
+    const int k = (int)(r * 16u + (lane >> 1));
+    const int slab = right ? (int)xr0 + k : (int)xr0 - 1 - k;
+    const bool valid = slab >= 0 && slab < (int)h;
     unsigned long long dx2 = ~0ull;
     uint32_t x = 0, ys = 0, ye = 0, yr0 = 0;
     if (valid) {
@@ -213,12 +213,12 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
     }
     best.warp_min();
     if (active) {
-      long long R2 = (long long)yr0 + 1, L2 = (long long)yr0 - 2;
+      int R2 = (int)yr0 + 1, L2 = (int)yr0 - 2;
       while (true) {
-        const bool hR = R2 < (long long)ye, hL = L2 >= (long long)ys;
+        const bool hR = R2 < (int)ye, hL = L2 >= (int)ys;
         if (!hR && !hL) break;
-        const unsigned long long eR = hR ? absdiff(__ldg(a.idx1 + R2), qy) : ~0ull;
-        const unsigned long long eL = hL ? absdiff(__ldg(a.idx1 + L2), qy) : ~0ull;
+        const uint32_t eR = hR ? absdiff(__ldg(a.idx1 + R2), qy) : 0xffffffffu;
+        const uint32_t eL = hL ? absdiff(__ldg(a.idx1 + L2), qy) : 0xffffffffu;
         const bool gR = hR && (!hL || eR <= eL);
         const unsigned long long dy = gR ? eR : eL;
         const unsigned long long dxy = dx2 + dy * dy;
@@ -297,14 +297,14 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
   const uint32_t sh = level_shift<K>(sg), cell = 1u << sh;
   const uint32_t qyc = q.cy >> sh;
   const uint32_t split = lower_bound_u16(L.idx2, x0, x1, q.cx >> sh);
-  long long r = split, l = (long long)split - 1;
+  int r = (int)split, l = (int)split - 1;
   while (true) {
-    const bool hr = r < (long long)x1, hl = l >= (long long)x0;
+    const bool hr = r < (int)x1, hl = l >= (int)x0;
     if (!hr && !hl) break;
     const uint32_t vr = hr ? (uint32_t)__ldg(L.idx2 + r) : 0u;
     const uint32_t vl = hl ? (uint32_t)__ldg(L.idx2 + l) : 0u;
-    const unsigned long long er = hr ? interval_dist(q.x, vr << sh, cell) : ~0ull;
-    const unsigned long long el = hl ? interval_dist(q.x, vl << sh, cell) : ~0ull;
+    const uint32_t er = hr ? interval_dist(q.x, vr << sh, cell) : 0xffffffffu;
+    const uint32_t el = hl ? interval_dist(q.x, vl << sh, cell) : 0xffffffffu;
     const bool gr = hr && (!hl || er <= el);
     const unsigned long long dxl = gr ? er : el;
     const unsigned long long dxl2 = dxl * dxl;
@@ -329,14 +329,14 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
       fx0 = __ldg(sg.xs[K - 1] + xi);
       fx1 = __ldg(sg.xs[K - 1] + xi + 1);
     }
-    long long R = cs, Lc = (long long)cs - 1;
+    int R = (int)cs, Lc = (int)cs - 1;
     while (true) {
-      const bool hR = R < (long long)c1, hL = Lc >= (long long)c0;
+      const bool hR = R < (int)c1, hL = Lc >= (int)c0;
       if (!hR && !hL) break;
       const uint32_t yR = hR ? (uint32_t)__ldg(L.idx1 + R) : 0u;
       const uint32_t yL = hL ? (uint32_t)__ldg(L.idx1 + Lc) : 0u;
-      const unsigned long long eR = hR ? interval_dist(q.y, yR << sh, cell) : ~0ull;
-      const unsigned long long eL = hL ? interval_dist(q.y, yL << sh, cell) : ~0ull;
+      const uint32_t eR = hR ? interval_dist(q.y, yR << sh, cell) : 0xffffffffu;
+      const uint32_t eL = hL ? interval_dist(q.y, yL << sh, cell) : 0xffffffffu;
       const bool gR = hR && (!hL || eR <= eL);
       const unsigned long long dyl = gR ? eR : eL;
       if (dxl2 + dyl * dyl > best.d2) break;
@@ -414,10 +414,10 @@ __device__ void search_levels(const NnSeg& sg, const Qry& q, uint32_t lane, Best
     // nearest in y (box lower bound with z from the column's nearest cells);
     // only the column with the least bound in the warp is refined, so the
     // rounds below start from a real candidate instead of an infinite bound.
-    const long long slab = right ? (long long)xr0 + (lane >> 1) : (long long)xr0 - 1 - (lane >> 1);
+    const int slab = right ? (int)xr0 + (int)(lane >> 1) : (int)xr0 - 1 - (int)(lane >> 1);
     unsigned long long lb = ~0ull, sdx2 = 0, sdy2 = 0;
     uint32_t sc = 0, scy = 0, sfx0 = 0, sfx1 = 0;
-    if (slab >= 0 && slab < (long long)hc) {
+    if (slab >= 0 && slab < (int)hc) {
       const unsigned long long dxl = interval_dist(q.x, (uint32_t)__ldg(c.idx2 + slab) << L, s);
       const uint32_t ys = __ldg(c.ptr2 + slab), ye = __ldg(c.ptr2 + slab + 1);
       const uint32_t yr0 = lower_bound_u16(c.idx1, ys, ye, cqy_c);
@@ -457,9 +457,9 @@ __device__ void search_levels(const NnSeg& sg, const Qry& q, uint32_t lane, Best
     best.warp_min();
   }
   for (uint32_t r = 0;; ++r) {
-    const long long k = (long long)r * 16 + (lane >> 1);
-    const long long slab = right ? (long long)xr0 + k : (long long)xr0 - 1 - k;
-    const bool valid = slab >= 0 && slab < (long long)hc;
+    const int k = (int)(r * 16u + (lane >> 1));
+    const int slab = right ? (int)xr0 + k : (int)xr0 - 1 - k;
+    const bool valid = slab >= 0 && slab < (int)hc;
     unsigned long long dxl2 = ~0ull;
     if (valid) {
       const unsigned long long dxl = interval_dist(q.x, (uint32_t)__ldg(c.idx2 + slab) << L, s);
@@ -487,14 +487,14 @@ __device__ void search_levels(const NnSeg& sg, const Qry& q, uint32_t lane, Best
     }
     best.warp_min();
     if (active) {
-      long long R2 = (long long)yr0 + 1, L2 = (long long)yr0 - 2;
+      int R2 = (int)yr0 + 1, L2 = (int)yr0 - 2;
       while (true) {
-        const bool hR = R2 < (long long)ye, hL = L2 >= (long long)ys;
+        const bool hR = R2 < (int)ye, hL = L2 >= (int)ys;
         if (!hR && !hL) break;
-        const unsigned long long eR =
-            hR ? interval_dist(q.y, (uint32_t)__ldg(c.idx1 + R2) << L, s) : ~0ull;
-        const unsigned long long eL =
-            hL ? interval_dist(q.y, (uint32_t)__ldg(c.idx1 + L2) << L, s) : ~0ull;
+        const uint32_t eR =
+            hR ? interval_dist(q.y, (uint32_t)__ldg(c.idx1 + R2) << L, s) : 0xffffffffu;
+        const uint32_t eL =
+            hL ? interval_dist(q.y, (uint32_t)__ldg(c.idx1 + L2) << L, s) : 0xffffffffu;
         const bool gR = hR && (!hL || eR <= eL);
         const unsigned long long dyl = gR ? eR : eL;
         if (dxl2 + dyl * dyl > best.d2) break;

@@ -19,10 +19,6 @@ namespace libcga {
 
 namespace {
 
-__device__ __forceinline__ unsigned long long absdiff_ll(long long a, long long b) {
-  return (unsigned long long)(a > b ? a - b : b - a);
-}
-
 // Largest s with s * s <= v (v < 2^63).  Below 2^46 a single-precision
 // estimate is within 2 of the root (the rounding of v to float moves the
 // root by at most a quarter, sqrtf's own rounding by at most half a unit of
@@ -37,8 +33,33 @@ __device__ __forceinline__ unsigned long long isqrt_u64(unsigned long long v) {
   return s;
 }
 
+// |v - q| of a stored coordinate and a query coordinate (clamped to
+// +-2^30, so the difference fits 31 bits).
+__device__ __forceinline__ uint32_t absdiff32(uint32_t v, int q) {
+  const int d = (int)v - q;
+  return (uint32_t)(d < 0 ? -d : d);
+}
+
+__device__ __forceinline__ unsigned long long sq(uint32_t d) {
+  return (unsigned long long)d * d;
+}
+
+// The grid coordinates [lo, hi] within reach of q on one axis, where rem is
+// the squared distance left for it: [q - isqrt(rem), q + isqrt(rem)] cut to
+// [0, top] (in 64 bits: the reach may exceed 2^31).  False when empty.
+__device__ __forceinline__ bool axis_window(int q, unsigned long long rem, int top, int& lo,
+                                            int& hi) {
+  const long long r = (long long)isqrt_u64(rem);
+  const long long l = (long long)q - r, h = (long long)q + r;
+  if (h < 0 || l > top) return false;
+  lo = (int)max(l, 0ll);
+  hi = (int)min(h, (long long)top);
+  return true;
+}
+
+
 struct RQuery {
-  long long x, y, z;  // query voxel (unclamped)
+  int x, y, z;  // query voxel (clamped only to +-2^30)
   bool valid;
 };
 
@@ -47,9 +68,9 @@ __device__ __forceinline__ RQuery radius_query(const SearchSeg& sg, uint32_t j) 
   const float px = __ldg(p), py = __ldg(p + 1), pz = __ldg(p + 2);
   RQuery q;
   q.valid = isfinite(px) && isfinite(py) && isfinite(pz);
-  q.x = q.valid ? quantize_query(px, sg.scale, sg.off[0]) : 0;
-  q.y = q.valid ? quantize_query(py, sg.scale, sg.off[1]) : 0;
-  q.z = q.valid ? quantize_query(pz, sg.scale, sg.off[2]) : 0;
+  q.x = q.valid ? (int)quantize_query(px, sg.scale, sg.off[0]) : 0;
+  q.y = q.valid ? (int)quantize_query(py, sg.scale, sg.off[1]) : 0;
+  q.z = q.valid ? (int)quantize_query(pz, sg.scale, sg.off[2]) : 0;
   return q;
 }
 
@@ -58,11 +79,10 @@ __device__ __forceinline__ void radius_slabs(const Levels& a, uint32_t h, const 
                                              unsigned long long r2, uint32_t& s0, uint32_t& s1) {
   s0 = s1 = 0;
   if (!q.valid || h == 0) return;
-  const long long r = (long long)isqrt_u64(r2), top = (1ll << a.bits) - 1;
-  const long long lo = q.x - r, hi = q.x + r;
-  if (hi < 0 || lo > top) return;
-  s0 = lower_bound_u16(a.idx2, 0, h, (uint32_t)max(lo, 0ll));
-  s1 = lower_bound_u16(a.idx2, s0, h, (uint32_t)min(hi, top) + 1);
+  int lo, hi;
+  if (!axis_window(q.x, r2, (1 << a.bits) - 1, lo, hi)) return;
+  s0 = lower_bound_u16(a.idx2, 0, h, (uint32_t)lo);
+  s1 = lower_bound_u16(a.idx2, s0, h, (uint32_t)hi + 1);
 }
 
 // Count (EMIT = false) or write in (y, z) order from position `pos` (EMIT =
@@ -72,28 +92,26 @@ __device__ __forceinline__ unsigned long long radius_slab(const Levels& a, uint3
                                                           const RQuery& q, unsigned long long r2,
                                                           uint32_t* idx, unsigned long long* d2,
                                                           unsigned long long pos) {
-  const long long top = (1ll << a.bits) - 1;
+  const int top = (1 << a.bits) - 1;
   const uint32_t x = __ldg(a.idx2 + slab);
-  const unsigned long long dx = absdiff_ll(x, q.x), dx2 = dx * dx;
+  const unsigned long long dx2 = sq(absdiff32(x, q.x));
   if (dx2 > r2) return 0;
-  const long long ry = (long long)isqrt_u64(r2 - dx2);
-  const long long ylo = q.y - ry, yhi = q.y + ry;
-  if (yhi < 0 || ylo > top) return 0;
+  int ylo, yhi;
+  if (!axis_window(q.y, r2 - dx2, top, ylo, yhi)) return 0;
   const uint32_t ys = __ldg(a.ptr2 + slab), ye = __ldg(a.ptr2 + slab + 1);
   unsigned long long n = 0;
-  for (uint32_t c = lower_bound_u16(a.idx1, ys, ye, (uint32_t)max(ylo, 0ll)); c < ye; ++c) {
+  for (uint32_t c = lower_bound_u16(a.idx1, ys, ye, (uint32_t)ylo); c < ye; ++c) {
     const uint32_t y = __ldg(a.idx1 + c);
-    if ((long long)y > yhi) break;
-    const unsigned long long dy = absdiff_ll(y, q.y), dxy = dx2 + dy * dy;
-    const long long rz = (long long)isqrt_u64(r2 - dxy);
-    const long long zlo = q.z - rz, zhi = q.z + rz;
-    if (zhi < 0 || zlo > top) continue;
+    if ((int)y > yhi) break;
+    const unsigned long long dxy = dx2 + sq(absdiff32(y, q.y));
+    int zlo, zhi;
+    if (!axis_window(q.z, r2 - dxy, top, zlo, zhi)) continue;
     const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
-    const uint32_t p0 = lower_bound_u16(a.idx0, zs, ze, (uint32_t)max(zlo, 0ll));
-    const uint32_t p1 = lower_bound_u16(a.idx0, p0, ze, (uint32_t)min(zhi, top) + 1);
+    const uint32_t p0 = lower_bound_u16(a.idx0, zs, ze, (uint32_t)zlo);
+    const uint32_t p1 = lower_bound_u16(a.idx0, p0, ze, (uint32_t)zhi + 1);
     if (EMIT) {
       for (uint32_t p = p0; p < p1; ++p) {
-        const unsigned long long dz = absdiff_ll(__ldg(a.idx0 + p), q.z);
+        const unsigned long long dz = absdiff32(__ldg(a.idx0 + p), q.z);
         idx[pos + n + (p - p0)] = p;
         d2[pos + n + (p - p0)] = dxy + dz * dz;
       }
@@ -429,17 +447,6 @@ struct SmemList {
   }
 };
 
-// |v - q| of a stored coordinate and a query coordinate (clamped to
-// +-2^30, so the difference fits 31 bits).
-__device__ __forceinline__ uint32_t absdiff32(uint32_t v, int q) {
-  const int d = (int)v - q;
-  return (uint32_t)(d < 0 ? -d : d);
-}
-
-__device__ __forceinline__ unsigned long long sq(uint32_t d) {
-  return (unsigned long long)d * d;
-}
-
 // k nearest of one query, one warp: slab rounds as in the NN search (16 per
 // side), every lane walking its slab's columns nearest-first in y and each
 // column's voxels nearest-first in z.  The lanes step in lockstep, each step
@@ -470,7 +477,7 @@ __global__ void __launch_bounds__(LARGE ? kKnnLargeThreads : 256, LARGE ? 1 : 4)
     }
     const RQuery q = radius_query(sg, j);
     if (q.valid && u > 0) {
-      const int qx = (int)q.x, qy = (int)q.y, qz = (int)q.z;
+      const int qx = q.x, qy = q.y, qz = q.z;
       const uint32_t cqy = (uint32_t)min(max(qy, 0), top);
       const uint32_t cqz = (uint32_t)min(max(qz, 0), top);
       const uint32_t xr0 = lower_bound_u16(a.idx2, 0, h, (uint32_t)min(max(qx, 0), top));
