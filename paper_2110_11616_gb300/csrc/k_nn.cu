@@ -242,6 +242,12 @@ __device__ __forceinline__ uint32_t interval_dist(int q, uint32_t lo, uint32_t s
 // (cx, cy, cz) inside the grid for searches.
 constexpr int kQueryLimit = 1 << 30;
 
+// Blocks per SM the fine-only search is compiled for (its register budget;
+// measured on GB300: 6 beats 5 (48 registers, no cap) and 8 (spills)).
+#ifndef CGA_NN_FINE_BLOCKS
+#define CGA_NN_FINE_BLOCKS 6
+#endif
+
 struct Qry {
   int x, y, z;
   uint32_t cx, cy, cz;
@@ -507,12 +513,13 @@ __device__ void search_levels(const NnSeg& sg, const Qry& q, uint32_t lane, Best
   }
 }
 
-// NC: the most coarse levels any segment of the launch carries (0, 1 or 2);
-// the fine-only instantiation keeps fewer registers.  The coarse ones are
-// held to 64 registers (four blocks per SM): the extra warps hide more of the
-// search's load latency than the few spilled values cost.
+// NC: the most coarse levels any segment of the launch carries (0, 1 or 2).
+// The fine-only instantiation is held to 40 registers (six blocks per SM),
+// the coarse ones to 64 (four blocks per SM): the extra warps hide more of
+// the search's load latency than the few spilled values cost (eight blocks,
+// 32 registers, spill enough to be slower).
 template <int NC>
-__global__ void __launch_bounds__(256, NC > 0 ? 4 : 1) k_nn_warp(const NnSeg* __restrict__ segs, int S,
+__global__ void __launch_bounds__(256, NC > 0 ? 4 : CGA_NN_FINE_BLOCKS) k_nn_warp(const NnSeg* __restrict__ segs, int S,
                                                  NnSeg inline_seg, uint32_t total_slots,
                                                  const unsigned long long* __restrict__ order,
                                                  const unsigned int* __restrict__ order_err) {
