@@ -242,10 +242,14 @@ __device__ __forceinline__ uint32_t interval_dist(int q, uint32_t lo, uint32_t s
 // (cx, cy, cz) inside the grid for searches.
 constexpr int kQueryLimit = 1 << 30;
 
-// Blocks per SM the fine-only search is compiled for (its register budget;
-// measured on GB300: 6 beats 5 (48 registers, no cap) and 8 (spills)).
+// Blocks per SM the fine-only and the coarse searches are compiled for (their
+// register budgets; measured on GB300: fine 6 beats 5 and 8, coarse 5 beats
+// 4 and 6).
 #ifndef CGA_NN_FINE_BLOCKS
 #define CGA_NN_FINE_BLOCKS 6
+#endif
+#ifndef CGA_NN_COARSE_BLOCKS
+#define CGA_NN_COARSE_BLOCKS 5
 #endif
 
 struct Qry {
@@ -515,11 +519,11 @@ __device__ void search_levels(const NnSeg& sg, const Qry& q, uint32_t lane, Best
 
 // NC: the most coarse levels any segment of the launch carries (0, 1 or 2).
 // The fine-only instantiation is held to 40 registers (six blocks per SM),
-// the coarse ones to 64 (four blocks per SM): the extra warps hide more of
-// the search's load latency than the few spilled values cost (eight blocks,
-// 32 registers, spill enough to be slower).
+// the coarse ones to 48 (five blocks per SM): the extra warps hide more of
+// the search's load latency than the spilled values cost (eight and six
+// blocks respectively spill enough to be slower).
 template <int NC>
-__global__ void __launch_bounds__(256, NC > 0 ? 4 : CGA_NN_FINE_BLOCKS) k_nn_warp(const NnSeg* __restrict__ segs, int S,
+__global__ void __launch_bounds__(256, NC > 0 ? CGA_NN_COARSE_BLOCKS : CGA_NN_FINE_BLOCKS) k_nn_warp(const NnSeg* __restrict__ segs, int S,
                                                  NnSeg inline_seg, uint32_t total_slots,
                                                  const unsigned long long* __restrict__ order,
                                                  const unsigned int* __restrict__ order_err) {
