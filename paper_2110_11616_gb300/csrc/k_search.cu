@@ -15,6 +15,15 @@
 
 #include "k_common.cuh"
 
+// Blocks per SM the search kernels are compiled for (their register budgets;
+// measured on GB300: 5 or 6 blocks were no faster for either kernel).
+#ifndef CGA_KNN_BLOCKS
+#define CGA_KNN_BLOCKS 4
+#endif
+#ifndef CGA_RADIUS_BLOCKS
+#define CGA_RADIUS_BLOCKS 1
+#endif
+
 namespace libcga {
 
 namespace {
@@ -134,7 +143,7 @@ __device__ __forceinline__ uint32_t slot_query(const unsigned long long* order, 
   return order != nullptr ? (uint32_t)__ldg(order + slot) : slot;
 }
 
-__global__ void k_radius_count(SearchSeg sg, unsigned long long r2,
+__global__ void __launch_bounds__(256, CGA_RADIUS_BLOCKS) k_radius_count(SearchSeg sg, unsigned long long r2,
                                const unsigned long long* __restrict__ order,
                                unsigned long long* counts) {
   const uint32_t lane = threadIdx.x & 31;
@@ -154,7 +163,7 @@ __global__ void k_radius_count(SearchSeg sg, unsigned long long r2,
   }
 }
 
-__global__ void k_radius_fill(SearchSeg sg, unsigned long long r2,
+__global__ void __launch_bounds__(256, CGA_RADIUS_BLOCKS) k_radius_fill(SearchSeg sg, unsigned long long r2,
                               const unsigned long long* __restrict__ order,
                               const unsigned long long* __restrict__ offsets, uint32_t* idx,
                               unsigned long long* d2) {
@@ -455,7 +464,7 @@ struct SmemList {
 // runs out moves to its next column (and offers that column's nearest voxel)
 // in the same step.
 template <bool LARGE>
-__global__ void __launch_bounds__(LARGE ? kKnnLargeThreads : 256, LARGE ? 1 : 4)
+__global__ void __launch_bounds__(LARGE ? kKnnLargeThreads : 256, LARGE ? 1 : CGA_KNN_BLOCKS)
     k_knn(SearchSeg sg, uint32_t k, uint32_t cap, const unsigned long long* __restrict__ order,
           uint32_t* out_idx, unsigned long long* out_d2) {
   extern __shared__ unsigned long long s_knn[];
