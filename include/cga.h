@@ -163,7 +163,9 @@ int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
  * Every call also builds (once) an x directory per level: for each x value v
  * the index of the first X_index entry >= v -- the dense per-x table of
  * G-Arrays (Sec. V) used only to start a slab walk in one lookup
- * (4 * (2^bits + 1) bytes for the CGA itself).
+ * (4 * (2^bits + 1) bytes for the CGA itself), and a column table of the
+ * CGA: per column its voxel range and its lowest and highest z, 16 bytes per
+ * column of capacity, read by one load when a search visits the column.
  * shifts: count (0..CGA_NN_MAX_LEVELS) strictly increasing values in
  * 1..min(CGA_NN_MAX_SHIFT, bits-1), host memory; count 0 drops the coarse
  * levels and keeps only the x directory (fine search).  Replaces any earlier

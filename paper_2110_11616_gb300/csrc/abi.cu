@@ -43,7 +43,7 @@ struct cga {
   uint32_t* xdir = nullptr;
   // column z ranges of this CGA for NN (cga_nn_prepare)
   void* zrmem = nullptr;
-  uint32_t* zr0 = nullptr;
+  uint4* ctab = nullptr;
 };
 
 struct cga2d {
@@ -224,7 +224,7 @@ void release(cga* h) {
 // NN searches use the coarse levels that cga_nn_prepare_levels built.
 void attach_coarse(const cga* a, libcga::NnSeg& seg) {
   seg.xdir = a->xdir;
-  seg.zr0 = a->zr0;
+  seg.ctab = a->ctab;
   seg.ncoarse = a->ncoarse;
   for (uint32_t k = 0; k < a->ncoarse; ++k) {
     seg.c[k] = a->clv[k];
@@ -862,15 +862,15 @@ int cga_nn_prepare_levels(cga_t* a, const uint32_t* shifts, uint32_t count, void
     a->xdir = static_cast<uint32_t*>(xm);
   }
   if (a->zrmem == nullptr) {
-    void* zm = dalloc(A, (size_t)std::max<uint64_t>(a->lv.cap1, 1) * 4, s);
+    void* zm = dalloc(A, (size_t)std::max<uint64_t>(a->lv.cap1, 1) * sizeof(uint4), s);
     if (zm == nullptr) return CGA_ERR_OOM;
-    const int rc = cuda_rc(libcga::run_column_zrange(a->lv, static_cast<uint32_t*>(zm), s));
+    const int rc = cuda_rc(libcga::run_column_table(a->lv, static_cast<uint4*>(zm), s));
     if (rc != CGA_OK) {
       dfree(A, a->has_alloc, zm, s);
       return rc;
     }
     a->zrmem = zm;
-    a->zr0 = static_cast<uint32_t*>(zm);
+    a->ctab = static_cast<uint4*>(zm);
   }
   for (uint32_t k = 0; k < count; ++k) {
     const int rc = build_coarse_level(a, (int)k, shifts[k], s);

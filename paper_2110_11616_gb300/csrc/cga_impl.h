@@ -294,8 +294,9 @@ struct NnSeg {
   // optional x directory of `a` (cga_nn_prepare): for every x value v of the
   // grid, the index of the first X_index entry >= v
   const uint32_t* xdir;
-  // optional column z ranges of `a` (cga_nn_prepare): lowest | highest << 16
-  const uint32_t* zr0;
+  // optional column table of `a` (cga_nn_prepare): per column {first voxel,
+  // end, lowest z | highest z << 16, 0}
+  const uint4* ctab;
   float scale;
   float off[3];
   const float* q;
@@ -349,6 +350,8 @@ cudaError_t run_child_columns(const Levels& f, const Levels& c, const uint32_t* 
 // zr[c] = Z_index[Y_pointer[c]] | Z_index[Y_pointer[c + 1] - 1] << 16 for every column c
 // of a (a.cap1 entries reserved).
 cudaError_t run_column_zrange(const Levels& a, uint32_t* zr, cudaStream_t stream);
+// t[c] = {Y_pointer[c], Y_pointer[c + 1], zr as above, 0} (a.cap1 entries reserved).
+cudaError_t run_column_table(const Levels& a, uint4* t, cudaStream_t stream);
 // xdir[v] = first index of a's X_index with value >= v, for v in [0, 2^bits].
 cudaError_t run_x_directory(const Levels& a, uint32_t* xdir, cudaStream_t stream);
 

@@ -133,16 +133,19 @@ struct Best {
   }
 };
 
-// The two z neighbours of the query in column c.  zr0 (or null): the
-// column's lowest | highest z << 16; when the query lies below or above the
-// whole column, that end is the only neighbour and no search is needed.
-__device__ __forceinline__ void visit_column(const Levels& a, const uint32_t* zr0, uint32_t c,
+// The two z neighbours of the query in column c.  ctab (or null): the column
+// table, whose entry holds the column's voxel range and its lowest | highest
+// z << 16 in one 16-byte load; when the query lies below or above the whole
+// column, that end is the only neighbour and no search is needed.
+__device__ __forceinline__ void visit_column(const Levels& a, const uint4* ctab, uint32_t c,
                                              unsigned long long dxy, int qz, uint32_t cqz,
                                              Best& b) {
-  // the column's voxel range, loaded together with its z range
-  const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
-  if (zr0 != nullptr) {
-    const uint32_t zz = __ldg(zr0 + c);
+  uint32_t zs, ze;
+  if (ctab != nullptr) {
+    const uint4 e = __ldg(ctab + c);
+    zs = e.x;
+    ze = e.y;
+    const uint32_t zz = e.z;
     const uint32_t zlo = zz & 0xffffu, zhi = zz >> 16;
     if (cqz <= zlo) {
       const unsigned long long dz = absdiff(zlo, qz);
@@ -154,6 +157,9 @@ __device__ __forceinline__ void visit_column(const Levels& a, const uint32_t* zr
       b.offer(dxy + dz * dz, ze - 1);
       return;
     }
+  } else {
+    zs = __ldg(a.ptr1 + c);
+    ze = __ldg(a.ptr1 + c + 1);
   }
   const uint32_t zr = lower_bound_u16(a.idx0, zs, ze, cqz);
   if (zr < ze) {
@@ -170,7 +176,7 @@ __device__ __forceinline__ void visit_column(const Levels& a, const uint32_t* zr
 
 // Window search over the fine CGA alone (one warp, 16 slabs per side per round).
 __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdir,
-                                            const uint32_t* zr0, uint32_t h,
+                                            const uint4* ctab, uint32_t h,
                                             int qx, int qy, int qz,
                                             uint32_t cqx, uint32_t cqy, uint32_t cqz,
                                             uint32_t lane, Best& best) {
@@ -199,7 +205,7 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
         const unsigned long long dy = absdiff(y, qy);
         const unsigned long long dxy = dx2 + dy * dy;
         if (dxy <= best.d2) {
-          visit_column(a, zr0, yr0, dxy, qz, cqz, best);
+          visit_column(a, ctab, yr0, dxy, qz, cqz, best);
         }
       }
       if (yr0 > ys) {
@@ -207,7 +213,7 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
         const unsigned long long dy = absdiff(y, qy);
         const unsigned long long dxy = dx2 + dy * dy;
         if (dxy <= best.d2) {
-          visit_column(a, zr0, yr0 - 1, dxy, qz, cqz, best);
+          visit_column(a, ctab, yr0 - 1, dxy, qz, cqz, best);
         }
       }
     }
@@ -225,7 +231,7 @@ __device__ __forceinline__ void search_fine(const Levels& a, const uint32_t* xdi
         if (dxy > best.d2) break;
         const uint32_t c = (uint32_t)(gR ? R2 : L2);
         if (gR) ++R2; else --L2;
-        visit_column(a, zr0, c, dxy, qz, cqz, best);
+        visit_column(a, ctab, c, dxy, qz, cqz, best);
       }
     }
     best.warp_min();
@@ -298,7 +304,7 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
         const unsigned long long dy = absdiff(y, q.y);
         const unsigned long long dxy = dx2 + dy * dy;
         if (dxy > best.d2) continue;
-        visit_column(a, sg.zr0, c, dxy, q.z, q.cz, best);
+        visit_column(a, sg.ctab, c, dxy, q.z, q.cz, best);
       }
     }
     return;
@@ -353,7 +359,7 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
       const uint32_t c = (uint32_t)(gR ? R : Lc), yv = gR ? yR : yL;
       if (gR) ++R; else --Lc;
       if constexpr (K == 0) {
-        visit_column(L, sg.zr0, c, dxl2 + dyl * dyl, q.z, q.cz, best);
+        visit_column(L, sg.ctab, c, dxl2 + dyl * dyl, q.z, q.cz, best);
       } else {
         visit_cell_column<K>(sg, c, yv, dxl2, dyl * dyl, fx0, fx1, q, best);
       }
@@ -575,7 +581,7 @@ __global__ void __launch_bounds__(256, NC > 0 ? CGA_NN_COARSE_BLOCKS : CGA_NN_FI
     } else if (NC >= 1 && sg.ncoarse >= 1) {
       if constexpr (NC >= 1) search_levels<1>(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane, best);
     } else {
-      search_fine(a, sg.xdir, sg.zr0, h, qx, qy, qz, cqx, cqy, cqz, lane, best);
+      search_fine(a, sg.xdir, sg.ctab, h, qx, qy, qz, cqx, cqy, cqz, lane, best);
     }
     if (lane == 0) {
       sg.idx[j] = best.idx;

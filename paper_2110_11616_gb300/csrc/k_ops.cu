@@ -282,6 +282,18 @@ __global__ void k_child_columns(Levels f, Levels c, const uint32_t* __restrict__
 // ------------------------------------------------------- column z range
 // Lowest and highest z of every column: a bound that needs no search when
 // the query lies below or above the whole column.
+// The fine column table of the NN search: per column its first voxel, its
+// end and its z range (lowest | highest << 16), read by one 16-byte load.
+__global__ void k_column_table(Levels a, uint4* t) {
+  const uint32_t g = (uint32_t)a.hdr->cnt[1];
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < g; c += stride) {
+    const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
+    t[c] = make_uint4(zs, ze,
+                      (uint32_t)__ldg(a.idx0 + zs) | ((uint32_t)__ldg(a.idx0 + ze - 1) << 16), 0u);
+  }
+}
+
 __global__ void k_column_zrange(Levels a, uint32_t* zr) {
   const uint32_t g = (uint32_t)a.hdr->cnt[1];
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -437,6 +449,14 @@ cudaError_t run_column_zrange(const Levels& a, uint32_t* zr, cudaStream_t stream
   const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
                                                        (uint64_t)device_sm_count() * 8);
   k_column_zrange<<<blocks, 256, 0, stream>>>(a, zr);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t run_column_table(const Levels& a, uint4* t, cudaStream_t stream) {
+  const unsigned blocks = (unsigned)std::min<uint64_t>((std::max<uint64_t>(a.cap1, 1) + 255) / 256,
+                                                       (uint64_t)device_sm_count() * 8);
+  k_column_table<<<blocks, 256, 0, stream>>>(a, t);
   count_launch(1);
   return cudaGetLastError();
 }
