@@ -470,6 +470,7 @@ libcga::SearchSeg search_segment(const cga_t* a, const float* d_q, uint64_t m) {
   for (int k = 0; k < 3; ++k) sg.off[k] = a->grid.offset[k];
   sg.q = d_q;
   sg.m = (uint32_t)m;
+  sg.ctab = a->ctab;
   return sg;
 }
 

@@ -207,6 +207,7 @@ struct SearchSeg {
   float off[3];
   const float* q;  // m points, float32 AoS
   uint32_t m;
+  const uint4* ctab;  // the NN column table of `a` (cga_nn_prepare) or null
 };
 size_t radius_scratch_bytes();
 // order (or null): the queries' Morton keys of the NN search (query index in

@@ -83,6 +83,26 @@ __device__ __forceinline__ RQuery radius_query(const SearchSeg& sg, uint32_t j) 
   return q;
 }
 
+// Column c's voxel range [zs, ze) and z range [zlo, zhi]: one load from the
+// column table when there is one, else the range is taken as the whole axis
+// (so every shortcut below falls back to a search).
+__device__ __forceinline__ void column_of(const Levels& a, const uint4* ctab, uint32_t c,
+                                          uint32_t& zs, uint32_t& ze, uint32_t& zlo,
+                                          uint32_t& zhi) {
+  if (ctab != nullptr) {
+    const uint4 e = __ldg(ctab + c);
+    zs = e.x;
+    ze = e.y;
+    zlo = e.z & 0xffffu;
+    zhi = e.z >> 16;
+  } else {
+    zs = __ldg(a.ptr1 + c);
+    ze = __ldg(a.ptr1 + c + 1);
+    zlo = 0;
+    zhi = 0xffffu;
+  }
+}
+
 // Slabs [s0, s1) of a whose x lies within the radius of the query.
 __device__ __forceinline__ void radius_slabs(const Levels& a, uint32_t h, const RQuery& q,
                                              unsigned long long r2, uint32_t& s0, uint32_t& s1) {
@@ -97,7 +117,8 @@ __device__ __forceinline__ void radius_slabs(const Levels& a, uint32_t h, const 
 // Count (EMIT = false) or write in (y, z) order from position `pos` (EMIT =
 // true) the voxels of one slab within the radius; returns the count.
 template <bool EMIT>
-__device__ __forceinline__ unsigned long long radius_slab(const Levels& a, uint32_t slab,
+__device__ __forceinline__ unsigned long long radius_slab(const Levels& a, const uint4* ctab,
+                                                          uint32_t slab,
                                                           const RQuery& q, unsigned long long r2,
                                                           uint32_t* idx, unsigned long long* d2,
                                                           unsigned long long pos) {
@@ -115,9 +136,12 @@ __device__ __forceinline__ unsigned long long radius_slab(const Levels& a, uint3
     const unsigned long long dxy = dx2 + sq(absdiff32(y, q.y));
     int zlo, zhi;
     if (!axis_window(q.z, r2 - dxy, top, zlo, zhi)) continue;
-    const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
-    const uint32_t p0 = lower_bound_u16(a.idx0, zs, ze, (uint32_t)zlo);
-    const uint32_t p1 = lower_bound_u16(a.idx0, p0, ze, (uint32_t)zhi + 1);
+    uint32_t zs, ze, clo, chi;
+    column_of(a, ctab, c, zs, ze, clo, chi);
+    if ((uint32_t)zhi < clo || (uint32_t)zlo > chi) continue;
+    const uint32_t p0 = (uint32_t)zlo <= clo ? zs : lower_bound_u16(a.idx0, zs, ze, (uint32_t)zlo);
+    const uint32_t p1 =
+        (uint32_t)zhi >= chi ? ze : lower_bound_u16(a.idx0, p0, ze, (uint32_t)zhi + 1);
     if (EMIT) {
       for (uint32_t p = p0; p < p1; ++p) {
         const unsigned long long dz = absdiff32(__ldg(a.idx0 + p), q.z);
@@ -156,7 +180,7 @@ __global__ void __launch_bounds__(256, CGA_RADIUS_BLOCKS) k_radius_count(SearchS
     radius_slabs(sg.a, h, q, r2, s0, s1);
     unsigned long long n = 0;
     for (uint32_t s = s0 + lane; s < s1; s += 32) {
-      n += radius_slab<false>(sg.a, s, q, r2, nullptr, nullptr, 0);
+      n += radius_slab<false>(sg.a, sg.ctab, s, q, r2, nullptr, nullptr, 0);
     }
     n = warp_sum_u64(n);
     if (lane == 0) counts[j] = n;
@@ -179,14 +203,14 @@ __global__ void __launch_bounds__(256, CGA_RADIUS_BLOCKS) k_radius_fill(SearchSe
     for (uint32_t g = s0; g < s1; g += 32) {
       const uint32_t s = g + lane;
       const unsigned long long n =
-          s < s1 ? radius_slab<false>(sg.a, s, q, r2, nullptr, nullptr, 0) : 0ull;
+          s < s1 ? radius_slab<false>(sg.a, sg.ctab, s, q, r2, nullptr, nullptr, 0) : 0ull;
       unsigned long long inc = n;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= (uint32_t)o) inc += t;
       }
-      if (n > 0) radius_slab<true>(sg.a, s, q, r2, idx, d2, base + inc - n);
+      if (n > 0) radius_slab<true>(sg.a, sg.ctab, s, q, r2, idx, d2, base + inc - n);
       base += __shfl_sync(0xffffffffu, inc, 31);
     }
   }
@@ -533,9 +557,9 @@ __global__ void __launch_bounds__(LARGE ? kKnnLargeThreads : 256, LARGE ? 1 : CG
               } else {
                 const uint32_t c = gr ? cr++ : --cl;
                 dxy = d;
-                zs = __ldg(a.ptr1 + c);
-                ze = __ldg(a.ptr1 + c + 1);
-                zu = lower_bound_u16(a.idx0, zs, ze, cqz);
+                uint32_t clo, chi;
+                column_of(a, sg.ctab, c, zs, ze, clo, chi);
+                zu = cqz <= clo ? zs : (cqz > chi ? ze : lower_bound_u16(a.idx0, zs, ze, cqz));
                 zd = zu;
                 in_col = true;
               }

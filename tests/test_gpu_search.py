@@ -101,6 +101,26 @@ def test_knn_large_k_few_voxels(cg, orc):
         np.testing.assert_array_equal(d2.cpu().numpy().view(np.uint64), od)
 
 
+@pytest.mark.parametrize("kind,bits", [("uniform", 10), ("surface", 10), ("lidar", 16)])
+def test_prepared_world_parity(cg, orc, kind, bits):
+    """After cga_nn_prepare the walks read each column's voxel and z range from
+    the column table and skip the z searches it makes unnecessary."""
+    pts, lo, ext, g, og, a, oa = world(cg, orc, kind, bits)
+    cg.cga_nn_prepare(a)
+    q = queries(pts, lo, ext, 9000, bits + 11)
+    for r2 in (40, 700):
+        off, idx, d2 = cg.cga_radius(a, dev(q), r2)
+        ooff, oidx, od2 = orc.radius(oa, og, q, r2)
+        np.testing.assert_array_equal(off.cpu().numpy().view(np.uint64), ooff)
+        np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), oidx)
+        np.testing.assert_array_equal(d2.cpu().numpy().view(np.uint64), od2)
+    for k in (8, 100):
+        ki, kd = cg.cga_knn(a, dev(q[:3000]), k)
+        oi, od = orc.knn(oa, og, q[:3000], k)
+        np.testing.assert_array_equal(kd.cpu().numpy().view(np.uint64), od)
+        np.testing.assert_array_equal(ki.cpu().numpy().view(np.uint32), oi)
+
+
 def test_knn_one_equals_nn(cg):
     pts = synth.uniform_cube(30_000, seed=3)
     g = cg.grid_from_box([0, 0, 0], 1.0, 12)
