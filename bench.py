@@ -358,10 +358,10 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
         },
         "roofline": {"kernel": "k_nn_warp (NN search)", "bound": "hbm",
                      "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 5), "traffic": 35_867_648,
+                     "frac": round(achieved / peak, 5), "traffic": 45_711_616,
                      "peak_source": f"{peak_kind} hbm_gbs",
-                     "note": "latency-bound search: ncu shows L1 throughput 74% of peak, "
-                             "DRAM 0.16%; traffic = ncu dram read+write of one launch of the "
+                     "note": "latency-bound search: ncu shows L1 throughput 72% of peak, "
+                             "DRAM 0.25%; traffic = ncu dram read+write of one launch of the "
                              "timed step (profiles/launches_lidar_frame_set.md)"},
         "e2e": {"value": round(e2e_val, 3), "unit": "Mpts/s",
                 "h2d_bytes_per_step": P.bytes_in(), "d2h_bytes_per_step": P.bytes_out()},
