@@ -32,7 +32,7 @@ struct cga {
   uint32_t* xs[libcga::kMaxCoarse] = {};
   uint32_t cshift[libcga::kMaxCoarse] = {};
   uint32_t* cxdir[libcga::kMaxCoarse] = {};
-  uint32_t* czr[libcga::kMaxCoarse] = {};
+  uint4* czr[libcga::kMaxCoarse] = {};
   uint32_t* cchild[libcga::kMaxCoarse] = {};
   // Value array (cga_build_values / cga_merge_values): channels bytes per voxel
   void* vmem = nullptr;
@@ -781,7 +781,7 @@ int build_coarse_level(cga* a, int k, uint32_t shift, cudaStream_t s) {
   const size_t lb = levels_bytes(cap, cap1, cap2, 3);
   const size_t xsb = align_up((cap2 + 1) * 4);
   const size_t xdb = align_up(((size_t)pow2(bc) + 1) * 4);
-  const size_t zrb = align_up(cap1 * 4);
+  const size_t zrb = align_up(cap1 * sizeof(uint4));
   // child-column table: skipped (searched instead) when it would be large
   const size_t chb = (cap1 << dsh) * 4 <= kChildTableMaxBytes ? align_up((cap1 << dsh) * 4) : 0;
   void* mem = dalloc(A, lb + xsb + xdb + zrb + chb, s);
@@ -789,7 +789,7 @@ int build_coarse_level(cga* a, int k, uint32_t shift, cudaStream_t s) {
   const Levels clv = levels_carve(mem, bc, cap, cap1, cap2, 3);
   uint32_t* xs = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb);
   uint32_t* cxdir = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb + xsb);
-  uint32_t* czr = reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb + xsb + xdb);
+  uint4* czr = reinterpret_cast<uint4*>(static_cast<char*>(mem) + lb + xsb + xdb);
   uint32_t* cchild =
       chb ? reinterpret_cast<uint32_t*>(static_cast<char*>(mem) + lb + xsb + xdb + zrb) : nullptr;
   libcga::SortSeg seg{};
@@ -814,7 +814,7 @@ int build_coarse_level(cga* a, int k, uint32_t shift, cudaStream_t s) {
     cudaError_t e = libcga::run_sort_pipeline(&seg, 1, tiles, seg.passes, key64, sc, s);
     if (e == cudaSuccess) e = libcga::run_coarse_slab_index(fine, clv, dsh, xs, s);
     if (e == cudaSuccess) e = libcga::run_x_directory(clv, cxdir, s);
-    if (e == cudaSuccess) e = libcga::run_column_zrange(clv, czr, s);
+    if (e == cudaSuccess) e = libcga::run_column_table(clv, czr, s);
     if (e == cudaSuccess && cchild != nullptr) {
       e = libcga::run_child_columns(fine, clv, xs, dsh, cchild, s);
     }

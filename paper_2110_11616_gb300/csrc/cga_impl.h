@@ -285,8 +285,9 @@ struct NnSeg {
   const uint32_t* xs[kMaxCoarse];
   uint32_t shift[kMaxCoarse];
   const uint32_t* cxdir[kMaxCoarse];
-  // zr[k][c] = lowest | highest << 16 cell z of column c of c[k] (or null)
-  const uint32_t* zr[kMaxCoarse];
+  // zr[k][c] = {first cell, end, lowest | highest << 16 cell z, 0} of column c
+  // of c[k] (or null): the column table of the level
+  const uint4* zr[kMaxCoarse];
   // child[k][(c << dsh) + j]: for column c of c[k] (dsh = its shift minus the
   // next finer level's), the first column of the j-th finer slab under it
   // with y >= its y << dsh (or null: found by a search instead)
@@ -348,10 +349,9 @@ cudaError_t run_coarse_slab_index(const Levels& a, const Levels& c, uint32_t shi
 // above its y range.  child has c.cap1 << dsh entries.
 cudaError_t run_child_columns(const Levels& f, const Levels& c, const uint32_t* xs, uint32_t dsh,
                               uint32_t* child, cudaStream_t stream);
-// zr[c] = Z_index[Y_pointer[c]] | Z_index[Y_pointer[c + 1] - 1] << 16 for every column c
-// of a (a.cap1 entries reserved).
-cudaError_t run_column_zrange(const Levels& a, uint32_t* zr, cudaStream_t stream);
-// t[c] = {Y_pointer[c], Y_pointer[c + 1], zr as above, 0} (a.cap1 entries reserved).
+// t[c] = {Y_pointer[c], Y_pointer[c + 1], Z_index[Y_pointer[c]] |
+// Z_index[Y_pointer[c + 1] - 1] << 16, 0} for every column c of a (a.cap1
+// entries reserved).
 cudaError_t run_column_table(const Levels& a, uint4* t, cudaStream_t stream);
 // xdir[v] = first index of a's X_index with value >= v, for v in [0, 2^bits].
 cudaError_t run_x_directory(const Levels& a, uint32_t* xdir, cudaStream_t stream);

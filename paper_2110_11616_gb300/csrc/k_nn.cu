@@ -374,15 +374,22 @@ __device__ __forceinline__ unsigned long long cell_z_dist(const NnSeg& sg, uint3
                                                           const Qry& q) {
   const Levels& L = level<K>(sg);
   const uint32_t sh = level_shift<K>(sg), cell = 1u << sh;
-  const uint32_t* zrange = sg.zr[K - 1];
-  if (zrange != nullptr) {
-    // below or above the whole column: the nearest cell is its lowest or highest
-    const uint32_t zz = __ldg(zrange + c), qc = q.cz >> sh;
-    const uint32_t zlo = zz & 0xffffu, zhi = zz >> 16;
+  const uint4* ctab = sg.zr[K - 1];
+  uint32_t zs, ze;
+  if (ctab != nullptr) {
+    // one load: the column's cell range and z range; below or above the whole
+    // column, the nearest cell is its lowest or highest
+    const uint4 e = __ldg(ctab + c);
+    const uint32_t qc = q.cz >> sh;
+    const uint32_t zlo = e.z & 0xffffu, zhi = e.z >> 16;
     if (qc <= zlo) return interval_dist(q.z, zlo << sh, cell);
     if (qc >= zhi) return interval_dist(q.z, zhi << sh, cell);
+    zs = e.x;
+    ze = e.y;
+  } else {
+    zs = __ldg(L.ptr1 + c);
+    ze = __ldg(L.ptr1 + c + 1);
   }
-  const uint32_t zs = __ldg(L.ptr1 + c), ze = __ldg(L.ptr1 + c + 1);
   const uint32_t zr = lower_bound_u16(L.idx0, zs, ze, q.cz >> sh);
   unsigned long long dzl = ~0ull;
   if (zr < ze) dzl = min(dzl, (unsigned long long)interval_dist(q.z, (uint32_t)__ldg(L.idx0 + zr) << sh, cell));

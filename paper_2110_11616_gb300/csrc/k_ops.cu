@@ -294,15 +294,6 @@ __global__ void k_column_table(Levels a, uint4* t) {
   }
 }
 
-__global__ void k_column_zrange(Levels a, uint32_t* zr) {
-  const uint32_t g = (uint32_t)a.hdr->cnt[1];
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < g; c += stride) {
-    const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
-    zr[c] = (uint32_t)__ldg(a.idx0 + zs) | ((uint32_t)__ldg(a.idx0 + ze - 1) << 16);
-  }
-}
-
 // ------------------------------------------------------------ x directory
 // The dense per-x-value table of G-Arrays (Sec. V), here only as a lookup
 // accelerator: xdir[v] = number of stored x values below v.
@@ -440,15 +431,6 @@ cudaError_t run_child_columns(const Levels& f, const Levels& c, const uint32_t* 
   const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
                                                        (uint64_t)device_sm_count() * 8);
   k_child_columns<<<blocks, 256, 0, stream>>>(f, c, xs, dsh, child);
-  count_launch(1);
-  return cudaGetLastError();
-}
-
-cudaError_t run_column_zrange(const Levels& a, uint32_t* zr, cudaStream_t stream) {
-  const uint64_t work = std::max<uint64_t>(a.cap1, 1);
-  const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256,
-                                                       (uint64_t)device_sm_count() * 8);
-  k_column_zrange<<<blocks, 256, 0, stream>>>(a, zr);
   count_launch(1);
   return cudaGetLastError();
 }
