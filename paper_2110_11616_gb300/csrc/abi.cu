@@ -41,7 +41,7 @@ struct cga {
   // x directory of this CGA for NN (cga_nn_prepare): first X_index entry >= v
   void* xdmem = nullptr;
   uint32_t* xdir = nullptr;
-  // column z ranges of this CGA for NN (cga_nn_prepare)
+  // column table of this CGA for NN (cga_nn_prepare): voxel range + z range
   void* zrmem = nullptr;
   uint4* ctab = nullptr;
 };

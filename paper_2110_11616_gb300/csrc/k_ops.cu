@@ -279,11 +279,11 @@ __global__ void k_child_columns(Levels f, Levels c, const uint32_t* __restrict__
   }
 }
 
-// ------------------------------------------------------- column z range
-// Lowest and highest z of every column: a bound that needs no search when
-// the query lies below or above the whole column.
-// The fine column table of the NN search: per column its first voxel, its
-// end and its z range (lowest | highest << 16), read by one 16-byte load.
+// -------------------------------------------------------- column table
+// The column table of the NN search (the CGA's, and each coarse level's):
+// per column its first voxel, its end and its z range (lowest | highest <<
+// 16), read by one 16-byte load; the z range settles a column without a
+// search when the query lies below or above all of it.
 __global__ void k_column_table(Levels a, uint4* t) {
   const uint32_t g = (uint32_t)a.hdr->cnt[1];
   const uint32_t stride = gridDim.x * blockDim.x;
