@@ -75,6 +75,37 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert out.value is None
 
 
+def test_search_and_compression_arguments_rejected_on_host(lib):
+    """Null handles and out-of-range sizes are refused before any device work."""
+    from paper_2110_11616_gb300 import cga
+    P, U32, U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+    sig = {
+        "cga_knn": [P, P, U64, U32, P, P, P],
+        "cga_radius_count": [P, P, U64, U64, P, P],
+        "cga_radius_fill": [P, P, U64, U64, P, P, P, P],
+        "cga_kmeans": [P, U32, P, P, P, P, P],
+        "cga_motion_vectors": [P, P, P, P, P, P],
+        "cga_reconstruct": [P, P, P, P, P],
+        "cga_nn_query_voxels": [P, P, U64, P, P, P],
+        "cga_lookup": [P, P, U64, P, P],
+        "cga_garrays_x": [P, P, P],
+        "cga_garrays_lookup": [P, P, P, U64, P, P],
+    }
+    for name, args in sig.items():
+        getattr(lib, name).argtypes = args
+    bad = cga.ERR_INVALID_ARG
+    assert lib.cga_knn(None, None, 1, 8, None, None, None) == bad
+    assert lib.cga_radius_count(None, None, 1, 4, None, None) == bad
+    assert lib.cga_radius_fill(None, None, 1, 4, None, None, None, None) == bad
+    assert lib.cga_kmeans(None, 10, None, None, None, None, None) == bad
+    assert lib.cga_motion_vectors(None, None, None, None, None, None) == bad
+    assert lib.cga_reconstruct(None, None, None, None, None) == bad
+    assert lib.cga_nn_query_voxels(None, None, 1, None, None, None) == bad
+    assert lib.cga_lookup(None, None, 1, None, None) == bad
+    assert lib.cga_garrays_x(None, None, None) == bad
+    assert lib.cga_garrays_lookup(None, None, None, 1, None, None) == bad
+
+
 def test_strerror_names_every_code(lib):
     from paper_2110_11616_gb300 import cga
     seen = set()
