@@ -108,6 +108,7 @@ def lib():
         _lib.orc_kmeans.argtypes = [C, U32, P, P, P, P]
         _lib.orc_motion_vectors.argtypes = [P, P, P, P, P]
         _lib.orc_reconstruct.argtypes = [C, P, P, P]
+        _lib.orc_residual.argtypes = [P, U64, P, U64, P, U32, P]
         for fn in (_lib.orc_nn_brute, _lib.orc_nn_window):
             fn.argtypes = [ctypes.POINTER(_Cga), F, P, P, U64, P, P]
     return _lib
@@ -469,3 +470,17 @@ def reconstruct(a: Cga, labels, mv):
     s = a._struct()
     _check(lib().orc_reconstruct(ctypes.byref(s), _ptr(lab), _ptr(m), _ptr(out)))
     return out[:a.u]
+
+
+def residual(pred_values, ref_values, idx):
+    """Residual frame (Sec. V-D): pred - ref[idx] per channel as int16 (pred where
+    idx has no reference point)."""
+    pv = np.ascontiguousarray(np.asarray(pred_values, np.uint8))
+    rv = np.ascontiguousarray(np.asarray(ref_values, np.uint8))
+    ch = pv.shape[1] if pv.ndim > 1 else 1
+    ix = np.ascontiguousarray(np.asarray(idx, np.uint32))
+    u_pred = len(ix)
+    u_ref = len(rv) if rv.ndim > 1 else len(rv) // ch
+    out = np.zeros((max(u_pred, 1), ch), np.int16)
+    _check(lib().orc_residual(_ptr(pv), u_pred, _ptr(rv), u_ref, _ptr(ix), ch, _ptr(out)))
+    return out[:u_pred]

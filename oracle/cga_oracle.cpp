@@ -788,4 +788,21 @@ int orc_reconstruct(const orc_cga* a, const uint8_t* label, const int64_t* mv, i
   return ORC_OK;
 }
 
+// Sec. V-D residual frame: for every point of the reconstructed (predicted)
+// frame the difference between its attributes and those of its
+// corresponding reference point, res = pred - ref[idx] per channel; a point
+// without a correspondence (idx out of range) keeps its own attributes.
+int orc_residual(const uint8_t* pred, uint64_t u_pred, const uint8_t* ref, uint64_t u_ref,
+                 const uint32_t* idx, uint32_t channels, int16_t* out) {
+  if (channels < 1 || channels > 4) return ORC_ERR_INVALID_ARG;
+  for (uint64_t i = 0; i < u_pred; ++i) {
+    for (uint32_t c = 0; c < channels; ++c) {
+      const int16_t p = (int16_t)pred[i * channels + c];
+      out[i * channels + c] =
+          idx[i] < u_ref ? (int16_t)(p - (int16_t)ref[(uint64_t)idx[i] * channels + c]) : p;
+    }
+  }
+  return ORC_OK;
+}
+
 }  // extern "C"

@@ -192,6 +192,10 @@ int orc_motion_vectors(const int64_t* ref_centres, const uint64_t* ref_counts,
                        const int64_t* pred_centres, const uint64_t* pred_counts, int64_t* mv);
 /* out[3i + a] = voxel_a + floor((mv[label][a] + 128) / 256), u * 3 int32. */
 int orc_reconstruct(const orc_cga* a, const uint8_t* label, const int64_t* mv, int32_t* out);
+/* Residual frame (Sec. V-D): out[i*C + c] = pred[i*C + c] - ref[idx[i]*C + c]
+ * (int16), or pred[i*C + c] when idx[i] >= u_ref (no correspondence). */
+int orc_residual(const uint8_t* pred, uint64_t u_pred, const uint8_t* ref, uint64_t u_ref,
+                 const uint32_t* idx, uint32_t channels, int16_t* out);
 
 #ifdef __cplusplus
 }

@@ -186,3 +186,45 @@ def test_nn_voxels_matches_float_queries():
                                          np.float32))
     np.testing.assert_array_equal(i3, i4)
     np.testing.assert_array_equal(d3, d4)
+
+
+def test_residual_hand_example():
+    """Sec. V-D residual: pred - ref[idx] per channel; no correspondence keeps pred."""
+    pred = np.array([[10, 20, 30], [5, 5, 5], [0, 255, 128]], np.uint8)
+    ref = np.array([[1, 2, 3], [200, 0, 255]], np.uint8)
+    idx = np.array([1, U32_MAX, 0], np.uint32)
+    np.testing.assert_array_equal(orc.residual(pred, ref, idx),
+                                  [[-190, 20, -225], [5, 5, 5], [-1, 253, 125]])
+
+
+def test_residual_reconstructs_prediction():
+    rng = np.random.default_rng(8)
+    ref = rng.integers(0, 256, (500, 3)).astype(np.uint8)
+    pred = rng.integers(0, 256, (700, 3)).astype(np.uint8)
+    idx = rng.integers(0, 500, 700).astype(np.uint32)
+    idx[::50] = U32_MAX
+    res = orc.residual(pred, ref, idx).astype(np.int64)
+    have = idx != U32_MAX
+    np.testing.assert_array_equal(ref[idx[have]].astype(np.int64) + res[have], pred[have])
+    np.testing.assert_array_equal(res[~have], pred[~have])
+
+
+def test_prediction_chain_residual_is_zero_under_translation():
+    """Values that move with their voxels: clustering, motion vectors,
+    reconstruction and NN correspondence bring every predicted voxel onto its
+    reference voxel, so the residual frame is all zeros."""
+    rng = np.random.default_rng(12)
+    ref_v = np.unique(rng.integers(20, 230, (2000, 3)), axis=0)
+    shift = np.array([4, -3, 2])
+    colour = lambda v: np.stack([(v[:, 0] * 7 + v[:, 1]) % 256, (v[:, 1] * 5) % 256,
+                                 (v[:, 2] * 3 + 1) % 256], 1).astype(np.uint8)
+    g = orc.Grid(8, 1.0, (0.0, 0.0, 0.0))
+    ref, ref_vals = orc.build_values((ref_v + 0.5).astype(np.float32), colour(ref_v), g)
+    pred, pred_vals = orc.build_values((ref_v + shift + 0.5).astype(np.float32), colour(ref_v), g)
+    lr, cr, nr, _ = orc.kmeans(ref, 300)
+    lp, cp, npd, _ = orc.kmeans(pred, 300)
+    mv = orc.motion_vectors(cr, nr, cp, npd)
+    rec = orc.reconstruct(pred, lp, mv)
+    idx, d2 = orc.nn_voxels(ref, rec)
+    assert not d2.any()
+    assert not orc.residual(pred_vals, ref_vals, idx).any()
