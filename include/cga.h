@@ -323,7 +323,14 @@ int cga_knn(const cga_t* a, const float* d_q, uint64_t m, uint32_t k, uint32_t* 
  * of the whole axis, which Sec. V contrasts with the CGA's compact X_index +
  * X_pointer): d_xptr[v] = number of (x, y) columns with x < v, for v in
  * [0, 2^bits] (2^bits + 1 uint32, device).  cga_garrays_lookup answers
- * cga_lookup through it (x indexes the pointer array directly). */
+ * cga_lookup through it (x indexes the pointer array directly).
+ *
+ * cga_residual: the residual frame of Sec. V-D: for each point i of the
+ * reconstructed frame (u_pred points, values d_pred_values, channels per
+ * point) and its corresponding reference point d_idx[i] (e.g. from
+ * cga_nn_query_voxels; the reference has u_ref points, values d_ref_values):
+ * d_out[i * channels + c] = pred - ref (int16), or pred itself when d_idx[i]
+ * >= u_ref (no corresponding point).  All device pointers; channels 1..4. */
 #define CGA_KMEANS_MAX_ITER 1024
 int cga_kmeans(const cga_t* a, uint32_t max_iter, uint8_t* d_label, int64_t* d_centres,
                uint64_t* d_counts, uint32_t* d_iters, void* stream);
@@ -335,6 +342,9 @@ int cga_reconstruct(const cga_t* pred, const uint8_t* d_label, const int64_t* d_
 int cga_nn_query_voxels(const cga_t* a, const int32_t* d_qv, uint64_t m, uint32_t* d_idx,
                         uint64_t* d_dist2, void* stream);
 int cga_lookup(const cga_t* a, const int32_t* d_qv, uint64_t m, uint32_t* d_idx, void* stream);
+int cga_residual(const uint8_t* d_pred_values, uint64_t u_pred, const uint8_t* d_ref_values,
+                 uint64_t u_ref, const uint32_t* d_idx, uint32_t channels, int16_t* d_out,
+                 void* stream);
 int cga_garrays_x(const cga_t* a, uint32_t* d_xptr, void* stream);
 int cga_garrays_lookup(const cga_t* a, const uint32_t* d_xptr, const int32_t* d_qv, uint64_t m,
                        uint32_t* d_idx, void* stream);

@@ -43,7 +43,7 @@ EXPORTS = (
     "cga_build_values", "cga_merge_values", "cga_values", "cga_perspective",
     "cga_radius_count", "cga_radius_fill", "cga_knn",
     "cga_kmeans", "cga_motion_vectors", "cga_reconstruct", "cga_nn_query_voxels", "cga_lookup",
-    "cga_garrays_x", "cga_garrays_lookup",
+    "cga_garrays_x", "cga_garrays_lookup", "cga_residual",
     "cga_selftest_wait_timeout",
 )
 
@@ -1044,3 +1044,24 @@ def cga_garrays_lookup(a: Cga, xptr, qv, stream=None):
     _check(lib.cga_garrays_lookup(a.ptr, P(xptr.data_ptr()), P(qv.data_ptr()), m,
                                   P(idx.data_ptr()), _stream(stream)), "cga_garrays_lookup")
     return idx[:m]
+
+
+def cga_residual(pred_values, ref_values, idx, stream=None):
+    """Residual frame (Sec. V-D): pred - ref[idx] per channel as an (u_pred, C) int16
+    tensor (pred where idx has no reference point).  Values: (u, C) uint8 CUDA
+    tensors; idx: (u_pred,) int32 CUDA tensor holding uint32."""
+    torch = _torch()
+    lib = load()
+    P = ctypes.c_void_p
+    lib.cga_residual.argtypes = [P, ctypes.c_uint64, P, ctypes.c_uint64, P, ctypes.c_uint32, P, P]
+    for t in (pred_values, ref_values, idx):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise TypeError("cga_residual: expected contiguous CUDA tensors")
+    ch = pred_values.shape[1] if pred_values.dim() > 1 else 1
+    u_pred = idx.numel()
+    u_ref = ref_values.numel() // ch
+    out = torch.empty((max(u_pred, 1), ch), dtype=torch.int16, device="cuda")
+    _check(lib.cga_residual(P(pred_values.data_ptr()), u_pred, P(ref_values.data_ptr()), u_ref,
+                            P(idx.data_ptr()), ch, P(out.data_ptr()), _stream(stream)),
+           "cga_residual")
+    return out[:u_pred]

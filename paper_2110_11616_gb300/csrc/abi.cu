@@ -724,6 +724,19 @@ int cga_reconstruct(const cga_t* pred, const uint8_t* d_label, const int64_t* d_
                                          static_cast<cudaStream_t>(stream)));
 }
 
+int cga_residual(const uint8_t* d_pred_values, uint64_t u_pred, const uint8_t* d_ref_values,
+                 uint64_t u_ref, const uint32_t* d_idx, uint32_t channels, int16_t* d_out,
+                 void* stream) {
+  if (channels < 1 || channels > CGA_MAX_CHANNELS || u_pred > CGA_MAX_POINTS ||
+      u_ref > CGA_MAX_POINTS ||
+      (u_pred > 0 && (d_pred_values == nullptr || d_idx == nullptr || d_out == nullptr)) ||
+      (u_ref > 0 && d_ref_values == nullptr)) {
+    return CGA_ERR_INVALID_ARG;
+  }
+  return cuda_rc(libcga::run_residual(d_pred_values, u_pred, d_ref_values, u_ref, d_idx, channels,
+                                      d_out, static_cast<cudaStream_t>(stream)));
+}
+
 int cga_garrays_x(const cga_t* a, uint32_t* d_xptr, void* stream) {
   if (a == nullptr || d_xptr == nullptr) return CGA_ERR_INVALID_ARG;
   return cuda_rc(libcga::run_garrays_x(a->lv, d_xptr, static_cast<cudaStream_t>(stream)));

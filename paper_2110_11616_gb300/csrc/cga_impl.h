@@ -254,6 +254,10 @@ cudaError_t run_motion(const long long* ref_c, const unsigned long long* ref_n,
 // out: u * 3 int32 voxels.
 cudaError_t run_reconstruct(const Levels& a, const uint8_t* labels, const long long* mv, int* out,
                             cudaStream_t stream);
+// res: u_pred * channels int16.
+cudaError_t run_residual(const uint8_t* pred, uint64_t u_pred, const uint8_t* ref, uint64_t u_ref,
+                         const uint32_t* idx, uint32_t channels, int16_t* res,
+                         cudaStream_t stream);
 // xptr: 2^bits + 1 entries.
 cudaError_t run_garrays_x(const Levels& a, uint32_t* xptr, cudaStream_t stream);
 // xptr == nullptr: the CGA lookup; else through the dense X pointer.

@@ -10,6 +10,9 @@
 //   k_motion          mv = ref - pred for clusters non-empty in both frames
 //   k_reconstruct     every voxel moved by its cluster's vector rounded half
 //                     up to whole voxels
+//   k_residual        the residual frame: each reconstructed point's
+//                     attributes minus those of its corresponding reference
+//                     point
 //   k_garrays_x       the dense X pointer, one cell per x value of the axis
 //   k_lookup          the Sec. V-A point lookup of integer voxels, through
 //                     X_index (CGA) or through the dense X pointer (G-Arrays)
@@ -238,6 +241,22 @@ __global__ void __launch_bounds__(kThreads) k_reconstruct(Levels a, const uint8_
   }
 }
 
+// res[i*C + c] = pred[i*C + c] - ref[idx[i]*C + c], or pred[i*C + c] when
+// idx[i] >= u_ref (no corresponding point).  One thread per output entry.
+__global__ void k_residual(const uint8_t* __restrict__ pred, uint64_t u_pred,
+                           const uint8_t* __restrict__ ref, uint64_t u_ref,
+                           const uint32_t* __restrict__ idx, uint32_t C, int16_t* __restrict__ res) {
+  const uint64_t total = u_pred * C;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total; e += stride) {
+    const uint64_t i = e / C;
+    const uint32_t c = (uint32_t)(e - i * C);
+    const uint32_t j = __ldg(idx + i);
+    const int p = __ldg(pred + e);
+    res[e] = (int16_t)(j < u_ref ? p - (int)__ldg(ref + (uint64_t)j * C + c) : p);
+  }
+}
+
 __global__ void k_garrays_x(Levels a, uint32_t* xptr) {
   const uint32_t h = (uint32_t)a.hdr->cnt[2];
   const uint32_t n = 1u << a.bits;
@@ -315,6 +334,16 @@ cudaError_t run_reconstruct(const Levels& a, const uint8_t* labels, const long l
   const uint64_t tiles = (a.cap + kTile - 1) / kTile;
   if (tiles == 0) return cudaSuccess;
   k_reconstruct<<<(unsigned)tiles, kThreads, 0, stream>>>(a, labels, mv, out);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t run_residual(const uint8_t* pred, uint64_t u_pred, const uint8_t* ref, uint64_t u_ref,
+                         const uint32_t* idx, uint32_t channels, int16_t* res,
+                         cudaStream_t stream) {
+  if (u_pred == 0) return cudaSuccess;
+  k_residual<<<grid_for(u_pred * channels), 256, 0, stream>>>(pred, u_pred, ref, u_ref, idx,
+                                                              channels, res);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -90,6 +90,7 @@ def test_search_and_compression_arguments_rejected_on_host(lib):
         "cga_lookup": [P, P, U64, P, P],
         "cga_garrays_x": [P, P, P],
         "cga_garrays_lookup": [P, P, P, U64, P, P],
+        "cga_residual": [P, U64, P, U64, P, U32, P, P],
     }
     for name, args in sig.items():
         getattr(lib, name).argtypes = args
@@ -104,6 +105,8 @@ def test_search_and_compression_arguments_rejected_on_host(lib):
     assert lib.cga_lookup(None, None, 1, None, None) == bad
     assert lib.cga_garrays_x(None, None, None) == bad
     assert lib.cga_garrays_lookup(None, None, None, 1, None, None) == bad
+    assert lib.cga_residual(None, 1, None, 1, None, 3, None, None) == bad
+    assert lib.cga_residual(None, 0, None, 0, None, 0, None, None) == bad  # channels 0
 
 
 def test_strerror_names_every_code(lib):

@@ -121,6 +121,26 @@ def test_prediction_chain_parity(cg, orc, kind, bits):
     np.testing.assert_array_equal(d2.cpu().numpy().view(np.uint64), od)
 
 
+def test_residual_frame_parity(cg, orc):
+    """The residual of the reconstructed frame against its NN correspondence in
+    the reference, with the frames' averaged colours (Value arrays)."""
+    ref, pred, lo, ext = frames("surface", 10, 21)
+    g, og = cg.grid_from_box(lo, ext, 10), orc.grid_from_box(lo, ext, 10)
+    col = lambda p: (np.abs(p) * 2.55 % 256).astype(np.uint8)
+    a_ref = cg.cga_build_values(dev(ref), torch.from_numpy(col(ref)).cuda(), g)
+    a_pred = cg.cga_build_values(dev(pred), torch.from_numpy(col(pred)).cuda(), g)
+    o_ref, ov_ref = orc.build_values(ref, col(ref), og)
+    o_pred, ov_pred = orc.build_values(pred, col(pred), og)
+    _, cr, nr, _ = cg.cga_kmeans(a_ref, 64)
+    lp, cp, npd, _ = cg.cga_kmeans(a_pred, 64)
+    rec = cg.cga_reconstruct(a_pred, lp, cg.cga_motion_vectors(cr, nr, cp, npd))
+    idx, _ = cg.cga_nn_query_voxels(a_ref, rec)
+    idx[::97] = -1  # some points without a corresponding point
+    res = cg.cga_residual(cg.cga_values(a_pred), cg.cga_values(a_ref), idx)
+    want = orc.residual(ov_pred, ov_ref, u32(idx))
+    np.testing.assert_array_equal(res.cpu().numpy(), want)
+
+
 def test_nn_query_voxels_extremes(cg, orc):
     pts = synth.uniform_cube(20_000, 5)
     g, og = cg.grid_from_box([0, 0, 0], 1.0, 9), orc.grid_from_box([0, 0, 0], 1.0, 9)
