@@ -256,8 +256,8 @@ class LidarStep:
 
 def tune_record(shifts, times):
     """cga_nn_autotune's choice and sample timings for the JSON line."""
-    name = lambda c: ",".join(map(str, c)) if c else "fine"
-    return {"chosen_coarse_shifts": list(shifts),
+    name = lambda c: "tree" if c == (0xFFFFFFFF,) else (",".join(map(str, c)) if c else "fine")
+    return {"chosen": name(tuple(shifts)),
             "sample_ms": {name(c): round(t, 4) for c, t in times.items()}}
 
 

@@ -148,9 +148,10 @@ int cga_project(const cga_t* a, int plane, const cga_allocator* A, void* stream,
 int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
                  uint64_t* d_dist2, void* stream);
 
-#define CGA_NN_MAX_LEVELS 2          /* coarse levels cga_nn_prepare_levels takes */
-#define CGA_NN_MAX_SHIFT 12          /* largest coarse cell: 2^12 voxels per axis */
-#define CGA_NN_AUTOTUNE_CANDIDATES 9 /* strategies cga_nn_autotune measures */
+#define CGA_NN_MAX_LEVELS 2           /* coarse levels cga_nn_prepare_levels takes */
+#define CGA_NN_MAX_SHIFT 12           /* largest coarse cell: 2^12 voxels per axis */
+#define CGA_NN_AUTOTUNE_CANDIDATES 10 /* strategies cga_nn_autotune measures */
+#define CGA_NN_TREE 0xFFFFFFFFu       /* shifts = {CGA_NN_TREE}, count 1: occupancy tree */
 
 /* Build (once per CGA) the coarse levels that let NN search skip empty space.
  * Level k is the CGA of the occupied cells of 2^shifts[k] voxels per axis
@@ -168,9 +169,22 @@ int cga_nn_query(const cga_t* a, const float* d_q, uint64_t m, uint32_t* d_idx,
  * column of capacity, read by one load when a search visits the column.
  * shifts: count (0..CGA_NN_MAX_LEVELS) strictly increasing values in
  * 1..min(CGA_NN_MAX_SHIFT, bits-1), host memory; count 0 drops the coarse
- * levels and keeps only the x directory (fine search).  Replaces any earlier
- * preparation.  Memory comes from a's allocator and is released with a.
- * Stream-ordered.  CGA_ERR_INVALID_ARG for a view handle or bad shifts. */
+ * levels and keeps only the x directory (fine search).
+ * shifts = {CGA_NN_TREE} with count 1 builds, instead of coarse levels, an
+ * occupancy tree: a 64-ary tree in which a node of level l is a cell of 4^l
+ * voxels per axis that records which of its 4 x 4 x 4 sub-cells hold a voxel
+ * (a level-1 node, a brick, records its 64 voxels), ceil(bits / 2) levels.
+ * NN calls then descend it nearest child first and skip every cell whose box
+ * lies farther than the best voxel found so far (same exact results; for
+ * queries far from every voxel, e.g. a surface in a large box, this visits
+ * far fewer cells than the slab walk).  It is built on the device by a sort
+ * of the voxels' tree keys and one compaction per level; its arrays take 8
+ * bytes per brick and 16 per node of each higher level, reserved by the
+ * capacity bounds (at most the CGA's capacity or the level's cell count per
+ * level).
+ * Replaces any earlier preparation.  Memory comes from a's allocator and is
+ * released with a.  Stream-ordered.  CGA_ERR_INVALID_ARG for a view handle or
+ * bad shifts. */
 int cga_nn_prepare_levels(cga_t* a, const uint32_t* shifts, uint32_t count, void* stream);
 
 /* cga_nn_prepare_levels with one coarse level of 2^shift voxel cells, or none
@@ -180,9 +194,10 @@ int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream);
 /* Pick the NN search strategy for `a` by measurement: run the m sample queries
  * d_q (device; a few tens of thousands representative queries suffice) under
  * each candidate and keep the fastest prepared on `a`.  Candidates, in order
- * (coarse shifts): none (fine search alone); 2; 3; 4; 5; 2,5; 3,6; 3,7; 4,8.
+ * (coarse shifts): none (fine search alone); 2; 3; 4; 5; 2,5; 3,6; 3,7; 4,8;
+ * CGA_NN_TREE (the occupancy tree).
  * chosen_shifts (CGA_NN_MAX_LEVELS entries) receives the winner's shifts, 0
- * for an unused level.  times_ms (NULL or CGA_NN_AUTOTUNE_CANDIDATES floats)
+ * for an unused level ({CGA_NN_TREE, 0} for the tree).  times_ms (NULL or CGA_NN_AUTOTUNE_CANDIDATES floats)
  * receives each candidate's time, -1 for one the grid cannot take.  Waits for
  * the timings. */
 int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shifts,
@@ -212,7 +227,11 @@ int cga_nn_query_ordered(const cga_t* a, const float* d_q, uint64_t m, const uin
  * CGA_ERR_CAPACITY and nothing is queued.  The caller passes the CGA, the
  * queries and the outputs exactly as for cga_nn_query.
  * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  All calls share
+ * device).  Each call copies its small segment tables from host memory into
+ * the array (cudaMemcpyAsync), so the call is not meant to be recorded into a
+ * CUDA graph by stream capture.  A search structure that cga_nn_prepare_levels
+ * built on `a` (x directory, column table, coarse levels or occupancy tree)
+ * is used as cga_nn_query uses it.  All calls share
  * the one array and each call resets what it needs, so calls whose work
  * overlaps on the GPU (different streams, or different host threads) race:
  * serialize them, e.g. on one stream.  Nothing is allocated: no cudaMalloc,

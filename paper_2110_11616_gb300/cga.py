@@ -669,13 +669,19 @@ def cga_nn_query_ordered(a: Cga, queries, order, idx, dist2, stream=None):
 
 
 NN_MAX_LEVELS = 2
+NN_TREE = 0xFFFFFFFF  # shifts (NN_TREE,): the occupancy tree instead of coarse levels
 # cga_nn_autotune's candidates, in the order of its timings (coarse shifts)
-NN_AUTOTUNE_CANDIDATES = ((), (2,), (3,), (4,), (5,), (2, 5), (3, 6), (3, 7), (4, 8))
+NN_AUTOTUNE_CANDIDATES = ((), (2,), (3,), (4,), (5,), (2, 5), (3, 6), (3, 7), (4, 8), (NN_TREE,))
 
 
 def cga_nn_prepare(a: Cga, shifts=(), stream=None):
     """Build the coarse levels (cells of 2^shift voxels, finest first) used by
-    NN search; an int is one level, 0 or () none (x directory only)."""
+    NN search; an int is one level, 0 or () none (x directory only),
+    (NN_TREE,) or "tree" the occupancy tree."""
+    if isinstance(shifts, str):
+        if shifts != "tree":
+            raise ValueError(f"cga_nn_prepare: unknown strategy {shifts!r}")
+        shifts = (NN_TREE,)
     if isinstance(shifts, int):
         shifts = () if shifts == 0 else (shifts,)
     shifts = tuple(int(v) for v in shifts)

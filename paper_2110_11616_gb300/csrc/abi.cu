@@ -44,6 +44,9 @@ struct cga {
   // column table of this CGA for NN (cga_nn_prepare): voxel range + z range
   void* zrmem = nullptr;
   uint4* ctab = nullptr;
+  // occupancy tree for NN (cga_nn_prepare_levels with CGA_NN_TREE)
+  void* tmem = nullptr;
+  libcga::TreeView tree{};
 };
 
 struct cga2d {
@@ -63,6 +66,7 @@ void handle_parts(const cga_t* a, Levels* lv, cga_grid* g) {
   *lv = a->lv;
   *g = a->grid;
 }
+void nn_attach(const cga_t* a, NnSeg& seg);
 void rebind_stream(cga_t* a, cga2d_t* p, cudaStream_t s) {
   if (a != nullptr) a->stream = s;
   if (p != nullptr) p->stream = s;
@@ -217,6 +221,7 @@ void release(cga* h) {
   if (h->xdmem != nullptr) dfree(&h->alloc, h->has_alloc, h->xdmem, h->stream);
   if (h->vmem != nullptr) dfree(&h->alloc, h->has_alloc, h->vmem, h->stream);
   if (h->zrmem != nullptr) dfree(&h->alloc, h->has_alloc, h->zrmem, h->stream);
+  if (h->tmem != nullptr) dfree(&h->alloc, h->has_alloc, h->tmem, h->stream);
   dfree(&h->alloc, h->has_alloc, h->mem, h->stream);
   delete h;
 }
@@ -225,6 +230,7 @@ void release(cga* h) {
 void attach_coarse(const cga* a, libcga::NnSeg& seg) {
   seg.xdir = a->xdir;
   seg.ctab = a->ctab;
+  seg.tree = a->tree;
   seg.ncoarse = a->ncoarse;
   for (uint32_t k = 0; k < a->ncoarse; ++k) {
     seg.c[k] = a->clv[k];
@@ -237,6 +243,12 @@ void attach_coarse(const cga* a, libcga::NnSeg& seg) {
 }
 
 }  // namespace
+
+namespace libcga {
+// The NN search structures prepared on a handle (x directory, column table,
+// coarse levels or occupancy tree), for entry points in other files.
+void nn_attach(const cga_t* a, NnSeg& seg) { attach_coarse(a, seg); }
+}  // namespace libcga
 
 extern "C" {
 
@@ -778,6 +790,32 @@ void drop_coarse(cga* a) {
     a->cshift[k] = 0;
   }
   a->ncoarse = 0;
+  if (a->tmem != nullptr) dfree(A, a->has_alloc, a->tmem, a->stream);
+  a->tmem = nullptr;
+  a->tree = libcga::TreeView{};
+}
+
+// The occupancy tree of `a` (errors of its bounded waits land in a's header).
+int build_tree(cga* a, cudaStream_t s) {
+  const cga_allocator* A = a->has_alloc ? &a->alloc : nullptr;
+  const libcga::TreeLayout L = libcga::tree_layout(a->grid.bits, a->lv.cap);
+  const libcga::Tuning tu = libcga::tuning_for(a->grid.bits, a->lv.cap);
+  void* mem = dalloc(A, L.bytes, s);
+  if (mem == nullptr) return CGA_ERR_OOM;
+  void* scratch = dalloc(A, libcga::tree_scratch_bytes(L, tu.radix_bits), s);
+  if (scratch == nullptr) {
+    dfree(A, a->has_alloc, mem, s);
+    return CGA_ERR_OOM;
+  }
+  const int rc = cuda_rc(libcga::run_tree_build(a->lv, L, mem, scratch, tu, &a->lv.hdr->err, s));
+  dfree(A, a->has_alloc, scratch, s);
+  if (rc != CGA_OK) {
+    dfree(A, a->has_alloc, mem, s);
+    return rc;
+  }
+  a->tmem = mem;
+  a->tree = libcga::tree_view(L, mem);
+  return CGA_OK;
 }
 
 // Coarse level k of `a`: re-key the next finer level (the CGA itself for
@@ -855,7 +893,8 @@ int cga_nn_prepare_levels(cga_t* a, const uint32_t* shifts, uint32_t count, void
   if (a == nullptr || a->view || count > CGA_NN_MAX_LEVELS || (count > 0 && shifts == nullptr)) {
     return CGA_ERR_INVALID_ARG;
   }
-  for (uint32_t k = 0; k < count; ++k) {
+  const bool tree = count == 1 && shifts[0] == CGA_NN_TREE;
+  for (uint32_t k = 0; k < count && !tree; ++k) {
     if (shifts[k] < 1 || shifts[k] >= a->grid.bits || shifts[k] > CGA_NN_MAX_SHIFT ||
         (k > 0 && shifts[k] <= shifts[k - 1])) {
       return CGA_ERR_INVALID_ARG;
@@ -885,6 +924,11 @@ int cga_nn_prepare_levels(cga_t* a, const uint32_t* shifts, uint32_t count, void
     }
     a->zrmem = zm;
     a->ctab = static_cast<uint4*>(zm);
+  }
+  if (tree) {
+    const int rc = build_tree(a, s);
+    if (rc != CGA_OK) drop_coarse(a);
+    return rc;
   }
   for (uint32_t k = 0; k < count; ++k) {
     const int rc = build_coarse_level(a, (int)k, shifts[k], s);
@@ -916,15 +960,15 @@ int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shi
   int rc = cuda_rc(cudaEventCreate(&e0));
   if (rc == CGA_OK) rc = cuda_rc(cudaEventCreate(&e1));
   // candidates (coarse shifts, 0 = unused): the fine search alone, one coarse
-  // level of 4..32 voxel cells, two coarse levels
+  // level of 4..32 voxel cells, two coarse levels, the occupancy tree
   static const uint32_t cand[CGA_NN_AUTOTUNE_CANDIDATES][CGA_NN_MAX_LEVELS] = {
-      {0, 0}, {2, 0}, {3, 0}, {4, 0}, {5, 0}, {2, 5}, {3, 6}, {3, 7}, {4, 8}};
+      {0, 0}, {2, 0}, {3, 0}, {4, 0}, {5, 0}, {2, 5}, {3, 6}, {3, 7}, {4, 8}, {CGA_NN_TREE, 0}};
   float best_ms = 0.0f;
   int best = 0;
   bool have = false;
   for (int k = 0; k < CGA_NN_AUTOTUNE_CANDIDATES && rc == CGA_OK; ++k) {
     const uint32_t count = cand[k][0] == 0 ? 0u : (cand[k][1] == 0 ? 1u : 2u);
-    if (count > 0 && cand[k][count - 1] >= a->grid.bits) {
+    if (count > 0 && cand[k][0] != CGA_NN_TREE && cand[k][count - 1] >= a->grid.bits) {
       if (times_ms) times_ms[k] = -1.0f;
       continue;
     }

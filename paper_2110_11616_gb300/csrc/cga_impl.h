@@ -72,8 +72,9 @@ struct SortSeg {
   uint32_t has_x;
   // projection input: the source CGA and the plane
   Levels src;
-  int32_t plane;      // 0 xy, 1 xz, 2 yz: 2D re-key; 3: coarsen (3D, >> shift)
-  uint32_t shift;     // plane 3: coarse cell = 2^shift voxels per axis
+  int32_t plane;      // 0 xy, 1 xz, 2 yz: 2D re-key; 3: coarsen (3D, >> shift);
+                      // 4: occupancy-tree key (tree_key of x, y, z over `shift` levels)
+  uint32_t shift;     // plane 3: coarse cell = 2^shift voxels per axis; plane 4: levels
   uint32_t from_cga;  // 1: keys come from src (projection), 0: from xyz
   // common
   uint32_t n_host;      // element count when known on the host (build)
@@ -117,6 +118,12 @@ void init_nn_kernels();
 // histograms filled, look-back words zeroed).
 cudaError_t run_radix_passes(int S, uint32_t total_tiles, uint32_t max_passes, bool key64,
                              const SortScratch& sc, cudaStream_t stream);
+
+// Only key generation and the radix passes of 64-bit keys (segment table on
+// the device; no compaction): the sorted keys end in keys0 after an even
+// number of passes, in keys1 after an odd one.
+cudaError_t run_sort_keys_device(int S, uint32_t total_tiles, uint32_t max_passes,
+                                 const SortScratch& sc, cudaStream_t stream);
 
 // Sort pipeline with the segment table already on the device (sc.segs).
 cudaError_t run_sort_device(int S, uint32_t total_tiles, uint32_t max_passes, bool key64,
@@ -279,6 +286,54 @@ cudaError_t run_project_xy_device(const ProjPair* d_pairs, int S, uint64_t max_c
 // Morton curve so that neighbouring warps search neighbouring space.
 constexpr int kMaxCoarse = 2;
 
+// Occupancy tree of a CGA for NN search (cga_nn_prepare_levels with
+// CGA_NN_TREE): a 64-ary tree over the grid in which a node of level l covers
+// 4^l voxels per axis and has up to 4 x 4 x 4 children of level l - 1.  Child
+// c = cx << 4 | cy << 2 | cz (each 0..3), so the bit order of a node's child
+// set is the key order (x, then y, then z) of its children.  Level 1 nodes
+// (bricks) hold their 64 voxels as occupancy bits; the root is level
+// tree_levels(bits), with node 0 of that level the only one.
+constexpr int kTreeMaxLevels = 8;  // ceil(16 / 2)
+inline uint32_t tree_levels(uint32_t bits) { return (bits + 1) / 2; }
+// Key of voxel (x, y, z) in the tree's order: bits [6(l-1), 6l) hold the
+// child index (c = cx << 4 | cy << 2 | cz) of the voxel's level-(l-1) cell
+// inside its level-l cell, for l = 1..levels.  Ascending keys list the
+// voxels brick by brick in a depth-first walk of the tree.
+__host__ __device__ inline unsigned long long tree_key(uint32_t x, uint32_t y, uint32_t z,
+                                                       uint32_t levels) {
+  unsigned long long k = 0;
+  for (uint32_t l = 0; l < levels; ++l) {
+    const uint32_t c = ((x >> (2 * l)) & 3u) << 4 | ((y >> (2 * l)) & 3u) << 2 | ((z >> (2 * l)) & 3u);
+    k |= (unsigned long long)c << (6 * l);
+  }
+  return k;
+}
+struct TreeView {
+  const unsigned long long* brick;        // level 1: voxel occupancy of each brick
+  const uint4* node[kTreeMaxLevels + 1];  // level l >= 2: {child set lo, hi, first child, 0}
+  uint32_t cap[kTreeMaxLevels + 1];       // entries reserved per level (a search never reads beyond)
+  uint32_t levels;                        // 0: no tree
+};
+// Capacity of every level (cap[0]: voxels) and the bytes of the tree arrays
+// (offsets from one base: off[1] bricks, off[l] nodes of level l, off[0] the
+// device counts, one 32-bit word per level).
+struct TreeLayout {
+  uint64_t cap[kTreeMaxLevels + 1];
+  size_t off[kTreeMaxLevels + 1];
+  size_t bytes;
+  uint32_t levels;
+};
+TreeLayout tree_layout(uint32_t bits, uint64_t cap);
+// Scratch of one tree build (the Morton-key sort and the per-level
+// look-back words).
+size_t tree_scratch_bytes(const TreeLayout& L, uint32_t radix_bits);
+// Build the tree of a into mem (laid out by L): Morton keys of the voxels,
+// sorted by radix passes, then one compaction per level from the bricks up.
+// Errors of a bounded wait are recorded in err.
+cudaError_t run_tree_build(const Levels& a, const TreeLayout& L, void* mem, void* scratch,
+                           const Tuning& tu, unsigned int* err, cudaStream_t stream);
+TreeView tree_view(const TreeLayout& L, void* mem);
+
 struct NnSeg {
   Levels a;
   // optional coarse levels (ncoarse = 0..kMaxCoarse, coarsest last): c[k] is
@@ -303,6 +358,8 @@ struct NnSeg {
   // optional column table of `a` (cga_nn_prepare): per column {first voxel,
   // end, lowest z | highest z << 16, 0}
   const uint4* ctab;
+  // optional occupancy tree of `a`; when present the tree search runs
+  TreeView tree;
   float scale;
   float off[3];
   const float* q;
@@ -337,11 +394,14 @@ cudaError_t nn_upload_one(const NnSeg& h_seg, const NnTables& t, cudaStream_t st
 cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
                                cudaStream_t stream);
 cudaError_t run_nn_search(const NnSeg& seg, const unsigned long long* order, cudaStream_t stream);
+// Search kernel a segment needs: 0 the fine search, 1 or 2 the coarse
+// levels, 3 the occupancy tree.
+inline uint32_t nn_kind(const NnSeg& s) { return s.tree.levels > 0 ? 3u : s.ncoarse; }
 // Run with the tables on the device (capturable: memsets and kernels only).
-// max_coarse: the most coarse levels any segment carries (selects the kernel
-// instantiation).
+// max_kind: the largest nn_kind of any segment (selects the kernel
+// instantiation; kind 3 searches segments without a tree by the fine search).
 cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream,
-                          uint32_t max_coarse = 0);
+                          uint32_t max_kind = 0);
 
 // For each slab k of the coarse CGA c (cells of 2^shift voxels), xs[k] = first
 // index of a's X_index whose x >> shift equals c's X_index[k]; xs[h_c] = h_a.

@@ -257,6 +257,9 @@ constexpr int kQueryLimit = 1 << 30;
 #ifndef CGA_NN_COARSE_BLOCKS
 #define CGA_NN_COARSE_BLOCKS 5
 #endif
+#ifndef CGA_NN_TREE_BLOCKS
+#define CGA_NN_TREE_BLOCKS 4
+#endif
 
 struct Qry {
   int x, y, z;
@@ -530,16 +533,189 @@ __device__ void search_levels(const NnSeg& sg, const Qry& q, uint32_t lane, Best
   }
 }
 
+// ---- occupancy-tree search (cga_nn_prepare_levels with CGA_NN_TREE) -------
+//
+// A depth-first descent of the 64-ary occupancy tree (k_tree.cu), nearest
+// child first.  The warp keeps one frame per level on the path: the node's
+// child set, the children still to visit and the node's cell.  Each step the
+// lanes bound two children each (box distance of the child cell; lane i takes
+// children i and i + 32), drop every child whose bound exceeds the best
+// distance so far, and the warp enters the remaining child with the least
+// bound.  Children of a level-2 node are bricks: their 64 voxels are examined
+// at once (two per lane).  A child is dropped only when its bound exceeds the
+// best distance, and the best distance never falls below the final one, so
+// every cell holding a voxel at the final distance is entered: the result is
+// Eq. 8's nearest voxel, ties to the smaller key.
+
+// Squared distance from q to the cell [lo, lo + s - 1] along one axis.
+__device__ __forceinline__ unsigned long long axis_lb2(int q, uint32_t lo, uint32_t s) {
+  const unsigned long long d = interval_dist(q, lo, s);
+  return d * d;
+}
+
+struct TreeFrame {
+  unsigned long long mask, rem;
+  uint32_t first, ox, oy, oz;
+};
+
+// The best (distance^2, key) of the tree search.
+struct BestKey {
+  unsigned long long d2, key;
+  // Lexicographic minimum of the lanes' (d, k), by 32-bit warp reductions.
+  __device__ __forceinline__ void warp_min_of(unsigned long long d, unsigned long long k) {
+    const uint32_t full = 0xffffffffu;
+    const uint32_t dh = (uint32_t)(d >> 32), dl = (uint32_t)d;
+    const uint32_t mh = __reduce_min_sync(full, dh);
+    const uint32_t ml = __reduce_min_sync(full, dh == mh ? dl : full);
+    const bool at = dh == mh && dl == ml;
+    const uint32_t kh = __reduce_min_sync(full, at ? (uint32_t)(k >> 32) : full);
+    const uint32_t kl = __reduce_min_sync(full, at && (uint32_t)(k >> 32) == kh ? (uint32_t)k : full);
+    d2 = ((unsigned long long)mh << 32) | ml;
+    key = ((unsigned long long)kh << 32) | kl;
+  }
+};
+
+// The voxels of the brick at brick coordinates (bx, by, bz) with occupancy
+// m: lane i takes voxels i and i + 32 (bit c = cx << 4 | cy << 2 | cz).
+__device__ __forceinline__ void tree_brick(unsigned long long m, uint32_t bx, uint32_t by,
+                                           uint32_t bz, const Qry& q, uint32_t b, uint32_t lane,
+                                           BestKey& best) {
+  const uint32_t y = (by << 2) + ((lane >> 2) & 3u), z = (bz << 2) + (lane & 3u);
+  const uint32_t x0 = (bx << 2) + (lane >> 4);
+  const unsigned long long dy = absdiff(y, q.y), dz = absdiff(z, q.z);
+  const unsigned long long dyz = dy * dy + dz * dz;
+  const unsigned long long yz = ((unsigned long long)y << b) | z;
+  unsigned long long cd = ~0ull, ck = ~0ull;
+  if ((m >> lane) & 1ull) {
+    const unsigned long long dx = absdiff(x0, q.x);
+    cd = dx * dx + dyz;
+    ck = ((unsigned long long)x0 << (2 * b)) | yz;
+  }
+  if ((m >> (lane + 32)) & 1ull) {
+    const unsigned long long dx = absdiff(x0 + 2, q.x);
+    const unsigned long long d = dx * dx + dyz;
+    if (d < cd) {  // on a tie the smaller x (smaller key) stays
+      cd = d;
+      ck = ((unsigned long long)(x0 + 2) << (2 * b)) | yz;
+    }
+  }
+  const bool better = cd < best.d2 || (cd == best.d2 && ck < best.key);
+  if (__any_sync(0xffffffffu, better)) {
+    best.warp_min_of(better ? cd : best.d2, better ? ck : best.key);
+  }
+}
+
+__device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFrame* fr,
+                            BestKey& best) {
+  const uint32_t full = 0xffffffffu;
+  const TreeView& tv = sg.tree;
+  const uint32_t T = tv.levels, b = sg.a.bits;
+  if (T == 1) {
+    tree_brick(__ldg(tv.brick), 0, 0, 0, q, b, lane, best);
+    return;
+  }
+  uint32_t lvl = T;
+  const uint4 r0 = __ldg(tv.node[T]);
+  unsigned long long mask = r0.x | ((unsigned long long)r0.y << 32), rem = mask;
+  uint32_t first = r0.z, ox = 0, oy = 0, oz = 0;
+  int depth = 0;
+  const uint32_t cy = (lane >> 2) & 3u, cz = lane & 3u, cx0 = lane >> 4;
+  while (true) {
+    const uint32_t sh = 2 * (lvl - 1), s = 1u << sh;
+    const unsigned long long dyz = axis_lb2(q.y, ((oy << 2) + cy) << sh, s) +
+                                   axis_lb2(q.z, ((oz << 2) + cz) << sh, s);
+    const uint32_t bx = (ox << 2) + cx0;
+    const unsigned long long lb0 = axis_lb2(q.x, bx << sh, s) + dyz;
+    const unsigned long long lb1 = axis_lb2(q.x, (bx + 2) << sh, s) + dyz;
+    const bool in0 = ((rem >> lane) & 1ull) && lb0 <= best.d2;
+    const bool in1 = ((rem >> (lane + 32)) & 1ull) && lb1 <= best.d2;
+    const uint32_t s0 = __ballot_sync(full, in0), s1 = __ballot_sync(full, in1);
+    if ((s0 | s1) == 0u) {
+      if (depth == 0) break;
+      --depth;
+      ++lvl;
+      __syncwarp();
+      const TreeFrame f = fr[depth];
+      mask = f.mask;
+      rem = f.rem;
+      first = f.first;
+      ox = f.ox;
+      oy = f.oy;
+      oz = f.oz;
+      continue;
+    }
+    // the surviving child with the least bound
+    unsigned long long v = in0 ? lb0 : ~0ull;
+    uint32_t c = lane;
+    if (in1 && lb1 < v) {
+      v = lb1;
+      c = lane + 32;
+    }
+    const uint32_t vh = (uint32_t)(v >> 32), vl = (uint32_t)v;
+    const uint32_t mh = __reduce_min_sync(full, vh);
+    const uint32_t ml = __reduce_min_sync(full, vh == mh ? vl : full);
+    const uint32_t win = __ballot_sync(full, vh == mh && vl == ml);
+    const uint32_t cs = __shfl_sync(full, c, __ffs(win) - 1);
+    rem = ((((unsigned long long)s1) << 32) | s0) & ~(1ull << cs);
+    const uint32_t ci = first + (uint32_t)__popcll(mask & ((1ull << cs) - 1ull));
+    const uint32_t nx = (ox << 2) + (cs >> 4), ny = (oy << 2) + ((cs >> 2) & 3u),
+                   nz = (oz << 2) + (cs & 3u);
+    if (ci >= tv.cap[lvl - 1]) continue;  // never for a tree built by k_tree_level
+    if (lvl > 2) {
+      __syncwarp();
+      if (lane == 0) fr[depth] = TreeFrame{mask, rem, first, ox, oy, oz};
+      __syncwarp();
+      ++depth;
+      --lvl;
+      const uint4 r = __ldg(tv.node[lvl] + ci);
+      mask = r.x | ((unsigned long long)r.y << 32);
+      rem = mask;
+      first = r.z;
+      ox = nx;
+      oy = ny;
+      oz = nz;
+    } else {
+      tree_brick(__ldg(tv.brick + ci), nx, ny, nz, q, b, lane, best);
+    }
+  }
+}
+
+// CGA index of the stored voxel with key `key` (the Sec. V-A lookup by the
+// whole warp: x directory or X_index, the slab's Y range, the column's Z
+// range).
+__device__ __forceinline__ uint32_t stored_index(const NnSeg& sg, unsigned long long key) {
+  const Levels& a = sg.a;
+  const uint32_t b = a.bits, mk = (1u << b) - 1u;
+  const uint32_t x = (uint32_t)(key >> (2 * b)), y = (uint32_t)(key >> b) & mk,
+                 z = (uint32_t)key & mk;
+  const uint32_t h = (uint32_t)a.hdr->cnt[2];
+  const uint32_t slab = sg.xdir != nullptr ? __ldg(sg.xdir + x) : warp_lower_bound_u16(a.idx2, 0, h, x);
+  const uint32_t ys = __ldg(a.ptr2 + slab), ye = __ldg(a.ptr2 + slab + 1);
+  const uint32_t c = warp_lower_bound_u16(a.idx1, ys, ye, y);
+  uint32_t zs, ze;
+  if (sg.ctab != nullptr) {
+    const uint4 e = __ldg(sg.ctab + c);
+    zs = e.x;
+    ze = e.y;
+  } else {
+    zs = __ldg(a.ptr1 + c);
+    ze = __ldg(a.ptr1 + c + 1);
+  }
+  return warp_lower_bound_u16(a.idx0, zs, ze, z);
+}
+
 // NC: the most coarse levels any segment of the launch carries (0, 1 or 2).
 // The fine-only instantiation is held to 40 registers (six blocks per SM),
 // the coarse ones to 48 (five blocks per SM): the extra warps hide more of
 // the search's load latency than the spilled values cost (eight and six
 // blocks respectively spill enough to be slower).
 template <int NC>
-__global__ void __launch_bounds__(256, NC > 0 ? CGA_NN_COARSE_BLOCKS : CGA_NN_FINE_BLOCKS) k_nn_warp(const NnSeg* __restrict__ segs, int S,
-                                                 NnSeg inline_seg, uint32_t total_slots,
-                                                 const unsigned long long* __restrict__ order,
-                                                 const unsigned int* __restrict__ order_err) {
+__global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
+                                               : (NC > 0 ? CGA_NN_COARSE_BLOCKS : CGA_NN_FINE_BLOCKS))
+    k_nn_warp(const NnSeg* __restrict__ segs, int S, NnSeg inline_seg, uint32_t total_slots,
+              const unsigned long long* __restrict__ order,
+              const unsigned int* __restrict__ order_err) {
+  __shared__ TreeFrame s_fr[NC == 3 ? 8 * kTreeMaxLevels : 1];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const bool sorted = order != nullptr && (order_err == nullptr || *order_err == 0u);
@@ -582,11 +758,27 @@ __global__ void __launch_bounds__(256, NC > 0 ? CGA_NN_COARSE_BLOCKS : CGA_NN_FI
     const uint32_t cqx = (uint32_t)min(max(qx, 0), top);
     const uint32_t cqy = (uint32_t)min(max(qy, 0), top);
     const uint32_t cqz = (uint32_t)min(max(qz, 0), top);
+    if constexpr (NC == 3) {
+      if (sg.tree.levels > 0) {
+        BestKey bk{~0ull, ~0ull};
+        search_tree(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane,
+                    s_fr + (threadIdx.x >> 5) * kTreeMaxLevels, bk);
+        const uint32_t ix = bk.d2 != ~0ull ? stored_index(sg, bk.key) : 0xffffffffu;
+        if (lane == 0) {
+          sg.idx[j] = ix;
+          sg.d2[j] = bk.d2;
+        }
+        continue;
+      }
+    }
     Best best{~0ull, 0xffffffffu};
-    if (NC >= 2 && sg.ncoarse >= 2) {
-      if constexpr (NC >= 2) search_levels<2>(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane, best);
-    } else if (NC >= 1 && sg.ncoarse >= 1) {
-      if constexpr (NC >= 1) search_levels<1>(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane, best);
+    // (the tree kernel searches a segment without a tree by the fine search)
+    if (NC == 2 && sg.ncoarse >= 2) {
+      if constexpr (NC == 2) search_levels<2>(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane, best);
+    } else if ((NC == 1 || NC == 2) && sg.ncoarse >= 1) {
+      if constexpr (NC == 1 || NC == 2) {
+        search_levels<1>(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane, best);
+      }
     } else {
       search_fine(a, sg.xdir, sg.ctab, h, qx, qy, qz, cqx, cqy, cqz, lane, best);
     }
@@ -653,13 +845,14 @@ cudaError_t nn_upload_one(const NnSeg& h_seg, const NnTables& t, cudaStream_t st
 
 // Blocks of k_nn_warp<kind> that fit on one SM (queried once per kind).
 static uint32_t resident_blocks(uint32_t kind) {
-  static std::atomic<int> cache[3] = {{0}, {0}, {0}};
+  static std::atomic<int> cache[4] = {{0}, {0}, {0}, {0}};
   int n = cache[kind].load(std::memory_order_relaxed);
   if (n == 0) {
     cudaError_t e = cudaErrorInvalidValue;
     if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_warp<0>, 256, 0);
     if (kind == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_warp<1>, 256, 0);
     if (kind == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_warp<2>, 256, 0);
+    if (kind == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_warp<3>, 256, 0);
     if (e != cudaSuccess || n <= 0) {
       cudaGetLastError();
       n = 4;
@@ -671,18 +864,21 @@ static uint32_t resident_blocks(uint32_t kind) {
 
 static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
                           uint32_t total_tiles, const unsigned long long* order,
-                          const unsigned int* order_err, uint32_t ncoarse,
+                          const unsigned int* order_err, uint32_t kind,
                           cudaStream_t stream) {
   const uint32_t total_slots = total_tiles * (uint32_t)kTile;
   // one wave: as many blocks as stay resident (the warps stride over the
   // query slots, so a second wave would only add its own tail)
-  const uint32_t kind = ncoarse >= 2 ? 2u : ncoarse;
+  kind = std::min(kind, 3u);
   const uint32_t blocks = std::min<uint32_t>((total_slots + 7) / 8,
                                              (uint32_t)device_sm_count() * resident_blocks(kind));
-  if (ncoarse >= 2) {
+  if (kind == 3) {
+    k_nn_warp<3><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
+                                             order_err);
+  } else if (kind == 2) {
     k_nn_warp<2><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
                                              order_err);
-  } else if (ncoarse == 1) {
+  } else if (kind == 1) {
     k_nn_warp<1><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
                                              order_err);
   } else {
@@ -693,7 +889,7 @@ static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
 }
 
 void init_nn_kernels() {
-  for (uint32_t k = 0; k < 3; ++k) resident_blocks(k);
+  for (uint32_t k = 0; k < 4; ++k) resident_blocks(k);
 }
 
 cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
@@ -710,12 +906,12 @@ cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
 
 cudaError_t run_nn_search(const NnSeg& seg, const unsigned long long* order, cudaStream_t stream) {
   if (seg.m == 0) return cudaSuccess;
-  launch_search(nullptr, 1, seg, seg.num_tiles, order, nullptr, seg.ncoarse, stream);
+  launch_search(nullptr, 1, seg, seg.num_tiles, order, nullptr, nn_kind(seg), stream);
   return cudaGetLastError();
 }
 
 cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream,
-                          uint32_t max_coarse) {
+                          uint32_t max_kind) {
   if (total_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(t.err, 0, sizeof(Header), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(t.sort.hist, 0, t.sort.zero_bytes, stream);
@@ -727,7 +923,7 @@ cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaSt
   if (e != cudaSuccess) return e;
   // four passes leave the sorted keys in keys0
   launch_search(t.segs, S, NnSeg{}, total_tiles,
-                static_cast<const unsigned long long*>(t.sort.keys0), &t.err->err, max_coarse,
+                static_cast<const unsigned long long*>(t.sort.keys0), &t.err->err, max_kind,
                 stream);
   return cudaGetLastError();
 }
@@ -737,16 +933,16 @@ cudaError_t run_nn(const NnSeg* h_segs, int S, uint32_t total_tiles, void* scrat
   if (total_tiles == 0) return cudaSuccess;
   if (scratch == nullptr) {
     if (S != 1) return cudaErrorInvalidValue;
-    launch_search(nullptr, 1, h_segs[0], total_tiles, nullptr, nullptr, h_segs[0].ncoarse,
+    launch_search(nullptr, 1, h_segs[0], total_tiles, nullptr, nullptr, nn_kind(h_segs[0]),
                   stream);
     return cudaGetLastError();
   }
   const NnTables t = nn_tables(scratch, total_tiles, S);
   const cudaError_t e = nn_upload(h_segs, S, t, stream);
   if (e != cudaSuccess) return e;
-  uint32_t max_coarse = 0;
-  for (int s = 0; s < S; ++s) max_coarse = std::max(max_coarse, h_segs[s].ncoarse);
-  return run_nn_device(S, total_tiles, t, stream, max_coarse);
+  uint32_t max_kind = 0;
+  for (int s = 0; s < S; ++s) max_kind = std::max(max_kind, nn_kind(h_segs[s]));
+  return run_nn_device(S, total_tiles, t, stream, max_kind);
 }
 
 }  // namespace libcga

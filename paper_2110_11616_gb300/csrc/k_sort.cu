@@ -136,6 +136,8 @@ __global__ void __launch_bounds__(kThreads) k_keys_hist(const SortSeg* __restric
         if (sg.plane == 3) {
           const uint32_t L = sg.shift;
           key = ((K)(x >> L) << (2 * b)) | ((K)(y >> L) << b) | (K)(z >> L);
+        } else if (sg.plane == 4) {
+          key = (K)tree_key(x, y, z, sg.shift);
         } else {
           uint32_t u = x, v = y;
           if (sg.plane == 1) { u = x; v = z; }
@@ -462,6 +464,30 @@ static cudaError_t launch_pipeline(int S, uint32_t total_tiles, uint32_t max_pas
     k_compact<K, 2><<<total_tiles, kThreads, 0, stream>>>(sc.segs, S, k0, k1, sc.clook,
                                                           sc.counters + kMaxPasses);
   }
+  return cudaGetLastError();
+}
+
+template <typename K>
+static void launch_keys(int S, uint32_t total_tiles, const SortScratch& sc, cudaStream_t stream) {
+  const uint32_t ctas = std::min<uint32_t>(total_tiles, (uint32_t)device_sm_count() * 4);
+  const uint32_t per = (total_tiles + ctas - 1) / ctas;
+  K* k0 = static_cast<K*>(sc.keys0);
+  if (sc.radix_bits == 9) {
+    k_keys_hist<K, 9><<<ctas, kThreads, 0, stream>>>(sc.segs, S, total_tiles, per, k0, sc.hist);
+  } else {
+    k_keys_hist<K, 8><<<ctas, kThreads, 0, stream>>>(sc.segs, S, total_tiles, per, k0, sc.hist);
+  }
+  count_launch(1);
+}
+
+cudaError_t run_sort_keys_device(int S, uint32_t total_tiles, uint32_t max_passes,
+                                 const SortScratch& sc, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(sc.hist, 0, sc.zero_bytes, stream);
+  if (e != cudaSuccess || total_tiles == 0) return e;
+  e = init_sort_kernels();
+  if (e != cudaSuccess) return e;
+  launch_keys<unsigned long long>(S, total_tiles, sc, stream);
+  launch_passes<unsigned long long>(S, total_tiles, max_passes, sc, stream);
   return cudaGetLastError();
 }
 

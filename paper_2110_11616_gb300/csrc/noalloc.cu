@@ -15,6 +15,7 @@
 
 namespace libcga {
 void handle_parts(const cga_t* a, Levels* lv, cga_grid* g);
+void nn_attach(const cga_t* a, NnSeg& seg);
 }
 
 namespace {
@@ -73,10 +74,12 @@ extern "C" int cga_nn_query_noalloc(const cga_t* a, const float* d_q, uint64_t m
   seg.d2 = reinterpret_cast<unsigned long long*>(d_dist2);
   seg.tile_base = 0;
   seg.num_tiles = tiles;
+  // the search structures cga_nn_prepare_levels built on `a`, as cga_nn_query uses them
+  libcga::nn_attach(a, seg);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const libcga::NnTables t = libcga::nn_tables(scratch, tiles, 1);
   cudaError_t e = libcga::nn_upload_one(seg, t, s);
-  if (e == cudaSuccess) e = libcga::run_nn_device(1, tiles, t, s);
+  if (e == cudaSuccess) e = libcga::run_nn_device(1, tiles, t, s, libcga::nn_kind(seg));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return CGA_ERR_CUDA;

@@ -1,0 +1,161 @@
+"""GPU parity of the NN search over the occupancy tree (cga_nn_prepare_levels
+with CGA_NN_TREE): every answer equals the CPU oracle's exact NN (Eq. 7-8,
+smaller key on ties), bit for bit, on every grid width (1..16 bits: one to
+eight tree levels, odd widths whose root is only partly used), on uniform,
+surface and LiDAR clouds, for queries on the data, uniform in the box and far
+outside it, in query order and in Morton order, and through every NN entry
+point that reads a prepared handle."""
+import numpy as np
+import pytest
+
+from paper_2110_11616_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_11616_gb300 import build_ext, cga
+    build_ext.build()
+    cga.load()
+    return cga
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).reshape(-1, 3)).cuda()
+
+
+def check(cg, orc, a, oa, og, q, brute):
+    idx, d2 = cg.cga_nn_query(a, dev(q))
+    oi, od = (orc.nn_brute if brute else orc.nn_window)(oa, og, q)
+    np.testing.assert_array_equal(d2.cpu().numpy().view(np.uint64), od, err_msg="dist2")
+    np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), oi, err_msg="idx")
+
+
+@pytest.mark.parametrize("bits", [1, 2, 3, 4, 5, 7, 8, 11, 12, 13, 16])
+def test_tree_every_grid_width(cg, orc, bits):
+    pts = synth.uniform_cube(3000, seed=500 + bits)
+    g, og = cg.grid_from_box([0, 0, 0], 1.0, bits), orc.grid_from_box([0, 0, 0], 1.0, bits)
+    a = cg.cga_build(dev(pts), g)
+    cg.cga_nn_prepare(a, "tree")
+    q = np.concatenate([synth.uniform_queries(1500, 501, [0, 0, 0], 1.0),
+                        synth.uniform_queries(300, 502, [-3, -3, -3], 7.0), pts[:200]])
+    check(cg, orc, a, orc.build(pts, og), og, q, brute=True)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "surface", "lidar"])
+def test_tree_parity_clouds(cg, orc, kind):
+    """Near, uniform and far queries; the small batch runs in query order, the
+    tiled batch (above the Morton-sort threshold) in Morton order."""
+    if kind == "uniform":
+        pts = synth.uniform_cube(40_000, seed=510)
+        lo, ext, bits = [0.0] * 3, 1.0, 10
+    elif kind == "surface":
+        scene = synth.superellipsoid_scene(n_objects=16, seed=511, extent=100.0)
+        pts = synth.sample_surfaces(scene, 120_000, seed=512)
+        lo, ext, bits = [0.0] * 3, 100.0, 12
+    else:
+        sc = synth.lidar_sweeps(2, 64, 512, seed=513)
+        pts = sc.world.astype(np.float32)
+        lo, ext, bits = [-128.0] * 3, 256.0, 16
+    g, og = cg.grid_from_box(lo, ext, bits), orc.grid_from_box(lo, ext, bits)
+    a = cg.cga_build(dev(pts), g)
+    cg.cga_nn_prepare(a, "tree")
+    oa = orc.build(pts, og)
+    lo_a = np.asarray(lo, np.float64)
+    q = np.concatenate([
+        pts[:1500].astype(np.float64) + np.random.default_rng(514).normal(0, ext / 200, (1500, 3)),
+        synth.uniform_queries(2500, 515, lo, ext),
+        synth.uniform_queries(300, 516, lo_a - ext, 3 * ext),
+    ]).astype(np.float32)
+    check(cg, orc, a, oa, og, q, brute=False)
+    big = np.tile(q, (4, 1))
+    idx, d2 = cg.cga_nn_query(a, dev(big))
+    oi, od = orc.nn_window(oa, og, q)
+    assert np.array_equal(d2.cpu().numpy().view(np.uint64), np.tile(od, 4))
+    assert np.array_equal(idx.cpu().numpy().view(np.uint32), np.tile(oi, 4))
+
+
+def test_tree_ties_sentinels_and_empty(cg, orc):
+    ug = cg.make_grid(4, 1.0, (0.0, 0.0, 0.0))
+    oug = orc.Grid(4, 1.0, (0.0, 0.0, 0.0))
+    # equidistant voxels around (5, 5, 5), across brick boundaries (x = 4 | 5 ...)
+    vox = np.array([[6, 5, 5], [5, 6, 5], [5, 5, 6], [4, 5, 5], [5, 4, 5], [0, 0, 0], [2, 0, 0],
+                    [0, 2, 9], [0, 0, 11], [8, 8, 8], [7, 8, 8], [8, 7, 8], [8, 8, 7]], np.float32)
+    a = cg.cga_build(dev(vox), ug)
+    cg.cga_nn_prepare(a, "tree")
+    q = np.array([[5, 5, 5], [1, 0, 0], [0, 1, 10], [np.nan, 1, 1], [1, np.inf, 1],
+                  [-100, -100, -100], [3.5, 3.5, 3.5], [7.5, 7.5, 7.5], [1e9, -1e9, 1e9],
+                  [15, 15, 15], [4.2, 4.9, 5.1]], np.float32)
+    check(cg, orc, a, orc.build(vox, oug), oug, q, brute=True)
+    empty = cg.cga_build(dev(np.zeros((0, 3), np.float32)), ug)
+    cg.cga_nn_prepare(empty, "tree")
+    idx, d2 = cg.cga_nn_query(empty, dev(q))
+    assert np.all(idx.cpu().numpy().view(np.uint32) == 0xFFFFFFFF)
+    assert np.all(d2.cpu().numpy().view(np.uint64) == np.uint64(0xFFFFFFFFFFFFFFFF))
+
+
+def test_tree_full_lattice(cg):
+    """On a full k^3 lattice the nearest voxel is the query clamped into it."""
+    k = 21
+    ax = np.arange(k, dtype=np.float32)
+    vox = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3)
+    a = cg.cga_build(dev(vox), cg.make_grid(5, 1.0, (0.0, 0.0, 0.0)))
+    cg.cga_nn_prepare(a, "tree")
+    q = np.random.default_rng(517).uniform(-40, 60, size=(20_000, 3)).astype(np.float32)
+    idx, d2 = cg.cga_nn_query(a, dev(q))
+    qi = np.floor(q.astype(np.float64)).astype(np.int64)
+    c = np.clip(qi, 0, k - 1)
+    assert np.array_equal(d2.cpu().numpy(), ((qi - c) ** 2).sum(1))
+    assert np.array_equal(idx.cpu().numpy().astype(np.int64), c[:, 0] * k * k + c[:, 1] * k + c[:, 2])
+
+
+def test_tree_every_entry_point(cg, orc):
+    """The ordered two-step call, integer query voxels and a batch that mixes a
+    tree-prepared handle with unprepared and coarse-level ones all give the
+    oracle's answers."""
+    scene = synth.superellipsoid_scene(n_objects=8, seed=520, extent=100.0)
+    pts = synth.sample_surfaces(scene, 50_000, seed=521)
+    g, og = cg.grid_from_box([0.0] * 3, 100.0, 12), orc.grid_from_box([0.0] * 3, 100.0, 12)
+    a = cg.cga_build(dev(pts), g)
+    b = cg.cga_build(dev(pts[::2]), g)
+    c = cg.cga_build(dev(pts[1::3]), g)
+    cg.cga_nn_prepare(a, "tree")
+    cg.cga_nn_prepare(c, 3)
+    q = synth.uniform_queries(20_000, 522, [0.0] * 3, 100.0)
+    qd = dev(q)
+    order = cg.cga_nn_sort_queries(a, qd)
+    idx = torch.empty(len(q), dtype=torch.int32, device="cuda")
+    d2 = torch.empty(len(q), dtype=torch.int64, device="cuda")
+    cg.cga_nn_query_ordered(a, qd, order, idx, d2)
+    oa = orc.build(pts, og)
+    oi, od = orc.nn_window(oa, og, q)
+    assert np.array_equal(d2.cpu().numpy().view(np.uint64), od)
+    assert np.array_equal(idx.cpu().numpy().view(np.uint32), oi)
+    qv, valid = orc.query_voxels(og, q)
+    assert valid.all()
+    vi, vd = cg.cga_nn_query_voxels(a, torch.from_numpy(qv.astype(np.int32)).cuda())
+    assert np.array_equal(vd.cpu().numpy().view(np.uint64), od)
+    assert np.array_equal(vi.cpu().numpy().view(np.uint32), oi)
+    res = cg.cga_nn_query_batch([a, b, c], [qd, qd[:5000].contiguous(), qd[7:9000].contiguous()])
+    for (ri, rd), (h, qq) in zip(res, [(pts, q), (pts[::2], q[:5000]), (pts[1::3], q[7:9000])]):
+        ei, ed = orc.nn_window(orc.build(h, og), og, qq)
+        assert np.array_equal(rd.cpu().numpy().view(np.uint64), ed)
+        assert np.array_equal(ri.cpu().numpy().view(np.uint32), ei)
+
+
+def test_tree_replaced_by_other_preparations(cg, orc):
+    pts = synth.uniform_cube(30_000, seed=530)
+    g, og = cg.grid_from_box([0, 0, 0], 1.0, 11), orc.grid_from_box([0, 0, 0], 1.0, 11)
+    a = cg.cga_build(dev(pts), g)
+    oa = orc.build(pts, og)
+    q = synth.uniform_queries(10_000, 531, [-0.2] * 3, 1.4)
+    for prep in ["tree", (3,), "tree", (), "tree", (2, 5)]:
+        cg.cga_nn_prepare(a, prep)
+        check(cg, orc, a, oa, og, q, brute=False)
+    shifts, times = cg.cga_nn_autotune(a, dev(q))
+    assert (cg.NN_TREE,) in times and min(times, key=times.get) == shifts
+    check(cg, orc, a, oa, og, q, brute=False)
