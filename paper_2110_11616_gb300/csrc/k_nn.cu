@@ -555,7 +555,7 @@ __device__ __forceinline__ unsigned long long axis_lb2(int q, uint32_t lo, uint3
 
 struct TreeFrame {
   unsigned long long mask, rem;
-  uint32_t first, ox, oy, oz;
+  uint32_t first, ox, oy, oz, lvl, pad;
 };
 
 // The best (distance^2, key) of the tree search.
@@ -621,21 +621,59 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
   int depth = 0;
   const uint32_t cy = (lane >> 2) & 3u, cz = lane & 3u, cx0 = lane >> 4;
   while (true) {
-    const uint32_t sh = 2 * (lvl - 1), s = 1u << sh;
-    const unsigned long long dyz = axis_lb2(q.y, ((oy << 2) + cy) << sh, s) +
-                                   axis_lb2(q.z, ((oz << 2) + cz) << sh, s);
-    const uint32_t bx = (ox << 2) + cx0;
-    const unsigned long long lb0 = axis_lb2(q.x, bx << sh, s) + dyz;
-    const unsigned long long lb1 = axis_lb2(q.x, (bx + 2) << sh, s) + dyz;
-    const bool in0 = ((rem >> lane) & 1ull) && lb0 <= best.d2;
-    const bool in1 = ((rem >> (lane + 32)) & 1ull) && lb1 <= best.d2;
+    // Each lane loads the records of its two children (a node's child set and
+    // first child, or a brick's voxels) with their box codes, so that the
+    // chosen child's record is already in a register when the warp enters it.
+    // The bound of child c is the box of its occupied sub-cells (its box code)
+    // inside its cell of 4^(lvl-1) voxels per axis.
+    const uint32_t sh = 2 * (lvl - 1), ss = sh - 2;
+    const bool h0 = (rem >> lane) & 1ull, h1 = (rem >> (lane + 32)) & 1ull;
+    const uint32_t i0 = first + (uint32_t)__popcll(mask & ((1ull << lane) - 1ull));
+    const uint32_t i1 = first + (uint32_t)__popcll(mask & ((1ull << (lane + 32)) - 1ull));
+    const uint32_t cap = tv.cap[lvl - 1];
+    uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = make_uint4(0u, 0u, 0u, 0u);
+    if (lvl == 2) {
+      if (h0 && i0 < cap) {
+        const unsigned long long m0 = __ldg(tv.brick + i0);
+        c0 = make_uint4((uint32_t)m0, (uint32_t)(m0 >> 32), 0u, __ldg(tv.bcode + i0));
+      }
+      if (h1 && i1 < cap) {
+        const unsigned long long m1 = __ldg(tv.brick + i1);
+        c1 = make_uint4((uint32_t)m1, (uint32_t)(m1 >> 32), 0u, __ldg(tv.bcode + i1));
+      }
+    } else {
+      const uint4* nd = tv.node[lvl - 1];
+      if (h0 && i0 < cap) c0 = __ldg(nd + i0);
+      if (h1 && i1 < cap) c1 = __ldg(nd + i1);
+    }
+    const uint32_t Y = ((oy << 2) + cy) << sh, Z = ((oz << 2) + cz) << sh;
+    const uint32_t X0 = ((ox << 2) + cx0) << sh, X1 = X0 + (2u << sh);
+    unsigned long long lb0 = ~0ull, lb1 = ~0ull;
+    if (h0) {
+      const uint32_t k = c0.w;
+      const uint32_t lx = k & 3u, hx = (k >> 2) & 3u, ly = (k >> 4) & 3u, hy = (k >> 6) & 3u,
+                     lz = (k >> 8) & 3u, hz = (k >> 10) & 3u;
+      lb0 = axis_lb2(q.x, X0 + (lx << ss), (hx - lx + 1) << ss) +
+            axis_lb2(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
+            axis_lb2(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
+    }
+    if (h1) {
+      const uint32_t k = c1.w;
+      const uint32_t lx = k & 3u, hx = (k >> 2) & 3u, ly = (k >> 4) & 3u, hy = (k >> 6) & 3u,
+                     lz = (k >> 8) & 3u, hz = (k >> 10) & 3u;
+      lb1 = axis_lb2(q.x, X1 + (lx << ss), (hx - lx + 1) << ss) +
+            axis_lb2(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
+            axis_lb2(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
+    }
+    const bool in0 = h0 && i0 < cap && lb0 <= best.d2;
+    const bool in1 = h1 && i1 < cap && lb1 <= best.d2;
     const uint32_t s0 = __ballot_sync(full, in0), s1 = __ballot_sync(full, in1);
     if ((s0 | s1) == 0u) {
       if (depth == 0) break;
       --depth;
-      ++lvl;
       __syncwarp();
       const TreeFrame f = fr[depth];
+      lvl = f.lvl;
       mask = f.mask;
       rem = f.rem;
       first = f.first;
@@ -644,7 +682,8 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
       oz = f.oz;
       continue;
     }
-    // the surviving child with the least bound
+    // the surviving child with the least bound, and its record from the lane
+    // that loaded it
     unsigned long long v = in0 ? lb0 : ~0ull;
     uint32_t c = lane;
     if (in1 && lb1 < v) {
@@ -655,27 +694,47 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
     const uint32_t mh = __reduce_min_sync(full, vh);
     const uint32_t ml = __reduce_min_sync(full, vh == mh ? vl : full);
     const uint32_t win = __ballot_sync(full, vh == mh && vl == ml);
-    const uint32_t cs = __shfl_sync(full, c, __ffs(win) - 1);
+    const int owner = __ffs(win) - 1;
+    const uint32_t cs = __shfl_sync(full, c, owner);
+    const uint4 mine = cs >= 32 ? c1 : c0;
+    const uint32_t rx = __shfl_sync(full, mine.x, owner);
+    const uint32_t ry = __shfl_sync(full, mine.y, owner);
+    const uint32_t rz = __shfl_sync(full, mine.z, owner);
     rem = ((((unsigned long long)s1) << 32) | s0) & ~(1ull << cs);
-    const uint32_t ci = first + (uint32_t)__popcll(mask & ((1ull << cs) - 1ull));
     const uint32_t nx = (ox << 2) + (cs >> 4), ny = (oy << 2) + ((cs >> 2) & 3u),
                    nz = (oz << 2) + (cs & 3u);
-    if (ci >= tv.cap[lvl - 1]) continue;  // never for a tree built by k_tree_level
     if (lvl > 2) {
-      __syncwarp();
-      if (lane == 0) fr[depth] = TreeFrame{mask, rem, first, ox, oy, oz};
-      __syncwarp();
-      ++depth;
+      // the last surviving child replaces its parent's frame (nothing to come
+      // back to); otherwise the parent's frame is kept for the way back
+      if (rem != 0ull) {
+        __syncwarp();
+        if (lane == 0) fr[depth] = TreeFrame{mask, rem, first, ox, oy, oz, lvl, 0u};
+        __syncwarp();
+        ++depth;
+      }
       --lvl;
-      const uint4 r = __ldg(tv.node[lvl] + ci);
-      mask = r.x | ((unsigned long long)r.y << 32);
+      mask = rx | ((unsigned long long)ry << 32);
       rem = mask;
-      first = r.z;
+      first = rz;
       ox = nx;
       oy = ny;
       oz = nz;
     } else {
-      tree_brick(__ldg(tv.brick + ci), nx, ny, nz, q, b, lane, best);
+      tree_brick(rx | ((unsigned long long)ry << 32), nx, ny, nz, q, b, lane, best);
+      if (rem == 0ull) {
+        // the level-2 node is done: back to the nearest kept frame
+        if (depth == 0) break;
+        --depth;
+        __syncwarp();
+        const TreeFrame f = fr[depth];
+        lvl = f.lvl;
+        mask = f.mask;
+        rem = f.rem;
+        first = f.first;
+        ox = f.ox;
+        oy = f.oy;
+        oz = f.oz;
+      }
     }
   }
 }

@@ -2,12 +2,15 @@
 bench.py times.
 
 Every CGA array (builds, merges, projections, decode) is compared whole with
-the CPU oracle.  NN: a seeded sample of queries is compared with the oracle's
-window search one by one; every query's (idx, dist2) pair is checked for
-consistency (dist2 is the squared distance from the query voxel to the voxel
-at idx) on the whole set.
+the CPU oracle.  NN: the plain configuration's 10k queries and all 1M LiDAR
+queries are compared with the oracle's window search one by one (the LiDAR
+check under the fine search, the occupancy tree and the autotuned strategy);
+elsewhere a seeded sample is compared and every query's (idx, dist2) pair is
+checked for consistency (dist2 is the squared distance from the query voxel
+to the voxel at idx) on the whole set.
 """
 import numpy as np
+import oracle_threads
 import pytest
 
 from paper_2110_11616_gb300 import synth
@@ -113,6 +116,17 @@ def test_config_lidar_frames(cg, orc):
     ow = merge_tree(os_, orc.merge)
     assert_cga(gw, ow, "world")
     assert_2d(cg.cga_project(gw, "xy"), orc.project(ow, "xy"), "xy")
-    check_nn(cg, orc, gw, ow, og, q, n_sample=3000, seed=9)
+    # all 1M answers against the oracle (threads over query chunks), for the
+    # fine search, the occupancy tree and the strategy cga_nn_autotune picks
+    # on the benchmark's 64k sample (the launch configuration bench.py times)
+    oi, od = oracle_threads.nn_window(orc, ow, og, q)
+    for prep in [(), "tree", "autotune"]:
+        if prep == "autotune":
+            cg.cga_nn_autotune(gw, dev(q[:65536]))
+        else:
+            cg.cga_nn_prepare(gw, prep)
+        idx, d2 = cg.cga_nn_query(gw, dev(q))
+        np.testing.assert_array_equal(d2.cpu().numpy().view(np.uint64), od, err_msg=f"{prep} dist2")
+        np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), oi, err_msg=f"{prep} idx")
     dec = cg.cga_decode(gw).cpu().numpy().astype(np.uint32)
     np.testing.assert_array_equal(dec, orc.decode(ow))

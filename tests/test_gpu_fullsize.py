@@ -3,15 +3,18 @@ the same GPU generators and calls bench.py times.
 
 Surface (30M points, b = 12): every CGA array of both halves, the merge, the
 three projections and the decode is compared whole with the CPU oracle; NN
-runs over all 8M queries through one coarse level, a seeded sample is
-compared with the oracle's window search one by one, and every answer is
-checked for consistency with the decoded voxels.
+runs over all 8M queries with the strategy cga_nn_autotune picks (as
+bench.py does), a seeded sample of 4000 on-surface and 20000 uniform queries
+is compared with the oracle's window search one by one (threads over query
+chunks), and every answer is checked for consistency with the decoded
+voxels.
 
 Batched (512 clouds): the pipeline is replayed from its CUDA graph; a seeded
 sample of clouds (with the smallest and the largest) is compared whole with
 the oracle: cloud, twin, merge, xy projection and all 4096 NN answers.
 """
 import numpy as np
+import oracle_threads
 import pytest
 
 from paper_2110_11616_gb300 import synth
@@ -64,7 +67,10 @@ def test_config_surface_30M(cg, orc):
     mg = cg.cga_merge(a, b, allocator=None)
     planes = ["xy", "xz", "yz"]
     pr = cg.cga_project_batch([mg] * 3, planes, allocator=None)
-    cg.cga_nn_prepare(mg, (2,))
+    # the NN strategy bench.py times: cga_nn_autotune on the same 64k sample
+    gen = torch.Generator("cuda").manual_seed(7)
+    sample = q[torch.randperm(m, device="cuda", generator=gen)[:65536]].contiguous()
+    chosen, _ = cg.cga_nn_autotune(mg, sample)
     order = torch.empty(m, dtype=torch.int64, device="cuda")
     idx = torch.empty(m, dtype=torch.int32, device="cuda")
     d2 = torch.empty(m, dtype=torch.int64, device="cuda")
@@ -88,12 +94,14 @@ def test_config_surface_30M(cg, orc):
     qh = host(q)
     gi = host(idx).view(np.uint32)
     gd = host(d2).view(np.uint64)
+    # 4000 on-surface and 20000 uniform (far) queries against the oracle's
+    # window search, on every host core
     rng = np.random.default_rng(9)
-    pick = np.concatenate([rng.choice(m // 2, 600, replace=False),
-                           m // 2 + rng.choice(m // 2, 40, replace=False)])
-    oi, od = orc.nn_window(om, og, qh[pick])
-    np.testing.assert_array_equal(gd[pick], od, err_msg="sampled dist2")
-    np.testing.assert_array_equal(gi[pick], oi, err_msg="sampled idx")
+    pick = np.concatenate([rng.choice(m // 2, 4_000, replace=False),
+                           m // 2 + rng.choice(m // 2, 20_000, replace=False)])
+    oi, od = oracle_threads.nn_window(orc, om, og, qh[pick])
+    np.testing.assert_array_equal(gd[pick], od, err_msg=f"sampled dist2 ({chosen})")
+    np.testing.assert_array_equal(gi[pick], oi, err_msg=f"sampled idx ({chosen})")
     # every answer: a stored voxel at exactly the reported squared distance
     assert np.all(gi < u)
     qv, ok = orc.query_voxels(og, qh)

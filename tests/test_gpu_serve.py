@@ -112,3 +112,83 @@ def test_server_rejects_bad_requests(cg):
         server.submit_nn(0, big, idx, d2)   # footprint above the 1 MiB budget
     assert e.value.code == cg.ERR_OOM
     server.free()
+
+
+def test_served_results_match_oracle(cg, orc):
+    """Served results against the CPU oracle at serving sizes: a pool of six
+    LiDAR and surface clouds of 0.1M to 4M points (16-bit grid), NN requests
+    of up to 1M jittered queries and merge + projection requests, all in one
+    continuous-batching mix.  Every merge and projection is compared whole
+    with orc.merge and orc.project; for every NN request a seeded sample of
+    queries is compared with the oracle's window search and every answer is
+    checked to be a stored voxel at exactly the reported squared distance."""
+    import oracle_threads
+    from paper_2110_11616_gb300 import synth_gpu
+    g = cg.grid_from_box([-128.0] * 3, 256.0, 16)
+    og = orc.grid_from_box([-128.0] * 3, 256.0, 16)
+    sizes = [100_000, 4_000_000, 350_000, 1_500_000, 800_000, 2_500_000]
+    pool, opool, pts = [], [], []
+    for i, n in enumerate(sizes):
+        p = (synth_gpu.lidar_cloud(n, seed=700 + i) if i % 2 == 0 else
+             synth_gpu.surface_cloud(n, seed=700 + i, n_objects=40))
+        if i % 2 == 1:  # surface clouds centred in the LiDAR box
+            p = (p - 50.0).contiguous()
+        pool.append(cg.cga_build(p, g))
+        ph = p.cpu().numpy()
+        opool.append(orc.build(ph, og))
+        pts.append(p)
+    rng = np.random.default_rng(701)
+    reqs = []
+    for r in range(24):
+        if r % 3 != 2:
+            a = int(rng.integers(len(pool)))
+            m = 1_000_000 if r == 0 else int(np.exp(rng.uniform(0, np.log(1_000_000))))
+            q = synth_gpu.jitter_queries(pts[a], m, 0.2, seed=7000 + r)
+            reqs.append(("nn", a, q))
+        else:
+            a, b = (int(v) for v in rng.integers(len(pool), size=2))
+            reqs.append(("mp", a, b, ["xy", "xz", "yz"][int(rng.integers(3))]))
+    server = cg.Server(pool, memory_budget=8 << 30, slots=4, max_batch=16)
+    tickets = {}
+    for req in reqs:
+        if req[0] == "nn":
+            m = req[2].shape[0]
+            idx = torch.empty(m, dtype=torch.int32, device="cuda")
+            d2 = torch.empty(m, dtype=torch.int64, device="cuda")
+            tickets[server.submit_nn(req[1], req[2], idx, d2)] = (req, idx, d2)
+        else:
+            tickets[server.submit_merge_project(req[1], req[2], req[3])] = (req, None, None)
+    server.drain()
+    done = server.poll(max_n=len(reqs) + 10)
+    assert len(done) == len(reqs)
+    decoded = {}
+    for c in done:
+        assert c["status"] == cg.OK
+        req, idx, d2 = tickets[c["ticket"]]
+        if req[0] == "nn":
+            a = req[1]
+            oa = opool[a]
+            qh = req[2].cpu().numpy()
+            gi = idx.cpu().numpy().view(np.uint32)
+            gd = d2.cpu().numpy().view(np.uint64)
+            pick = np.random.default_rng(702 + c["ticket"]).choice(
+                len(qh), size=min(3000, len(qh)), replace=False)
+            oi, od = oracle_threads.nn_window(orc, oa, og, qh[pick])
+            np.testing.assert_array_equal(gd[pick], od, err_msg=f"request {c['ticket']} dist2")
+            np.testing.assert_array_equal(gi[pick], oi, err_msg=f"request {c['ticket']} idx")
+            if a not in decoded:
+                decoded[a] = orc.decode(oa).astype(np.int64)
+            qv, ok = orc.query_voxels(og, qh)
+            assert ok.all() and np.all(gi < oa.u)
+            rd = ((qv - decoded[a][gi]) ** 2).sum(1).astype(np.uint64)
+            np.testing.assert_array_equal(rd, gd, err_msg=f"request {c['ticket']} consistency")
+        else:
+            om = orc.merge(opool[req[1]], opool[req[2]])
+            got_m = c["merged"].download()
+            for k in ("X_index", "X_pointer", "Y_index", "Y_pointer", "Z_index"):
+                np.testing.assert_array_equal(got_m[k], getattr(om, k), err_msg=f"merge {k}")
+            op = orc.project(om, req[3])
+            got_p = c["projected"].download()
+            for k in ("U_index", "U_pointer", "V_index"):
+                np.testing.assert_array_equal(got_p[k], getattr(op, k), err_msg=f"{req[3]} {k}")
+    server.free()
