@@ -1,27 +1,29 @@
 #!/usr/bin/env python3
 """Benchmark of the CGA hot path (libcga) on GB300.
 
-Default workload (--config lidar; one "step" = one pass of the whole hot path):
-the LiDAR-shaped frame set -- 10 sweeps of 64 beams x 2048 azimuth steps
-(1,310,720 float32 points) on a 16-bit-per-axis grid over [-128, 128)^3 m:
-  build    the 10 sweep CGAs in one batched call, each sweep's ego pose fused
-           into its quantization
-  merge    a merge tree over the sweeps (t with t+1, then upwards; 9 merges,
-           one batched call per level) into the world CGA
-  project  the world CGA onto the xy plane
-  nn       1,000,000 exact NN queries (world points + N(0, 0.2 m) jitter):
-           the Morton query sort, then the search
-  decode   the world CGA back to voxel triples
+Default workload (--config surface; one "step" = one pass of the whole hot
+path): 30M float32 points sampled on the surfaces of 200 seeded
+superellipsoids in a 100 m cube, on a 12-bit-per-axis grid (24.4 mm voxels):
+  build    the even- and odd-index halves (15M points each) in one batched call
+  merge    the two half CGAs (Eq. 1)
+  project  the merged CGA onto the xy, xz and yz planes (Eq. 3)
+  nn       8,000,000 exact NN queries (4M fresh surface samples + 4M uniform
+           in the box): the search structure of the merged CGA (the
+           strategy cga_nn_autotune picked before timing), the Morton query
+           sort, then the search (Eq. 7-8)
+  decode   the merged CGA back to voxel triples
 Inputs are resident in HBM before the timed region; L2 (129 MB) is flushed
 between timed steps by writing a 512 MB buffer.
 
-Other workloads: --config plain (100k uniform + twin), surface (30M points on
-superellipsoids), batched (512 uneven clouds through the pre-planned pipeline
-replayed from a CUDA graph, against 512 sequential plain calls), served
-(Poisson requests over 64 resident CGAs).
+Other workloads: --config lidar (10 LiDAR sweeps, 1.31M points, b = 16, 1M
+jittered queries), plain (100k uniform + twin), batched (512 uneven clouds
+through the pre-planned pipeline replayed from a CUDA graph, against 512
+sequential plain calls), served (requests over 64 resident CGAs), and the
+rows after the hot path: values, perspective, search, compress.
 
 python bench.py [--gpus N --steps K --warmup W] [--config C] [--impl reference]
-prints ONE JSON line.  --impl reference times the CPU oracle on the host cores.
+prints ONE JSON line.  --impl reference times the CPU oracle on the host cores
+on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -43,9 +45,22 @@ sys.path.insert(0, ROOT)
 from paper_2110_11616_gb300 import synth  # noqa: E402
 
 METRIC = "CGA build Mpts/s, NN queries/s, merge GB/s vs HBM peak; batched vs plain"
-WORKLOAD = ("LiDAR frame set: 10 sweeps x 64 beams x 2048 azimuth (1,310,720 pts), b=16, "
-            "batched build (ego pose fused) + 9-merge tree (batched per level) + xy projection "
-            "+ 1M jittered NN + decode")
+WORKLOAD = ("surface: 30M pts on 200 superellipsoids in a 100 m cube, b=12; batched build of the "
+            "even/odd halves, merge, xy/xz/yz projections, NN search structure + Morton sort + "
+            "8M exact NN (4M on-surface + 4M uniform), decode")
+WORKLOAD_LIDAR = ("LiDAR frame set: 10 sweeps x 64 beams x 2048 azimuth (1,310,720 pts), b=16, "
+                  "batched build (ego pose fused) + 9-merge tree (batched per level) + xy "
+                  "projection + 1M jittered NN + decode")
+S_POINTS, S_QUERIES, S_BITS, S_EXTENT = 30_000_000, 8_000_000, 12, 100.0
+# the oracle's bounded sample of the surface step (cpu_baseline and --impl
+# reference): build / merge / project / decode of the first S_SAMPLE_PTS points
+# of each half; NN of the first S_SAMPLE_SURF on-surface and the first
+# S_SAMPLE_UNIF uniform queries against the whole merged world
+S_SAMPLE_PTS, S_SAMPLE_SURF, S_SAMPLE_UNIF = 1_000_000, 64, 32
+# ncu summary of the dominant kernel of the default workload (per-launch DRAM
+# bytes, and the hash of the sources the counters were taken on)
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_nn_warp_tree_surface_8M.txt")
+NN_SOURCES = ("k_nn.cu", "k_tree.cu", "k_common.cuh", "cga_impl.h")
 N_SWEEPS, BEAMS, STEPS_AZ, N_QUERIES = 10, 64, 2048, 1_000_000
 LO, EXTENT, BITS = (-128.0, -128.0, -128.0), 256.0, 16
 
@@ -58,7 +73,7 @@ def parse():
     ap.add_argument("--impl", choices=["cga", "reference"], default="cga")
     ap.add_argument("--config", choices=["lidar", "plain", "surface", "batched", "served", "values",
                                          "perspective", "search", "compress"],
-                    default="lidar")
+                    default="surface")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
@@ -72,6 +87,52 @@ def measured_peaks():
         return float(p["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def sources_hash(names) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2110_11616_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(path, names):
+    """Per-launch DRAM bytes of an ncu summary, or None when the summary is
+    missing or the kernel sources changed since its counters were taken."""
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") != sources_hash(names):
+            return None, "kernel sources changed since the ncu capture"
+        return int(kv["traffic_bytes_per_launch"]), kv.get("traffic_note", "")
+    except (OSError, KeyError, ValueError):
+        return None, "no ncu capture"
 
 
 # ----------------------------------------------------------------- workload
@@ -339,7 +400,7 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
     algo = N_QUERIES * (12 + 8 + 4 + 8) + winfo["bytes"]
     achieved = algo / (search_ms / 1e3) / 1e9
     out = base_line(args, world_size, METRIC, value, "Mpts/s", max_total / args.steps,
-                    {"workload": WORKLOAD, "points_per_step": pts, "queries_per_step": N_QUERIES,
+                    {"workload": WORKLOAD_LIDAR, "points_per_step": pts, "queries_per_step": N_QUERIES,
                      "grid_bits": BITS, "l2": f"flushed between steps ({args.flush_mb} MB write)",
                      "parallelism": f"replicas x{world_size}" if world_size > 1 else "1 GPU"},
                     "synthetic (seeded LiDAR generator; stands in for the paper's LiDAR scans)")
@@ -378,37 +439,197 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
     return out, (scene, queries)
 
 
-# ------------------------------------------------------------ GPU arm: C1, C3
+# ----------------------------------------------------- GPU arm: C3 (default)
+def surface_inputs(device):
+    """The surface workload's float32 inputs (seeded, drawn on `device`): the
+    two 15M-point halves and the 8M queries (4M on-surface, then 4M uniform)."""
+    from paper_2110_11616_gb300 import synth_gpu
+    scene = synth_gpu.surface_scene(3, device=device)
+    full = synth_gpu.sample_scene(scene, S_POINTS, seed=4)
+    halves = [full[0::2].contiguous(), full[1::2].contiguous()]
+    del full
+    surf = synth_gpu.sample_scene(scene, S_QUERIES // 2, seed=5)
+    uni = synth_gpu.uniform_queries(S_QUERIES // 2, 6, [0.0, 0.0, 0.0], S_EXTENT, device=device)
+    import torch
+    return halves, torch.cat([surf, uni]).contiguous()
+
+
+def surface_config(args, world_size):
+    return {"workload": WORKLOAD, "points_per_step": S_POINTS, "queries_per_step": S_QUERIES,
+            "grid_bits": S_BITS, "l2": f"flushed between steps ({args.flush_mb} MB write)",
+            "parallelism": f"replicas x{world_size}" if world_size > 1 else "1 GPU"}
+
+
+class SurfaceStep:
+    def __init__(self, torch, cga):
+        self.torch, self.cga = torch, cga
+        self.grid = cga.grid_from_box([0.0, 0.0, 0.0], S_EXTENT, S_BITS)
+        self.d_halves, self.d_q = surface_inputs("cuda")
+        self.h_halves = [h.cpu().pin_memory() for h in self.d_halves]
+        self.h_q = self.d_q.cpu().pin_memory()
+        m = S_QUERIES
+        self.order = torch.empty(m, dtype=torch.int64, device="cuda")
+        self.idx = torch.empty(m, dtype=torch.int32, device="cuda")
+        self.d2 = torch.empty(m, dtype=torch.int64, device="cuda")
+        self.h_idx = torch.empty(m, dtype=torch.int32).pin_memory()
+        self.h_d2 = torch.empty(m, dtype=torch.int64).pin_memory()
+        self.dec = torch.empty((S_POINTS, 3), dtype=torch.int32, device="cuda")
+        self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        self.nn_strategy = "tree"  # replaced by cga_nn_autotune's choice before timing
+
+    def step(self, timed_events=True):
+        cga, ev = self.cga, self.ev
+        rec = (lambda i: ev[i].record()) if timed_events else (lambda i: None)
+        rec(0)
+        a, b = cga.cga_build_batch(self.d_halves, self.grid, [None, None], allocator=None)
+        rec(1)
+        mg = cga.cga_merge(a, b, allocator=None)
+        rec(2)
+        pr = cga.cga_project_batch([mg] * 3, ["xy", "xz", "yz"], allocator=None)
+        rec(3)
+        cga.cga_nn_prepare(mg, self.nn_strategy)
+        cga.cga_nn_sort_queries(mg, self.d_q, self.order)
+        rec(4)
+        cga.cga_nn_query_ordered(mg, self.d_q, self.order, self.idx, self.d2)
+        rec(5)
+        cga.cga_decode(mg, out=self.dec)
+        rec(6)
+        self.last = (a, b, mg, pr)
+
+    def op_times(self):
+        e = self.ev
+        return [e[i].elapsed_time(e[i + 1]) for i in range(6)]
+
+    def e2e_step(self):
+        for h, d in zip(self.h_halves, self.d_halves):
+            d.copy_(h, non_blocking=True)
+        self.d_q.copy_(self.h_q, non_blocking=True)
+        self.step(timed_events=False)
+        self.h_idx.copy_(self.idx, non_blocking=True)
+        self.h_d2.copy_(self.d2, non_blocking=True)
+
+    def bytes_in(self):
+        return sum(h.numel() * 4 for h in self.h_halves) + self.h_q.numel() * 4
+
+    def bytes_out(self):
+        return self.h_idx.numel() * 4 + self.h_d2.numel() * 8
+
+
+def run_surface(args, world_size, local_rank, torch, dist, cga):
+    P = SurfaceStep(torch, cga)
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world_size > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # sort / merge launch shapes by measurement on a half and on the whole cloud
+    reps = [P.d_halves[0], torch.cat(P.d_halves)]
+    shapes = tune_launch_shapes(cga, reps, P.grid)
+    del reps
+    # NN strategy by measurement on a 64k sample mixing both query halves
+    P.step(timed_events=False)
+    gen = torch.Generator("cuda").manual_seed(7)
+    sample = P.d_q[torch.randperm(S_QUERIES, device="cuda", generator=gen)[:65536]].contiguous()
+    shifts, nn_tune = cga.cga_nn_autotune(P.last[2], sample)
+    P.nn_strategy = shifts
+    for _ in range(args.warmup):
+        P.step()
+    torch.cuda.synchronize()
+    clocks = start_clocks(local_rank)
+    time.sleep(0.3)
+    op_ms = np.zeros(6)
+    step_ms = []
+    launches0 = cga.kernel_launches()
+    barrier()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        step_ms.append(timed(torch, P.step, flush, float(k)))
+        op_ms += np.array(P.op_times())
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = cga.kernel_launches() - launches0
+    e2e_ms = []
+    for k in range(max(3, args.steps // 3)):
+        torch.cuda.synchronize()
+        e2e_ms.append(timed(torch, P.e2e_step, flush, float(k)))
+    clk = clocks.stop()
+
+    a, b, mg, pr = P.last
+    ai, bi, mi = a.info(), b.info(), mg.info()
+    merge_bytes = ai["bytes"] + bi["bytes"] + mi["bytes"]
+    op = op_ms / args.steps
+    total_ms = float(sum(step_ms))
+    max_total = max_over_ranks(total_ms, world_size, torch, dist, "cuda")
+    value = job_value(S_POINTS, args.steps, world_size, max_total)
+    e2e_val = S_POINTS * world_size / (float(np.mean(e2e_ms)) / 1e3) / 1e6
+    peak, peak_kind = measured_peaks()
+    # dominant kernel: the NN search (one launch of k_nn_warp per step, timed
+    # live between events 4 and 5).  Algorithmic bytes per launch (compulsory):
+    # 12 B query read + 4 B index + 8 B distance written per query.
+    search_ms = op[4]
+    algo = S_QUERIES * (12 + 4 + 8)
+    achieved = algo / (search_ms / 1e3) / 1e9
+    traffic, traffic_note = profiled_traffic(TRAFFIC_PROFILE, NN_SOURCES)
+    passes = math.ceil(3 * S_BITS / shapes[str(S_POINTS // 2)]["shape"]["radix_bits"])
+    build_design = (S_POINTS * (12 + 8 + 16 * passes + 8) + ai["bytes"] + bi["bytes"])
+    out = base_line(args, world_size, METRIC, value, "Mpts/s", max_total / args.steps,
+                    surface_config(args, world_size),
+                    "synthetic (seeded superellipsoid surfaces; stands in for the paper's "
+                    "8iVSLF surface sequences)")
+    out.update({
+        "breakdown_ms": {"build": round(op[0], 4), "merge": round(op[1], 4),
+                         "project_xy_xz_yz": round(op[2], 4),
+                         "nn_prepare_sort": round(op[3], 4), "nn_search": round(op[4], 4),
+                         "decode": round(op[5], 4)},
+        "derived": {
+            "build_Mpts_s": round(S_POINTS / (op[0] / 1e3) / 1e6, 2),
+            "build_by_design_GB_s": round(build_design / (op[0] / 1e3) / 1e9, 1),
+            "build_by_design_frac_of_hbm": round(build_design / (op[0] / 1e3) / 1e9 / peak, 4),
+            "nn_queries_s": round(S_QUERIES / ((op[3] + op[4]) / 1e3), 1),
+            "nn_search_queries_s": round(S_QUERIES / (op[4] / 1e3), 1),
+            "merge_GB_s": round(merge_bytes / (op[1] / 1e3) / 1e9, 2),
+            "merge_frac_of_hbm": round(merge_bytes / (op[1] / 1e3) / 1e9 / peak, 5),
+            "merge_compulsory_bytes": merge_bytes,
+            "merged_u": mi["u"], "merged_g": mi["g"], "merged_h": mi["h"],
+            "merged_bytes": mi["bytes"], "raw_bytes": S_POINTS * 12,
+        },
+        "roofline": {"kernel": "k_nn_warp<3> (NN search over the occupancy tree)",
+                     "bound": "hbm", "achieved": round(achieved, 3), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 6), "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                     "algorithmic_bytes_per_launch": algo,
+                     "note": "compulsory bytes: 12 B query in + 12 B result out per query over "
+                             "the live CUDA-event time of the search launch; the search is "
+                             "bound by dependent L1/L2 loads and instruction issue, not HBM. "
+                             "traffic: ncu dram read+write per launch "
+                             + (f"({traffic_note})" if traffic_note else "")},
+        "e2e": {"value": round(e2e_val, 3), "unit": "Mpts/s",
+                "h2d_bytes_per_step": P.bytes_in(), "d2h_bytes_per_step": P.bytes_out()},
+        "nn_autotune": tune_record(tuple(shifts), nn_tune),
+        "launch_shapes": shapes,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "wall_s": round(t_wall, 3),
+    })
+    return out, P
+
+
+# ------------------------------------------------------------------ GPU arm: C1
 def run_single(args, world_size, local_rank, torch, cga, which):
     from paper_2110_11616_gb300 import synth_gpu
-    if which == "plain":
-        pts = torch.from_numpy(synth.uniform_cube(100_000, seed=1)).cuda()
-        X = synth.rigid_xform(seed=2)
-        halves = [pts, pts]
-        xforms = [None, X]
-        grid = cga.grid_from_box([0, 0, 0], 1.0, 10)
-        q = torch.from_numpy(synth.uniform_queries(10_000, 3, [0, 0, 0], 1.0)).cuda()
-        planes = ["xy"]
-        workload = ("plain: 100k uniform pts + rigidly transformed twin, b=10; batched build of "
-                    "both, merge, xy projection, 10k uniform NN, decode")
-        n_points = 200_000
-        coarse_shift = ()
-    else:
-        scene = synth_gpu.surface_scene(3)
-        full = synth_gpu.sample_scene(scene, 30_000_000, seed=4)
-        halves = [full[0::2].contiguous(), full[1::2].contiguous()]
-        del full
-        xforms = [None, None]
-        grid = cga.grid_from_box([0, 0, 0], 100.0, 12)
-        surf = synth_gpu.sample_scene(scene, 4_000_000, seed=5)
-        uni = synth_gpu.uniform_queries(4_000_000, 6, [0.0, 0.0, 0.0], 100.0)
-        q = torch.cat([surf, uni]).contiguous()
-        planes = ["xy", "xz", "yz"]
-        workload = ("surface: 30M pts on 200 superellipsoids, b=12; batched build of the even/odd "
-                    "halves, merge, xy/xz/yz projections, 8M NN (4M on-surface + 4M uniform), "
-                    "decode")
-        n_points = 30_000_000
-        coarse_shift = ()  # NN coarse levels: set by cga_nn_autotune below
+    pts = torch.from_numpy(synth.uniform_cube(100_000, seed=1)).cuda()
+    X = synth.rigid_xform(seed=2)
+    halves = [pts, pts]
+    xforms = [None, X]
+    grid = cga.grid_from_box([0, 0, 0], 1.0, 10)
+    q = torch.from_numpy(synth.uniform_queries(10_000, 3, [0, 0, 0], 1.0)).cuda()
+    planes = ["xy"]
+    workload = ("plain: 100k uniform pts + rigidly transformed twin, b=10; batched build of "
+                "both, merge, xy projection, 10k uniform NN, decode")
+    n_points = 200_000
+    coarse_shift = ()
     m = q.shape[0]
     order = torch.empty(m, dtype=torch.int64, device="cuda")
     idx = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -435,8 +656,7 @@ def run_single(args, world_size, local_rank, torch, cga, which):
         state["last"] = (a, b, mg, pr)
 
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
-    # sort / merge launch shapes by measurement (the surface config's halves and
-    # the whole cloud; the plain config's cloud)
+    # sort / merge launch shapes by measurement (the cloud and the pair)
     reps = [halves[0], torch.cat(halves)]
     shapes = tune_launch_shapes(cga, reps, grid)
     del reps
@@ -964,21 +1184,159 @@ def oracle_step(orc, og, scene, queries, n_sample):
     return (t1 - t0) + (t2 - t1) + (t3 - t2) + nn_full + (t5 - t4), t5 - t0
 
 
-def cpu_baseline(scene, queries, n_sample=20_000):
+LIDAR_NN_SAMPLE = 5_000
+
+
+def cpu_baseline(scene, queries, n_sample=LIDAR_NN_SAMPLE):
     import oracle as orc
     og = orc.grid_from_box(LO, EXTENT, BITS)
     t, _ = oracle_step(orc, og, scene, queries, n_sample)
     pts = sum(len(s) for s in scene.sweeps)
     return {"value": round(pts / t / 1e6, 4), "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"full build/merge/project/decode of the step; NN on {n_sample} of "
                       f"{len(queries)} queries, scaled to all"}
 
 
+class OracleSurface:
+    """The CPU oracle on the surface workload: the whole merged world is built
+    once (untimed) for the NN sample; a step times build / merge / xy, xz, yz
+    projections / decode of the first n_pts points of each half, and NN of
+    the first n_surf on-surface and n_unif uniform queries against the world,
+    then scales each part to the full step by its unit count."""
+
+    def __init__(self, halves, queries):
+        import oracle as orc
+        self.orc = orc
+        self.og = orc.grid_from_box([0.0, 0.0, 0.0], S_EXTENT, S_BITS)
+        self.halves = [np.ascontiguousarray(h) for h in halves]
+        self.q = np.ascontiguousarray(queries)
+        self.world = orc.merge(orc.build(self.halves[0], self.og), orc.build(self.halves[1], self.og))
+
+    def _pipeline(self, pts_a, pts_b):
+        orc, og = self.orc, self.og
+        a, b = orc.build(pts_a, og), orc.build(pts_b, og)
+        m = orc.merge(a, b)
+        for pl in ("xy", "xz", "yz"):
+            orc.project(m, pl)
+        orc.decode(m)
+
+    def step(self, n_pts=S_SAMPLE_PTS, n_surf=S_SAMPLE_SURF, n_unif=S_SAMPLE_UNIF):
+        """(scaled seconds for the full step, wall seconds of the sample)"""
+        orc, og, h = self.orc, self.og, S_QUERIES // 2
+        t0 = time.perf_counter()
+        self._pipeline(self.halves[0][:n_pts], self.halves[1][:n_pts])
+        t1 = time.perf_counter()
+        orc.nn_window(self.world, og, self.q[:n_surf])
+        t2 = time.perf_counter()
+        orc.nn_window(self.world, og, self.q[h:h + n_unif])
+        t3 = time.perf_counter()
+        scaled = ((t1 - t0) * (S_POINTS // 2) / n_pts + (t2 - t1) * h / n_surf
+                  + (t3 - t2) * h / n_unif)
+        return scaled, t3 - t0
+
+    def step_threads(self, cores, n_pts=S_SAMPLE_PTS, n_surf=S_SAMPLE_SURF, n_unif=S_SAMPLE_UNIF):
+        """The same sample partitioned over `cores` threads (the oracle calls
+        release the GIL): each half's points in `cores` chunks built in
+        parallel and merged by a parallel merge tree, the three projections in
+        parallel, and cores x the single-thread NN sample split over the
+        threads.  Returns (scaled seconds for the full step, wall seconds)."""
+        import concurrent.futures as cf
+        orc, og, h = self.orc, self.og, S_QUERIES // 2
+        with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+            t0 = time.perf_counter()
+            parts = []
+            for half in self.halves:
+                pts = half[:n_pts]
+                step = -(-len(pts) // cores)
+                parts.append([pts[i:i + step] for i in range(0, len(pts), step)])
+            built = [list(ex.map(lambda p: orc.build(p, og), ch)) for ch in parts]
+            trees = []
+            for lv in built:
+                while len(lv) > 1:
+                    pairs = [(lv[i], lv[i + 1]) for i in range(0, len(lv) - 1, 2)]
+                    nxt = list(ex.map(lambda ab: orc.merge(*ab), pairs))
+                    if len(lv) % 2:
+                        nxt.append(lv[-1])
+                    lv = nxt
+                trees.append(lv[0])
+            m = orc.merge(trees[0], trees[1])
+            list(ex.map(lambda pl: orc.project(m, pl), ("xy", "xz", "yz")))
+            orc.decode(m)
+            t1 = time.perf_counter()
+            ns, nu = n_surf * cores, n_unif * cores
+            chunks = [self.q[i * n_surf:(i + 1) * n_surf] for i in range(cores)]
+            chunks += [self.q[h + i * n_unif:h + (i + 1) * n_unif] for i in range(cores)]
+            list(ex.map(lambda qq: orc.nn_window(self.world, og, qq), chunks[:cores]))
+            t2 = time.perf_counter()
+            list(ex.map(lambda qq: orc.nn_window(self.world, og, qq), chunks[cores:]))
+            t3 = time.perf_counter()
+        scaled = ((t1 - t0) * (S_POINTS // 2) / n_pts + (t2 - t1) * h / ns + (t3 - t2) * h / nu)
+        return scaled, t3 - t0
+
+
+def sample_text(n_pts=S_SAMPLE_PTS, n_surf=S_SAMPLE_SURF, n_unif=S_SAMPLE_UNIF, cores=1):
+    return (f"build/merge/xy,xz,yz projections/decode of the first {n_pts} points of each half "
+            f"(scaled by {S_POINTS // 2}/{n_pts}); NN (Sec. V-C window search) of "
+            f"{n_surf * cores} on-surface and {n_unif * cores} uniform queries against the whole "
+            f"merged world (scaled to 4M each)")
+
+
+def cpu_baseline_surface(h_halves, h_q):
+    o = OracleSurface(h_halves, h_q)
+    t1, w1 = o.step()
+    cores = host_cores()
+    tc, wc = o.step_threads(cores)
+    return {"value": round(S_POINTS / t1 / 1e6, 6), "unit": "Mpts/s", "cores": 1,
+            "kind": "oracle", "cpu_model": cpu_model(), "sample": sample_text(),
+            "wall_s": round(w1, 3),
+            "all_cores": {"value": round(S_POINTS / tc / 1e6, 6), "unit": "Mpts/s",
+                          "cores": cores, "kind": "oracle, thread-partitioned",
+                          "sample": sample_text(cores=cores), "wall_s": round(wc, 3)}}
+
+
 def run_reference(args):
+    if args.config == "lidar":
+        return run_reference_lidar(args)
+    if args.config != "surface":
+        return {"impl": "reference", "unavailable": f"the reference arm times the default "
+                f"(surface) and lidar workloads only, not --config {args.config}"}
+    import torch
+    device = "cuda" if torch.cuda.is_available() else "cpu"
+    halves, q = surface_inputs(device)
+    o = OracleSurface([h.cpu().numpy() for h in halves], q.cpu().numpy())
+    del halves, q
+    for _ in range(args.warmup):
+        o.step()
+    runs = [o.step() for _ in range(args.steps)]
+    scaled = sum(r[0] for r in runs)
+    wall = sum(r[1] for r in runs)
+    val = S_POINTS * args.steps / scaled / 1e6
+    world_size = 1
+    cfg = surface_config(args, world_size)
+    return {"impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "Mpts/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(wall / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32->u16/u32/u64",
+            "data": "synthetic (seeded superellipsoid surfaces, the GPU arm's inputs)"
+                    + ("" if device == "cuda" else "; drawn on the host (no GPU)"),
+            "config": cfg,
+            "scaled_ms_per_full_step": round(scaled / args.steps * 1e3, 3),
+            "note": "each step runs the oracle on the bounded sample below; ms_per_step is "
+                    "that sample's wall time, value the full step's throughput with every "
+                    "part scaled from the sample by its unit count",
+            "cpu_baseline": {"value": round(val, 6), "unit": "Mpts/s", "cores": 1,
+                             "kind": "oracle", "cpu_model": cpu_model(),
+                             "sample": sample_text()},
+            "e2e": {"value": round(val, 6), "unit": "Mpts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def run_reference_lidar(args):
     scene, queries = make_workload(0)
     import oracle as orc
     og = orc.grid_from_box(LO, EXTENT, BITS)
-    n_sample = 5_000
+    n_sample = LIDAR_NN_SAMPLE
     for _ in range(args.warmup):
         oracle_step(orc, og, scene, queries, n_sample)
     runs = [oracle_step(orc, og, scene, queries, n_sample) for _ in range(args.steps)]
@@ -988,16 +1346,19 @@ def run_reference(args):
     val = pts * args.steps / sum(ts) / 1e6
     sample = (f"each step: full build/merge/project/decode; NN on {n_sample} of "
               f"{len(queries)} queries, time scaled to all")
+    cfg = {"workload": WORKLOAD_LIDAR, "points_per_step": pts, "queries_per_step": N_QUERIES,
+           "grid_bits": BITS, "l2": f"flushed between steps ({args.flush_mb} MB write)",
+           "parallelism": "1 GPU"}
     return {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "Mpts/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(sum(ts) / args.steps * 1e3, 3), "higher_is_better": True,
+            "ms_per_step": round(sum(wall) / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32->u16/u32/u64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
-            "wall_ms_per_step": round(sum(wall) / args.steps * 1e3, 3),
-            "note": "ms_per_step is the step's time with the NN part scaled from the sample to "
-                    "all queries; wall_ms_per_step is what each sampled step took",
+            "data": "synthetic", "config": cfg,
+            "scaled_ms_per_full_step": round(sum(ts) / args.steps * 1e3, 3),
+            "note": "ms_per_step is each sampled step's wall time; value scales the NN part "
+                    "from the sample to all queries",
             "cpu_baseline": {"value": round(val, 4), "unit": "Mpts/s", "cores": 1,
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": round(val, 4), "unit": "Mpts/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -1019,11 +1380,18 @@ def main():
     torch.cuda.set_device(local_rank)
     if world_size > 1:
         dist.init_process_group("nccl")
-    if args.config == "lidar":
+    if args.config == "surface":
+        out, P = run_surface(args, world_size, local_rank, torch, dist, cga)
+        if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
+            h_halves = [h.numpy() for h in P.h_halves]
+            h_q = P.h_q.numpy()
+            del P
+            out["cpu_baseline"] = cpu_baseline_surface(h_halves, h_q)
+    elif args.config == "lidar":
         out, (scene, queries) = run_lidar(args, rank, world_size, local_rank, torch, dist, cga)
         if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(scene, queries)
-    elif args.config in ("plain", "surface"):
+    elif args.config == "plain":
         out = run_single(args, world_size, local_rank, torch, cga, args.config)
     elif args.config == "batched":
         out = run_batched(args, world_size, local_rank, torch, cga)
