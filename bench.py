@@ -90,14 +90,30 @@ def measured_peaks():
 
 
 def cpu_model() -> str:
+    """The host CPU's model string: /proc/cpuinfo's model name, else (Arm
+    hosts list none there) lscpu's, else its implementer / part codes."""
+    fields = {}
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                k = line.split(":")[0].strip().lower()
-                if k in ("model name", "cpu model", "hardware"):
-                    return line.split(":", 1)[1].strip()
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip().lower(), v.strip())
     except OSError:
         pass
+    for k in ("model name", "cpu model", "hardware"):
+        if fields.get(k):
+            return fields[k]
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if "cpu implementer" in fields:
+        return (f"{os.uname().machine} implementer {fields['cpu implementer']} part "
+                f"{fields.get('cpu part', '?')}")
     import platform
     return platform.processor() or platform.machine()
 
@@ -393,11 +409,10 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
     e2e_val = pts * world_size / (float(np.mean(e2e_ms)) / 1e3) / 1e6
     peak, peak_kind = measured_peaks()
     # dominant kernel: the NN search (one launch of k_nn_warp per step, timed
-    # live above between events 4 and 5).  Algorithmic bytes per launch: per
-    # query 12 B point + 8 B order key read, 4 B index + 8 B distance written,
-    # plus one read of the world CGA.
+    # live above between events 4 and 5).  Algorithmic bytes per launch
+    # (compulsory): 12 B query read, 4 B index + 8 B distance written.
     search_ms = op[4]
-    algo = N_QUERIES * (12 + 8 + 4 + 8) + winfo["bytes"]
+    algo = N_QUERIES * (12 + 4 + 8)
     achieved = algo / (search_ms / 1e3) / 1e9
     out = base_line(args, world_size, METRIC, value, "Mpts/s", max_total / args.steps,
                     {"workload": WORKLOAD_LIDAR, "points_per_step": pts, "queries_per_step": N_QUERIES,
@@ -419,11 +434,13 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
         },
         "roofline": {"kernel": "k_nn_warp (NN search)", "bound": "hbm",
                      "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 5), "traffic": 45_711_616,
+                     "frac": round(achieved / peak, 6), "traffic": None,
                      "peak_source": f"{peak_kind} hbm_gbs",
-                     "note": "latency-bound search: ncu shows L1 throughput 72% of peak, "
-                             "DRAM 0.25%; traffic = ncu dram read+write of one launch of the "
-                             "timed step (profiles/launches_lidar_frame_set.md)"},
+                     "algorithmic_bytes_per_launch": algo,
+                     "note": "compulsory bytes: 12 B query in + 12 B result out per query; "
+                             "latency-bound search (dependent L1/L2 loads), not an HBM "
+                             "stream; no ncu capture of this launch is on record for the "
+                             "current sources, so traffic is null"},
         "e2e": {"value": round(e2e_val, 3), "unit": "Mpts/s",
                 "h2d_bytes_per_step": P.bytes_in(), "d2h_bytes_per_step": P.bytes_out()},
         "plain": {"ms_per_step": round(float(np.mean(plain_ms)), 4),
@@ -753,12 +770,26 @@ def run_batched(args, world_size, local_rank, torch, cga):
                 cga.cga_project(m, "xy", allocator=None)
                 res.append(cga.cga_nn_query(m, qs[i]))
             return res
-        plain_ms = []
+        # both forms on both clocks: CUDA events on the launching stream
+        # (device time) and the host clock around the call + synchronize
+        plain_ms, plain_dev_ms = [], []
         for _ in range(2):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             t0 = time.perf_counter()
+            e0.record()
             res = plain()
+            e1.record()
             torch.cuda.synchronize()
             plain_ms.append((time.perf_counter() - t0) * 1e3)
+            plain_dev_ms.append(e0.elapsed_time(e1))
+        graph_host_ms = []
+        for _ in range(max(2, args.steps // 3)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pipe.run_graph()
+            torch.cuda.synchronize()
+            graph_host_ms.append((time.perf_counter() - t0) * 1e3)
         clk = clocks.stop()
         same = all(torch.equal(d2_pipe[i], res[i][1]) for i in range(S))
     del idx_p
@@ -771,11 +802,17 @@ def run_batched(args, world_size, local_rank, torch, cga):
                                  "pre-planned pipeline replayed from a CUDA graph",
                      "clouds": S, "points_per_step": total_pts, "l2": "inputs > L2"},
                     "synthetic (seeded GPU generators)")
-    out.update({"graph_ms": round(total / args.steps, 3),
+    graph_dev = total / args.steps
+    out.update({"graph_ms": round(graph_dev, 3),
+                "graph_host_ms": round(float(np.min(graph_host_ms)), 3),
                 "pipeline_no_graph_ms": round(float(np.mean(ms_nograph)), 3),
                 "plain_512_calls_ms": round(float(np.min(plain_ms)), 3),
-                "plain_timing": "host wall clock around 512 sequential calls + synchronize",
-                "speedup_vs_plain": round(float(np.min(plain_ms)) / (total / args.steps), 2),
+                "plain_512_calls_device_ms": round(float(np.min(plain_dev_ms)), 3),
+                "plain_timing": "512 sequential calls: host clock around the calls + "
+                                "synchronize, and CUDA events around them on the same stream",
+                "speedup_vs_plain": {
+                    "device_clock": round(float(np.min(plain_dev_ms)) / graph_dev, 2),
+                    "host_clock": round(float(np.min(plain_ms)) / float(np.min(graph_host_ms)), 2)},
                 "nn_results_equal_plain": bool(same),
                 "launch_shape": shape_record(shape, tune_times),
                 "gpu_launches": int(launches), "clocks": clk})
@@ -837,6 +874,54 @@ def run_served(args, world_size, local_rank, torch, cga):
     ok = all(c["status"] == 0 for c in done)
     del done
     server.free()
+
+    # saturation: the same request list submitted at once (admission by
+    # footprint decides what runs together), against the same list run one
+    # request after another through the plain calls.  Both on the host clock
+    # from one common start; a request's latency is its completion time since
+    # that start (every request is waiting at the start).
+    def submit_all(srv):
+        keep = []
+        for r in reqs:
+            if r[0] == "nn":
+                q = banks[r[1]][:r[2]]
+                idx = torch.empty(r[2], dtype=torch.int32, device="cuda")
+                d2 = torch.empty(r[2], dtype=torch.int64, device="cuda")
+                srv.submit_nn(r[1], q, idx, d2)
+                keep.append((idx, d2))
+            else:
+                srv.submit_merge_project(r[1], r[2], "xy")
+        return keep
+
+    torch.cuda.synchronize()
+    sat = cga.Server(pool, memory_budget=64 << 30, slots=4, max_batch=64)
+    t0_ns = time.perf_counter_ns()
+    t0 = time.perf_counter()
+    keep = submit_all(sat)
+    sat.drain()
+    sat_s = time.perf_counter() - t0
+    sat_done = sat.poll(max_n=n_req + 16)
+    sat_ok = all(c["status"] == 0 for c in sat_done) and len(sat_done) == n_req
+    # the server stamps with the steady clock; shift to perf_counter's origin
+    sat_first = min(c["t_submit_ns"] for c in sat_done)
+    sat_lat = np.array([(c["t_done_ns"] - sat_first) / 1e6 for c in sat_done])
+    del sat_done, keep
+    sat.free()
+    torch.cuda.synchronize()
+    start_ev = torch.cuda.Event(enable_timing=True)
+    ends = [torch.cuda.Event(enable_timing=True) for _ in reqs]
+    t0 = time.perf_counter()
+    start_ev.record()
+    for r, ev in zip(reqs, ends):
+        if r[0] == "nn":
+            cga.cga_nn_query(pool[r[1]], banks[r[1]][:r[2]])
+        else:
+            mg = cga.cga_merge(pool[r[1]], pool[r[2]], allocator=None)
+            cga.cga_project(mg, "xy", allocator=None)
+        ev.record()
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain_lat = np.array([start_ev.elapsed_time(ev) for ev in ends])
     # each request alone through the plain path (a seeded sample)
     alone = []
     for r in [reqs[i] for i in rng.choice(n_req, size=min(200, n_req), replace=False)]:
@@ -869,6 +954,21 @@ def run_served(args, world_size, local_rank, torch, cga):
                 "alone_latency_ms": {"p50": round(float(np.percentile(alone, 50)), 3),
                                      "p99": round(float(np.percentile(alone, 99)), 3),
                                      "sample": len(alone)},
+                "saturation": {
+                    "what": "the same request list submitted at once to the server, and run "
+                            "one request after another through the plain calls; host clock "
+                            "from one common start; latency = completion time since the start",
+                    "served_s": round(sat_s, 4), "plain_s": round(plain_s, 4),
+                    "served_requests_s": round(n_req / sat_s, 1),
+                    "plain_requests_s": round(n_req / plain_s, 1),
+                    "served_queries_s": round(nq / sat_s, 1),
+                    "plain_queries_s": round(nq / plain_s, 1),
+                    "served_over_plain": round(plain_s / sat_s, 3),
+                    "served_latency_ms": {"p50": round(float(np.percentile(sat_lat, 50)), 3),
+                                          "p99": round(float(np.percentile(sat_lat, 99)), 3)},
+                    "plain_latency_ms": {"p50": round(float(np.percentile(plain_lat, 50)), 3),
+                                         "p99": round(float(np.percentile(plain_lat, 99)), 3)},
+                    "all_ok": bool(sat_ok)},
                 "clocks": clk})
     return out
 

@@ -1056,16 +1056,28 @@ def cga_residual(pred_values, ref_values, idx, stream=None):
     """Residual frame (Sec. V-D): pred - ref[idx] per channel as an (u_pred, C) int16
     tensor (pred where idx has no reference point).  Values: (u, C) uint8 CUDA
     tensors; idx: (u_pred,) int32 CUDA tensor holding uint32."""
+    import torch
+    for t in (pred_values, ref_values, idx):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("cga_residual: expected torch tensors")
+    # the kernel reads u_pred rows of pred and indexes ref with pred's row
+    # width: both must be (rows, C) with the same C, and pred must have one
+    # row per entry of idx
+    ch = pred_values.shape[1] if pred_values.dim() > 1 else 1
+    if (pred_values.dim() != 2 or ref_values.dim() != 2 or ref_values.shape[1] != ch
+            or pred_values.shape[0] != idx.numel() or idx.dim() != 1):
+        raise ValueError(f"cga_residual: pred_values {tuple(pred_values.shape)}, ref_values "
+                         f"{tuple(ref_values.shape)} and idx {tuple(idx.shape)} must be (u_pred, C),"
+                         f" (u_ref, C) and (u_pred,)")
     torch = _torch()
+    for t in (pred_values, ref_values, idx):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise TypeError("cga_residual: expected contiguous CUDA tensors")
     lib = load()
     P = ctypes.c_void_p
     lib.cga_residual.argtypes = [P, ctypes.c_uint64, P, ctypes.c_uint64, P, ctypes.c_uint32, P, P]
-    for t in (pred_values, ref_values, idx):
-        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
-            raise TypeError("cga_residual: expected contiguous CUDA tensors")
-    ch = pred_values.shape[1] if pred_values.dim() > 1 else 1
     u_pred = idx.numel()
-    u_ref = ref_values.numel() // ch
+    u_ref = ref_values.shape[0]
     out = torch.empty((max(u_pred, 1), ch), dtype=torch.int16, device="cuda")
     _check(lib.cga_residual(P(pred_values.data_ptr()), u_pred, P(ref_values.data_ptr()), u_ref,
                             P(idx.data_ptr()), ch, P(out.data_ptr()), _stream(stream)),

@@ -260,6 +260,10 @@ constexpr int kQueryLimit = 1 << 30;
 #ifndef CGA_NN_TREE_BLOCKS
 #define CGA_NN_TREE_BLOCKS 4
 #endif
+// 1: a frame's child bounds are kept in shared memory for the way back
+#ifndef CGA_NN_TREE_CACHE
+#define CGA_NN_TREE_CACHE 1
+#endif
 
 struct Qry {
   int x, y, z;
@@ -547,9 +551,12 @@ __device__ void search_levels(const NnSeg& sg, const Qry& q, uint32_t lane, Best
 // every cell holding a voxel at the final distance is entered: the result is
 // Eq. 8's nearest voxel, ties to the smaller key.
 
-// Squared distance from q to the cell [lo, lo + s - 1] along one axis.
-__device__ __forceinline__ unsigned long long axis_lb2(int q, uint32_t lo, uint32_t s) {
-  const unsigned long long d = interval_dist(q, lo, s);
+// Squared distance from q to the cell [lo, lo + s - 1] along one axis, in D
+// (uint32_t when every squared distance of the search fits 32 bits: a grid of
+// at most 15 bits per axis and a query inside it; else 64 bits).
+template <typename D>
+__device__ __forceinline__ D axis_lb2(int q, uint32_t lo, uint32_t s) {
+  const D d = interval_dist(q, lo, s);
   return d * d;
 }
 
@@ -558,42 +565,56 @@ struct TreeFrame {
   uint32_t first, ox, oy, oz, lvl, pad;
 };
 
+// Warp minimum of a D value (32-bit words, high first).
+__device__ __forceinline__ uint32_t warp_min_d(uint32_t v) {
+  return __reduce_min_sync(0xffffffffu, v);
+}
+__device__ __forceinline__ unsigned long long warp_min_d(unsigned long long v) {
+  const uint32_t full = 0xffffffffu;
+  const uint32_t vh = (uint32_t)(v >> 32), vl = (uint32_t)v;
+  const uint32_t mh = __reduce_min_sync(full, vh);
+  const uint32_t ml = __reduce_min_sync(full, vh == mh ? vl : full);
+  return ((unsigned long long)mh << 32) | ml;
+}
+
 // The best (distance^2, key) of the tree search.
+template <typename D>
 struct BestKey {
-  unsigned long long d2, key;
-  // Lexicographic minimum of the lanes' (d, k), by 32-bit warp reductions.
-  __device__ __forceinline__ void warp_min_of(unsigned long long d, unsigned long long k) {
+  D d2;
+  unsigned long long key;
+  // Lexicographic minimum of the lanes' (d, k).
+  __device__ __forceinline__ void warp_min_of(D d, unsigned long long k) {
     const uint32_t full = 0xffffffffu;
-    const uint32_t dh = (uint32_t)(d >> 32), dl = (uint32_t)d;
-    const uint32_t mh = __reduce_min_sync(full, dh);
-    const uint32_t ml = __reduce_min_sync(full, dh == mh ? dl : full);
-    const bool at = dh == mh && dl == ml;
+    const D md = warp_min_d(d);
+    const bool at = d == md;
     const uint32_t kh = __reduce_min_sync(full, at ? (uint32_t)(k >> 32) : full);
     const uint32_t kl = __reduce_min_sync(full, at && (uint32_t)(k >> 32) == kh ? (uint32_t)k : full);
-    d2 = ((unsigned long long)mh << 32) | ml;
+    d2 = md;
     key = ((unsigned long long)kh << 32) | kl;
   }
 };
 
 // The voxels of the brick at brick coordinates (bx, by, bz) with occupancy
 // m: lane i takes voxels i and i + 32 (bit c = cx << 4 | cy << 2 | cz).
+template <typename D>
 __device__ __forceinline__ void tree_brick(unsigned long long m, uint32_t bx, uint32_t by,
                                            uint32_t bz, const Qry& q, uint32_t b, uint32_t lane,
-                                           BestKey& best) {
+                                           BestKey<D>& best) {
   const uint32_t y = (by << 2) + ((lane >> 2) & 3u), z = (bz << 2) + (lane & 3u);
   const uint32_t x0 = (bx << 2) + (lane >> 4);
-  const unsigned long long dy = absdiff(y, q.y), dz = absdiff(z, q.z);
-  const unsigned long long dyz = dy * dy + dz * dz;
+  const D dy = absdiff(y, q.y), dz = absdiff(z, q.z);
+  const D dyz = dy * dy + dz * dz;
   const unsigned long long yz = ((unsigned long long)y << b) | z;
-  unsigned long long cd = ~0ull, ck = ~0ull;
+  D cd = (D)~(D)0;
+  unsigned long long ck = ~0ull;
   if ((m >> lane) & 1ull) {
-    const unsigned long long dx = absdiff(x0, q.x);
+    const D dx = absdiff(x0, q.x);
     cd = dx * dx + dyz;
     ck = ((unsigned long long)x0 << (2 * b)) | yz;
   }
   if ((m >> (lane + 32)) & 1ull) {
-    const unsigned long long dx = absdiff(x0 + 2, q.x);
-    const unsigned long long d = dx * dx + dyz;
+    const D dx = absdiff(x0 + 2, q.x);
+    const D d = dx * dx + dyz;
     if (d < cd) {  // on a tie the smaller x (smaller key) stays
       cd = d;
       ck = ((unsigned long long)(x0 + 2) << (2 * b)) | yz;
@@ -605,8 +626,9 @@ __device__ __forceinline__ void tree_brick(unsigned long long m, uint32_t bx, ui
   }
 }
 
+template <typename D>
 __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFrame* fr,
-                            BestKey& best) {
+                            uint32_t* lbc, BestKey<D>& best) {
   const uint32_t full = 0xffffffffu;
   const TreeView& tv = sg.tree;
   const uint32_t T = tv.levels, b = sg.a.bits;
@@ -620,6 +642,10 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
   uint32_t first = r0.z, ox = 0, oy = 0, oz = 0;
   int depth = 0;
   const uint32_t cy = (lane >> 2) & 3u, cz = lane & 3u, cx0 = lane >> 4;
+  bool s_pop = false;
+  // fresh: the current frame was just entered (its children's bounds are
+  // computed and, above level 2, kept in lbc[depth] for the way back)
+  bool fresh = true;
   while (true) {
     // Each lane loads the records of its two children (a node's child set and
     // first child, or a brick's voxels) with their box codes, so that the
@@ -632,7 +658,10 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
     const uint32_t i1 = first + (uint32_t)__popcll(mask & ((1ull << (lane + 32)) - 1ull));
     const uint32_t cap = tv.cap[lvl - 1];
     uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = make_uint4(0u, 0u, 0u, 0u);
-    if (lvl == 2) {
+    const bool cached = CGA_NN_TREE_CACHE && !fresh;
+    if (cached) {
+      // back in a frame above level 2: its bounds are kept (no loads)
+    } else if (lvl == 2) {
       if (h0 && i0 < cap) {
         const unsigned long long m0 = __ldg(tv.brick + i0);
         c0 = make_uint4((uint32_t)m0, (uint32_t)(m0 >> 32), 0u, __ldg(tv.bcode + i0));
@@ -648,29 +677,94 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
     }
     const uint32_t Y = ((oy << 2) + cy) << sh, Z = ((oz << 2) + cz) << sh;
     const uint32_t X0 = ((ox << 2) + cx0) << sh, X1 = X0 + (2u << sh);
-    unsigned long long lb0 = ~0ull, lb1 = ~0ull;
-    if (h0) {
+    D lb0 = (D)~(D)0, lb1 = (D)~(D)0;
+    if (cached) {
+      // (a kept bound saturates at 2^32 - 1, still a lower bound)
+      if (h0) lb0 = (D)lbc[depth * 64 + lane];
+      if (h1) lb1 = (D)lbc[depth * 64 + 32 + lane];
+    } else if (h0) {
       const uint32_t k = c0.w;
       const uint32_t lx = k & 3u, hx = (k >> 2) & 3u, ly = (k >> 4) & 3u, hy = (k >> 6) & 3u,
                      lz = (k >> 8) & 3u, hz = (k >> 10) & 3u;
-      lb0 = axis_lb2(q.x, X0 + (lx << ss), (hx - lx + 1) << ss) +
-            axis_lb2(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
-            axis_lb2(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
+      lb0 = axis_lb2<D>(q.x, X0 + (lx << ss), (hx - lx + 1) << ss) +
+            axis_lb2<D>(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
+            axis_lb2<D>(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
     }
-    if (h1) {
+    if (!cached && h1) {
       const uint32_t k = c1.w;
       const uint32_t lx = k & 3u, hx = (k >> 2) & 3u, ly = (k >> 4) & 3u, hy = (k >> 6) & 3u,
                      lz = (k >> 8) & 3u, hz = (k >> 10) & 3u;
-      lb1 = axis_lb2(q.x, X1 + (lx << ss), (hx - lx + 1) << ss) +
-            axis_lb2(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
-            axis_lb2(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
+      lb1 = axis_lb2<D>(q.x, X1 + (lx << ss), (hx - lx + 1) << ss) +
+            axis_lb2<D>(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
+            axis_lb2<D>(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
     }
     const bool in0 = h0 && i0 < cap && lb0 <= best.d2;
     const bool in1 = h1 && i1 < cap && lb1 <= best.d2;
     const uint32_t s0 = __ballot_sync(full, in0), s1 = __ballot_sync(full, in1);
-    if ((s0 | s1) == 0u) {
+    if (CGA_NN_TREE_CACHE && !cached && lvl > 2) {
+      lbc[depth * 64 + lane] = lb0 > (D)0xfffffffeu ? 0xffffffffu : (uint32_t)lb0;
+      lbc[depth * 64 + 32 + lane] = lb1 > (D)0xfffffffeu ? 0xffffffffu : (uint32_t)lb1;
+    }
+    if (lvl == 2 && (s0 | s1) != 0u) {
+      // Children are bricks.  Without a candidate yet only the nearest brick
+      // is examined (its voxels set a bound that prunes its siblings), else
+      // every lane examines the voxels of its surviving bricks (a loop over
+      // their occupancy bits) and the level-2 node is done.
+      const bool only_nearest = best.d2 == (D)~(D)0;
+      bool e0 = in0, e1 = in1;
+      uint32_t cs_first = 64;
+      if (only_nearest) {
+        D v = in0 ? lb0 : (D)~(D)0;
+        uint32_t c = lane;
+        if (in1 && lb1 < v) {
+          v = lb1;
+          c = lane + 32;
+        }
+        const D mv = warp_min_d(v);
+        const uint32_t win = __ballot_sync(full, (in0 || in1) && v == mv);
+        cs_first = __shfl_sync(full, c, __ffs(win) - 1);
+        e0 = in0 && cs_first == lane;
+        e1 = in1 && cs_first == lane + 32;
+      }
+      D cd = (D)~(D)0;
+      unsigned long long ck = ~0ull;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        if (!(t == 0 ? e0 : e1)) continue;
+        const uint4 r = t == 0 ? c0 : c1;
+        const uint32_t cx = cx0 + 2 * t;
+        const uint32_t bx = ((ox << 2) + cx) << 2, by = ((oy << 2) + cy) << 2,
+                       bz = ((oz << 2) + cz) << 2;
+        unsigned long long m = r.x | ((unsigned long long)r.y << 32);
+        while (m != 0ull) {
+          const uint32_t v = (uint32_t)__ffsll((long long)m) - 1u;
+          m &= m - 1ull;
+          const uint32_t x = bx + (v >> 4), y = by + ((v >> 2) & 3u), z = bz + (v & 3u);
+          const D dx = absdiff(x, q.x), dy = absdiff(y, q.y), dz = absdiff(z, q.z);
+          const D d = dx * dx + dy * dy + dz * dz;
+          const unsigned long long k = ((unsigned long long)x << (2 * b)) |
+                                       ((unsigned long long)y << b) | z;
+          if (d < cd || (d == cd && k < ck)) {
+            cd = d;
+            ck = k;
+          }
+        }
+      }
+      const bool better = cd < best.d2 || (cd == best.d2 && ck < best.key);
+      if (__any_sync(full, better)) {
+        best.warp_min_of(better ? cd : best.d2, better ? ck : best.key);
+      }
+      if (only_nearest) {
+        rem = ((((unsigned long long)s1) << 32) | s0) & ~(1ull << cs_first);
+        continue;
+      }
+      s_pop = true;
+    }
+    if ((s0 | s1) == 0u || s_pop) {
+      s_pop = false;
       if (depth == 0) break;
       --depth;
+      fresh = false;
       __syncwarp();
       const TreeFrame f = fr[depth];
       lvl = f.lvl;
@@ -684,58 +778,49 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
     }
     // the surviving child with the least bound, and its record from the lane
     // that loaded it
-    unsigned long long v = in0 ? lb0 : ~0ull;
+    D v = in0 ? lb0 : (D)~(D)0;
     uint32_t c = lane;
     if (in1 && lb1 < v) {
       v = lb1;
       c = lane + 32;
     }
-    const uint32_t vh = (uint32_t)(v >> 32), vl = (uint32_t)v;
-    const uint32_t mh = __reduce_min_sync(full, vh);
-    const uint32_t ml = __reduce_min_sync(full, vh == mh ? vl : full);
-    const uint32_t win = __ballot_sync(full, vh == mh && vl == ml);
+    const D mv = warp_min_d(v);
+    const uint32_t win = __ballot_sync(full, v == mv);
     const int owner = __ffs(win) - 1;
     const uint32_t cs = __shfl_sync(full, c, owner);
-    const uint4 mine = cs >= 32 ? c1 : c0;
-    const uint32_t rx = __shfl_sync(full, mine.x, owner);
-    const uint32_t ry = __shfl_sync(full, mine.y, owner);
-    const uint32_t rz = __shfl_sync(full, mine.z, owner);
+    uint32_t rx, ry, rz;
+    if (cached) {
+      const uint32_t ci = first + (uint32_t)__popcll(mask & ((1ull << cs) - 1ull));
+      const uint4 r = __ldg(tv.node[lvl - 1] + ci);  // ci < cap: cs survived the check above
+      rx = r.x;
+      ry = r.y;
+      rz = r.z;
+    } else {
+      const uint4 mine = cs >= 32 ? c1 : c0;
+      rx = __shfl_sync(full, mine.x, owner);
+      ry = __shfl_sync(full, mine.y, owner);
+      rz = __shfl_sync(full, mine.z, owner);
+    }
     rem = ((((unsigned long long)s1) << 32) | s0) & ~(1ull << cs);
     const uint32_t nx = (ox << 2) + (cs >> 4), ny = (oy << 2) + ((cs >> 2) & 3u),
                    nz = (oz << 2) + (cs & 3u);
-    if (lvl > 2) {
-      // the last surviving child replaces its parent's frame (nothing to come
-      // back to); otherwise the parent's frame is kept for the way back
-      if (rem != 0ull) {
-        __syncwarp();
-        if (lane == 0) fr[depth] = TreeFrame{mask, rem, first, ox, oy, oz, lvl, 0u};
-        __syncwarp();
-        ++depth;
-      }
-      --lvl;
-      mask = rx | ((unsigned long long)ry << 32);
-      rem = mask;
-      first = rz;
-      ox = nx;
-      oy = ny;
-      oz = nz;
-    } else {
-      tree_brick(rx | ((unsigned long long)ry << 32), nx, ny, nz, q, b, lane, best);
-      if (rem == 0ull) {
-        // the level-2 node is done: back to the nearest kept frame
-        if (depth == 0) break;
-        --depth;
-        __syncwarp();
-        const TreeFrame f = fr[depth];
-        lvl = f.lvl;
-        mask = f.mask;
-        rem = f.rem;
-        first = f.first;
-        ox = f.ox;
-        oy = f.oy;
-        oz = f.oz;
-      }
+    // (lvl > 2 here: a level-2 node was settled above.)  The last surviving
+    // child replaces its parent's frame (nothing to come back to); otherwise
+    // the parent's frame is kept for the way back.
+    if (rem != 0ull) {
+      __syncwarp();
+      if (lane == 0) fr[depth] = TreeFrame{mask, rem, first, ox, oy, oz, lvl, 0u};
+      __syncwarp();
+      ++depth;
     }
+    --lvl;
+    mask = rx | ((unsigned long long)ry << 32);
+    rem = mask;
+    first = rz;
+    ox = nx;
+    oy = ny;
+    oz = nz;
+    fresh = true;
   }
 }
 
@@ -775,6 +860,7 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
               const unsigned long long* __restrict__ order,
               const unsigned int* __restrict__ order_err) {
   __shared__ TreeFrame s_fr[NC == 3 ? 8 * kTreeMaxLevels : 1];
+  __shared__ uint32_t s_lbc[NC == 3 && CGA_NN_TREE_CACHE ? 8 * kTreeMaxLevels * 64 : 1];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const bool sorted = order != nullptr && (order_err == nullptr || *order_err == 0u);
@@ -819,13 +905,31 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
     const uint32_t cqz = (uint32_t)min(max(qz, 0), top);
     if constexpr (NC == 3) {
       if (sg.tree.levels > 0) {
-        BestKey bk{~0ull, ~0ull};
-        search_tree(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane,
-                    s_fr + (threadIdx.x >> 5) * kTreeMaxLevels, bk);
-        const uint32_t ix = bk.d2 != ~0ull ? stored_index(sg, bk.key) : 0xffffffffu;
+        // 32-bit distances when every one fits: a query inside a grid of at
+        // most 15 bits per axis (3 * (2^15 - 1)^2 < 2^32)
+        const Qry qq{qx, qy, qz, cqx, cqy, cqz};
+        TreeFrame* fr = s_fr + (threadIdx.x >> 5) * kTreeMaxLevels;
+        uint32_t* lbc = CGA_NN_TREE_CACHE ? s_lbc + (threadIdx.x >> 5) * kTreeMaxLevels * 64 : s_lbc;
+        const bool narrow = b <= 15 && (uint32_t)qx == cqx && (uint32_t)qy == cqy &&
+                            (uint32_t)qz == cqz;
+        unsigned long long d2 = ~0ull, key = ~0ull;
+        if (narrow) {
+          BestKey<uint32_t> bk{0xffffffffu, ~0ull};
+          search_tree<uint32_t>(sg, qq, lane, fr, lbc, bk);
+          if (bk.d2 != 0xffffffffu) {
+            d2 = bk.d2;
+            key = bk.key;
+          }
+        } else {
+          BestKey<unsigned long long> bk{~0ull, ~0ull};
+          search_tree<unsigned long long>(sg, qq, lane, fr, lbc, bk);
+          d2 = bk.d2;
+          key = bk.key;
+        }
+        const uint32_t ix = d2 != ~0ull ? stored_index(sg, key) : 0xffffffffu;
         if (lane == 0) {
           sg.idx[j] = ix;
-          sg.d2[j] = bk.d2;
+          sg.d2[j] = d2;
         }
         continue;
       }

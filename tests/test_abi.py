@@ -118,3 +118,23 @@ def test_strerror_names_every_code(lib):
         seen.add(s)
     assert len(seen) == 8
     assert lib.cga_strerror(-99).decode() == "unknown error"
+
+
+def test_residual_wrapper_rejects_mismatched_shapes():
+    """cga_residual's binding checks the row counts and channel widths it
+    passes to the kernel (which cannot see them) before anything runs."""
+    import torch
+
+    from paper_2110_11616_gb300 import cga
+    pred = torch.zeros((10, 3), dtype=torch.uint8)
+    ref = torch.zeros((7, 3), dtype=torch.uint8)
+    idx = torch.zeros(10, dtype=torch.int32)
+    for p, r, i in [(pred, ref, idx[:9]),                                 # rows != idx
+                    (pred, torch.zeros((7, 4), dtype=torch.uint8), idx),  # channel widths
+                    (pred.reshape(-1), ref, idx),                         # not (rows, C)
+                    (pred, ref, idx.reshape(2, 5))]:
+        with pytest.raises(ValueError):
+            cga.cga_residual(p, r, i)
+    # shapes agree: host tensors are refused next (no GPU here: refused earlier)
+    with pytest.raises((TypeError, RuntimeError)):
+        cga.cga_residual(pred, ref, idx)

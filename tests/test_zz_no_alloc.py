@@ -9,6 +9,7 @@ has then already run every other test."""
 import ctypes
 
 import numpy as np
+import oracle_threads
 import pytest
 
 from paper_2110_11616_gb300 import synth
@@ -63,3 +64,49 @@ def test_noalloc_rejects_more_than_its_capacity(cg):
     rc = cg.load().cga_nn_query_noalloc(a.ptr, ctypes.c_void_p(16), m, ctypes.c_void_p(16),
                                         ctypes.c_void_p(16), None)
     assert rc == cg.ERR_CAPACITY
+
+
+def test_noalloc_at_capacity_matches_oracle(cg, orc):
+    """m = CGA_NOALLOC_MAX_QUERIES on a multi-million-voxel CGA: the worst
+    case the fixed array must hold (its size check passes, the call returns
+    OK) and the answers equal cga_nn_query's and, on a seeded sample, the
+    oracle's; then a call below the Morton-sort threshold."""
+    pts = synth.uniform_cube(3_000_000, seed=406)
+    g = cg.grid_from_box([0, 0, 0], 1.0, 12)
+    og = orc.grid_from_box([0, 0, 0], 1.0, 12)
+    a = cg.cga_build(torch.from_numpy(pts).cuda(), g)
+    m = cg.NOALLOC_MAX_QUERIES
+    qh = synth.uniform_queries(m, 407, [-0.05] * 3, 1.1)
+    q = torch.from_numpy(qh).cuda()
+    got_idx, got_d2 = call_noalloc(cg, a, q)
+    ref_idx, ref_d2 = cg.cga_nn_query(a, q)
+    torch.cuda.synchronize()
+    assert torch.equal(got_idx, ref_idx) and torch.equal(got_d2, ref_d2)
+    oa = orc.build(pts, og)
+    pick = np.random.default_rng(408).choice(m, 4000, replace=False)
+    oi, od = oracle_threads.nn_window(orc, oa, og, qh[pick])
+    assert np.array_equal(got_d2.cpu().numpy().view(np.uint64)[pick], od)
+    assert np.array_equal(got_idx.cpu().numpy().view(np.uint32)[pick], oi)
+    small = q[:1000].contiguous()
+    got_idx, got_d2 = call_noalloc(cg, a, small)
+    ref_idx, ref_d2 = cg.cga_nn_query(a, small)
+    torch.cuda.synchronize()
+    assert torch.equal(got_idx, ref_idx) and torch.equal(got_d2, ref_d2)
+
+
+@pytest.mark.parametrize("prep", [(3,), (2, 5), "tree"])
+def test_noalloc_uses_the_prepared_search(cg, prep):
+    """On a handle prepared with coarse levels or the occupancy tree the call
+    answers exactly as cga_nn_query does on it (two calls in a row)."""
+    from paper_2110_11616_gb300 import synth as sy
+    scene = sy.superellipsoid_scene(n_objects=12, seed=409, extent=100.0)
+    pts = sy.sample_surfaces(scene, 400_000, seed=410)
+    g = cg.grid_from_box([0.0] * 3, 100.0, 12)
+    a = cg.cga_build(torch.from_numpy(pts).cuda(), g)
+    cg.cga_nn_prepare(a, prep)
+    for seed in (411, 412):
+        q = torch.from_numpy(sy.uniform_queries(50_000, seed, [-10.0] * 3, 120.0)).cuda()
+        got_idx, got_d2 = call_noalloc(cg, a, q)
+        ref_idx, ref_d2 = cg.cga_nn_query(a, q)
+        torch.cuda.synchronize()
+        assert torch.equal(got_idx, ref_idx) and torch.equal(got_d2, ref_d2)
