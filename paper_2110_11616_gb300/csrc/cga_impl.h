@@ -308,18 +308,44 @@ __host__ __device__ inline unsigned long long tree_key(uint32_t x, uint32_t y, u
   }
   return k;
 }
+// Bounding box of a node's occupied children, in child units (0..3 per axis):
+// lo_x | hi_x << 2 | lo_y << 4 | hi_y << 6 | lo_z << 8 | hi_z << 10, from its
+// child set m (m != 0; bit c = cx << 4 | cy << 2 | cz).
+__host__ __device__ inline uint32_t tree_box_code(unsigned long long m) {
+  const uint32_t xo = ((m & 0xFFFFull) ? 1u : 0u) | (((m >> 16) & 0xFFFFull) ? 2u : 0u) |
+                      (((m >> 32) & 0xFFFFull) ? 4u : 0u) | ((m >> 48) ? 8u : 0u);
+  const uint32_t t = (uint32_t)((m | (m >> 16) | (m >> 32) | (m >> 48)) & 0xFFFFull);
+  const uint32_t yo = ((t & 0xFu) ? 1u : 0u) | ((t & 0xF0u) ? 2u : 0u) | ((t & 0xF00u) ? 4u : 0u) |
+                      ((t & 0xF000u) ? 8u : 0u);
+  const uint32_t zo = (t | (t >> 4) | (t >> 8) | (t >> 12)) & 0xFu;
+  uint32_t code = 0;
+  const uint32_t occ[3] = {xo, yo, zo};
+  for (int a = 0; a < 3; ++a) {
+    uint32_t lo = 0, hi = 3;
+    while (!((occ[a] >> lo) & 1u)) ++lo;
+    while (!((occ[a] >> hi) & 1u)) --hi;
+    code |= (lo | hi << 2) << (4 * a);
+  }
+  return code;
+}
+// A node of level l >= 2 keeps the box of its occupied voxels at the
+// granularity of its grandchildren (cells of 4^(l-2) voxels; 16 per axis of
+// the node): lo_x | hi_x << 4 | lo_y << 8 | hi_y << 12 | lo_z << 16 | hi_z << 20.
 struct TreeView {
   const unsigned long long* brick;        // level 1: voxel occupancy of each brick
-  const uint4* node[kTreeMaxLevels + 1];  // level l >= 2: {child set lo, hi, first child, 0}
+  const uint16_t* bcode;                  // level 1: tree_box_code of each brick (voxel units)
+  const uint4* node[kTreeMaxLevels + 1];  // level l >= 2: {child set lo, hi, first child,
+                                          //  box of the voxels in grandchild units}
   uint32_t cap[kTreeMaxLevels + 1];       // entries reserved per level (a search never reads beyond)
   uint32_t levels;                        // 0: no tree
 };
 // Capacity of every level (cap[0]: voxels) and the bytes of the tree arrays
-// (offsets from one base: off[1] bricks, off[l] nodes of level l, off[0] the
-// device counts, one 32-bit word per level).
+// (offsets from one base: off[1] bricks, off_bcode their box codes, off[l]
+// nodes of level l, off[0] the device counts, one 32-bit word per level).
 struct TreeLayout {
   uint64_t cap[kTreeMaxLevels + 1];
   size_t off[kTreeMaxLevels + 1];
+  size_t off_bcode;
   size_t bytes;
   uint32_t levels;
 };

@@ -652,7 +652,10 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
     // chosen child's record is already in a register when the warp enters it.
     // The bound of child c is the box of its occupied sub-cells (its box code)
     // inside its cell of 4^(lvl-1) voxels per axis.
-    const uint32_t sh = 2 * (lvl - 1), ss = sh - 2;
+    // box codes: bricks (children of level 2) in voxels, 2 bits per bound;
+    // nodes in their grandchild units (4^(lvl-3) voxels), 4 bits per bound
+    const uint32_t sh = 2 * (lvl - 1);
+    const uint32_t ss = lvl == 2 ? 0u : sh - 4, fb = lvl == 2 ? 2u : 4u, fm = (1u << fb) - 1u;
     const bool h0 = (rem >> lane) & 1ull, h1 = (rem >> (lane + 32)) & 1ull;
     const uint32_t i0 = first + (uint32_t)__popcll(mask & ((1ull << lane) - 1ull));
     const uint32_t i1 = first + (uint32_t)__popcll(mask & ((1ull << (lane + 32)) - 1ull));
@@ -684,16 +687,16 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
       if (h1) lb1 = (D)lbc[depth * 64 + 32 + lane];
     } else if (h0) {
       const uint32_t k = c0.w;
-      const uint32_t lx = k & 3u, hx = (k >> 2) & 3u, ly = (k >> 4) & 3u, hy = (k >> 6) & 3u,
-                     lz = (k >> 8) & 3u, hz = (k >> 10) & 3u;
+      const uint32_t lx = k & fm, hx = (k >> fb) & fm, ly = (k >> (2 * fb)) & fm,
+                     hy = (k >> (3 * fb)) & fm, lz = (k >> (4 * fb)) & fm, hz = (k >> (5 * fb)) & fm;
       lb0 = axis_lb2<D>(q.x, X0 + (lx << ss), (hx - lx + 1) << ss) +
             axis_lb2<D>(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
             axis_lb2<D>(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
     }
     if (!cached && h1) {
       const uint32_t k = c1.w;
-      const uint32_t lx = k & 3u, hx = (k >> 2) & 3u, ly = (k >> 4) & 3u, hy = (k >> 6) & 3u,
-                     lz = (k >> 8) & 3u, hz = (k >> 10) & 3u;
+      const uint32_t lx = k & fm, hx = (k >> fb) & fm, ly = (k >> (2 * fb)) & fm,
+                     hy = (k >> (3 * fb)) & fm, lz = (k >> (4 * fb)) & fm, hz = (k >> (5 * fb)) & fm;
       lb1 = axis_lb2<D>(q.x, X1 + (lx << ss), (hx - lx + 1) << ss) +
             axis_lb2<D>(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
             axis_lb2<D>(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
@@ -836,15 +839,9 @@ __device__ __forceinline__ uint32_t stored_index(const NnSeg& sg, unsigned long 
   const uint32_t slab = sg.xdir != nullptr ? __ldg(sg.xdir + x) : warp_lower_bound_u16(a.idx2, 0, h, x);
   const uint32_t ys = __ldg(a.ptr2 + slab), ye = __ldg(a.ptr2 + slab + 1);
   const uint32_t c = warp_lower_bound_u16(a.idx1, ys, ye, y);
-  uint32_t zs, ze;
-  if (sg.ctab != nullptr) {
-    const uint4 e = __ldg(sg.ctab + c);
-    zs = e.x;
-    ze = e.y;
-  } else {
-    zs = __ldg(a.ptr1 + c);
-    ze = __ldg(a.ptr1 + c + 1);
-  }
+  // the column's voxel range from Y_pointer (4 bytes a column; the 16-byte
+  // column table is left out of L2's working set here)
+  const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
   return warp_lower_bound_u16(a.idx0, zs, ze, z);
 }
 
@@ -870,7 +867,9 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
     const NnSeg& sg = segs != nullptr ? segs[find_nn_seg(segs, S, tile)] : inline_seg;
     const uint32_t local = slot - sg.tile_base * (uint32_t)kTile;
     if (local >= sg.m) continue;
-    const uint32_t j = sorted ? (uint32_t)order[slot] : local;
+    // queries, the order and the results stream through once: loaded and
+    // stored evict-first, so that L2 keeps the CGA and the search structures
+    const uint32_t j = sorted ? (uint32_t)__ldcs(order + slot) : local;
     if (j >= sg.m) continue;  // a caller-given order that is not a permutation
     const Levels& a = sg.a;
     const uint32_t u = (uint32_t)a.hdr->cnt[0], h = (uint32_t)a.hdr->cnt[2];
@@ -885,7 +884,7 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
       valid = true;
     } else {
       const float* p = sg.q + 3 * (size_t)j;
-      const float px = p[0], py = p[1], pz = p[2];
+      const float px = __ldcs(p), py = __ldcs(p + 1), pz = __ldcs(p + 2);
       valid = isfinite(px) && isfinite(py) && isfinite(pz);
       qx = valid ? (int)quantize_query(px, sg.scale, sg.off[0]) : 0;
       qy = valid ? (int)quantize_query(py, sg.scale, sg.off[1]) : 0;
@@ -893,8 +892,8 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
     }
     if (!valid || u == 0) {
       if (lane == 0) {
-        sg.idx[j] = 0xffffffffu;
-        sg.d2[j] = ~0ull;
+        __stcs(sg.idx + j, 0xffffffffu);
+        __stcs(sg.d2 + j, ~0ull);
       }
       continue;
     }
@@ -928,8 +927,8 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
         }
         const uint32_t ix = d2 != ~0ull ? stored_index(sg, key) : 0xffffffffu;
         if (lane == 0) {
-          sg.idx[j] = ix;
-          sg.d2[j] = d2;
+          __stcs(sg.idx + j, ix);
+          __stcs(sg.d2 + j, d2);
         }
         continue;
       }
@@ -946,8 +945,8 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
       search_fine(a, sg.xdir, sg.ctab, h, qx, qy, qz, cqx, cqy, cqz, lane, best);
     }
     if (lane == 0) {
-      sg.idx[j] = best.idx;
-      sg.d2[j] = best.d2;
+      __stcs(sg.idx + j, best.idx);
+      __stcs(sg.d2 + j, best.d2);
     }
   }
 }

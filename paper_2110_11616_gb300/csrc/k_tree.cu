@@ -38,11 +38,15 @@ __global__ void k_tree_init(const Header* __restrict__ src, uint32_t* counts, ui
 // level below (level 1: the voxels' tree keys): the distinct P >> 6 in order,
 // each with its child set (bits P & 63) and the index in P of its first child.
 // A tile of kTile prefixes is 256 threads x 16 consecutive entries.
+// The box of a level-l node (l >= 2) comes from its children's boxes: a
+// brick's (ccode1, voxel units) or a node's (cnode[.].w, in the child's
+// grandchild units), each placed at its child position.
 __global__ void __launch_bounds__(kThreads) k_tree_level(
     const unsigned long long* __restrict__ P, const uint32_t* n_in,
     unsigned long long* __restrict__ NP, unsigned long long* __restrict__ brick,
-    uint4* __restrict__ node, uint32_t* n_out, uint32_t* look, uint32_t* counter,
-    unsigned int* err) {
+    uint16_t* __restrict__ bcode, uint4* __restrict__ node,
+    const uint16_t* __restrict__ ccode1, const uint4* __restrict__ cnode, uint32_t* n_out,
+    uint32_t* look, uint32_t* counter, unsigned int* err) {
   __shared__ uint32_t s_warp[kWarps];
   __shared__ uint32_t s_tile, s_excl;
   const uint32_t tid = threadIdx.x;
@@ -86,18 +90,47 @@ __global__ void __launch_bounds__(kThreads) k_tree_level(
     if (!((heads >> i) & 1u)) continue;
     const uint32_t e = start + e0 + i;
     const unsigned long long pr = k[i] >> 6;
-    unsigned long long mask = 1ull << (k[i] & 63);
+    unsigned long long mask = 0;
+    uint32_t lo[3] = {15u, 15u, 15u}, hi[3] = {0u, 0u, 0u};
     // a node has at most 64 children, so its run ends within 64 entries
-    for (uint32_t f = e + 1; f < n && f < e + 64; ++f) {
-      const unsigned long long v = __ldg(P + f);
+    for (uint32_t f = e; f < n && f < e + 64; ++f) {
+      const unsigned long long v = f == e ? k[i] : __ldg(P + f);
       if ((v >> 6) != pr) break;
-      mask |= 1ull << (v & 63);
+      const uint32_t c = (uint32_t)(v & 63);
+      mask |= 1ull << c;
+      if (brick == nullptr) {
+        // the child's box in this node's grandchild units
+        const uint32_t pos[3] = {c >> 4, (c >> 2) & 3u, c & 3u};
+        uint32_t cl[3], ch[3];
+        if (ccode1 != nullptr) {
+          const uint32_t cc = __ldg(ccode1 + f);  // brick: voxel units, 2 bits per bound
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            cl[a] = (cc >> (4 * a)) & 3u;
+            ch[a] = (cc >> (4 * a + 2)) & 3u;
+          }
+        } else {
+          const uint32_t cc = __ldg(&cnode[f].w);  // node: its grandchild units, 4 bits
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            cl[a] = ((cc >> (8 * a)) & 15u) >> 2;
+            ch[a] = ((cc >> (8 * a + 4)) & 15u) >> 2;
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = min(lo[a], pos[a] * 4 + cl[a]);
+          hi[a] = max(hi[a], pos[a] * 4 + ch[a]);
+        }
+      }
     }
     if (NP != nullptr) NP[j] = pr;
     if (brick != nullptr) {
       brick[j] = mask;
+      bcode[j] = (uint16_t)tree_box_code(mask);
     } else {
-      node[j] = make_uint4((uint32_t)mask, (uint32_t)(mask >> 32), e, 0u);
+      const uint32_t box = lo[0] | hi[0] << 4 | lo[1] << 8 | hi[1] << 12 | lo[2] << 16 | hi[2] << 20;
+      node[j] = make_uint4((uint32_t)mask, (uint32_t)(mask >> 32), e, box);
     }
     ++j;
   }
@@ -127,6 +160,8 @@ TreeLayout tree_layout(uint32_t bits, uint64_t cap) {
   p += align_up(sizeof(Header) + (kTreeMaxLevels + 1) * 4);
   L.off[1] = p;
   p += align_up(std::max<uint64_t>(L.cap[1], 1) * 8);
+  L.off_bcode = p;
+  p += align_up(std::max<uint64_t>(L.cap[1], 1) * 2);
   for (uint32_t l = 2; l <= L.levels; ++l) {
     L.off[l] = p;
     p += align_up(std::max<uint64_t>(L.cap[l], 1) * sizeof(uint4));
@@ -139,6 +174,7 @@ TreeView tree_view(const TreeLayout& L, void* mem) {
   TreeView v{};
   char* b = static_cast<char*>(mem);
   v.brick = reinterpret_cast<const unsigned long long*>(b + L.off[1]);
+  v.bcode = reinterpret_cast<const uint16_t*>(b + L.off_bcode);
   for (uint32_t l = 2; l <= L.levels; ++l) v.node[l] = reinterpret_cast<const uint4*>(b + L.off[l]);
   for (uint32_t l = 1; l <= L.levels; ++l) v.cap[l] = (uint32_t)std::max<uint64_t>(L.cap[l], 1);
   v.levels = L.levels;
@@ -198,9 +234,12 @@ cudaError_t run_tree_build(const Levels& a, const TreeLayout& L, void* mem, void
     const uint32_t lt = tiles_of(L.cap[l - 1]);
     unsigned long long* np = l < L.levels ? buf[cur ^ 1] : nullptr;
     unsigned long long* br = l == 1 ? reinterpret_cast<unsigned long long*>(m + L.off[1]) : nullptr;
+    uint16_t* bc = l == 1 ? reinterpret_cast<uint16_t*>(m + L.off_bcode) : nullptr;
     uint4* nd = l >= 2 ? reinterpret_cast<uint4*>(m + L.off[l]) : nullptr;
-    k_tree_level<<<lt, kThreads, 0, stream>>>(buf[cur], counts + (l - 1), np, br, nd, counts + l,
-                                             w, w + lt, herr);
+    const uint16_t* cc1 = l == 2 ? reinterpret_cast<const uint16_t*>(m + L.off_bcode) : nullptr;
+    const uint4* cn = l >= 3 ? reinterpret_cast<const uint4*>(m + L.off[l - 1]) : nullptr;
+    k_tree_level<<<lt, kThreads, 0, stream>>>(buf[cur], counts + (l - 1), np, br, bc, nd, cc1, cn,
+                                             counts + l, w, w + lt, herr);
     count_launch(1);
     w += lt + 1;
     cur ^= 1;
