@@ -626,9 +626,43 @@ __device__ __forceinline__ void tree_brick(unsigned long long m, uint32_t bx, ui
   }
 }
 
+// Bound of a child cell from its box code: the box of its occupied voxels
+// (fb-bit bounds in cells of 2^ss voxels) inside the cell at voxel origin
+// (X, Y, Z).
+template <typename D>
+__device__ __forceinline__ D child_lb(const Qry& q, uint32_t X, uint32_t Y, uint32_t Z,
+                                      uint32_t k, uint32_t fb, uint32_t fm, uint32_t ss) {
+  const uint32_t lx = k & fm, hx = (k >> fb) & fm, ly = (k >> (2 * fb)) & fm,
+                 hy = (k >> (3 * fb)) & fm, lz = (k >> (4 * fb)) & fm, hz = (k >> (5 * fb)) & fm;
+  return axis_lb2<D>(q.x, X + (lx << ss), (hx - lx + 1) << ss) +
+         axis_lb2<D>(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
+         axis_lb2<D>(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
+}
+
+// The warp's smallest key among the voxels of the bricks given to this lane
+// (occupancy m, voxel origin (bx, by, bz)) that beat `best`, merged into it.
+template <typename D>
+__device__ __forceinline__ void brick_voxels(unsigned long long m, uint32_t bx, uint32_t by,
+                                             uint32_t bz, const Qry& q, uint32_t b, D& cd,
+                                             unsigned long long& ck) {
+  while (m != 0ull) {
+    const uint32_t v = (uint32_t)__ffsll((long long)m) - 1u;
+    m &= m - 1ull;
+    const uint32_t x = bx + (v >> 4), y = by + ((v >> 2) & 3u), z = bz + (v & 3u);
+    const D dx = absdiff(x, q.x), dy = absdiff(y, q.y), dz = absdiff(z, q.z);
+    const D d = dx * dx + dy * dy + dz * dz;
+    const unsigned long long k = ((unsigned long long)x << (2 * b)) |
+                                 ((unsigned long long)y << b) | z;
+    if (d < cd || (d == cd && k < ck)) {
+      cd = d;
+      ck = k;
+    }
+  }
+}
+
 template <typename D>
 __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFrame* fr,
-                            uint32_t* lbc, BestKey<D>& best) {
+                            uint32_t* lbc, uint32_t* pos, BestKey<D>& best) {
   const uint32_t full = 0xffffffffu;
   const TreeView& tv = sg.tree;
   const uint32_t T = tv.levels, b = sg.a.bits;
@@ -641,74 +675,86 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
   unsigned long long mask = r0.x | ((unsigned long long)r0.y << 32), rem = mask;
   uint32_t first = r0.z, ox = 0, oy = 0, oz = 0;
   int depth = 0;
-  const uint32_t cy = (lane >> 2) & 3u, cz = lane & 3u, cx0 = lane >> 4;
   bool s_pop = false;
   // fresh: the current frame was just entered (its children's bounds are
   // computed and, above level 2, kept in lbc[depth] for the way back)
   bool fresh = true;
   while (true) {
-    // Each lane loads the records of its two children (a node's child set and
-    // first child, or a brick's voxels) with their box codes, so that the
-    // chosen child's record is already in a register when the warp enters it.
-    // The bound of child c is the box of its occupied sub-cells (its box code)
-    // inside its cell of 4^(lvl-1) voxels per axis.
+    // a stored voxel at distance 0 is the answer (voxels are unique, so no
+    // other voxel can tie with it)
+    if (best.d2 == (D)0) break;
+    // The children still to visit, compacted: lane k takes the k-th of them
+    // (and the (k+32)-th when more than 32 are left), so a node with few
+    // children keeps few lanes busy instead of two fixed slots per lane.
+    // Each lane loads the record of its child (a node's child set and first
+    // child, or a brick's voxels) with its box code, so that the chosen
+    // child's record is already in a register when the warp enters it.
+    const uint32_t rlo = (uint32_t)rem, rhi = (uint32_t)(rem >> 32);
+    const uint32_t nlo = __popc(rlo), nr = nlo + __popc(rhi);
+    const uint32_t ltm = lanemask_lt();
+    __syncwarp();
+    if ((rlo >> lane) & 1u) pos[__popc(rlo & ltm)] = lane;
+    if ((rhi >> lane) & 1u) pos[nlo + __popc(rhi & ltm)] = lane + 32;
+    __syncwarp();
+    const bool two = nr > 32;  // warp-uniform
+    const bool h0 = lane < nr, h1 = two && lane + 32 < nr;
+    const uint32_t c0 = h0 ? pos[lane] : 0u, c1 = h1 ? pos[lane + 32] : 0u;
     // box codes: bricks (children of level 2) in voxels, 2 bits per bound;
     // nodes in their grandchild units (4^(lvl-3) voxels), 4 bits per bound
     const uint32_t sh = 2 * (lvl - 1);
     const uint32_t ss = lvl == 2 ? 0u : sh - 4, fb = lvl == 2 ? 2u : 4u, fm = (1u << fb) - 1u;
-    const bool h0 = (rem >> lane) & 1ull, h1 = (rem >> (lane + 32)) & 1ull;
-    const uint32_t i0 = first + (uint32_t)__popcll(mask & ((1ull << lane) - 1ull));
-    const uint32_t i1 = first + (uint32_t)__popcll(mask & ((1ull << (lane + 32)) - 1ull));
     const uint32_t cap = tv.cap[lvl - 1];
-    uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t i0 = first + (uint32_t)__popcll(mask & ((1ull << c0) - 1ull));
+    const uint32_t i1 = first + (uint32_t)__popcll(mask & ((1ull << c1) - 1ull));
     const bool cached = CGA_NN_TREE_CACHE && !fresh;
-    if (cached) {
-      // back in a frame above level 2: its bounds are kept (no loads)
-    } else if (lvl == 2) {
-      if (h0 && i0 < cap) {
-        const unsigned long long m0 = __ldg(tv.brick + i0);
-        c0 = make_uint4((uint32_t)m0, (uint32_t)(m0 >> 32), 0u, __ldg(tv.bcode + i0));
-      }
-      if (h1 && i1 < cap) {
-        const unsigned long long m1 = __ldg(tv.brick + i1);
-        c1 = make_uint4((uint32_t)m1, (uint32_t)(m1 >> 32), 0u, __ldg(tv.bcode + i1));
-      }
-    } else {
-      const uint4* nd = tv.node[lvl - 1];
-      if (h0 && i0 < cap) c0 = __ldg(nd + i0);
-      if (h1 && i1 < cap) c1 = __ldg(nd + i1);
-    }
-    const uint32_t Y = ((oy << 2) + cy) << sh, Z = ((oz << 2) + cz) << sh;
-    const uint32_t X0 = ((ox << 2) + cx0) << sh, X1 = X0 + (2u << sh);
+    uint4 k0 = make_uint4(0u, 0u, 0u, 0u), k1 = make_uint4(0u, 0u, 0u, 0u);
     D lb0 = (D)~(D)0, lb1 = (D)~(D)0;
     if (cached) {
-      // (a kept bound saturates at 2^32 - 1, still a lower bound)
-      if (h0) lb0 = (D)lbc[depth * 64 + lane];
-      if (h1) lb1 = (D)lbc[depth * 64 + 32 + lane];
-    } else if (h0) {
-      const uint32_t k = c0.w;
-      const uint32_t lx = k & fm, hx = (k >> fb) & fm, ly = (k >> (2 * fb)) & fm,
-                     hy = (k >> (3 * fb)) & fm, lz = (k >> (4 * fb)) & fm, hz = (k >> (5 * fb)) & fm;
-      lb0 = axis_lb2<D>(q.x, X0 + (lx << ss), (hx - lx + 1) << ss) +
-            axis_lb2<D>(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
-            axis_lb2<D>(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
-    }
-    if (!cached && h1) {
-      const uint32_t k = c1.w;
-      const uint32_t lx = k & fm, hx = (k >> fb) & fm, ly = (k >> (2 * fb)) & fm,
-                     hy = (k >> (3 * fb)) & fm, lz = (k >> (4 * fb)) & fm, hz = (k >> (5 * fb)) & fm;
-      lb1 = axis_lb2<D>(q.x, X1 + (lx << ss), (hx - lx + 1) << ss) +
-            axis_lb2<D>(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
-            axis_lb2<D>(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
+      // back in a frame above level 2: its bounds are kept (no loads; a kept
+      // bound saturates at 2^32 - 1, still a lower bound)
+      if (h0) lb0 = (D)lbc[depth * 64 + c0];
+      if (h1) lb1 = (D)lbc[depth * 64 + c1];
+    } else {
+      if (lvl == 2) {
+        if (h0 && i0 < cap) {
+          const unsigned long long m0 = __ldg(tv.brick + i0);
+          k0 = make_uint4((uint32_t)m0, (uint32_t)(m0 >> 32), 0u, __ldg(tv.bcode + i0));
+        }
+        if (h1 && i1 < cap) {
+          const unsigned long long m1 = __ldg(tv.brick + i1);
+          k1 = make_uint4((uint32_t)m1, (uint32_t)(m1 >> 32), 0u, __ldg(tv.bcode + i1));
+        }
+      } else {
+        const uint4* nd = tv.node[lvl - 1];
+        if (h0 && i0 < cap) k0 = __ldg(nd + i0);
+        if (h1 && i1 < cap) k1 = __ldg(nd + i1);
+      }
+      if (h0) {
+        lb0 = child_lb<D>(q, ((ox << 2) + (c0 >> 4)) << sh, ((oy << 2) + ((c0 >> 2) & 3u)) << sh,
+                          ((oz << 2) + (c0 & 3u)) << sh, k0.w, fb, fm, ss);
+      }
+      if (two && h1) {
+        lb1 = child_lb<D>(q, ((ox << 2) + (c1 >> 4)) << sh, ((oy << 2) + ((c1 >> 2) & 3u)) << sh,
+                          ((oz << 2) + (c1 & 3u)) << sh, k1.w, fb, fm, ss);
+      }
+      if (CGA_NN_TREE_CACHE && lvl > 2) {
+        if (h0) lbc[depth * 64 + c0] = lb0 > (D)0xfffffffeu ? 0xffffffffu : (uint32_t)lb0;
+        if (h1) lbc[depth * 64 + c1] = lb1 > (D)0xfffffffeu ? 0xffffffffu : (uint32_t)lb1;
+      }
     }
     const bool in0 = h0 && i0 < cap && lb0 <= best.d2;
     const bool in1 = h1 && i1 < cap && lb1 <= best.d2;
     const uint32_t s0 = __ballot_sync(full, in0), s1 = __ballot_sync(full, in1);
-    if (CGA_NN_TREE_CACHE && !cached && lvl > 2) {
-      lbc[depth * 64 + lane] = lb0 > (D)0xfffffffeu ? 0xffffffffu : (uint32_t)lb0;
-      lbc[depth * 64 + 32 + lane] = lb1 > (D)0xfffffffeu ? 0xffffffffu : (uint32_t)lb1;
+    // the surviving children as a child set
+    const uint32_t o0 = in0 ? c0 : 64u, o1 = in1 ? c1 : 64u;
+    unsigned long long surv = 0ull;
+    if (s0 | s1) {
+      const uint32_t bl0 = o0 < 32 ? 1u << o0 : 0u, bh0 = o0 >= 32 && o0 < 64 ? 1u << (o0 - 32) : 0u;
+      const uint32_t bl1 = o1 < 32 ? 1u << o1 : 0u, bh1 = o1 >= 32 && o1 < 64 ? 1u << (o1 - 32) : 0u;
+      const uint32_t sl = __reduce_or_sync(full, bl0 | bl1), shi = __reduce_or_sync(full, bh0 | bh1);
+      surv = ((unsigned long long)shi << 32) | sl;
     }
-    if (lvl == 2 && (s0 | s1) != 0u) {
+    if (lvl == 2 && surv != 0ull) {
       // Children are bricks.  Without a candidate yet only the nearest brick
       // is examined (its voxels set a bound that prunes its siblings), else
       // every lane examines the voxels of its surviving bricks (a loop over
@@ -718,52 +764,40 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
       uint32_t cs_first = 64;
       if (only_nearest) {
         D v = in0 ? lb0 : (D)~(D)0;
-        uint32_t c = lane;
+        uint32_t c = c0;
         if (in1 && lb1 < v) {
           v = lb1;
-          c = lane + 32;
+          c = c1;
         }
         const D mv = warp_min_d(v);
         const uint32_t win = __ballot_sync(full, (in0 || in1) && v == mv);
         cs_first = __shfl_sync(full, c, __ffs(win) - 1);
-        e0 = in0 && cs_first == lane;
-        e1 = in1 && cs_first == lane + 32;
+        e0 = in0 && cs_first == c0;
+        e1 = in1 && cs_first == c1;
       }
       D cd = (D)~(D)0;
       unsigned long long ck = ~0ull;
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        if (!(t == 0 ? e0 : e1)) continue;
-        const uint4 r = t == 0 ? c0 : c1;
-        const uint32_t cx = cx0 + 2 * t;
-        const uint32_t bx = ((ox << 2) + cx) << 2, by = ((oy << 2) + cy) << 2,
-                       bz = ((oz << 2) + cz) << 2;
-        unsigned long long m = r.x | ((unsigned long long)r.y << 32);
-        while (m != 0ull) {
-          const uint32_t v = (uint32_t)__ffsll((long long)m) - 1u;
-          m &= m - 1ull;
-          const uint32_t x = bx + (v >> 4), y = by + ((v >> 2) & 3u), z = bz + (v & 3u);
-          const D dx = absdiff(x, q.x), dy = absdiff(y, q.y), dz = absdiff(z, q.z);
-          const D d = dx * dx + dy * dy + dz * dz;
-          const unsigned long long k = ((unsigned long long)x << (2 * b)) |
-                                       ((unsigned long long)y << b) | z;
-          if (d < cd || (d == cd && k < ck)) {
-            cd = d;
-            ck = k;
-          }
-        }
+      if (e0) {
+        brick_voxels<D>(k0.x | ((unsigned long long)k0.y << 32),
+                        ((ox << 2) + (c0 >> 4)) << 2, ((oy << 2) + ((c0 >> 2) & 3u)) << 2,
+                        ((oz << 2) + (c0 & 3u)) << 2, q, b, cd, ck);
+      }
+      if (e1) {
+        brick_voxels<D>(k1.x | ((unsigned long long)k1.y << 32),
+                        ((ox << 2) + (c1 >> 4)) << 2, ((oy << 2) + ((c1 >> 2) & 3u)) << 2,
+                        ((oz << 2) + (c1 & 3u)) << 2, q, b, cd, ck);
       }
       const bool better = cd < best.d2 || (cd == best.d2 && ck < best.key);
       if (__any_sync(full, better)) {
         best.warp_min_of(better ? cd : best.d2, better ? ck : best.key);
       }
       if (only_nearest) {
-        rem = ((((unsigned long long)s1) << 32) | s0) & ~(1ull << cs_first);
+        rem = surv & ~(1ull << cs_first);
         continue;
       }
       s_pop = true;
     }
-    if ((s0 | s1) == 0u || s_pop) {
+    if (surv == 0ull || s_pop) {
       s_pop = false;
       if (depth == 0) break;
       --depth;
@@ -782,13 +816,13 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
     // the surviving child with the least bound, and its record from the lane
     // that loaded it
     D v = in0 ? lb0 : (D)~(D)0;
-    uint32_t c = lane;
+    uint32_t c = c0;
     if (in1 && lb1 < v) {
       v = lb1;
-      c = lane + 32;
+      c = c1;
     }
     const D mv = warp_min_d(v);
-    const uint32_t win = __ballot_sync(full, v == mv);
+    const uint32_t win = __ballot_sync(full, (in0 || in1) && v == mv);
     const int owner = __ffs(win) - 1;
     const uint32_t cs = __shfl_sync(full, c, owner);
     uint32_t rx, ry, rz;
@@ -799,12 +833,12 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
       ry = r.y;
       rz = r.z;
     } else {
-      const uint4 mine = cs >= 32 ? c1 : c0;
+      const uint4 mine = cs == c1 && in1 ? k1 : k0;
       rx = __shfl_sync(full, mine.x, owner);
       ry = __shfl_sync(full, mine.y, owner);
       rz = __shfl_sync(full, mine.z, owner);
     }
-    rem = ((((unsigned long long)s1) << 32) | s0) & ~(1ull << cs);
+    rem = surv & ~(1ull << cs);
     const uint32_t nx = (ox << 2) + (cs >> 4), ny = (oy << 2) + ((cs >> 2) & 3u),
                    nz = (oz << 2) + (cs & 3u);
     // (lvl > 2 here: a level-2 node was settled above.)  The last surviving
@@ -858,6 +892,7 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
               const unsigned int* __restrict__ order_err) {
   __shared__ TreeFrame s_fr[NC == 3 ? 8 * kTreeMaxLevels : 1];
   __shared__ uint32_t s_lbc[NC == 3 && CGA_NN_TREE_CACHE ? 8 * kTreeMaxLevels * 64 : 1];
+  __shared__ uint32_t s_pos[NC == 3 ? 8 * 64 : 1];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const bool sorted = order != nullptr && (order_err == nullptr || *order_err == 0u);
@@ -909,19 +944,20 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
         const Qry qq{qx, qy, qz, cqx, cqy, cqz};
         TreeFrame* fr = s_fr + (threadIdx.x >> 5) * kTreeMaxLevels;
         uint32_t* lbc = CGA_NN_TREE_CACHE ? s_lbc + (threadIdx.x >> 5) * kTreeMaxLevels * 64 : s_lbc;
+        uint32_t* pos = s_pos + (threadIdx.x >> 5) * 64;
         const bool narrow = b <= 15 && (uint32_t)qx == cqx && (uint32_t)qy == cqy &&
                             (uint32_t)qz == cqz;
         unsigned long long d2 = ~0ull, key = ~0ull;
         if (narrow) {
           BestKey<uint32_t> bk{0xffffffffu, ~0ull};
-          search_tree<uint32_t>(sg, qq, lane, fr, lbc, bk);
+          search_tree<uint32_t>(sg, qq, lane, fr, lbc, pos, bk);
           if (bk.d2 != 0xffffffffu) {
             d2 = bk.d2;
             key = bk.key;
           }
         } else {
           BestKey<unsigned long long> bk{~0ull, ~0ull};
-          search_tree<unsigned long long>(sg, qq, lane, fr, lbc, bk);
+          search_tree<unsigned long long>(sg, qq, lane, fr, lbc, pos, bk);
           d2 = bk.d2;
           key = bk.key;
         }
