@@ -140,11 +140,12 @@ cudaError_t run_sort_pipeline(const SortSeg* h_segs, int S, uint32_t total_tiles
 // Decode a CGA to uint32 (x, y, z) triples in CGA order.
 cudaError_t run_decode(const Levels& a, uint32_t* xyz, cudaStream_t stream);
 
-// Merge: sorted union of pairs of 3-level CGAs.  Splitter keys are taken at
-// every half-th point of each input (half = Tuning::merge_half <= kTile / 2);
-// between consecutive splitters (in key order) each input contributes at most
-// half points, so one tile of 2 * half <= kTile keys always holds the merged
-// run.
+// Merge: sorted union of pairs of 3-level CGAs, column by column.  Splitters
+// are taken at every half-th (x, y) column of each input (half =
+// Tuning::merge_half <= kTile / 2; `cap` below is a column capacity);
+// between consecutive splitters (in column-key order) each input contributes
+// at most half columns, so one tile of at most 2 * half columns always holds
+// the merged run.
 constexpr int kMergeHalf = kTile / 2;  // largest partition
 inline uint32_t merge_splitters(uint64_t cap, uint32_t half) {
   return cap > 0 ? (uint32_t)((cap - 1) / half) : 0u;
@@ -159,7 +160,7 @@ struct MergePair {
 };
 
 struct MergeScratch {
-  uint32_t* bounds;         // [(total_tiles + S) * 2]; pair p at 2 * (tile_base + p)
+  uint32_t* bounds;         // [(total_tiles + S) * 4]; pair p at 4 * (tile_base + p)
   uint32_t* ntiles;         // [S]
   uint32_t* clook;          // [total_tiles][3]
   uint32_t* counter;        // [1]

@@ -39,6 +39,18 @@ __global__ void __launch_bounds__(kThreads) k_decode(Levels a, uint32_t* __restr
 }
 
 // ------------------------------------------------------------------- merge
+// Merge (Eq. 1, Sec. V-A) of pairs of CGAs in one grid, column by column.
+// The (x, y) columns of both inputs are merged in key order (key x << b | y);
+// a column present in both gets the union of its two sorted z lists, a column
+// of one input keeps its z list.  Splitters sit at every `half`-th column of
+// each input; a cut at column key s takes, from both inputs, the columns with
+// key < s, so a column present in both never straddles two tiles and every
+// tile can settle its columns alone.  Per tile: the columns' keys (slab of
+// each column by a scatter of slab starts and a block max-scan), merge path,
+// per output column its voxel count, block scans, and one decoupled look-back
+// over the pair's tiles for the voxel, column and slab offsets; then each
+// output column writes its y, its Y_pointer and its z list, and each new x its
+// X_index and X_pointer entries.
 __device__ __forceinline__ int find_pair_spl(const MergePair* __restrict__ P, int S, uint32_t i) {
   int lo = 0, hi = S - 1;
   while (lo < hi) {
@@ -57,10 +69,15 @@ __device__ __forceinline__ int find_pair_tile(const MergePair* __restrict__ P, i
   return lo;
 }
 
-__device__ __forceinline__ uint32_t n_splitters(uint32_t u, uint32_t reserved, uint32_t half) {
-  const uint32_t k = u > 0 ? (u - 1) / half : 0u;
+// Splitters of an input with g columns (at most `reserved`).
+__device__ __forceinline__ uint32_t n_splitters(uint32_t g, uint32_t reserved, uint32_t half) {
+  const uint32_t k = g > 0 ? (g - 1) / half : 0u;
   return min(k, reserved);
 }
+
+// A tile bound: the first column of A and of B at or after the cut, and the
+// slab holding each of them (h for the end of the input).
+constexpr int kBoundWords = 4;
 
 // Output header, empty-CGA sentinels, first and last tile bounds.
 __global__ void k_merge_init(const MergePair* __restrict__ pairs, int S, uint32_t half,
@@ -68,15 +85,20 @@ __global__ void k_merge_init(const MergePair* __restrict__ pairs, int S, uint32_
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= S) return;
   const MergePair& P = pairs[p];
-  const uint32_t uA = (uint32_t)P.a.hdr->cnt[0], uB = (uint32_t)P.b.hdr->cnt[0];
-  const uint32_t NA = n_splitters(uA, P.spl_a, half), NB = n_splitters(uB, P.spl_b, half);
+  const uint32_t gA = (uint32_t)P.a.hdr->cnt[1], gB = (uint32_t)P.b.hdr->cnt[1];
+  const uint32_t hA = (uint32_t)P.a.hdr->cnt[2], hB = (uint32_t)P.b.hdr->cnt[2];
+  const uint32_t NA = n_splitters(gA, P.spl_a, half), NB = n_splitters(gB, P.spl_b, half);
   const uint32_t nt = NA + NB + 1;
   ntiles[p] = nt;
-  uint32_t* bnd = bounds + 2 * ((size_t)P.tile_base + p);
+  uint32_t* bnd = bounds + (size_t)kBoundWords * ((size_t)P.tile_base + p);
   bnd[0] = 0;
   bnd[1] = 0;
-  bnd[2 * nt] = uA;
-  bnd[2 * nt + 1] = uB;
+  bnd[2] = 0;
+  bnd[3] = 0;
+  bnd[kBoundWords * nt + 0] = gA;
+  bnd[kBoundWords * nt + 1] = gB;
+  bnd[kBoundWords * nt + 2] = hA;
+  bnd[kBoundWords * nt + 3] = hB;
   P.out.hdr->cnt[0] = 0;
   P.out.hdr->cnt[1] = 0;
   P.out.hdr->cnt[2] = 0;
@@ -85,13 +107,13 @@ __global__ void k_merge_init(const MergePair* __restrict__ pairs, int S, uint32_
   P.out.ptr2[0] = 0;
 }
 
-// Tile cuts, one warp per splitter.  Splitter k of A is A's key s at
-// position (k + 1) * half; its cut is (rank_A(s), rank_B(s)) = ((k + 1) *
-// half, #B keys < s), and its place among all splitters (A's before B's on
-// equal keys) is k + #B splitters < s, where B splitter j (the key at
-// (j + 1) * half) is below s exactly when (j + 1) * half < rank_B(s).  B's
-// splitters mirror this with #A keys <= s.  The Sec. V-A lookup gives the
-// ranks.
+// Tile cuts, one warp per splitter.  Splitter k of A is A's column c = (k +
+// 1) * half with key s; its cut is (c, #B columns < s), and its place among
+// all splitters (A's before B's on equal keys) is k + #B splitters < s, where
+// B splitter j (column (j + 1) * half) is below s exactly when (j + 1) * half
+// < #B columns < s.  B's splitters mirror this, counting A's splitters with
+// key <= s for the order but cutting A at key < s.  The ranks come from the
+// Sec. V-A lookup at column level (x in X_index, then y in that slab).
 __global__ void k_merge_cuts(const MergePair* __restrict__ pairs, int S, uint32_t total,
                              uint32_t half, uint32_t* bounds) {
   const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -100,47 +122,96 @@ __global__ void k_merge_cuts(const MergePair* __restrict__ pairs, int S, uint32_
   const int p = find_pair_spl(pairs, S, i);
   const MergePair& P = pairs[p];
   const uint32_t local = i - P.spl_base;
-  const uint32_t uA = (uint32_t)P.a.hdr->cnt[0], uB = (uint32_t)P.b.hdr->cnt[0];
-  const uint32_t NA = n_splitters(uA, P.spl_a, half), NB = n_splitters(uB, P.spl_b, half);
+  const uint32_t gA = (uint32_t)P.a.hdr->cnt[1], gB = (uint32_t)P.b.hdr->cnt[1];
+  const uint32_t NA = n_splitters(gA, P.spl_a, half), NB = n_splitters(gB, P.spl_b, half);
   const bool isA = local < P.spl_a;
   const uint32_t k = isA ? local : local - P.spl_a;
   if (k >= (isA ? NA : NB)) return;
   const Levels& own = isA ? P.a : P.b;
   const Levels& oth = isA ? P.b : P.a;
-  const unsigned long long s =
-      warp_key_at(own, (uint32_t)own.hdr->cnt[1], (uint32_t)own.hdr->cnt[2], (k + 1) * half);
+  const uint32_t hown = (uint32_t)own.hdr->cnt[2];
+  const uint32_t goth = (uint32_t)oth.hdr->cnt[1], hoth = (uint32_t)oth.hdr->cnt[2];
+  const uint32_t c = (k + 1) * half;  // < g of own
+  const uint32_t s_own = warp_search_le(own.ptr2, 0, hown - 1, c);
+  const uint32_t x = __ldg(own.idx2 + s_own), y = __ldg(own.idx1 + c);
+  // #oth columns with key < (x, y), whether (x, y) is one, and the slab
+  // holding the first column at or after the cut
+  const uint32_t xr = warp_lower_bound_u16(oth.idx2, 0, hoth, x);
+  uint32_t r = goth, slab_r = hoth;
   bool found = false;
-  const uint32_t r = warp_rank_of(oth, (uint32_t)oth.hdr->cnt[2], s, &found);
-  // other-side splitters before this one: below s (A's turn), or at most s (B's)
+  if (xr < hoth && __ldg(oth.idx2 + xr) == x) {
+    const uint32_t ys = __ldg(oth.ptr2 + xr), ye = __ldg(oth.ptr2 + xr + 1);
+    r = warp_lower_bound_u16(oth.idx1, ys, ye, y);
+    found = r < ye && __ldg(oth.idx1 + r) == y;
+    slab_r = r < ye ? xr : xr + 1;
+  } else if (xr < hoth) {
+    r = __ldg(oth.ptr2 + xr);
+    slab_r = xr;
+  }
   const uint32_t rk = isA ? r : r + (found ? 1u : 0u);
   const uint32_t before = rk > 0 ? min(isA ? NB : NA, (rk - 1) / half) : 0u;
   const uint32_t pos = k + before;
   if (lane == 0) {
-    uint32_t* bnd = bounds + 2 * ((size_t)P.tile_base + p);
-    bnd[2 * (pos + 1)] = isA ? (k + 1) * half : r;
-    bnd[2 * (pos + 1) + 1] = isA ? r : (k + 1) * half;
+    uint32_t* bnd = bounds + (size_t)kBoundWords * ((size_t)P.tile_base + p + pos + 1);
+    bnd[0] = isA ? c : r;
+    bnd[1] = isA ? r : c;
+    bnd[2] = isA ? s_own : slab_r;
+    bnd[3] = isA ? slab_r : s_own;
   }
 }
 
-// Merge one tile: decode both runs (at most MH points each) into shared
-// memory, merge-path split per thread, sequential merge, then the shared
-// dedupe + compaction.
+// Size of the union of two ascending z lists (in shared or global memory).
+__device__ __forceinline__ uint32_t union_count(const uint16_t* za, uint32_t na,
+                                                const uint16_t* zb, uint32_t nb) {
+  uint32_t i = 0, j = 0, n = 0;
+  while (i < na && j < nb) {
+    const uint32_t u = za[i], v = zb[j];
+    i += u <= v;
+    j += v <= u;
+    ++n;
+  }
+  return n + (na - i) + (nb - j);
+}
+
+// Write the union of two ascending z lists to out.
+__device__ __forceinline__ void union_write(const uint16_t* za, uint32_t na, const uint16_t* zb,
+                                            uint32_t nb, uint16_t* __restrict__ out) {
+  uint32_t i = 0, j = 0, n = 0;
+  while (i < na && j < nb) {
+    const uint32_t u = za[i], v = zb[j];
+    out[n++] = (uint16_t)min(u, v);
+    i += u <= v;
+    j += v <= u;
+  }
+  while (i < na) out[n++] = za[i++];
+  while (j < nb) out[n++] = zb[j++];
+}
+
+// z entries of each input a merge tile stages in shared memory (a tile whose
+// columns hold more reads them from global memory instead).
+template <int MH>
+constexpr int merge_stage() { return MH == 2048 ? 1536 : 6144; }
+
+// Merge one tile of at most MH columns of each input (one splitter spacing).
 template <int MH>
 __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __restrict__ pairs,
                                                           int S, const uint32_t* __restrict__ bounds,
                                                           const uint32_t* __restrict__ ntiles,
                                                           uint32_t* clook, uint32_t* counter) {
-  constexpr int IT = 2 * MH / kThreads;  // merged keys per thread
-  static_assert(IT * kThreads == 2 * MH && 2 * MH <= kTile, "merge tile shape");
-  __shared__ unsigned long long s_ab[2 * MH];
-  __shared__ uint16_t s_col[MH], s_slab[MH];
+  constexpr int IT = 2 * MH / kThreads;  // merged columns per thread
+  static_assert(IT * kThreads == 2 * MH && MH % kThreads == 0, "merge tile shape");
+  // column keys of A and B; merged keys and sources (the slab expansion of
+  // the columns uses the merged arrays' space before the merge)
+  constexpr int ZS = merge_stage<MH>();
+  __shared__ uint32_t s_ka[MH], s_kb[MH], s_mk[2 * MH];
+  __shared__ uint16_t s_ms[2 * MH];
+  __shared__ uint16_t s_za[ZS], s_zb[ZS];
   __shared__ uint32_t s_warp[kWarps];
-  __shared__ CompactSmem sm;
-  __shared__ Window s_wa, s_wb;
-  __shared__ unsigned long long s_prev, s_prev2[2];
-  __shared__ uint32_t s_tile, s_has_prev;
+  __shared__ uint32_t s_tile, s_tot[6], s_prevx, s_hasprev;
   __shared__ int s_p;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  uint16_t* s_sa = reinterpret_cast<uint16_t*>(s_mk);
+  uint16_t* s_sb = s_sa + MH;
+  const int tid = threadIdx.x;
   if (tid == 0) {
     const uint32_t t = atomicAdd(counter, 1u);
     s_tile = t;
@@ -153,102 +224,189 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
   const uint32_t lt = t - P.tile_base;
   const uint32_t nt = ntiles[p];
   if (lt >= nt) return;
-  const uint32_t* bnd = bounds + 2 * ((size_t)P.tile_base + p + lt);
-  uint32_t a0 = bnd[0], b0 = bnd[1], a1 = bnd[2], b1 = bnd[3];
+  const Levels &A = P.a, &B = P.b, &O = P.out;
+  const uint32_t b = O.bits, ymask = (1u << b) - 1u;
+  const uint32_t* bnd = bounds + (size_t)kBoundWords * ((size_t)P.tile_base + p + lt);
+  const uint32_t a0 = bnd[0], b0 = bnd[1], sa0 = bnd[2], sb0 = bnd[3];
+  const uint32_t a1 = bnd[4], b1 = bnd[5], sa1 = bnd[6], sb1 = bnd[7];
   uint32_t na = a1 - a0, nb = b1 - b0;
   const bool bad = a1 < a0 || b1 < b0 || na > (uint32_t)MH || nb > (uint32_t)MH;
   if (bad) {
     na = 0;
     nb = 0;
   }
-  const uint32_t gA = (uint32_t)P.a.hdr->cnt[1], hA = (uint32_t)P.a.hdr->cnt[2];
-  const uint32_t gB = (uint32_t)P.b.hdr->cnt[1], hB = (uint32_t)P.b.hdr->cnt[2];
-  // the tile's windows in both inputs and the key just before it: four
-  // independent warp-cooperative searches
-  if (w == 0) {
-    if (bad && lane == 0) atomicOr(&P.out.hdr->err, kErrInternal);
-    if (na) {
-      const Window wa = warp_window_of(P.a, gA, hA, a0, a1 - 1);
-      if (lane == 0) s_wa = wa;
-    }
-  } else if (w == 1) {
-    if (nb) {
-      const Window wb = warp_window_of(P.b, gB, hB, b0, b1 - 1);
-      if (lane == 0) s_wb = wb;
-    }
-  } else if (w == 2) {
-    const unsigned long long ka = a0 > 0 ? warp_key_at(P.a, gA, hA, a0 - 1) : 0ull;
-    if (lane == 0) s_prev2[0] = ka;
-  } else if (w == 3) {
-    const unsigned long long kb = b0 > 0 ? warp_key_at(P.b, gB, hB, b0 - 1) : 0ull;
-    if (lane == 0) s_prev2[1] = kb;
-  }
-  __syncthreads();
+  // the slab of the tile's last column: the slab of the next tile's first
+  // column, one less when that column opens its slab
+  const uint32_t saL = na ? (__ldg(A.ptr2 + sa1) == a1 ? sa1 - 1 : sa1) : sa0;
+  const uint32_t sbL = nb ? (__ldg(B.ptr2 + sb1) == b1 ? sb1 - 1 : sb1) : sb0;
+  for (uint32_t e = tid; e < na; e += kThreads) s_sa[e] = 0;
+  for (uint32_t e = tid; e < nb; e += kThreads) s_sb[e] = 0;
   if (tid == 0) {
-    // the predecessor key of the merged run is the larger of the two
-    s_prev = max(a0 > 0 ? s_prev2[0] : 0ull, b0 > 0 ? s_prev2[1] : 0ull);
-    s_has_prev = (a0 > 0 || b0 > 0) ? 1u : 0u;
+    if (bad) atomicOr(&O.hdr->err, kErrInternal);
+    // x of the column just before the tile (the larger of A's and B's)
+    uint32_t px = 0, pk = 0;
+    const bool hp = a0 > 0 || b0 > 0;
+    if (a0 > 0) {
+      const uint32_t s = __ldg(A.ptr2 + sa0) == a0 ? sa0 - 1 : sa0;
+      pk = ((uint32_t)__ldg(A.idx2 + s) << b) | __ldg(A.idx1 + a0 - 1);
+    }
+    if (b0 > 0) {
+      const uint32_t s = __ldg(B.ptr2 + sb0) == b0 ? sb0 - 1 : sb0;
+      pk = max(pk, ((uint32_t)__ldg(B.idx2 + s) << b) | __ldg(B.idx1 + b0 - 1));
+    }
+    px = pk >> b;
+    s_prevx = px;
+    s_hasprev = hp ? 1u : 0u;
   }
   __syncthreads();
-  const uint32_t bA = P.a.bits;
-  // decode both runs (tile-uniform branches: the window expansion has barriers)
-  if (na) {
-    const Window wa = s_wa;
-    expand_window(P.a, wa, a0, na, s_col, s_slab, s_warp);
-    for (uint32_t e = tid; e < na; e += kThreads) {
-      const uint32_t cr = s_col[e];
-      const uint32_t x = __ldg(P.a.idx2 + wa.x0 + s_slab[cr]), y = __ldg(P.a.idx1 + wa.c0 + cr);
-      s_ab[e] = ((unsigned long long)x << (2 * bA)) | ((unsigned long long)y << bA) |
-                __ldg(P.a.idx0 + a0 + e);
-    }
-    __syncthreads();
-  }
-  if (nb) {
-    const Window wb = s_wb;
-    expand_window(P.b, wb, b0, nb, s_col, s_slab, s_warp);
-    for (uint32_t e = tid; e < nb; e += kThreads) {
-      const uint32_t cr = s_col[e];
-      const uint32_t x = __ldg(P.b.idx2 + wb.x0 + s_slab[cr]), y = __ldg(P.b.idx1 + wb.c0 + cr);
-      s_ab[MH + e] = ((unsigned long long)x << (2 * bA)) | ((unsigned long long)y << bA) |
-                     __ldg(P.b.idx0 + b0 + e);
-    }
-  }
+  for (uint32_t s = sa0 + 1 + tid; s <= saL; s += kThreads) s_sa[__ldg(A.ptr2 + s) - a0] = (uint16_t)(s - sa0);
+  for (uint32_t s = sb0 + 1 + tid; s <= sbL; s += kThreads) s_sb[__ldg(B.ptr2 + s) - b0] = (uint16_t)(s - sb0);
   __syncthreads();
-  const uint32_t cnt = na + nb;
-  const uint32_t diag = min((uint32_t)(tid * IT), cnt);
-  uint32_t lo = diag > nb ? diag - nb : 0u, hi = min(diag, na);
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (s_ab[mid] <= s_ab[MH + diag - 1 - mid]) lo = mid + 1; else hi = mid;
+  block_max_scan_u16<MH / kThreads>(s_sa, na, s_warp);
+  block_max_scan_u16<MH / kThreads>(s_sb, nb, s_warp);
+  for (uint32_t e = tid; e < na; e += kThreads) {
+    s_ka[e] = ((uint32_t)__ldg(A.idx2 + sa0 + s_sa[e]) << b) | __ldg(A.idx1 + a0 + e);
   }
-  uint32_t i = lo, j = diag - lo;
-  unsigned long long r[IT];
+  for (uint32_t e = tid; e < nb; e += kThreads) {
+    s_kb[e] = ((uint32_t)__ldg(B.idx2 + sb0 + s_sb[e]) << b) | __ldg(B.idx1 + b0 + e);
+  }
+  // the tile's z entries of each input are one contiguous range: staged in
+  // shared memory by coalesced loads when they fit
+  const uint32_t zA0 = na ? __ldg(A.ptr1 + a0) : 0u, zA1 = na ? __ldg(A.ptr1 + a1) : 0u;
+  const uint32_t zB0 = nb ? __ldg(B.ptr1 + b0) : 0u, zB1 = nb ? __ldg(B.ptr1 + b1) : 0u;
+  const bool stA = zA1 - zA0 <= (uint32_t)ZS, stB = zB1 - zB0 <= (uint32_t)ZS;
+  if (stA) {
+    for (uint32_t e = tid; e < zA1 - zA0; e += kThreads) s_za[e] = __ldg(A.idx0 + zA0 + e);
+  }
+  if (stB) {
+    for (uint32_t e = tid; e < zB1 - zB0; e += kThreads) s_zb[e] = __ldg(B.idx0 + zB0 + e);
+  }
+  const uint16_t* zAb = stA ? s_za - zA0 : A.idx0;  // z entry i of A at zAb[i]
+  const uint16_t* zBb = stB ? s_zb - zB0 : B.idx0;
+  __syncthreads();
+  // merge path (A first on equal keys); sources: A's column i as i, B's
+  // column j as MH + j
+  const uint32_t n = na + nb;
+  const uint32_t diag = min((uint32_t)(tid * IT), n);
+  {
+    uint32_t lo = diag > nb ? diag - nb : 0u, hi = min(diag, na);
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_ka[mid] <= s_kb[diag - 1 - mid]) lo = mid + 1; else hi = mid;
+    }
+    uint32_t i = lo, j = diag - lo;
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const bool takeA = i < na && (j >= nb || s_ab[i] <= s_ab[MH + j]);
-    const bool any = i < na || j < nb;
-    unsigned long long v = 0;
-    if (any) v = takeA ? s_ab[i] : s_ab[MH + j];
-    if (any) {
+    for (int it = 0; it < IT; ++it) {
+      if (diag + it >= n) break;
+      const bool takeA = i < na && (j >= nb || s_ka[i] <= s_kb[j]);
+      s_mk[diag + it] = takeA ? s_ka[i] : s_kb[j];
+      s_ms[diag + it] = (uint16_t)(takeA ? i : MH + j);
       if (takeA) ++i; else ++j;
     }
-    r[it] = v;
   }
   __syncthreads();
+  // output columns: a merged key that differs from the one before it; a key
+  // present in both inputs appears twice in a row (A's, then B's)
+  const uint32_t prevx = s_prevx;
+  const bool hasprev = s_hasprev != 0;
+  uint32_t cnt[IT];
+  uint32_t nv = 0, nh = 0, ns = 0;
 #pragma unroll
   for (int it = 0; it < IT; ++it) {
-    const uint32_t pos = diag + it;
-    if (pos < cnt) s_ab[pos] = r[it];
+    cnt[it] = 0;
+    const uint32_t ps = diag + it;
+    if (ps >= n) continue;
+    const uint32_t key = s_mk[ps];
+    if (ps > 0 && s_mk[ps - 1] == key) continue;  // B's copy of a shared column
+    const uint32_t src = s_ms[ps];
+    const bool pair = ps + 1 < n && s_mk[ps + 1] == key;
+    uint32_t c;
+    if (pair) {
+      const uint32_t ca = a0 + src, cb = b0 + (s_ms[ps + 1] - MH);
+      const uint32_t za = __ldg(A.ptr1 + ca), zb = __ldg(B.ptr1 + cb);
+      c = union_count(zAb + za, __ldg(A.ptr1 + ca + 1) - za, zBb + zb,
+                      __ldg(B.ptr1 + cb + 1) - zb);
+    } else if (src < MH) {
+      c = __ldg(A.ptr1 + a0 + src + 1) - __ldg(A.ptr1 + a0 + src);
+    } else {
+      c = __ldg(B.ptr1 + b0 + src - MH + 1) - __ldg(B.ptr1 + b0 + src - MH);
+    }
+    cnt[it] = c;
+    const uint32_t x = key >> b;
+    const bool newslab = ps > 0 ? (s_mk[ps - 1] >> b) != x : (!hasprev || x != prevx);
+    nv += c;
+    ++nh;
+    ns += newslab ? 1u : 0u;
+  }
+  uint32_t tv = 0, thc = 0;
+  const uint32_t ov = block_excl_scan<uint32_t>(nv, tv, s_warp);
+  const uint32_t ohs = block_excl_scan<uint32_t>(nh | (ns << 16), thc, s_warp);
+  if (tid < 3) {
+    const uint32_t run = tid == 0 ? tv : (tid == 1 ? (thc & 0xffffu) : (thc >> 16));
+    uint32_t* my = clook + (size_t)t * 3 + tid;
+    uint32_t excl = 0;
+    if (lt == 0) {
+      st_relaxed(my, kFlagInc | run);
+    } else {
+      st_relaxed(my, kFlagAgg | run);
+      excl = lookback(clook + tid, 3, t, P.tile_base, &O.hdr->err);
+      st_relaxed(my, kFlagInc | ((excl + run) & kValMask));
+    }
+    s_tot[tid] = excl;
+    s_tot[3 + tid] = excl + run;
   }
   __syncthreads();
-  unsigned long long k[kItems];
+  uint32_t vo = s_tot[0] + ov, co = s_tot[1] + (ohs & 0xffffu), so = s_tot[2] + (ohs >> 16);
+  bool over = false;
 #pragma unroll
-  for (int it = 0; it < kItems; ++it) {
-    const uint32_t e = (uint32_t)(w * 32 * kItems + it * 32 + lane);
-    k[it] = (e < cnt) ? s_ab[e] : 0ull;
+  for (int it = 0; it < IT; ++it) {
+    const uint32_t ps = diag + it;
+    if (ps >= n) continue;
+    const uint32_t key = s_mk[ps];
+    if (ps > 0 && s_mk[ps - 1] == key) continue;
+    const uint32_t src = s_ms[ps];
+    const bool pair = ps + 1 < n && s_mk[ps + 1] == key;
+    const uint32_t c = cnt[it];
+    if (co >= O.cap1 || vo + c > O.cap) {
+      over = true;
+      continue;
+    }
+    O.idx1[co] = (uint16_t)(key & ymask);
+    O.ptr1[co] = vo;
+    if (pair) {
+      const uint32_t ca = a0 + src, cb = b0 + (s_ms[ps + 1] - MH);
+      const uint32_t za = __ldg(A.ptr1 + ca), zb = __ldg(B.ptr1 + cb);
+      union_write(zAb + za, __ldg(A.ptr1 + ca + 1) - za, zBb + zb,
+                  __ldg(B.ptr1 + cb + 1) - zb, O.idx0 + vo);
+    } else {
+      const bool fromA = src < MH;
+      const uint32_t col = fromA ? a0 + src : b0 + src - MH;
+      const uint16_t* zz = (fromA ? zAb : zBb) + __ldg((fromA ? A.ptr1 : B.ptr1) + col);
+      for (uint32_t q = 0; q < c; ++q) O.idx0[vo + q] = zz[q];
+    }
+    const uint32_t x = key >> b;
+    const bool newslab = ps > 0 ? (s_mk[ps - 1] >> b) != x : (!hasprev || x != prevx);
+    if (newslab) {
+      if (so < O.cap2) {
+        O.idx2[so] = (uint16_t)x;
+        O.ptr2[so] = co;
+      } else {
+        over = true;
+      }
+      ++so;
+    }
+    vo += c;
+    ++co;
   }
-  compact_tile<3, unsigned long long>(k, cnt, s_has_prev != 0, s_prev, t, P.tile_base,
-                                      lt == nt - 1, P.out, clook, sm);
+  if (over) atomicOr(&O.hdr->err, kErrInternal);
+  if (lt == nt - 1 && tid == 0) {
+    const uint32_t U = s_tot[3], G = s_tot[4], H = s_tot[5];
+    if (G <= O.cap1) O.ptr1[G] = U;
+    if (H <= O.cap2) O.ptr2[H] = G;
+    O.hdr->cnt[0] = U;
+    O.hdr->cnt[1] = G;
+    O.hdr->cnt[2] = H;
+  }
 }
 
 // ------------------------------------------------------- coarse slab index
@@ -346,7 +504,7 @@ cudaError_t run_decode(const Levels& a, uint32_t* xyz, cudaStream_t stream) {
 size_t merge_scratch_bytes(uint32_t total_spl, uint32_t total_tiles, int S) {
   (void)total_spl;
   size_t b = 0;
-  b += align_up(((size_t)total_tiles + S) * 2 * 4 + 8);
+  b += align_up(((size_t)total_tiles + S) * kBoundWords * 4 + 16);
   b += align_up((size_t)S * 4);
   b += align_up((size_t)total_tiles * 3 * 4);
   b += align_up(4);
@@ -361,7 +519,7 @@ MergeScratch merge_scratch_carve(void* base, uint32_t total_spl, uint32_t total_
   sc.half = half;
   (void)total_spl;
   sc.bounds = reinterpret_cast<uint32_t*>(p);
-  p += align_up(((size_t)total_tiles + S) * 2 * 4 + 8);
+  p += align_up(((size_t)total_tiles + S) * kBoundWords * 4 + 16);
   sc.ntiles = reinterpret_cast<uint32_t*>(p);
   p += align_up((size_t)S * 4);
   char* z0 = p;
