@@ -627,16 +627,22 @@ __device__ __forceinline__ void tree_brick(unsigned long long m, uint32_t bx, ui
 }
 
 // Bound of a child cell from its box code: the box of its occupied voxels
-// (fb-bit bounds in cells of 2^ss voxels) inside the cell at voxel origin
+// (FB-bit bounds in cells of 2^ss voxels) inside the cell at voxel origin
 // (X, Y, Z).
-template <typename D>
+template <typename D, int FB>
 __device__ __forceinline__ D child_lb(const Qry& q, uint32_t X, uint32_t Y, uint32_t Z,
-                                      uint32_t k, uint32_t fb, uint32_t fm, uint32_t ss) {
-  const uint32_t lx = k & fm, hx = (k >> fb) & fm, ly = (k >> (2 * fb)) & fm,
-                 hy = (k >> (3 * fb)) & fm, lz = (k >> (4 * fb)) & fm, hz = (k >> (5 * fb)) & fm;
+                                      uint32_t k, uint32_t ss) {
+  constexpr uint32_t fm = (1u << FB) - 1u;
+  const uint32_t lx = k & fm, hx = (k >> FB) & fm, ly = (k >> (2 * FB)) & fm,
+                 hy = (k >> (3 * FB)) & fm, lz = (k >> (4 * FB)) & fm, hz = (k >> (5 * FB)) & fm;
   return axis_lb2<D>(q.x, X + (lx << ss), (hx - lx + 1) << ss) +
          axis_lb2<D>(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
          axis_lb2<D>(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
+}
+template <typename D>
+__device__ __forceinline__ D child_lb_any(bool brick, const Qry& q, uint32_t X, uint32_t Y,
+                                          uint32_t Z, uint32_t k, uint32_t ss) {
+  return brick ? child_lb<D, 2>(q, X, Y, Z, k, 0u) : child_lb<D, 4>(q, X, Y, Z, k, ss);
 }
 
 // The warp's smallest key among the voxels of the bricks given to this lane
@@ -651,11 +657,13 @@ __device__ __forceinline__ void brick_voxels(unsigned long long m, uint32_t bx, 
     const uint32_t x = bx + (v >> 4), y = by + ((v >> 2) & 3u), z = bz + (v & 3u);
     const D dx = absdiff(x, q.x), dy = absdiff(y, q.y), dz = absdiff(z, q.z);
     const D d = dx * dx + dy * dy + dz * dz;
-    const unsigned long long k = ((unsigned long long)x << (2 * b)) |
-                                 ((unsigned long long)y << b) | z;
-    if (d < cd || (d == cd && k < ck)) {
-      cd = d;
-      ck = k;
+    if (d <= cd) {  // the key is formed only for a voxel that can win
+      const unsigned long long k = ((unsigned long long)x << (2 * b)) |
+                                   ((unsigned long long)y << b) | z;
+      if (d < cd || k < ck) {
+        cd = d;
+        ck = k;
+      }
     }
   }
 }
@@ -702,7 +710,7 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
     // box codes: bricks (children of level 2) in voxels, 2 bits per bound;
     // nodes in their grandchild units (4^(lvl-3) voxels), 4 bits per bound
     const uint32_t sh = 2 * (lvl - 1);
-    const uint32_t ss = lvl == 2 ? 0u : sh - 4, fb = lvl == 2 ? 2u : 4u, fm = (1u << fb) - 1u;
+    const uint32_t ss = lvl == 2 ? 0u : sh - 4;
     const uint32_t cap = tv.cap[lvl - 1];
     const uint32_t i0 = first + (uint32_t)__popcll(mask & ((1ull << c0) - 1ull));
     const uint32_t i1 = first + (uint32_t)__popcll(mask & ((1ull << c1) - 1ull));
@@ -730,12 +738,14 @@ __device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFr
         if (h1 && i1 < cap) k1 = __ldg(nd + i1);
       }
       if (h0) {
-        lb0 = child_lb<D>(q, ((ox << 2) + (c0 >> 4)) << sh, ((oy << 2) + ((c0 >> 2) & 3u)) << sh,
-                          ((oz << 2) + (c0 & 3u)) << sh, k0.w, fb, fm, ss);
+        lb0 = child_lb_any<D>(lvl == 2, q, ((ox << 2) + (c0 >> 4)) << sh,
+                              ((oy << 2) + ((c0 >> 2) & 3u)) << sh, ((oz << 2) + (c0 & 3u)) << sh,
+                              k0.w, ss);
       }
       if (two && h1) {
-        lb1 = child_lb<D>(q, ((ox << 2) + (c1 >> 4)) << sh, ((oy << 2) + ((c1 >> 2) & 3u)) << sh,
-                          ((oz << 2) + (c1 & 3u)) << sh, k1.w, fb, fm, ss);
+        lb1 = child_lb_any<D>(lvl == 2, q, ((ox << 2) + (c1 >> 4)) << sh,
+                              ((oy << 2) + ((c1 >> 2) & 3u)) << sh, ((oz << 2) + (c1 & 3u)) << sh,
+                              k1.w, ss);
       }
       if (CGA_NN_TREE_CACHE && lvl > 2) {
         if (h0) lbc[depth * 64 + c0] = lb0 > (D)0xfffffffeu ? 0xffffffffu : (uint32_t)lb0;
