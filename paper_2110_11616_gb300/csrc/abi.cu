@@ -333,8 +333,8 @@ int cga_merge(const cga_t* a, const cga_t* b, const cga_allocator* A, void* stre
   P.out = h->lv;
   P.spl_base = 0;
   const uint32_t half = libcga::tuning_for(bits, a->lv.cap + b->lv.cap).merge_half;
-  P.spl_a = libcga::merge_splitters(a->lv.cap1, half);
-  P.spl_b = libcga::merge_splitters(b->lv.cap1, half);
+  P.spl_a = libcga::merge_splitters(a->lv.cap, half);
+  P.spl_b = libcga::merge_splitters(b->lv.cap, half);
   P.tile_base = 0;
   P.num_tiles = P.spl_a + P.spl_b + 1;
   const uint32_t total_spl = P.spl_a + P.spl_b;
@@ -1243,8 +1243,8 @@ int plan_merges(const cga_t* const* a, const cga_t* const* b, uint32_t count,
     P.a = a[i]->lv;
     P.b = b[i]->lv;
     P.out = hs[i]->lv;
-    P.spl_a = libcga::merge_splitters(a[i]->lv.cap1, half);
-    P.spl_b = libcga::merge_splitters(b[i]->lv.cap1, half);
+    P.spl_a = libcga::merge_splitters(a[i]->lv.cap, half);
+    P.spl_b = libcga::merge_splitters(b[i]->lv.cap, half);
     P.spl_base = (uint32_t)spl;
     P.tile_base = (uint32_t)tiles;
     P.num_tiles = P.spl_a + P.spl_b + 1;
@@ -1636,6 +1636,10 @@ int cga_pipeline_create(const cga_pipeline_item* items, uint32_t count, const cg
   }
   p->merge =
       libcga::merge_scratch_carve(base + o_merge, (uint32_t)spl, (uint32_t)mtiles, (int)S, half);
+  p->merge.key_level = S > 0;
+  for (uint32_t i = 0; i < S; ++i) {
+    p->merge.key_level = p->merge.key_level && libcga::merge_key_level(pairs[i].a.bits);
+  }
   p->merge_spl = (uint32_t)spl;
   p->merge_tiles = (uint32_t)mtiles;
   std::vector<libcga::ProjPair> proj(S);

@@ -140,12 +140,12 @@ cudaError_t run_sort_pipeline(const SortSeg* h_segs, int S, uint32_t total_tiles
 // Decode a CGA to uint32 (x, y, z) triples in CGA order.
 cudaError_t run_decode(const Levels& a, uint32_t* xyz, cudaStream_t stream);
 
-// Merge: sorted union of pairs of 3-level CGAs, column by column.  Splitters
-// are taken at every half-th (x, y) column of each input (half =
-// Tuning::merge_half <= kTile / 2; `cap` below is a column capacity);
-// between consecutive splitters (in column-key order) each input contributes
-// at most half columns, so one tile of at most 2 * half columns always holds
-// the merged run.
+// Merge: sorted union of pairs of 3-level CGAs, column by column (or, on fine
+// grids, key by key).  Splitters are taken at every half-th (x, y) column
+// (or point) of each input (half = Tuning::merge_half <= kTile / 2; `cap`
+// below is a point capacity, which bounds the columns too); between
+// consecutive splitters each input contributes at most half columns (points),
+// so one tile of at most 2 * half of them always holds the merged run.
 constexpr int kMergeHalf = kTile / 2;  // largest partition
 inline uint32_t merge_splitters(uint64_t cap, uint32_t half) {
   return cap > 0 ? (uint32_t)((cap - 1) / half) : 0u;
@@ -167,7 +167,11 @@ struct MergeScratch {
   MergePair* pairs;         // [S]
   size_t zero_bytes;        // clook .. counter
   uint32_t half;            // merge-path partition the splitters were counted with
+  bool key_level;           // merge the key sequences instead of the columns
 };
+// The merge form for pairs on grids of `bits` per axis: key-level from 14 bits
+// on (a column then holds about one voxel), column-level below.
+inline bool merge_key_level(uint32_t bits) { return bits >= 14; }
 
 size_t merge_scratch_bytes(uint32_t total_spl, uint32_t total_tiles, int S);
 MergeScratch merge_scratch_carve(void* base, uint32_t total_spl, uint32_t total_tiles, int S,

@@ -409,6 +409,207 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
   }
 }
 
+// ---------------------------------------------------------- key-level merge
+// On fine grids (14 or more bits per axis) a column holds about one voxel, so
+// the column-level merge has nothing to gain; there the two sorted key
+// sequences are merged directly: splitters at every half-th point of each
+// input, each tile decodes both runs into 64-bit keys in shared memory
+// (window expansion), merges them by merge path and re-compacts them.
+__device__ __forceinline__ uint32_t n_splitters_pts(uint32_t u, uint32_t reserved, uint32_t half) {
+  const uint32_t k = u > 0 ? (u - 1) / half : 0u;
+  return min(k, reserved);
+}
+
+// Key-level merge (fine grids): output header, empty-CGA sentinels, first and
+// last tile bounds (two words per bound: the first point of A and of B).
+__global__ void k_kmerge_init(const MergePair* __restrict__ pairs, int S, uint32_t half,
+                             uint32_t* bounds, uint32_t* ntiles) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= S) return;
+  const MergePair& P = pairs[p];
+  const uint32_t uA = (uint32_t)P.a.hdr->cnt[0], uB = (uint32_t)P.b.hdr->cnt[0];
+  const uint32_t NA = n_splitters_pts(uA, P.spl_a, half), NB = n_splitters_pts(uB, P.spl_b, half);
+  const uint32_t nt = NA + NB + 1;
+  ntiles[p] = nt;
+  uint32_t* bnd = bounds + 2 * ((size_t)P.tile_base + p);
+  bnd[0] = 0;
+  bnd[1] = 0;
+  bnd[2 * nt] = uA;
+  bnd[2 * nt + 1] = uB;
+  P.out.hdr->cnt[0] = 0;
+  P.out.hdr->cnt[1] = 0;
+  P.out.hdr->cnt[2] = 0;
+  P.out.hdr->err = P.a.hdr->err | P.b.hdr->err;
+  P.out.ptr1[0] = 0;
+  P.out.ptr2[0] = 0;
+}
+
+// Key-level merge: tile cuts, one warp per splitter.  Splitter k of A is A's key s at
+// position (k + 1) * half; its cut is (rank_A(s), rank_B(s)) = ((k + 1) *
+// half, #B keys < s), and its place among all splitters (A's before B's on
+// equal keys) is k + #B splitters < s, where B splitter j (the key at
+// (j + 1) * half) is below s exactly when (j + 1) * half < rank_B(s).  B's
+// splitters mirror this with #A keys <= s.  The Sec. V-A lookup gives the
+// ranks.
+__global__ void k_kmerge_cuts(const MergePair* __restrict__ pairs, int S, uint32_t total,
+                             uint32_t half, uint32_t* bounds) {
+  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  if (i >= total) return;
+  const int p = find_pair_spl(pairs, S, i);
+  const MergePair& P = pairs[p];
+  const uint32_t local = i - P.spl_base;
+  const uint32_t uA = (uint32_t)P.a.hdr->cnt[0], uB = (uint32_t)P.b.hdr->cnt[0];
+  const uint32_t NA = n_splitters_pts(uA, P.spl_a, half), NB = n_splitters_pts(uB, P.spl_b, half);
+  const bool isA = local < P.spl_a;
+  const uint32_t k = isA ? local : local - P.spl_a;
+  if (k >= (isA ? NA : NB)) return;
+  const Levels& own = isA ? P.a : P.b;
+  const Levels& oth = isA ? P.b : P.a;
+  const unsigned long long s =
+      warp_key_at(own, (uint32_t)own.hdr->cnt[1], (uint32_t)own.hdr->cnt[2], (k + 1) * half);
+  bool found = false;
+  const uint32_t r = warp_rank_of(oth, (uint32_t)oth.hdr->cnt[2], s, &found);
+  // other-side splitters before this one: below s (A's turn), or at most s (B's)
+  const uint32_t rk = isA ? r : r + (found ? 1u : 0u);
+  const uint32_t before = rk > 0 ? min(isA ? NB : NA, (rk - 1) / half) : 0u;
+  const uint32_t pos = k + before;
+  if (lane == 0) {
+    uint32_t* bnd = bounds + 2 * ((size_t)P.tile_base + p);
+    bnd[2 * (pos + 1)] = isA ? (k + 1) * half : r;
+    bnd[2 * (pos + 1) + 1] = isA ? r : (k + 1) * half;
+  }
+}
+
+// Key-level merge of one tile: decode both runs (at most MH points each) into shared
+// memory, merge-path split per thread, sequential merge, then the shared
+// dedupe + compaction.
+template <int MH>
+__global__ void __launch_bounds__(kThreads) k_kmerge_tiles(const MergePair* __restrict__ pairs,
+                                                          int S, const uint32_t* __restrict__ bounds,
+                                                          const uint32_t* __restrict__ ntiles,
+                                                          uint32_t* clook, uint32_t* counter) {
+  constexpr int IT = 2 * MH / kThreads;  // merged keys per thread
+  static_assert(IT * kThreads == 2 * MH && 2 * MH <= kTile, "merge tile shape");
+  __shared__ unsigned long long s_ab[2 * MH];
+  __shared__ uint16_t s_col[MH], s_slab[MH];
+  __shared__ uint32_t s_warp[kWarps];
+  __shared__ CompactSmem sm;
+  __shared__ Window s_wa, s_wb;
+  __shared__ unsigned long long s_prev, s_prev2[2];
+  __shared__ uint32_t s_tile, s_has_prev;
+  __shared__ int s_p;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) {
+    const uint32_t t = atomicAdd(counter, 1u);
+    s_tile = t;
+    s_p = find_pair_tile(pairs, S, t);
+  }
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const int p = s_p;
+  const MergePair& P = pairs[p];
+  const uint32_t lt = t - P.tile_base;
+  const uint32_t nt = ntiles[p];
+  if (lt >= nt) return;
+  const uint32_t* bnd = bounds + 2 * ((size_t)P.tile_base + p + lt);
+  uint32_t a0 = bnd[0], b0 = bnd[1], a1 = bnd[2], b1 = bnd[3];
+  uint32_t na = a1 - a0, nb = b1 - b0;
+  const bool bad = a1 < a0 || b1 < b0 || na > (uint32_t)MH || nb > (uint32_t)MH;
+  if (bad) {
+    na = 0;
+    nb = 0;
+  }
+  const uint32_t gA = (uint32_t)P.a.hdr->cnt[1], hA = (uint32_t)P.a.hdr->cnt[2];
+  const uint32_t gB = (uint32_t)P.b.hdr->cnt[1], hB = (uint32_t)P.b.hdr->cnt[2];
+  // the tile's windows in both inputs and the key just before it: four
+  // independent warp-cooperative searches
+  if (w == 0) {
+    if (bad && lane == 0) atomicOr(&P.out.hdr->err, kErrInternal);
+    if (na) {
+      const Window wa = warp_window_of(P.a, gA, hA, a0, a1 - 1);
+      if (lane == 0) s_wa = wa;
+    }
+  } else if (w == 1) {
+    if (nb) {
+      const Window wb = warp_window_of(P.b, gB, hB, b0, b1 - 1);
+      if (lane == 0) s_wb = wb;
+    }
+  } else if (w == 2) {
+    const unsigned long long ka = a0 > 0 ? warp_key_at(P.a, gA, hA, a0 - 1) : 0ull;
+    if (lane == 0) s_prev2[0] = ka;
+  } else if (w == 3) {
+    const unsigned long long kb = b0 > 0 ? warp_key_at(P.b, gB, hB, b0 - 1) : 0ull;
+    if (lane == 0) s_prev2[1] = kb;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // the predecessor key of the merged run is the larger of the two
+    s_prev = max(a0 > 0 ? s_prev2[0] : 0ull, b0 > 0 ? s_prev2[1] : 0ull);
+    s_has_prev = (a0 > 0 || b0 > 0) ? 1u : 0u;
+  }
+  __syncthreads();
+  const uint32_t bA = P.a.bits;
+  // decode both runs (tile-uniform branches: the window expansion has barriers)
+  if (na) {
+    const Window wa = s_wa;
+    expand_window(P.a, wa, a0, na, s_col, s_slab, s_warp);
+    for (uint32_t e = tid; e < na; e += kThreads) {
+      const uint32_t cr = s_col[e];
+      const uint32_t x = __ldg(P.a.idx2 + wa.x0 + s_slab[cr]), y = __ldg(P.a.idx1 + wa.c0 + cr);
+      s_ab[e] = ((unsigned long long)x << (2 * bA)) | ((unsigned long long)y << bA) |
+                __ldg(P.a.idx0 + a0 + e);
+    }
+    __syncthreads();
+  }
+  if (nb) {
+    const Window wb = s_wb;
+    expand_window(P.b, wb, b0, nb, s_col, s_slab, s_warp);
+    for (uint32_t e = tid; e < nb; e += kThreads) {
+      const uint32_t cr = s_col[e];
+      const uint32_t x = __ldg(P.b.idx2 + wb.x0 + s_slab[cr]), y = __ldg(P.b.idx1 + wb.c0 + cr);
+      s_ab[MH + e] = ((unsigned long long)x << (2 * bA)) | ((unsigned long long)y << bA) |
+                     __ldg(P.b.idx0 + b0 + e);
+    }
+  }
+  __syncthreads();
+  const uint32_t cnt = na + nb;
+  const uint32_t diag = min((uint32_t)(tid * IT), cnt);
+  uint32_t lo = diag > nb ? diag - nb : 0u, hi = min(diag, na);
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (s_ab[mid] <= s_ab[MH + diag - 1 - mid]) lo = mid + 1; else hi = mid;
+  }
+  uint32_t i = lo, j = diag - lo;
+  unsigned long long r[IT];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const bool takeA = i < na && (j >= nb || s_ab[i] <= s_ab[MH + j]);
+    const bool any = i < na || j < nb;
+    unsigned long long v = 0;
+    if (any) v = takeA ? s_ab[i] : s_ab[MH + j];
+    if (any) {
+      if (takeA) ++i; else ++j;
+    }
+    r[it] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const uint32_t pos = diag + it;
+    if (pos < cnt) s_ab[pos] = r[it];
+  }
+  __syncthreads();
+  unsigned long long k[kItems];
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const uint32_t e = (uint32_t)(w * 32 * kItems + it * 32 + lane);
+    k[it] = (e < cnt) ? s_ab[e] : 0ull;
+  }
+  compact_tile<3, unsigned long long>(k, cnt, s_has_prev != 0, s_prev, t, P.tile_base,
+                                      lt == nt - 1, P.out, clook, sm);
+}
+
 // ------------------------------------------------------- coarse slab index
 __global__ void k_coarse_slab_index(Levels a, Levels c, uint32_t shift, uint32_t* xs) {
   const uint32_t hc = (uint32_t)c.hdr->cnt[2], ha = (uint32_t)a.hdr->cnt[2];
@@ -537,8 +738,26 @@ cudaError_t run_merge_device(int S, uint32_t total_spl, uint32_t total_tiles,
   cudaError_t e = cudaMemsetAsync(sc.clook, 0, sc.zero_bytes, stream);
   if (e != cudaSuccess) return e;
   if (sc.half != 512 && sc.half != 1024 && sc.half != 2048) return cudaErrorInvalidValue;
-  k_merge_init<<<(S + 127) / 128, 128, 0, stream>>>(sc.pairs, S, sc.half, sc.bounds, sc.ntiles);
   count_launch(total_spl > 0 ? 3 : 2);
+  if (sc.key_level) {
+    k_kmerge_init<<<(S + 127) / 128, 128, 0, stream>>>(sc.pairs, S, sc.half, sc.bounds, sc.ntiles);
+    if (total_spl > 0) {
+      k_kmerge_cuts<<<(total_spl + 7) / 8, 256, 0, stream>>>(sc.pairs, S, total_spl, sc.half,
+                                                            sc.bounds);
+    }
+    if (sc.half == 512) {
+      k_kmerge_tiles<512><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles,
+                                                                sc.clook, sc.counter);
+    } else if (sc.half == 1024) {
+      k_kmerge_tiles<1024><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds,
+                                                                 sc.ntiles, sc.clook, sc.counter);
+    } else {
+      k_kmerge_tiles<2048><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds,
+                                                                 sc.ntiles, sc.clook, sc.counter);
+    }
+    return cudaGetLastError();
+  }
+  k_merge_init<<<(S + 127) / 128, 128, 0, stream>>>(sc.pairs, S, sc.half, sc.bounds, sc.ntiles);
   if (total_spl > 0) {
     k_merge_cuts<<<(total_spl + 7) / 8, 256, 0, stream>>>(sc.pairs, S, total_spl, sc.half,
                                                          sc.bounds);
@@ -561,7 +780,10 @@ cudaError_t run_merge(const MergePair* h_pairs, int S, uint32_t total_spl, uint3
   cudaError_t e = cudaMemcpyAsync(sc.pairs, h_pairs, sizeof(MergePair) * S,
                                   cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return e;
-  return run_merge_device(S, total_spl, total_tiles, sc, stream);
+  MergeScratch s2 = sc;
+  s2.key_level = S > 0;
+  for (int i = 0; i < S; ++i) s2.key_level = s2.key_level && merge_key_level(h_pairs[i].a.bits);
+  return run_merge_device(S, total_spl, total_tiles, s2, stream);
 }
 
 cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stream) {
