@@ -182,11 +182,22 @@ constexpr size_t onesweep_smem() {
          (size_t)(TH / 32) * 4;
 }
 
+// Blocks per SM a pass kernel is compiled for (its register budget), per
+// threads per tile; measured on GB300 (30M-key builds): more resident warps
+// hide more of the key loads and look-back waits than the few spilled values
+// cost.
+#ifndef CGA_SORT_BLOCKS_512
+#define CGA_SORT_BLOCKS_512 4
+#endif
+#ifndef CGA_SORT_BLOCKS_256
+#define CGA_SORT_BLOCKS_256 5
+#endif
+
 // One LSD pass over digit `pass` (RB bits) of every segment that still needs
 // it.  A tile of kTile keys is TH threads x kTile/TH keys (warp-striped);
 // threads tid < 2^RB own one digit each for the per-digit steps.
 template <typename K, int TH, int RB>
-__global__ void __launch_bounds__(TH, 2) k_onesweep(const SortSeg* __restrict__ segs, int S,
+__global__ void __launch_bounds__(TH, TH == 512 ? CGA_SORT_BLOCKS_512 : CGA_SORT_BLOCKS_256) k_onesweep(const SortSeg* __restrict__ segs, int S,
                                                  int pass, const K* __restrict__ in,
                                                  K* __restrict__ out,
                                                  const uint32_t* __restrict__ hist,

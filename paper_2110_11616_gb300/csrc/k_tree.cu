@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(kThreads) k_tree_level(
     uint32_t* look, uint32_t* counter, unsigned int* err) {
   __shared__ uint32_t s_warp[kWarps];
   __shared__ uint32_t s_tile, s_excl;
+  __shared__ unsigned long long s_k[kTile];
   const uint32_t tid = threadIdx.x;
   if (tid == 0) s_tile = atomicAdd(counter, 1u);
   __syncthreads();
@@ -57,16 +58,21 @@ __global__ void __launch_bounds__(kThreads) k_tree_level(
   const uint32_t start = t * (uint32_t)kTile;
   if (start >= n) return;
   const uint32_t cnt = min((uint32_t)kTile, n - start);
+  // the tile's prefixes staged by coalesced loads; each thread then takes 16
+  // consecutive ones
+  for (uint32_t e = tid; e < cnt; e += kThreads) s_k[e] = __ldg(P + start + e);
+  __syncthreads();
   const uint32_t e0 = tid * kItems;
   unsigned long long k[kItems];
   uint32_t heads = 0;
-  unsigned long long prev = (e0 < cnt && start + e0 > 0) ? __ldg(P + start + e0 - 1) : 0ull;
+  unsigned long long prev =
+      e0 < cnt ? (e0 > 0 ? s_k[e0 - 1] : (start > 0 ? __ldg(P + start - 1) : 0ull)) : 0ull;
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     const uint32_t e = e0 + i;
     k[i] = 0;
     if (e < cnt) {
-      k[i] = __ldg(P + start + e);
+      k[i] = s_k[e];
       if (start + e == 0 || (k[i] >> 6) != (prev >> 6)) heads |= 1u << i;
       prev = k[i];
     }
@@ -94,7 +100,7 @@ __global__ void __launch_bounds__(kThreads) k_tree_level(
     uint32_t lo[3] = {15u, 15u, 15u}, hi[3] = {0u, 0u, 0u};
     // a node has at most 64 children, so its run ends within 64 entries
     for (uint32_t f = e; f < n && f < e + 64; ++f) {
-      const unsigned long long v = f == e ? k[i] : __ldg(P + f);
+      const unsigned long long v = f == e ? k[i] : (f - start < cnt ? s_k[f - start] : __ldg(P + f));
       if ((v >> 6) != pr) break;
       const uint32_t c = (uint32_t)(v & 63);
       mask |= 1ull << c;
