@@ -200,17 +200,14 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
                                                           uint32_t* clook, uint32_t* counter) {
   constexpr int IT = 2 * MH / kThreads;  // merged columns per thread
   static_assert(IT * kThreads == 2 * MH && MH % kThreads == 0, "merge tile shape");
-  // column keys of A and B; merged keys and sources (the slab expansion of
-  // the columns uses the merged arrays' space before the merge)
+  // column keys of A and B; merged keys and sources; staged z entries
   constexpr int ZS = merge_stage<MH>();
   __shared__ uint32_t s_ka[MH], s_kb[MH], s_mk[2 * MH];
   __shared__ uint16_t s_ms[2 * MH];
   __shared__ uint16_t s_za[ZS], s_zb[ZS];
-  __shared__ uint32_t s_warp[kWarps];
+  __shared__ unsigned long long s_warp64[kWarps];
   __shared__ uint32_t s_tile, s_tot[6], s_prevx, s_hasprev;
   __shared__ int s_p;
-  uint16_t* s_sa = reinterpret_cast<uint16_t*>(s_mk);
-  uint16_t* s_sb = s_sa + MH;
   const int tid = threadIdx.x;
   if (tid == 0) {
     const uint32_t t = atomicAdd(counter, 1u);
@@ -239,8 +236,6 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
   // column, one less when that column opens its slab
   const uint32_t saL = na ? (__ldg(A.ptr2 + sa1) == a1 ? sa1 - 1 : sa1) : sa0;
   const uint32_t sbL = nb ? (__ldg(B.ptr2 + sb1) == b1 ? sb1 - 1 : sb1) : sb0;
-  for (uint32_t e = tid; e < na; e += kThreads) s_sa[e] = 0;
-  for (uint32_t e = tid; e < nb; e += kThreads) s_sb[e] = 0;
   if (tid == 0) {
     if (bad) atomicOr(&O.hdr->err, kErrInternal);
     // x of the column just before the tile (the larger of A's and B's)
@@ -258,17 +253,15 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
     s_prevx = px;
     s_hasprev = hp ? 1u : 0u;
   }
-  __syncthreads();
-  for (uint32_t s = sa0 + 1 + tid; s <= saL; s += kThreads) s_sa[__ldg(A.ptr2 + s) - a0] = (uint16_t)(s - sa0);
-  for (uint32_t s = sb0 + 1 + tid; s <= sbL; s += kThreads) s_sb[__ldg(B.ptr2 + s) - b0] = (uint16_t)(s - sb0);
-  __syncthreads();
-  block_max_scan_u16<MH / kThreads>(s_sa, na, s_warp);
-  block_max_scan_u16<MH / kThreads>(s_sb, nb, s_warp);
+  // column keys: each column's slab by a search of the tile's few slabs
+  // (their X_pointer entries stay in L1)
   for (uint32_t e = tid; e < na; e += kThreads) {
-    s_ka[e] = ((uint32_t)__ldg(A.idx2 + sa0 + s_sa[e]) << b) | __ldg(A.idx1 + a0 + e);
+    const uint32_t sl = search_le(A.ptr2, sa0, saL, a0 + e);
+    s_ka[e] = ((uint32_t)__ldg(A.idx2 + sl) << b) | __ldg(A.idx1 + a0 + e);
   }
   for (uint32_t e = tid; e < nb; e += kThreads) {
-    s_kb[e] = ((uint32_t)__ldg(B.idx2 + sb0 + s_sb[e]) << b) | __ldg(B.idx1 + b0 + e);
+    const uint32_t sl = search_le(B.ptr2, sb0, sbL, b0 + e);
+    s_kb[e] = ((uint32_t)__ldg(B.idx2 + sl) << b) | __ldg(B.idx1 + b0 + e);
   }
   // the tile's z entries of each input are one contiguous range: staged in
   // shared memory by coalesced loads when they fit
@@ -338,9 +331,14 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
     ++nh;
     ns += newslab ? 1u : 0u;
   }
-  uint32_t tv = 0, thc = 0;
-  const uint32_t ov = block_excl_scan<uint32_t>(nv, tv, s_warp);
-  const uint32_t ohs = block_excl_scan<uint32_t>(nh | (ns << 16), thc, s_warp);
+  // one block scan of (voxels | columns << 32 | slabs << 48): a tile holds at
+  // most 2 * MH <= 4096 columns and slabs and fewer than 2^32 voxels
+  unsigned long long tp = 0;
+  const unsigned long long op = block_excl_scan<unsigned long long>(
+      (unsigned long long)nv | ((unsigned long long)nh << 32) | ((unsigned long long)ns << 48),
+      tp, s_warp64);
+  const uint32_t ov = (uint32_t)op, ohs = (uint32_t)(op >> 32);
+  const uint32_t tv = (uint32_t)tp, thc = (uint32_t)(tp >> 32);
   if (tid < 3) {
     const uint32_t run = tid == 0 ? tv : (tid == 1 ? (thc & 0xffffu) : (thc >> 16));
     uint32_t* my = clook + (size_t)t * 3 + tid;
