@@ -59,7 +59,7 @@ S_POINTS, S_QUERIES, S_BITS, S_EXTENT = 30_000_000, 8_000_000, 12, 100.0
 S_SAMPLE_PTS, S_SAMPLE_SURF, S_SAMPLE_UNIF = 1_000_000, 64, 32
 # ncu summary of the dominant kernel of the default workload (per-launch DRAM
 # bytes, and the hash of the sources the counters were taken on)
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_nn_warp_tree_surface_8M.txt")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_nn_tree_surface_8M.txt")
 NN_SOURCES = ("k_nn.cu", "k_tree.cu", "k_common.cuh", "cga_impl.h")
 N_SWEEPS, BEAMS, STEPS_AZ, N_QUERIES = 10, 64, 2048, 1_000_000
 LO, EXTENT, BITS = (-128.0, -128.0, -128.0), 256.0, 16
@@ -409,9 +409,10 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
     value = job_value(pts, args.steps, world_size, max_total)
     e2e_val = pts * world_size / (float(np.mean(e2e_ms)) / 1e3) / 1e6
     peak, peak_kind = measured_peaks()
-    # dominant kernel: the NN search (one launch of k_nn_warp per step, timed
-    # live above between events 4 and 5).  Algorithmic bytes per launch
-    # (compulsory): 12 B query read, 4 B index + 8 B distance written.
+    # dominant kernel: the NN search (one launch per step of k_nn_warp, or of
+    # k_nn_tree when the autotuner picked the tree, timed live above between
+    # events 4 and 5).  Algorithmic bytes per launch (compulsory): 12 B query
+    # read, 4 B index + 8 B distance written.
     search_ms = op[4]
     algo = N_QUERIES * (12 + 4 + 8)
     achieved = algo / (search_ms / 1e3) / 1e9
@@ -433,7 +434,9 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
             "world_u": winfo["u"], "world_g": winfo["g"], "world_h": winfo["h"],
             "world_bytes": winfo["bytes"], "raw_bytes": pts * 12,
         },
-        "roofline": {"kernel": "k_nn_warp (NN search)", "bound": "hbm",
+        "roofline": {"kernel": ("k_nn_tree (NN search over the occupancy tree)"
+                                if tuple(P.nn_shift) == (0xFFFFFFFF,) else
+                                "k_nn_warp (NN window search)"), "bound": "hbm",
                      "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 6), "traffic": None,
                      "peak_source": f"{peak_kind} hbm_gbs",
@@ -586,9 +589,9 @@ def run_surface(args, world_size, local_rank, torch, dist, cga):
     value = job_value(S_POINTS, args.steps, world_size, max_total)
     e2e_val = S_POINTS * world_size / (float(np.mean(e2e_ms)) / 1e3) / 1e6
     peak, peak_kind = measured_peaks()
-    # dominant kernel: the NN search (one launch of k_nn_warp per step, timed
-    # live between events 4 and 5).  Algorithmic bytes per launch (compulsory):
-    # 12 B query read + 4 B index + 8 B distance written per query.
+    # dominant kernel: the NN search (one launch of k_nn_tree per step under the
+    # tree, timed live between events 4 and 5).  Algorithmic bytes per launch
+    # (compulsory): 12 B query read + 4 B index + 8 B distance written per query.
     search_ms = op[4]
     algo = S_QUERIES * (12 + 4 + 8)
     achieved = algo / (search_ms / 1e3) / 1e9
@@ -616,7 +619,9 @@ def run_surface(args, world_size, local_rank, torch, dist, cga):
             "merged_u": mi["u"], "merged_g": mi["g"], "merged_h": mi["h"],
             "merged_bytes": mi["bytes"], "raw_bytes": S_POINTS * 12,
         },
-        "roofline": {"kernel": "k_nn_warp<3> (NN search over the occupancy tree)",
+        "roofline": {"kernel": ("k_nn_tree (NN search over the occupancy tree)"
+                                if tuple(P.nn_strategy) == (0xFFFFFFFF,) else
+                                "k_nn_warp (NN window search)"),
                      "bound": "hbm", "achieved": round(achieved, 3), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 6), "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs (burst copy)",

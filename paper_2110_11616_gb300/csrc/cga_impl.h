@@ -300,56 +300,81 @@ constexpr int kMaxCoarse = 2;
 // tree_levels(bits), with node 0 of that level the only one.
 constexpr int kTreeMaxLevels = 8;  // ceil(16 / 2)
 inline uint32_t tree_levels(uint32_t bits) { return (bits + 1) / 2; }
+// Number of the child cell (cx, cy, cz) in [0, 4)^3 of a tree cell:
+// p = s << 4 | t << 2 | cx with s = (cx + cy) mod 4 and t = (cy + cz) mod 4.
+// Any plane of cells with one coordinate fixed holds one cell of each
+// (s, t), so a search that gives each lane the children of a fixed range of
+// numbers (4, 8 or 16 consecutive ones) sees the 16 children of such a plane
+// split evenly over its lanes.  Voxels inside a brick are numbered the same
+// way.
+__host__ __device__ inline uint32_t tree_child(uint32_t cx, uint32_t cy, uint32_t cz) {
+  return ((cx + cy) & 3u) << 4 | ((cy + cz) & 3u) << 2 | cx;
+}
+// The cell of child number p (the inverse of tree_child).
+__host__ __device__ inline void tree_cell(uint32_t p, uint32_t& cx, uint32_t& cy, uint32_t& cz) {
+  cx = p & 3u;
+  cy = ((p >> 4) - cx) & 3u;
+  cz = (((p >> 2) & 3u) - cy) & 3u;
+}
 // Key of voxel (x, y, z) in the tree's order: bits [6(l-1), 6l) hold the
-// child index (c = cx << 4 | cy << 2 | cz) of the voxel's level-(l-1) cell
-// inside its level-l cell, for l = 1..levels.  Ascending keys list the
-// voxels brick by brick in a depth-first walk of the tree.
+// child number (tree_child) of the voxel's level-(l-1) cell inside its
+// level-l cell, for l = 1..levels.  Ascending keys list the voxels brick by
+// brick in a depth-first walk of the tree.
 __host__ __device__ inline unsigned long long tree_key(uint32_t x, uint32_t y, uint32_t z,
                                                        uint32_t levels) {
   unsigned long long k = 0;
   for (uint32_t l = 0; l < levels; ++l) {
-    const uint32_t c = ((x >> (2 * l)) & 3u) << 4 | ((y >> (2 * l)) & 3u) << 2 | ((z >> (2 * l)) & 3u);
+    const uint32_t c = tree_child((x >> (2 * l)) & 3u, (y >> (2 * l)) & 3u, (z >> (2 * l)) & 3u);
     k |= (unsigned long long)c << (6 * l);
   }
   return k;
 }
-// Bounding box of a node's occupied children, in child units (0..3 per axis):
-// lo_x | hi_x << 2 | lo_y << 4 | hi_y << 6 | lo_z << 8 | hi_z << 10, from its
-// child set m (m != 0; bit c = cx << 4 | cy << 2 | cz).
+// Box of a brick's occupied voxels from its voxel set m (m != 0; bit p =
+// tree_child of the voxel inside the brick), in voxels (0..3 per axis):
+// lo_x | hi_x << 4 | lo_y << 8 | hi_y << 12 | lo_z << 16 | hi_z << 20 (the
+// field layout of a node's box).
 __host__ __device__ inline uint32_t tree_box_code(unsigned long long m) {
-  const uint32_t xo = ((m & 0xFFFFull) ? 1u : 0u) | (((m >> 16) & 0xFFFFull) ? 2u : 0u) |
-                      (((m >> 32) & 0xFFFFull) ? 4u : 0u) | ((m >> 48) ? 8u : 0u);
-  const uint32_t t = (uint32_t)((m | (m >> 16) | (m >> 32) | (m >> 48)) & 0xFFFFull);
-  const uint32_t yo = ((t & 0xFu) ? 1u : 0u) | ((t & 0xF0u) ? 2u : 0u) | ((t & 0xF00u) ? 4u : 0u) |
-                      ((t & 0xF000u) ? 8u : 0u);
-  const uint32_t zo = (t | (t >> 4) | (t >> 8) | (t >> 12)) & 0xFu;
-  uint32_t code = 0;
-  const uint32_t occ[3] = {xo, yo, zo};
-  for (int a = 0; a < 3; ++a) {
-    uint32_t lo = 0, hi = 3;
-    while (!((occ[a] >> lo) & 1u)) ++lo;
-    while (!((occ[a] >> hi) & 1u)) --hi;
-    code |= (lo | hi << 2) << (4 * a);
+  uint32_t lo[3] = {3u, 3u, 3u}, hi[3] = {0u, 0u, 0u};
+  for (; m != 0ull; m &= m - 1ull) {
+#ifdef __CUDA_ARCH__
+    const uint32_t p = (uint32_t)__ffsll((long long)m) - 1u;
+#else
+    const uint32_t p = (uint32_t)__builtin_ctzll(m);
+#endif
+    uint32_t c[3];
+    tree_cell(p, c[0], c[1], c[2]);
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = c[a] < lo[a] ? c[a] : lo[a];
+      hi[a] = c[a] > hi[a] ? c[a] : hi[a];
+    }
   }
-  return code;
+  return lo[0] | hi[0] << 4 | lo[1] << 8 | hi[1] << 12 | lo[2] << 16 | hi[2] << 20;
 }
 // A node of level l >= 2 keeps the box of its occupied voxels at the
 // granularity of its grandchildren (cells of 4^(l-2) voxels; 16 per axis of
 // the node): lo_x | hi_x << 4 | lo_y << 8 | hi_y << 12 | lo_z << 16 | hi_z << 20.
+// Every entry of a level l below the root also keeps its box in its parent's
+// frame (pcode): 6-bit bounds counted from the parent's origin in cells of
+// 4^(l-2) voxels (l >= 2) or in voxels (bricks), Lx | Hx << 6 | Ly << 12 |
+// Hy << 18 in .x and Lz | Hz << 6 in .y; the box along x covers
+// [Lx * u, (Hx + 1) * u) voxels from the parent's origin for that unit u.
 struct TreeView {
   const unsigned long long* brick;        // level 1: voxel occupancy of each brick
-  const uint16_t* bcode;                  // level 1: tree_box_code of each brick (voxel units)
+  const uint32_t* bcode;                  // level 1: tree_box_code of each brick (voxel units)
   const uint4* node[kTreeMaxLevels + 1];  // level l >= 2: {child set lo, hi, first child,
                                           //  box of the voxels in grandchild units}
+  const uint2* pcode[kTreeMaxLevels + 1]; // level l < levels: box in the parent's frame
   uint32_t cap[kTreeMaxLevels + 1];       // entries reserved per level (a search never reads beyond)
   uint32_t levels;                        // 0: no tree
 };
 // Capacity of every level (cap[0]: voxels) and the bytes of the tree arrays
 // (offsets from one base: off[1] bricks, off_bcode their box codes, off[l]
-// nodes of level l, off[0] the device counts, one 32-bit word per level).
+// nodes of level l, off_pcode[l] the boxes of level l in their parents'
+// frames, off[0] the device counts, one 32-bit word per level).
 struct TreeLayout {
   uint64_t cap[kTreeMaxLevels + 1];
   size_t off[kTreeMaxLevels + 1];
+  size_t off_pcode[kTreeMaxLevels + 1];
   size_t off_bcode;
   size_t bytes;
   uint32_t levels;
@@ -429,10 +454,11 @@ cudaError_t run_nn_search(const NnSeg& seg, const unsigned long long* order, cud
 // levels, 3 the occupancy tree.
 inline uint32_t nn_kind(const NnSeg& s) { return s.tree.levels > 0 ? 3u : s.ncoarse; }
 // Run with the tables on the device (capturable: memsets and kernels only).
-// max_kind: the largest nn_kind of any segment (selects the kernel
-// instantiation; kind 3 searches segments without a tree by the fine search).
+// kinds: bit k set when some segment has nn_kind k (selects the kernels: the
+// tree search for segments with a tree, the window search of the largest
+// other kind for the rest).
 cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream,
-                          uint32_t max_kind = 0);
+                          uint32_t kinds = 1u);
 
 // For each slab k of the coarse CGA c (cells of 2^shift voxels), xs[k] = first
 // index of a's X_index whose x >> shift equals c's X_index[k]; xs[h_c] = h_a.

@@ -248,9 +248,9 @@ __device__ __forceinline__ uint32_t interval_dist(int q, uint32_t lo, uint32_t s
 // (cx, cy, cz) inside the grid for searches.
 constexpr int kQueryLimit = 1 << 30;
 
-// Blocks per SM the fine-only and the coarse searches are compiled for (their
-// register budgets; measured on GB300: fine 6 beats 5 and 8, coarse 5 beats
-// 4 and 6).
+// Blocks per SM the fine-only, the coarse and the tree searches are compiled
+// for (their register budgets; measured on GB300: fine 6 beats 5 and 8,
+// coarse 5 beats 4 and 6), and the lanes per query of the tree search.
 #ifndef CGA_NN_FINE_BLOCKS
 #define CGA_NN_FINE_BLOCKS 6
 #endif
@@ -260,10 +260,34 @@ constexpr int kQueryLimit = 1 << 30;
 #ifndef CGA_NN_TREE_BLOCKS
 #define CGA_NN_TREE_BLOCKS 4
 #endif
-// 1: a frame's child bounds are kept in shared memory for the way back
-#ifndef CGA_NN_TREE_CACHE
-#define CGA_NN_TREE_CACHE 1
+#ifndef CGA_NN_TREE_DEFER
+#define CGA_NN_TREE_DEFER 0
 #endif
+#ifndef CGA_NN_TREE_GROUP
+#define CGA_NN_TREE_GROUP 4
+#endif
+
+// Voxel of query j of a segment, clamped to +-2^30 (so every coordinate
+// difference fits 31 bits); false for a non-finite query point.
+__device__ __forceinline__ bool query_voxel(const NnSeg& sg, uint32_t j, int& qx, int& qy,
+                                            int& qz) {
+  if (sg.qv != nullptr) {
+    const int* v = sg.qv + 3 * (size_t)j;
+    qx = min(max(__ldg(v), -kQueryLimit), kQueryLimit);
+    qy = min(max(__ldg(v + 1), -kQueryLimit), kQueryLimit);
+    qz = min(max(__ldg(v + 2), -kQueryLimit), kQueryLimit);
+    return true;
+  }
+  // queries stream through once: loaded evict-first, so that L2 keeps the
+  // CGA and the search structures
+  const float* p = sg.q + 3 * (size_t)j;
+  const float px = __ldcs(p), py = __ldcs(p + 1), pz = __ldcs(p + 2);
+  const bool valid = isfinite(px) && isfinite(py) && isfinite(pz);
+  qx = valid ? (int)quantize_query(px, sg.scale, sg.off[0]) : 0;
+  qy = valid ? (int)quantize_query(py, sg.scale, sg.off[1]) : 0;
+  qz = valid ? (int)quantize_query(pz, sg.scale, sg.off[2]) : 0;
+  return valid;
+}
 
 struct Qry {
   int x, y, z;
@@ -332,7 +356,7 @@ __device__ void refine_level(const NnSeg& sg, uint32_t x0, uint32_t x1, uint32_t
     const unsigned long long dxl = gr ? er : el;
     const unsigned long long dxl2 = dxl * dxl;
     if (dxl2 > best.d2) break;
-    const uint32_t xi = (uint32_t)(gr ? r : l), xv = gr ? vr : vl;
+    const uint32_t xi = (uint32_t)(gr ? r : l);
     if (gr) ++r; else --l;
     const uint32_t ys = __ldg(L.ptr2 + xi), ye = __ldg(L.ptr2 + xi + 1);
     // columns [c0, c1) of this slab lie in the y range; cs: the first at or
@@ -540,113 +564,74 @@ __device__ void search_levels(const NnSeg& sg, const Qry& q, uint32_t lane, Best
 // ---- occupancy-tree search (cga_nn_prepare_levels with CGA_NN_TREE) -------
 //
 // A depth-first descent of the 64-ary occupancy tree (k_tree.cu), nearest
-// child first.  The warp keeps one frame per level on the path: the node's
-// child set, the children still to visit and the node's cell.  Each step the
-// lanes bound two children each (box distance of the child cell; lane i takes
-// children i and i + 32), drop every child whose bound exceeds the best
-// distance so far, and the warp enters the remaining child with the least
-// bound.  Children of a level-2 node are bricks: their 64 voxels are examined
-// at once (two per lane).  A child is dropped only when its bound exceeds the
-// best distance, and the best distance never falls below the final one, so
-// every cell holding a voxel at the final distance is entered: the result is
-// Eq. 8's nearest voxel, ties to the smaller key.
+// child first, by a group of G lanes per query (32 / G queries per warp).
+// Lane g of a group owns the children numbered [g * 64/G, (g + 1) * 64/G)
+// of every node (tree_child numbers, so the children of a planar patch of
+// surface spread evenly over the lanes).  Each step the lanes bound their
+// children still to visit (box distance of the child's occupied voxels),
+// drop every child whose bound exceeds the best distance so far, and the
+// group enters the surviving child with the least bound.  Children of a
+// level-2 node are bricks: until a first candidate exists the nearest brick
+// is examined alone (its voxels give a bound that prunes its siblings), after
+// that every surviving brick at once, and the node is done.  A child is
+// dropped only when its bound exceeds the best distance, and the best
+// distance never falls below the final one, so every cell holding a voxel at
+// the final distance is entered: the result is Eq. 8's nearest voxel, ties to
+// the smaller key.
 
-// Squared distance from q to the cell [lo, lo + s - 1] along one axis, in D
-// (uint32_t when every squared distance of the search fits 32 bits: a grid of
-// at most 15 bits per axis and a query inside it; else 64 bits).
-template <typename D>
-__device__ __forceinline__ D axis_lb2(int q, uint32_t lo, uint32_t s) {
-  const D d = interval_dist(q, lo, s);
-  return d * d;
+// Minimum of a D value over the lanes in gm (64-bit: high word first).
+__device__ __forceinline__ uint32_t group_min(uint32_t gm, uint32_t v) {
+  return __reduce_min_sync(gm, v);
 }
-
-struct TreeFrame {
-  unsigned long long mask, rem;
-  uint32_t first, ox, oy, oz, lvl, pad;
-};
-
-// Warp minimum of a D value (32-bit words, high first).
-__device__ __forceinline__ uint32_t warp_min_d(uint32_t v) {
-  return __reduce_min_sync(0xffffffffu, v);
-}
-__device__ __forceinline__ unsigned long long warp_min_d(unsigned long long v) {
-  const uint32_t full = 0xffffffffu;
+__device__ __forceinline__ unsigned long long group_min(uint32_t gm, unsigned long long v) {
   const uint32_t vh = (uint32_t)(v >> 32), vl = (uint32_t)v;
-  const uint32_t mh = __reduce_min_sync(full, vh);
-  const uint32_t ml = __reduce_min_sync(full, vh == mh ? vl : full);
+  const uint32_t mh = __reduce_min_sync(gm, vh);
+  const uint32_t ml = __reduce_min_sync(gm, vh == mh ? vl : 0xffffffffu);
   return ((unsigned long long)mh << 32) | ml;
 }
 
-// The best (distance^2, key) of the tree search.
+// The best (distance^2, key) of the tree search, the same in every lane of
+// the group.
 template <typename D>
 struct BestKey {
   D d2;
   unsigned long long key;
-  // Lexicographic minimum of the lanes' (d, k).
-  __device__ __forceinline__ void warp_min_of(D d, unsigned long long k) {
-    const uint32_t full = 0xffffffffu;
-    const D md = warp_min_d(d);
+  // Merge the lanes' candidates (d, k): lexicographic minimum over the group
+  // with the current best.
+  __device__ __forceinline__ void merge(uint32_t gm, D d, unsigned long long k) {
+    const bool better = d < d2 || (d == d2 && k < key);
+    if (!__any_sync(gm, better)) return;
+    if (!better) {
+      d = d2;
+      k = key;
+    }
+    const D md = group_min(gm, d);
     const bool at = d == md;
-    const uint32_t kh = __reduce_min_sync(full, at ? (uint32_t)(k >> 32) : full);
-    const uint32_t kl = __reduce_min_sync(full, at && (uint32_t)(k >> 32) == kh ? (uint32_t)k : full);
+    const uint32_t kh = __reduce_min_sync(gm, at ? (uint32_t)(k >> 32) : 0xffffffffu);
+    const uint32_t kl =
+        __reduce_min_sync(gm, at && (uint32_t)(k >> 32) == kh ? (uint32_t)k : 0xffffffffu);
     d2 = md;
     key = ((unsigned long long)kh << 32) | kl;
   }
 };
 
-// The voxels of the brick at brick coordinates (bx, by, bz) with occupancy
-// m: lane i takes voxels i and i + 32 (bit c = cx << 4 | cy << 2 | cz).
+// Bound of a child from its box in the parent's frame (TreeView::pcode):
+// (tx, ty, tz) is the query's offset from the parent's origin, ub = 1 - 2^ss
+// and 2^ss voxels the box unit.  Along an axis the distance to [L u, (H + 1) u - 1]
+// is max(L u - t, t + ub - H u, 0).
 template <typename D>
-__device__ __forceinline__ void tree_brick(unsigned long long m, uint32_t bx, uint32_t by,
-                                           uint32_t bz, const Qry& q, uint32_t b, uint32_t lane,
-                                           BestKey<D>& best) {
-  const uint32_t y = (by << 2) + ((lane >> 2) & 3u), z = (bz << 2) + (lane & 3u);
-  const uint32_t x0 = (bx << 2) + (lane >> 4);
-  const D dy = absdiff(y, q.y), dz = absdiff(z, q.z);
-  const D dyz = dy * dy + dz * dz;
-  const unsigned long long yz = ((unsigned long long)y << b) | z;
-  D cd = (D)~(D)0;
-  unsigned long long ck = ~0ull;
-  if ((m >> lane) & 1ull) {
-    const D dx = absdiff(x0, q.x);
-    cd = dx * dx + dyz;
-    ck = ((unsigned long long)x0 << (2 * b)) | yz;
-  }
-  if ((m >> (lane + 32)) & 1ull) {
-    const D dx = absdiff(x0 + 2, q.x);
-    const D d = dx * dx + dyz;
-    if (d < cd) {  // on a tie the smaller x (smaller key) stays
-      cd = d;
-      ck = ((unsigned long long)(x0 + 2) << (2 * b)) | yz;
-    }
-  }
-  const bool better = cd < best.d2 || (cd == best.d2 && ck < best.key);
-  if (__any_sync(0xffffffffu, better)) {
-    best.warp_min_of(better ? cd : best.d2, better ? ck : best.key);
-  }
+__device__ __forceinline__ D parent_frame_lb(uint2 c, int tx, int ty, int tz, int ub, uint32_t ss) {
+  const int lx = (int)((c.x & 63u) << ss), hx = (int)(((c.x >> 6) & 63u) << ss);
+  const int ly = (int)(((c.x >> 12) & 63u) << ss), hy = (int)(((c.x >> 18) & 63u) << ss);
+  const int lz = (int)((c.y & 63u) << ss), hz = (int)(((c.y >> 6) & 63u) << ss);
+  const D dx = (uint32_t)max(max(lx - tx, tx + ub - hx), 0);
+  const D dy = (uint32_t)max(max(ly - ty, ty + ub - hy), 0);
+  const D dz = (uint32_t)max(max(lz - tz, tz + ub - hz), 0);
+  return dx * dx + dy * dy + dz * dz;
 }
 
-// Bound of a child cell from its box code: the box of its occupied voxels
-// (FB-bit bounds in cells of 2^ss voxels) inside the cell at voxel origin
-// (X, Y, Z).
-template <typename D, int FB>
-__device__ __forceinline__ D child_lb(const Qry& q, uint32_t X, uint32_t Y, uint32_t Z,
-                                      uint32_t k, uint32_t ss) {
-  constexpr uint32_t fm = (1u << FB) - 1u;
-  const uint32_t lx = k & fm, hx = (k >> FB) & fm, ly = (k >> (2 * FB)) & fm,
-                 hy = (k >> (3 * FB)) & fm, lz = (k >> (4 * FB)) & fm, hz = (k >> (5 * FB)) & fm;
-  return axis_lb2<D>(q.x, X + (lx << ss), (hx - lx + 1) << ss) +
-         axis_lb2<D>(q.y, Y + (ly << ss), (hy - ly + 1) << ss) +
-         axis_lb2<D>(q.z, Z + (lz << ss), (hz - lz + 1) << ss);
-}
-template <typename D>
-__device__ __forceinline__ D child_lb_any(bool brick, const Qry& q, uint32_t X, uint32_t Y,
-                                          uint32_t Z, uint32_t k, uint32_t ss) {
-  return brick ? child_lb<D, 2>(q, X, Y, Z, k, 0u) : child_lb<D, 4>(q, X, Y, Z, k, ss);
-}
-
-// The warp's smallest key among the voxels of the bricks given to this lane
-// (occupancy m, voxel origin (bx, by, bz)) that beat `best`, merged into it.
+// The smallest (distance^2, key) among the voxels of set m (tree_child
+// numbers) of the brick at voxel origin (bx, by, bz), merged into (cd, ck).
 template <typename D>
 __device__ __forceinline__ void brick_voxels(unsigned long long m, uint32_t bx, uint32_t by,
                                              uint32_t bz, const Qry& q, uint32_t b, D& cd,
@@ -654,7 +639,9 @@ __device__ __forceinline__ void brick_voxels(unsigned long long m, uint32_t bx, 
   while (m != 0ull) {
     const uint32_t v = (uint32_t)__ffsll((long long)m) - 1u;
     m &= m - 1ull;
-    const uint32_t x = bx + (v >> 4), y = by + ((v >> 2) & 3u), z = bz + (v & 3u);
+    uint32_t vx, vy, vz;
+    tree_cell(v, vx, vy, vz);
+    const uint32_t x = bx + vx, y = by + vy, z = bz + vz;
     const D dx = absdiff(x, q.x), dy = absdiff(y, q.y), dz = absdiff(z, q.z);
     const D d = dx * dx + dy * dy + dz * dz;
     if (d <= cd) {  // the key is formed only for a voxel that can win
@@ -668,226 +655,277 @@ __device__ __forceinline__ void brick_voxels(unsigned long long m, uint32_t bx, 
   }
 }
 
-template <typename D>
-__device__ void search_tree(const NnSeg& sg, const Qry& q, uint32_t lane, TreeFrame* fr,
-                            uint32_t* lbc, uint32_t* pos, BestKey<D>& best) {
-  const uint32_t full = 0xffffffffu;
-  const TreeView& tv = sg.tree;
-  const uint32_t T = tv.levels, b = sg.a.bits;
-  if (T == 1) {
-    tree_brick(__ldg(tv.brick), 0, 0, 0, q, b, lane, best);
-    return;
+// One brick examined by the whole group: lane g takes the voxels numbered
+// [g * 64/G, (g + 1) * 64/G).
+template <int G, typename D>
+__device__ __forceinline__ void group_brick(uint32_t gm, uint32_t g, unsigned long long m,
+                                            uint32_t bx, uint32_t by, uint32_t bz, const Qry& q,
+                                            uint32_t b, BestKey<D>& best) {
+  constexpr uint32_t NB = 64 / G;
+  const unsigned long long own = (G == 1 ? ~0ull : ((1ull << NB) - 1ull)) << (g * NB);
+  D cd = (D)~(D)0;
+  unsigned long long ck = ~0ull;
+  brick_voxels<D>(m & own, bx, by, bz, q, b, cd, ck);
+  best.merge(gm, cd, ck);
+}
+
+// The search state of one lane: the current node (its cell, level and the
+// lane's share of its children), and the same for each node on the path
+// above it, in local memory (two words per frame).
+template <int G, typename D>
+struct TreeWalk {
+  static constexpr uint32_t NB = 64 / G;
+  unsigned long long stk[2 * kTreeMaxLevels];
+  uint32_t base;  // tree index of the lane's first child
+  uint32_t mine;  // the lane's children (bit k: child g * NB + k)
+  uint32_t rem;   // those still to visit
+  uint32_t ox, oy, oz, lvl;
+  int depth;
+  bool done;
+
+  __device__ __forceinline__ void enter(const uint4& r, uint32_t g) {
+    const unsigned long long m = r.x | ((unsigned long long)r.y << 32);
+    mine = (uint32_t)(m >> (g * NB)) & (uint32_t)((1ull << NB) - 1ull);
+    base = r.z + (uint32_t)__popcll(m & ((1ull << (g * NB)) - 1ull));
+    rem = mine;
   }
-  uint32_t lvl = T;
-  const uint4 r0 = __ldg(tv.node[T]);
-  unsigned long long mask = r0.x | ((unsigned long long)r0.y << 32), rem = mask;
-  uint32_t first = r0.z, ox = 0, oy = 0, oz = 0;
-  int depth = 0;
-  bool s_pop = false;
-  // fresh: the current frame was just entered (its children's bounds are
-  // computed and, above level 2, kept in lbc[depth] for the way back)
-  bool fresh = true;
-  while (true) {
-    // a stored voxel at distance 0 is the answer (voxels are unique, so no
-    // other voxel can tie with it)
-    if (best.d2 == (D)0) break;
-    // The children still to visit, compacted: lane k takes the k-th of them
-    // (and the (k+32)-th when more than 32 are left), so a node with few
-    // children keeps few lanes busy instead of two fixed slots per lane.
-    // Each lane loads the record of its child (a node's child set and first
-    // child, or a brick's voxels) with its box code, so that the chosen
-    // child's record is already in a register when the warp enters it.
-    const uint32_t rlo = (uint32_t)rem, rhi = (uint32_t)(rem >> 32);
-    const uint32_t nlo = __popc(rlo), nr = nlo + __popc(rhi);
-    const uint32_t ltm = lanemask_lt();
-    __syncwarp();
-    if ((rlo >> lane) & 1u) pos[__popc(rlo & ltm)] = lane;
-    if ((rhi >> lane) & 1u) pos[nlo + __popc(rhi & ltm)] = lane + 32;
-    __syncwarp();
-    const bool two = nr > 32;  // warp-uniform
-    const bool h0 = lane < nr, h1 = two && lane + 32 < nr;
-    const uint32_t c0 = h0 ? pos[lane] : 0u, c1 = h1 ? pos[lane + 32] : 0u;
-    // box codes: bricks (children of level 2) in voxels, 2 bits per bound;
-    // nodes in their grandchild units (4^(lvl-3) voxels), 4 bits per bound
-    const uint32_t sh = 2 * (lvl - 1);
-    const uint32_t ss = lvl == 2 ? 0u : sh - 4;
+
+  __device__ __forceinline__ void pop() {
+    if (depth == 0) {
+      done = true;
+      return;
+    }
+    --depth;
+    const unsigned long long f0 = stk[2 * depth], f1 = stk[2 * depth + 1];
+    base = (uint32_t)f0;
+    mine = (uint32_t)(f0 >> 32) & 0xFFFFu;
+    rem = (uint32_t)(f0 >> 48);
+    ox = (uint32_t)f1 & 0xFFFFu;
+    oy = (uint32_t)(f1 >> 16) & 0xFFFFu;
+    oz = (uint32_t)(f1 >> 32) & 0xFFFFu;
+    lvl = (uint32_t)(f1 >> 48);
+  }
+
+  // One step of the descent (the group's lanes together).
+  __device__ __forceinline__ void step(const TreeView& tv, const Qry& q, uint32_t b, uint32_t gm,
+                                       uint32_t g, BestKey<D>& best) {
+    // a stored voxel at distance 0 is the answer (voxels are unique)
+    if (best.d2 == (D)0) {
+      done = true;
+      return;
+    }
+    const bool bricks = lvl == 2;
     const uint32_t cap = tv.cap[lvl - 1];
-    const uint32_t i0 = first + (uint32_t)__popcll(mask & ((1ull << c0) - 1ull));
-    const uint32_t i1 = first + (uint32_t)__popcll(mask & ((1ull << c1) - 1ull));
-    const bool cached = CGA_NN_TREE_CACHE && !fresh;
-    uint4 k0 = make_uint4(0u, 0u, 0u, 0u), k1 = make_uint4(0u, 0u, 0u, 0u);
-    D lb0 = (D)~(D)0, lb1 = (D)~(D)0;
-    if (cached) {
-      // back in a frame above level 2: its bounds are kept (no loads; a kept
-      // bound saturates at 2^32 - 1, still a lower bound)
-      if (h0) lb0 = (D)lbc[depth * 64 + c0];
-      if (h1) lb1 = (D)lbc[depth * 64 + c1];
-    } else {
-      if (lvl == 2) {
-        if (h0 && i0 < cap) {
-          const unsigned long long m0 = __ldg(tv.brick + i0);
-          k0 = make_uint4((uint32_t)m0, (uint32_t)(m0 >> 32), 0u, __ldg(tv.bcode + i0));
+    const uint4* nd = tv.node[lvl - 1];
+    const uint2* pc = tv.pcode[lvl - 1];
+    const uint32_t OX = ox << 2, OY = oy << 2, OZ = oz << 2;
+    // the query from the node's origin, and the same less the width of a box
+    // unit (the children's boxes are in cells of 2^ss voxels from there)
+    const uint32_t ss = bricks ? 0u : 2 * (lvl - 3);
+    const int tx = q.x - (int)(ox << (2 * lvl)), ty = q.y - (int)(oy << (2 * lvl)),
+              tz = q.z - (int)(oz << (2 * lvl));
+    const int ub = 1 - (1 << ss);
+    D mlb = (D)~(D)0;
+    uint32_t mk = 0, mci = 0, surv = 0;
+    for (uint32_t r = rem; r != 0u; r &= r - 1u) {
+      const uint32_t k = (uint32_t)__ffs((int)r) - 1u;
+      const uint32_t ci = base + (uint32_t)__popc(mine & ((1u << k) - 1u));
+      if (ci >= cap) continue;
+      const D lb = parent_frame_lb<D>(__ldg(pc + ci), tx, ty, tz, ub, ss);
+      if (lb <= best.d2) {
+        surv |= 1u << k;
+        if (lb < mlb) {
+          mlb = lb;
+          mk = k;
+          mci = ci;
         }
-        if (h1 && i1 < cap) {
-          const unsigned long long m1 = __ldg(tv.brick + i1);
-          k1 = make_uint4((uint32_t)m1, (uint32_t)(m1 >> 32), 0u, __ldg(tv.bcode + i1));
-        }
-      } else {
-        const uint4* nd = tv.node[lvl - 1];
-        if (h0 && i0 < cap) k0 = __ldg(nd + i0);
-        if (h1 && i1 < cap) k1 = __ldg(nd + i1);
-      }
-      if (h0) {
-        lb0 = child_lb_any<D>(lvl == 2, q, ((ox << 2) + (c0 >> 4)) << sh,
-                              ((oy << 2) + ((c0 >> 2) & 3u)) << sh, ((oz << 2) + (c0 & 3u)) << sh,
-                              k0.w, ss);
-      }
-      if (two && h1) {
-        lb1 = child_lb_any<D>(lvl == 2, q, ((ox << 2) + (c1 >> 4)) << sh,
-                              ((oy << 2) + ((c1 >> 2) & 3u)) << sh, ((oz << 2) + (c1 & 3u)) << sh,
-                              k1.w, ss);
-      }
-      if (CGA_NN_TREE_CACHE && lvl > 2) {
-        if (h0) lbc[depth * 64 + c0] = lb0 > (D)0xfffffffeu ? 0xffffffffu : (uint32_t)lb0;
-        if (h1) lbc[depth * 64 + c1] = lb1 > (D)0xfffffffeu ? 0xffffffffu : (uint32_t)lb1;
       }
     }
-    const bool in0 = h0 && i0 < cap && lb0 <= best.d2;
-    const bool in1 = h1 && i1 < cap && lb1 <= best.d2;
-    const uint32_t s0 = __ballot_sync(full, in0), s1 = __ballot_sync(full, in1);
-    // the surviving children as a child set
-    const uint32_t o0 = in0 ? c0 : 64u, o1 = in1 ? c1 : 64u;
-    unsigned long long surv = 0ull;
-    if (s0 | s1) {
-      const uint32_t bl0 = o0 < 32 ? 1u << o0 : 0u, bh0 = o0 >= 32 && o0 < 64 ? 1u << (o0 - 32) : 0u;
-      const uint32_t bl1 = o1 < 32 ? 1u << o1 : 0u, bh1 = o1 >= 32 && o1 < 64 ? 1u << (o1 - 32) : 0u;
-      const uint32_t sl = __reduce_or_sync(full, bl0 | bl1), shi = __reduce_or_sync(full, bh0 | bh1);
-      surv = ((unsigned long long)shi << 32) | sl;
+    if (__ballot_sync(gm, surv != 0u) == 0u) {
+      pop();
+      return;
     }
-    if (lvl == 2 && surv != 0ull) {
-      // Children are bricks.  Without a candidate yet only the nearest brick
-      // is examined (its voxels set a bound that prunes its siblings), else
-      // every lane examines the voxels of its surviving bricks (a loop over
-      // their occupancy bits) and the level-2 node is done.
-      const bool only_nearest = best.d2 == (D)~(D)0;
-      bool e0 = in0, e1 = in1;
-      uint32_t cs_first = 64;
-      if (only_nearest) {
-        D v = in0 ? lb0 : (D)~(D)0;
-        uint32_t c = c0;
-        if (in1 && lb1 < v) {
-          v = lb1;
-          c = c1;
-        }
-        const D mv = warp_min_d(v);
-        const uint32_t win = __ballot_sync(full, (in0 || in1) && v == mv);
-        cs_first = __shfl_sync(full, c, __ffs(win) - 1);
-        e0 = in0 && cs_first == c0;
-        e1 = in1 && cs_first == c1;
+    // the surviving child with the least bound (the lowest lane on a tie)
+    const D gmin = group_min(gm, mlb);
+    const uint32_t ow = (uint32_t)__ffs((int)__ballot_sync(gm, surv != 0u && mlb == gmin)) - 1u;
+    const uint32_t cs = __shfl_sync(gm, g * NB + mk, ow);
+    const uint32_t csi = __shfl_sync(gm, mci, ow);
+    rem = surv;
+    if ((threadIdx.x & 31u) == ow) rem &= ~(1u << mk);
+    uint32_t cx, cy, cz;
+    tree_cell(cs, cx, cy, cz);
+    const uint32_t nx = OX + cx, ny = OY + cy, nz = OZ + cz;
+    if (bricks) {
+      if (best.d2 == (D)~(D)0) {
+        // no candidate yet: the nearest brick alone; the next step bounds
+        // the node's other bricks against the distance it gives
+        group_brick<G, D>(gm, g, __ldg(tv.brick + csi), nx << 2, ny << 2, nz << 2, q, b, best);
+        return;
       }
+      // every surviving brick, each lane its own, and the node is done
       D cd = (D)~(D)0;
       unsigned long long ck = ~0ull;
-      if (e0) {
-        brick_voxels<D>(k0.x | ((unsigned long long)k0.y << 32),
-                        ((ox << 2) + (c0 >> 4)) << 2, ((oy << 2) + ((c0 >> 2) & 3u)) << 2,
-                        ((oz << 2) + (c0 & 3u)) << 2, q, b, cd, ck);
+      for (uint32_t r = surv; r != 0u; r &= r - 1u) {
+        const uint32_t k = (uint32_t)__ffs((int)r) - 1u;
+        const uint32_t ci = base + (uint32_t)__popc(mine & ((1u << k) - 1u));
+        uint32_t bx, by, bz;
+        tree_cell(g * NB + k, bx, by, bz);
+        brick_voxels<D>(__ldg(tv.brick + ci), (OX + bx) << 2, (OY + by) << 2, (OZ + bz) << 2, q,
+                        b, cd, ck);
       }
-      if (e1) {
-        brick_voxels<D>(k1.x | ((unsigned long long)k1.y << 32),
-                        ((ox << 2) + (c1 >> 4)) << 2, ((oy << 2) + ((c1 >> 2) & 3u)) << 2,
-                        ((oz << 2) + (c1 & 3u)) << 2, q, b, cd, ck);
-      }
-      const bool better = cd < best.d2 || (cd == best.d2 && ck < best.key);
-      if (__any_sync(full, better)) {
-        best.warp_min_of(better ? cd : best.d2, better ? ck : best.key);
-      }
-      if (only_nearest) {
-        rem = surv & ~(1ull << cs_first);
-        continue;
-      }
-      s_pop = true;
+      best.merge(gm, cd, ck);
+      pop();
+      return;
     }
-    if (surv == 0ull || s_pop) {
-      s_pop = false;
-      if (depth == 0) break;
-      --depth;
-      fresh = false;
-      __syncwarp();
-      const TreeFrame f = fr[depth];
-      lvl = f.lvl;
-      mask = f.mask;
-      rem = f.rem;
-      first = f.first;
-      ox = f.ox;
-      oy = f.oy;
-      oz = f.oz;
-      continue;
-    }
-    // the surviving child with the least bound, and its record from the lane
-    // that loaded it
-    D v = in0 ? lb0 : (D)~(D)0;
-    uint32_t c = c0;
-    if (in1 && lb1 < v) {
-      v = lb1;
-      c = c1;
-    }
-    const D mv = warp_min_d(v);
-    const uint32_t win = __ballot_sync(full, (in0 || in1) && v == mv);
-    const int owner = __ffs(win) - 1;
-    const uint32_t cs = __shfl_sync(full, c, owner);
-    uint32_t rx, ry, rz;
-    if (cached) {
-      const uint32_t ci = first + (uint32_t)__popcll(mask & ((1ull << cs) - 1ull));
-      const uint4 r = __ldg(tv.node[lvl - 1] + ci);  // ci < cap: cs survived the check above
-      rx = r.x;
-      ry = r.y;
-      rz = r.z;
-    } else {
-      const uint4 mine = cs == c1 && in1 ? k1 : k0;
-      rx = __shfl_sync(full, mine.x, owner);
-      ry = __shfl_sync(full, mine.y, owner);
-      rz = __shfl_sync(full, mine.z, owner);
-    }
-    rem = surv & ~(1ull << cs);
-    const uint32_t nx = (ox << 2) + (cs >> 4), ny = (oy << 2) + ((cs >> 2) & 3u),
-                   nz = (oz << 2) + (cs & 3u);
-    // (lvl > 2 here: a level-2 node was settled above.)  The last surviving
-    // child replaces its parent's frame (nothing to come back to); otherwise
-    // the parent's frame is kept for the way back.
-    if (rem != 0ull) {
-      __syncwarp();
-      if (lane == 0) fr[depth] = TreeFrame{mask, rem, first, ox, oy, oz, lvl, 0u};
-      __syncwarp();
+    // the node's frame is kept only while a lane has children left to visit
+    if (__any_sync(gm, rem != 0u)) {
+      stk[2 * depth] = base | ((unsigned long long)mine << 32) | ((unsigned long long)rem << 48);
+      stk[2 * depth + 1] = ox | ((unsigned long long)oy << 16) | ((unsigned long long)oz << 32) |
+                           ((unsigned long long)lvl << 48);
       ++depth;
     }
+    enter(__ldg(nd + csi), g);
     --lvl;
-    mask = rx | ((unsigned long long)ry << 32);
-    rem = mask;
-    first = rz;
     ox = nx;
     oy = ny;
     oz = nz;
-    fresh = true;
   }
-}
+};
 
-// CGA index of the stored voxel with key `key` (the Sec. V-A lookup by the
-// whole warp: x directory or X_index, the slab's Y range, the column's Z
-// range).
+// CGA index of the stored voxel with key `key` (the Sec. V-A lookup: x
+// directory or X_index, the slab's Y range, the column's Z range).
 __device__ __forceinline__ uint32_t stored_index(const NnSeg& sg, unsigned long long key) {
   const Levels& a = sg.a;
   const uint32_t b = a.bits, mk = (1u << b) - 1u;
   const uint32_t x = (uint32_t)(key >> (2 * b)), y = (uint32_t)(key >> b) & mk,
                  z = (uint32_t)key & mk;
   const uint32_t h = (uint32_t)a.hdr->cnt[2];
-  const uint32_t slab = sg.xdir != nullptr ? __ldg(sg.xdir + x) : warp_lower_bound_u16(a.idx2, 0, h, x);
-  const uint32_t ys = __ldg(a.ptr2 + slab), ye = __ldg(a.ptr2 + slab + 1);
-  const uint32_t c = warp_lower_bound_u16(a.idx1, ys, ye, y);
-  // the column's voxel range from Y_pointer (4 bytes a column; the 16-byte
-  // column table is left out of L2's working set here)
-  const uint32_t zs = __ldg(a.ptr1 + c), ze = __ldg(a.ptr1 + c + 1);
-  return warp_lower_bound_u16(a.idx0, zs, ze, z);
+  const uint32_t slab = sg.xdir != nullptr ? __ldg(sg.xdir + x) : lower_bound_u16(a.idx2, 0, h, x);
+  const uint32_t c = lower_bound_u16(a.idx1, __ldg(a.ptr2 + slab), __ldg(a.ptr2 + slab + 1), y);
+  return lower_bound_u16(a.idx0, __ldg(a.ptr1 + c), __ldg(a.ptr1 + c + 1), z);
 }
+
+template <int G, typename D>
+__device__ void search_tree(const TreeView& tv, const Qry& q, uint32_t b, bool active,
+                                   uint32_t gm, uint32_t g, BestKey<D>& best) {
+  if (tv.levels == 1) {
+    if (active) group_brick<G, D>(gm, g, __ldg(tv.brick), 0u, 0u, 0u, q, b, best);
+    return;
+  }
+  TreeWalk<G, D> w;
+  w.done = !active;
+  if (active) {
+    w.lvl = tv.levels;
+    w.ox = w.oy = w.oz = 0;
+    w.depth = 0;
+    w.enter(__ldg(tv.node[tv.levels]), g);
+  }
+  while (__any_sync(0xffffffffu, !w.done)) {
+    if (!w.done) w.step(tv, q, b, gm, g, best);
+  }
+}
+
+// G lanes per query slot over every segment with a tree (a segment without
+// one is left to k_nn_warp).  A warp takes 32 / G consecutive slots at a time
+// (neighbouring queries in Morton order) and moves on when all are answered;
+// the loop is warp-uniform, so that the descent's warp votes see every lane.
+template <int G>
+__global__ void __launch_bounds__(256, CGA_NN_TREE_BLOCKS)
+    k_nn_tree(const NnSeg* __restrict__ segs, int S, NnSeg inline_seg, uint32_t total_slots,
+                     const unsigned long long* __restrict__ order,
+                     const unsigned int* __restrict__ order_err) {
+  constexpr uint32_t QW = 32 / G;
+  const bool sorted = order != nullptr && (order_err == nullptr || *order_err == 0u);
+  const uint32_t lane = threadIdx.x & 31, g = lane % G;
+  const uint32_t gm = G == 32 ? 0xffffffffu : (uint32_t)((1ull << G) - 1ull) << (lane - g);
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * QW; base < total_slots;
+       base += nwarps * QW) {
+    const uint32_t slot = base + lane / G;
+    bool active = slot < total_slots;
+    const NnSeg& sg = segs != nullptr ? segs[find_nn_seg(segs, S, base / (uint32_t)kTile)]
+                                      : inline_seg;
+    const uint32_t local = slot - sg.tile_base * (uint32_t)kTile;
+    active = active && sg.tree.levels > 0 && local < sg.m;
+    const uint32_t j = active ? (sorted ? (uint32_t)__ldcs(order + slot) : local) : 0u;
+    active = active && j < sg.m;
+    int qx = 0, qy = 0, qz = 0;
+    if (active) {
+      const bool valid = query_voxel(sg, j, qx, qy, qz);
+      if (!valid || sg.a.hdr->cnt[0] == 0) {
+        if (g == 0) {
+          __stcs(sg.idx + j, 0xffffffffu);
+          __stcs(sg.d2 + j, ~0ull);
+        }
+        active = false;
+      }
+    }
+    const uint32_t b = sg.a.bits;
+    const int top = (1 << b) - 1;
+    const uint32_t cqx = (uint32_t)min(max(qx, 0), top);
+    const uint32_t cqy = (uint32_t)min(max(qy, 0), top);
+    const uint32_t cqz = (uint32_t)min(max(qz, 0), top);
+    const Qry qq{qx, qy, qz, cqx, cqy, cqz};
+    unsigned long long d2 = ~0ull, key = ~0ull;
+    const bool narrow = b <= 15 && (uint32_t)qx == cqx && (uint32_t)qy == cqy &&
+                        (uint32_t)qz == cqz;
+    if (__all_sync(0xffffffffu, narrow || !active)) {
+      BestKey<uint32_t> best{0xffffffffu, ~0ull};
+      search_tree<G, uint32_t>(sg.tree, qq, b, active, gm, g, best);
+      if (best.d2 != 0xffffffffu) {
+        d2 = best.d2;
+        key = best.key;
+      }
+    } else {
+      BestKey<unsigned long long> best{~0ull, ~0ull};
+      search_tree<G, unsigned long long>(sg.tree, qq, b, active, gm, g, best);
+      d2 = best.d2;
+      key = best.key;
+    }
+    if (active && g == 0) {
+#if CGA_NN_TREE_DEFER
+      __stcs(sg.d2 + j, d2 != ~0ull ? key : ~0ull);
+#else
+      __stcs(sg.idx + j, d2 != ~0ull ? stored_index(sg, key) : 0xffffffffu);
+      __stcs(sg.d2 + j, d2);
+#endif
+    }
+  }
+}
+
+#if CGA_NN_TREE_DEFER
+// The answers of the tree search: the key left in the distance output
+// becomes the CGA index (Sec. V-A lookup) and the exact squared distance
+// from the query voxel (all ones in both for no answer).  One thread per
+// query of every segment with a tree.
+__global__ void __launch_bounds__(256) k_nn_tree_index(const NnSeg* __restrict__ segs, int S,
+                                                       NnSeg inline_seg,
+                                                       uint32_t total_slots) {
+  for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < total_slots;
+       slot += gridDim.x * blockDim.x) {
+    const NnSeg& sg = segs != nullptr ? segs[find_nn_seg(segs, S, slot / (uint32_t)kTile)]
+                                      : inline_seg;
+    const uint32_t j = slot - sg.tile_base * (uint32_t)kTile;
+    if (sg.tree.levels == 0 || j >= sg.m) continue;
+    const unsigned long long key = __ldcs(sg.d2 + j);
+    const uint32_t b = sg.a.bits, mk = (1u << b) - 1u;
+    // (a key outside the grid: an output the search never wrote, under a
+    // caller-given order that is not a permutation)
+    if (key == ~0ull || (key >> (3 * b)) != 0ull) {
+      __stcs(sg.idx + j, 0xffffffffu);
+      __stcs(sg.d2 + j, ~0ull);
+      continue;
+    }
+    int qx, qy, qz;
+    query_voxel(sg, j, qx, qy, qz);
+    const unsigned long long dx = absdiff((uint32_t)(key >> (2 * b)), qx),
+                             dy = absdiff((uint32_t)(key >> b) & mk, qy),
+                             dz = absdiff((uint32_t)key & mk, qz);
+    __stcs(sg.idx + j, stored_index(sg, key));
+    __stcs(sg.d2 + j, dx * dx + dy * dy + dz * dz);
+  }
+}
+#endif
 
 // NC: the most coarse levels any segment of the launch carries (0, 1 or 2).
 // The fine-only instantiation is held to 40 registers (six blocks per SM),
@@ -895,14 +933,10 @@ __device__ __forceinline__ uint32_t stored_index(const NnSeg& sg, unsigned long 
 // the search's load latency than the spilled values cost (eight and six
 // blocks respectively spill enough to be slower).
 template <int NC>
-__global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
-                                               : (NC > 0 ? CGA_NN_COARSE_BLOCKS : CGA_NN_FINE_BLOCKS))
+__global__ void __launch_bounds__(256, NC > 0 ? CGA_NN_COARSE_BLOCKS : CGA_NN_FINE_BLOCKS)
     k_nn_warp(const NnSeg* __restrict__ segs, int S, NnSeg inline_seg, uint32_t total_slots,
               const unsigned long long* __restrict__ order,
               const unsigned int* __restrict__ order_err) {
-  __shared__ TreeFrame s_fr[NC == 3 ? 8 * kTreeMaxLevels : 1];
-  __shared__ uint32_t s_lbc[NC == 3 && CGA_NN_TREE_CACHE ? 8 * kTreeMaxLevels * 64 : 1];
-  __shared__ uint32_t s_pos[NC == 3 ? 8 * 64 : 1];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const bool sorted = order != nullptr && (order_err == nullptr || *order_err == 0u);
@@ -910,6 +944,7 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
        slot += nwarps) {
     const uint32_t tile = slot / (uint32_t)kTile;
     const NnSeg& sg = segs != nullptr ? segs[find_nn_seg(segs, S, tile)] : inline_seg;
+    if (sg.tree.levels > 0) continue;  // searched by k_nn_tree
     const uint32_t local = slot - sg.tile_base * (uint32_t)kTile;
     if (local >= sg.m) continue;
     // queries, the order and the results stream through once: loaded and
@@ -920,21 +955,7 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
     const uint32_t u = (uint32_t)a.hdr->cnt[0], h = (uint32_t)a.hdr->cnt[2];
     // query voxel, clamped to +-2^30 (so every coordinate difference fits 31 bits)
     int qx, qy, qz;
-    bool valid;
-    if (sg.qv != nullptr) {
-      const int* v = sg.qv + 3 * (size_t)j;
-      qx = min(max(__ldg(v), -kQueryLimit), kQueryLimit);
-      qy = min(max(__ldg(v + 1), -kQueryLimit), kQueryLimit);
-      qz = min(max(__ldg(v + 2), -kQueryLimit), kQueryLimit);
-      valid = true;
-    } else {
-      const float* p = sg.q + 3 * (size_t)j;
-      const float px = __ldcs(p), py = __ldcs(p + 1), pz = __ldcs(p + 2);
-      valid = isfinite(px) && isfinite(py) && isfinite(pz);
-      qx = valid ? (int)quantize_query(px, sg.scale, sg.off[0]) : 0;
-      qy = valid ? (int)quantize_query(py, sg.scale, sg.off[1]) : 0;
-      qz = valid ? (int)quantize_query(pz, sg.scale, sg.off[2]) : 0;
-    }
+    const bool valid = query_voxel(sg, j, qx, qy, qz);
     if (!valid || u == 0) {
       if (lane == 0) {
         __stcs(sg.idx + j, 0xffffffffu);
@@ -947,40 +968,7 @@ __global__ void __launch_bounds__(256, NC == 3 ? CGA_NN_TREE_BLOCKS
     const uint32_t cqx = (uint32_t)min(max(qx, 0), top);
     const uint32_t cqy = (uint32_t)min(max(qy, 0), top);
     const uint32_t cqz = (uint32_t)min(max(qz, 0), top);
-    if constexpr (NC == 3) {
-      if (sg.tree.levels > 0) {
-        // 32-bit distances when every one fits: a query inside a grid of at
-        // most 15 bits per axis (3 * (2^15 - 1)^2 < 2^32)
-        const Qry qq{qx, qy, qz, cqx, cqy, cqz};
-        TreeFrame* fr = s_fr + (threadIdx.x >> 5) * kTreeMaxLevels;
-        uint32_t* lbc = CGA_NN_TREE_CACHE ? s_lbc + (threadIdx.x >> 5) * kTreeMaxLevels * 64 : s_lbc;
-        uint32_t* pos = s_pos + (threadIdx.x >> 5) * 64;
-        const bool narrow = b <= 15 && (uint32_t)qx == cqx && (uint32_t)qy == cqy &&
-                            (uint32_t)qz == cqz;
-        unsigned long long d2 = ~0ull, key = ~0ull;
-        if (narrow) {
-          BestKey<uint32_t> bk{0xffffffffu, ~0ull};
-          search_tree<uint32_t>(sg, qq, lane, fr, lbc, pos, bk);
-          if (bk.d2 != 0xffffffffu) {
-            d2 = bk.d2;
-            key = bk.key;
-          }
-        } else {
-          BestKey<unsigned long long> bk{~0ull, ~0ull};
-          search_tree<unsigned long long>(sg, qq, lane, fr, lbc, pos, bk);
-          d2 = bk.d2;
-          key = bk.key;
-        }
-        const uint32_t ix = d2 != ~0ull ? stored_index(sg, key) : 0xffffffffu;
-        if (lane == 0) {
-          __stcs(sg.idx + j, ix);
-          __stcs(sg.d2 + j, d2);
-        }
-        continue;
-      }
-    }
     Best best{~0ull, 0xffffffffu};
-    // (the tree kernel searches a segment without a tree by the fine search)
     if (NC == 2 && sg.ncoarse >= 2) {
       if constexpr (NC == 2) search_levels<2>(sg, Qry{qx, qy, qz, cqx, cqy, cqz}, lane, best);
     } else if ((NC == 1 || NC == 2) && sg.ncoarse >= 1) {
@@ -1051,7 +1039,8 @@ cudaError_t nn_upload_one(const NnSeg& h_seg, const NnTables& t, cudaStream_t st
   return e;
 }
 
-// Blocks of k_nn_warp<kind> that fit on one SM (queried once per kind).
+// Blocks of a search kernel that fit on one SM (queried once per kernel:
+// 0-2 k_nn_warp of that many coarse levels, 3 k_nn_tree).
 static uint32_t resident_blocks(uint32_t kind) {
   static std::atomic<int> cache[4] = {{0}, {0}, {0}, {0}};
   int n = cache[kind].load(std::memory_order_relaxed);
@@ -1060,7 +1049,9 @@ static uint32_t resident_blocks(uint32_t kind) {
     if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_warp<0>, 256, 0);
     if (kind == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_warp<1>, 256, 0);
     if (kind == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_warp<2>, 256, 0);
-    if (kind == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_warp<3>, 256, 0);
+    if (kind == 3) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nn_tree<CGA_NN_TREE_GROUP>, 256, 0);
+    }
     if (e != cudaSuccess || n <= 0) {
       cudaGetLastError();
       n = 4;
@@ -1070,20 +1061,34 @@ static uint32_t resident_blocks(uint32_t kind) {
   return (uint32_t)n;
 }
 
+// kinds: bit k set when some segment of the launch has nn_kind k.  Segments
+// with a tree go to k_nn_tree, the others to k_nn_warp of their largest kind.
+// Each kernel runs one wave of resident blocks striding over the query slots
+// (a second wave would only add its own tail).
 static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
                           uint32_t total_tiles, const unsigned long long* order,
-                          const unsigned int* order_err, uint32_t kind,
+                          const unsigned int* order_err, uint32_t kinds,
                           cudaStream_t stream) {
   const uint32_t total_slots = total_tiles * (uint32_t)kTile;
-  // one wave: as many blocks as stay resident (the warps stride over the
-  // query slots, so a second wave would only add its own tail)
-  kind = std::min(kind, 3u);
-  const uint32_t blocks = std::min<uint32_t>((total_slots + 7) / 8,
-                                             (uint32_t)device_sm_count() * resident_blocks(kind));
-  if (kind == 3) {
-    k_nn_warp<3><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
-                                             order_err);
-  } else if (kind == 2) {
+  const uint32_t sms = (uint32_t)device_sm_count();
+  if (kinds & 8u) {
+    constexpr uint32_t qpb = 256 / CGA_NN_TREE_GROUP;  // queries per block and round
+    const uint32_t blocks = std::min<uint32_t>((total_slots + qpb - 1) / qpb,
+                                               sms * resident_blocks(3));
+    k_nn_tree<CGA_NN_TREE_GROUP><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots,
+                                                             order, order_err);
+    count_launch(1);
+#if CGA_NN_TREE_DEFER
+    k_nn_tree_index<<<std::min<uint32_t>((total_slots + 255) / 256, sms * 8), 256, 0, stream>>>(
+        d_segs, S, inline_seg, total_slots);
+    count_launch(1);
+#endif
+  }
+  kinds &= 7u;
+  if (kinds == 0) return;
+  const uint32_t kind = kinds >= 4u ? 2u : (kinds >= 2u ? 1u : 0u);
+  const uint32_t blocks = std::min<uint32_t>((total_slots + 7) / 8, sms * resident_blocks(kind));
+  if (kind == 2) {
     k_nn_warp<2><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots, order,
                                              order_err);
   } else if (kind == 1) {
@@ -1114,12 +1119,12 @@ cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
 
 cudaError_t run_nn_search(const NnSeg& seg, const unsigned long long* order, cudaStream_t stream) {
   if (seg.m == 0) return cudaSuccess;
-  launch_search(nullptr, 1, seg, seg.num_tiles, order, nullptr, nn_kind(seg), stream);
+  launch_search(nullptr, 1, seg, seg.num_tiles, order, nullptr, 1u << nn_kind(seg), stream);
   return cudaGetLastError();
 }
 
 cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaStream_t stream,
-                          uint32_t max_kind) {
+                          uint32_t kinds) {
   if (total_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(t.err, 0, sizeof(Header), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(t.sort.hist, 0, t.sort.zero_bytes, stream);
@@ -1131,8 +1136,7 @@ cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaSt
   if (e != cudaSuccess) return e;
   // four passes leave the sorted keys in keys0
   launch_search(t.segs, S, NnSeg{}, total_tiles,
-                static_cast<const unsigned long long*>(t.sort.keys0), &t.err->err, max_kind,
-                stream);
+                static_cast<const unsigned long long*>(t.sort.keys0), &t.err->err, kinds, stream);
   return cudaGetLastError();
 }
 
@@ -1141,16 +1145,16 @@ cudaError_t run_nn(const NnSeg* h_segs, int S, uint32_t total_tiles, void* scrat
   if (total_tiles == 0) return cudaSuccess;
   if (scratch == nullptr) {
     if (S != 1) return cudaErrorInvalidValue;
-    launch_search(nullptr, 1, h_segs[0], total_tiles, nullptr, nullptr, nn_kind(h_segs[0]),
+    launch_search(nullptr, 1, h_segs[0], total_tiles, nullptr, nullptr, 1u << nn_kind(h_segs[0]),
                   stream);
     return cudaGetLastError();
   }
   const NnTables t = nn_tables(scratch, total_tiles, S);
   const cudaError_t e = nn_upload(h_segs, S, t, stream);
   if (e != cudaSuccess) return e;
-  uint32_t max_kind = 0;
-  for (int s = 0; s < S; ++s) max_kind = std::max(max_kind, nn_kind(h_segs[s]));
-  return run_nn_device(S, total_tiles, t, stream, max_kind);
+  uint32_t kinds = 0;
+  for (int s = 0; s < S; ++s) kinds |= 1u << nn_kind(h_segs[s]);
+  return run_nn_device(S, total_tiles, t, stream, kinds);
 }
 
 }  // namespace libcga

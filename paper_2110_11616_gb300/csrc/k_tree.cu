@@ -11,7 +11,7 @@
 // nearest voxel with the smaller-key rule.
 //
 // Build (all on the device, no host wait): the voxels are re-keyed by
-// tree_key (each level's child index in 6 bits, coarsest level highest) by
+// tree_key (each level's child number in 6 bits, coarsest level highest) by
 // the sort pipeline's key pass, sorted by its radix passes, and every level
 // is then one compaction of the sorted distinct prefixes of the level below
 // (decoupled look-back over tiles for the output positions).
@@ -44,8 +44,9 @@ __global__ void k_tree_init(const Header* __restrict__ src, uint32_t* counts, ui
 __global__ void __launch_bounds__(kThreads) k_tree_level(
     const unsigned long long* __restrict__ P, const uint32_t* n_in,
     unsigned long long* __restrict__ NP, unsigned long long* __restrict__ brick,
-    uint16_t* __restrict__ bcode, uint4* __restrict__ node,
-    const uint16_t* __restrict__ ccode1, const uint4* __restrict__ cnode, uint32_t* n_out,
+    uint32_t* __restrict__ bcode, uint4* __restrict__ node,
+    const uint32_t* __restrict__ ccode1, const uint4* __restrict__ cnode,
+    uint2* __restrict__ cpcode, uint32_t* n_out,
     uint32_t* look, uint32_t* counter, unsigned int* err) {
   __shared__ uint32_t s_warp[kWarps];
   __shared__ uint32_t s_tile, s_excl;
@@ -106,34 +107,30 @@ __global__ void __launch_bounds__(kThreads) k_tree_level(
       mask |= 1ull << c;
       if (brick == nullptr) {
         // the child's box in this node's grandchild units
-        const uint32_t pos[3] = {c >> 4, (c >> 2) & 3u, c & 3u};
-        uint32_t cl[3], ch[3];
-        if (ccode1 != nullptr) {
-          const uint32_t cc = __ldg(ccode1 + f);  // brick: voxel units, 2 bits per bound
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            cl[a] = (cc >> (4 * a)) & 3u;
-            ch[a] = (cc >> (4 * a + 2)) & 3u;
-          }
-        } else {
-          const uint32_t cc = __ldg(&cnode[f].w);  // node: its grandchild units, 4 bits
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            cl[a] = ((cc >> (8 * a)) & 15u) >> 2;
-            ch[a] = ((cc >> (8 * a + 4)) & 15u) >> 2;
-          }
-        }
+        uint32_t pos[3];
+        tree_cell(c, pos[0], pos[1], pos[2]);
+        // the child's box in its own units: a brick's in voxels (0..3), a
+        // node's in its grandchild cells (0..15)
+        const uint32_t cc = ccode1 != nullptr ? __ldg(ccode1 + f) : __ldg(&cnode[f].w);
+        const uint32_t m = ccode1 != nullptr ? 4u : 16u;  // child cell in those units
+        uint32_t pl[3], ph[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          lo[a] = min(lo[a], pos[a] * 4 + cl[a]);
-          hi[a] = max(hi[a], pos[a] * 4 + ch[a]);
+          const uint32_t cl = (cc >> (8 * a)) & 15u, ch = (cc >> (8 * a + 4)) & 15u;
+          pl[a] = pos[a] * m + cl;
+          ph[a] = pos[a] * m + ch;
+          // in this node's grandchild cells (a node child's units are 4x finer)
+          const uint32_t s = ccode1 != nullptr ? 0u : 2u;
+          lo[a] = min(lo[a], pos[a] * 4 + (cl >> s));
+          hi[a] = max(hi[a], pos[a] * 4 + (ch >> s));
         }
+        cpcode[f] = make_uint2(pl[0] | ph[0] << 6 | pl[1] << 12 | ph[1] << 18, pl[2] | ph[2] << 6);
       }
     }
     if (NP != nullptr) NP[j] = pr;
     if (brick != nullptr) {
       brick[j] = mask;
-      bcode[j] = (uint16_t)tree_box_code(mask);
+      bcode[j] = tree_box_code(mask);
     } else {
       const uint32_t box = lo[0] | hi[0] << 4 | lo[1] << 8 | hi[1] << 12 | lo[2] << 16 | hi[2] << 20;
       node[j] = make_uint4((uint32_t)mask, (uint32_t)(mask >> 32), e, box);
@@ -167,10 +164,14 @@ TreeLayout tree_layout(uint32_t bits, uint64_t cap) {
   L.off[1] = p;
   p += align_up(std::max<uint64_t>(L.cap[1], 1) * 8);
   L.off_bcode = p;
-  p += align_up(std::max<uint64_t>(L.cap[1], 1) * 2);
+  p += align_up(std::max<uint64_t>(L.cap[1], 1) * 4);
   for (uint32_t l = 2; l <= L.levels; ++l) {
     L.off[l] = p;
     p += align_up(std::max<uint64_t>(L.cap[l], 1) * sizeof(uint4));
+  }
+  for (uint32_t l = 1; l < L.levels; ++l) {
+    L.off_pcode[l] = p;
+    p += align_up(std::max<uint64_t>(L.cap[l], 1) * sizeof(uint2));
   }
   L.bytes = p;
   return L;
@@ -180,8 +181,9 @@ TreeView tree_view(const TreeLayout& L, void* mem) {
   TreeView v{};
   char* b = static_cast<char*>(mem);
   v.brick = reinterpret_cast<const unsigned long long*>(b + L.off[1]);
-  v.bcode = reinterpret_cast<const uint16_t*>(b + L.off_bcode);
+  v.bcode = reinterpret_cast<const uint32_t*>(b + L.off_bcode);
   for (uint32_t l = 2; l <= L.levels; ++l) v.node[l] = reinterpret_cast<const uint4*>(b + L.off[l]);
+  for (uint32_t l = 1; l < L.levels; ++l) v.pcode[l] = reinterpret_cast<const uint2*>(b + L.off_pcode[l]);
   for (uint32_t l = 1; l <= L.levels; ++l) v.cap[l] = (uint32_t)std::max<uint64_t>(L.cap[l], 1);
   v.levels = L.levels;
   return v;
@@ -240,12 +242,13 @@ cudaError_t run_tree_build(const Levels& a, const TreeLayout& L, void* mem, void
     const uint32_t lt = tiles_of(L.cap[l - 1]);
     unsigned long long* np = l < L.levels ? buf[cur ^ 1] : nullptr;
     unsigned long long* br = l == 1 ? reinterpret_cast<unsigned long long*>(m + L.off[1]) : nullptr;
-    uint16_t* bc = l == 1 ? reinterpret_cast<uint16_t*>(m + L.off_bcode) : nullptr;
+    uint32_t* bc = l == 1 ? reinterpret_cast<uint32_t*>(m + L.off_bcode) : nullptr;
     uint4* nd = l >= 2 ? reinterpret_cast<uint4*>(m + L.off[l]) : nullptr;
-    const uint16_t* cc1 = l == 2 ? reinterpret_cast<const uint16_t*>(m + L.off_bcode) : nullptr;
+    const uint32_t* cc1 = l == 2 ? reinterpret_cast<const uint32_t*>(m + L.off_bcode) : nullptr;
     const uint4* cn = l >= 3 ? reinterpret_cast<const uint4*>(m + L.off[l - 1]) : nullptr;
+    uint2* cp = l >= 2 ? reinterpret_cast<uint2*>(m + L.off_pcode[l - 1]) : nullptr;
     k_tree_level<<<lt, kThreads, 0, stream>>>(buf[cur], counts + (l - 1), np, br, bc, nd, cc1, cn,
-                                             counts + l, w, w + lt, herr);
+                                             cp, counts + l, w, w + lt, herr);
     count_launch(1);
     w += lt + 1;
     cur ^= 1;

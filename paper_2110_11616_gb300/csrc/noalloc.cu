@@ -79,7 +79,7 @@ extern "C" int cga_nn_query_noalloc(const cga_t* a, const float* d_q, uint64_t m
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const libcga::NnTables t = libcga::nn_tables(scratch, tiles, 1);
   cudaError_t e = libcga::nn_upload_one(seg, t, s);
-  if (e == cudaSuccess) e = libcga::run_nn_device(1, tiles, t, s, libcga::nn_kind(seg));
+  if (e == cudaSuccess) e = libcga::run_nn_device(1, tiles, t, s, 1u << libcga::nn_kind(seg));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return CGA_ERR_CUDA;
