@@ -260,9 +260,6 @@ constexpr int kQueryLimit = 1 << 30;
 #ifndef CGA_NN_TREE_BLOCKS
 #define CGA_NN_TREE_BLOCKS 4
 #endif
-#ifndef CGA_NN_TREE_DEFER
-#define CGA_NN_TREE_DEFER 0
-#endif
 #ifndef CGA_NN_TREE_GROUP
 #define CGA_NN_TREE_GROUP 4
 #endif
@@ -883,49 +880,12 @@ __global__ void __launch_bounds__(256, CGA_NN_TREE_BLOCKS)
       key = best.key;
     }
     if (active && g == 0) {
-#if CGA_NN_TREE_DEFER
-      __stcs(sg.d2 + j, d2 != ~0ull ? key : ~0ull);
-#else
       __stcs(sg.idx + j, d2 != ~0ull ? stored_index(sg, key) : 0xffffffffu);
       __stcs(sg.d2 + j, d2);
-#endif
     }
   }
 }
 
-#if CGA_NN_TREE_DEFER
-// The answers of the tree search: the key left in the distance output
-// becomes the CGA index (Sec. V-A lookup) and the exact squared distance
-// from the query voxel (all ones in both for no answer).  One thread per
-// query of every segment with a tree.
-__global__ void __launch_bounds__(256) k_nn_tree_index(const NnSeg* __restrict__ segs, int S,
-                                                       NnSeg inline_seg,
-                                                       uint32_t total_slots) {
-  for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < total_slots;
-       slot += gridDim.x * blockDim.x) {
-    const NnSeg& sg = segs != nullptr ? segs[find_nn_seg(segs, S, slot / (uint32_t)kTile)]
-                                      : inline_seg;
-    const uint32_t j = slot - sg.tile_base * (uint32_t)kTile;
-    if (sg.tree.levels == 0 || j >= sg.m) continue;
-    const unsigned long long key = __ldcs(sg.d2 + j);
-    const uint32_t b = sg.a.bits, mk = (1u << b) - 1u;
-    // (a key outside the grid: an output the search never wrote, under a
-    // caller-given order that is not a permutation)
-    if (key == ~0ull || (key >> (3 * b)) != 0ull) {
-      __stcs(sg.idx + j, 0xffffffffu);
-      __stcs(sg.d2 + j, ~0ull);
-      continue;
-    }
-    int qx, qy, qz;
-    query_voxel(sg, j, qx, qy, qz);
-    const unsigned long long dx = absdiff((uint32_t)(key >> (2 * b)), qx),
-                             dy = absdiff((uint32_t)(key >> b) & mk, qy),
-                             dz = absdiff((uint32_t)key & mk, qz);
-    __stcs(sg.idx + j, stored_index(sg, key));
-    __stcs(sg.d2 + j, dx * dx + dy * dy + dz * dz);
-  }
-}
-#endif
 
 // NC: the most coarse levels any segment of the launch carries (0, 1 or 2).
 // The fine-only instantiation is held to 40 registers (six blocks per SM),
@@ -1078,11 +1038,6 @@ static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
     k_nn_tree<CGA_NN_TREE_GROUP><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots,
                                                              order, order_err);
     count_launch(1);
-#if CGA_NN_TREE_DEFER
-    k_nn_tree_index<<<std::min<uint32_t>((total_slots + 255) / 256, sms * 8), 256, 0, stream>>>(
-        d_segs, S, inline_seg, total_slots);
-    count_launch(1);
-#endif
   }
   kinds &= 7u;
   if (kinds == 0) return;
