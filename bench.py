@@ -332,7 +332,9 @@ class LidarStep:
 
 
 def tune_record(shifts, times):
-    """cga_nn_autotune's choice and sample timings for the JSON line."""
+    """cga_nn_autotune's choice and each strategy's measured cost for the JSON
+    line (its preparation plus the sample's search scaled to the step's
+    queries, where the step prepares the world itself)."""
     name = lambda c: "tree" if c == (0xFFFFFFFF,) else (",".join(map(str, c)) if c else "fine")
     return {"chosen": name(tuple(shifts)),
             "sample_ms": {name(c): round(t, 4) for c, t in times.items()}}
@@ -370,9 +372,13 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
     # sweeps (the size buckets of the builds and of each merge level)
     shapes = tune_launch_shapes(
         cga, [torch.cat(P.d_sweeps[:k]) for k in (1, 2, 4, 8) if k <= len(P.d_sweeps)], P.grid)
-    # NN strategy by measurement on a 64k sample of this workload's queries
+    # NN strategy by measurement on a random 64k sample of this workload's
+    # queries; the world is prepared every step for all of them, so each
+    # strategy is charged its preparation plus the search scaled to the step
     P.step(timed_events=False)
-    P.nn_shift, nn_tune = cga.cga_nn_autotune(P.last[2], P.d_q[:65536].contiguous())
+    gen = torch.Generator("cuda").manual_seed(7)
+    sample = P.d_q[torch.randperm(N_QUERIES, device="cuda", generator=gen)[:65536]].contiguous()
+    P.nn_shift, nn_tune = cga.cga_nn_autotune(P.last[2], sample, queries_per_prepare=N_QUERIES)
     for _ in range(args.warmup):
         P.step()
     torch.cuda.synchronize()
@@ -549,11 +555,13 @@ def run_surface(args, world_size, local_rank, torch, dist, cga):
     reps = [P.d_halves[0], torch.cat(P.d_halves)]
     shapes = tune_launch_shapes(cga, reps, P.grid)
     del reps
-    # NN strategy by measurement on a 64k sample mixing both query halves
+    # NN strategy by measurement on a 64k sample mixing both query halves,
+    # each strategy charged its preparation (done every step) plus the search
+    # scaled to the step's queries
     P.step(timed_events=False)
     gen = torch.Generator("cuda").manual_seed(7)
     sample = P.d_q[torch.randperm(S_QUERIES, device="cuda", generator=gen)[:65536]].contiguous()
-    shifts, nn_tune = cga.cga_nn_autotune(P.last[2], sample)
+    shifts, nn_tune = cga.cga_nn_autotune(P.last[2], sample, queries_per_prepare=S_QUERIES)
     P.nn_strategy = shifts
     for _ in range(args.warmup):
         P.step()
@@ -690,7 +698,7 @@ def run_single(args, world_size, local_rank, torch, cga, which):
     step()
     sample = q[torch.randperm(m, device="cuda", generator=torch.Generator("cuda").manual_seed(7))
                [:65536]].contiguous()
-    coarse_shift, nn_tune = cga.cga_nn_autotune(state["last"][2], sample)
+    coarse_shift, nn_tune = cga.cga_nn_autotune(state["last"][2], sample, queries_per_prepare=m)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()

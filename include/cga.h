@@ -203,6 +203,14 @@ int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream);
 int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shifts,
                     float* times_ms, void* stream);
 
+/* cga_nn_autotune for a CGA that is prepared once per m_per_prepare queries
+ * (for instance rebuilt every step and searched by that many): a candidate's
+ * cost is its preparation time plus the sample's search time scaled by
+ * m_per_prepare / m, and times_ms receives that cost.  m_per_prepare == 0 is
+ * cga_nn_autotune (the search alone). */
+int cga_nn_autotune_for(cga_t* a, const float* d_q, uint64_t m, uint64_t m_per_prepare,
+                        uint32_t* chosen_shifts, float* times_ms, void* stream);
+
 /* The two halves of cga_nn_query, for callers that reuse one query order or
  * time the search on its own.  cga_nn_sort_queries writes m 64-bit keys
  * (30-bit Morton code of the query's grid voxel << 32 | query index), sorted

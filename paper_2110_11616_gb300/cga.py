@@ -38,7 +38,7 @@ EXPORTS = (
     "cga_pipeline_view_xy", "cga_pipeline_free", "cga_nn_query_noalloc",
     "cga_server_create", "cga_server_submit", "cga_server_poll", "cga_server_drain",
     "cga_server_free", "cga_now_ns", "cga_nn_sort_queries", "cga_nn_query_ordered",
-    "cga_nn_prepare", "cga_nn_prepare_levels", "cga_nn_autotune",
+    "cga_nn_prepare", "cga_nn_prepare_levels", "cga_nn_autotune", "cga_nn_autotune_for",
     "cga_tuning_set", "cga_tuning_get", "cga_autotune", "cga_pipeline_autotune",
     "cga_build_values", "cga_merge_values", "cga_values", "cga_perspective",
     "cga_radius_count", "cga_radius_fill", "cga_knn",
@@ -694,18 +694,22 @@ def cga_nn_prepare(a: Cga, shifts=(), stream=None):
     return a
 
 
-def cga_nn_autotune(a: Cga, sample_queries, stream=None):
+def cga_nn_autotune(a: Cga, sample_queries, stream=None, queries_per_prepare: int = 0):
     """Measure the NN strategies on a query sample; keep the fastest on `a`.
-    Returns (shifts, {shifts: ms}) with shifts a tuple of coarse shifts."""
+    With queries_per_prepare > 0 (a CGA prepared once per that many queries)
+    a strategy's cost is its preparation time plus the sample's search time
+    scaled to that many queries (cga_nn_autotune_for).  Returns (shifts,
+    {shifts: ms}) with shifts a tuple of coarse shifts."""
     lib = load()
     P = ctypes.c_void_p
-    lib.cga_nn_autotune.argtypes = [P, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32),
-                                    P, P]
+    lib.cga_nn_autotune_for.argtypes = [P, P, ctypes.c_uint64, ctypes.c_uint64,
+                                        ctypes.POINTER(ctypes.c_uint32), P, P]
     _dev_f32(sample_queries, "cga_nn_autotune")
     chosen = (ctypes.c_uint32 * NN_MAX_LEVELS)()
     times = (ctypes.c_float * len(NN_AUTOTUNE_CANDIDATES))()
-    _check(lib.cga_nn_autotune(a.ptr, P(sample_queries.data_ptr()), sample_queries.numel() // 3,
-                               chosen, times, _stream(stream)), "cga_nn_autotune")
+    _check(lib.cga_nn_autotune_for(a.ptr, P(sample_queries.data_ptr()),
+                                   sample_queries.numel() // 3, int(queries_per_prepare),
+                                   chosen, times, _stream(stream)), "cga_nn_autotune")
     shifts = tuple(int(v) for v in chosen if v != 0)
     return shifts, {c: float(t) for c, t in zip(NN_AUTOTUNE_CANDIDATES, times) if t >= 0}
 

@@ -944,8 +944,8 @@ int cga_nn_prepare(cga_t* a, uint32_t shift, void* stream) {
   return cga_nn_prepare_levels(a, &shift, shift == 0 ? 0u : 1u, stream);
 }
 
-int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shifts,
-                    float* times_ms, void* stream) {
+int cga_nn_autotune_for(cga_t* a, const float* d_q, uint64_t m, uint64_t m_per_prepare,
+                        uint32_t* chosen_shifts, float* times_ms, void* stream) {
   if (a == nullptr || a->view || chosen_shifts == nullptr || m == 0 || d_q == nullptr ||
       m > libcga::kNnMaxQueries) {
     return CGA_ERR_INVALID_ARG;
@@ -956,9 +956,9 @@ int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shi
   if (out == nullptr) return CGA_ERR_OOM;
   uint32_t* idx = static_cast<uint32_t*>(out);
   uint64_t* d2 = reinterpret_cast<uint64_t*>(static_cast<char*>(out) + align_up((size_t)m * 4));
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int rc = cuda_rc(cudaEventCreate(&e0));
-  if (rc == CGA_OK) rc = cuda_rc(cudaEventCreate(&e1));
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int rc = CGA_OK;
+  for (int i = 0; i < 4 && rc == CGA_OK; ++i) rc = cuda_rc(cudaEventCreate(&ev[i]));
   // candidates (coarse shifts, 0 = unused): the fine search alone, one coarse
   // level of 4..32 voxel cells, two coarse levels, the occupancy tree
   static const uint32_t cand[CGA_NN_AUTOTUNE_CANDIDATES][CGA_NN_MAX_LEVELS] = {
@@ -972,31 +972,44 @@ int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shi
       if (times_ms) times_ms[k] = -1.0f;
       continue;
     }
-    rc = cga_nn_prepare_levels(a, cand[k], count, stream);
+    rc = cuda_rc(cudaEventRecord(ev[0], s));
+    if (rc == CGA_OK) rc = cga_nn_prepare_levels(a, cand[k], count, stream);
+    if (rc == CGA_OK) rc = cuda_rc(cudaEventRecord(ev[1], s));
     if (rc == CGA_OK) rc = cga_nn_query(a, d_q, m, idx, d2, stream);  // warm-up
-    if (rc == CGA_OK) rc = cuda_rc(cudaEventRecord(e0, s));
+    if (rc == CGA_OK) rc = cuda_rc(cudaEventRecord(ev[2], s));
     if (rc == CGA_OK) rc = cga_nn_query(a, d_q, m, idx, d2, stream);
-    if (rc == CGA_OK) rc = cuda_rc(cudaEventRecord(e1, s));
-    if (rc == CGA_OK) rc = cuda_rc(cudaEventSynchronize(e1));
-    float ms = 0.0f;
-    if (rc == CGA_OK) rc = cuda_rc(cudaEventElapsedTime(&ms, e0, e1));
+    if (rc == CGA_OK) rc = cuda_rc(cudaEventRecord(ev[3], s));
+    if (rc == CGA_OK) rc = cuda_rc(cudaEventSynchronize(ev[3]));
+    float prep = 0.0f, ms = 0.0f;
+    if (rc == CGA_OK) rc = cuda_rc(cudaEventElapsedTime(&prep, ev[0], ev[1]));
+    if (rc == CGA_OK) rc = cuda_rc(cudaEventElapsedTime(&ms, ev[2], ev[3]));
     if (rc != CGA_OK) break;
-    if (times_ms) times_ms[k] = ms;
-    if (!have || ms < best_ms) {
-      best_ms = ms;
+    // the cost per preparation: its own time and the search of the queries
+    // it serves (the sample's time scaled), or the sample's search alone
+    const float cost =
+        m_per_prepare > 0 ? prep + ms * (float)((double)m_per_prepare / (double)m) : ms;
+    if (times_ms) times_ms[k] = cost;
+    if (!have || cost < best_ms) {
+      best_ms = cost;
       best = k;
       have = true;
     }
   }
   const uint32_t best_count = cand[best][0] == 0 ? 0u : (cand[best][1] == 0 ? 1u : 2u);
   if (rc == CGA_OK) rc = cga_nn_prepare_levels(a, cand[best], best_count, stream);
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
+  for (int i = 0; i < 4; ++i) {
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  }
   dfree(A, a->has_alloc, out, s);
   if (rc == CGA_OK) {
     for (int k = 0; k < CGA_NN_MAX_LEVELS; ++k) chosen_shifts[k] = cand[best][k];
   }
   return rc;
+}
+
+int cga_nn_autotune(cga_t* a, const float* d_q, uint64_t m, uint32_t* chosen_shifts,
+                    float* times_ms, void* stream) {
+  return cga_nn_autotune_for(a, d_q, m, 0, chosen_shifts, times_ms, stream);
 }
 
 int cga_nn_sort_queries(const cga_t* a, const float* d_q, uint64_t m, uint64_t* d_order,

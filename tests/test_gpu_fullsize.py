@@ -70,7 +70,7 @@ def test_config_surface_30M(cg, orc):
     # the NN strategy bench.py times: cga_nn_autotune on the same 64k sample
     gen = torch.Generator("cuda").manual_seed(7)
     sample = q[torch.randperm(m, device="cuda", generator=gen)[:65536]].contiguous()
-    chosen, _ = cg.cga_nn_autotune(mg, sample)
+    chosen, _ = cg.cga_nn_autotune(mg, sample, queries_per_prepare=m)
     order = torch.empty(m, dtype=torch.int64, device="cuda")
     idx = torch.empty(m, dtype=torch.int32, device="cuda")
     d2 = torch.empty(m, dtype=torch.int64, device="cuda")

@@ -159,3 +159,9 @@ def test_tree_replaced_by_other_preparations(cg, orc):
     shifts, times = cg.cga_nn_autotune(a, dev(q))
     assert (cg.NN_TREE,) in times and min(times, key=times.get) == shifts
     check(cg, orc, a, oa, og, q, brute=False)
+    # charged with its preparation per 10M queries: every strategy's cost
+    # includes a preparation, the cheapest is kept and answers exactly
+    shifts, times = cg.cga_nn_autotune(a, dev(q), queries_per_prepare=10_000_000)
+    assert (cg.NN_TREE,) in times and min(times, key=times.get) == shifts
+    assert all(t > 0 for t in times.values())
+    check(cg, orc, a, oa, og, q, brute=False)
