@@ -372,13 +372,12 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
     # sweeps (the size buckets of the builds and of each merge level)
     shapes = tune_launch_shapes(
         cga, [torch.cat(P.d_sweeps[:k]) for k in (1, 2, 4, 8) if k <= len(P.d_sweeps)], P.grid)
-    # NN strategy by measurement on a random 64k sample of this workload's
-    # queries; the world is prepared every step for all of them, so each
-    # strategy is charged its preparation plus the search scaled to the step
+    # NN strategy by measurement on this workload's 1M queries themselves (a
+    # sparser sample changes how neighbouring queries share a warp's loads and
+    # misjudges the window search); the world is prepared every step, so each
+    # strategy is charged its preparation plus the search
     P.step(timed_events=False)
-    gen = torch.Generator("cuda").manual_seed(7)
-    sample = P.d_q[torch.randperm(N_QUERIES, device="cuda", generator=gen)[:65536]].contiguous()
-    P.nn_shift, nn_tune = cga.cga_nn_autotune(P.last[2], sample, queries_per_prepare=N_QUERIES)
+    P.nn_shift, nn_tune = cga.cga_nn_autotune(P.last[2], P.d_q, queries_per_prepare=N_QUERIES)
     for _ in range(args.warmup):
         P.step()
     torch.cuda.synchronize()

@@ -241,13 +241,21 @@ __global__ void __launch_bounds__(TH, TH == 512 ? CGA_SORT_BLOCKS_512 : CGA_SORT
     k[i] = v ? src[e] : (K)0;
     dg[i] = v ? ((uint32_t)(k[i] >> shift) & (R - 1)) : 0xffffffffu;
   }
-  // warp-level ranking: lanes holding the same digit form one match group
+  // warp-level ranking: lanes holding the same digit form one peer group
   uint16_t* wh = s_wh[w];
   const uint32_t ltm = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < IT; ++i) {
     const uint32_t d = dg[i];
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    // lanes with the same digit: one warp vote per digit bit and one for
+    // validity (votes issue faster than a match over the digit)
+    uint32_t peers = __ballot_sync(0xffffffffu, d < (uint32_t)R);
+    if (d >= (uint32_t)R) peers = ~peers;
+#pragma unroll
+    for (int bit = 0; bit < RB; ++bit) {
+      const uint32_t v = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+      peers &= ((d >> bit) & 1u) ? v : ~v;
+    }
     const uint32_t base = (d < (uint32_t)R) ? wh[d] : 0u;
     __syncwarp();
     if (d < (uint32_t)R && lane == __ffs(peers) - 1) wh[d] = (uint16_t)(base + __popc(peers));

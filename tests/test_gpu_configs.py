@@ -118,15 +118,12 @@ def test_config_lidar_frames(cg, orc):
     assert_2d(cg.cga_project(gw, "xy"), orc.project(ow, "xy"), "xy")
     # all 1M answers against the oracle (threads over query chunks), for the
     # fine search, the occupancy tree and the strategy cga_nn_autotune picks
-    # on the benchmark's random 64k sample with the preparation charged per
-    # 1M queries (the launch configuration bench.py times)
+    # on all the queries with the preparation charged per step (the launch
+    # configuration bench.py times)
     oi, od = oracle_threads.nn_window(orc, ow, og, q)
     for prep in [(), "tree", "autotune"]:
         if prep == "autotune":
-            dq = dev(q)
-            gen = torch.Generator("cuda").manual_seed(7)
-            sample = dq[torch.randperm(len(q), device="cuda", generator=gen)[:65536]].contiguous()
-            cg.cga_nn_autotune(gw, sample, queries_per_prepare=len(q))
+            cg.cga_nn_autotune(gw, dev(q), queries_per_prepare=len(q))
         else:
             cg.cga_nn_prepare(gw, prep)
         idx, d2 = cg.cga_nn_query(gw, dev(q))
