@@ -1,5 +1,6 @@
 // Operations on built CGAs: decode, merge, xy projection, exact NN search.
 #include <algorithm>
+#include <atomic>
 
 #include "k_compact.cuh"
 
@@ -194,10 +195,10 @@ constexpr int merge_stage() { return MH == 2048 ? 1536 : 6144; }
 
 // Merge one tile of at most MH columns of each input (one splitter spacing).
 template <int MH>
-__global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __restrict__ pairs,
-                                                          int S, const uint32_t* __restrict__ bounds,
-                                                          const uint32_t* __restrict__ ntiles,
-                                                          uint32_t* clook, uint32_t* counter) {
+__device__ __forceinline__ void merge_tile(const MergePair* __restrict__ pairs, int S,
+                                           const uint32_t* __restrict__ bounds,
+                                           const uint32_t* __restrict__ ntiles, uint32_t* clook,
+                                           uint32_t t, int p) {
   constexpr int IT = 2 * MH / kThreads;  // merged columns per thread
   static_assert(IT * kThreads == 2 * MH && MH % kThreads == 0, "merge tile shape");
   // column keys of A and B; merged keys and sources; staged z entries
@@ -205,18 +206,10 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
   __shared__ uint32_t s_ka[MH], s_kb[MH], s_mk[2 * MH];
   __shared__ uint16_t s_ms[2 * MH];
   __shared__ uint16_t s_za[ZS], s_zb[ZS];
+  __shared__ uint32_t s_pa[MH + 1], s_pb[MH + 1];  // the tile's Y_pointer entries
   __shared__ unsigned long long s_warp64[kWarps];
-  __shared__ uint32_t s_tile, s_tot[6], s_prevx, s_hasprev;
-  __shared__ int s_p;
+  __shared__ uint32_t s_tot[6], s_prevx, s_hasprev;
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    const uint32_t t = atomicAdd(counter, 1u);
-    s_tile = t;
-    s_p = find_pair_tile(pairs, S, t);
-  }
-  __syncthreads();
-  const uint32_t t = s_tile;
-  const int p = s_p;
   const MergePair& P = pairs[p];
   const uint32_t lt = t - P.tile_base;
   const uint32_t nt = ntiles[p];
@@ -276,6 +269,10 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
   }
   const uint16_t* zAb = stA ? s_za - zA0 : A.idx0;  // z entry i of A at zAb[i]
   const uint16_t* zBb = stB ? s_zb - zB0 : B.idx0;
+  // Y_pointer of the tile's columns (and the one after), column i of A at
+  // pA[i] (i relative to a0)
+  for (uint32_t e = tid; e <= na; e += kThreads) s_pa[e] = na ? __ldg(A.ptr1 + a0 + e) : 0u;
+  for (uint32_t e = tid; e <= nb; e += kThreads) s_pb[e] = nb ? __ldg(B.ptr1 + b0 + e) : 0u;
   __syncthreads();
   // merge path (A first on equal keys); sources: A's column i as i, B's
   // column j as MH + j
@@ -315,14 +312,13 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
     const bool pair = ps + 1 < n && s_mk[ps + 1] == key;
     uint32_t c;
     if (pair) {
-      const uint32_t ca = a0 + src, cb = b0 + (s_ms[ps + 1] - MH);
-      const uint32_t za = __ldg(A.ptr1 + ca), zb = __ldg(B.ptr1 + cb);
-      c = union_count(zAb + za, __ldg(A.ptr1 + ca + 1) - za, zBb + zb,
-                      __ldg(B.ptr1 + cb + 1) - zb);
+      const uint32_t ia = src, ib = s_ms[ps + 1] - MH;
+      const uint32_t za = s_pa[ia], zb = s_pb[ib];
+      c = union_count(zAb + za, s_pa[ia + 1] - za, zBb + zb, s_pb[ib + 1] - zb);
     } else if (src < MH) {
-      c = __ldg(A.ptr1 + a0 + src + 1) - __ldg(A.ptr1 + a0 + src);
+      c = s_pa[src + 1] - s_pa[src];
     } else {
-      c = __ldg(B.ptr1 + b0 + src - MH + 1) - __ldg(B.ptr1 + b0 + src - MH);
+      c = s_pb[src - MH + 1] - s_pb[src - MH];
     }
     cnt[it] = c;
     const uint32_t x = key >> b;
@@ -372,14 +368,12 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
     O.idx1[co] = (uint16_t)(key & ymask);
     O.ptr1[co] = vo;
     if (pair) {
-      const uint32_t ca = a0 + src, cb = b0 + (s_ms[ps + 1] - MH);
-      const uint32_t za = __ldg(A.ptr1 + ca), zb = __ldg(B.ptr1 + cb);
-      union_write(zAb + za, __ldg(A.ptr1 + ca + 1) - za, zBb + zb,
-                  __ldg(B.ptr1 + cb + 1) - zb, O.idx0 + vo);
+      const uint32_t ia = src, ib = s_ms[ps + 1] - MH;
+      const uint32_t za = s_pa[ia], zb = s_pb[ib];
+      union_write(zAb + za, s_pa[ia + 1] - za, zBb + zb, s_pb[ib + 1] - zb, O.idx0 + vo);
     } else {
       const bool fromA = src < MH;
-      const uint32_t col = fromA ? a0 + src : b0 + src - MH;
-      const uint16_t* zz = (fromA ? zAb : zBb) + __ldg((fromA ? A.ptr1 : B.ptr1) + col);
+      const uint16_t* zz = fromA ? zAb + s_pa[src] : zBb + s_pb[src - MH];
       for (uint32_t q = 0; q < c; ++q) O.idx0[vo + q] = zz[q];
     }
     const uint32_t x = key >> b;
@@ -404,6 +398,32 @@ __global__ void __launch_bounds__(kThreads) k_merge_tiles(const MergePair* __res
     O.hdr->cnt[0] = U;
     O.hdr->cnt[1] = G;
     O.hdr->cnt[2] = H;
+  }
+}
+
+// Merge tiles by the resident blocks: each takes tile ids from the counter in
+// launch order until the reserved tiles are handed out (tiles beyond a
+// pair's actual count are skipped), so the look-back always finds its
+// predecessors running or done.
+template <int MH>
+__global__ void __launch_bounds__(kThreads, 4) k_merge_tiles(const MergePair* __restrict__ pairs,
+                                                          int S, const uint32_t* __restrict__ bounds,
+                                                          const uint32_t* __restrict__ ntiles,
+                                                          uint32_t* clook, uint32_t* counter,
+                                                          uint32_t total_tiles) {
+  __shared__ uint32_t s_tile;
+  __shared__ int s_p;
+  for (;;) {
+    __syncthreads();  // the previous tile's shared data is read no more
+    if (threadIdx.x == 0) {
+      const uint32_t t = atomicAdd(counter, 1u);
+      s_tile = t;
+      s_p = t < total_tiles ? find_pair_tile(pairs, S, t) : 0;
+    }
+    __syncthreads();
+    const uint32_t t = s_tile;
+    if (t >= total_tiles) return;
+    merge_tile<MH>(pairs, S, bounds, ntiles, clook, t, s_p);
   }
 }
 
@@ -483,10 +503,10 @@ __global__ void k_kmerge_cuts(const MergePair* __restrict__ pairs, int S, uint32
 // memory, merge-path split per thread, sequential merge, then the shared
 // dedupe + compaction.
 template <int MH>
-__global__ void __launch_bounds__(kThreads) k_kmerge_tiles(const MergePair* __restrict__ pairs,
-                                                          int S, const uint32_t* __restrict__ bounds,
-                                                          const uint32_t* __restrict__ ntiles,
-                                                          uint32_t* clook, uint32_t* counter) {
+__device__ __forceinline__ void kmerge_tile(const MergePair* __restrict__ pairs, int S,
+                                            const uint32_t* __restrict__ bounds,
+                                            const uint32_t* __restrict__ ntiles, uint32_t* clook,
+                                            uint32_t t, int p) {
   constexpr int IT = 2 * MH / kThreads;  // merged keys per thread
   static_assert(IT * kThreads == 2 * MH && 2 * MH <= kTile, "merge tile shape");
   __shared__ unsigned long long s_ab[2 * MH];
@@ -495,17 +515,8 @@ __global__ void __launch_bounds__(kThreads) k_kmerge_tiles(const MergePair* __re
   __shared__ CompactSmem sm;
   __shared__ Window s_wa, s_wb;
   __shared__ unsigned long long s_prev, s_prev2[2];
-  __shared__ uint32_t s_tile, s_has_prev;
-  __shared__ int s_p;
+  __shared__ uint32_t s_has_prev;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (tid == 0) {
-    const uint32_t t = atomicAdd(counter, 1u);
-    s_tile = t;
-    s_p = find_pair_tile(pairs, S, t);
-  }
-  __syncthreads();
-  const uint32_t t = s_tile;
-  const int p = s_p;
   const MergePair& P = pairs[p];
   const uint32_t lt = t - P.tile_base;
   const uint32_t nt = ntiles[p];
@@ -606,6 +617,29 @@ __global__ void __launch_bounds__(kThreads) k_kmerge_tiles(const MergePair* __re
   }
   compact_tile<3, unsigned long long>(k, cnt, s_has_prev != 0, s_prev, t, P.tile_base,
                                       lt == nt - 1, P.out, clook, sm);
+}
+
+// Key-level merge tiles by the resident blocks (as k_merge_tiles).
+template <int MH>
+__global__ void __launch_bounds__(kThreads, 4) k_kmerge_tiles(const MergePair* __restrict__ pairs,
+                                                           int S, const uint32_t* __restrict__ bounds,
+                                                           const uint32_t* __restrict__ ntiles,
+                                                           uint32_t* clook, uint32_t* counter,
+                                                           uint32_t total_tiles) {
+  __shared__ uint32_t s_tile;
+  __shared__ int s_p;
+  for (;;) {
+    __syncthreads();  // the previous tile's shared data is read no more
+    if (threadIdx.x == 0) {
+      const uint32_t t = atomicAdd(counter, 1u);
+      s_tile = t;
+      s_p = t < total_tiles ? find_pair_tile(pairs, S, t) : 0;
+    }
+    __syncthreads();
+    const uint32_t t = s_tile;
+    if (t >= total_tiles) return;
+    kmerge_tile<MH>(pairs, S, bounds, ntiles, clook, t, s_p);
+  }
 }
 
 // ------------------------------------------------------- coarse slab index
@@ -731,12 +765,29 @@ MergeScratch merge_scratch_carve(void* base, uint32_t total_spl, uint32_t total_
   return sc;
 }
 
+// Resident blocks of a merge tile kernel on the device (queried once per
+// kernel), the grid of its persistent launch.
+template <typename F>
+static uint32_t merge_grid(F* kernel, std::atomic<int>& cache, uint32_t total_tiles) {
+  int n = cache.load(std::memory_order_relaxed);
+  if (n == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kThreads, 0) != cudaSuccess ||
+        n <= 0) {
+      cudaGetLastError();
+      n = 2;
+    }
+    cache.store(n, std::memory_order_relaxed);
+  }
+  return std::max<uint32_t>(1u, std::min<uint32_t>(total_tiles, (uint32_t)(n * device_sm_count())));
+}
+
 cudaError_t run_merge_device(int S, uint32_t total_spl, uint32_t total_tiles,
                              const MergeScratch& sc, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(sc.clook, 0, sc.zero_bytes, stream);
   if (e != cudaSuccess) return e;
   if (sc.half != 512 && sc.half != 1024 && sc.half != 2048) return cudaErrorInvalidValue;
   count_launch(total_spl > 0 ? 3 : 2);
+  static std::atomic<int> occ[6] = {{0}, {0}, {0}, {0}, {0}, {0}};
   if (sc.key_level) {
     k_kmerge_init<<<(S + 127) / 128, 128, 0, stream>>>(sc.pairs, S, sc.half, sc.bounds, sc.ntiles);
     if (total_spl > 0) {
@@ -744,14 +795,17 @@ cudaError_t run_merge_device(int S, uint32_t total_spl, uint32_t total_tiles,
                                                             sc.bounds);
     }
     if (sc.half == 512) {
-      k_kmerge_tiles<512><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles,
-                                                                sc.clook, sc.counter);
+      k_kmerge_tiles<512><<<merge_grid(k_kmerge_tiles<512>, occ[0], total_tiles), kThreads, 0,
+                            stream>>>(sc.pairs, S, sc.bounds, sc.ntiles, sc.clook, sc.counter,
+                                      total_tiles);
     } else if (sc.half == 1024) {
-      k_kmerge_tiles<1024><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds,
-                                                                 sc.ntiles, sc.clook, sc.counter);
+      k_kmerge_tiles<1024><<<merge_grid(k_kmerge_tiles<1024>, occ[1], total_tiles), kThreads, 0,
+                             stream>>>(sc.pairs, S, sc.bounds, sc.ntiles, sc.clook, sc.counter,
+                                       total_tiles);
     } else {
-      k_kmerge_tiles<2048><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds,
-                                                                 sc.ntiles, sc.clook, sc.counter);
+      k_kmerge_tiles<2048><<<merge_grid(k_kmerge_tiles<2048>, occ[2], total_tiles), kThreads, 0,
+                             stream>>>(sc.pairs, S, sc.bounds, sc.ntiles, sc.clook, sc.counter,
+                                       total_tiles);
     }
     return cudaGetLastError();
   }
@@ -761,14 +815,17 @@ cudaError_t run_merge_device(int S, uint32_t total_spl, uint32_t total_tiles,
                                                          sc.bounds);
   }
   if (sc.half == 512) {
-    k_merge_tiles<512><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles,
-                                                             sc.clook, sc.counter);
+    k_merge_tiles<512><<<merge_grid(k_merge_tiles<512>, occ[3], total_tiles), kThreads, 0,
+                         stream>>>(sc.pairs, S, sc.bounds, sc.ntiles, sc.clook, sc.counter,
+                                   total_tiles);
   } else if (sc.half == 1024) {
-    k_merge_tiles<1024><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles,
-                                                              sc.clook, sc.counter);
+    k_merge_tiles<1024><<<merge_grid(k_merge_tiles<1024>, occ[4], total_tiles), kThreads, 0,
+                          stream>>>(sc.pairs, S, sc.bounds, sc.ntiles, sc.clook, sc.counter,
+                                    total_tiles);
   } else {
-    k_merge_tiles<2048><<<total_tiles, kThreads, 0, stream>>>(sc.pairs, S, sc.bounds, sc.ntiles,
-                                                              sc.clook, sc.counter);
+    k_merge_tiles<2048><<<merge_grid(k_merge_tiles<2048>, occ[5], total_tiles), kThreads, 0,
+                          stream>>>(sc.pairs, S, sc.bounds, sc.ntiles, sc.clook, sc.counter,
+                                    total_tiles);
   }
   return cudaGetLastError();
 }
