@@ -596,9 +596,11 @@ def run_surface(args, world_size, local_rank, torch, dist, cga):
     value = job_value(S_POINTS, args.steps, world_size, max_total)
     e2e_val = S_POINTS * world_size / (float(np.mean(e2e_ms)) / 1e3) / 1e6
     peak, peak_kind = measured_peaks()
-    # dominant kernel: the NN search (one launch of k_nn_tree per step under the
-    # tree, timed live between events 4 and 5).  Algorithmic bytes per launch
-    # (compulsory): 12 B query read + 4 B index + 8 B distance written per query.
+    # dominant kernel: the NN search under the tree (k_nn_tree, two launches
+    # per step: every 32nd query in Morton order, then the rest seeded by
+    # them), timed live as one region between events 4 and 5.  Algorithmic
+    # bytes per search (compulsory): 12 B query read + 4 B index + 8 B
+    # distance written per query.
     search_ms = op[4]
     algo = S_QUERIES * (12 + 4 + 8)
     achieved = algo / (search_ms / 1e3) / 1e9
@@ -634,9 +636,10 @@ def run_surface(args, world_size, local_rank, torch, dist, cga):
                      "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                      "algorithmic_bytes_per_launch": algo,
                      "note": "compulsory bytes: 12 B query in + 12 B result out per query over "
-                             "the live CUDA-event time of the search launch; the search is "
-                             "bound by dependent L1/L2 loads and instruction issue, not HBM. "
-                             "traffic: ncu dram read+write per launch "
+                             "the live CUDA-event time of the search (both launches of the "
+                             "tree search); the search is bound by integer instruction issue "
+                             "and L1/L2 latency, not HBM. traffic: ncu dram read+write of the "
+                             "search's launches "
                              + (f"({traffic_note})" if traffic_note else "")},
         "e2e": {"value": round(e2e_val, 3), "unit": "Mpts/s",
                 "h2d_bytes_per_step": P.bytes_in(), "d2h_bytes_per_step": P.bytes_out()},

@@ -753,9 +753,9 @@ struct TreeWalk {
     tree_cell(cs, cx, cy, cz);
     const uint32_t nx = OX + cx, ny = OY + cy, nz = OZ + cz;
     if (bricks) {
-      if (best.d2 == (D)~(D)0) {
-        // no candidate yet: the nearest brick alone; the next step bounds
-        // the node's other bricks against the distance it gives
+      if (best.key == ~0ull) {
+        // no stored voxel found yet: the nearest brick alone; the next step
+        // bounds the node's other bricks against the distance it gives
         group_brick<G, D>(gm, g, __ldg(tv.brick + csi), nx << 2, ny << 2, nz << 2, q, b, best);
         return;
       }
@@ -802,45 +802,91 @@ __device__ __forceinline__ uint32_t stored_index(const NnSeg& sg, unsigned long 
   return lower_bound_u16(a.idx0, __ldg(a.ptr1 + c), __ldg(a.ptr1 + c + 1), z);
 }
 
+// The whole descent.  The loop runs while any group of the warp is still
+// searching (a warp vote each step), so the warp's lanes re-converge at
+// every step.  `best` may start from an upper bound without a voxel (key all
+// ones): every voxel at or below the bound is still examined.
 template <int G, typename D>
 __device__ void search_tree(const TreeView& tv, const Qry& q, uint32_t b, bool active,
-                                   uint32_t gm, uint32_t g, BestKey<D>& best) {
-  if (tv.levels == 1) {
-    if (active) group_brick<G, D>(gm, g, __ldg(tv.brick), 0u, 0u, 0u, q, b, best);
-    return;
-  }
+                            uint32_t gm, uint32_t g, BestKey<D>& best) {
   TreeWalk<G, D> w;
-  w.done = !active;
+  w.done = true;
   if (active) {
-    w.lvl = tv.levels;
-    w.ox = w.oy = w.oz = 0;
-    w.depth = 0;
-    w.enter(__ldg(tv.node[tv.levels]), g);
+    if (tv.levels == 1) {
+      group_brick<G, D>(gm, g, __ldg(tv.brick), 0u, 0u, 0u, q, b, best);
+    } else {
+      w.lvl = tv.levels;
+      w.ox = w.oy = w.oz = 0;
+      w.depth = 0;
+      w.done = false;
+      w.enter(__ldg(tv.node[tv.levels]), g);
+    }
   }
   while (__any_sync(0xffffffffu, !w.done)) {
     if (!w.done) w.step(tv, q, b, gm, g, best);
   }
 }
 
+// Slots of the Morton order taken by one pass of a sorted search: every
+// stride-th slot that is not a multiple of `parent` (parent 0: every
+// stride-th slot).  The passes of a sorted search run with strides
+// CGA_NN_SEED_TOP, CGA_NN_SEED_MID (if not 0) and 1, each seeded from the
+// slots of the one before.
+#ifndef CGA_NN_SEED_TOP
+#define CGA_NN_SEED_TOP 32
+#endif
+#ifndef CGA_NN_SEED_MID
+#define CGA_NN_SEED_MID 0
+#endif
+static_assert(kTile % CGA_NN_SEED_TOP == 0 && CGA_NN_SEED_TOP % (CGA_NN_SEED_MID ? CGA_NN_SEED_MID : 1) == 0,
+              "seed groups nest and lie in one tile");
+
+__device__ __forceinline__ uint32_t pass_count(uint32_t total, uint32_t stride, uint32_t parent) {
+  return parent == 0 ? total / stride : total / stride - total / parent;
+}
+
+__device__ __forceinline__ uint32_t pass_slot(uint32_t i, uint32_t stride, uint32_t parent) {
+  if (parent == 0) return i * stride;
+  const uint32_t r = parent / stride - 1;  // slots of the pass per parent group
+  return (i / r) * parent + (i % r + 1) * stride;
+}
+
+// Upper bound on the squared distance from query voxel q to the answer of
+// query voxel q0 (squared distance d0 from q0): (sqrt(d0) + |q - q0|)^2 by the
+// triangle inequality, rounded up with margin; all ones when it does not fit.
+__device__ __forceinline__ unsigned long long seed_bound(unsigned long long d0, int qx, int qy,
+                                                         int qz, int px, int py, int pz) {
+  const double dx = (double)qx - px, dy = (double)qy - py, dz = (double)qz - pz;
+  const double r = sqrt((double)d0) + sqrt(dx * dx + dy * dy + dz * dz);
+  const double bnd = r * r * (1.0 + 1e-9) + 4.0;
+  return bnd < 1.8e19 ? (unsigned long long)bnd : ~0ull;
+}
+
 // G lanes per query slot over every segment with a tree (a segment without
-// one is left to k_nn_warp).  A warp takes 32 / G consecutive slots at a time
-// (neighbouring queries in Morton order) and moves on when all are answered;
-// the loop is warp-uniform, so that the descent's warp votes see every lane.
+// one is left to k_nn_warp).  A warp takes 32 / G consecutive slots of the
+// pass at a time (neighbouring queries in Morton order) and moves on when all
+// are answered; the loop is warp-uniform, so that the descent's warp votes
+// see every lane.  The pass takes the slots pass_slot gives; with parent > 0
+// each search starts from the bound that the answer of the slot's parent
+// group head (found by an earlier pass) gives: a bound without a voxel, so
+// the result is the same.
 template <int G>
 __global__ void __launch_bounds__(256, CGA_NN_TREE_BLOCKS)
     k_nn_tree(const NnSeg* __restrict__ segs, int S, NnSeg inline_seg, uint32_t total_slots,
-                     const unsigned long long* __restrict__ order,
-                     const unsigned int* __restrict__ order_err) {
+              const unsigned long long* __restrict__ order,
+              const unsigned int* __restrict__ order_err, uint32_t stride, uint32_t parent) {
   constexpr uint32_t QW = 32 / G;
   const bool sorted = order != nullptr && (order_err == nullptr || *order_err == 0u);
   const uint32_t lane = threadIdx.x & 31, g = lane % G;
   const uint32_t gm = G == 32 ? 0xffffffffu : (uint32_t)((1ull << G) - 1ull) << (lane - g);
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * QW; base < total_slots;
+  const uint32_t n_pass = pass_count(total_slots, stride, parent);
+  for (uint32_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * QW; base < n_pass;
        base += nwarps * QW) {
-    const uint32_t slot = base + lane / G;
-    bool active = slot < total_slots;
-    const NnSeg& sg = segs != nullptr ? segs[find_nn_seg(segs, S, base / (uint32_t)kTile)]
+    const uint32_t i = base + lane / G;
+    bool active = i < n_pass;
+    const uint32_t slot = pass_slot(active ? i : base, stride, parent);
+    const NnSeg& sg = segs != nullptr ? segs[find_nn_seg(segs, S, slot / (uint32_t)kTile)]
                                       : inline_seg;
     const uint32_t local = slot - sg.tile_base * (uint32_t)kTile;
     active = active && sg.tree.levels > 0 && local < sg.m;
@@ -857,6 +903,19 @@ __global__ void __launch_bounds__(256, CGA_NN_TREE_BLOCKS)
         active = false;
       }
     }
+    // the seed: the answer of the parent group's first slot
+    unsigned long long seed = ~0ull;
+    if (parent != 0 && active) {
+      const uint32_t s0 = slot - slot % parent, l0 = s0 - sg.tile_base * (uint32_t)kTile;
+      const uint32_t j0 = l0 < sg.m ? (sorted ? (uint32_t)__ldg(order + s0) : l0) : 0xffffffffu;
+      if (j0 < sg.m) {
+        const unsigned long long d0 = __ldg(sg.d2 + j0);
+        int px, py, pz;
+        if (d0 != ~0ull && query_voxel(sg, j0, px, py, pz)) {
+          seed = seed_bound(d0, qx, qy, qz, px, py, pz);
+        }
+      }
+    }
     const uint32_t b = sg.a.bits;
     const int top = (1 << b) - 1;
     const uint32_t cqx = (uint32_t)min(max(qx, 0), top);
@@ -867,17 +926,31 @@ __global__ void __launch_bounds__(256, CGA_NN_TREE_BLOCKS)
     const bool narrow = b <= 15 && (uint32_t)qx == cqx && (uint32_t)qy == cqy &&
                         (uint32_t)qz == cqz;
     if (__all_sync(0xffffffffu, narrow || !active)) {
-      BestKey<uint32_t> best{0xffffffffu, ~0ull};
+      BestKey<uint32_t> best{seed < 0xffffffffull ? (uint32_t)seed : 0xffffffffu, ~0ull};
       search_tree<G, uint32_t>(sg.tree, qq, b, active, gm, g, best);
-      if (best.d2 != 0xffffffffu) {
+      // (a seeded search always meets the group's first answer; searched
+      // again without the seed should it not)
+      const bool again = active && best.key == ~0ull && seed != ~0ull;
+      if (__any_sync(0xffffffffu, again)) {
+        if (again) best = BestKey<uint32_t>{0xffffffffu, ~0ull};
+        search_tree<G, uint32_t>(sg.tree, qq, b, again, gm, g, best);
+      }
+      if (best.key != ~0ull) {
         d2 = best.d2;
         key = best.key;
       }
     } else {
-      BestKey<unsigned long long> best{~0ull, ~0ull};
+      BestKey<unsigned long long> best{seed, ~0ull};
       search_tree<G, unsigned long long>(sg.tree, qq, b, active, gm, g, best);
-      d2 = best.d2;
-      key = best.key;
+      const bool again = active && best.key == ~0ull && seed != ~0ull;
+      if (__any_sync(0xffffffffu, again)) {
+        if (again) best = BestKey<unsigned long long>{~0ull, ~0ull};
+        search_tree<G, unsigned long long>(sg.tree, qq, b, again, gm, g, best);
+      }
+      if (best.key != ~0ull) {
+        d2 = best.d2;
+        key = best.key;
+      }
     }
     if (active && g == 0) {
       __stcs(sg.idx + j, d2 != ~0ull ? stored_index(sg, key) : 0xffffffffu);
@@ -885,7 +958,6 @@ __global__ void __launch_bounds__(256, CGA_NN_TREE_BLOCKS)
     }
   }
 }
-
 
 // NC: the most coarse levels any segment of the launch carries (0, 1 or 2).
 // The fine-only instantiation is held to 40 registers (six blocks per SM),
@@ -1032,12 +1104,35 @@ static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
   const uint32_t total_slots = total_tiles * (uint32_t)kTile;
   const uint32_t sms = (uint32_t)device_sm_count();
   if (kinds & 8u) {
+    // in Morton order: every CGA_NN_SEED_TOP-th query, then (seeded by those)
+    // every CGA_NN_SEED_MID-th, then the rest; in query order one pass
+    // (neighbouring slots are not close queries)
     constexpr uint32_t qpb = 256 / CGA_NN_TREE_GROUP;  // queries per block and round
-    const uint32_t blocks = std::min<uint32_t>((total_slots + qpb - 1) / qpb,
-                                               sms * resident_blocks(3));
-    k_nn_tree<CGA_NN_TREE_GROUP><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg, total_slots,
-                                                             order, order_err);
-    count_launch(1);
+    const uint32_t cap_blocks = sms * resident_blocks(3);
+    uint32_t pstride[3], pparent[3];
+    int np = 0;
+    if (order != nullptr) {
+      pstride[np] = CGA_NN_SEED_TOP;
+      pparent[np++] = 0;
+      if (CGA_NN_SEED_MID > 1) {
+        pstride[np] = CGA_NN_SEED_MID;
+        pparent[np++] = CGA_NN_SEED_TOP;
+      }
+      pstride[np] = 1;
+      pparent[np++] = CGA_NN_SEED_MID > 1 ? CGA_NN_SEED_MID : CGA_NN_SEED_TOP;
+    } else {
+      pstride[np] = 1;
+      pparent[np++] = 0;
+    }
+    for (int k = 0; k < np; ++k) {
+      const uint32_t n = pparent[k] == 0 ? total_slots / pstride[k]
+                                         : total_slots / pstride[k] - total_slots / pparent[k];
+      const uint32_t blocks = std::min<uint32_t>((n + qpb - 1) / qpb, cap_blocks);
+      k_nn_tree<CGA_NN_TREE_GROUP><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg,
+                                                               total_slots, order, order_err,
+                                                               pstride[k], pparent[k]);
+      count_launch(1);
+    }
   }
   kinds &= 7u;
   if (kinds == 0) return;
