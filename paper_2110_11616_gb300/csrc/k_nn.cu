@@ -903,16 +903,21 @@ __global__ void __launch_bounds__(256, CGA_NN_TREE_BLOCKS)
         active = false;
       }
     }
-    // the seed: the answer of the parent group's first slot
+    // the seed: the tighter of the bounds that the answers of the slot's
+    // own group head and of the next group's head give
     unsigned long long seed = ~0ull;
     if (parent != 0 && active) {
-      const uint32_t s0 = slot - slot % parent, l0 = s0 - sg.tile_base * (uint32_t)kTile;
-      const uint32_t j0 = l0 < sg.m ? (sorted ? (uint32_t)__ldg(order + s0) : l0) : 0xffffffffu;
-      if (j0 < sg.m) {
+      const uint32_t h0 = slot - slot % parent;
+#pragma unroll
+      for (uint32_t e = 0; e < 2; ++e) {
+        const uint32_t s0 = h0 + e * parent, l0 = s0 - sg.tile_base * (uint32_t)kTile;
+        if (l0 >= sg.m) continue;  // (beyond the segment's queries)
+        const uint32_t j0 = sorted ? (uint32_t)__ldg(order + s0) : l0;
+        if (j0 >= sg.m) continue;
         const unsigned long long d0 = __ldg(sg.d2 + j0);
         int px, py, pz;
         if (d0 != ~0ull && query_voxel(sg, j0, px, py, pz)) {
-          seed = seed_bound(d0, qx, qy, qz, px, py, pz);
+          seed = min(seed, seed_bound(d0, qx, qy, qz, px, py, pz));
         }
       }
     }
