@@ -853,13 +853,40 @@ __device__ __forceinline__ uint32_t pass_slot(uint32_t i, uint32_t stride, uint3
 
 // Upper bound on the squared distance from query voxel q to the answer of
 // query voxel q0 (squared distance d0 from q0): (sqrt(d0) + |q - q0|)^2 by the
-// triangle inequality, rounded up with margin; all ones when it does not fit.
+// triangle inequality, in single precision (correctly rounded square roots,
+// each step off by at most a few units in the last place) enlarged by a
+// relative 1e-4 and 16 so that it stays above the exact value; all ones when
+// it does not fit.
 __device__ __forceinline__ unsigned long long seed_bound(unsigned long long d0, int qx, int qy,
                                                          int qz, int px, int py, int pz) {
-  const double dx = (double)qx - px, dy = (double)qy - py, dz = (double)qz - pz;
-  const double r = sqrt((double)d0) + sqrt(dx * dx + dy * dy + dz * dz);
-  const double bnd = r * r * (1.0 + 1e-9) + 4.0;
-  return bnd < 1.8e19 ? (unsigned long long)bnd : ~0ull;
+  const float dx = (float)qx - (float)px, dy = (float)qy - (float)py, dz = (float)qz - (float)pz;
+  const float r = (__fsqrt_ru((float)d0) + __fsqrt_ru(dx * dx + dy * dy + dz * dz)) * 1.0001f;
+  const float bnd = r * r + 16.0f;
+  return bnd < 1.8e19f ? (unsigned long long)bnd : ~0ull;
+}
+
+// The seed of slot `slot` (query voxel q) in a pass with seed groups of
+// `parent` slots: the tighter of the bounds that the answers of the slot's
+// own group head and of the next group's head give (all ones: none).
+__device__ __forceinline__ unsigned long long seed_of(const NnSeg& sg, uint32_t slot,
+                                                      uint32_t parent, bool sorted,
+                                                      const unsigned long long* order, int qx,
+                                                      int qy, int qz) {
+  unsigned long long seed = ~0ull;
+  const uint32_t h0 = slot - slot % parent;
+#pragma unroll
+  for (uint32_t e = 0; e < 2; ++e) {
+    const uint32_t s0 = h0 + e * parent, l0 = s0 - sg.tile_base * (uint32_t)kTile;
+    if (l0 >= sg.m) continue;  // (beyond the segment's queries)
+    const uint32_t j0 = sorted ? (uint32_t)__ldg(order + s0) : l0;
+    if (j0 >= sg.m) continue;
+    const unsigned long long d0 = __ldg(sg.d2 + j0);
+    int px, py, pz;
+    if (d0 != ~0ull && query_voxel(sg, j0, px, py, pz)) {
+      seed = min(seed, seed_bound(d0, qx, qy, qz, px, py, pz));
+    }
+  }
+  return seed;
 }
 
 // G lanes per query slot over every segment with a tree (a segment without
@@ -903,24 +930,8 @@ __global__ void __launch_bounds__(256, CGA_NN_TREE_BLOCKS)
         active = false;
       }
     }
-    // the seed: the tighter of the bounds that the answers of the slot's
-    // own group head and of the next group's head give
-    unsigned long long seed = ~0ull;
-    if (parent != 0 && active) {
-      const uint32_t h0 = slot - slot % parent;
-#pragma unroll
-      for (uint32_t e = 0; e < 2; ++e) {
-        const uint32_t s0 = h0 + e * parent, l0 = s0 - sg.tile_base * (uint32_t)kTile;
-        if (l0 >= sg.m) continue;  // (beyond the segment's queries)
-        const uint32_t j0 = sorted ? (uint32_t)__ldg(order + s0) : l0;
-        if (j0 >= sg.m) continue;
-        const unsigned long long d0 = __ldg(sg.d2 + j0);
-        int px, py, pz;
-        if (d0 != ~0ull && query_voxel(sg, j0, px, py, pz)) {
-          seed = min(seed, seed_bound(d0, qx, qy, qz, px, py, pz));
-        }
-      }
-    }
+    const unsigned long long seed =
+        parent != 0 && active ? seed_of(sg, slot, parent, sorted, order, qx, qy, qz) : ~0ull;
     const uint32_t b = sg.a.bits;
     const int top = (1 << b) - 1;
     const uint32_t cqx = (uint32_t)min(max(qx, 0), top);

@@ -165,3 +165,43 @@ def test_tree_replaced_by_other_preparations(cg, orc):
     assert (cg.NN_TREE,) in times and min(times, key=times.get) == shifts
     assert all(t > 0 for t in times.values())
     check(cg, orc, a, oa, og, q, brute=False)
+
+
+@pytest.mark.parametrize("strategy", ["tree", (), (3,)])
+def test_seeded_passes_exact(cg, orc, strategy):
+    """Sorted tree searches run in two passes, every 32nd query of the Morton
+    order first and the rest starting from bounds their group heads' answers
+    give (the window searches, run here too, take one pass).
+    Against brute force on a batch above the sort threshold holding the cases
+    a seed could get wrong: repeated queries, queries on stored voxels (the
+    answer at distance 0), queries far outside the grid (64-bit distances in
+    the same warps as 32-bit ones), non-finite queries (a head without an
+    answer gives no seed), through the internal sort and through caller
+    orders that are the identity, reversed and a random permutation (heads then
+    are not near their groups)."""
+    pts = synth.uniform_cube(6000, seed=560)
+    g, og = cg.grid_from_box([0, 0, 0], 1.0, 10), orc.grid_from_box([0, 0, 0], 1.0, 10)
+    a = cg.cga_build(dev(pts), g)
+    oa = orc.build(pts, og)
+    cg.cga_nn_prepare(a, strategy)
+    rng = np.random.default_rng(561)
+    q = np.concatenate([synth.uniform_queries(9000, 562, [0, 0, 0], 1.0),
+                        np.repeat(synth.uniform_queries(200, 563, [0, 0, 0], 1.0), 8, axis=0),
+                        pts[rng.choice(len(pts), 2000, replace=False)],
+                        synth.uniform_queries(1500, 564, [-40, -40, -40], 81.0)]).astype(np.float32)
+    q[rng.choice(len(q), 300, replace=False)] = np.nan
+    rng.shuffle(q)
+    oi, od = orc.nn_brute(oa, og, q)
+    idx, d2 = cg.cga_nn_query(a, dev(q))
+    np.testing.assert_array_equal(d2.cpu().numpy().view(np.uint64), od, err_msg="dist2")
+    np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), oi, err_msg="idx")
+    m = len(q)
+    dq = dev(q)
+    for name, perm in [("identity", np.arange(m)), ("reversed", np.arange(m)[::-1]),
+                       ("random", rng.permutation(m))]:
+        order = torch.from_numpy(perm.astype(np.int64)).cuda()
+        idx = torch.empty(m, dtype=torch.int32, device="cuda")
+        d2 = torch.empty(m, dtype=torch.int64, device="cuda")
+        cg.cga_nn_query_ordered(a, dq, order, idx, d2)
+        np.testing.assert_array_equal(d2.cpu().numpy().view(np.uint64), od, err_msg=name)
+        np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), oi, err_msg=name)
