@@ -54,49 +54,49 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
 }
 
 // Sort keys (morton30 << 32 | query index) and per-segment digit histograms
-// of the four passes over bits 32..63.  A block covers 256 slots of one tile.
+// of the four passes over bits 32..63.  A block covers one tile.
 __global__ void __launch_bounds__(256) k_nn_keys(const NnSeg* __restrict__ segs, int S,
                                                  unsigned long long* __restrict__ keys,
                                                  uint32_t* __restrict__ hist) {
   __shared__ uint32_t s_hist[4][kRadix];
   for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
   __syncthreads();
-  const uint32_t slot = blockIdx.x * 256u + threadIdx.x;
-  const uint32_t tile = blockIdx.x / (kTile / 256);
+  // one block per tile: its digit counts reach the global histogram once
+  const uint32_t tile = blockIdx.x;
   const int s = find_nn_seg(segs, S, tile);
   const NnSeg& sg = segs[s];
-  const uint32_t local = slot - sg.tile_base * (uint32_t)kTile;
-  if (local < sg.m && sg.qv != nullptr) {
-    // integer query voxels: clamped to the grid for the ordering only
-    const uint32_t bits = sg.a.bits;
-    const int top = (1 << bits) - 1;
-    uint32_t c[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const uint32_t u = (uint32_t)min(max(__ldg(sg.qv + 3 * (size_t)local + a), 0), top);
-      c[a] = bits >= 10 ? (u >> (bits - 10)) : (u << (10 - bits));
-    }
-    const uint32_t mort = (spread3(c[0]) << 2) | (spread3(c[1]) << 1) | spread3(c[2]);
-    keys[slot] = ((unsigned long long)mort << 32) | local;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) atomicAdd(&s_hist[k][(mort >> (8 * k)) & (kRadix - 1)], 1u);
-  } else if (local < sg.m) {
-    const float* p = sg.q + 3 * (size_t)local;
-    const float px = p[0], py = p[1], pz = p[2];
+  const uint32_t bits = sg.a.bits;
+  for (uint32_t e = threadIdx.x; e < (uint32_t)kTile; e += 256u) {
+    const uint32_t slot = tile * (uint32_t)kTile + e;
+    const uint32_t local = slot - sg.tile_base * (uint32_t)kTile;
+    if (local >= sg.m) break;
     uint32_t mort = 0x3fffffffu;
-    if (isfinite(px) && isfinite(py) && isfinite(pz)) {
-      const uint32_t bits = sg.a.bits;
-      const float top = (float)((1u << bits) - 1u);
-      const float v[3] = {px, py, pz};
+    if (sg.qv != nullptr) {
+      // integer query voxels: clamped to the grid for the ordering only
+      const int top = (1 << bits) - 1;
       uint32_t c[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        float f = floorf(__fmaf_rn(v[a], sg.scale, sg.off[a]));
-        f = fminf(fmaxf(f, 0.0f), top);
-        const uint32_t u = (uint32_t)f;
+        const uint32_t u = (uint32_t)min(max(__ldg(sg.qv + 3 * (size_t)local + a), 0), top);
         c[a] = bits >= 10 ? (u >> (bits - 10)) : (u << (10 - bits));
       }
       mort = (spread3(c[0]) << 2) | (spread3(c[1]) << 1) | spread3(c[2]);
+    } else {
+      const float* p = sg.q + 3 * (size_t)local;
+      const float px = p[0], py = p[1], pz = p[2];
+      if (isfinite(px) && isfinite(py) && isfinite(pz)) {
+        const float top = (float)((1u << bits) - 1u);
+        const float v[3] = {px, py, pz};
+        uint32_t c[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          float f = floorf(__fmaf_rn(v[a], sg.scale, sg.off[a]));
+          f = fminf(fmaxf(f, 0.0f), top);
+          const uint32_t u = (uint32_t)f;
+          c[a] = bits >= 10 ? (u >> (bits - 10)) : (u << (10 - bits));
+        }
+        mort = (spread3(c[0]) << 2) | (spread3(c[1]) << 1) | spread3(c[2]);
+      }
     }
     keys[slot] = ((unsigned long long)mort << 32) | local;
 #pragma unroll
@@ -1177,7 +1177,7 @@ cudaError_t run_nn_sort_device(int S, uint32_t total_tiles, const NnTables& t,
   cudaError_t e = cudaMemsetAsync(t.err, 0, sizeof(Header), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(t.sort.hist, 0, t.sort.zero_bytes, stream);
   if (e != cudaSuccess) return e;
-  k_nn_keys<<<total_tiles * (kTile / 256), 256, 0, stream>>>(
+  k_nn_keys<<<total_tiles, 256, 0, stream>>>(
       t.segs, S, static_cast<unsigned long long*>(t.sort.keys0), t.sort.hist);
   count_launch(1);
   return run_radix_passes(S, total_tiles, 4, true, t.sort, stream);
@@ -1195,7 +1195,7 @@ cudaError_t run_nn_device(int S, uint32_t total_tiles, const NnTables& t, cudaSt
   cudaError_t e = cudaMemsetAsync(t.err, 0, sizeof(Header), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(t.sort.hist, 0, t.sort.zero_bytes, stream);
   if (e != cudaSuccess) return e;
-  k_nn_keys<<<total_tiles * (kTile / 256), 256, 0, stream>>>(
+  k_nn_keys<<<total_tiles, 256, 0, stream>>>(
       t.segs, S, static_cast<unsigned long long*>(t.sort.keys0), t.sort.hist);
   count_launch(1);
   e = run_radix_passes(S, total_tiles, 4, true, t.sort, stream);
