@@ -329,26 +329,34 @@ __host__ __device__ inline unsigned long long tree_key(uint32_t x, uint32_t y, u
   }
   return k;
 }
+// The child numbers whose cell has coordinate v on axis a: bit p of
+// tree_axis_set(a, v) is set when tree_cell(p) puts p at v on that axis.
+__host__ __device__ constexpr unsigned long long tree_axis_set(int a, uint32_t v) {
+  unsigned long long m = 0;
+  for (uint32_t p = 0; p < 64; ++p) {
+    const uint32_t cx = p & 3u, cy = ((p >> 4) - cx) & 3u, cz = (((p >> 2) & 3u) - cy) & 3u;
+    if ((a == 0 ? cx : (a == 1 ? cy : cz)) == v) m |= 1ull << p;
+  }
+  return m;
+}
 // Box of a brick's occupied voxels from its voxel set m (m != 0; bit p =
 // tree_child of the voxel inside the brick), in voxels (0..3 per axis):
 // lo_x | hi_x << 4 | lo_y << 8 | hi_y << 12 | lo_z << 16 | hi_z << 20 (the
-// field layout of a node's box).
+// field layout of a node's box).  Per axis the occupied coordinates are the
+// coordinate sets m meets; their least and greatest are the bounds.
+template <int A>
+__host__ __device__ inline uint32_t tree_axis_bounds(unsigned long long m) {
+  // (constants: the four coordinate sets of axis A)
+  constexpr unsigned long long s0 = tree_axis_set(A, 0), s1 = tree_axis_set(A, 1),
+                               s2 = tree_axis_set(A, 2), s3 = tree_axis_set(A, 3);
+  const uint32_t occ = ((m & s0) ? 1u : 0u) | ((m & s1) ? 2u : 0u) | ((m & s2) ? 4u : 0u) |
+                       ((m & s3) ? 8u : 0u);
+  const uint32_t lo = occ & 1u ? 0u : (occ & 2u ? 1u : (occ & 4u ? 2u : 3u));
+  const uint32_t hi = occ & 8u ? 3u : (occ & 4u ? 2u : (occ & 2u ? 1u : 0u));
+  return lo | hi << 4;
+}
 __host__ __device__ inline uint32_t tree_box_code(unsigned long long m) {
-  uint32_t lo[3] = {3u, 3u, 3u}, hi[3] = {0u, 0u, 0u};
-  for (; m != 0ull; m &= m - 1ull) {
-#ifdef __CUDA_ARCH__
-    const uint32_t p = (uint32_t)__ffsll((long long)m) - 1u;
-#else
-    const uint32_t p = (uint32_t)__builtin_ctzll(m);
-#endif
-    uint32_t c[3];
-    tree_cell(p, c[0], c[1], c[2]);
-    for (int a = 0; a < 3; ++a) {
-      lo[a] = c[a] < lo[a] ? c[a] : lo[a];
-      hi[a] = c[a] > hi[a] ? c[a] : hi[a];
-    }
-  }
-  return lo[0] | hi[0] << 4 | lo[1] << 8 | hi[1] << 12 | lo[2] << 16 | hi[2] << 20;
+  return tree_axis_bounds<0>(m) | tree_axis_bounds<1>(m) << 8 | tree_axis_bounds<2>(m) << 16;
 }
 // A node of level l >= 2 keeps the box of its occupied voxels at the
 // granularity of its grandchildren (cells of 4^(l-2) voxels; 16 per axis of
