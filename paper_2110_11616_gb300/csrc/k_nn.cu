@@ -260,6 +260,9 @@ constexpr int kQueryLimit = 1 << 30;
 #ifndef CGA_NN_TREE_BLOCKS
 #define CGA_NN_TREE_BLOCKS 4
 #endif
+#ifndef CGA_NN_HEAD_GROUP
+#define CGA_NN_HEAD_GROUP 16
+#endif
 #ifndef CGA_NN_TREE_GROUP
 #define CGA_NN_TREE_GROUP 4
 #endif
@@ -1143,6 +1146,16 @@ static void launch_search(const NnSeg* d_segs, int S, const NnSeg& inline_seg,
     for (int k = 0; k < np; ++k) {
       const uint32_t n = pparent[k] == 0 ? total_slots / pstride[k]
                                          : total_slots / pstride[k] - total_slots / pparent[k];
+#if CGA_NN_HEAD_GROUP
+      if (np > 1 && k == 0) {
+        constexpr uint32_t hq = 256 / CGA_NN_HEAD_GROUP;
+        k_nn_tree<CGA_NN_HEAD_GROUP><<<std::min<uint32_t>((n + hq - 1) / hq, cap_blocks), 256, 0,
+                                       stream>>>(d_segs, S, inline_seg, total_slots, order,
+                                                 order_err, pstride[k], pparent[k]);
+        count_launch(1);
+        continue;
+      }
+#endif
       const uint32_t blocks = std::min<uint32_t>((n + qpb - 1) / qpb, cap_blocks);
       k_nn_tree<CGA_NN_TREE_GROUP><<<blocks, 256, 0, stream>>>(d_segs, S, inline_seg,
                                                                total_slots, order, order_err,

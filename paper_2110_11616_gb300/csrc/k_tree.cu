@@ -91,51 +91,167 @@ __global__ void __launch_bounds__(kThreads) k_tree_level(
     if (start + cnt == n) *n_out = excl + tot;
   }
   __syncthreads();
+  // Each item is a child of the node its prefix >> 6 names: its contribution
+  // (its bit in the child set and, above the bricks, its box in the node's
+  // grandchild cells, as bytes lo_x | lo_y << 8 | lo_z << 16 and the same for
+  // hi) is formed item by item, and runs of one node are reduced within the
+  // thread, then across threads by a reverse segmented scan: a node's record
+  // is written by the thread holding its first child once its run is whole.
+  // Only the tile's last run can go on into the next tile: its head thread
+  // reads the rest (at most 63 children) from global memory.
+  const bool nodes = brick == nullptr;
+  auto contrib = [&](uint32_t f, unsigned long long v, uint32_t& lo, uint32_t& hi) {
+    lo = 0x0F0F0Fu;
+    hi = 0u;
+    if (!nodes) return;
+    const uint32_t c = (uint32_t)(v & 63);
+    uint32_t pos[3];
+    tree_cell(c, pos[0], pos[1], pos[2]);
+    // the child's box in its own units: a brick's in voxels (0..3), a node's
+    // in its grandchild cells (0..15)
+    const uint32_t cc = ccode1 != nullptr ? __ldg(ccode1 + f) : __ldg(&cnode[f].w);
+    const uint32_t m = ccode1 != nullptr ? 4u : 16u;  // child cell in those units
+    const uint32_t s = ccode1 != nullptr ? 0u : 2u;   // a node child's units are 4x finer
+    uint32_t pl[3], ph[3];
+    lo = 0u;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const uint32_t cl = (cc >> (8 * a)) & 15u, ch = (cc >> (8 * a + 4)) & 15u;
+      pl[a] = pos[a] * m + cl;
+      ph[a] = pos[a] * m + ch;
+      lo |= (pos[a] * 4 + (cl >> s)) << (8 * a);
+      hi |= (pos[a] * 4 + (ch >> s)) << (8 * a);
+    }
+    cpcode[f] = make_uint2(pl[0] | ph[0] << 6 | pl[1] << 12 | ph[1] << 18, pl[2] | ph[2] << 6);
+  };
+  auto write_node = [&](uint32_t jj, uint32_t first, unsigned long long pr,
+                        unsigned long long mask, uint32_t lo, uint32_t hi) {
+    if (NP != nullptr) NP[jj] = pr;
+    if (!nodes) {
+      brick[jj] = mask;
+      bcode[jj] = tree_box_code(mask);
+    } else {
+      uint32_t box = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        box |= (((lo >> (8 * a)) & 15u) | ((hi >> (8 * a)) & 15u) << 4) << (8 * a);
+      }
+      node[jj] = make_uint4((uint32_t)mask, (uint32_t)(mask >> 32), first, box);
+    }
+  };
   uint32_t j = s_excl + off;
+  // the thread's own items: the leading part (before its first head) and
+  // the run of its last head so far
+  unsigned long long am = 0, lead_m = 0, hpr = 0;  // hpr: the current head's node
+  uint32_t alo = 0x0F0F0Fu, ahi = 0u, lead_lo = 0x0F0F0Fu, lead_hi = 0u, hfirst = 0;
+  int head_i = -1;
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
-    if (!((heads >> i) & 1u)) continue;
-    const uint32_t e = start + e0 + i;
-    const unsigned long long pr = k[i] >> 6;
-    unsigned long long mask = 0;
-    uint32_t lo[3] = {15u, 15u, 15u}, hi[3] = {0u, 0u, 0u};
-    // a node has at most 64 children, so its run ends within 64 entries
-    for (uint32_t f = e; f < n && f < e + 64; ++f) {
-      const unsigned long long v = f == e ? k[i] : (f - start < cnt ? s_k[f - start] : __ldg(P + f));
-      if ((v >> 6) != pr) break;
-      const uint32_t c = (uint32_t)(v & 63);
-      mask |= 1ull << c;
-      if (brick == nullptr) {
-        // the child's box in this node's grandchild units
-        uint32_t pos[3];
-        tree_cell(c, pos[0], pos[1], pos[2]);
-        // the child's box in its own units: a brick's in voxels (0..3), a
-        // node's in its grandchild cells (0..15)
-        const uint32_t cc = ccode1 != nullptr ? __ldg(ccode1 + f) : __ldg(&cnode[f].w);
-        const uint32_t m = ccode1 != nullptr ? 4u : 16u;  // child cell in those units
-        uint32_t pl[3], ph[3];
+    const uint32_t e = e0 + i;
+    if (e >= cnt) break;
+    uint32_t clo, chi;
+    contrib(start + e, k[i], clo, chi);
+    if ((heads >> i) & 1u) {
+      if (head_i < 0) {
+        lead_m = am;
+        lead_lo = alo;
+        lead_hi = ahi;
+      } else {
+        // the previous head's run ends inside the thread
+        write_node(j, hfirst, hpr, am, alo, ahi);
+        ++j;
+      }
+      head_i = i;
+      hpr = k[i] >> 6;
+      hfirst = start + e;
+      am = 0;
+      alo = 0x0F0F0Fu;
+      ahi = 0u;
+    }
+    am |= 1ull << (k[i] & 63);
+    alo = __vminu4(alo, clo);
+    ahi = __vmaxu4(ahi, chi);
+  }
+  if (head_i < 0) {
+    lead_m = am;
+    lead_lo = alo;
+    lead_hi = ahi;
+  }
+  // reverse segmented scan over the threads of the leading parts: thread u
+  // ends with the union of the leading parts of threads u, u + 1, ... up to
+  // and including the first thread that holds a head
+  const uint32_t lane = tid & 31u, w = tid >> 5;
+  unsigned long long sm = lead_m;
+  uint32_t slo = lead_lo, shi = lead_hi;
+  bool sf = head_i >= 0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const uint32_t cl = (cc >> (8 * a)) & 15u, ch = (cc >> (8 * a + 4)) & 15u;
-          pl[a] = pos[a] * m + cl;
-          ph[a] = pos[a] * m + ch;
-          // in this node's grandchild cells (a node child's units are 4x finer)
+  for (uint32_t d = 1; d < 32; d <<= 1) {
+    const unsigned long long om = __shfl_down_sync(0xffffffffu, sm, d);
+    const uint32_t olo = __shfl_down_sync(0xffffffffu, slo, d);
+    const uint32_t ohi = __shfl_down_sync(0xffffffffu, shi, d);
+    const bool of = __shfl_down_sync(0xffffffffu, sf, d);
+    if (lane + d < 32 && !sf) {
+      sm |= om;
+      slo = __vminu4(slo, olo);
+      shi = __vmaxu4(shi, ohi);
+      sf = of;
+    }
+  }
+  __shared__ unsigned long long s_wm[kWarps], s_tm[kThreads];
+  __shared__ uint32_t s_wlo[kWarps], s_whi[kWarps], s_tlo[kThreads], s_thi[kThreads];
+  __shared__ uint8_t s_wf[kWarps], s_tf[kThreads];
+  if (lane == 0) {
+    s_wm[w] = sm;
+    s_wlo[w] = slo;
+    s_whi[w] = shi;
+    s_wf[w] = sf ? 1 : 0;
+  }
+  __syncthreads();
+  for (uint32_t x = w + 1; x < (uint32_t)kWarps && !sf; ++x) {
+    sm |= s_wm[x];
+    slo = __vminu4(slo, s_wlo[x]);
+    shi = __vmaxu4(shi, s_whi[x]);
+    sf = s_wf[x] != 0;
+  }
+  s_tm[tid] = sm;
+  s_tlo[tid] = slo;
+  s_thi[tid] = shi;
+  s_tf[tid] = sf ? 1 : 0;
+  __syncthreads();
+  if (head_i >= 0) {
+    // the last head's run: the thread's tail, the leading parts that follow
+    bool closed = false;
+    if (tid + 1 < (uint32_t)kThreads) {
+      am |= s_tm[tid + 1];
+      alo = __vminu4(alo, s_tlo[tid + 1]);
+      ahi = __vmaxu4(ahi, s_thi[tid + 1]);
+      closed = s_tf[tid + 1] != 0;
+    }
+    if (!closed) {
+      // the run reaches the end of the tile: the rest lies in the next one
+      for (uint32_t f = start + cnt; f < n && f < start + cnt + 64; ++f) {
+        const unsigned long long v = __ldg(P + f);
+        if ((v >> 6) != hpr) break;
+        am |= 1ull << (v & 63);
+        if (nodes) {
+          // (the next tile writes this child's own box in the parent frame)
+          const uint32_t c = (uint32_t)(v & 63);
+          uint32_t pos[3];
+          tree_cell(c, pos[0], pos[1], pos[2]);
+          const uint32_t cc = ccode1 != nullptr ? __ldg(ccode1 + f) : __ldg(&cnode[f].w);
           const uint32_t s = ccode1 != nullptr ? 0u : 2u;
-          lo[a] = min(lo[a], pos[a] * 4 + (cl >> s));
-          hi[a] = max(hi[a], pos[a] * 4 + (ch >> s));
+          uint32_t clo = 0, chi = 0;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            clo |= (pos[a] * 4 + (((cc >> (8 * a)) & 15u) >> s)) << (8 * a);
+            chi |= (pos[a] * 4 + (((cc >> (8 * a + 4)) & 15u) >> s)) << (8 * a);
+          }
+          alo = __vminu4(alo, clo);
+          ahi = __vmaxu4(ahi, chi);
         }
-        cpcode[f] = make_uint2(pl[0] | ph[0] << 6 | pl[1] << 12 | ph[1] << 18, pl[2] | ph[2] << 6);
       }
     }
-    if (NP != nullptr) NP[j] = pr;
-    if (brick != nullptr) {
-      brick[j] = mask;
-      bcode[j] = tree_box_code(mask);
-    } else {
-      const uint32_t box = lo[0] | hi[0] << 4 | lo[1] << 8 | hi[1] << 12 | lo[2] << 16 | hi[2] << 20;
-      node[j] = make_uint4((uint32_t)mask, (uint32_t)(mask >> 32), e, box);
-    }
-    ++j;
+    write_node(j, hfirst, hpr, am, alo, ahi);
   }
 }
 
