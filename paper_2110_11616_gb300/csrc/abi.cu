@@ -619,6 +619,14 @@ int cga_project(const cga_t* a, int plane, const cga_allocator* A, void* stream,
   int rc;
   if (plane == CGA_PLANE_XY) {
     rc = cuda_rc(libcga::run_project_xy(a->lv, p->lv, s));
+  } else if (b >= libcga::kProjBitmapMinBits && b <= libcga::kProjBitmapMaxBits) {
+    void* scratch = dalloc(A, libcga::project_bitmap_scratch_bytes(b), s);
+    if (scratch == nullptr) {
+      rc = CGA_ERR_OOM;
+    } else {
+      rc = cuda_rc(libcga::run_project_bitmap(a->lv, plane, p->lv, scratch, s));
+      dfree(A, A != nullptr, scratch, s);
+    }
   } else {
     libcga::SortSeg seg{};
     seg.src = a->lv;
@@ -1317,6 +1325,7 @@ int cga_project_batch(const cga_t* const* a, const int* planes, uint32_t count,
   std::vector<cga2d*> ps(count, nullptr);
   std::vector<libcga::ProjPair> xy;
   std::vector<libcga::SortSeg> segs;
+  std::vector<uint32_t> bitmap;  // xz / yz projections of small grids (no sort)
   uint64_t tiles = 0, max_cap1 = 0;
   int rc = CGA_OK;
   for (uint32_t i = 0; i < count && rc == CGA_OK; ++i) {
@@ -1347,6 +1356,8 @@ int cga_project_batch(const cga_t* const* a, const int* planes, uint32_t count,
     if (planes[i] == CGA_PLANE_XY) {
       xy.push_back(libcga::ProjPair{a[i]->lv, p->lv});
       max_cap1 = std::max<uint64_t>(max_cap1, a[i]->lv.cap1);
+    } else if (b >= libcga::kProjBitmapMinBits && b <= libcga::kProjBitmapMaxBits) {
+      bitmap.push_back(i);
     } else {
       libcga::SortSeg sg{};
       sg.src = a[i]->lv;
@@ -1375,6 +1386,20 @@ int cga_project_batch(const cga_t* const* a, const int* planes, uint32_t count,
       }
       rc = cuda_rc(e);
       dfree(A, A != nullptr, tab, s);
+    }
+  }
+  if (rc == CGA_OK && !bitmap.empty()) {
+    uint32_t max_bits = 0;
+    for (uint32_t i : bitmap) max_bits = std::max(max_bits, a[i]->grid.bits);
+    void* scratch = dalloc(A, libcga::project_bitmap_scratch_bytes(max_bits), s);
+    if (scratch == nullptr) {
+      rc = CGA_ERR_OOM;
+    } else {
+      for (uint32_t i : bitmap) {
+        if (rc != CGA_OK) break;
+        rc = cuda_rc(libcga::run_project_bitmap(a[i]->lv, planes[i], ps[i]->lv, scratch, s));
+      }
+      dfree(A, A != nullptr, scratch, s);
     }
   }
   if (rc == CGA_OK && !segs.empty()) {

@@ -278,6 +278,13 @@ cudaError_t run_lookup(const Levels& a, const uint32_t* xptr, const int* qv, uin
 
 // Copy the top two levels of a CGA into a 2-level projection (plane xy).
 cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stream);
+// The xz (plane 1) or yz (plane 2) projection of a CGA on a grid of 5 to 13
+// bits per axis through a bitmap of its 2D voxels (no sort); scratch of
+// project_bitmap_scratch_bytes(bits).
+constexpr uint32_t kProjBitmapMinBits = 5, kProjBitmapMaxBits = 13;
+size_t project_bitmap_scratch_bytes(uint32_t bits);
+cudaError_t run_project_bitmap(const Levels& a, int plane, const Levels& out, void* scratch,
+                               cudaStream_t stream);
 struct ProjPair {
   Levels a, out;
 };
@@ -293,11 +300,11 @@ constexpr int kMaxCoarse = 2;
 
 // Occupancy tree of a CGA for NN search (cga_nn_prepare_levels with
 // CGA_NN_TREE): a 64-ary tree over the grid in which a node of level l covers
-// 4^l voxels per axis and has up to 4 x 4 x 4 children of level l - 1.  Child
-// c = cx << 4 | cy << 2 | cz (each 0..3), so the bit order of a node's child
-// set is the key order (x, then y, then z) of its children.  Level 1 nodes
-// (bricks) hold their 64 voxels as occupancy bits; the root is level
-// tree_levels(bits), with node 0 of that level the only one.
+// 4^l voxels per axis and has up to 4 x 4 x 4 children of level l - 1,
+// numbered by tree_child (bit p of a node's child set is its child number p).
+// Level 1 nodes (bricks) hold their 64 voxels as occupancy bits, numbered the
+// same way; the root is level tree_levels(bits), with node 0 of that level
+// the only one.
 constexpr int kTreeMaxLevels = 8;  // ceil(16 / 2)
 inline uint32_t tree_levels(uint32_t bits) { return (bits + 1) / 2; }
 // Number of the child cell (cx, cy, cz) in [0, 4)^3 of a tree cell:

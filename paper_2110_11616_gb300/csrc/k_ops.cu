@@ -724,6 +724,127 @@ __global__ void k_project_xy(Levels a, Levels o) {
   project_xy_body(a, o, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
+// ------------------------------------------------------ bitmap projection
+// The xz or yz projection (Eq. 3) of a CGA on a grid of 5 to 13 bits per axis
+// without a sort: one bit per 2D voxel (2^(2b) bits, row = the kept first
+// axis, column = z) is set for every stored voxel, and the set bits read row
+// by row, in order, are the distinct 2D voxels in key order: U_index the
+// non-empty rows, V_index the set columns of each.
+
+// Set the bits of a's voxels (a tile of Z positions per block, decoded by the
+// X -> Y -> Z walk of Sec. V-A as in k_decode).
+__global__ void __launch_bounds__(kThreads) k_proj_set(Levels a, int plane,
+                                                       uint32_t* __restrict__ bits) {
+  __shared__ Window s_win;
+  __shared__ uint16_t s_col[kTile], s_slab[kTile];
+  __shared__ uint32_t s_warp[kWarps];
+  const uint32_t u = (uint32_t)a.hdr->cnt[0];
+  const uint32_t start = blockIdx.x * kTile;
+  if (start >= u) return;
+  const uint32_t cnt = min((uint32_t)kTile, u - start);
+  if (threadIdx.x < 32) {
+    const Window wv =
+        warp_window_of(a, (uint32_t)a.hdr->cnt[1], (uint32_t)a.hdr->cnt[2], start, start + cnt - 1);
+    if (threadIdx.x == 0) s_win = wv;
+  }
+  __syncthreads();
+  const Window w = s_win;
+  expand_window(a, w, start, cnt, s_col, s_slab, s_warp);
+  const uint32_t b = a.bits;
+  for (uint32_t e = threadIdx.x; e < cnt; e += kThreads) {
+    const uint32_t cr = s_col[e];
+    const uint32_t r = plane == 1 ? (uint32_t)__ldg(a.idx2 + w.x0 + s_slab[cr])
+                                  : (uint32_t)__ldg(a.idx1 + w.c0 + cr);
+    const uint32_t key = (r << b) | __ldg(a.idx0 + start + e);
+    atomicOr(bits + (key >> 5), 1u << (key & 31u));
+  }
+}
+
+// Set bits of each row: one warp per row, each lane a run of the row's words.
+__global__ void __launch_bounds__(256) k_proj_rows(const uint32_t* __restrict__ bits, uint32_t b,
+                                                   uint32_t* __restrict__ rowcnt) {
+  const uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31u;
+  if (row >= (1u << b)) return;
+  const uint32_t words = 1u << (b - 5), per = words > 32u ? words / 32u : 1u;
+  const uint32_t* rw = bits + (size_t)row * words;
+  uint32_t c = 0;
+  for (uint32_t k = 0; k < per; ++k) {
+    const uint32_t wi = lane * per + k;
+    if (wi < words) c += (uint32_t)__popc(__ldg(rw + wi));
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if (lane == 0) rowcnt[row] = c;
+}
+
+// Row offsets (exclusive scan of the row counts) and the U arrays, by one
+// block: thread i takes rows [i * per, (i + 1) * per).
+__global__ void __launch_bounds__(kThreads) k_proj_scan(const uint32_t* __restrict__ rowcnt,
+                                                        uint32_t b, uint32_t* __restrict__ rowoff,
+                                                        Levels o, const Header* __restrict__ src) {
+  __shared__ unsigned long long s_warp[kWarps];
+  const uint32_t rows = 1u << b, per = (rows + kThreads - 1) / kThreads;
+  const uint32_t r0 = threadIdx.x * per;
+  uint32_t v = 0, ne = 0;
+  for (uint32_t k = 0; k < per && r0 + k < rows; ++k) {
+    const uint32_t c = rowcnt[r0 + k];
+    v += c;
+    ne += c != 0u;
+  }
+  // voxels in the low word, non-empty rows in the high word
+  unsigned long long tot = 0;
+  const unsigned long long ex = block_excl_scan<unsigned long long>(
+      (unsigned long long)v | ((unsigned long long)ne << 32), tot, s_warp);
+  uint32_t off = (uint32_t)ex, ui = (uint32_t)(ex >> 32);
+  for (uint32_t k = 0; k < per && r0 + k < rows; ++k) {
+    const uint32_t r = r0 + k, c = rowcnt[r];
+    rowoff[r] = off;
+    if (c != 0u) {
+      o.idx1[ui] = (uint16_t)r;
+      o.ptr1[ui] = off;
+      ++ui;
+    }
+    off += c;
+  }
+  if (threadIdx.x == 0) {
+    const uint32_t total = (uint32_t)tot, h = (uint32_t)(tot >> 32);
+    o.ptr1[h] = total;
+    o.hdr->cnt[0] = total;
+    o.hdr->cnt[1] = h;
+    o.hdr->cnt[2] = 0;
+    o.hdr->err = src->err;
+  }
+}
+
+// V_index: the set columns of each row in order (one warp per row).
+__global__ void __launch_bounds__(256) k_proj_write(const uint32_t* __restrict__ bits, uint32_t b,
+                                                    const uint32_t* __restrict__ rowoff, Levels o) {
+  const uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31u;
+  if (row >= (1u << b)) return;
+  const uint32_t words = 1u << (b - 5), per = words > 32u ? words / 32u : 1u;
+  const uint32_t* rw = bits + (size_t)row * words;
+  uint32_t c = 0;
+  for (uint32_t k = 0; k < per; ++k) {
+    const uint32_t wi = lane * per + k;
+    if (wi < words) c += (uint32_t)__popc(__ldg(rw + wi));
+  }
+  // the lane's first output position: the row's offset and the set bits of
+  // the lanes before it
+  uint32_t incl = c;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= (uint32_t)d) incl += x;
+  }
+  uint32_t pos = __ldg(rowoff + row) + incl - c;
+  for (uint32_t k = 0; k < per; ++k) {
+    const uint32_t wi = lane * per + k;
+    if (wi >= words) break;
+    for (uint32_t m = __ldg(rw + wi); m != 0u; m &= m - 1u) {
+      o.idx0[pos++] = (uint16_t)(wi * 32u + (uint32_t)__ffs((int)m) - 1u);
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t run_decode(const Levels& a, uint32_t* xyz, cudaStream_t stream) {
@@ -847,6 +968,33 @@ cudaError_t run_project_xy(const Levels& a, const Levels& out, cudaStream_t stre
                                                        (uint64_t)device_sm_count() * 8);
   k_project_xy<<<blocks, 256, 0, stream>>>(a, out);
   count_launch(1);
+  return cudaGetLastError();
+}
+
+size_t project_bitmap_scratch_bytes(uint32_t bits) {
+  return align_up(((size_t)1 << (2 * bits)) / 8) + 2 * align_up(((size_t)1 << bits) * 4);
+}
+
+cudaError_t run_project_bitmap(const Levels& a, int plane, const Levels& out, void* scratch,
+                               cudaStream_t stream) {
+  const uint32_t b = a.bits;
+  if (b < 5 || b > 13 || (plane != 1 && plane != 2)) return cudaErrorInvalidValue;
+  char* p = static_cast<char*>(scratch);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(p);
+  const size_t bit_bytes = ((size_t)1 << (2 * b)) / 8;
+  p += align_up(bit_bytes);
+  uint32_t* rowcnt = reinterpret_cast<uint32_t*>(p);
+  p += align_up(((size_t)1 << b) * 4);
+  uint32_t* rowoff = reinterpret_cast<uint32_t*>(p);
+  cudaError_t e = cudaMemsetAsync(bits, 0, bit_bytes, stream);
+  if (e != cudaSuccess) return e;
+  const uint64_t tiles = (a.cap + kTile - 1) / kTile;
+  if (tiles > 0) k_proj_set<<<(unsigned)tiles, kThreads, 0, stream>>>(a, plane, bits);
+  const unsigned row_blocks = ((1u << b) + 7u) / 8u;  // a warp per row
+  k_proj_rows<<<row_blocks, 256, 0, stream>>>(bits, b, rowcnt);
+  k_proj_scan<<<1, kThreads, 0, stream>>>(rowcnt, b, rowoff, out, a.hdr);
+  k_proj_write<<<row_blocks, 256, 0, stream>>>(bits, b, rowoff, out);
+  count_launch(tiles > 0 ? 4 : 3);
   return cudaGetLastError();
 }
 

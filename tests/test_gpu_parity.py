@@ -196,9 +196,13 @@ def test_merge_grid_mismatch(cg):
 
 # -------------------------------------------------------------- projection
 @pytest.mark.parametrize("plane", ["xy", "xz", "yz"])
-@pytest.mark.parametrize("bits,n", [(4, 3000), (10, 100_000), (12, 50_000), (16, 20_000),
-                                    (16, 0), (10, 1)])
+@pytest.mark.parametrize("bits,n", [(4, 3000), (5, 3000), (10, 100_000), (12, 50_000),
+                                    (13, 40_000), (14, 20_000), (16, 20_000), (16, 0), (10, 1),
+                                    (12, 0)])
 def test_project_parity(cg, orc, plane, bits, n):
+    """xy copies the top two levels; xz and yz go through a bitmap of the 2D
+    voxels on grids of 5 to 13 bits and through the sort pipeline otherwise
+    (both edges of that range, empty and single-point clouds included)."""
     pts = synth.uniform_cube(n, seed=50 + bits)
     g, og = grids(cg, orc, [0, 0, 0], 1.0, bits)
     a = cg.cga_build(dev(pts), g)
