@@ -84,6 +84,28 @@ def test_shape_build_merge_project(cg, orc, shaped, sort, half, bits):
     np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), oi)
 
 
+@pytest.mark.parametrize("half", HALVES)
+def test_merge_dense_and_sparse_tiles(cg, orc, shaped, half):
+    """One merge whose tiles take both tile paths: voxel by voxel where the
+    columns hold few voxels, column by column across blocks of full columns
+    (more voxels per tile than the voxel-level stage holds), with columns of
+    both blocks overlapping so that their z lists are united."""
+    shaped({"radix_bits": 8, "sort_threads": 256, "merge_half": half})
+    bits = 10
+    g, og = cg.make_grid(bits, 1.0, (0.0, 0.0, 0.0)), orc.Grid(bits, 1.0, (0.0, 0.0, 0.0))
+    rng = np.random.default_rng(half)
+    sparse = rng.integers(0, 1 << bits, (80_000, 3)).astype(np.float32) + 0.5
+    v = np.stack(np.meshgrid(np.arange(300, 348), np.arange(500, 540), np.arange(100, 148),
+                             indexing="ij"), -1).reshape(-1, 3).astype(np.float32) + 0.5
+    pa = np.concatenate([sparse[:40_000], v])
+    pb = np.concatenate([sparse[40_000:], v[::2] + np.float32([0, 10, 20])])
+    oa, ob = orc.build(pa, og), orc.build(pb, og)
+    m = cg.cga_merge(cg.cga_build(dev(pa), g), cg.cga_build(dev(pb), g))
+    om = orc.merge(oa, ob)
+    assert_cga(m, om, "merge")
+    assert_cga(cg.cga_merge(cg.cga_build(dev(pb), g), cg.cga_build(dev(pa), g)), om, "merge B, A")
+
+
 @pytest.mark.parametrize("shape", [(8, 256, 512), (9, 512, 1024), (9, 512, 2048)])
 def test_shape_batches_and_graph_pipeline(cg, orc, shaped, shape):
     shaped(dict(zip(("radix_bits", "sort_threads", "merge_half"), shape)))
