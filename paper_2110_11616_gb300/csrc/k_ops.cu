@@ -188,25 +188,63 @@ __device__ __forceinline__ void union_write(const uint16_t* za, uint32_t na, con
   while (j < nb) out[n++] = zb[j++];
 }
 
-// z entries of each input a merge tile stages in shared memory (a tile whose
-// columns hold more reads them from global memory instead).
+// z entries of each input the column-by-column tile path stages in shared
+// memory (a tile whose columns hold more reads them from global memory).
 template <int MH>
 constexpr int merge_stage() { return MH == 2048 ? 1536 : 6144; }
 
-// Merge one tile of at most MH columns of each input (one splitter spacing).
+// Voxels of each input the voxel-level tile path holds in shared memory (a
+// tile with more on either side takes the column-by-column path).
+template <int MH>
+constexpr int merge_vstage() { return MH == 512 ? 1536 : (MH == 1024 ? 2560 : 2816); }
+
+// Slabs of each input whose X_pointer and X_index entries the voxel-level
+// tile path stages (a tile over more slabs searches them in global memory).
+constexpr int kMergeSlabStage = 64;
+
+// Shared memory of one merge tile: the larger of the two paths' layouts.
+template <int MH>
+constexpr size_t merge_col_bytes() { return 28 * (size_t)MH + 4 * (size_t)merge_stage<MH>() + 8; }
+// voxel keys of both inputs, then one region holding first the staged
+// Y_pointer, Y_index and slab entries and later the output z entries
+template <int MH>
+constexpr size_t merge_vox_stage_bytes() {
+  return 8 * ((size_t)MH + 1) + 4 * (size_t)MH + 12 * (size_t)kMergeSlabStage;
+}
+template <int MH>
+constexpr size_t merge_vox_bytes() {
+  return 16 * (size_t)merge_vstage<MH>() +
+         (4 * (size_t)merge_vstage<MH>() > merge_vox_stage_bytes<MH>() ? 4 * (size_t)merge_vstage<MH>()
+                                                                        : merge_vox_stage_bytes<MH>());
+}
+template <int MH>
+constexpr size_t merge_smem_bytes() {
+  return ((merge_col_bytes<MH>() > merge_vox_bytes<MH>() ? merge_col_bytes<MH>()
+                                                          : merge_vox_bytes<MH>()) + 15) & ~(size_t)15;
+}
+
+// Merge one tile of at most MH columns of each input (one splitter spacing)
+// column by column: merge path over the column keys, then per output column
+// its z list (a copy, or the union of two lists).  raw: merge_smem_bytes<MH>()
+// bytes of shared memory, 16-byte aligned.
 template <int MH>
 __device__ __forceinline__ void merge_tile(const MergePair* __restrict__ pairs, int S,
                                            const uint32_t* __restrict__ bounds,
                                            const uint32_t* __restrict__ ntiles, uint32_t* clook,
-                                           uint32_t t, int p) {
+                                           uint32_t t, int p, unsigned char* raw) {
   constexpr int IT = 2 * MH / kThreads;  // merged columns per thread
   static_assert(IT * kThreads == 2 * MH && MH % kThreads == 0, "merge tile shape");
-  // column keys of A and B; merged keys and sources; staged z entries
+  // merged keys; column keys of A and B; the tile's Y_pointer entries; merged
+  // sources; staged z entries
   constexpr int ZS = merge_stage<MH>();
-  __shared__ uint32_t s_ka[MH], s_kb[MH], s_mk[2 * MH];
-  __shared__ uint16_t s_ms[2 * MH];
-  __shared__ uint16_t s_za[ZS], s_zb[ZS];
-  __shared__ uint32_t s_pa[MH + 1], s_pb[MH + 1];  // the tile's Y_pointer entries
+  uint32_t* s_mk = reinterpret_cast<uint32_t*>(raw);
+  uint32_t* s_ka = s_mk + 2 * MH;
+  uint32_t* s_kb = s_ka + MH;
+  uint32_t* s_pa = s_kb + MH;
+  uint32_t* s_pb = s_pa + MH + 1;
+  uint16_t* s_ms = reinterpret_cast<uint16_t*>(s_pb + MH + 1);
+  uint16_t* s_za = s_ms + 2 * MH;
+  uint16_t* s_zb = s_za + ZS;
   __shared__ unsigned long long s_warp64[kWarps];
   __shared__ uint32_t s_tot[6], s_prevx, s_hasprev;
   const int tid = threadIdx.x;
@@ -401,6 +439,298 @@ __device__ __forceinline__ void merge_tile(const MergePair* __restrict__ pairs, 
   }
 }
 
+// Next tile id for a resident block (total_tiles when none is left).  A
+// reserved tile at or beyond its pair's actual count means the pair's later
+// ones hold nothing either: the counter jumps to the next pair's first tile,
+// and after the last pair the block stops.  Each round moves to a later pair,
+// and real tiles still go out in increasing order.
+__device__ __forceinline__ uint32_t next_merge_tile(const MergePair* __restrict__ pairs, int S,
+                                                    const uint32_t* __restrict__ ntiles,
+                                                    uint32_t* counter, uint32_t total_tiles,
+                                                    int& p) {
+  for (;;) {
+    const uint32_t t = atomicAdd(counter, 1u);
+    p = 0;
+    if (t >= total_tiles) return total_tiles;
+    p = find_pair_tile(pairs, S, t);
+    if (t - pairs[p].tile_base < ntiles[p]) return t;
+    if (p + 1 >= S) {
+      p = 0;
+      return total_tiles;
+    }
+    atomicMax(counter, pairs[p + 1].tile_base);
+  }
+}
+
+// Merge one tile voxel by voxel.  Each voxel of the tile gets its full key
+// (x << b | y) << 16 | z; both key runs are ascending, so the tile's output is
+// their merge with equal keys (a voxel present in both inputs, adjacent in the
+// merge) kept once.  Merge path splits the tile's voxels evenly over the
+// threads whatever the columns hold; an output voxel opens a column when its
+// column key differs from the previous output voxel's, and a slab when its x
+// does.  One block scan of (voxels, columns, slabs) and the look-back give the
+// tile's offsets; z entries go out through shared memory in one coalesced
+// pass, column and slab entries straight from the walk.  A tile with more than
+// merge_vstage<MH>() voxels on either side (dense columns) takes the
+// column-by-column path instead.
+template <int MH>
+__device__ __forceinline__ void merge_tile_v(const MergePair* __restrict__ pairs, int S,
+                                             const uint32_t* __restrict__ bounds,
+                                             const uint32_t* __restrict__ ntiles, uint32_t* clook,
+                                             uint32_t t, int p, unsigned char* raw) {
+  constexpr int VS = merge_vstage<MH>();
+  static_assert(2 * VS <= 32 * kThreads, "a thread's merged voxels fit one 32-bit mask");
+  constexpr unsigned long long kF = (1ull << 21) - 1ull;  // one field of the packed scan
+  __shared__ unsigned long long s_w64[kWarps];
+  __shared__ uint32_t s_vt[6], s_vprevck, s_vhasprev;
+  const int tid = threadIdx.x;
+  const MergePair& P = pairs[p];
+  const uint32_t lt = t - P.tile_base;
+  const uint32_t nt = ntiles[p];
+  if (lt >= nt) return;
+  const Levels &A = P.a, &B = P.b, &O = P.out;
+  const uint32_t b = O.bits, ymask = (1u << b) - 1u;
+  const uint32_t* bnd = bounds + (size_t)kBoundWords * ((size_t)P.tile_base + p + lt);
+  const uint32_t a0 = bnd[0], b0 = bnd[1], sa0 = bnd[2], sb0 = bnd[3];
+  const uint32_t a1 = bnd[4], b1 = bnd[5], sa1 = bnd[6], sb1 = bnd[7];
+  const uint32_t na = a1 - a0, nb = b1 - b0;
+  const bool bad = a1 < a0 || b1 < b0 || na > (uint32_t)MH || nb > (uint32_t)MH;
+  uint32_t zA0 = 0, zA1 = 0, zB0 = 0, zB1 = 0;
+  if (!bad) {
+    if (na) {
+      zA0 = __ldg(A.ptr1 + a0);
+      zA1 = __ldg(A.ptr1 + a1);
+    }
+    if (nb) {
+      zB0 = __ldg(B.ptr1 + b0);
+      zB1 = __ldg(B.ptr1 + b1);
+    }
+  }
+  const uint32_t nva = zA1 - zA0, nvb = zB1 - zB0;  // wraps (and so falls back) if corrupt
+  if (bad || nva > (uint32_t)VS || nvb > (uint32_t)VS) {
+    merge_tile<MH>(pairs, S, bounds, ntiles, clook, t, p, raw);
+    return;
+  }
+  unsigned long long* s_va = reinterpret_cast<unsigned long long*>(raw);
+  unsigned long long* s_vb = s_va + VS;
+  uint16_t* s_oz = reinterpret_cast<uint16_t*>(s_vb + VS);  // 2 * VS output z entries
+  // staged entries of the tile's columns and slabs (the same region as s_oz)
+  uint32_t* s_pa = reinterpret_cast<uint32_t*>(s_vb + VS);  // Y_pointer, na + 1
+  uint32_t* s_pb = s_pa + MH + 1;
+  uint16_t* s_ya = reinterpret_cast<uint16_t*>(s_pb + MH + 1);  // Y_index, na
+  uint16_t* s_yb = s_ya + MH;
+  uint32_t* s_xpa = reinterpret_cast<uint32_t*>(s_yb + MH);  // X_pointer of the slabs
+  uint32_t* s_xpb = s_xpa + kMergeSlabStage;
+  uint16_t* s_xa = reinterpret_cast<uint16_t*>(s_xpb + kMergeSlabStage);  // X_index
+  uint16_t* s_xb = s_xa + kMergeSlabStage;
+  const uint32_t saL = na ? (__ldg(A.ptr2 + sa1) == a1 ? sa1 - 1 : sa1) : sa0;
+  const uint32_t sbL = nb ? (__ldg(B.ptr2 + sb1) == b1 ? sb1 - 1 : sb1) : sb0;
+  const uint32_t nsa = na ? saL - sa0 + 1 : 0u, nsb = nb ? sbL - sb0 + 1 : 0u;
+  const bool xsa = nsa <= (uint32_t)kMergeSlabStage, xsb = nsb <= (uint32_t)kMergeSlabStage;
+  if (tid == 0) {
+    // key of the column just before the tile (the larger of A's and B's)
+    uint32_t pk = 0;
+    if (a0 > 0) {
+      const uint32_t s = __ldg(A.ptr2 + sa0) == a0 ? sa0 - 1 : sa0;
+      pk = ((uint32_t)__ldg(A.idx2 + s) << b) | __ldg(A.idx1 + a0 - 1);
+    }
+    if (b0 > 0) {
+      const uint32_t s = __ldg(B.ptr2 + sb0) == b0 ? sb0 - 1 : sb0;
+      pk = max(pk, ((uint32_t)__ldg(B.idx2 + s) << b) | __ldg(B.idx1 + b0 - 1));
+    }
+    s_vprevck = pk;
+    s_vhasprev = (a0 > 0 || b0 > 0) ? 1u : 0u;
+  }
+  // stage the tile's z entries (the low bits of the voxel keys), Y_pointer
+  // and Y_index entries and its slabs' entries: independent coalesced loads
+  for (uint32_t e = tid; e < nva; e += kThreads) s_va[e] = __ldg(A.idx0 + zA0 + e);
+  for (uint32_t e = tid; e < nvb; e += kThreads) s_vb[e] = __ldg(B.idx0 + zB0 + e);
+  if (na) {
+    for (uint32_t e = tid; e <= na; e += kThreads) s_pa[e] = __ldg(A.ptr1 + a0 + e);
+    for (uint32_t e = tid; e < na; e += kThreads) s_ya[e] = __ldg(A.idx1 + a0 + e);
+  }
+  if (nb) {
+    for (uint32_t e = tid; e <= nb; e += kThreads) s_pb[e] = __ldg(B.ptr1 + b0 + e);
+    for (uint32_t e = tid; e < nb; e += kThreads) s_yb[e] = __ldg(B.idx1 + b0 + e);
+  }
+  if (xsa) {
+    for (uint32_t e = tid; e < nsa; e += kThreads) {
+      s_xpa[e] = __ldg(A.ptr2 + sa0 + e);
+      s_xa[e] = __ldg(A.idx2 + sa0 + e);
+    }
+  }
+  if (xsb) {
+    for (uint32_t e = tid; e < nsb; e += kThreads) {
+      s_xpb[e] = __ldg(B.ptr2 + sb0 + e);
+      s_xb[e] = __ldg(B.idx2 + sb0 + e);
+    }
+  }
+  __syncthreads();
+  // voxel keys: each column's key (its slab by a search of the tile's slabs)
+  // over its Y_pointer range, clamped to the tile's z range
+  for (uint32_t e = tid; e < na; e += kThreads) {
+    uint32_t x;
+    if (xsa) {
+      uint32_t lo = 0, hi = nsa - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (s_xpa[mid] <= a0 + e) lo = mid; else hi = mid - 1;
+      }
+      x = s_xa[lo];
+    } else {
+      x = __ldg(A.idx2 + search_le(A.ptr2, sa0, saL, a0 + e));
+    }
+    const unsigned long long ck = (unsigned long long)((x << b) | s_ya[e]) << 16;
+    const uint32_t q0 = max(s_pa[e], zA0), q1 = min(s_pa[e + 1], zA1);
+    for (uint32_t q = q0; q < q1; ++q) s_va[q - zA0] |= ck;
+  }
+  for (uint32_t e = tid; e < nb; e += kThreads) {
+    uint32_t x;
+    if (xsb) {
+      uint32_t lo = 0, hi = nsb - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (s_xpb[mid] <= b0 + e) lo = mid; else hi = mid - 1;
+      }
+      x = s_xb[lo];
+    } else {
+      x = __ldg(B.idx2 + search_le(B.ptr2, sb0, sbL, b0 + e));
+    }
+    const unsigned long long ck = (unsigned long long)((x << b) | s_yb[e]) << 16;
+    const uint32_t q0 = max(s_pb[e], zB0), q1 = min(s_pb[e + 1], zB1);
+    for (uint32_t q = q0; q < q1; ++q) s_vb[q - zB0] |= ck;
+  }
+  __syncthreads();
+  // merge path over the tile's voxels (A first on equal keys), the same
+  // number of merged positions for every thread
+  const uint32_t nv = nva + nvb;
+  const uint32_t per = (nv + kThreads - 1) / kThreads;
+  const uint32_t diag = min(tid * per, nv), dend = min(diag + per, nv);
+  uint32_t i0, j0;
+  {
+    uint32_t lo = diag > nvb ? diag - nvb : 0u, hi = min(diag, nva);
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_va[mid] <= s_vb[diag - 1 - mid]) lo = mid + 1; else hi = mid;
+    }
+    i0 = lo;
+    j0 = diag - lo;
+  }
+  // the merged voxel before the thread's first one: the larger of the last
+  // taken of A and of B; before the tile's first voxel, a key whose column
+  // differs and whose x differs exactly when no column precedes the tile or
+  // the preceding column's x differs
+  unsigned long long pk0;
+  if (diag > 0) {
+    pk0 = 0;
+    if (i0 > 0) pk0 = s_va[i0 - 1];
+    if (j0 > 0) pk0 = max(pk0, s_vb[j0 - 1]);
+  } else {
+    pk0 = s_vhasprev ? (((unsigned long long)s_vprevck << 16) | 0xffffull) : ~0ull;
+  }
+  // first walk: the merge decisions and, against the previous merged key,
+  // whether each voxel is new (not B's copy of A's), opens a column, opens a
+  // slab; kept as bit masks for the second walk
+  const uint32_t cnt = dend - diag;  // at most 32
+  const uint32_t sh = 16 + b;
+  uint32_t mA = 0, mU = 0, mC = 0, mS = 0, cv = 0, cc = 0, cs = 0;
+  {
+    uint32_t i = i0, j = j0;
+    unsigned long long ka = i < nva ? s_va[i] : ~0ull, kb = j < nvb ? s_vb[j] : ~0ull, pk = pk0;
+    for (uint32_t q = 0; q < cnt; ++q) {
+      const bool takeA = ka <= kb;  // keys are below 2^48: ~0 marks an input used up
+      const unsigned long long k = takeA ? ka : kb;
+      if (takeA) {
+        ++i;
+        ka = i < nva ? s_va[i] : ~0ull;
+      } else {
+        ++j;
+        kb = j < nvb ? s_vb[j] : ~0ull;
+      }
+      const unsigned long long d = k ^ pk;
+      const uint32_t u = d != 0ull, c = (d >> 16) != 0ull, sl = (d >> sh) != 0ull;
+      mA |= (uint32_t)takeA << q;
+      mU |= u << q;
+      mC |= c << q;
+      mS |= sl << q;
+      cv += u;
+      cc += c;
+      cs += sl;
+      pk = k;
+    }
+  }
+  unsigned long long tp = 0;
+  const unsigned long long op = block_excl_scan<unsigned long long>(
+      (unsigned long long)cv | ((unsigned long long)cc << 21) | ((unsigned long long)cs << 42), tp,
+      s_w64);
+  if (tid < 3) {
+    const uint32_t run = (uint32_t)((tp >> (21 * tid)) & kF);
+    uint32_t* my = clook + (size_t)t * 3 + tid;
+    uint32_t excl = 0;
+    if (lt == 0) {
+      st_relaxed(my, kFlagInc | run);
+    } else {
+      st_relaxed(my, kFlagAgg | run);
+      excl = lookback(clook + tid, 3, t, P.tile_base, &O.hdr->err);
+      st_relaxed(my, kFlagInc | ((excl + run) & kValMask));
+    }
+    s_vt[tid] = excl;
+    s_vt[3 + tid] = excl + run;
+  }
+  __syncthreads();
+  // second walk, replaying the masks: z entries to shared memory, column and
+  // slab entries out
+  const uint32_t vo0 = s_vt[0], co0 = s_vt[1], so0 = s_vt[2];
+  bool over = false;
+  {
+    uint32_t o = (uint32_t)(op & kF), c = co0 + (uint32_t)((op >> 21) & kF),
+             sx = so0 + (uint32_t)(op >> 42);
+    uint32_t i = i0, j = j0;
+    for (uint32_t q = 0; q < cnt; ++q) {
+      const bool takeA = (mA >> q) & 1u;
+      const unsigned long long k = *(takeA ? s_va + i : s_vb + j);
+      i += takeA ? 1u : 0u;
+      j += takeA ? 0u : 1u;
+      if (!((mU >> q) & 1u)) continue;
+      s_oz[o] = (uint16_t)k;
+      if ((mC >> q) & 1u) {
+        const uint32_t col = (uint32_t)(k >> 16);
+        if ((mS >> q) & 1u) {
+          if (sx < O.cap2) {
+            O.idx2[sx] = (uint16_t)(col >> b);
+            O.ptr2[sx] = c;
+          } else {
+            over = true;
+          }
+          ++sx;
+        }
+        if (c < O.cap1) {
+          O.idx1[c] = (uint16_t)(col & ymask);
+          O.ptr1[c] = vo0 + o;
+        } else {
+          over = true;
+        }
+        ++c;
+      }
+      ++o;
+    }
+  }
+  __syncthreads();
+  const uint32_t nu = (uint32_t)(tp & kF);
+  for (uint32_t e = tid; e < nu; e += kThreads) {
+    if (vo0 + e < O.cap) O.idx0[vo0 + e] = s_oz[e]; else over = true;
+  }
+  if (over) atomicOr(&O.hdr->err, kErrInternal);
+  if (lt == nt - 1 && tid == 0) {
+    const uint32_t U = s_vt[3], G = s_vt[4], H = s_vt[5];
+    if (G <= O.cap1) O.ptr1[G] = U;
+    if (H <= O.cap2) O.ptr2[H] = G;
+    O.hdr->cnt[0] = U;
+    O.hdr->cnt[1] = G;
+    O.hdr->cnt[2] = H;
+  }
+}
+
 // Merge tiles by the resident blocks: each takes tile ids from the counter in
 // launch order until the reserved tiles are handed out (tiles beyond a
 // pair's actual count are skipped), so the look-back always finds its
@@ -411,19 +741,20 @@ __global__ void __launch_bounds__(kThreads, 4) k_merge_tiles(const MergePair* __
                                                           const uint32_t* __restrict__ ntiles,
                                                           uint32_t* clook, uint32_t* counter,
                                                           uint32_t total_tiles) {
+  __shared__ __align__(16) unsigned char s_raw[merge_smem_bytes<MH>()];
   __shared__ uint32_t s_tile;
   __shared__ int s_p;
   for (;;) {
     __syncthreads();  // the previous tile's shared data is read no more
     if (threadIdx.x == 0) {
-      const uint32_t t = atomicAdd(counter, 1u);
-      s_tile = t;
-      s_p = t < total_tiles ? find_pair_tile(pairs, S, t) : 0;
+      int p;
+      s_tile = next_merge_tile(pairs, S, ntiles, counter, total_tiles, p);
+      s_p = p;
     }
     __syncthreads();
     const uint32_t t = s_tile;
     if (t >= total_tiles) return;
-    merge_tile<MH>(pairs, S, bounds, ntiles, clook, t, s_p);
+    merge_tile_v<MH>(pairs, S, bounds, ntiles, clook, t, s_p, s_raw);
   }
 }
 
@@ -631,9 +962,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_kmerge_tiles(const MergePair* _
   for (;;) {
     __syncthreads();  // the previous tile's shared data is read no more
     if (threadIdx.x == 0) {
-      const uint32_t t = atomicAdd(counter, 1u);
-      s_tile = t;
-      s_p = t < total_tiles ? find_pair_tile(pairs, S, t) : 0;
+      int p;
+      s_tile = next_merge_tile(pairs, S, ntiles, counter, total_tiles, p);
+      s_p = p;
     }
     __syncthreads();
     const uint32_t t = s_tile;
