@@ -256,6 +256,40 @@ def base_line(args, world_size, metric, value, unit, ms_per_step, config, data):
             "data": data, "config": config}
 
 
+def check_e2e(torch, P):
+    """The results the end-to-end steps copied back equal the device results."""
+    torch.cuda.synchronize()
+    if not (torch.equal(P.h_idx, P.idx.cpu()) and torch.equal(P.h_d2, P.d2.cpu())):
+        raise RuntimeError("end-to-end NN results differ from the device results")
+
+
+def overlapped_e2e(P, h_clouds, d_clouds):
+    """One step from pinned host buffers to results in pinned host memory, as
+    a user would run it: the clouds go up first (the build needs them); the
+    queries go up on a side stream while the clouds are built, merged and
+    projected; the NN results come down on that stream while the merged cloud
+    is decoded.  The current stream waits for the side stream before the
+    query sort and at the end, so every copy lies inside the caller's timed
+    region, and the next step's writes wait for this step's reads."""
+    torch = P.torch
+    main = torch.cuda.current_stream()
+    side = P.side
+    for h, d in zip(h_clouds, d_clouds):
+        d.copy_(h, non_blocking=True)
+    side.wait_stream(main)
+    with torch.cuda.stream(side):
+        P.d_q.copy_(P.h_q, non_blocking=True)
+
+    def results_down():
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            P.h_idx.copy_(P.idx, non_blocking=True)
+            P.h_d2.copy_(P.d2, non_blocking=True)
+
+    P.step(timed_events=False, before_sort=lambda: main.wait_stream(side), after_nn=results_down)
+    main.wait_stream(side)
+
+
 # --------------------------------------------------------------- GPU arm: C2
 class LidarStep:
     def __init__(self, scene, queries, torch, cga):
@@ -276,8 +310,9 @@ class LidarStep:
         self.dec = torch.empty((self.n_points, 3), dtype=torch.int32, device="cuda")
         self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         self.nn_shift = ()  # NN coarse levels picked by cga_nn_autotune before timing
+        self.side = torch.cuda.Stream()  # host copies overlapped with the step (e2e_step)
 
-    def step(self, timed_events=True, batched=True):
+    def step(self, timed_events=True, batched=True, before_sort=None, after_nn=None):
         cga, ev = self.cga, self.ev
         rec = (lambda i: ev[i].record()) if timed_events else (lambda i: None)
         rec(0)
@@ -304,10 +339,14 @@ class LidarStep:
         proj = cga.cga_project(world, "xy", allocator=None)
         rec(3)
         cga.cga_nn_prepare(world, self.nn_shift)
+        if before_sort is not None:
+            before_sort()
         cga.cga_nn_sort_queries(world, self.d_q, self.order)
         rec(4)
         cga.cga_nn_query_ordered(world, self.d_q, self.order, self.idx, self.d2)
         rec(5)
+        if after_nn is not None:
+            after_nn()
         cga.cga_decode(world, out=self.dec)
         rec(6)
         self.last = (sweeps, merges, world, proj)
@@ -317,12 +356,7 @@ class LidarStep:
         return [e[i].elapsed_time(e[i + 1]) for i in range(6)]
 
     def e2e_step(self):
-        for h, d in zip(self.h_sweeps, self.d_sweeps):
-            d.copy_(h, non_blocking=True)
-        self.d_q.copy_(self.h_q, non_blocking=True)
-        self.step(timed_events=False)
-        self.h_idx.copy_(self.idx, non_blocking=True)
-        self.h_d2.copy_(self.d2, non_blocking=True)
+        overlapped_e2e(self, self.h_sweeps, self.d_sweeps)
 
     def bytes_in(self):
         return sum(h.numel() * 4 for h in self.h_sweeps) + self.h_q.numel() * 4
@@ -403,6 +437,7 @@ def run_lidar(args, rank, world_size, local_rank, torch, dist, cga):
         torch.cuda.synchronize()
         e2e_ms.append(timed(torch, P.e2e_step, flush, float(k)))
     clk = clocks.stop()
+    check_e2e(torch, P)
 
     sweeps, merges, world, proj = P.last
     winfo = world.info()
@@ -502,8 +537,9 @@ class SurfaceStep:
         self.dec = torch.empty((S_POINTS, 3), dtype=torch.int32, device="cuda")
         self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         self.nn_strategy = "tree"  # replaced by cga_nn_autotune's choice before timing
+        self.side = torch.cuda.Stream()  # host copies overlapped with the step (e2e_step)
 
-    def step(self, timed_events=True):
+    def step(self, timed_events=True, before_sort=None, after_nn=None):
         cga, ev = self.cga, self.ev
         rec = (lambda i: ev[i].record()) if timed_events else (lambda i: None)
         rec(0)
@@ -514,10 +550,14 @@ class SurfaceStep:
         pr = cga.cga_project_batch([mg] * 3, ["xy", "xz", "yz"], allocator=None)
         rec(3)
         cga.cga_nn_prepare(mg, self.nn_strategy)
+        if before_sort is not None:
+            before_sort()
         cga.cga_nn_sort_queries(mg, self.d_q, self.order)
         rec(4)
         cga.cga_nn_query_ordered(mg, self.d_q, self.order, self.idx, self.d2)
         rec(5)
+        if after_nn is not None:
+            after_nn()
         cga.cga_decode(mg, out=self.dec)
         rec(6)
         self.last = (a, b, mg, pr)
@@ -527,12 +567,7 @@ class SurfaceStep:
         return [e[i].elapsed_time(e[i + 1]) for i in range(6)]
 
     def e2e_step(self):
-        for h, d in zip(self.h_halves, self.d_halves):
-            d.copy_(h, non_blocking=True)
-        self.d_q.copy_(self.h_q, non_blocking=True)
-        self.step(timed_events=False)
-        self.h_idx.copy_(self.idx, non_blocking=True)
-        self.h_d2.copy_(self.d2, non_blocking=True)
+        overlapped_e2e(self, self.h_halves, self.d_halves)
 
     def bytes_in(self):
         return sum(h.numel() * 4 for h in self.h_halves) + self.h_q.numel() * 4
@@ -586,6 +621,7 @@ def run_surface(args, world_size, local_rank, torch, dist, cga):
         torch.cuda.synchronize()
         e2e_ms.append(timed(torch, P.e2e_step, flush, float(k)))
     clk = clocks.stop()
+    check_e2e(torch, P)
 
     a, b, mg, pr = P.last
     ai, bi, mi = a.info(), b.info(), mg.info()
