@@ -40,18 +40,19 @@ __global__ void __launch_bounds__(kThreads) k_decode(Levels a, uint32_t* __restr
 }
 
 // ------------------------------------------------------------------- merge
-// Merge (Eq. 1, Sec. V-A) of pairs of CGAs in one grid, column by column.
-// The (x, y) columns of both inputs are merged in key order (key x << b | y);
-// a column present in both gets the union of its two sorted z lists, a column
-// of one input keeps its z list.  Splitters sit at every `half`-th column of
-// each input; a cut at column key s takes, from both inputs, the columns with
-// key < s, so a column present in both never straddles two tiles and every
-// tile can settle its columns alone.  Per tile: the columns' keys (slab of
-// each column by a scatter of slab starts and a block max-scan), merge path,
-// per output column its voxel count, block scans, and one decoupled look-back
-// over the pair's tiles for the voxel, column and slab offsets; then each
-// output column writes its y, its Y_pointer and its z list, and each new x its
-// X_index and X_pointer entries.
+// Merge (Eq. 1, Sec. V-A) of pairs of CGAs in one grid, in tiles cut at
+// column boundaries.  The (x, y) columns of both inputs are in key order (key
+// x << b | y); a column present in both gets the union of its two sorted z
+// lists, a column of one input keeps its z list.  Splitters sit at every
+// `half`-th column of each input; a cut at column key s takes, from both
+// inputs, the columns with key < s, so a column present in both never
+// straddles two tiles and every tile can settle its columns alone.  A tile
+// merges its voxels by (column key, z) keys (merge_tile_v), or, when its
+// columns hold more voxels than shared memory stages, column by column
+// (merge_tile); either way one packed block scan and one decoupled look-back
+// over the pair's tiles give its voxel, column and slab offsets, and it
+// writes its z entries, each output column's y and Y_pointer, and each new
+// x's X_index and X_pointer entries.
 __device__ __forceinline__ int find_pair_spl(const MergePair* __restrict__ P, int S, uint32_t i) {
   int lo = 0, hi = S - 1;
   while (lo < hi) {
