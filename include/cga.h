@@ -236,8 +236,7 @@ int cga_nn_query_ordered(const cga_t* a, const float* d_q, uint64_t m, const uin
  * queries and the outputs exactly as for cga_nn_query.
  * The first call on a device looks up the array's device address (once per
  * device).  Each call copies its small segment tables from host memory into
- * the array (cudaMemcpyAsync), so the call is not meant to be recorded into a
- * CUDA graph by stream capture.  A search structure that cga_nn_prepare_levels
+ * the array (cudaMemcpyAsync).  A search structure that cga_nn_prepare_levels
  * built on `a` (x directory, column table, coarse levels or occupancy tree)
  * is used as cga_nn_query uses it.  All calls share
  * the one array and each call resets what it needs, so calls whose work
