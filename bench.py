@@ -538,12 +538,16 @@ class SurfaceStep:
         self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         self.nn_strategy = "tree"  # replaced by cga_nn_autotune's choice before timing
         self.side = torch.cuda.Stream()  # host copies overlapped with the step (e2e_step)
+        self.half_up = torch.cuda.Event()
 
-    def step(self, timed_events=True, before_sort=None, after_nn=None):
+    def step(self, timed_events=True, before_sort=None, after_nn=None, build=None):
         cga, ev = self.cga, self.ev
         rec = (lambda i: ev[i].record()) if timed_events else (lambda i: None)
         rec(0)
-        a, b = cga.cga_build_batch(self.d_halves, self.grid, [None, None], allocator=None)
+        if build is None:
+            a, b = cga.cga_build_batch(self.d_halves, self.grid, [None, None], allocator=None)
+        else:
+            a, b = build()
         rec(1)
         mg = cga.cga_merge(a, b, allocator=None)
         rec(2)
@@ -567,7 +571,35 @@ class SurfaceStep:
         return [e[i].elapsed_time(e[i + 1]) for i in range(6)]
 
     def e2e_step(self):
-        overlapped_e2e(self, self.h_halves, self.d_halves)
+        """As overlapped_e2e, with the second half's upload overlapped too: it
+        goes up on the side stream while the first half is built, and the
+        halves are built by one cga_build each (the same CGAs as the batched
+        build)."""
+        torch, cga = self.torch, self.cga
+        main = torch.cuda.current_stream()
+        side = self.side
+        (h0, h1), (d0, d1) = self.h_halves, self.d_halves
+        d0.copy_(h0, non_blocking=True)
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            d1.copy_(h1, non_blocking=True)
+            self.half_up.record(side)
+            self.d_q.copy_(self.h_q, non_blocking=True)
+
+        def build():
+            a = cga.cga_build(d0, self.grid, allocator=None)
+            main.wait_event(self.half_up)
+            return a, cga.cga_build(d1, self.grid, allocator=None)
+
+        def results_down():
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                self.h_idx.copy_(self.idx, non_blocking=True)
+                self.h_d2.copy_(self.d2, non_blocking=True)
+
+        self.step(timed_events=False, before_sort=lambda: main.wait_stream(side),
+                  after_nn=results_down, build=build)
+        main.wait_stream(side)
 
     def bytes_in(self):
         return sum(h.numel() * 4 for h in self.h_halves) + self.h_q.numel() * 4
